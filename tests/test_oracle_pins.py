@@ -1,0 +1,451 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix (no GPU).
+
+Each test names the passage it pins. None of them re-types the oracle's formula: they use closed
+forms, invariants, special cases that reduce to a textbook method, brute force on tiny inputs and
+values the paper prints.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _rng(s):
+    return np.random.default_rng(1000 + s)
+
+
+def _planted(rng, m, n, r, noise=0.0):
+    W0 = rng.exponential(1.0, (m, r))
+    H0 = rng.exponential(1.0, (r, n))
+    X = W0 @ H0
+    if noise:
+        X = np.maximum(0.0, X + noise * X.std() * rng.standard_normal(X.shape))
+    return X, W0, H0
+
+
+# ---------------------------------------------------------------- QR (Section 3, Eq. 3.4-3.5)
+
+def _mgs2(Y):
+    """Modified Gram-Schmidt applied twice: an independent QR with positive R diagonal."""
+    Q = np.array(Y, dtype=np.float64)
+    for _ in range(2):
+        for j in range(Q.shape[1]):
+            for i in range(j):
+                Q[:, j] -= (Q[:, i] @ Q[:, j]) * Q[:, i]
+            Q[:, j] /= np.linalg.norm(Q[:, j])
+    return Q
+
+
+@pytest.mark.parametrize("shape", [(50, 8), (200, 18), (33, 33)])
+def test_qr_orthonormal_and_reconstructs(shape):
+    Y = _rng(0).standard_normal(shape)
+    Q = O.qr_orthonormal(Y)
+    assert np.abs(Q.T @ Q - np.eye(shape[1])).max() <= 1e-12
+    R = Q.T @ Y
+    assert np.abs(np.tril(R, -1)).max() <= 1e-12          # R upper triangular
+    assert (np.diag(R) >= 0).all()                          # sign convention
+    assert np.linalg.norm(Q @ R - Y) / np.linalg.norm(Y) <= 1e-13
+
+
+def test_qr_unique_positive_diagonal_matches_gram_schmidt():
+    Y = _rng(1).standard_normal((60, 10))
+    assert np.abs(O.qr_orthonormal(Y) - _mgs2(Y)).max() <= 1e-12
+
+
+# ---------------------------------------------------------------- sketch (Section 3, 3.1)
+
+def test_power_product_singular_values_are_raised_to_2w_plus_1():
+    """Section 3: sigma_j((X X^T)^w X) = sigma_j(X)^(2w+1). With Omega = I the oracle's
+    literal Eq. 3.5 product must show exactly this spectrum."""
+    X = _rng(2).uniform(0.0, 1.0, (30, 20)) / 3.0
+    s = np.linalg.svd(X, compute_uv=False)
+    for w in (0, 1, 2, 3):
+        P = O.power_product(X, np.eye(20), w)
+        sp = np.linalg.svd(P, compute_uv=False)
+        # SVD is accurate to eps * sigma_1 in absolute terms
+        np.testing.assert_allclose(sp, s ** (2 * w + 1), rtol=1e-10, atol=1e-14 * sp[0])
+
+
+@pytest.mark.parametrize("w", [0, 1, 2, 3])
+def test_sketch_captures_exact_low_rank(w):
+    """Closed form: for X of exact rank r <= l, range(Q_L) contains range(X) and range(Q_R)
+    contains range(X^T), so both projections reproduce X (Section 3.1: min(d,n) >> l > k)."""
+    rng = _rng(3)
+    X, _, _ = _planted(rng, 120, 90, 5)
+    oL, oR = rng.standard_normal((90, 9)), rng.standard_normal((120, 9))
+    QL, QR = O.sketch(X, oL, oR, w)
+    assert QL.shape == (120, 9) and QR.shape == (90, 9)
+    nx = np.linalg.norm(X)
+    assert np.linalg.norm(QL @ (QL.T @ X) - X) / nx <= 1e-12
+    assert np.linalg.norm((X @ QR) @ QR.T - X) / nx <= 1e-12
+
+
+def test_sketch_span_equals_literal_power_product():
+    """The re-orthonormalised chain spans the same subspace as Eq. 3.5's literal product
+    (well-conditioned case, where the literal product keeps all directions)."""
+    rng = _rng(4)
+    X = rng.uniform(0.5, 1.0, (40, 30)) + 3.0 * np.eye(40, 30)
+    oL, oR = rng.standard_normal((30, 6)), rng.standard_normal((40, 6))
+    for w in (0, 1):
+        QL, QR = O.sketch(X, oL, oR, w)
+        PL = O.qr_orthonormal(O.power_product(X, oL, w))
+        PR = O.qr_orthonormal(O.power_product(X.T, oR, w))
+        assert np.abs(QL @ QL.T - PL @ PL.T).max() <= 1e-9
+        assert np.abs(QR @ QR.T - PR @ PR.T).max() <= 1e-9
+
+
+def test_sketch_right_chain_is_left_chain_of_transpose():
+    """Section 3.1: R comes from P(X^T). A transposed operand in either chain breaks this."""
+    rng = _rng(5)
+    X = rng.uniform(0, 1, (70, 50))
+    oL, oR = rng.standard_normal((50, 7)), rng.standard_normal((70, 7))
+    QL, QR = O.sketch(X, oL, oR, 2)
+    QL2, QR2 = O.sketch(X.T, oR, oL, 2)
+    assert np.abs(QR - QL2).max() <= 1e-10
+    assert np.abs(QL - QR2).max() <= 1e-10
+
+
+def test_power_iterations_reduce_tail_error():
+    """Section 3: power iterations sharpen the spectrum, so the projection error of a matrix
+    with a slowly decaying spectrum does not grow with w (median over seeds)."""
+    rng = _rng(6)
+    U, _ = np.linalg.qr(rng.standard_normal((200, 60)))
+    V, _ = np.linalg.qr(rng.standard_normal((150, 60)))
+    X = (U * (np.arange(1, 61) ** -0.5)) @ V.T
+    errs = {w: [] for w in (0, 1, 3)}
+    for s in range(20):
+        oL = np.random.default_rng(s).standard_normal((150, 12))
+        oR = np.random.default_rng(100 + s).standard_normal((200, 12))
+        for w in errs:
+            QL, _ = O.sketch(X, oL, oR, w)
+            errs[w].append(np.linalg.norm(X - QL @ (QL.T @ X)))
+    med = {w: np.median(v) for w, v in errs.items()}
+    assert med[3] <= med[1] <= med[0]
+    # and never below the optimal rank-12 error (Eckart-Young)
+    s = np.linalg.svd(X, compute_uv=False)
+    assert med[3] >= np.sqrt(np.sum(s[12:] ** 2)) * (1 - 1e-12)
+
+
+def test_compress_with_square_projections_is_lossless():
+    """l = min(m, n) = m = n: Q_L, Q_R are orthogonal, so Q_L X_hat = X and X_chk Q_R^T = X."""
+    rng = _rng(7)
+    X = rng.uniform(0, 1, (16, 16))
+    QL, QR = O.sketch(X, rng.standard_normal((16, 16)), rng.standard_normal((16, 16)), 1)
+    Xhat, Xchk = O.compress(X, QL, QR)
+    assert np.abs(QL @ Xhat - X).max() <= 1e-12
+    assert np.abs(Xchk @ QR.T - X).max() <= 1e-12
+
+
+# ---------------------------------------------------------------- FastHALS-RP (Section 4)
+
+def _compressed(seed, m=40, n=30, r=4, ell=9, w=2, noise=0.05):
+    rng = _rng(seed)
+    X, _, _ = _planted(rng, m, n, r, noise)
+    QL, QR = O.sketch(X, rng.standard_normal((n, ell)), rng.standard_normal((m, ell)), w)
+    Xhat, Xchk = O.compress(X, QL, QR)
+    W = rng.uniform(0, 1, (m, r))
+    H = rng.uniform(0, 1, (r, n))
+    return X, QL, QR, Xhat, Xchk, W, H
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_fasthals_rp_equals_hals_rp_with_explicit_residuals(seed):
+    """Eq. fastHALS_a is Eq. hals_update with Eq. 4.6 substituted: the two forms agree."""
+    _, QL, QR, Xhat, Xchk, W, H = _compressed(seed)
+    for _ in range(5):
+        Wf, Hf = O.fasthals_rp_step(W, H, QL, QR, Xhat, Xchk)
+        Wh, Hh = O.hals_rp_step(W, H, QL, QR, Xhat, Xchk, order="block")
+        assert np.abs(Wf - Wh).max() <= 1e-12 * max(1.0, np.abs(Wh).max())
+        assert np.abs(Hf - Hh).max() <= 1e-11 * max(1.0, np.abs(Hh).max())
+        W, H = Wf, Hf
+
+
+def test_fasthals_rp_with_square_projections_is_fasthals():
+    """l = m = n: the compressed problem is the full one; FastHALS-RP reduces to FastHALS,
+    which in turn equals HALS (Algorithm 2, Eq. 2.2_3) with explicit component residuals."""
+    rng = _rng(8)
+    X, _, _ = _planted(rng, 14, 14, 3, 0.05)
+    QL, QR = O.sketch(X, rng.standard_normal((14, 14)), rng.standard_normal((14, 14)), 1)
+    Xhat, Xchk = O.compress(X, QL, QR)
+    W, H = rng.uniform(0, 1, (14, 3)), rng.uniform(0, 1, (3, 14))
+    for _ in range(5):
+        Wc, Hc = O.fasthals_rp_step(W, H, QL, QR, Xhat, Xchk)
+        Wf, Hf = O.fasthals_step(W, H, X)
+        assert np.abs(Wc - Wf).max() <= 1e-11 and np.abs(Hc - Hf).max() <= 1e-10
+        # HALS with explicit X_j = X - A B^T + a_j b_j^T (identity projections)
+        I = np.eye(14)
+        Wh, Hh = O.hals_rp_step(W, H, I, I, X, X, order="block")
+        assert np.abs(Wh - Wf).max() <= 1e-11 and np.abs(Hh - Hf).max() <= 1e-10
+        W, H = Wf, Hf
+
+
+def _golden_min(f, lo, hi, tol=1e-13):
+    g = (np.sqrt(5) - 1) / 2
+    a, b = lo, hi
+    c, d = b - g * (b - a), a + g * (b - a)
+    while b - a > tol * max(1.0, abs(b)):
+        if f(c) < f(d):
+            b, d = d, c
+            c = b - g * (b - a)
+        else:
+            a, c = c, d
+            d = a + g * (b - a)
+    return 0.5 * (a + b)
+
+
+def test_fasthals_rp_step_matches_brute_force_minimisers():
+    """Algorithm 4 lines 3-4 define each update as the argmin over a_j >= 0 (b_j >= 0) of the
+    compressed component cost. Solve every scalar sub-problem by golden-section search on the
+    cost itself (no closed form), in block order with the compensated normalisation, and compare
+    with one oracle step."""
+    _, QL, QR, Xhat, Xchk, W, H = _compressed(3, m=12, n=10, r=3, ell=6)
+    A, B = W.copy(), H.T.copy()
+    R = QR.T
+    k = A.shape[1]
+    for j in range(k):
+        Bc = R @ B
+        Xc_j = Xchk - A @ Bc.T + np.outer(A[:, j], Bc[:, j])
+        for i in range(A.shape[0]):
+            f = lambda a: np.sum((Xc_j[i] - a * Bc[:, j]) ** 2)
+            A[i, j] = _golden_min(f, 0.0, 50.0)
+    s = np.linalg.norm(A, axis=0)
+    A /= s
+    B *= s
+    for j in range(k):
+        Ah = QL.T @ A
+        Xh_j = Xhat - Ah @ B.T + np.outer(Ah[:, j], B[:, j])
+        for c in range(B.shape[0]):
+            f = lambda b: np.sum((Xh_j[:, c] - b * Ah[:, j]) ** 2)
+            B[c, j] = _golden_min(f, 0.0, 200.0)
+    Wo, Ho = O.fasthals_rp_step(W, H, QL, QR, Xhat, Xchk)
+    np.testing.assert_allclose(A, Wo, atol=1e-6)
+    np.testing.assert_allclose(B.T, Ho, atol=1e-5)
+
+
+def test_each_component_update_satisfies_kkt():
+    """Eq. hals_a / hals_b: the update zeroes the gradient where the entry is positive and
+    leaves it non-negative where the entry is clamped. In an interleaved Algorithm 4 sweep the
+    last update (b_k) is an exact minimiser given everything else; the gradient is formed from
+    the explicit residual of Eq. 4.6."""
+    _, QL, QR, Xhat, Xchk, W, H = _compressed(4)
+    for _ in range(3):
+        A2, H2 = O.hals_rp_step(W, H, QL, QR, Xhat, Xchk, order="interleaved", normalize=False)
+        B2 = H2.T
+        jl = A2.shape[1] - 1
+        Ah = QL.T @ A2
+        Xh = Xhat - Ah @ B2.T + np.outer(Ah[:, jl], B2[:, jl])
+        gb = B2[:, jl] * (Ah[:, jl] @ Ah[:, jl]) - Xh.T @ Ah[:, jl]      # Eq. hals_b
+        pos = B2[:, jl] > 0
+        scale = np.abs(Xh.T @ Ah[:, jl]).max()
+        assert np.abs(gb[pos]).max(initial=0) <= 1e-11 * scale
+        assert (gb[~pos] >= -1e-11 * scale).all()
+        W, H = O.fasthals_rp_step(W, H, QL, QR, Xhat, Xchk)
+    # W half-step of a single component (r = 1) is an exact NNLS solve, Eq. hals_a
+    _, QL, QR, Xhat, Xchk, W, H = _compressed(5, r=1)
+    Wn, _ = O.hals_rp_step(W, H, QL, QR, Xhat, Xchk, order="block", normalize=False)
+    bc = (H @ QR)[0]
+    ga = Wn[:, 0] * (bc @ bc) - Xchk @ bc
+    pos = Wn[:, 0] > 0
+    sc = np.abs(Xchk @ bc).max()
+    assert np.abs(ga[pos]).max(initial=0) <= 1e-11 * sc and (ga[~pos] >= -1e-11 * sc).all()
+
+
+def test_normalisation_keeps_product_and_unit_columns():
+    """Section 4 (after Eq. fastHALS_a): a_j <- a_j / ||a_j||. With the scale moved to b_j, the
+    iteration is invariant: W H after one step is the same with or without normalisation, and
+    the normalised W has unit columns."""
+    _, QL, QR, Xhat, Xchk, W, H = _compressed(6)
+    for _ in range(4):
+        Wn, Hn = O.fasthals_rp_step(W, H, QL, QR, Xhat, Xchk, normalize=True)
+        Wu, Hu = O.fasthals_rp_step(W, H, QL, QR, Xhat, Xchk, normalize=False)
+        assert np.abs(Wn @ Hn - Wu @ Hu).max() <= 1e-11 * np.abs(Wu @ Hu).max()
+        nz = np.linalg.norm(Wn, axis=0) > 0
+        np.testing.assert_allclose(np.linalg.norm(Wn, axis=0)[nz], 1.0, atol=1e-14)
+        W, H = Wn, Hn
+
+
+def test_regularised_update_reduces_to_plain_and_sparsifies():
+    """Section 4.1: alpha = beta = 0 is Eq. fastHALS_a; a large alpha zeroes H (the l1 term's
+    soft threshold exceeds every correlation)."""
+    _, QL, QR, Xhat, Xchk, W, H = _compressed(7)
+    W1, H1 = O.fasthals_rp_step(W, H, QL, QR, Xhat, Xchk)
+    W2, H2 = O.fasthals_rp_step(W, H, QL, QR, Xhat, Xchk, alpha=0.0, beta=0.0)
+    assert np.array_equal(W1, W2) and np.array_equal(H1, H2)
+    _, H3 = O.fasthals_rp_step(W, H, QL, QR, Xhat, Xchk, alpha=1e6)
+    assert np.all(H3 == 0.0)
+    # the regularised b_j minimises 1/2||X_hat_j - a b^T||^2 + alpha|b|_1 + beta/2|b|^2 per entry
+    alpha, beta = 0.3, 0.7
+    _, QL, QR, Xhat, Xchk, W, H = _compressed(8, r=1)
+    Wn, Hn = O.fasthals_rp_step(W, H, QL, QR, Xhat, Xchk, alpha=alpha, beta=beta)
+    ah = (QL.T @ Wn)[:, 0]
+    for c in range(Xhat.shape[1]):
+        f = lambda b: 0.5 * np.sum((Xhat[:, c] - b * ah) ** 2) + alpha * abs(b) + 0.5 * beta * b * b
+        assert abs(_golden_min(f, 0.0, 100.0) - Hn[0, c]) <= 1e-6
+
+
+def test_planted_exact_recovery():
+    """North-star pin: X = W0 H0 exactly, separable W0 (an r x r identity block), recovered by
+    FastHALS-RP to relative residual < 1e-8 from the best of a few random starts."""
+    rng = _rng(9)
+    m, n, r, ell = 40, 30, 3, 8
+    W0 = rng.uniform(0.0, 1.0, (m, r))
+    W0[:r] = 2.0 * np.eye(r)
+    H0 = rng.uniform(0.0, 1.0, (r, n))
+    H0[:, :r] += np.eye(r)
+    X = W0 @ H0
+    QL, QR = O.sketch(X, rng.standard_normal((n, ell)), rng.standard_normal((m, ell)), 2)
+    Xhat, Xchk = O.compress(X, QL, QR)
+    best = np.inf
+    for s in range(5):
+        g = np.random.default_rng(s)
+        W, H = g.uniform(0, 1, (m, r)), g.uniform(0, 1, (r, n))
+        for it in range(4000):
+            W, H = O.fasthals_rp_step(W, H, QL, QR, Xhat, Xchk)
+            if it % 200 == 199 and O.residual(X, W, H)[0] < 1e-9:
+                break
+        best = min(best, O.residual(X, W, H)[0])
+        if best < 1e-8:
+            break
+    assert best < 1e-8
+    assert (W >= 0).all() and (H >= 0).all()
+
+
+# ---------------------------------------------------------------- MU, MU-RP (Sections 2.1, 3.1)
+
+def test_lee_seung_mu_is_monotone():
+    """Multiplicative updates on the full data never increase J (Lee & Seung 2001, cited in
+    Section 2.1)."""
+    rng = _rng(10)
+    X, _, _ = _planted(rng, 30, 25, 4, 0.1)
+    W, H = rng.uniform(0.1, 1, (30, 4)), rng.uniform(0.1, 1, (4, 25))
+    J = O.objective(X, W, H)
+    for _ in range(200):
+        W, H = O.mu_step(W, H, X)
+        Jn = O.objective(X, W, H)
+        assert Jn <= J * (1 + 1e-12)
+        J = Jn
+    assert (W >= 0).all() and (H >= 0).all()
+
+
+def test_mu_rp_half_steps_are_monotone_in_their_own_objectives():
+    """Algorithm 3: line 2 minimises ||X R^T - A (R B)^T|| over A >= 0, line 3 minimises
+    ||L^T X - (L^T A) B^T|| over B >= 0. The semi-NMF rule (Ding, Li & Jordan 2010) never
+    increases the objective of the half-step it performs."""
+    _, QL, QR, Xhat, Xchk, W, H = _compressed(11, m=60, n=50, r=5, ell=12)
+    for _ in range(100):
+        Ht = H @ QR
+        jw0 = np.sum((Xchk - W @ Ht) ** 2)
+        Wn, Hn = O.mu_rp_step(W, H, QL, QR, Xhat, Xchk)
+        jw1 = np.sum((Xchk - Wn @ Ht) ** 2)
+        assert jw1 <= jw0 * (1 + 1e-12)
+        Wt = QL.T @ Wn
+        jh0 = np.sum((Xhat - Wt @ H) ** 2)
+        jh1 = np.sum((Xhat - Wt @ Hn) ** 2)
+        assert jh1 <= jh0 * (1 + 1e-12)
+        assert (Wn >= 0).all() and (Hn >= 0).all()
+        W, H = Wn, Hn
+
+
+def test_mu_rp_fixed_point_at_exact_factorisation():
+    """At X = W0 H0 (exact, positive factors) both semi-NMF ratios are 1: one step moves
+    neither factor."""
+    rng = _rng(12)
+    m, n, r, ell = 30, 20, 3, 8
+    W0, H0 = rng.uniform(0.5, 1.5, (m, r)), rng.uniform(0.5, 1.5, (r, n))
+    X = W0 @ H0
+    QL, QR = O.sketch(X, rng.standard_normal((n, ell)), rng.standard_normal((m, ell)), 1)
+    Xhat, Xchk = O.compress(X, QL, QR)
+    W1, H1 = O.mu_rp_step(W0, H0, QL, QR, Xhat, Xchk)
+    assert np.abs(W1 - W0).max() <= 1e-12 * 10 and np.abs(H1 - H0).max() <= 1e-12 * 10
+
+
+# ---------------------------------------------------------------- residual, monitor, init, Gini
+
+def test_residual_closed_form():
+    """Eq. 2.2 on a constructed case: X = 2 * ones, W H = ones -> ||X - WH||^2 = m n,
+    ||X||^2 = 4 m n, rel = 1/2, J = m n / 2."""
+    m, n = 7, 5
+    X = 2.0 * np.ones((m, n))
+    W, H = np.ones((m, 1)), np.ones((1, n))
+    rel, e2, x2 = O.residual(X, W, H)
+    assert rel == 0.5 and e2 == m * n and x2 == 4 * m * n
+    assert O.objective(X, W, H) == m * n / 2
+
+
+def test_compressed_error_estimate_is_exact_with_square_projection():
+    rng = _rng(13)
+    X = rng.uniform(0, 1, (12, 12))
+    QL, QR = O.sketch(X, rng.standard_normal((12, 12)), rng.standard_normal((12, 12)), 0)
+    Xhat, _ = O.compress(X, QL, QR)
+    W, H = rng.uniform(0, 1, (12, 3)), rng.uniform(0, 1, (3, 12))
+    _, e2, x2 = O.residual(X, W, H)
+    assert abs(O.compressed_sq_error(x2, QL, Xhat, W, H) - e2) <= 1e-10 * x2
+
+
+def test_nndsvd_rank_one_and_nonnegative():
+    """NNDSVD of a positive rank-1 matrix reproduces it with its first component."""
+    rng = _rng(14)
+    u, v = rng.uniform(0.5, 2, 25), rng.uniform(0.5, 2, 18)
+    X = np.outer(u, v)
+    QL, QR = O.sketch(X, rng.standard_normal((18, 6)), rng.standard_normal((25, 6)), 1)
+    Xhat, _ = O.compress(X, QL, QR)
+    W, H = O.nndsvd_compressed(QL, Xhat, 3)
+    assert np.abs(np.outer(W[:, 0], H[0]) - X).max() <= 1e-10
+    X2, _, _ = _planted(rng, 40, 30, 4, 0.1)
+    QL, QR = O.sketch(X2, rng.standard_normal((30, 10)), rng.standard_normal((40, 10)), 2)
+    Xhat, _ = O.compress(X2, QL, QR)
+    W, H = O.nndsvd_compressed(QL, Xhat, 4)
+    assert (W >= 0).all() and (H >= 0).all()
+    assert O.residual(X2, W, H)[0] < 0.9
+
+
+def test_gini_closed_forms():
+    """Section 5.1 Gini formula: all-equal entries give 0, a single non-zero gives 1 - 1/N."""
+    assert abs(O.gini(np.ones((4, 5)))) <= 1e-15
+    B = np.zeros((4, 5))
+    B[2, 3] = 7.0
+    assert abs(O.gini(B) - (1 - 1 / 20)) <= 1e-15
+    # half zeros, half equal values: the Lorenz-curve area gives exactly 1/2
+    assert abs(O.gini(np.array([[0.0, 3.0], [3.0, 0.0]])) - 0.5) <= 1e-15
+    # order of entries does not matter (the formula sorts)
+    B = np.random.default_rng(0).exponential(1.0, (6, 7))
+    assert O.gini(B) == O.gini(B.T[::-1])
+
+
+def test_memory_formula_matches_printed_tables():
+    """Section 4.2 Table 4.1 memory (2(r+r_ov)+k)(d+n) and (dn+dk+nk) against the values printed
+    in Tables 5.2 and 5.3 (tests/golden/table_memory.txt)."""
+    rows = [l.split() for l in open(os.path.join(GOLD, "table_memory.txt")) if l[0] != "#"]
+    for d, n, k, ell, p_rp, p_full, unit in rows:
+        d, n, k, ell = int(d), int(n), int(k), int(ell)
+        unit = float(unit)
+        # the tables print two significant digits, truncated (e.g. 172.8 -> 170, 53.6 -> 53)
+        def two_sig(v):
+            e = int(np.floor(np.log10(v)))
+            return int(np.floor(v / 10.0 ** (e - 1)) * 10 ** (e - 1))
+        assert two_sig(O.memory_floats_rp(d, n, k, ell) / unit) == int(p_rp)
+        assert two_sig((d * n + d * k + n * k) / unit) == int(p_full)
+
+
+# ---------------------------------------------------------------- generator for Omega
+
+def test_philox_known_answers():
+    rows = [l.split() for l in open(os.path.join(GOLD, "philox4x32_10_kat.txt")) if l[0] != "#"]
+    assert len(rows) == 3
+    for row in rows:
+        v = [int(x, 16) for x in row]
+        assert O.philox4x32_10(v[0:4], v[4:6]) == tuple(v[6:10])
+
+
+def test_philox_normal_box_muller_pairs():
+    """Box-Muller invariant: z0^2 + z1^2 = -2 ln u0 for the pair drawn from one Philox block;
+    sample moments of a few thousand draws are those of N(0,1)."""
+    Z = O.philox_normal(64, 40, seed=7, stream=1).ravel()
+    x = O.philox4x32_10((0, 0, 1, 0), (7, 0))
+    u0 = ((x[0] >> 8) + 0.5) * 2.0 ** -24
+    assert abs(Z[0] ** 2 + Z[1] ** 2 + 2 * np.log(u0)) <= 1e-12
+    assert abs(Z.mean()) < 0.06 and abs(Z.std() - 1) < 0.05
