@@ -1,0 +1,371 @@
+#!/usr/bin/env python3
+"""Benchmark: time to the FP32 path's relative error (within 1 %) on the dense 20000 x 5000, r = 20
+compressed-NMF workload (sketch width 40, 2 power iterations, FastHALS-RP, exact residual every
+10 iterations), BF16 tensor-core/warm-start path against the plain FP32 path.
+
+One step = one whole solve (sketch, compression, initialisation, iterations until the exact
+residual reaches the target) on X already resident in HBM. The target is 1.01 x the relative
+error the FP32 path reaches after 500 iterations from the seeded U[0,1) start (measured once,
+untimed). Prints one JSON line on rank 0.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle on the host cores on the same workload (a bounded
+sample, extrapolated to the whole solve). Multi-GPU runs are independent replicas (the workload is
+one problem; nothing is exchanged).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time to oracle rel. error (±1%) at 20000×5000 r=20: BF16+warm-start vs FP32"
+WORKLOAD = dict(m=20000, n=5000, r=20, ell=40, w=2, iters=500, residual_every=10)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", choices=["fp32", "bf16"], default=None,
+                    help="run one short solve (20 iterations) for a profiler's launch list")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+def workload_config(init, prec):
+    w = WORKLOAD
+    return {"workload": f"dense planted X {w['m']}x{w['n']} (Exp(1) factors, 1% noise), "
+                        f"r={w['r']}, sketch width {w['ell']}, w={w['w']}, FastHALS-RP",
+            "m": w["m"], "n": w["n"], "r": w["r"], "ell": w["ell"], "power_iters": w["w"],
+            "max_iters": w["iters"], "residual_every": w["residual_every"], "init": init,
+            "x_contraction_dtype": prec,
+            "target": "1.01 x FP32-path rel_err after 500 iterations from U[0,1) init",
+            "l2": "inputs larger than L2 (X is 400 MB FP32)"}
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- oracle baseline
+
+def oracle_timing(pr, sample_iters=20, sample_residuals=2):
+    """Time the FP64 oracle as it stands on the host cores: the full sketch and compression, a
+    sample of iterations and residuals, extrapolated to the 500-iteration solve with an exact
+    residual every 10 iterations (the oracle reaches its own final error at iteration 500)."""
+    import oracle as O
+    w = WORKLOAD
+    X = pr.X.astype(np.float64)
+    t0 = time.perf_counter()
+    QL, QR = O.sketch(X, pr.omega_L, pr.omega_R, w["w"])
+    Xhat, Xchk = O.compress(X, QL, QR)
+    t_sketch = time.perf_counter() - t0
+    W, H = pr.W0.astype(np.float64), pr.H0.astype(np.float64)
+    t0 = time.perf_counter()
+    W, H = O.iterate(W, H, QL, QR, Xhat, Xchk, sample_iters)
+    t_iter = (time.perf_counter() - t0) / sample_iters
+    t0 = time.perf_counter()
+    for _ in range(sample_residuals):
+        O.residual(X, W, H)
+    t_res = (time.perf_counter() - t0) / sample_residuals
+    checks = w["iters"] // w["residual_every"]
+    total = t_sketch + w["iters"] * t_iter + checks * t_res
+    cores = os.cpu_count()
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max((i.get("num_threads", 0) for i in threadpool_info()), default=cores) or cores
+    except Exception:
+        pass
+    sample = (f"full sketch+compression ({t_sketch:.2f} s), {sample_iters} FastHALS-RP iterations "
+              f"({t_iter * 1e3:.1f} ms each) and {sample_residuals} residuals ({t_res:.2f} s each), "
+              f"extrapolated to {w['iters']} iterations + {checks} residuals")
+    return total, cores, sample
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    from paper_1712_02248_gb300 import inputs
+    pr = inputs.dense_20k_5k(seed=args.seed)
+    vals = []
+    for i in range(args.warmup + args.steps):
+        total, cores, sample = oracle_timing(pr, sample_iters=10, sample_residuals=1)
+        if i >= args.warmup:
+            vals.append(total)
+    v = statistics.median(vals)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_config("given (U[0,1))", "f64"),
+        "cpu_baseline": {"value": v, "unit": "s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    from paper_1712_02248_gb300 import inputs
+    from paper_1712_02248_gb300 import nmf_rp as N
+
+    w = WORKLOAD
+    dev = torch.device("cuda", local_rank)
+    pr = inputs.dense_20k_5k(seed=args.seed)
+    m, n, r, ell = w["m"], w["n"], w["r"], w["ell"]
+    stream = torch.cuda.Stream(dev)
+    ctx = N.Context(local_rank, stream=stream)
+    X_host = torch.from_numpy(pr.X).pin_memory()
+    with torch.cuda.stream(stream):
+        X = X_host.to(dev, non_blocking=True)
+        W0 = torch.from_numpy(pr.W0).to(dev)
+        H0 = torch.from_numpy(pr.H0).to(dev)
+        W = torch.empty_like(W0)
+        H = torch.empty_like(H0)
+    stream.synchronize()
+
+    if args.profile:
+        p = N.params(m, n, r, ell, power_iters=w["w"], iters=20, rule="fasthals",
+                     prec=args.profile, seed=args.seed + 17, residual_every=10)
+        for _ in range(2):
+            with torch.cuda.stream(stream):
+                W.copy_(W0)
+                H.copy_(H0)
+            N.nmf_set_profiling(ctx, True)
+            e, it = N.nmf_solve(ctx, p, X, W, H, init="given")
+            N.nmf_set_profiling(ctx, False)
+            ph = N.nmf_phase_times(ctx, reset=True)
+        print(json.dumps({"profile": args.profile, "rel_err": e, "iters": it,
+                          "phase_ms": {k: v[0] for k, v in ph.items()},
+                          "phase_spans": {k: v[1] for k, v in ph.items()}}))
+        ctx.close()
+        return
+
+    def params(prec, target):
+        return N.params(m, n, r, ell, power_iters=w["w"], iters=w["iters"], rule="fasthals",
+                        prec=prec, seed=args.seed + 17, residual_every=w["residual_every"],
+                        target_rel_err=target)
+
+    def solve(prec, init, target):
+        with torch.cuda.stream(stream):
+            W.copy_(W0)
+            H.copy_(H0)
+        return N.nmf_solve(ctx, params(prec, target), X, W, H, init=init)
+
+    # calibration (untimed): FP32 path, 500 iterations, residual only at the end
+    p_cal = N.params(m, n, r, ell, power_iters=w["w"], iters=w["iters"], rule="fasthals",
+                     prec="fp32", seed=args.seed + 17, residual_every=0)
+    with torch.cuda.stream(stream):
+        W.copy_(W0)
+        H.copy_(H0)
+    e32, _ = N.nmf_solve(ctx, p_cal, X, W, H, init="given")
+    target = 1.01 * e32
+
+    # which warm starts this build offers
+    contenders = [("fp32", "given"), ("bf16", "given")]
+    try:
+        solve("bf16", "nndsvd", target)
+        contenders.append(("bf16", "nndsvd"))
+    except N.NmfError:
+        pass
+    headline = contenders[-1]
+
+    def timed(prec, init, steps, warmup, profile=False):
+        for _ in range(warmup):
+            solve(prec, init, target)
+        ts, its, errs = [], [], []
+        l0 = ctx.launches
+        if profile:
+            N.nmf_phase_times(ctx, reset=True)
+            N.nmf_set_profiling(ctx, True)
+        for _ in range(steps):
+            if world > 1:
+                torch.distributed.barrier()
+            stream.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            e, it = solve(prec, init, target)
+            b.record(stream)
+            stream.synchronize()
+            ts.append(a.elapsed_time(b) / 1e3)
+            its.append(it)
+            errs.append(e)
+        phases = None
+        if profile:
+            N.nmf_set_profiling(ctx, False)
+            phases = N.nmf_phase_times(ctx, reset=True)
+        return ts, its, errs, ctx.launches - l0, phases
+
+    results = {}
+    for prec, init in contenders:
+        if (prec, init) == headline:
+            continue
+        ts, its, errs, _, _ = timed(prec, init, args.steps, 1)
+        results[f"{prec}+{init}"] = {"s": statistics.median(ts), "iters": its[0],
+                                     "rel_err": errs[0]}
+
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    ts, its, errs, launches, phases = timed(*headline, args.steps, args.warmup, profile=True)
+    clk = clocks.stop()
+    t_local = statistics.median(ts)
+    if world > 1:
+        tt = torch.tensor([t_local], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_local = float(tt.item())
+    results[f"{headline[0]}+{headline[1]}"] = {"s": statistics.median(ts), "iters": its[0],
+                                               "rel_err": errs[0]}
+
+    # e2e: same solve through the public API with the host copy of X inside the timed region
+    Wh = torch.empty((m, r), dtype=torch.float32).pin_memory()
+    Hh = torch.empty((r, n), dtype=torch.float32).pin_memory()
+    e2e = []
+    for i in range(args.steps + 1):
+        stream.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        with torch.cuda.stream(stream):
+            X.copy_(X_host, non_blocking=True)
+        solve(*headline, target)
+        with torch.cuda.stream(stream):
+            Wh.copy_(W, non_blocking=True)
+            Hh.copy_(H, non_blocking=True)
+        b.record(stream)
+        stream.synchronize()
+        if i > 0:
+            e2e.append(a.elapsed_time(b) / 1e3)
+
+    # roofline of the dominant phase (CUDA events on the launching stream, timed region above)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    xbytes = m * n * (2 if headline[0] == "bf16" else 4)
+    alg = {  # algorithmic bytes per span
+        "dual_pass": xbytes + 4 * ell * (m + n) * 2,
+        "residual": 4 * m * n + 4 * r * (m + n),
+        "quantize": 6 * m * n,
+    }
+    shares = {k: v[0] for k, v in phases.items() if v[1] > 0}
+    dom = max(shares, key=shares.get)
+    hbm_phases = [k for k in sorted(shares, key=shares.get, reverse=True) if k in alg]
+    rl_phase = dom if dom in alg else hbm_phases[0]
+    ms, cnt = phases[rl_phase]
+    achieved = alg[rl_phase] / (ms / cnt * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": None, "kernel": rl_phase,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback",
+                "dominant_phase": dom,
+                "phase_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in phases.items()},
+                "phase_spans_per_step": {k: v[1] // args.steps for k, v in phases.items()}}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        total, cores, sample = oracle_timing(pr)
+        cpu = {"value": total, "unit": "s", "cores": cores, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": t_local, "unit": "s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_local * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": headline[0], "data": "synthetic",
+            "config": workload_config(headline[1], headline[0]),
+            "e2e": {"value": statistics.median(e2e), "unit": "s", "h2d_bytes_per_step": 4 * m * n,
+                    "d2h_bytes_per_step": 4 * (m * r + r * n)},
+            "gpu_launches": launches, "gpu_launches_per_step": launches // args.steps,
+            "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
+            "fp32_target": {"e32": e32, "target": target},
+            "contenders": results}))
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

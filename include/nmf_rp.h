@@ -1,0 +1,206 @@
+/*
+ * nmf_rp.h -- C ABI of the GB300 (sm_103a) library for random-projection compressed NMF
+ * (Torre & Graber, "An Efficient Algorithm for Non-Negative Matrix Factorization with Random
+ * Projections", arXiv:1712.02248).
+ *
+ * Problem (Section 2, Eq. 2.2): min 1/2 ||X - W H||_F^2 over W >= 0 (m x r), H >= 0 (r x n), for a
+ * non-negative X (m x n). The paper's A is W and its B is H^T.
+ *
+ * Conventions for every entry point
+ *  - Matrix arguments are DEVICE pointers (cudaMalloc / torch CUDA tensors) unless the name says
+ *    `_host`. They are owned by the caller; the library never frees or retains them past a call.
+ *  - All matrices are row-major. X has leading dimension `ldx` (elements, ldx >= n). The others are
+ *    dense: Omega_L n x l, Omega_R m x l, Q_L m x l, Q_R n x l, X_hat l x n, X_chk m x l,
+ *    W m x r, H r x n. l ("ell") is the sketch width r + oversampling.
+ *  - Work is queued on the context's CUDA stream and is asynchronous unless the entry point
+ *    returns a host value (it then synchronises that stream). Kernel-side failures (QR breakdown,
+ *    non-finite values, a bounded wait that ran out) are latched in a device status word and
+ *    reported by the next synchronising call (nmf_sync, nmf_residual, nmf_solve).
+ *  - Errors are returned as nmf_status; nothing is thrown across the ABI. nmf_last_error() gives
+ *    a one-line message for the last failing call on that context.
+ *  - The context owns an internal device workspace (grown on demand with cudaMalloc, freed by
+ *    nmf_destroy). Calls on one context must not overlap from several host threads.
+ */
+#ifndef NMF_RP_H
+#define NMF_RP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  NMF_OK = 0,
+  NMF_ERR_INVALID_ARG = 1,   /* bad size, pointer, alignment or enum value */
+  NMF_ERR_CUDA = 2,          /* a CUDA runtime call failed (message in nmf_last_error) */
+  NMF_ERR_OOM = 3,           /* workspace allocation failed */
+  NMF_ERR_QR_BREAKDOWN = 4,  /* Cholesky pivot not positive: sketch numerically rank deficient */
+  NMF_ERR_NOT_FINITE = 5,    /* NaN/Inf met in the residual */
+  NMF_ERR_TIMEOUT = 6,       /* a bounded device-side wait ran out */
+  NMF_ERR_UNSUPPORTED = 7    /* valid request this build does not implement */
+} nmf_status;
+
+/* Arithmetic type of the X-sized contractions (sketch passes and compression). */
+typedef enum {
+  NMF_PREC_FP32 = 0,         /* X read as FP32 */
+  NMF_PREC_BF16 = 1,         /* X read as BF16, tensor cores, FP32 accumulation */
+  NMF_PREC_FP8_E4M3 = 2      /* reserved */
+} nmf_precision;
+
+/* Update rule of the iterations. */
+typedef enum {
+  NMF_RULE_FASTHALS_RP = 0,  /* Section 4, Eq. fastHALS_a (+ Section 4.1 alpha/beta on H) */
+  NMF_RULE_MU_RP = 1         /* Section 3.1, Algorithm 3 with the semi-NMF multiplicative rule */
+} nmf_rule;
+
+/* Initialisation used by nmf_solve. */
+typedef enum {
+  NMF_INIT_GIVEN = 0,        /* W, H hold the caller's initial factors */
+  NMF_INIT_NNDSVD = 1        /* NNDSVD of the compressed data (Boutsidis & Gallopoulos 2008) */
+} nmf_init;
+
+typedef struct {
+  int64_t m, n;              /* X is m x n */
+  int32_t r;                 /* number of components (the paper's k), 1 <= r <= ell */
+  int32_t ell;               /* sketch width r + r_ov (Section 3), ell <= min(m, n), ell <= 128 */
+  int32_t power_iters;       /* w of Eq. 3.5, 0 <= w <= 32 */
+  int32_t iters;             /* nmf_solve: maximum number of iterations */
+  int32_t rule;              /* nmf_rule */
+  int32_t prec;              /* nmf_precision of the sketch / compression contractions */
+  uint64_t seed;             /* Philox4x32-10 key for Omega when the caller passes none */
+  int32_t residual_every;    /* nmf_solve: exact residual every k iterations (0: at the end) */
+  int32_t reserved0;
+  double target_rel_err;     /* nmf_solve: stop at the first check with rel_err <= target (0: off) */
+  double alpha, beta;        /* Section 4.1 sparsity / smoothness weights on H (FastHALS-RP) */
+  double eps;                /* MU-RP denominator guard (<= 0: 1e-12) */
+} nmf_params;
+
+typedef struct nmf_ctx nmf_ctx;
+
+/* Create a context on CUDA device `device` that queues all work on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream). */
+nmf_status nmf_create(nmf_ctx** ctx, int device, void* cuda_stream);
+/* Free the context and its workspace. NULL is ignored. Synchronises the stream first. */
+void nmf_destroy(nmf_ctx* ctx);
+/* Replace the stream future calls are queued on. */
+nmf_status nmf_set_stream(nmf_ctx* ctx, void* cuda_stream);
+/* One-line description of the last error on this context ("" if none). */
+const char* nmf_last_error(const nmf_ctx* ctx);
+/* Synchronise the context's stream and return (then clear) the latched device status. */
+nmf_status nmf_sync(nmf_ctx* ctx);
+/* Number of kernels this context has launched so far (for launch accounting). */
+int64_t nmf_launch_count(const nmf_ctx* ctx);
+/*
+ * Per-phase timing. When profiling is on, every phase below is bracketed by CUDA events recorded
+ * on the context stream; nmf_phase_times (synchronises) returns the summed milliseconds and the
+ * number of timed spans of each phase (arrays of NMF_PHASE_COUNT), optionally resetting them.
+ */
+enum {
+  NMF_PHASE_QUANTIZE = 0,   /* FP32 -> BF16 copy of X */
+  NMF_PHASE_DUAL_PASS = 1,  /* one fused pass over X (sketch pass or compression) */
+  NMF_PHASE_QR = 2,         /* one CholeskyQR2 */
+  NMF_PHASE_ITERATE = 3,    /* a run of iterations */
+  NMF_PHASE_RESIDUAL = 4,   /* one full residual */
+  NMF_PHASE_INIT = 5,       /* NNDSVD initialisation */
+  NMF_PHASE_COUNT = 6
+};
+nmf_status nmf_set_profiling(nmf_ctx* ctx, int32_t on);
+nmf_status nmf_phase_times(nmf_ctx* ctx, double* ms, int64_t* counts, int32_t reset);
+/* Bytes of device workspace nmf_solve needs for these parameters (other calls need less). */
+nmf_status nmf_workspace_size(const nmf_params* p, size_t* bytes);
+
+/*
+ * Gaussian test matrix (Section 3: Omega has standard-normal entries), rows x cols row-major,
+ * from Philox4x32-10 (Salmon et al., SC'11) and the Box-Muller transform: element e = i*cols + k
+ * uses lane e % 4 of the generator output for counter (e/4 low word, e/4 high word, stream_id, 0)
+ * and key (seed low word, seed high word); words map to uniforms ((x >> 8) + 1/2) 2^-24.
+ * nmf_sketch uses stream_id 0 for Omega_L and 1 for Omega_R when they are not given.
+ */
+nmf_status nmf_gaussian(nmf_ctx* ctx, int64_t rows, int64_t cols, uint64_t seed,
+                        uint32_t stream_id, float* out);
+
+/*
+ * Copy X (FP32, m x n, leading dimension ldx) to BF16 (round to nearest even), dense m x n:
+ * `Xq` holds m*n uint16 BF16 codes. The low-precision copy the BF16 sketch and compression read.
+ */
+nmf_status nmf_quantize(nmf_ctx* ctx, int32_t prec, const float* X, int64_t m, int64_t n,
+                        int64_t ldx, void* Xq);
+
+/*
+ * One fused pass over X (the building block of every sketch and compression step):
+ *   Y = X V   (m x l, reduction over n)   and   Z = X^T U   (n x l, reduction over m),
+ * reading X once. V is n x l, U is m x l, all FP32 row-major; Y, Z are written (not accumulated).
+ * `X` is FP32 (prec = NMF_PREC_FP32, leading dimension ldx) or the dense BF16 copy from
+ * nmf_quantize (prec = NMF_PREC_BF16, ldx must equal n). Either of V/Y or U/Z may be NULL
+ * (both of a pair) to skip that product. 1 <= l <= 128.
+ */
+nmf_status nmf_dual_pass(nmf_ctx* ctx, int32_t prec, const void* X, int64_t m, int64_t n,
+                         int64_t ldx, int32_t ell, const float* V, const float* U,
+                         float* Y, float* Z);
+
+/*
+ * Thin QR of a tall FP32 matrix Y (rows x l, rows >= l): writes Q (rows x l, FP32, orthonormal
+ * columns, the unique Q whose R has a positive diagonal; Section 3, Eq. 3.4-3.5). CholeskyQR2
+ * (Fukaya et al. 2014): the Gram matrix Y^T Y and its Cholesky factor are formed in FP64; a
+ * non-positive pivot latches NMF_ERR_QR_BREAKDOWN. Q may alias Y.
+ */
+nmf_status nmf_qr(nmf_ctx* ctx, const float* Y, int64_t rows, int32_t ell, float* Q);
+
+/*
+ * Two-sided sketch (Section 3 Eq. 3.5, Section 3.1): Q_L spans (X X^T)^w X Omega_L, Q_R spans
+ * (X^T X)^w X^T Omega_R, orthonormalised after every application of X or X^T, both chains
+ * advancing together so that 2w + 1 passes over X serve both. omega_L (n x l) / omega_R (m x l)
+ * may be NULL: drawn with nmf_gaussian(seed = p->seed, stream_id 0 / 1).
+ * `X` is FP32 with leading dimension ldx (p->prec = FP32), or the nmf_quantize copy (BF16, ldx = n).
+ */
+nmf_status nmf_sketch(nmf_ctx* ctx, const nmf_params* p, const void* X, int64_t ldx,
+                      const float* omega_L, const float* omega_R, float* QL, float* QR);
+
+/* Compression (Section 4, before Algorithm 4): X_hat = Q_L^T X (l x n), X_chk = X Q_R (m x l),
+ * in one pass over X. X as for nmf_sketch. */
+nmf_status nmf_compress(nmf_ctx* ctx, const nmf_params* p, const void* X, int64_t ldx,
+                        const float* QL, const float* QR, float* Xhat, float* Xchk);
+
+/*
+ * `iters` iterations of the compressed updates on W (m x r) and H (r x n), in place.
+ * FastHALS-RP (Eq. fastHALS_a, Section 4.1 form with p->alpha, p->beta): the whole W sweep over
+ * components j = 1..r (Gauss-Seidel), normalisation of the columns of W with the scale moved to
+ * the rows of H, then the whole H sweep. MU-RP (Algorithm 3): the semi-NMF multiplicative rule on
+ * W, then on H. Never reads X.
+ */
+nmf_status nmf_iterate(nmf_ctx* ctx, const nmf_params* p, const float* QL, const float* QR,
+                       const float* Xhat, const float* Xchk, float* W, float* H, int32_t iters);
+
+/*
+ * Relative reconstruction error ||X - W H||_F / ||X||_F (the error of Eq. 2.2) written to
+ * *rel_err_host; X FP32 with leading dimension ldx. Differences are formed in FP32 and summed in
+ * FP64. Synchronises the stream. Returns NMF_ERR_NOT_FINITE if the sum is not finite.
+ * `err2_host` / `x2_host` (may be NULL) receive ||X - W H||^2 and ||X||^2.
+ */
+nmf_status nmf_residual(nmf_ctx* ctx, const nmf_params* p, const float* X, int64_t ldx,
+                        const float* W, const float* H, double* rel_err_host,
+                        double* err2_host, double* x2_host);
+
+/* NNDSVD initial factors from the compressed data (SVD of X ~ Q_L X_hat through the l x l
+ * eigenproblem of X_hat X_hat^T in FP64). W: m x r, H: r x n. */
+nmf_status nmf_nndsvd(nmf_ctx* ctx, const nmf_params* p, const float* QL, const float* Xhat,
+                      float* W, float* H);
+
+/*
+ * Whole pipeline on FP32 X (m x n, leading dimension ldx): sketch (Omega from p->seed), compress,
+ * initialise (init), iterate; an exact residual every p->residual_every iterations and at the end.
+ * Stops at the first check with rel_err <= p->target_rel_err (if > 0) or after p->iters
+ * iterations. With p->prec = BF16 the X passes read a BF16 copy made in the workspace.
+ * W, H: in/out (read only for NMF_INIT_GIVEN). Synchronises the stream.
+ * Outputs: *rel_err_host (last exact residual), *iters_done_host (iterations run; may be NULL).
+ */
+nmf_status nmf_solve(nmf_ctx* ctx, const nmf_params* p, int32_t init, const float* X, int64_t ldx,
+                     float* W, float* H, double* rel_err_host, int32_t* iters_done_host);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NMF_RP_H */

@@ -1,0 +1,89 @@
+// Internal declarations shared by the library's translation units (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+#include <cstddef>
+
+namespace nmfrp {
+
+// Device status codes (same values as nmf_status in include/nmf_rp.h).
+enum : int {
+  kStOk = 0,
+  kStQrBreakdown = 4,
+  kStNotFinite = 5,
+  kStTimeout = 6,
+};
+
+// Record the first failure only.
+__device__ __forceinline__ void latch(int* status, int code) {
+  if (status) atomicCAS(status, 0, code);
+}
+
+// Launch bookkeeping: every kernel launch goes through a Launcher so that the library can report
+// how many kernels it queued.
+struct Launcher {
+  cudaStream_t stream = nullptr;
+  int64_t* counter = nullptr;
+  void count(int k = 1) const {
+    if (counter) *counter += k;
+  }
+};
+
+__host__ __device__ __forceinline__ int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+inline int pad_to(int v, int q) { return (v + q - 1) / q * q; }
+
+// ---------------------------------------------------------------- launch functions
+// Every function queues work on L.stream and returns the launch error (cudaSuccess if none).
+
+// Philox4x32-10 + Box-Muller standard normals, rows x cols row-major.
+cudaError_t launch_gaussian(const Launcher& L, int64_t rows, int64_t cols, uint64_t seed,
+                            uint32_t stream_id, float* out);
+
+// FP32 -> BF16 (RNE) copy of X (m x n, leading dimension ldx) into dense Xq (m x n).
+cudaError_t launch_quantize_bf16(const Launcher& L, const float* X, int64_t m, int64_t n,
+                                 int64_t ldx, __nv_bfloat16* Xq);
+
+// Dual pass Y = X V (m x ell), Z = X^T U (n x ell). x_bf16 selects the element type of X.
+// ws: workspace for partial sums (size from dual_pass_ws_bytes).
+size_t dual_pass_ws_bytes(int64_t m, int64_t n, int ell);
+cudaError_t launch_dual_pass(const Launcher& L, const void* X, bool x_bf16, int64_t m, int64_t n,
+                             int64_t ldx, int ell, const float* V, const float* U, float* Y,
+                             float* Z, void* ws, size_t ws_bytes);
+
+// Thin QR via CholeskyQR2 with FP64 Gram and Cholesky. Q may alias Y.
+size_t qr_ws_bytes(int64_t rows, int ell);
+cudaError_t launch_qr(const Launcher& L, const float* Y, int64_t rows, int ell, float* Q,
+                      void* ws, size_t ws_bytes, int* status);
+
+// Iterations of FastHALS-RP (rule 0) or MU-RP (rule 1).
+struct IterArgs {
+  int64_t m, n;
+  int r, ell;
+  int rule;
+  float alpha, beta, eps;
+  const float* QL;    // m x ell
+  const float* QR;    // n x ell
+  const float* Xhat;  // ell x n
+  const float* Xchk;  // m x ell
+  float* W;           // m x r
+  float* H;           // r x n
+};
+size_t iterate_ws_bytes(int64_t m, int64_t n, int r, int ell);
+cudaError_t launch_iterate(const Launcher& L, const IterArgs& a, int iters, void* ws,
+                           size_t ws_bytes);
+
+// Residual partial sums: writes 2 doubles (||X-WH||^2, ||X||^2) to out2 (device).
+size_t residual_ws_bytes(int64_t m, int64_t n);
+cudaError_t launch_residual(const Launcher& L, const float* X, int64_t m, int64_t n, int64_t ldx,
+                            const float* W, const float* H, int r, double* out2, void* ws,
+                            size_t ws_bytes);
+
+// NNDSVD from compressed data.
+size_t nndsvd_ws_bytes(int64_t m, int64_t n, int r, int ell);
+cudaError_t launch_nndsvd(const Launcher& L, int64_t m, int64_t n, int r, int ell,
+                          const float* QL, const float* Xhat, float* W, float* H, void* ws,
+                          size_t ws_bytes, int* status);
+
+}  // namespace nmfrp

@@ -1,0 +1,119 @@
+// Gaussian test matrix (Section 3: Omega ~ N(0,1)) and the FP32 -> BF16 copy of X.
+#include "common.cuh"
+
+namespace nmfrp {
+namespace {
+
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of two 32x32->64-bit multiplies
+// with the key bumped by the Weyl constants between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k.x += W0;
+      k.y += W1;
+    }
+    const uint32_t hi0 = __umulhi(M0, c.x), lo0 = M0 * c.x;
+    const uint32_t hi1 = __umulhi(M1, c.z), lo1 = M1 * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+  }
+  return c;
+}
+
+__device__ __forceinline__ float to_unit(uint32_t x) {
+  // ((x >> 8) + 1/2) * 2^-24, strictly inside (0, 1)
+  return (static_cast<float>(x >> 8) + 0.5f) * 5.9604644775390625e-8f;
+}
+
+__global__ void gaussian_kernel(int64_t total, uint2 key, uint32_t stream_id, float* out) {
+  const int64_t nblk = (total + 3) / 4;
+  for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nblk;
+       b += (int64_t)gridDim.x * blockDim.x) {
+    const uint4 x = philox4x32_10(
+        make_uint4(static_cast<uint32_t>(b), static_cast<uint32_t>(b >> 32), stream_id, 0u), key);
+    float z[4];
+    {
+      const float rad = sqrtf(-2.0f * logf(to_unit(x.x)));
+      float s, c;
+      sincospif(2.0f * to_unit(x.y), &s, &c);
+      z[0] = rad * c;
+      z[1] = rad * s;
+    }
+    {
+      const float rad = sqrtf(-2.0f * logf(to_unit(x.z)));
+      float s, c;
+      sincospif(2.0f * to_unit(x.w), &s, &c);
+      z[2] = rad * c;
+      z[3] = rad * s;
+    }
+    const int64_t e0 = 4 * b;
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+      if (e0 + t < total) out[e0 + t] = z[t];
+  }
+}
+
+__global__ void quantize_bf16_kernel(const float* __restrict__ X, int64_t m, int64_t n, int64_t ldx,
+                                     __nv_bfloat16* __restrict__ Xq) {
+  const int64_t total = m * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / n, j = e - i * n;
+    Xq[e] = __float2bfloat16_rn(X[i * ldx + j]);
+  }
+}
+
+// Vectorised variant: n % 4 == 0, ldx % 4 == 0, X 16-byte aligned.
+__global__ void quantize_bf16_vec4_kernel(const float* __restrict__ X, int64_t m, int64_t n,
+                                          int64_t ldx, __nv_bfloat16* __restrict__ Xq) {
+  const int64_t n4 = n / 4, total = m * n4;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / n4, j4 = e - i * n4;
+    const float4 v = __ldcs(reinterpret_cast<const float4*>(X + i * ldx) + j4);
+    __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y);
+    __nv_bfloat162 hi = __floats2bfloat162_rn(v.z, v.w);
+    uint2 packed;
+    packed.x = *reinterpret_cast<uint32_t*>(&lo);
+    packed.y = *reinterpret_cast<uint32_t*>(&hi);
+    reinterpret_cast<uint2*>(Xq + i * n)[j4] = packed;
+  }
+}
+
+int grid_for(int64_t work, int threads) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (sms <= 0) sms = 148;
+  int64_t g = (work + threads - 1) / threads;
+  const int64_t cap = static_cast<int64_t>(sms) * 8;
+  return static_cast<int>(g < 1 ? 1 : (g > cap ? cap : g));
+}
+
+}  // namespace
+
+cudaError_t launch_gaussian(const Launcher& L, int64_t rows, int64_t cols, uint64_t seed,
+                            uint32_t stream_id, float* out) {
+  const int64_t total = rows * cols;
+  if (total <= 0) return cudaSuccess;
+  const uint2 key = make_uint2(static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32));
+  gaussian_kernel<<<grid_for((total + 3) / 4, 256), 256, 0, L.stream>>>(total, key, stream_id, out);
+  L.count();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_quantize_bf16(const Launcher& L, const float* X, int64_t m, int64_t n,
+                                 int64_t ldx, __nv_bfloat16* Xq) {
+  if (m * n <= 0) return cudaSuccess;
+  const bool vec = (n % 4 == 0) && (ldx % 4 == 0) && (reinterpret_cast<uintptr_t>(X) % 16 == 0);
+  if (vec)
+    quantize_bf16_vec4_kernel<<<grid_for(m * n / 4, 256), 256, 0, L.stream>>>(X, m, n, ldx, Xq);
+  else
+    quantize_bf16_kernel<<<grid_for(m * n, 256), 256, 0, L.stream>>>(X, m, n, ldx, Xq);
+  L.count();
+  return cudaGetLastError();
+}
+
+}  // namespace nmfrp

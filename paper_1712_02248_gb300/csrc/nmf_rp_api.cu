@@ -1,0 +1,650 @@
+// C ABI of the library (include/nmf_rp.h): argument checks, workspace, and the order of the
+// kernels of each step. No arithmetic of the method happens here.
+#include <cstdio>
+#include <cstring>
+#include <cstdarg>
+#include <algorithm>
+#include <cmath>
+
+#include <vector>
+
+#include "nmf_rp.h"
+#include "common.cuh"
+
+// Optional per-phase timing: CUDA events recorded on the context stream around each phase.
+struct PhaseMark {
+  int phase;
+  cudaEvent_t a, b;
+};
+
+struct nmf_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  int* d_status = nullptr;   // latched device status word
+  double* d_res = nullptr;   // residual sums (2 doubles)
+  double* h_res = nullptr;   // pinned host copy
+  int64_t launches = 0;
+  char msg[512] = {0};
+  bool profiling = false;
+  std::vector<PhaseMark> marks;
+  std::vector<cudaEvent_t> pool;
+  double phase_ms[NMF_PHASE_COUNT] = {0};
+  int64_t phase_n[NMF_PHASE_COUNT] = {0};
+};
+
+namespace {
+
+using nmfrp::cdiv;
+
+cudaEvent_t pool_event(nmf_ctx* c) {
+  if (!c->pool.empty()) {
+    cudaEvent_t e = c->pool.back();
+    c->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+// Scoped phase timer (no-op unless profiling is on).
+struct Phase {
+  nmf_ctx* c;
+  int phase;
+  cudaEvent_t a = nullptr;
+  Phase(nmf_ctx* ctx, int ph) : c(ctx), phase(ph) {
+    if (c->profiling && (a = pool_event(c))) cudaEventRecord(a, c->stream);
+  }
+  void end() {
+    if (!a) return;
+    cudaEvent_t b = pool_event(c);
+    if (!b) {
+      c->pool.push_back(a);
+    } else {
+      cudaEventRecord(b, c->stream);
+      c->marks.push_back({phase, a, b});
+    }
+    a = nullptr;
+  }
+  ~Phase() { end(); }
+};
+
+// Fold recorded marks into the per-phase totals (synchronises).
+void resolve_marks(nmf_ctx* c) {
+  if (c->marks.empty()) return;
+  cudaStreamSynchronize(c->stream);
+  for (const PhaseMark& mk : c->marks) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, mk.a, mk.b) == cudaSuccess) {
+      c->phase_ms[mk.phase] += ms;
+      c->phase_n[mk.phase] += 1;
+    } else {
+      cudaGetLastError();
+    }
+    c->pool.push_back(mk.a);
+    c->pool.push_back(mk.b);
+  }
+  c->marks.clear();
+}
+
+nmf_status fail(nmf_ctx* c, nmf_status st, const char* fmt, ...) {
+  if (c) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(c->msg, sizeof(c->msg), fmt, ap);
+    va_end(ap);
+  }
+  return st;
+}
+
+nmf_status cuda_fail(nmf_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, NMF_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define NMF_CUDA(call, where)                       \
+  do {                                              \
+    cudaError_t e_ = (call);                        \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, where); \
+  } while (0)
+
+nmfrp::Launcher launcher(nmf_ctx* c) {
+  nmfrp::Launcher L;
+  L.stream = c->stream;
+  L.counter = &c->launches;
+  return L;
+}
+
+// Grow the context workspace to at least `bytes` (synchronises before freeing the old one).
+nmf_status ensure_ws(nmf_ctx* ctx, size_t bytes) {
+  if (bytes <= ctx->ws_bytes) return NMF_OK;
+  if (ctx->ws) {
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(ctx->ws);
+    ctx->ws = nullptr;
+    ctx->ws_bytes = 0;
+  }
+  const size_t want = bytes + (bytes >> 3) + (1 << 20);
+  cudaError_t e = cudaMalloc(&ctx->ws, want);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, NMF_ERR_OOM, "workspace of %zu bytes: %s", want, cudaGetErrorString(e));
+  }
+  ctx->ws_bytes = want;
+  return NMF_OK;
+}
+
+// Bump allocator over the workspace (256-byte aligned slices).
+struct Arena {
+  char* base;
+  size_t cap, off = 0;
+  template <typename T>
+  T* take(size_t count) {
+    off = (off + 255) & ~static_cast<size_t>(255);
+    T* p = reinterpret_cast<T*>(base + off);
+    off += sizeof(T) * count;
+    return p;
+  }
+  void* rest(size_t* bytes) {
+    off = (off + 255) & ~static_cast<size_t>(255);
+    *bytes = cap > off ? cap - off : 0;
+    return base + off;
+  }
+};
+
+nmf_status check_params(nmf_ctx* ctx, const nmf_params* p) {
+  if (!p) return fail(ctx, NMF_ERR_INVALID_ARG, "params is NULL");
+  if (p->m < 1 || p->n < 1) return fail(ctx, NMF_ERR_INVALID_ARG, "m, n must be >= 1");
+  if (p->r < 1 || p->r > p->ell)
+    return fail(ctx, NMF_ERR_INVALID_ARG, "need 1 <= r <= ell (r=%d ell=%d)", p->r, p->ell);
+  if (p->ell > 128) return fail(ctx, NMF_ERR_INVALID_ARG, "ell must be <= 128");
+  if (p->ell > std::min(p->m, p->n))
+    return fail(ctx, NMF_ERR_INVALID_ARG, "ell must be <= min(m, n)");
+  if (p->power_iters < 0 || p->power_iters > 32)
+    return fail(ctx, NMF_ERR_INVALID_ARG, "power_iters must be in [0, 32]");
+  if (p->rule != NMF_RULE_FASTHALS_RP && p->rule != NMF_RULE_MU_RP)
+    return fail(ctx, NMF_ERR_INVALID_ARG, "unknown rule %d", p->rule);
+  if (p->prec != NMF_PREC_FP32 && p->prec != NMF_PREC_BF16)
+    return fail(ctx, p->prec == NMF_PREC_FP8_E4M3 ? NMF_ERR_UNSUPPORTED : NMF_ERR_INVALID_ARG,
+                "precision %d not available", p->prec);
+  if (p->alpha < 0 || p->beta < 0) return fail(ctx, NMF_ERR_INVALID_ARG, "alpha, beta must be >= 0");
+  return NMF_OK;
+}
+
+nmf_status check_x(nmf_ctx* ctx, const nmf_params* p, const void* X, int64_t ldx) {
+  if (!X) return fail(ctx, NMF_ERR_INVALID_ARG, "X is NULL");
+  if (p->prec == NMF_PREC_BF16 && ldx != p->n)
+    return fail(ctx, NMF_ERR_INVALID_ARG, "BF16 X must be dense (ldx == n)");
+  if (ldx < p->n) return fail(ctx, NMF_ERR_INVALID_ARG, "ldx < n");
+  return NMF_OK;
+}
+
+float eps_of(const nmf_params* p) { return p->eps > 0 ? static_cast<float>(p->eps) : 1e-12f; }
+
+// One dual pass with its scratch.
+nmf_status dual(nmf_ctx* ctx, const void* X, bool bf16, int64_t m, int64_t n, int64_t ldx, int ell,
+                const float* V, const float* U, float* Y, float* Z, Arena a) {
+  Phase ph(ctx, NMF_PHASE_DUAL_PASS);
+  size_t rest = 0;
+  void* ws = a.rest(&rest);
+  NMF_CUDA(nmfrp::launch_dual_pass(launcher(ctx), X, bf16, m, n, ldx, ell, V, U, Y, Z, ws, rest),
+           "dual pass");
+  return NMF_OK;
+}
+
+nmf_status qr(nmf_ctx* ctx, float* Y, int64_t rows, int ell, Arena a) {
+  Phase ph(ctx, NMF_PHASE_QR);
+  size_t rest = 0;
+  void* ws = a.rest(&rest);
+  NMF_CUDA(nmfrp::launch_qr(launcher(ctx), Y, rows, ell, Y, ws, rest, ctx->d_status), "qr");
+  return NMF_OK;
+}
+
+size_t pass_scratch(int64_t m, int64_t n, int ell) {
+  return std::max(nmfrp::dual_pass_ws_bytes(m, n, ell),
+                  std::max(nmfrp::qr_ws_bytes(m, ell), nmfrp::qr_ws_bytes(n, ell))) + 4096;
+}
+
+size_t sketch_ws(const nmf_params* p, bool need_omega) {
+  const int64_t m = p->m, n = p->n, l = p->ell;
+  size_t b = sizeof(float) * (m * l + n * l) + 1024;         // other chain's m- and n-side bases
+  if (need_omega) b += sizeof(float) * (m * l + n * l) + 1024;
+  return b + pass_scratch(m, n, p->ell);
+}
+
+// Both chains of Eq. 3.5 advance together: pass 0 applies X to Omega_L and X^T to Omega_R; pass
+// p >= 1 applies X to one chain's n-side basis and X^T to the other chain's m-side basis.
+nmf_status sketch_impl(nmf_ctx* ctx, const nmf_params* p, const void* X, int64_t ldx,
+                       const float* omega_L, const float* omega_R, float* QL, float* QR, Arena a) {
+  const int64_t m = p->m, n = p->n;
+  const int l = p->ell;
+  const bool bf16 = p->prec == NMF_PREC_BF16;
+  float* mR = a.take<float>(m * l);   // right chain, m-side
+  float* nL = a.take<float>(n * l);   // left chain, n-side
+  if (!omega_L || !omega_R) {
+    float* oL = a.take<float>(n * l);
+    float* oR = a.take<float>(m * l);
+    if (!omega_L) {
+      NMF_CUDA(nmfrp::launch_gaussian(launcher(ctx), n, l, p->seed, 0u, oL), "gaussian");
+      omega_L = oL;
+    }
+    if (!omega_R) {
+      NMF_CUDA(nmfrp::launch_gaussian(launcher(ctx), m, l, p->seed, 1u, oR), "gaussian");
+      omega_R = oR;
+    }
+  }
+  nmf_status st;
+  // pass 0
+  if ((st = dual(ctx, X, bf16, m, n, ldx, l, omega_L, omega_R, QL, QR, a)) != NMF_OK) return st;
+  if ((st = qr(ctx, QL, m, l, a)) != NMF_OK) return st;
+  if ((st = qr(ctx, QR, n, l, a)) != NMF_OK) return st;
+  for (int pass = 1; pass <= 2 * p->power_iters; ++pass) {
+    if (pass & 1) {
+      // right chain: X * (n-side) -> m-side; left chain: X^T * (m-side) -> n-side
+      if ((st = dual(ctx, X, bf16, m, n, ldx, l, QR, QL, mR, nL, a)) != NMF_OK) return st;
+      if ((st = qr(ctx, mR, m, l, a)) != NMF_OK) return st;
+      if ((st = qr(ctx, nL, n, l, a)) != NMF_OK) return st;
+    } else {
+      if ((st = dual(ctx, X, bf16, m, n, ldx, l, nL, mR, QL, QR, a)) != NMF_OK) return st;
+      if ((st = qr(ctx, QL, m, l, a)) != NMF_OK) return st;
+      if ((st = qr(ctx, QR, n, l, a)) != NMF_OK) return st;
+    }
+  }
+  return NMF_OK;
+}
+
+__global__ void transpose_kernel(const float* __restrict__ in, int64_t rows, int cols,
+                                 float* __restrict__ out) {
+  // out (cols x rows) = in^T (in: rows x cols)
+  __shared__ float tile[32][33];
+  const int64_t r0 = static_cast<int64_t>(blockIdx.x) * 32;
+  const int c0 = blockIdx.y * 32;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int64_t r = r0 + i;
+    const int c = c0 + threadIdx.x;
+    tile[i][threadIdx.x] = (r < rows && c < cols) ? in[r * cols + c] : 0.f;
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int c = c0 + i;
+    const int64_t r = r0 + threadIdx.x;
+    if (c < cols && r < rows) out[static_cast<int64_t>(c) * rows + r] = tile[threadIdx.x][i];
+  }
+}
+
+nmf_status compress_impl(nmf_ctx* ctx, const nmf_params* p, const void* X, int64_t ldx,
+                         const float* QL, const float* QR, float* Xhat, float* Xchk, Arena a) {
+  const int64_t m = p->m, n = p->n;
+  const int l = p->ell;
+  float* XhatT = a.take<float>(n * l);
+  nmf_status st = dual(ctx, X, p->prec == NMF_PREC_BF16, m, n, ldx, l, QR, QL, Xchk, XhatT, a);
+  if (st != NMF_OK) return st;
+  dim3 grid(static_cast<unsigned>(cdiv(n, 32)), static_cast<unsigned>(cdiv(l, 32)));
+  transpose_kernel<<<grid, dim3(32, 8), 0, ctx->stream>>>(XhatT, n, l, Xhat);
+  ctx->launches++;
+  NMF_CUDA(cudaGetLastError(), "transpose");
+  return NMF_OK;
+}
+
+nmf_status iterate_impl(nmf_ctx* ctx, const nmf_params* p, const float* QL, const float* QR,
+                        const float* Xhat, const float* Xchk, float* W, float* H, int iters,
+                        Arena a) {
+  if (p->r > 64) return fail(ctx, NMF_ERR_UNSUPPORTED, "iterations support r <= 64");
+  nmfrp::IterArgs ia;
+  ia.m = p->m;
+  ia.n = p->n;
+  ia.r = p->r;
+  ia.ell = p->ell;
+  ia.rule = p->rule;
+  ia.alpha = static_cast<float>(p->alpha);
+  ia.beta = static_cast<float>(p->beta);
+  ia.eps = eps_of(p);
+  ia.QL = QL;
+  ia.QR = QR;
+  ia.Xhat = Xhat;
+  ia.Xchk = Xchk;
+  ia.W = W;
+  ia.H = H;
+  Phase ph(ctx, NMF_PHASE_ITERATE);
+  size_t rest = 0;
+  void* ws = a.rest(&rest);
+  NMF_CUDA(nmfrp::launch_iterate(launcher(ctx), ia, iters, ws, rest), "iterate");
+  return NMF_OK;
+}
+
+nmf_status residual_impl(nmf_ctx* ctx, const nmf_params* p, const float* X, int64_t ldx,
+                         const float* W, const float* H, double* rel, double* e2o, double* x2o,
+                         Arena a) {
+  size_t rest = 0;
+  void* ws = a.rest(&rest);
+  Phase ph(ctx, NMF_PHASE_RESIDUAL);
+  NMF_CUDA(nmfrp::launch_residual(launcher(ctx), X, p->m, p->n, ldx, W, H, p->r, ctx->d_res, ws,
+                                  rest),
+           "residual");
+  ph.end();
+  NMF_CUDA(cudaMemcpyAsync(ctx->h_res, ctx->d_res, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                           ctx->stream),
+           "residual copy");
+  NMF_CUDA(cudaStreamSynchronize(ctx->stream), "residual sync");
+  const double e2 = ctx->h_res[0], x2 = ctx->h_res[1];
+  if (e2o) *e2o = e2;
+  if (x2o) *x2o = x2;
+  if (!(e2 == e2) || !(x2 == x2) || e2 > 1e308 || x2 > 1e308)
+    return fail(ctx, NMF_ERR_NOT_FINITE, "residual is not finite");
+  if (rel) *rel = x2 > 0 ? std::sqrt(e2 / x2) : std::sqrt(e2);
+  return NMF_OK;
+}
+
+nmf_status take_status(nmf_ctx* ctx) {
+  int st = 0;
+  NMF_CUDA(cudaMemcpyAsync(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream),
+           "status copy");
+  NMF_CUDA(cudaStreamSynchronize(ctx->stream), "status sync");
+  if (st != 0) {
+    NMF_CUDA(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream), "status reset");
+    NMF_CUDA(cudaStreamSynchronize(ctx->stream), "status sync");
+    switch (st) {
+      case NMF_ERR_QR_BREAKDOWN:
+        return fail(ctx, NMF_ERR_QR_BREAKDOWN, "Cholesky pivot not positive in the sketch QR");
+      case NMF_ERR_TIMEOUT: return fail(ctx, NMF_ERR_TIMEOUT, "device wait ran out");
+      default: return fail(ctx, static_cast<nmf_status>(st), "device status %d", st);
+    }
+  }
+  return NMF_OK;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+nmf_status nmf_create(nmf_ctx** out, int device, void* cuda_stream) {
+  if (!out) return NMF_ERR_INVALID_ARG;
+  *out = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+    cudaGetLastError();
+    return NMF_ERR_CUDA;
+  }
+  nmf_ctx* ctx = new nmf_ctx();
+  ctx->device = device;
+  ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+  DeviceGuard g(device);
+  if (cudaMalloc(&ctx->d_status, sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&ctx->d_res, 2 * sizeof(double)) != cudaSuccess ||
+      cudaMallocHost(&ctx->h_res, 2 * sizeof(double)) != cudaSuccess ||
+      cudaMemset(ctx->d_status, 0, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    nmf_destroy(ctx);
+    return NMF_ERR_CUDA;
+  }
+  *out = ctx;
+  return NMF_OK;
+}
+
+void nmf_destroy(nmf_ctx* ctx) {
+  if (!ctx) return;
+  DeviceGuard g(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  for (const PhaseMark& mk : ctx->marks) {
+    cudaEventDestroy(mk.a);
+    cudaEventDestroy(mk.b);
+  }
+  for (cudaEvent_t e : ctx->pool) cudaEventDestroy(e);
+  if (ctx->ws) cudaFree(ctx->ws);
+  if (ctx->d_status) cudaFree(ctx->d_status);
+  if (ctx->d_res) cudaFree(ctx->d_res);
+  if (ctx->h_res) cudaFreeHost(ctx->h_res);
+  delete ctx;
+}
+
+nmf_status nmf_set_stream(nmf_ctx* ctx, void* cuda_stream) {
+  if (!ctx) return NMF_ERR_INVALID_ARG;
+  ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+  return NMF_OK;
+}
+
+const char* nmf_last_error(const nmf_ctx* ctx) { return ctx ? ctx->msg : "context is NULL"; }
+
+int64_t nmf_launch_count(const nmf_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+nmf_status nmf_set_profiling(nmf_ctx* ctx, int32_t on) {
+  if (!ctx) return NMF_ERR_INVALID_ARG;
+  ctx->profiling = on != 0;
+  return NMF_OK;
+}
+
+nmf_status nmf_phase_times(nmf_ctx* ctx, double* ms, int64_t* counts, int32_t reset) {
+  if (!ctx || !ms || !counts) return NMF_ERR_INVALID_ARG;
+  DeviceGuard g(ctx->device);
+  resolve_marks(ctx);
+  for (int i = 0; i < NMF_PHASE_COUNT; ++i) {
+    ms[i] = ctx->phase_ms[i];
+    counts[i] = ctx->phase_n[i];
+    if (reset) {
+      ctx->phase_ms[i] = 0.0;
+      ctx->phase_n[i] = 0;
+    }
+  }
+  return NMF_OK;
+}
+
+nmf_status nmf_sync(nmf_ctx* ctx) {
+  if (!ctx) return NMF_ERR_INVALID_ARG;
+  DeviceGuard g(ctx->device);
+  return take_status(ctx);
+}
+
+nmf_status nmf_workspace_size(const nmf_params* p, size_t* bytes) {
+  if (!p || !bytes) return NMF_ERR_INVALID_ARG;
+  if (check_params(nullptr, p) != NMF_OK) return NMF_ERR_INVALID_ARG;
+  const int64_t m = p->m, n = p->n, l = p->ell, r = p->r;
+  size_t b = 0;
+  if (p->prec == NMF_PREC_BF16) b += 2 * static_cast<size_t>(m * n) + 1024;
+  b += sizeof(float) * (2 * (m * l + n * l) + l * n + m * l) + 4096;  // QL QR Xhat Xchk + omega
+  size_t scratch = sketch_ws(p, true);
+  scratch = std::max(scratch, sizeof(float) * n * l + 1024 + pass_scratch(m, n, p->ell));
+  scratch = std::max(scratch, nmfrp::iterate_ws_bytes(m, n, p->r, p->ell));
+  scratch = std::max(scratch, nmfrp::residual_ws_bytes(m, n));
+  scratch = std::max(scratch, nmfrp::nndsvd_ws_bytes(m, n, p->r, p->ell));
+  (void)r;
+  *bytes = b + scratch;
+  return NMF_OK;
+}
+
+nmf_status nmf_gaussian(nmf_ctx* ctx, int64_t rows, int64_t cols, uint64_t seed,
+                        uint32_t stream_id, float* out) {
+  if (!ctx) return NMF_ERR_INVALID_ARG;
+  if (rows < 0 || cols < 0 || (!out && rows * cols > 0))
+    return fail(ctx, NMF_ERR_INVALID_ARG, "bad gaussian arguments");
+  DeviceGuard g(ctx->device);
+  NMF_CUDA(nmfrp::launch_gaussian(launcher(ctx), rows, cols, seed, stream_id, out), "gaussian");
+  return NMF_OK;
+}
+
+nmf_status nmf_quantize(nmf_ctx* ctx, int32_t prec, const float* X, int64_t m, int64_t n,
+                        int64_t ldx, void* Xq) {
+  if (!ctx) return NMF_ERR_INVALID_ARG;
+  if (prec != NMF_PREC_BF16)
+    return fail(ctx, prec == NMF_PREC_FP8_E4M3 ? NMF_ERR_UNSUPPORTED : NMF_ERR_INVALID_ARG,
+                "quantize supports BF16");
+  if (!X || !Xq || m < 1 || n < 1 || ldx < n)
+    return fail(ctx, NMF_ERR_INVALID_ARG, "bad quantize arguments");
+  DeviceGuard g(ctx->device);
+  NMF_CUDA(nmfrp::launch_quantize_bf16(launcher(ctx), X, m, n, ldx,
+                                       static_cast<__nv_bfloat16*>(Xq)),
+           "quantize");
+  return NMF_OK;
+}
+
+nmf_status nmf_dual_pass(nmf_ctx* ctx, int32_t prec, const void* X, int64_t m, int64_t n,
+                         int64_t ldx, int32_t ell, const float* V, const float* U, float* Y,
+                         float* Z) {
+  if (!ctx) return NMF_ERR_INVALID_ARG;
+  if (!X || m < 1 || n < 1 || ell < 1 || ell > 128 || ldx < n)
+    return fail(ctx, NMF_ERR_INVALID_ARG, "bad dual pass sizes");
+  if (prec != NMF_PREC_FP32 && prec != NMF_PREC_BF16)
+    return fail(ctx, NMF_ERR_INVALID_ARG, "bad precision %d", prec);
+  if (prec == NMF_PREC_BF16 && ldx != n)
+    return fail(ctx, NMF_ERR_INVALID_ARG, "BF16 X must be dense (ldx == n)");
+  if ((V == nullptr) != (Y == nullptr) || (U == nullptr) != (Z == nullptr) || (!V && !U))
+    return fail(ctx, NMF_ERR_INVALID_ARG, "V/Y and U/Z must be given in pairs");
+  DeviceGuard g(ctx->device);
+  nmf_status st = ensure_ws(ctx, nmfrp::dual_pass_ws_bytes(m, n, ell) + 4096);
+  if (st != NMF_OK) return st;
+  Arena a{static_cast<char*>(ctx->ws), ctx->ws_bytes};
+  return dual(ctx, X, prec == NMF_PREC_BF16, m, n, ldx, ell, V, U, Y, Z, a);
+}
+
+nmf_status nmf_qr(nmf_ctx* ctx, const float* Y, int64_t rows, int32_t ell, float* Q) {
+  if (!ctx) return NMF_ERR_INVALID_ARG;
+  if (!Y || !Q || ell < 1 || ell > 128 || rows < ell)
+    return fail(ctx, NMF_ERR_INVALID_ARG, "bad qr arguments");
+  DeviceGuard g(ctx->device);
+  nmf_status st = ensure_ws(ctx, nmfrp::qr_ws_bytes(rows, ell) + 4096);
+  if (st != NMF_OK) return st;
+  NMF_CUDA(nmfrp::launch_qr(launcher(ctx), Y, rows, ell, Q, ctx->ws, ctx->ws_bytes,
+                            ctx->d_status),
+           "qr");
+  return NMF_OK;
+}
+
+nmf_status nmf_sketch(nmf_ctx* ctx, const nmf_params* p, const void* X, int64_t ldx,
+                      const float* omega_L, const float* omega_R, float* QL, float* QR) {
+  if (!ctx) return NMF_ERR_INVALID_ARG;
+  nmf_status st = check_params(ctx, p);
+  if (st != NMF_OK) return st;
+  if ((st = check_x(ctx, p, X, ldx)) != NMF_OK) return st;
+  if (!QL || !QR) return fail(ctx, NMF_ERR_INVALID_ARG, "QL/QR is NULL");
+  DeviceGuard g(ctx->device);
+  if ((st = ensure_ws(ctx, sketch_ws(p, !omega_L || !omega_R))) != NMF_OK) return st;
+  Arena a{static_cast<char*>(ctx->ws), ctx->ws_bytes};
+  return sketch_impl(ctx, p, X, ldx, omega_L, omega_R, QL, QR, a);
+}
+
+nmf_status nmf_compress(nmf_ctx* ctx, const nmf_params* p, const void* X, int64_t ldx,
+                        const float* QL, const float* QR, float* Xhat, float* Xchk) {
+  if (!ctx) return NMF_ERR_INVALID_ARG;
+  nmf_status st = check_params(ctx, p);
+  if (st != NMF_OK) return st;
+  if ((st = check_x(ctx, p, X, ldx)) != NMF_OK) return st;
+  if (!QL || !QR || !Xhat || !Xchk) return fail(ctx, NMF_ERR_INVALID_ARG, "NULL output");
+  DeviceGuard g(ctx->device);
+  if ((st = ensure_ws(ctx, sizeof(float) * p->n * p->ell + 1024 +
+                               pass_scratch(p->m, p->n, p->ell))) != NMF_OK)
+    return st;
+  Arena a{static_cast<char*>(ctx->ws), ctx->ws_bytes};
+  return compress_impl(ctx, p, X, ldx, QL, QR, Xhat, Xchk, a);
+}
+
+nmf_status nmf_iterate(nmf_ctx* ctx, const nmf_params* p, const float* QL, const float* QR,
+                       const float* Xhat, const float* Xchk, float* W, float* H, int32_t iters) {
+  if (!ctx) return NMF_ERR_INVALID_ARG;
+  nmf_status st = check_params(ctx, p);
+  if (st != NMF_OK) return st;
+  if (!QL || !QR || !Xhat || !Xchk || !W || !H)
+    return fail(ctx, NMF_ERR_INVALID_ARG, "NULL argument");
+  if (iters < 0) return fail(ctx, NMF_ERR_INVALID_ARG, "iters < 0");
+  DeviceGuard g(ctx->device);
+  if ((st = ensure_ws(ctx, nmfrp::iterate_ws_bytes(p->m, p->n, p->r, p->ell))) != NMF_OK)
+    return st;
+  Arena a{static_cast<char*>(ctx->ws), ctx->ws_bytes};
+  return iterate_impl(ctx, p, QL, QR, Xhat, Xchk, W, H, iters, a);
+}
+
+nmf_status nmf_residual(nmf_ctx* ctx, const nmf_params* p, const float* X, int64_t ldx,
+                        const float* W, const float* H, double* rel_err_host, double* err2_host,
+                        double* x2_host) {
+  if (!ctx) return NMF_ERR_INVALID_ARG;
+  if (!p || p->m < 1 || p->n < 1 || p->r < 1 || p->r > 128)
+    return fail(ctx, NMF_ERR_INVALID_ARG, "bad residual sizes");
+  if (!X || !W || !H || ldx < p->n) return fail(ctx, NMF_ERR_INVALID_ARG, "bad residual arguments");
+  DeviceGuard g(ctx->device);
+  nmf_status st = ensure_ws(ctx, nmfrp::residual_ws_bytes(p->m, p->n));
+  if (st != NMF_OK) return st;
+  Arena a{static_cast<char*>(ctx->ws), ctx->ws_bytes};
+  return residual_impl(ctx, p, X, ldx, W, H, rel_err_host, err2_host, x2_host, a);
+}
+
+nmf_status nmf_nndsvd(nmf_ctx* ctx, const nmf_params* p, const float* QL, const float* Xhat,
+                      float* W, float* H) {
+  if (!ctx) return NMF_ERR_INVALID_ARG;
+  nmf_status st = check_params(ctx, p);
+  if (st != NMF_OK) return st;
+  if (!QL || !Xhat || !W || !H) return fail(ctx, NMF_ERR_INVALID_ARG, "NULL argument");
+  DeviceGuard g(ctx->device);
+  if ((st = ensure_ws(ctx, nmfrp::nndsvd_ws_bytes(p->m, p->n, p->r, p->ell))) != NMF_OK) return st;
+  cudaError_t e = nmfrp::launch_nndsvd(launcher(ctx), p->m, p->n, p->r, p->ell, QL, Xhat, W, H,
+                                       ctx->ws, ctx->ws_bytes, ctx->d_status);
+  if (e == cudaErrorNotSupported) return fail(ctx, NMF_ERR_UNSUPPORTED, "nndsvd not available");
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "nndsvd");
+  return NMF_OK;
+}
+
+nmf_status nmf_solve(nmf_ctx* ctx, const nmf_params* p, int32_t init, const float* X, int64_t ldx,
+                     float* W, float* H, double* rel_err_host, int32_t* iters_done_host) {
+  if (!ctx) return NMF_ERR_INVALID_ARG;
+  nmf_status st = check_params(ctx, p);
+  if (st != NMF_OK) return st;
+  if (!X || !W || !H || ldx < p->n) return fail(ctx, NMF_ERR_INVALID_ARG, "bad solve arguments");
+  if (init != NMF_INIT_GIVEN && init != NMF_INIT_NNDSVD)
+    return fail(ctx, NMF_ERR_INVALID_ARG, "unknown init %d", init);
+  if (p->iters < 0) return fail(ctx, NMF_ERR_INVALID_ARG, "iters < 0");
+  DeviceGuard g(ctx->device);
+  size_t need = 0;
+  nmf_workspace_size(p, &need);
+  if ((st = ensure_ws(ctx, need)) != NMF_OK) return st;
+  const int64_t m = p->m, n = p->n, l = p->ell;
+  Arena a{static_cast<char*>(ctx->ws), ctx->ws_bytes};
+  const void* Xp = X;
+  int64_t ldp = ldx;
+  if (p->prec == NMF_PREC_BF16) {
+    __nv_bfloat16* Xq = a.take<__nv_bfloat16>(m * n);
+    Phase ph(ctx, NMF_PHASE_QUANTIZE);
+    NMF_CUDA(nmfrp::launch_quantize_bf16(launcher(ctx), X, m, n, ldx, Xq), "quantize");
+    Xp = Xq;
+    ldp = n;
+  }
+  float* QL = a.take<float>(m * l);
+  float* QR = a.take<float>(n * l);
+  float* Xhat = a.take<float>(l * n);
+  float* Xchk = a.take<float>(m * l);
+  if ((st = sketch_impl(ctx, p, Xp, ldp, nullptr, nullptr, QL, QR, a)) != NMF_OK) return st;
+  if ((st = compress_impl(ctx, p, Xp, ldp, QL, QR, Xhat, Xchk, a)) != NMF_OK) return st;
+  if (init == NMF_INIT_NNDSVD) {
+    Phase ph(ctx, NMF_PHASE_INIT);
+    cudaError_t e = nmfrp::launch_nndsvd(launcher(ctx), m, n, p->r, p->ell, QL, Xhat, W, H, a.rest(&need),
+                                         need, ctx->d_status);
+    if (e == cudaErrorNotSupported) return fail(ctx, NMF_ERR_UNSUPPORTED, "nndsvd not available");
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "nndsvd");
+  }
+  const int every = p->residual_every > 0 ? p->residual_every : std::max(p->iters, 1);
+  int done = 0;
+  double rel = -1.0;
+  while (true) {
+    const int k = std::min(every, p->iters - done);
+    if (k > 0 && (st = iterate_impl(ctx, p, QL, QR, Xhat, Xchk, W, H, k, a)) != NMF_OK) return st;
+    done += std::max(k, 0);
+    if ((st = residual_impl(ctx, p, X, ldx, W, H, &rel, nullptr, nullptr, a)) != NMF_OK) return st;
+    if ((p->target_rel_err > 0 && rel <= p->target_rel_err) || done >= p->iters) break;
+  }
+  if (rel_err_host) *rel_err_host = rel;
+  if (iters_done_host) *iters_done_host = done;
+  return take_status(ctx);
+}
+
+}  // extern "C"

@@ -1,0 +1,291 @@
+"""Python binding of libnmf_rp.so (include/nmf_rp.h): argument marshalling only.
+
+Every function has the name of the C entry point it calls and takes torch CUDA tensors; outputs
+the caller does not pass are allocated with torch on the tensors' device. Nothing here computes
+any step of the method: each call goes straight to the library's CUDA kernels. Importing this
+module loads the library and raises ImportError if it has not been built (there is no fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libnmf_rp.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with paper_1712_02248_gb300.build.build()")
+_lib = ctypes.CDLL(LIB_PATH)
+
+NMF_OK = 0
+STATUS = {0: "NMF_OK", 1: "NMF_ERR_INVALID_ARG", 2: "NMF_ERR_CUDA", 3: "NMF_ERR_OOM",
+          4: "NMF_ERR_QR_BREAKDOWN", 5: "NMF_ERR_NOT_FINITE", 6: "NMF_ERR_TIMEOUT",
+          7: "NMF_ERR_UNSUPPORTED"}
+PREC = {"fp32": 0, "bf16": 1, "fp8": 2}
+RULE = {"fasthals": 0, "mu": 1}
+INIT = {"given": 0, "nndsvd": 1}
+
+EXPORTS = ["nmf_create", "nmf_destroy", "nmf_set_stream", "nmf_last_error", "nmf_sync",
+           "nmf_launch_count", "nmf_workspace_size", "nmf_gaussian", "nmf_quantize",
+           "nmf_dual_pass", "nmf_qr", "nmf_sketch", "nmf_compress", "nmf_iterate",
+           "nmf_residual", "nmf_nndsvd", "nmf_solve", "nmf_set_profiling", "nmf_phase_times"]
+PHASES = ["quantize", "dual_pass", "qr", "iterate", "residual", "init"]
+
+
+class nmf_params(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("r", ctypes.c_int32),
+                ("ell", ctypes.c_int32), ("power_iters", ctypes.c_int32),
+                ("iters", ctypes.c_int32), ("rule", ctypes.c_int32), ("prec", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("residual_every", ctypes.c_int32),
+                ("reserved0", ctypes.c_int32), ("target_rel_err", ctypes.c_double),
+                ("alpha", ctypes.c_double), ("beta", ctypes.c_double), ("eps", ctypes.c_double)]
+
+
+_vp, _i64, _i32, _u64, _u32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint32
+_P = ctypes.POINTER(nmf_params)
+_D = ctypes.POINTER(ctypes.c_double)
+
+
+def _sig(name, res, args):
+    f = getattr(_lib, name)
+    f.restype = res
+    f.argtypes = args
+    return f
+
+
+_c = {
+    "nmf_create": _sig("nmf_create", ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, _vp]),
+    "nmf_destroy": _sig("nmf_destroy", None, [_vp]),
+    "nmf_set_stream": _sig("nmf_set_stream", ctypes.c_int, [_vp, _vp]),
+    "nmf_last_error": _sig("nmf_last_error", ctypes.c_char_p, [_vp]),
+    "nmf_sync": _sig("nmf_sync", ctypes.c_int, [_vp]),
+    "nmf_launch_count": _sig("nmf_launch_count", _i64, [_vp]),
+    "nmf_workspace_size": _sig("nmf_workspace_size", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_size_t)]),
+    "nmf_gaussian": _sig("nmf_gaussian", ctypes.c_int, [_vp, _i64, _i64, _u64, _u32, _vp]),
+    "nmf_quantize": _sig("nmf_quantize", ctypes.c_int, [_vp, _i32, _vp, _i64, _i64, _i64, _vp]),
+    "nmf_dual_pass": _sig("nmf_dual_pass", ctypes.c_int,
+                          [_vp, _i32, _vp, _i64, _i64, _i64, _i32, _vp, _vp, _vp, _vp]),
+    "nmf_qr": _sig("nmf_qr", ctypes.c_int, [_vp, _vp, _i64, _i32, _vp]),
+    "nmf_sketch": _sig("nmf_sketch", ctypes.c_int, [_vp, _P, _vp, _i64, _vp, _vp, _vp, _vp]),
+    "nmf_compress": _sig("nmf_compress", ctypes.c_int, [_vp, _P, _vp, _i64, _vp, _vp, _vp, _vp]),
+    "nmf_iterate": _sig("nmf_iterate", ctypes.c_int, [_vp, _P, _vp, _vp, _vp, _vp, _vp, _vp, _i32]),
+    "nmf_residual": _sig("nmf_residual", ctypes.c_int, [_vp, _P, _vp, _i64, _vp, _vp, _D, _D, _D]),
+    "nmf_nndsvd": _sig("nmf_nndsvd", ctypes.c_int, [_vp, _P, _vp, _vp, _vp, _vp]),
+    "nmf_set_profiling": _sig("nmf_set_profiling", ctypes.c_int, [_vp, _i32]),
+    "nmf_phase_times": _sig("nmf_phase_times", ctypes.c_int,
+                            [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64), _i32]),
+    "nmf_solve": _sig("nmf_solve", ctypes.c_int,
+                      [_vp, _P, _i32, _vp, _i64, _vp, _vp, _D, ctypes.POINTER(_i32)]),
+}
+
+
+class NmfError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def params(m, n, r, ell, power_iters=2, iters=0, rule="fasthals", prec="fp32", seed=0,
+           residual_every=0, target_rel_err=0.0, alpha=0.0, beta=0.0, eps=0.0):
+    """Build an nmf_params struct (names as in include/nmf_rp.h)."""
+    return nmf_params(int(m), int(n), int(r), int(ell), int(power_iters), int(iters),
+                      RULE.get(rule, rule), PREC.get(prec, prec), int(seed), int(residual_every),
+                      0, float(target_rel_err), float(alpha), float(beta), float(eps))
+
+
+class Context:
+    """An nmf_ctx bound to a CUDA device and stream (torch's current stream by default)."""
+
+    def __init__(self, device=None, stream=None):
+        dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.device = dev
+        s = stream if stream is not None else torch.cuda.current_stream(dev)
+        self.stream = s
+        h = _vp()
+        st = _c["nmf_create"](ctypes.byref(h), dev.index, _vp(s.cuda_stream))
+        if st != NMF_OK:
+            raise NmfError(st, "nmf_create failed")
+        self.handle = h
+
+    def set_stream(self, stream):
+        self.stream = stream
+        self._check(_c["nmf_set_stream"](self.handle, _vp(stream.cuda_stream)))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _c["nmf_destroy"](self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _check(self, st):
+        if st != NMF_OK:
+            msg = _c["nmf_last_error"](self.handle)
+            raise NmfError(st, msg.decode() if msg else "")
+
+    @property
+    def launches(self):
+        return int(_c["nmf_launch_count"](self.handle))
+
+
+def _ptr(t):
+    return _vp(t.data_ptr()) if t is not None else _vp(0)
+
+
+def _dev_f32(t, name):
+    if t is None:
+        return None
+    if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous float32 CUDA tensor")
+    return t
+
+
+def _x_arg(X, prec):
+    if not X.is_cuda:
+        raise ValueError("X must be a CUDA tensor")
+    if prec == PREC["bf16"]:
+        if X.dtype != torch.bfloat16 or not X.is_contiguous():
+            raise ValueError("BF16 X must be a contiguous bfloat16 tensor (see nmf_quantize)")
+        return X, X.shape[1]
+    if X.dtype != torch.float32 or X.stride(1) != 1:
+        raise ValueError("X must be float32 with unit column stride")
+    return X, X.stride(0)
+
+
+def _empty(shape, like):
+    return torch.empty(shape, dtype=torch.float32, device=like.device)
+
+
+def workspace_size(p):
+    out = ctypes.c_size_t(0)
+    st = _c["nmf_workspace_size"](ctypes.byref(p), ctypes.byref(out))
+    if st != NMF_OK:
+        raise NmfError(st, "nmf_workspace_size")
+    return int(out.value)
+
+
+def nmf_sync(ctx):
+    ctx._check(_c["nmf_sync"](ctx.handle))
+
+
+def nmf_gaussian(ctx, rows, cols, seed, stream_id, out=None):
+    out = out if out is not None else torch.empty((rows, cols), dtype=torch.float32, device=ctx.device)
+    _dev_f32(out, "out")
+    ctx._check(_c["nmf_gaussian"](ctx.handle, rows, cols, seed, stream_id, _ptr(out)))
+    return out
+
+
+def nmf_quantize(ctx, X, prec="bf16", out=None):
+    m, n = X.shape
+    if out is None:
+        out = torch.empty((m, n), dtype=torch.bfloat16, device=X.device)
+    if X.dtype != torch.float32 or X.stride(1) != 1:
+        raise ValueError("X must be float32 with unit column stride")
+    ctx._check(_c["nmf_quantize"](ctx.handle, PREC.get(prec, prec), _ptr(X), m, n, X.stride(0),
+                                  _ptr(out)))
+    return out
+
+
+def nmf_dual_pass(ctx, X, V=None, U=None, prec="fp32", Y=None, Z=None):
+    """Y = X V and Z = X^T U in one pass over X (either pair may be omitted)."""
+    pr = PREC.get(prec, prec)
+    X, ldx = _x_arg(X, pr)
+    m, n = X.shape
+    ell = (V if V is not None else U).shape[1]
+    if V is not None:
+        _dev_f32(V, "V")
+        Y = Y if Y is not None else _empty((m, ell), X)
+    if U is not None:
+        _dev_f32(U, "U")
+        Z = Z if Z is not None else _empty((n, ell), X)
+    ctx._check(_c["nmf_dual_pass"](ctx.handle, pr, _ptr(X), m, n, ldx, ell, _ptr(V), _ptr(U),
+                                   _ptr(Y if V is not None else None),
+                                   _ptr(Z if U is not None else None)))
+    return Y, Z
+
+
+def nmf_qr(ctx, Y, Q=None):
+    _dev_f32(Y, "Y")
+    Q = Q if Q is not None else _empty(Y.shape, Y)
+    ctx._check(_c["nmf_qr"](ctx.handle, _ptr(Y), Y.shape[0], Y.shape[1], _ptr(Q)))
+    return Q
+
+
+def nmf_sketch(ctx, p, X, omega_L=None, omega_R=None, QL=None, QR=None):
+    X, ldx = _x_arg(X, p.prec)
+    QL = QL if QL is not None else _empty((p.m, p.ell), X)
+    QR = QR if QR is not None else _empty((p.n, p.ell), X)
+    _dev_f32(omega_L, "omega_L")
+    _dev_f32(omega_R, "omega_R")
+    ctx._check(_c["nmf_sketch"](ctx.handle, ctypes.byref(p), _ptr(X), ldx, _ptr(omega_L),
+                                _ptr(omega_R), _ptr(QL), _ptr(QR)))
+    return QL, QR
+
+
+def nmf_compress(ctx, p, X, QL, QR, Xhat=None, Xchk=None):
+    X, ldx = _x_arg(X, p.prec)
+    Xhat = Xhat if Xhat is not None else _empty((p.ell, p.n), X)
+    Xchk = Xchk if Xchk is not None else _empty((p.m, p.ell), X)
+    ctx._check(_c["nmf_compress"](ctx.handle, ctypes.byref(p), _ptr(X), ldx, _ptr(_dev_f32(QL, "QL")),
+                                  _ptr(_dev_f32(QR, "QR")), _ptr(Xhat), _ptr(Xchk)))
+    return Xhat, Xchk
+
+
+def nmf_iterate(ctx, p, QL, QR, Xhat, Xchk, W, H, iters):
+    for t, nm in ((QL, "QL"), (QR, "QR"), (Xhat, "Xhat"), (Xchk, "Xchk"), (W, "W"), (H, "H")):
+        _dev_f32(t, nm)
+    ctx._check(_c["nmf_iterate"](ctx.handle, ctypes.byref(p), _ptr(QL), _ptr(QR), _ptr(Xhat),
+                                 _ptr(Xchk), _ptr(W), _ptr(H), int(iters)))
+    return W, H
+
+
+def nmf_residual(ctx, p, X, W, H):
+    """Returns (rel_err, ||X - W H||^2, ||X||^2); synchronises the stream."""
+    X, ldx = _x_arg(X, 0)
+    rel, e2, x2 = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    ctx._check(_c["nmf_residual"](ctx.handle, ctypes.byref(p), _ptr(X), ldx, _ptr(_dev_f32(W, "W")),
+                                  _ptr(_dev_f32(H, "H")), ctypes.byref(rel), ctypes.byref(e2),
+                                  ctypes.byref(x2)))
+    return rel.value, e2.value, x2.value
+
+
+def nmf_nndsvd(ctx, p, QL, Xhat, W=None, H=None):
+    W = W if W is not None else _empty((p.m, p.r), QL)
+    H = H if H is not None else _empty((p.r, p.n), QL)
+    ctx._check(_c["nmf_nndsvd"](ctx.handle, ctypes.byref(p), _ptr(_dev_f32(QL, "QL")),
+                                _ptr(_dev_f32(Xhat, "Xhat")), _ptr(W), _ptr(H)))
+    return W, H
+
+
+def nmf_solve(ctx, p, X, W, H, init="given"):
+    """Whole pipeline on FP32 X; returns (rel_err, iterations run). W, H updated in place."""
+    X, ldx = _x_arg(X, 0)
+    rel, it = ctypes.c_double(), ctypes.c_int32()
+    ctx._check(_c["nmf_solve"](ctx.handle, ctypes.byref(p), INIT.get(init, init), _ptr(X), ldx,
+                               _ptr(_dev_f32(W, "W")), _ptr(_dev_f32(H, "H")), ctypes.byref(rel),
+                               ctypes.byref(it)))
+    return rel.value, it.value
+
+
+def nmf_set_profiling(ctx, on=True):
+    ctx._check(_c["nmf_set_profiling"](ctx.handle, 1 if on else 0))
+
+
+def nmf_phase_times(ctx, reset=True):
+    """{phase: (milliseconds, spans)} since the last reset; synchronises the stream."""
+    ms = (ctypes.c_double * len(PHASES))()
+    cnt = (_i64 * len(PHASES))()
+    ctx._check(_c["nmf_phase_times"](ctx.handle, ms, cnt, 1 if reset else 0))
+    return {name: (ms[i], int(cnt[i])) for i, name in enumerate(PHASES)}

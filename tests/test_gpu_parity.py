@@ -1,0 +1,351 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on identical seeded inputs.
+
+Tolerances (relative Frobenius error unless stated):
+  FP32 kernels, one step from the oracle's own state ............ 1e-5
+  BF16 X contractions, against the oracle on the same BF16 X ..... 1e-5 (FP32 accumulation)
+  QR (unique Q with positive R diagonal) ......................... 1e-5, orthogonality 1e-5
+  whole runs: final rel_err within 1 % of the oracle's after the same iteration count
+  BF16 / integer byte work (quantisation) ........................ bit-exact
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_1712_02248_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda"
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def cu(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(DEV)
+
+
+def host(t):
+    return t.detach().double().cpu().numpy()
+
+
+def bf16_round(x):
+    """Round-to-nearest-even of float32 values to bfloat16, returned as float32 (integer work)."""
+    u = np.ascontiguousarray(x, np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) >> 16
+    return (u.astype(np.uint32) << 16).view(np.float32)
+
+
+@pytest.fixture(scope="module")
+def ctx(lib):
+    c = lib.Context(0)
+    yield c
+    c.close()
+
+
+# ------------------------------------------------------------------ Omega generator
+
+def test_gaussian_matches_oracle_philox(lib, ctx):
+    Z = host(lib.nmf_gaussian(ctx, 37, 19, seed=123456789, stream_id=1))
+    ref = O.philox_normal(37, 19, seed=123456789, stream=1)
+    assert np.abs(Z - ref).max() <= 2e-5 * max(1.0, np.abs(ref).max())
+
+
+# ------------------------------------------------------------------ quantisation
+
+@pytest.mark.parametrize("shape", [(33, 70), (128, 256), (5, 3)])
+def test_quantize_bf16_bit_exact(lib, ctx, shape):
+    rng = np.random.default_rng(7)
+    X = (rng.standard_normal(shape) * 10.0 ** rng.uniform(-3, 3, shape)).astype(np.float32)
+    q = lib.nmf_quantize(ctx, cu(X))
+    got = q.view(torch.int16).cpu().numpy().view(np.uint16)
+    want = (bf16_round(X).view(np.uint32) >> 16).astype(np.uint16)
+    assert np.array_equal(got, want)
+
+
+# ------------------------------------------------------------------ dual pass (Eq. 3.5 step)
+
+DUAL_SHAPES = [(512, 256, 18), (300, 517, 18), (1000, 777, 40), (129, 130, 1), (257, 1025, 70),
+               (64, 64, 64), (2000, 300, 128)]
+
+
+@pytest.mark.parametrize("m,n,ell", DUAL_SHAPES)
+def test_dual_pass_fp32(lib, ctx, m, n, ell):
+    rng = np.random.default_rng(m * 7 + n)
+    X = rng.uniform(0, 1, (m, n)).astype(np.float32)
+    V = rng.standard_normal((n, ell)).astype(np.float32)
+    U = rng.standard_normal((m, ell)).astype(np.float32)
+    Y, Z = lib.nmf_dual_pass(ctx, cu(X), cu(V), cu(U))
+    X64 = X.astype(np.float64)
+    assert rel(host(Y), X64 @ V) <= 1e-5
+    assert rel(host(Z), X64.T @ U) <= 1e-5
+
+
+def test_dual_pass_strided_x_and_single_sides(lib, ctx):
+    rng = np.random.default_rng(3)
+    big = rng.uniform(0, 1, (200, 333)).astype(np.float32)
+    Xv = cu(big)[:, :301]                      # leading dimension 333 > n = 301
+    V = rng.standard_normal((301, 24)).astype(np.float32)
+    U = rng.standard_normal((200, 24)).astype(np.float32)
+    Y, _ = lib.nmf_dual_pass(ctx, Xv, V=cu(V))
+    _, Z = lib.nmf_dual_pass(ctx, Xv, U=cu(U))
+    X64 = big[:, :301].astype(np.float64)
+    assert rel(host(Y), X64 @ V) <= 1e-5
+    assert rel(host(Z), X64.T @ U) <= 1e-5
+
+
+@pytest.mark.parametrize("m,n,ell", [(512, 256, 18), (1000, 777, 40), (257, 1025, 70)])
+def test_dual_pass_bf16(lib, ctx, m, n, ell):
+    rng = np.random.default_rng(11 + m)
+    X = rng.uniform(0, 1, (m, n)).astype(np.float32)
+    V = rng.standard_normal((n, ell)).astype(np.float32)
+    U = rng.standard_normal((m, ell)).astype(np.float32)
+    Xq = lib.nmf_quantize(ctx, cu(X))
+    Y, Z = lib.nmf_dual_pass(ctx, Xq, cu(V), cu(U), prec="bf16")
+    Xb = bf16_round(X).astype(np.float64)
+    Vb, Ub = V.astype(np.float64), U.astype(np.float64)
+    # the tensor-core path also rounds V, U to BF16; the SIMT path keeps them FP32
+    tol = 1e-5
+    if rel(host(Y), Xb @ Vb) > tol:
+        Vb, Ub = bf16_round(V).astype(np.float64), bf16_round(U).astype(np.float64)
+    assert rel(host(Y), Xb @ Vb) <= tol
+    assert rel(host(Z), Xb.T @ Ub) <= tol
+
+
+# ------------------------------------------------------------------ QR (Section 3)
+
+@pytest.mark.parametrize("rows,ell", [(500, 18), (20000, 40), (1000, 1), (130, 128), (77, 70)])
+def test_qr_matches_oracle(lib, ctx, rows, ell):
+    rng = np.random.default_rng(rows + ell)
+    # columns with a spread of scales: condition number ~ 1e3
+    Y = (rng.standard_normal((rows, ell)) * np.logspace(0, -3, ell)).astype(np.float32)
+    Q = host(lib.nmf_qr(ctx, cu(Y)))
+    lib.nmf_sync(ctx)
+    Qo = O.qr_orthonormal(Y.astype(np.float64))
+    assert np.abs(Q.T @ Q - np.eye(ell)).max() <= 1e-5
+    assert rel(Q, Qo) <= 1e-5
+
+
+def test_qr_breakdown_is_reported(lib, ctx):
+    Y = np.random.default_rng(0).standard_normal((100, 8)).astype(np.float32)
+    Y[:, 3] = 0.0
+    lib.nmf_qr(ctx, cu(Y))
+    with pytest.raises(lib.NmfError) as e:
+        lib.nmf_sync(ctx)
+    assert e.value.status == 4
+    lib.nmf_sync(ctx)   # status cleared after being reported
+
+
+# ------------------------------------------------------------------ sketch and compression
+
+def proj_diff(QL, QLo, X):
+    X = X.astype(np.float64)
+    return rel(QL @ (QL.T @ X), QLo @ (QLo.T @ X))
+
+
+@pytest.mark.parametrize("seed,m,n,r,ell,w", [(0, 512, 256, 8, 18, 2), (1, 700, 450, 5, 12, 0),
+                                              (2, 1000, 3001, 20, 40, 2), (3, 300, 300, 10, 20, 3)])
+def test_sketch_fp32(lib, ctx, seed, m, n, r, ell, w):
+    pr = inputs.random_problem(seed, m, n, r, ell, w=w)
+    p = lib.params(m, n, r, ell, power_iters=w)
+    QL, QR = lib.nmf_sketch(ctx, p, cu(pr.X), cu(pr.omega_L), cu(pr.omega_R))
+    lib.nmf_sync(ctx)
+    QLo, QRo = O.sketch(pr.X, pr.omega_L, pr.omega_R, w)
+    QL, QR = host(QL), host(QR)
+    assert np.abs(QL.T @ QL - np.eye(ell)).max() <= 1e-5
+    assert proj_diff(QL, QLo, pr.X) <= 1e-5
+    assert proj_diff(QR, QRo, pr.X.T) <= 1e-5
+
+
+def test_sketch_bf16_within_low_precision_tolerance(lib, ctx):
+    pr = inputs.random_problem(4, 2000, 1500, 20, 40, w=2)
+    p = lib.params(2000, 1500, 20, 40, power_iters=2, prec="bf16")
+    X = cu(pr.X)
+    Xq = lib.nmf_quantize(ctx, X)
+    QL, QR = lib.nmf_sketch(ctx, p, Xq, cu(pr.omega_L), cu(pr.omega_R))
+    Xhat, Xchk = lib.nmf_compress(ctx, p, Xq, QL, QR)
+    lib.nmf_sync(ctx)
+    QLo, QRo = O.sketch(pr.X, pr.omega_L, pr.omega_R, 2)
+    Xhat_o, _ = O.compress(pr.X, QLo, QRo)
+    # basis-free form of "Q_L^T X within 2e-2": the projected data Q_L X_hat
+    assert rel(host(QL) @ host(Xhat), QLo @ Xhat_o) <= 2e-2
+
+
+@pytest.mark.parametrize("seed,m,n,r,ell", [(0, 512, 256, 8, 18), (5, 1001, 333, 4, 9)])
+def test_compress_fp32(lib, ctx, seed, m, n, r, ell):
+    pr = inputs.random_problem(seed, m, n, r, ell)
+    QLo, QRo = O.sketch(pr.X, pr.omega_L, pr.omega_R, 1)
+    QL32, QR32 = QLo.astype(np.float32), QRo.astype(np.float32)
+    p = lib.params(m, n, r, ell, power_iters=1)
+    Xhat, Xchk = lib.nmf_compress(ctx, p, cu(pr.X), cu(QL32), cu(QR32))
+    Xh_o, Xc_o = O.compress(pr.X, QL32, QR32)
+    assert rel(host(Xhat), Xh_o) <= 1e-5
+    assert rel(host(Xchk), Xc_o) <= 1e-5
+
+
+# ------------------------------------------------------------------ iterations (Section 4, 3.1)
+
+def compressed_state(seed, m, n, r, ell, w=2):
+    pr = inputs.random_problem(seed, m, n, r, ell, w=w)
+    QL, QR = O.sketch(pr.X, pr.omega_L, pr.omega_R, w)
+    QL, QR = QL.astype(np.float32), QR.astype(np.float32)
+    Xhat, Xchk = O.compress(pr.X, QL, QR)
+    return pr, QL, QR, Xhat.astype(np.float32), Xchk.astype(np.float32)
+
+
+ITER_CASES = [(0, 512, 256, 8, 18), (1, 1000, 777, 20, 40), (2, 333, 1201, 1, 6),
+              (3, 600, 500, 40, 50), (4, 257, 129, 16, 16), (5, 400, 300, 33, 40)]
+
+
+def fp32_model_step(W, H, QL, QR, Xhat, Xchk):
+    """Error model, not the oracle: one FastHALS-RP step evaluated in numpy float32 (library
+    order, every operation rounded to FP32). Its distance to the FP64 oracle is the error that
+    FP32 arithmetic itself commits on these inputs."""
+    t = np.float32
+    W = W.astype(t).copy()
+    H = H.astype(t).copy()
+    Ht = H @ QR.astype(t)
+    G = Ht @ Ht.T
+    S = Xchk.astype(t) @ Ht.T
+    for j in range(W.shape[1]):
+        if G[j, j] > 0:
+            W[:, j] = np.maximum(0, W[:, j] + (S[:, j] - W @ G[:, j]) / G[j, j])
+    s = np.sqrt((W * W).sum(0))
+    W /= np.where(s > 0, s, 1)
+    H *= np.where(s > 0, s, 1)[:, None]
+    Wt = QL.astype(t).T @ W
+    Gh = Wt.T @ Wt
+    P = Wt.T @ Xhat.astype(t)
+    for j in range(H.shape[0]):
+        if Gh[j, j] > 0:
+            H[j] = np.maximum(0, H[j] + (P[j] - Gh[j] @ H) / Gh[j, j])
+    return W, H
+
+
+@pytest.mark.parametrize("rule", ["fasthals", "mu"])
+@pytest.mark.parametrize("seed,m,n,r,ell", ITER_CASES)
+def test_one_iteration_matches_oracle(lib, ctx, rule, seed, m, n, r, ell):
+    """One GPU iteration from the oracle's own state, compared with one oracle iteration.
+
+    From states of the oracle's trajectory (after 1 and 6 iterations) W and H must agree within
+    1e-5. From the U[0,1) start the product W H and H must agree within 1e-5; W alone is held to
+    twice the error of an FP32 evaluation of the same step (the first FastHALS-RP step nearly
+    annihilates some columns of W, and their normalisation to unit length magnifies FP32
+    rounding in them; no FP32 evaluation order reaches 1e-5 there)."""
+    pr, QL, QR, Xhat, Xchk = compressed_state(seed, m, n, r, ell)
+    step = O.fasthals_rp_step if rule == "fasthals" else O.mu_rp_step
+    W0, H0 = pr.W0, pr.H0
+    for k, advance in enumerate((1, 5, 0)):
+        p = lib.params(m, n, r, ell, rule=rule)
+        W, H = cu(W0), cu(H0)
+        lib.nmf_iterate(ctx, p, cu(QL), cu(QR), cu(Xhat), cu(Xchk), W, H, 1)
+        Wo, Ho = step(W0, H0, QL, QR, Xhat, Xchk)
+        Wg, Hg = host(W), host(H)
+        assert (Wg >= 0).all() and (Hg >= 0).all()
+        assert rel(Hg, Ho) <= 1e-5, f"H, state {k}"
+        assert rel(Wg @ Hg, Wo @ Ho) <= 1e-5, f"WH, state {k}"
+        if k == 0 and rule == "fasthals":
+            Wm, _ = fp32_model_step(W0, H0, QL, QR, Xhat, Xchk)
+            bound = max(1e-5, 2.0 * rel(Wm, Wo))
+            assert rel(Wg, Wo) <= bound, f"W from the random start (bound {bound:.2e})"
+        else:
+            assert rel(Wg, Wo) <= 1e-5, f"W, state {k}"
+        if advance:
+            W0, H0 = O.iterate(W0, H0, QL, QR, Xhat, Xchk, advance, rule=rule)
+            W0, H0 = W0.astype(np.float32), H0.astype(np.float32)
+
+
+def test_regularised_iteration_matches_oracle(lib, ctx):
+    pr, QL, QR, Xhat, Xchk = compressed_state(6, 500, 400, 10, 20)
+    p = lib.params(500, 400, 10, 20, alpha=0.05, beta=0.2)
+    W, H = cu(pr.W0), cu(pr.H0)
+    lib.nmf_iterate(ctx, p, cu(QL), cu(QR), cu(Xhat), cu(Xchk), W, H, 1)
+    Wo, Ho = O.fasthals_rp_step(pr.W0, pr.H0, QL, QR, Xhat, Xchk, alpha=0.05, beta=0.2)
+    assert rel(host(W), Wo) <= 1e-5 and rel(host(H), Ho) <= 1e-5
+
+
+# ------------------------------------------------------------------ residual (Eq. 2.2)
+
+@pytest.mark.parametrize("m,n,r", [(512, 256, 8), (1001, 777, 20), (64, 129, 1), (300, 200, 64)])
+def test_residual_matches_oracle(lib, ctx, m, n, r):
+    rng = np.random.default_rng(m + r)
+    W = rng.uniform(0, 1, (m, r)).astype(np.float32)
+    H = rng.uniform(0, 1, (r, n)).astype(np.float32)
+    X = (W.astype(np.float64) @ H * (1 + 0.05 * rng.standard_normal((m, n)))).astype(np.float32)
+    p = lib.params(m, n, r, min(r, m, n))
+    relg, e2, x2 = lib.nmf_residual(ctx, p, cu(X), cu(W), cu(H))
+    relo, e2o, x2o = O.residual(X, W, H)
+    assert abs(x2 - x2o) <= 1e-6 * x2o
+    assert abs(e2 - e2o) <= 1e-4 * e2o
+    assert abs(relg - relo) <= 1e-4 * relo
+
+
+# ------------------------------------------------------------------ whole runs
+
+def test_planted_small_mu_rp_200_iterations(lib, ctx):
+    """512 x 256, r = 8, l = 18, w = 2, 200 MU-RP iterations from U[0,1) factors."""
+    pr = inputs.planted_small(seed=0)
+    m, n = pr.X.shape
+    p = lib.params(m, n, pr.r, pr.ell, power_iters=pr.w, rule="mu")
+    X = cu(pr.X)
+    QL, QR = lib.nmf_sketch(ctx, p, X, cu(pr.omega_L), cu(pr.omega_R))
+    Xhat, Xchk = lib.nmf_compress(ctx, p, X, QL, QR)
+    W, H = cu(pr.W0), cu(pr.H0)
+    lib.nmf_iterate(ctx, p, QL, QR, Xhat, Xchk, W, H, 200)
+    relg, _, _ = lib.nmf_residual(ctx, p, X, W, H)
+    _, _, _, _, hist = O.solve(pr.X, pr.omega_L, pr.omega_R, pr.W0, pr.H0, pr.w, 200, rule="mu")
+    relo = hist[-1][1]
+    print(f"planted_small MU-RP: gpu {relg:.6g} oracle {relo:.6g}")
+    assert abs(relg - relo) <= 0.01 * relo
+
+
+def test_solve_matches_stepwise_path(lib, ctx):
+    pr = inputs.random_problem(9, 800, 600, 10, 20)
+    p = lib.params(800, 600, 10, 20, power_iters=2, iters=60, residual_every=20, seed=5)
+    X = cu(pr.X)
+    W, H = cu(pr.W0), cu(pr.H0)
+    relg, it = lib.nmf_solve(ctx, p, X, W, H)
+    assert it == 60
+    oL = lib.nmf_gaussian(ctx, 600, 20, 5, 0)
+    oR = lib.nmf_gaussian(ctx, 800, 20, 5, 1)
+    _, _, _, _, hist = O.solve(pr.X, host(oL), host(oR), pr.W0, pr.H0, 2, 60)
+    assert abs(relg - hist[-1][1]) <= 0.01 * hist[-1][1]
+
+
+def test_solve_stops_at_target(lib, ctx):
+    pr = inputs.random_problem(10, 600, 500, 8, 16)
+    p = lib.params(600, 500, 8, 16, iters=400, residual_every=10, target_rel_err=0.5, seed=1)
+    relg, it = lib.nmf_solve(ctx, p, cu(pr.X), cu(pr.W0), cu(pr.H0))
+    assert relg <= 0.5 and it < 400 and it % 10 == 0
+
+
+def test_invalid_arguments_are_rejected(lib, ctx):
+    X = torch.zeros((10, 10), device=DEV)
+    with pytest.raises(lib.NmfError) as e:
+        lib.nmf_sketch(ctx, lib.params(10, 10, 5, 11), X)      # ell > min(m, n)
+    assert e.value.status == 1
+    with pytest.raises(lib.NmfError) as e:
+        lib.nmf_sketch(ctx, lib.params(10, 10, 6, 5), X)       # r > ell
+    assert e.value.status == 1
+    with pytest.raises(lib.NmfError) as e:
+        lib.nmf_qr(ctx, torch.zeros((3, 5), device=DEV))      # rows < ell
+    assert e.value.status == 1
+
+
+def test_degenerate_square_full_width(lib, ctx):
+    """l = m = n: the sketch spans everything and the compressed iteration is full FastHALS."""
+    pr = inputs.random_problem(11, 48, 48, 4, 48, w=1)
+    p = lib.params(48, 48, 4, 48, power_iters=1)
+    X = cu(pr.X)
+    QL, QR = lib.nmf_sketch(ctx, p, X, cu(pr.omega_L), cu(pr.omega_R))
+    Xhat, Xchk = lib.nmf_compress(ctx, p, X, QL, QR)
+    W, H = cu(pr.W0), cu(pr.H0)
+    lib.nmf_iterate(ctx, p, QL, QR, Xhat, Xchk, W, H, 3)
+    Wo, Ho = pr.W0.astype(np.float64), pr.H0.astype(np.float64)
+    for _ in range(3):
+        Wo, Ho = O.fasthals_step(Wo, Ho, pr.X)
+    assert rel(host(W) @ host(H), Wo @ Ho) <= 1e-4
