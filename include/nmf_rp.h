@@ -61,6 +61,16 @@ typedef enum {
   NMF_INIT_NNDSVD = 1        /* NNDSVD of the compressed data (Boutsidis & Gallopoulos 2008) */
 } nmf_init;
 
+/* nmf_params.flags bits. */
+enum {
+  /* run the iterations as one kernel launch per stage instead of one persistent cooperative
+     launch for all iterations (same arithmetic; for comparison and for r > 32, which always
+     uses the per-stage kernels) */
+  NMF_FLAG_STAGED_ITERATE = 1,
+  /* run BF16 passes over X on the SIMT pipes instead of the tcgen05 tensor-core kernel */
+  NMF_FLAG_SIMT_DUAL_PASS = 2
+};
+
 typedef struct {
   int64_t m, n;              /* X is m x n */
   int32_t r;                 /* number of components (the paper's k), 1 <= r <= ell */
@@ -71,7 +81,7 @@ typedef struct {
   int32_t prec;              /* nmf_precision of the sketch / compression contractions */
   uint64_t seed;             /* Philox4x32-10 key for Omega when the caller passes none */
   int32_t residual_every;    /* nmf_solve: exact residual every k iterations (0: at the end) */
-  int32_t reserved0;
+  int32_t flags;             /* NMF_FLAG_* bits (0 = defaults) */
   double target_rel_err;     /* nmf_solve: stop at the first check with rel_err <= target (0: off) */
   double alpha, beta;        /* Section 4.1 sparsity / smoothness weights on H (FastHALS-RP) */
   double eps;                /* MU-RP denominator guard (<= 0: 1e-12) */

@@ -41,21 +41,36 @@ inline int pad_to(int v, int q) { return (v + q - 1) / q * q; }
 cudaError_t launch_gaussian(const Launcher& L, int64_t rows, int64_t cols, uint64_t seed,
                             uint32_t stream_id, float* out);
 
-// FP32 -> BF16 (RNE) copy of X (m x n, leading dimension ldx) into dense Xq (m x n).
+// FP32 -> BF16 (RNE) copy of X (m x n, leading dimension ldx) into Xq (m x n, leading
+// dimension ldq >= n; columns n..ldq-1 are set to zero).
 cudaError_t launch_quantize_bf16(const Launcher& L, const float* X, int64_t m, int64_t n,
-                                 int64_t ldx, __nv_bfloat16* Xq);
+                                 int64_t ldx, __nv_bfloat16* Xq, int64_t ldq);
 
 // Dual pass Y = X V (m x ell), Z = X^T U (n x ell). x_bf16 selects the element type of X.
 // ws: workspace for partial sums (size from dual_pass_ws_bytes).
+// BF16 X with both products goes to the tensor-core kernel when TMA can address X (ldx a
+// multiple of 8, X 16-byte aligned) unless force_simt is set.
 size_t dual_pass_ws_bytes(int64_t m, int64_t n, int ell);
 cudaError_t launch_dual_pass(const Launcher& L, const void* X, bool x_bf16, int64_t m, int64_t n,
                              int64_t ldx, int ell, const float* V, const float* U, float* Y,
-                             float* Z, void* ws, size_t ws_bytes);
+                             float* Z, void* ws, size_t ws_bytes, int* status,
+                             bool force_simt = false);
+// tcgen05 + TMA dual pass (BF16 X).
+bool dual_pass_tc_supported(int64_t m, int64_t n, int64_t ldx, int ell, const void* X);
+size_t dual_pass_tc_ws_bytes(int64_t m, int64_t n, int ell);
+cudaError_t launch_dual_pass_tc(const Launcher& L, const __nv_bfloat16* X, int64_t m, int64_t n,
+                                int64_t ldx, int ell, const float* V, const float* U, float* Y,
+                                float* Z, void* ws, size_t ws_bytes, int* status);
 
 // Thin QR via CholeskyQR2 with FP64 Gram and Cholesky. Q may alias Y.
 size_t qr_ws_bytes(int64_t rows, int ell);
 cudaError_t launch_qr(const Launcher& L, const float* Y, int64_t rows, int ell, float* Q,
                       void* ws, size_t ws_bytes, int* status);
+// Up to two independent QRs (same ell) through one set of launches; qr_ws_bytes(max rows, ell)
+// of workspace suffices.
+cudaError_t launch_qr_batch(const Launcher& L, int nmat, const float* const* Y,
+                            const int64_t* rows, int ell, float* const* Q, void* ws,
+                            size_t ws_bytes, int* status);
 
 // Iterations of FastHALS-RP (rule 0) or MU-RP (rule 1).
 struct IterArgs {
@@ -73,6 +88,13 @@ struct IterArgs {
 size_t iterate_ws_bytes(int64_t m, int64_t n, int r, int ell);
 cudaError_t launch_iterate(const Launcher& L, const IterArgs& a, int iters, void* ws,
                            size_t ws_bytes);
+
+// All iterations in one cooperative launch (r <= 32); status receives NMF_ERR_TIMEOUT if a
+// grid barrier wait runs out.
+bool iterate_persistent_supported(int r, int ell);
+size_t iterate_persistent_ws_bytes(int r, int ell);
+cudaError_t launch_iterate_persistent(const Launcher& L, const IterArgs& a, int iters, void* ws,
+                                      size_t ws_bytes, int* status);
 
 // Residual partial sums: writes 2 doubles (||X-WH||^2, ||X||^2) to out2 (device).
 size_t residual_ws_bytes(int64_t m, int64_t n);

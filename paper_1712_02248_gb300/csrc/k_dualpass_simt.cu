@@ -215,13 +215,18 @@ cudaError_t dispatch(const Launcher& L, const XT* X, int64_t m, int64_t n, int64
 
 size_t dual_pass_ws_bytes(int64_t m, int64_t n, int ell) {
   const Split s = choose_split(m, n, lp_for(ell));
-  return sizeof(float) * static_cast<size_t>(s.nb * m * ell + s.na * n * ell);
+  const size_t simt = sizeof(float) * static_cast<size_t>(s.nb * m * ell + s.na * n * ell);
+  const size_t tc = dual_pass_tc_ws_bytes(m, n, ell);
+  return simt > tc ? simt : tc;
 }
 
 cudaError_t launch_dual_pass(const Launcher& L, const void* X, bool x_bf16, int64_t m, int64_t n,
                              int64_t ldx, int ell, const float* V, const float* U, float* Y,
-                             float* Z, void* ws, size_t ws_bytes) {
+                             float* Z, void* ws, size_t ws_bytes, int* status, bool force_simt) {
   if (ws_bytes < dual_pass_ws_bytes(m, n, ell)) return cudaErrorInvalidValue;
+  if (x_bf16 && V && U && !force_simt && dual_pass_tc_supported(m, n, ldx, ell, X))
+    return launch_dual_pass_tc(L, static_cast<const __nv_bfloat16*>(X), m, n, ldx, ell, V, U, Y,
+                               Z, ws, ws_bytes, status);
   if (x_bf16)
     return dispatch(L, static_cast<const __nv_bfloat16*>(X), m, n, ldx, ell, V, U, Y, Z,
                     static_cast<float*>(ws));

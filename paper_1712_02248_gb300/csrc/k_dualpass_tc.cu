@@ -1,0 +1,555 @@
+// Fused dual pass over a BF16 X on the 5th-generation tensor cores:
+//   Y = X V (m x l) and Z = X^T U (n x l) from one TMA stream of X.
+// This is every sketch pass (Section 3, Eq. 3.5: X applied to one chain's basis and X^T to the
+// other's) and the compression (Section 4: X_chk = X Q_R, X_hat = Q_L^T X).
+//
+// Tiling. A CTA owns a rectangle of row blocks (128 rows) x column tiles (128 columns). For each
+// 128 x 128 tile of X, staged in shared memory by TMA as two 128B-swizzled 128 x 64 halves:
+//   Y block (128 x LP) += X_tile (K-major A, K = columns)         . V_tile^T  (B: LP x 128)
+//   Z tile  (128 x LP) += X_tile viewed MN-major (A, K = rows)    . U_block^T (B: LP x 128)
+// (tcgen05.mma kind::f16, M = 128, N = LP = l rounded up to 16, BF16 inputs, FP32 accumulation
+// in tensor memory). The Y accumulator of the current row block is double-buffered in TMEM; the
+// Z accumulators of all the CTA's column tiles stay in TMEM for the whole rectangle. V^T and U^T
+// are BF16 copies made by a small preparation kernel (rows l..LP-1 zero).
+//
+// Warp roles (192 threads): warps 0-3 drain TMEM (each its 32-lane sub-partition) and write the
+// partial sums, warp 4 issues the TMA loads, warp 5 allocates TMEM and issues the MMAs. Partial
+// sums of Y (one per column group) and Z (one per row group) are added by the fixed-order slot
+// reduction of the SIMT path. Every mbarrier wait is bounded; on time-out the kernel latches
+// NMF_ERR_TIMEOUT, drains what it issued and frees its tensor memory.
+#include <cuda.h>
+
+#include "common.cuh"
+
+namespace nmfrp {
+namespace {
+
+constexpr int kRows = 128;          // rows per block (MMA M for Y)
+constexpr int kCols = 128;          // columns per tile (MMA M for Z)
+constexpr int kHalfCols = 64;       // 128-byte swizzle atom: 64 BF16 columns
+constexpr int kThreads = 192;
+constexpr long long kWaitCycles = 4000000000LL;   // every mbarrier wait gives up after ~2 s
+
+// ------------------------------------------------------------------ PTX wrappers
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait; returns false (and raises the CTA's abort flag) when it runs out.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_f) {
+  const long long t0 = clock64();
+  while (clock64() - t0 < kWaitCycles) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*abort_f) return false;
+  }
+  *abort_f = 1;
+  return false;
+}
+
+// Bounded wait that ignores the abort flag (draining copies and MMAs already issued).
+__device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (clock64() - t0 < kWaitCycles && !mbar_try_wait(bar, parity)) {
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                            uint32_t bar, uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+      " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar), "l"(policy)
+      : "memory");
+}
+
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+__device__ __forceinline__ uint64_t policy_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+
+// D[tmem] (+)= A[smem desc] * B[smem desc], kind::f16, one CTA.
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// Arrive on an mbarrier when all MMAs issued so far by this thread have completed.
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+
+// 32 lanes x 16 consecutive 32-bit TMEM columns -> 16 registers per thread.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor (tcgen05 format): start, leading / stride byte offsets,
+// version 1, 128-byte swizzle.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((addr >> 4) & 0x3FFF);
+  d |= static_cast<uint64_t>((lbo >> 4) & 0x3FFF) << 16;
+  d |= static_cast<uint64_t>((sbo >> 4) & 0x3FFF) << 32;
+  d |= 1ull << 46;
+  d |= 2ull << 61;
+  return d;
+}
+
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16, M = 128, N = LP.
+__host__ __device__ constexpr uint32_t idesc_bf16(int N, int a_mn_major) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(a_mn_major) << 15) |
+         (static_cast<uint32_t>(N >> 3) << 17) | (static_cast<uint32_t>(kRows >> 4) << 24);
+}
+
+// ------------------------------------------------------------------ kernel
+
+struct TcArgs {
+  int64_t m, n;
+  int ell;
+  int n_rowgroups, n_colgroups;   // grid = n_colgroups x n_rowgroups
+  int64_t n_rowblocks;            // ceil(m / 128)
+  int tiles_per_group;            // column tiles per column group (<= NCT)
+  int64_t n_coltiles;             // ceil(n / 128)
+  float* Ypart;                   // [n_colgroups][m][ell]
+  float* Zpart;                   // [n_rowgroups][n][ell]
+  int* status;
+};
+
+template <int LP, int NCT, int STAGES>
+__global__ void __launch_bounds__(kThreads, 1) dual_pass_tc_kernel(
+    const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapV,
+    const __grid_constant__ CUtensorMap mapU, TcArgs a) {
+  constexpr uint32_t kXHalf = kRows * kHalfCols * 2;   // 16 KB
+  constexpr uint32_t kBBox = LP * kHalfCols * 2;        // LP rows x 128 B
+  constexpr uint32_t kStage = 2 * kXHalf + 4 * kBBox;   // X halves, V boxes, U boxes
+  constexpr uint32_t kTxBytes = kStage;
+  constexpr int AS = (LP + 31) / 32 * 32;               // accumulator stride in TMEM columns
+  constexpr int kTmemNeed = (2 + NCT) * AS;
+  constexpr uint32_t kTmemCols = kTmemNeed <= 32 ? 32 : kTmemNeed <= 64 ? 64 : kTmemNeed <= 128
+                                                                                ? 128
+                                                                                : kTmemNeed <= 256
+                                                                                      ? 256
+                                                                                      : 512;
+  static_assert(kTmemNeed <= 512, "tensor memory budget");
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES];
+  __shared__ __align__(8) uint64_t ydone_bar[2], yfree_bar[2], zdone_bar, drain_bar;
+  __shared__ uint32_t tmem_base;
+  __shared__ volatile int abort_f;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int cg = blockIdx.x, rg = blockIdx.y;
+  // this CTA's row blocks [rb0, rb1) and column tiles [ct0, ct1)
+  const int64_t rb0 = rg * a.n_rowblocks / a.n_rowgroups;
+  const int64_t rb1 = (rg + 1) * a.n_rowblocks / a.n_rowgroups;
+  const int64_t ct0 = static_cast<int64_t>(cg) * a.tiles_per_group;
+  const int64_t ct1 = min(a.n_coltiles, ct0 + a.tiles_per_group);
+  const int nrb = static_cast<int>(rb1 - rb0), nct = static_cast<int>(ct1 - ct0);
+  const int ntiles = nrb * nct;
+
+  if (threadIdx.x == 0) {
+    abort_f = 0;
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(smem_u32(&full_bar[s]), 1);
+      mbar_init(smem_u32(&empty_bar[s]), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&ydone_bar[b]), 1);
+      mbar_init(smem_u32(&yfree_bar[b]), 128);
+    }
+    mbar_init(smem_u32(&zdone_bar), 1);
+    mbar_init(smem_u32(&drain_bar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 5) tmem_alloc(smem_u32(&tmem_base), kTmemCols);
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+
+  if (warp == 4) {
+    // ---------------- TMA producer
+    if (lane == 0 && ntiles > 0) {
+      const uint64_t pol_x = policy_evict_first(), pol_b = policy_evict_last();
+      int issued = 0;
+      for (int tI = 0; tI < ntiles; ++tI) {
+        const int s = tI % STAGES;
+        const uint32_t ph = (tI / STAGES) & 1;
+        if (!mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1, &abort_f)) break;
+        const int lr = tI / nct, lc = tI - lr * nct;
+        const int row0 = static_cast<int>((rb0 + lr) * kRows);
+        const int col0 = static_cast<int>((ct0 + lc) * kCols);
+        unsigned char* st = smem + s * kStage;
+        const uint32_t fb = smem_u32(&full_bar[s]);
+        mbar_expect_tx(fb, kTxBytes);
+        tma_load_2d(smem_u32(st), &mapX, col0, row0, fb, pol_x);
+        tma_load_2d(smem_u32(st + kXHalf), &mapX, col0 + kHalfCols, row0, fb, pol_x);
+        tma_load_2d(smem_u32(st + 2 * kXHalf), &mapV, col0, 0, fb, pol_b);
+        tma_load_2d(smem_u32(st + 2 * kXHalf + kBBox), &mapV, col0 + kHalfCols, 0, fb, pol_b);
+        tma_load_2d(smem_u32(st + 2 * kXHalf + 2 * kBBox), &mapU, row0, 0, fb, pol_b);
+        tma_load_2d(smem_u32(st + 2 * kXHalf + 3 * kBBox), &mapU, row0 + kHalfCols, 0, fb, pol_b);
+        issued = tI + 1;
+      }
+      // the last copy issued on each stage has landed before the CTA may leave
+      for (int tI = issued - STAGES > 0 ? issued - STAGES : 0; tI < issued; ++tI) {
+        mbar_drain(smem_u32(&full_bar[tI % STAGES]), (tI / STAGES) & 1);
+      }
+    }
+  } else if (warp == 5) {
+    // ---------------- MMA issuer
+    if (lane == 0 && ntiles > 0) {
+      constexpr uint32_t idY = idesc_bf16(LP, 0);   // A = X tile, K-major
+      constexpr uint32_t idZ = idesc_bf16(LP, 1);   // A = X tile, MN-major
+      int tI = 0;
+      bool ok = true;
+      for (int lr = 0; lr < nrb && ok; ++lr) {
+        const int yb = lr & 1;
+        if (!mbar_wait(smem_u32(&yfree_bar[yb]), ((lr >> 1) & 1) ^ 1, &abort_f)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t dY = tmem + static_cast<uint32_t>(yb * AS);
+        for (int lc = 0; lc < nct; ++lc, ++tI) {
+          const int s = tI % STAGES;
+          const uint32_t ph = (tI / STAGES) & 1;
+          if (!mbar_wait(smem_u32(&full_bar[s]), ph, &abort_f)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t st = smem_u32(smem + s * kStage);
+          const uint32_t xa = st, xb = st + kXHalf;
+          const uint32_t v0 = st + 2 * kXHalf, v1 = v0 + kBBox;
+          const uint32_t u0 = st + 2 * kXHalf + 2 * kBBox, u1 = u0 + kBBox;
+          const uint32_t dZ = tmem + static_cast<uint32_t>((2 + lc) * AS);
+#pragma unroll
+          for (int kk = 0; kk < 8; ++kk) {
+            const uint32_t off = (kk & 3) * 32;
+            // Y: K = columns of the tile
+            const uint64_t aY = sdesc((kk < 4 ? xa : xb) + off, 16, 1024);
+            const uint64_t bY = sdesc((kk < 4 ? v0 : v1) + off, 16, 1024);
+            mma_bf16(dY, aY, bY, idY, (lc > 0 || kk > 0) ? 1u : 0u);
+            // Z: K = rows of the tile; MN-major A spans both halves (LBO = 16 KB)
+            const uint64_t aZ = sdesc(xa + kk * 2048, kXHalf, 1024);
+            const uint64_t bZ = sdesc((kk < 4 ? u0 : u1) + off, 16, 1024);
+            mma_bf16(dZ, aZ, bZ, idZ, (lr > 0 || kk > 0) ? 1u : 0u);
+          }
+          mma_commit(smem_u32(&empty_bar[s]));
+        }
+        if (!ok) break;
+        mma_commit(smem_u32(&ydone_bar[yb]));
+      }
+      if (ok) mma_commit(smem_u32(&zdone_bar));
+      // drain: all MMAs issued by this thread complete before tensor memory is freed
+      mma_commit(smem_u32(&drain_bar));
+      mbar_drain(smem_u32(&drain_bar), 0);
+    }
+  } else {
+    // ---------------- epilogue: warps 0-3, TMEM lanes 32 warp .. 32 warp + 31
+    const uint32_t lane_base = static_cast<uint32_t>(warp * 32) << 16;
+    float v[LP];
+    for (int lr = 0; lr < (ntiles > 0 ? nrb : 0); ++lr) {
+      const int yb = lr & 1;
+      if (!mbar_wait(smem_u32(&ydone_bar[yb]), (lr >> 1) & 1, &abort_f)) break;
+      tc_fence_after();
+#pragma unroll
+      for (int c = 0; c < LP; c += 16) tmem_ld16(tmem + lane_base + yb * AS + c, v + c);
+      tc_fence_before();
+      mbar_arrive(smem_u32(&yfree_bar[yb]));
+      const int64_t row = (rb0 + lr) * kRows + warp * 32 + lane;
+      if (row < a.m) {
+        float* dst = a.Ypart + (static_cast<int64_t>(cg) * a.m + row) * a.ell;
+#pragma unroll
+        for (int k = 0; k < LP; ++k)
+          if (k < a.ell) dst[k] = v[k];
+      }
+    }
+    if (ntiles > 0 && mbar_wait(smem_u32(&zdone_bar), 0, &abort_f)) {
+      tc_fence_after();
+      for (int lc = 0; lc < nct; ++lc) {
+#pragma unroll
+        for (int c = 0; c < LP; c += 16)
+          tmem_ld16(tmem + lane_base + (2 + lc) * AS + c, v + c);
+        const int64_t col = (ct0 + lc) * kCols + warp * 32 + lane;
+        if (col < a.n) {
+          float* dst = a.Zpart + (static_cast<int64_t>(rg) * a.n + col) * a.ell;
+#pragma unroll
+          for (int k = 0; k < LP; ++k)
+            if (k < a.ell) dst[k] = v[k];
+        }
+      }
+      tc_fence_before();
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && abort_f) latch(a.status, kStTimeout);
+  if (warp == 5) {
+    tc_fence_after();
+    tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
+// V (rows x ell, FP32) -> Vt (LP x ld, BF16), rows ell..LP-1 and columns rows..ld-1 zero.
+__global__ void transpose_bf16_kernel(const float* __restrict__ V, int64_t rows, int ell, int LP,
+                                      int64_t ld, __nv_bfloat16* __restrict__ Vt) {
+  __shared__ float tile[32][33];
+  const int64_t r0 = static_cast<int64_t>(blockIdx.x) * 32;
+  const int k0 = blockIdx.y * 32;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int64_t r = r0 + i;
+    const int k = k0 + threadIdx.x;
+    tile[i][threadIdx.x] = (r < rows && k < ell) ? V[r * ell + k] : 0.f;
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int k = k0 + i;
+    const int64_t r = r0 + threadIdx.x;
+    if (k < LP && r < ld) Vt[static_cast<int64_t>(k) * ld + r] = __float2bfloat16_rn(tile[threadIdx.x][i]);
+  }
+}
+
+__global__ void reduce_slots_tc_kernel(const float* __restrict__ part, int slots, int64_t total,
+                                       float* __restrict__ out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    float s = 0.f;
+    for (int k = 0; k < slots; ++k) s += part[k * total + e];
+    out[e] = s;
+  }
+}
+
+// ------------------------------------------------------------------ host side
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// 2-D BF16 tensor map: inner dimension `inner` elements (row pitch `pitch` elements), `outer`
+// rows, box `box_inner` x `box_outer`, 128-byte swizzle, zero fill outside.
+bool make_map(CUtensorMap* map, const void* base, uint64_t inner, uint64_t outer, uint64_t pitch,
+              uint32_t box_inner, uint32_t box_outer) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {inner, outer};
+  const cuuint64_t strides[1] = {pitch * 2};
+  const cuuint32_t box[2] = {box_inner, box_outer};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box,
+            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int num_sms() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms > 0 ? sms : 148;
+}
+
+int lp16(int ell) { return (ell + 15) / 16 * 16; }
+
+struct Plan {
+  int LP, NCT, stages;
+  int rowgroups, colgroups, tiles_per_group;
+  int64_t rowblocks, coltiles;
+};
+
+Plan plan_for(int64_t m, int64_t n, int ell) {
+  Plan p;
+  p.LP = lp16(ell);
+  const int as = (p.LP + 31) / 32 * 32;
+  p.NCT = 512 / as - 2;
+  if (p.NCT > 14) p.NCT = 14;
+  p.stages = p.LP <= 64 ? 3 : 2;
+  p.rowblocks = cdiv(m, kRows);
+  p.coltiles = cdiv(n, kCols);
+  p.colgroups = static_cast<int>(cdiv(p.coltiles, p.NCT));
+  p.tiles_per_group = static_cast<int>(cdiv(p.coltiles, p.colgroups));
+  int rg = num_sms() / p.colgroups;
+  if (rg < 1) rg = 1;
+  if (rg > p.rowblocks) rg = static_cast<int>(p.rowblocks);
+  p.rowgroups = rg;
+  return p;
+}
+
+template <int LP, int NCT, int STAGES>
+cudaError_t launch_t(const Launcher& L, const CUtensorMap& mx, const CUtensorMap& mv,
+                     const CUtensorMap& mu, const TcArgs& a) {
+  auto k = dual_pass_tc_kernel<LP, NCT, STAGES>;
+  constexpr size_t stage = 2 * kRows * kHalfCols * 2 + 4 * LP * kHalfCols * 2;
+  size_t smem = STAGES * stage + 1024;
+  if (smem < 120 * 1024) smem = 120 * 1024;   // one CTA per SM: it owns the tensor memory
+  cudaError_t err =
+      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  if (err != cudaSuccess) return err;
+  dim3 grid(a.n_colgroups, a.n_rowgroups);
+  k<<<grid, kThreads, smem, L.stream>>>(mx, mv, mu, a);
+  L.count();
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool dual_pass_tc_supported(int64_t m, int64_t n, int64_t ldx, int ell, const void* X) {
+  if (ell < 1 || ell > 128) return false;
+  if (ldx % 8 != 0 || (reinterpret_cast<uintptr_t>(X) & 15) != 0) return false;
+  if (m > (int64_t(1) << 31) - kRows || n > (int64_t(1) << 31) - kCols) return false;
+  return encode_fn() != nullptr;
+}
+
+size_t dual_pass_tc_ws_bytes(int64_t m, int64_t n, int ell) {
+  const Plan p = plan_for(m, n, ell);
+  const int64_t ldv = (n + 7) / 8 * 8, ldu = (m + 7) / 8 * 8;
+  return sizeof(float) * static_cast<size_t>(p.colgroups * m * ell + p.rowgroups * n * ell) +
+         2 * static_cast<size_t>(p.LP) * (ldv + ldu) + 4096;
+}
+
+cudaError_t launch_dual_pass_tc(const Launcher& L, const __nv_bfloat16* X, int64_t m, int64_t n,
+                                int64_t ldx, int ell, const float* V, const float* U, float* Y,
+                                float* Z, void* ws, size_t ws_bytes, int* status) {
+  if (ws_bytes < dual_pass_tc_ws_bytes(m, n, ell)) return cudaErrorInvalidValue;
+  const Plan p = plan_for(m, n, ell);
+  const int64_t ldv = (n + 7) / 8 * 8, ldu = (m + 7) / 8 * 8;
+  char* w = static_cast<char*>(ws);
+  float* Ypart = reinterpret_cast<float*>(w);
+  float* Zpart = Ypart + p.colgroups * m * ell;
+  uintptr_t q = reinterpret_cast<uintptr_t>(Zpart + p.rowgroups * n * ell);
+  q = (q + 255) & ~uintptr_t(255);
+  __nv_bfloat16* Vt = reinterpret_cast<__nv_bfloat16*>(q);
+  q += 2 * static_cast<size_t>(p.LP) * ldv;
+  q = (q + 255) & ~uintptr_t(255);
+  __nv_bfloat16* Ut = reinterpret_cast<__nv_bfloat16*>(q);
+  {
+    dim3 gv(static_cast<unsigned>(cdiv(ldv, 32)), static_cast<unsigned>(cdiv(p.LP, 32)));
+    transpose_bf16_kernel<<<gv, dim3(32, 8), 0, L.stream>>>(V, n, ell, p.LP, ldv, Vt);
+    dim3 gu(static_cast<unsigned>(cdiv(ldu, 32)), static_cast<unsigned>(cdiv(p.LP, 32)));
+    transpose_bf16_kernel<<<gu, dim3(32, 8), 0, L.stream>>>(U, m, ell, p.LP, ldu, Ut);
+    L.count(2);
+  }
+  CUtensorMap mx, mv, mu;
+  if (!make_map(&mx, X, static_cast<uint64_t>(n), static_cast<uint64_t>(m),
+                static_cast<uint64_t>(ldx), kHalfCols, kRows) ||
+      !make_map(&mv, Vt, static_cast<uint64_t>(ldv), static_cast<uint64_t>(p.LP),
+                static_cast<uint64_t>(ldv), kHalfCols, static_cast<uint32_t>(p.LP)) ||
+      !make_map(&mu, Ut, static_cast<uint64_t>(ldu), static_cast<uint64_t>(p.LP),
+                static_cast<uint64_t>(ldu), kHalfCols, static_cast<uint32_t>(p.LP)))
+    return cudaErrorInvalidValue;
+  TcArgs a;
+  a.m = m;
+  a.n = n;
+  a.ell = ell;
+  a.n_rowgroups = p.rowgroups;
+  a.n_colgroups = p.colgroups;
+  a.n_rowblocks = p.rowblocks;
+  a.tiles_per_group = p.tiles_per_group;
+  a.n_coltiles = p.coltiles;
+  a.Ypart = Ypart;
+  a.Zpart = Zpart;
+  a.status = status;
+  cudaError_t err;
+  switch (p.LP) {
+    case 16: err = launch_t<16, 14, 3>(L, mx, mv, mu, a); break;
+    case 32: err = launch_t<32, 14, 3>(L, mx, mv, mu, a); break;
+    case 48: err = launch_t<48, 6, 3>(L, mx, mv, mu, a); break;
+    case 64: err = launch_t<64, 6, 3>(L, mx, mv, mu, a); break;
+    case 80: err = launch_t<80, 3, 2>(L, mx, mv, mu, a); break;
+    case 96: err = launch_t<96, 3, 2>(L, mx, mv, mu, a); break;
+    case 112: err = launch_t<112, 2, 2>(L, mx, mv, mu, a); break;
+    case 128: err = launch_t<128, 2, 2>(L, mx, mv, mu, a); break;
+    default: return cudaErrorInvalidValue;
+  }
+  if (err != cudaSuccess) return err;
+  const int64_t ty = m * ell, tz = n * ell;
+  reduce_slots_tc_kernel<<<static_cast<unsigned>(cdiv(ty, 256) < 4096 ? cdiv(ty, 256) : 4096), 256,
+                           0, L.stream>>>(Ypart, p.colgroups, ty, Y);
+  reduce_slots_tc_kernel<<<static_cast<unsigned>(cdiv(tz, 256) < 4096 ? cdiv(tz, 256) : 4096), 256,
+                           0, L.stream>>>(Zpart, p.rowgroups, tz, Z);
+  L.count(2);
+  return cudaGetLastError();
+}
+
+}  // namespace nmfrp

@@ -56,16 +56,16 @@ __global__ void gaussian_kernel(int64_t total, uint2 key, uint32_t stream_id, fl
 }
 
 __global__ void quantize_bf16_kernel(const float* __restrict__ X, int64_t m, int64_t n, int64_t ldx,
-                                     __nv_bfloat16* __restrict__ Xq) {
-  const int64_t total = m * n;
+                                     __nv_bfloat16* __restrict__ Xq, int64_t ldq) {
+  const int64_t total = m * ldq;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e / n, j = e - i * n;
-    Xq[e] = __float2bfloat16_rn(X[i * ldx + j]);
+    const int64_t i = e / ldq, j = e - i * ldq;
+    Xq[e] = __float2bfloat16_rn(j < n ? X[i * ldx + j] : 0.f);
   }
 }
 
-// Vectorised variant: n % 4 == 0, ldx % 4 == 0, X 16-byte aligned.
+// Vectorised variant: n % 4 == 0, ldx % 4 == 0, X 16-byte aligned, ldq == n.
 __global__ void quantize_bf16_vec4_kernel(const float* __restrict__ X, int64_t m, int64_t n,
                                           int64_t ldx, __nv_bfloat16* __restrict__ Xq) {
   const int64_t n4 = n / 4, total = m * n4;
@@ -105,13 +105,14 @@ cudaError_t launch_gaussian(const Launcher& L, int64_t rows, int64_t cols, uint6
 }
 
 cudaError_t launch_quantize_bf16(const Launcher& L, const float* X, int64_t m, int64_t n,
-                                 int64_t ldx, __nv_bfloat16* Xq) {
+                                 int64_t ldx, __nv_bfloat16* Xq, int64_t ldq) {
   if (m * n <= 0) return cudaSuccess;
-  const bool vec = (n % 4 == 0) && (ldx % 4 == 0) && (reinterpret_cast<uintptr_t>(X) % 16 == 0);
+  const bool vec = (n % 4 == 0) && (ldx % 4 == 0) && (ldq == n) &&
+                   (reinterpret_cast<uintptr_t>(X) % 16 == 0);
   if (vec)
     quantize_bf16_vec4_kernel<<<grid_for(m * n / 4, 256), 256, 0, L.stream>>>(X, m, n, ldx, Xq);
   else
-    quantize_bf16_kernel<<<grid_for(m * n, 256), 256, 0, L.stream>>>(X, m, n, ldx, Xq);
+    quantize_bf16_kernel<<<grid_for(m * ldq, 256), 256, 0, L.stream>>>(X, m, n, ldx, Xq, ldq);
   L.count();
   return cudaGetLastError();
 }

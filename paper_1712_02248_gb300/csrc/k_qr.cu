@@ -1,10 +1,18 @@
-// Thin QR of a tall FP32 matrix (Section 3, Eq. 3.4-3.5: Q from the QR decomposition of the
+// Thin QR of tall FP32 matrices (Section 3, Eq. 3.4-3.5: Q from the QR decomposition of the
 // sketch) by CholeskyQR2 (Fukaya, Nakatsukasa, Yanagisawa & Yamamoto 2014): twice
-//   G = Y^T Y (FP64 sums of exact FP32 products), G = R^T R (FP64 Cholesky), Y <- Y R^{-1}.
-// R^{-1} is formed in FP64. The first sweep applies it with FP64 accumulation (its entries are
-// as large as cond(Y), and products of that size cancel); the second sweep's factor is close to
-// the identity and is applied in FP32. The result is the Q of the QR factorisation whose R has a
-// positive diagonal, rounded to FP32.
+//   G = Y^T Y,  G = R^T R (Cholesky),  Y <- Y R^{-1}.
+//
+// Precision. Sweep 1 sees cond(G) = cond(Y)^2, so its Gram matrix is accumulated in float-float
+// arithmetic (error-free products by FMA and Knuth's TwoSum; about 48 significant bits, relative
+// error near 1e-12 over a 128-row slab) and summed across slabs in FP64; its Cholesky factor and
+// R^{-1} are formed in FP64 (an l x l problem) and R^{-1} is applied in float-float, since its
+// entries reach cond(Y) and their products cancel. The FP64 pipe of this GPU runs at 1/58 of the
+// FP32 rate, so the X-sized Gram and application run on the FP32 pipes. Sweep 2 starts from a
+// nearly orthonormal matrix: its Gram is float-float, its Cholesky and application FP32. The
+// result is the Q of the QR factorisation whose R has a positive diagonal.
+//
+// Up to two independent matrices (the two chains of the sketch) go through each kernel in one
+// launch: blockIdx.y (blockIdx.x for the Cholesky) selects the matrix.
 #include "common.cuh"
 
 namespace nmfrp {
@@ -12,90 +20,125 @@ namespace {
 
 constexpr int kGramRows = 128;   // rows per Gram block
 constexpr int kGramThreads = 256;
+constexpr int kMaxMats = 2;
 
-// Partial Gram of a 128-row slab: Gp[blk][p][q] for p <= q (2x2 register tiles, FP64 FMA).
+struct QrBatch {
+  const float* Y[kMaxMats];     // inputs of this sweep
+  float* Q[kMaxMats];           // outputs of this sweep
+  int64_t rows[kMaxMats];
+  int64_t part_off[kMaxMats];   // first Gram-partial slot of each matrix
+  int nmat;
+};
+
+// hi + lo += a * b with an error-free product and Knuth's TwoSum on the running sum.
+__device__ __forceinline__ void ff_fma(float a, float b, float& hi, float& lo) {
+  const float p = __fmul_rn(a, b);
+  const float e = __fmaf_rn(a, b, -p);
+  const float s = __fadd_rn(hi, p);
+  const float v = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, v)), __fsub_rn(p, v));
+  hi = s;
+  lo = __fadd_rn(lo, __fadd_rn(err, e));
+}
+
+// Partial Gram of a 128-row slab in float-float: Gp[slot][p][q] (FP64) for p <= q.
 template <int LP>
-__global__ void __launch_bounds__(kGramThreads) gram_partial_kernel(
-    const float* __restrict__ Y, int64_t rows, int ell, double* __restrict__ Gp) {
+__global__ void __launch_bounds__(kGramThreads) gram_partial_kernel(QrBatch b, int ell,
+                                                                    double* __restrict__ Gp) {
   extern __shared__ __align__(16) float Ysm[];   // [kGramRows][LP]
-  auto Ys = reinterpret_cast<float(*)[LP]>(Ysm);
-  const int t = threadIdx.x;
+  const int mat = blockIdx.y;
+  if (mat >= b.nmat) return;
+  const int64_t rows = b.rows[mat];
   const int64_t r0 = static_cast<int64_t>(blockIdx.x) * kGramRows;
+  if (r0 >= rows) return;
+  const float* Y = b.Y[mat];
+  const int t = threadIdx.x;
   for (int e = t; e < kGramRows * LP; e += kGramThreads) {
     const int i = e / LP, k = e - i * LP;
     const int64_t gr = r0 + i;
-    Ys[i][k] = (gr < rows && k < ell) ? Y[gr * ell + k] : 0.f;
+    Ysm[e] = (gr < rows && k < ell) ? Y[gr * ell + k] : 0.f;
   }
   __syncthreads();
   constexpr int T2 = LP / 2;
-  double* out = Gp + static_cast<int64_t>(blockIdx.x) * LP * LP;
+  double* out = Gp + (b.part_off[mat] + blockIdx.x) * LP * LP;
   for (int tile = t; tile < T2 * T2; tile += kGramThreads) {
     const int P = tile / T2, Qi = tile - P * T2;
     if (P > Qi) continue;
-    double a00 = 0, a01 = 0, a10 = 0, a11 = 0;
+    float h00 = 0, h01 = 0, h10 = 0, h11 = 0, l00 = 0, l01 = 0, l10 = 0, l11 = 0;
 #pragma unroll 4
     for (int i = 0; i < kGramRows; ++i) {
-      const float2 a = *reinterpret_cast<const float2*>(&Ys[i][2 * P]);
-      const float2 b = *reinterpret_cast<const float2*>(&Ys[i][2 * Qi]);
-      const double a0 = a.x, a1 = a.y, b0 = b.x, b1 = b.y;
-      a00 = fma(a0, b0, a00);
-      a01 = fma(a0, b1, a01);
-      a10 = fma(a1, b0, a10);
-      a11 = fma(a1, b1, a11);
+      const float2 a = *reinterpret_cast<const float2*>(&Ysm[i * LP + 2 * P]);
+      const float2 c = *reinterpret_cast<const float2*>(&Ysm[i * LP + 2 * Qi]);
+      ff_fma(a.x, c.x, h00, l00);
+      ff_fma(a.x, c.y, h01, l01);
+      ff_fma(a.y, c.x, h10, l10);
+      ff_fma(a.y, c.y, h11, l11);
     }
-    out[(2 * P) * LP + 2 * Qi] = a00;
-    out[(2 * P) * LP + 2 * Qi + 1] = a01;
-    out[(2 * P + 1) * LP + 2 * Qi] = a10;
-    out[(2 * P + 1) * LP + 2 * Qi + 1] = a11;
+    out[(2 * P) * LP + 2 * Qi] = static_cast<double>(h00) + static_cast<double>(l00);
+    out[(2 * P) * LP + 2 * Qi + 1] = static_cast<double>(h01) + static_cast<double>(l01);
+    out[(2 * P + 1) * LP + 2 * Qi] = static_cast<double>(h10) + static_cast<double>(l10);
+    out[(2 * P + 1) * LP + 2 * Qi + 1] = static_cast<double>(h11) + static_cast<double>(l11);
   }
 }
 
-// G[e] = sum_b Gp[b][e] for every entry e < LP*LP: one warp per entry, lanes stride the parts,
-// then a fixed shuffle tree (deterministic).
-__global__ void sum_parts_kernel(const double* __restrict__ Gp, int nparts, int entries,
+// G[mat][e] = sum over the matrix's slabs of Gp[slot][e]: one warp per entry, lanes stride the
+// slabs, then a fixed shuffle tree (deterministic).
+__global__ void sum_parts_kernel(const double* __restrict__ Gp, QrBatch b, int entries,
                                  double* __restrict__ G) {
+  const int mat = blockIdx.y;
+  if (mat >= b.nmat) return;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= entries) return;
+  const int64_t nparts = cdiv(b.rows[mat], kGramRows);
+  const double* base = Gp + b.part_off[mat] * entries;
   double s = 0.0;
-  for (int b = lane; b < nparts; b += 32) s += Gp[static_cast<int64_t>(b) * entries + warp];
+  for (int64_t k = lane; k < nparts; k += 32) s += base[k * entries + warp];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) G[warp] = s;
+  if (lane == 0) G[mat * entries + warp] = s;
 }
 
-// One CTA: Cholesky G = R^T R (in place on the upper triangle), T = R^{-1}. T's strictly upper
-// part is kept transposed in the lower triangle of the same array and its diagonal separately.
-// Writes T (ell x ell, row-major, FP32) for the application kernel.
-template <int LP>
-__global__ void __launch_bounds__(1024) chol_inv_kernel(const double* __restrict__ Gin, int ell,
-                                                        float* __restrict__ Tout,
-                                                        double* __restrict__ Tout64, int* status) {
+__device__ __forceinline__ double rsqrt_any(double v) { return rsqrt(v); }
+__device__ __forceinline__ float rsqrt_any(float v) { return rsqrtf(v); }
+
+// One CTA per matrix: Cholesky G = R^T R in precision F (in place on the upper triangle), then
+// T = R^{-1}, whose strictly upper part is kept transposed in the lower triangle of the same
+// array. Writes T split as T_hi + T_lo (two FP32 arrays, ell x ell row-major).
+template <int LP, typename F>
+__global__ void __launch_bounds__(256) chol_inv_kernel(const double* __restrict__ Gin, QrBatch b,
+                                                       int ell, float* __restrict__ Thi,
+                                                       float* __restrict__ Tlo, int* status) {
   constexpr int S = LP + 1;
-  extern __shared__ __align__(16) double sh[];
-  double* A = sh;          // [LP][S]
-  double* dT = A + LP * S; // [LP]
+  extern __shared__ __align__(16) unsigned char chol_sm[];
+  F* A = reinterpret_cast<F*>(chol_sm);   // [LP][S]
+  F* dinv = A + LP * S;                     // [LP]   1 / R[j][j]
   __shared__ int bad;
+  const int mat = blockIdx.x;
+  if (mat >= b.nmat) return;
+  const double* G = Gin + static_cast<int64_t>(mat) * LP * LP;
   const int t = threadIdx.x, nt = blockDim.x;
   if (t == 0) bad = 0;
   for (int e = t; e < LP * LP; e += nt) {
     const int p = e / LP, q = e - p * LP;
-    A[p * S + q] = (p <= q && q < ell) ? Gin[p * LP + q] : 0.0;
+    A[p * S + q] = (p <= q && q < ell) ? static_cast<F>(G[p * LP + q]) : F(0);
   }
   __syncthreads();
   for (int j = 0; j < ell; ++j) {
     if (t == 0) {
-      double d = A[j * S + j];
+      F d = A[j * S + j];
       // a non-positive pivot: the sketch is numerically rank deficient
-      if (!(d > 0.0)) {
+      if (!(d > F(0))) {
         bad = 1;
-        d = 1e-300;
+        d = F(1e-30);
       }
-      A[j * S + j] = sqrt(d);
+      const F inv = rsqrt_any(d);
+      A[j * S + j] = d * inv;
+      dinv[j] = inv;
     }
     __syncthreads();
-    const double rjj = A[j * S + j];
-    for (int q = j + 1 + t; q < ell; q += nt) A[j * S + q] /= rjj;
+    const F inv = dinv[j];
+    for (int q = j + 1 + t; q < ell; q += nt) A[j * S + q] *= inv;
     __syncthreads();
     const int w = ell - j - 1;
     for (int e = t; e < w * w; e += nt) {
@@ -104,70 +147,86 @@ __global__ void __launch_bounds__(1024) chol_inv_kernel(const double* __restrict
     }
     __syncthreads();
   }
-  // T = R^{-1}, column c by back substitution (one warp per column):
-  //   T[c][c] = 1 / R[c][c];  T[i][c] = -(sum_{k=i+1..c} R[i][k] T[k][c]) / R[i][i]
-  // T[k][c] (k < c) lives at A[c][k].
+  // T[c][c] = 1 / R[c][c];  T[i][c] = -(sum_{k=i+1..c} R[i][k] T[k][c]) / R[i][i]
+  // (one warp per column; T[k][c] for k < c lives at A[c][k])
   const int warp = t >> 5, lane = t & 31, nw = nt >> 5;
   for (int c = warp; c < ell; c += nw) {
-    const double tcc = 1.0 / A[c * S + c];
-    if (lane == 0) dT[c] = tcc;
+    const F tcc = dinv[c];
     for (int i = c - 1; i >= 0; --i) {
-      double s = 0.0;
-      for (int k = i + 1 + lane; k <= c; k += 32) {
-        const double tkc = (k == c) ? tcc : A[c * S + k];
-        s += A[i * S + k] * tkc;
-      }
+      F s = F(0);
+      for (int k = i + 1 + lane; k <= c; k += 32)
+        s += A[i * S + k] * ((k == c) ? tcc : A[c * S + k]);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) A[c * S + i] = -s / A[i * S + i];
+      if (lane == 0) A[c * S + i] = -s * dinv[i];
       __syncwarp();
     }
   }
   __syncthreads();
+  float* th = Thi + static_cast<int64_t>(mat) * ell * ell;
+  float* tl = Tlo + static_cast<int64_t>(mat) * ell * ell;
   for (int e = t; e < ell * ell; e += nt) {
     const int p = e / ell, q = e - p * ell;
-    double v = 0.0;
-    if (p == q) v = dT[p];
+    F v = F(0);
+    if (p == q) v = dinv[p];
     else if (p < q) v = A[q * S + p];
-    Tout[e] = static_cast<float>(v);
-    Tout64[e] = v;
+    const float hi = static_cast<float>(v);
+    th[e] = hi;
+    tl[e] = static_cast<float>(v - static_cast<F>(hi));
   }
   if (t == 0 && bad) latch(status, kStQrBreakdown);
 }
 
-// Q = Y T (T upper triangular ell x ell), accumulated in ACC (float or double), stored FP32.
+// Q = Y (T_hi + T_lo), T upper triangular. FF: float-float accumulation of the T_hi part.
 // One thread per (row, block of 8 columns).
-template <int LP, typename ACC>
-__global__ void __launch_bounds__(256) apply_tri_kernel(const float* __restrict__ Y, int64_t rows,
-                                                        int ell, const ACC* __restrict__ T,
-                                                        float* __restrict__ Q) {
-  extern __shared__ __align__(16) unsigned char tsm[];
-  ACC* Ts = reinterpret_cast<ACC*>(tsm);   // [LP][LP]
+template <int LP, bool FF>
+__global__ void __launch_bounds__(256) apply_tri_kernel(QrBatch b, int ell,
+                                                        const float* __restrict__ Thi,
+                                                        const float* __restrict__ Tlo) {
+  extern __shared__ __align__(16) float tsm[];
+  float* Th = tsm;             // [LP][LP]
+  float* Tl = tsm + LP * LP;   // [LP][LP]
+  const int mat = blockIdx.y;
+  if (mat >= b.nmat) return;
+  const float* th = Thi + static_cast<int64_t>(mat) * ell * ell;
+  const float* tl = Tlo + static_cast<int64_t>(mat) * ell * ell;
   for (int e = threadIdx.x; e < LP * LP; e += blockDim.x) {
     const int p = e / LP, q = e - p * LP;
-    Ts[e] = (p < ell && q < ell) ? T[p * ell + q] : ACC(0);
+    const bool in = p < ell && q < ell;
+    Th[e] = in ? th[p * ell + q] : 0.f;
+    Tl[e] = (FF && in) ? tl[p * ell + q] : 0.f;
   }
   __syncthreads();
+  const float* Y = b.Y[mat];
+  float* Q = b.Q[mat];
+  const int64_t rows = b.rows[mat];
   constexpr int CB = 8, NCB = LP / CB;
   const int64_t total = rows * NCB;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = e / NCB;
     const int cb = static_cast<int>(e - i * NCB);
-    ACC acc[CB];
+    float hi[CB], lo[CB];
 #pragma unroll
-    for (int q = 0; q < CB; ++q) acc[q] = ACC(0);
+    for (int q = 0; q < CB; ++q) hi[q] = lo[q] = 0.f;
     const float* yr = Y + i * ell;
     const int kmax = min(ell, (cb + 1) * CB);
     for (int k = 0; k < kmax; ++k) {
-      const ACC y = static_cast<ACC>(yr[k]);
+      const float y = yr[k];
 #pragma unroll
-      for (int q = 0; q < CB; ++q) acc[q] = fma(y, Ts[k * LP + cb * CB + q], acc[q]);
+      for (int q = 0; q < CB; ++q) {
+        if (FF) {
+          ff_fma(y, Th[k * LP + cb * CB + q], hi[q], lo[q]);
+          lo[q] = fmaf(y, Tl[k * LP + cb * CB + q], lo[q]);
+        } else {
+          hi[q] = fmaf(y, Th[k * LP + cb * CB + q], hi[q]);
+        }
+      }
     }
 #pragma unroll
     for (int q = 0; q < CB; ++q) {
       const int c = cb * CB + q;
-      if (c < ell) Q[i * ell + c] = static_cast<float>(acc[q]);
+      if (c < ell) Q[i * ell + c] = FF ? __fadd_rn(hi[q], lo[q]) : hi[q];
     }
   }
 }
@@ -181,69 +240,86 @@ int lp_for(int ell) {
   return 128;
 }
 
-struct QrWs {
-  double* Gp;   // nparts x LP x LP
-  double* G;    // LP x LP
-  double* T64;  // LP x LP
-  float* T;     // LP x LP
-  float* Q1;    // rows x ell
-};
-
-QrWs carve(char* ws, int64_t rows, int ell, int LP) {
-  const int64_t nparts = cdiv(rows, kGramRows);
-  QrWs w;
-  w.Gp = reinterpret_cast<double*>(ws);
-  w.G = w.Gp + nparts * LP * LP;
-  w.T64 = w.G + LP * LP;
-  w.T = reinterpret_cast<float*>(w.T64 + LP * LP);
-  w.Q1 = w.T + LP * LP;
-  return w;
+size_t ws_bytes_for(const int64_t* rows, int nmat, int ell) {
+  const int LP = lp_for(ell);
+  size_t slabs = 0;
+  for (int i = 0; i < nmat; ++i) slabs += cdiv(rows[i], kGramRows);
+  size_t b = sizeof(double) * (slabs + nmat) * LP * LP;
+  b += 2 * sizeof(float) * nmat * ell * ell + 256;
+  for (int i = 0; i < nmat; ++i) b += sizeof(float) * rows[i] * ell + 256;
+  return b + 4096;
 }
 
 template <int LP>
-cudaError_t run(const Launcher& L, const float* Y, int64_t rows, int ell, float* Q, char* ws,
-                int* status) {
-  const int64_t nparts = cdiv(rows, kGramRows);
-  const QrWs w = carve(ws, rows, ell, LP);
-  const size_t chol_smem = sizeof(double) * (LP * (LP + 1) + LP);
+cudaError_t run(const Launcher& L, QrBatch b, int ell, char* ws, int* status) {
+  const int nmat = b.nmat;
+  int64_t slabs = 0, max_slabs = 0, max_rows = 0;
+  for (int i = 0; i < nmat; ++i) {
+    b.part_off[i] = slabs;
+    const int64_t s = cdiv(b.rows[i], kGramRows);
+    slabs += s;
+    max_slabs = s > max_slabs ? s : max_slabs;
+    max_rows = b.rows[i] > max_rows ? b.rows[i] : max_rows;
+  }
+  double* Gp = reinterpret_cast<double*>(ws);
+  double* G = Gp + slabs * LP * LP;
+  float* Thi = reinterpret_cast<float*>(G + nmat * LP * LP);
+  float* Tlo = Thi + nmat * ell * ell;
+  char* p = reinterpret_cast<char*>(Tlo + nmat * ell * ell);
+  float* Q1[kMaxMats] = {nullptr, nullptr};
+  for (int i = 0; i < nmat; ++i) {
+    p = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(p) + 255) & ~uintptr_t(255));
+    Q1[i] = reinterpret_cast<float*>(p);
+    p += sizeof(float) * b.rows[i] * ell;
+  }
   const size_t gram_smem = sizeof(float) * kGramRows * LP;
-  const size_t apply_smem64 = sizeof(double) * LP * LP;
-  const size_t apply_smem32 = sizeof(float) * LP * LP;
+  const size_t apply_smem = sizeof(float) * 2 * LP * LP;
+  const size_t chol_smem64 = sizeof(double) * (LP * (LP + 1) + LP);
+  const size_t chol_smem32 = sizeof(float) * (LP * (LP + 1) + LP);
   cudaError_t err;
-  if ((err = cudaFuncSetAttribute(chol_inv_kernel<LP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  static_cast<int>(chol_smem))) != cudaSuccess ||
+  if ((err = cudaFuncSetAttribute(chol_inv_kernel<LP, double>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(chol_smem64))) != cudaSuccess ||
+      (err = cudaFuncSetAttribute(chol_inv_kernel<LP, float>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(chol_smem32))) != cudaSuccess ||
       (err = cudaFuncSetAttribute(gram_partial_kernel<LP>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   static_cast<int>(gram_smem))) != cudaSuccess ||
-      (err = cudaFuncSetAttribute(apply_tri_kernel<LP, double>,
+      (err = cudaFuncSetAttribute(apply_tri_kernel<LP, true>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  static_cast<int>(apply_smem64))) != cudaSuccess ||
-      (err = cudaFuncSetAttribute(apply_tri_kernel<LP, float>,
+                                  static_cast<int>(apply_smem))) != cudaSuccess ||
+      (err = cudaFuncSetAttribute(apply_tri_kernel<LP, false>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  static_cast<int>(apply_smem32))) != cudaSuccess)
+                                  static_cast<int>(apply_smem))) != cudaSuccess)
     return err;
-  const int chol_threads = LP >= 64 ? 1024 : 512;
-  const int64_t apply_work = rows * (LP / 8);
+  const int64_t apply_work = max_rows * (LP / 8);
   const unsigned apply_grid =
-      static_cast<unsigned>(cdiv(apply_work, 256) < 4096 ? cdiv(apply_work, 256) : 4096);
+      static_cast<unsigned>(cdiv(apply_work, 256) < 2048 ? cdiv(apply_work, 256) : 2048);
   const unsigned sum_grid = static_cast<unsigned>(cdiv(static_cast<int64_t>(LP) * LP * 32, 256));
-  // Q may alias Y: sweep 0 reads Y and writes the scratch Q1; sweep 1 reads Q1 and writes Q.
-  const float* src = Y;
   for (int sweep = 0; sweep < 2; ++sweep) {
-    gram_partial_kernel<LP><<<static_cast<unsigned>(nparts), kGramThreads, gram_smem, L.stream>>>(
-        src, rows, ell, w.Gp);
-    sum_parts_kernel<<<sum_grid, 256, 0, L.stream>>>(w.Gp, static_cast<int>(nparts), LP * LP,
-                                                     w.G);
-    chol_inv_kernel<LP><<<1, chol_threads, chol_smem, L.stream>>>(w.G, ell, w.T, w.T64, status);
-    if (sweep == 0)
-      apply_tri_kernel<LP, double><<<apply_grid, 256, apply_smem64, L.stream>>>(src, rows, ell,
-                                                                               w.T64, w.Q1);
-    else
-      apply_tri_kernel<LP, float><<<apply_grid, 256, apply_smem32, L.stream>>>(src, rows, ell,
-                                                                              w.T, Q);
+    // sweep 0 reads Y and writes the scratch Q1; sweep 1 reads Q1 and writes Q (Q may alias Y)
+    QrBatch bb = b;
+    for (int i = 0; i < nmat; ++i) {
+      bb.Y[i] = sweep == 0 ? b.Y[i] : Q1[i];
+      bb.Q[i] = sweep == 0 ? Q1[i] : b.Q[i];
+    }
+    gram_partial_kernel<LP><<<dim3(static_cast<unsigned>(max_slabs), nmat), kGramThreads,
+                              gram_smem, L.stream>>>(bb, ell, Gp);
+    sum_parts_kernel<<<dim3(sum_grid, nmat), 256, 0, L.stream>>>(Gp, bb, LP * LP, G);
+    if (sweep == 0) {
+      chol_inv_kernel<LP, double><<<nmat, 256, chol_smem64, L.stream>>>(G, bb, ell, Thi, Tlo,
+                                                                       status);
+      apply_tri_kernel<LP, true><<<dim3(apply_grid, nmat), 256, apply_smem, L.stream>>>(
+          bb, ell, Thi, Tlo);
+    } else {
+      chol_inv_kernel<LP, float><<<nmat, 256, chol_smem32, L.stream>>>(G, bb, ell, Thi, Tlo,
+                                                                      status);
+      apply_tri_kernel<LP, false><<<dim3(apply_grid, nmat), 256, apply_smem, L.stream>>>(
+          bb, ell, Thi, Tlo);
+    }
     L.count(4);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
-    src = w.Q1;
   }
   return cudaSuccess;
 }
@@ -251,23 +327,36 @@ cudaError_t run(const Launcher& L, const float* Y, int64_t rows, int ell, float*
 }  // namespace
 
 size_t qr_ws_bytes(int64_t rows, int ell) {
-  const int LP = lp_for(ell);
-  const int64_t nparts = cdiv(rows, kGramRows);
-  return sizeof(double) * (nparts + 2) * LP * LP + sizeof(float) * (LP * LP + rows * ell) + 256;
+  const int64_t r[2] = {rows, rows};
+  return ws_bytes_for(r, 2, ell);
+}
+
+cudaError_t launch_qr_batch(const Launcher& L, int nmat, const float* const* Y,
+                            const int64_t* rows, int ell, float* const* Q, void* ws,
+                            size_t ws_bytes, int* status) {
+  if (nmat < 1 || nmat > kMaxMats) return cudaErrorInvalidValue;
+  if (ws_bytes < ws_bytes_for(rows, nmat, ell)) return cudaErrorInvalidValue;
+  QrBatch b{};
+  b.nmat = nmat;
+  for (int i = 0; i < nmat; ++i) {
+    b.Y[i] = Y[i];
+    b.Q[i] = Q[i];
+    b.rows[i] = rows[i];
+  }
+  char* w = static_cast<char*>(ws);
+  switch (lp_for(ell)) {
+    case 16: return run<16>(L, b, ell, w, status);
+    case 32: return run<32>(L, b, ell, w, status);
+    case 48: return run<48>(L, b, ell, w, status);
+    case 64: return run<64>(L, b, ell, w, status);
+    case 96: return run<96>(L, b, ell, w, status);
+    default: return run<128>(L, b, ell, w, status);
+  }
 }
 
 cudaError_t launch_qr(const Launcher& L, const float* Y, int64_t rows, int ell, float* Q,
                       void* ws, size_t ws_bytes, int* status) {
-  if (ws_bytes < qr_ws_bytes(rows, ell)) return cudaErrorInvalidValue;
-  char* w = static_cast<char*>(ws);
-  switch (lp_for(ell)) {
-    case 16: return run<16>(L, Y, rows, ell, Q, w, status);
-    case 32: return run<32>(L, Y, rows, ell, Q, w, status);
-    case 48: return run<48>(L, Y, rows, ell, Q, w, status);
-    case 64: return run<64>(L, Y, rows, ell, Q, w, status);
-    case 96: return run<96>(L, Y, rows, ell, Q, w, status);
-    default: return run<128>(L, Y, rows, ell, Q, w, status);
-  }
+  return launch_qr_batch(L, 1, &Y, &rows, ell, &Q, ws, ws_bytes, status);
 }
 
 }  // namespace nmfrp

@@ -1,13 +1,18 @@
 // Full-size residual of Eq. 2.2: ||X - W H||_F^2 and ||X||_F^2 in one read of X.
-// W H is rebuilt per 64 x 128 tile from W rows and H columns staged in shared memory (K = r),
-// differences and squares are formed in FP32 per tile and added to per-thread FP64 sums; block
-// sums and the final sum are FP64 in a fixed order (deterministic).
+//
+// A block walks 128 x 128 tiles of X. For each tile it stages the 128 rows of W (transposed) and
+// the 128 columns of H in shared memory, issues its X loads first (16 x 128-bit per thread, so
+// the HBM latency overlaps the W H arithmetic), rebuilds its 8 x 8 outputs of W H in registers
+// (K = r FMAs each), and adds (x - wh)^2 and x^2 to per-thread sums. Per-tile sums are FP32 (64
+// terms), accumulated across tiles in FP64; block sums and the final sum are FP64 in a fixed
+// order (deterministic).
 #include "common.cuh"
 
 namespace nmfrp {
 namespace {
 
-constexpr int kTR = 64, kTC = 128, kThreads = 256;
+constexpr int kT = 128, kThreads = 256;
+constexpr int kWS = kT + 4;   // padded row of the transposed W tile
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -16,70 +21,86 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 template <bool VEC>
-__global__ void __launch_bounds__(kThreads) residual_kernel(
+__global__ void __launch_bounds__(kThreads, 1) residual_kernel(
     const float* __restrict__ X, int64_t m, int64_t n, int64_t ldx, const float* __restrict__ W,
     const float* __restrict__ H, int r, double* __restrict__ part) {
   extern __shared__ __align__(16) float sh[];
-  float* WsT = sh;                 // [r][kTR]
-  float* Hs = WsT + r * kTR;       // [r][kTC]
+  float* WsT = sh;                 // [r][kWS]   W tile transposed
+  float* Hs = WsT + r * kWS;       // [r][kT]
   __shared__ double red[2][kThreads / 32];
   const int t = threadIdx.x, ty = t >> 4, tx = t & 15;
-  const int64_t tiles_r = cdiv(m, kTR), tiles_c = cdiv(n, kTC);
+  const int64_t tiles_c = cdiv(n, kT), tiles = cdiv(m, kT) * tiles_c;
   double e2 = 0.0, x2 = 0.0;
-  for (int64_t tile = blockIdx.x; tile < tiles_r * tiles_c; tile += gridDim.x) {
-    const int64_t r0 = (tile / tiles_c) * kTR, c0 = (tile % tiles_c) * kTC;
-    __syncthreads();
-    for (int e = t; e < kTR * r; e += kThreads) {
-      const int i = e / r, k = e - i * r;
-      WsT[k * kTR + i] = (r0 + i < m) ? W[(r0 + i) * r + k] : 0.f;
-    }
-    for (int e = t; e < r * kTC; e += kThreads) {
-      const int k = e / kTC, c = e - k * kTC;
-      Hs[e] = (c0 + c < n) ? H[k * n + c0 + c] : 0.f;
-    }
-    __syncthreads();
-    float acc[4][8];
+  for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const int64_t r0 = (tile / tiles_c) * kT, c0 = (tile % tiles_c) * kT;
+    // X loads for this thread's 8 x 8 outputs: rows r0 + 8 ty + a, columns c0 + 4 tx + {0..3}
+    // and c0 + 64 + 4 tx + {0..3}
+    float xv[8][8];
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
-    for (int k = 0; k < r; ++k) {
-      const float4 w = *reinterpret_cast<const float4*>(&WsT[k * kTR + 4 * ty]);
-      const float4 h0 = *reinterpret_cast<const float4*>(&Hs[k * kTC + 4 * tx]);
-      const float4 h1 = *reinterpret_cast<const float4*>(&Hs[k * kTC + 64 + 4 * tx]);
-      const float wv[4] = {w.x, w.y, w.z, w.w};
-      const float hv[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 8; ++b) acc[a][b] = fmaf(wv[a], hv[b], acc[a][b]);
-    }
-    float te = 0.f, tx2 = 0.f;
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      const int64_t gr = r0 + 4 * ty + a;
-      if (gr >= m) continue;
-      const float* xr = X + gr * ldx;
+    for (int a = 0; a < 8; ++a) {
+      const int64_t gr = r0 + 8 * ty + a;
 #pragma unroll
       for (int g = 0; g < 2; ++g) {
         const int64_t gc = c0 + 64 * g + 4 * tx;
-        float xv[4];
-        if (VEC && gc + 3 < n) {
-          const float4 v = __ldcs(reinterpret_cast<const float4*>(xr + gc));
-          xv[0] = v.x; xv[1] = v.y; xv[2] = v.z; xv[3] = v.w;
+        if (gr < m) {
+          const float* xp = X + gr * ldx + gc;
+          if (VEC && gc + 3 < n) {
+            const float4 v = __ldcs(reinterpret_cast<const float4*>(xp));
+            xv[a][4 * g] = v.x;
+            xv[a][4 * g + 1] = v.y;
+            xv[a][4 * g + 2] = v.z;
+            xv[a][4 * g + 3] = v.w;
+          } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) xv[a][4 * g + q] = (gc + q < n) ? __ldcs(xp + q) : 0.f;
+          }
         } else {
 #pragma unroll
-          for (int q = 0; q < 4; ++q) xv[q] = (gc + q < n) ? xr[gc + q] : 0.f;
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          // out-of-range columns have xv = 0 and acc = 0 (H padded with zeros)
-          const float d = xv[q] - acc[a][4 * g + q];
-          te = fmaf(d, d, te);
-          tx2 = fmaf(xv[q], xv[q], tx2);
+          for (int q = 0; q < 4; ++q) xv[a][4 * g + q] = 0.f;
         }
       }
     }
+    __syncthreads();
+    // W tile: 128 rows x r, contiguous in global; stored transposed
+    for (int i = t >> 3; i < kT; i += kThreads >> 3) {
+      const int64_t gr = r0 + i;
+      for (int k = t & 7; k < r; k += 8) WsT[k * kWS + i] = (gr < m) ? W[gr * r + k] : 0.f;
+    }
+    // H tile: r rows x 128 columns
+    for (int k = t >> 5; k < r; k += kThreads >> 5) {
+      for (int c = t & 31; c < kT; c += 32) {
+        const int64_t gc = c0 + c;
+        Hs[k * kT + c] = (gc < n) ? H[k * n + gc] : 0.f;
+      }
+    }
+    __syncthreads();
+    float acc[8][8];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+      for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
+    for (int k = 0; k < r; ++k) {
+      const float4 w0 = *reinterpret_cast<const float4*>(&WsT[k * kWS + 8 * ty]);
+      const float4 w1 = *reinterpret_cast<const float4*>(&WsT[k * kWS + 8 * ty + 4]);
+      const float4 h0 = *reinterpret_cast<const float4*>(&Hs[k * kT + 4 * tx]);
+      const float4 h1 = *reinterpret_cast<const float4*>(&Hs[k * kT + 64 + 4 * tx]);
+      const float wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+      const float hv[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
+#pragma unroll
+      for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) acc[a][b] = fmaf(wv[a], hv[b], acc[a][b]);
+    }
+    // padded rows/columns have x = 0 and w h = 0 (zero-filled W, H tiles)
+    float te = 0.f, tx2 = 0.f;
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+      for (int b = 0; b < 8; ++b) {
+        const float d = xv[a][b] - acc[a][b];
+        te = fmaf(d, d, te);
+        tx2 = fmaf(xv[a][b], xv[a][b], tx2);
+      }
     e2 += te;
     x2 += tx2;
   }
@@ -118,12 +139,15 @@ __global__ void residual_final_kernel(const double* __restrict__ part, int npart
   }
 }
 
-int residual_grid() {
+int num_sms() {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  return (sms > 0 ? sms : 148) * 4;
+  return sms > 0 ? sms : 148;
 }
+
+// upper bound on the grid (blocks per SM is at most 4 for this kernel)
+int residual_grid() { return num_sms() * 4; }
 
 }  // namespace
 
@@ -135,26 +159,21 @@ cudaError_t launch_residual(const Launcher& L, const float* X, int64_t m, int64_
                             const float* W, const float* H, int r, double* out2, void* ws,
                             size_t ws_bytes) {
   if (ws_bytes < residual_ws_bytes(m, n)) return cudaErrorInvalidValue;
-  const int64_t tiles = cdiv(m, kTR) * cdiv(n, kTC);
-  int grid = residual_grid();
-  if (tiles < grid) grid = static_cast<int>(tiles);
+  const int64_t tiles = cdiv(m, kT) * cdiv(n, kT);
   double* part = static_cast<double*>(ws);
-  const size_t sm = sizeof(float) * (r * kTR + r * kTC);
+  const size_t sm = sizeof(float) * (r * kWS + r * kT);
   const bool vec = (ldx % 4 == 0) && (reinterpret_cast<uintptr_t>(X) % 16 == 0);
-  cudaError_t err;
-  if (vec) {
-    if ((err = cudaFuncSetAttribute(residual_kernel<true>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    static_cast<int>(sm))) != cudaSuccess)
-      return err;
-    residual_kernel<true><<<grid, kThreads, sm, L.stream>>>(X, m, n, ldx, W, H, r, part);
-  } else {
-    if ((err = cudaFuncSetAttribute(residual_kernel<false>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    static_cast<int>(sm))) != cudaSuccess)
-      return err;
-    residual_kernel<false><<<grid, kThreads, sm, L.stream>>>(X, m, n, ldx, W, H, r, part);
-  }
+  auto k = vec ? residual_kernel<true> : residual_kernel<false>;
+  cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(sm));
+  if (err != cudaSuccess) return err;
+  int per_sm = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, sm) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  int grid = num_sms() * (per_sm < 4 ? per_sm : 4);
+  if (tiles < grid) grid = static_cast<int>(tiles);
+  k<<<grid, kThreads, sm, L.stream>>>(X, m, n, ldx, W, H, r, part);
   residual_final_kernel<<<1, 32, 0, L.stream>>>(part, grid, out2);
   L.count(2);
   return cudaGetLastError();

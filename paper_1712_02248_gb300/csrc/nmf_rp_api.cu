@@ -187,11 +187,12 @@ float eps_of(const nmf_params* p) { return p->eps > 0 ? static_cast<float>(p->ep
 
 // One dual pass with its scratch.
 nmf_status dual(nmf_ctx* ctx, const void* X, bool bf16, int64_t m, int64_t n, int64_t ldx, int ell,
-                const float* V, const float* U, float* Y, float* Z, Arena a) {
+                const float* V, const float* U, float* Y, float* Z, Arena a, bool simt = false) {
   Phase ph(ctx, NMF_PHASE_DUAL_PASS);
   size_t rest = 0;
   void* ws = a.rest(&rest);
-  NMF_CUDA(nmfrp::launch_dual_pass(launcher(ctx), X, bf16, m, n, ldx, ell, V, U, Y, Z, ws, rest),
+  NMF_CUDA(nmfrp::launch_dual_pass(launcher(ctx), X, bf16, m, n, ldx, ell, V, U, Y, Z, ws, rest,
+                                   ctx->d_status, simt),
            "dual pass");
   return NMF_OK;
 }
@@ -201,6 +202,19 @@ nmf_status qr(nmf_ctx* ctx, float* Y, int64_t rows, int ell, Arena a) {
   size_t rest = 0;
   void* ws = a.rest(&rest);
   NMF_CUDA(nmfrp::launch_qr(launcher(ctx), Y, rows, ell, Y, ws, rest, ctx->d_status), "qr");
+  return NMF_OK;
+}
+
+// QR of the m-side and the n-side output of one pass together (both chains of the sketch).
+nmf_status qr2(nmf_ctx* ctx, float* Ym, int64_t m, float* Yn, int64_t n, int ell, Arena a) {
+  Phase ph(ctx, NMF_PHASE_QR);
+  size_t rest = 0;
+  void* ws = a.rest(&rest);
+  const float* ys[2] = {Ym, Yn};
+  float* qs[2] = {Ym, Yn};
+  const int64_t rows[2] = {m, n};
+  NMF_CUDA(nmfrp::launch_qr_batch(launcher(ctx), 2, ys, rows, ell, qs, ws, rest, ctx->d_status),
+           "qr");
   return NMF_OK;
 }
 
@@ -223,6 +237,7 @@ nmf_status sketch_impl(nmf_ctx* ctx, const nmf_params* p, const void* X, int64_t
   const int64_t m = p->m, n = p->n;
   const int l = p->ell;
   const bool bf16 = p->prec == NMF_PREC_BF16;
+  const bool simt = (p->flags & NMF_FLAG_SIMT_DUAL_PASS) != 0;
   float* mR = a.take<float>(m * l);   // right chain, m-side
   float* nL = a.take<float>(n * l);   // left chain, n-side
   if (!omega_L || !omega_R) {
@@ -239,19 +254,17 @@ nmf_status sketch_impl(nmf_ctx* ctx, const nmf_params* p, const void* X, int64_t
   }
   nmf_status st;
   // pass 0
-  if ((st = dual(ctx, X, bf16, m, n, ldx, l, omega_L, omega_R, QL, QR, a)) != NMF_OK) return st;
-  if ((st = qr(ctx, QL, m, l, a)) != NMF_OK) return st;
-  if ((st = qr(ctx, QR, n, l, a)) != NMF_OK) return st;
+  if ((st = dual(ctx, X, bf16, m, n, ldx, l, omega_L, omega_R, QL, QR, a, simt)) != NMF_OK)
+    return st;
+  if ((st = qr2(ctx, QL, m, QR, n, l, a)) != NMF_OK) return st;
   for (int pass = 1; pass <= 2 * p->power_iters; ++pass) {
     if (pass & 1) {
       // right chain: X * (n-side) -> m-side; left chain: X^T * (m-side) -> n-side
-      if ((st = dual(ctx, X, bf16, m, n, ldx, l, QR, QL, mR, nL, a)) != NMF_OK) return st;
-      if ((st = qr(ctx, mR, m, l, a)) != NMF_OK) return st;
-      if ((st = qr(ctx, nL, n, l, a)) != NMF_OK) return st;
+      if ((st = dual(ctx, X, bf16, m, n, ldx, l, QR, QL, mR, nL, a, simt)) != NMF_OK) return st;
+      if ((st = qr2(ctx, mR, m, nL, n, l, a)) != NMF_OK) return st;
     } else {
-      if ((st = dual(ctx, X, bf16, m, n, ldx, l, nL, mR, QL, QR, a)) != NMF_OK) return st;
-      if ((st = qr(ctx, QL, m, l, a)) != NMF_OK) return st;
-      if ((st = qr(ctx, QR, n, l, a)) != NMF_OK) return st;
+      if ((st = dual(ctx, X, bf16, m, n, ldx, l, nL, mR, QL, QR, a, simt)) != NMF_OK) return st;
+      if ((st = qr2(ctx, QL, m, QR, n, l, a)) != NMF_OK) return st;
     }
   }
   return NMF_OK;
@@ -281,7 +294,8 @@ nmf_status compress_impl(nmf_ctx* ctx, const nmf_params* p, const void* X, int64
   const int64_t m = p->m, n = p->n;
   const int l = p->ell;
   float* XhatT = a.take<float>(n * l);
-  nmf_status st = dual(ctx, X, p->prec == NMF_PREC_BF16, m, n, ldx, l, QR, QL, Xchk, XhatT, a);
+  nmf_status st = dual(ctx, X, p->prec == NMF_PREC_BF16, m, n, ldx, l, QR, QL, Xchk, XhatT, a,
+                       (p->flags & NMF_FLAG_SIMT_DUAL_PASS) != 0);
   if (st != NMF_OK) return st;
   dim3 grid(static_cast<unsigned>(cdiv(n, 32)), static_cast<unsigned>(cdiv(l, 32)));
   transpose_kernel<<<grid, dim3(32, 8), 0, ctx->stream>>>(XhatT, n, l, Xhat);
@@ -312,7 +326,12 @@ nmf_status iterate_impl(nmf_ctx* ctx, const nmf_params* p, const float* QL, cons
   Phase ph(ctx, NMF_PHASE_ITERATE);
   size_t rest = 0;
   void* ws = a.rest(&rest);
-  NMF_CUDA(nmfrp::launch_iterate(launcher(ctx), ia, iters, ws, rest), "iterate");
+  if (!(p->flags & NMF_FLAG_STAGED_ITERATE) && nmfrp::iterate_persistent_supported(p->r, p->ell)) {
+    NMF_CUDA(nmfrp::launch_iterate_persistent(launcher(ctx), ia, iters, ws, rest, ctx->d_status),
+             "iterate (persistent)");
+  } else {
+    NMF_CUDA(nmfrp::launch_iterate(launcher(ctx), ia, iters, ws, rest), "iterate");
+  }
   return NMF_OK;
 }
 
@@ -454,11 +473,12 @@ nmf_status nmf_workspace_size(const nmf_params* p, size_t* bytes) {
   if (check_params(nullptr, p) != NMF_OK) return NMF_ERR_INVALID_ARG;
   const int64_t m = p->m, n = p->n, l = p->ell, r = p->r;
   size_t b = 0;
-  if (p->prec == NMF_PREC_BF16) b += 2 * static_cast<size_t>(m * n) + 1024;
+  if (p->prec == NMF_PREC_BF16) b += 2 * static_cast<size_t>(m * ((n + 7) / 8 * 8)) + 1024;
   b += sizeof(float) * (2 * (m * l + n * l) + l * n + m * l) + 4096;  // QL QR Xhat Xchk + omega
   size_t scratch = sketch_ws(p, true);
   scratch = std::max(scratch, sizeof(float) * n * l + 1024 + pass_scratch(m, n, p->ell));
   scratch = std::max(scratch, nmfrp::iterate_ws_bytes(m, n, p->r, p->ell));
+  scratch = std::max(scratch, nmfrp::iterate_persistent_ws_bytes(p->r, p->ell));
   scratch = std::max(scratch, nmfrp::residual_ws_bytes(m, n));
   scratch = std::max(scratch, nmfrp::nndsvd_ws_bytes(m, n, p->r, p->ell));
   (void)r;
@@ -486,7 +506,7 @@ nmf_status nmf_quantize(nmf_ctx* ctx, int32_t prec, const float* X, int64_t m, i
     return fail(ctx, NMF_ERR_INVALID_ARG, "bad quantize arguments");
   DeviceGuard g(ctx->device);
   NMF_CUDA(nmfrp::launch_quantize_bf16(launcher(ctx), X, m, n, ldx,
-                                       static_cast<__nv_bfloat16*>(Xq)),
+                                       static_cast<__nv_bfloat16*>(Xq), n),
            "quantize");
   return NMF_OK;
 }
@@ -560,7 +580,8 @@ nmf_status nmf_iterate(nmf_ctx* ctx, const nmf_params* p, const float* QL, const
     return fail(ctx, NMF_ERR_INVALID_ARG, "NULL argument");
   if (iters < 0) return fail(ctx, NMF_ERR_INVALID_ARG, "iters < 0");
   DeviceGuard g(ctx->device);
-  if ((st = ensure_ws(ctx, nmfrp::iterate_ws_bytes(p->m, p->n, p->r, p->ell))) != NMF_OK)
+  if ((st = ensure_ws(ctx, std::max(nmfrp::iterate_ws_bytes(p->m, p->n, p->r, p->ell),
+                                     nmfrp::iterate_persistent_ws_bytes(p->r, p->ell)))) != NMF_OK)
     return st;
   Arena a{static_cast<char*>(ctx->ws), ctx->ws_bytes};
   return iterate_impl(ctx, p, QL, QR, Xhat, Xchk, W, H, iters, a);
@@ -613,11 +634,12 @@ nmf_status nmf_solve(nmf_ctx* ctx, const nmf_params* p, int32_t init, const floa
   const void* Xp = X;
   int64_t ldp = ldx;
   if (p->prec == NMF_PREC_BF16) {
-    __nv_bfloat16* Xq = a.take<__nv_bfloat16>(m * n);
+    const int64_t ldq = (n + 7) / 8 * 8;   // row pitch a TMA descriptor can address
+    __nv_bfloat16* Xq = a.take<__nv_bfloat16>(m * ldq);
     Phase ph(ctx, NMF_PHASE_QUANTIZE);
-    NMF_CUDA(nmfrp::launch_quantize_bf16(launcher(ctx), X, m, n, ldx, Xq), "quantize");
+    NMF_CUDA(nmfrp::launch_quantize_bf16(launcher(ctx), X, m, n, ldx, Xq, ldq), "quantize");
     Xp = Xq;
-    ldp = n;
+    ldp = ldq;
   }
   float* QL = a.take<float>(m * l);
   float* QR = a.take<float>(n * l);

@@ -39,7 +39,7 @@ class nmf_params(ctypes.Structure):
                 ("ell", ctypes.c_int32), ("power_iters", ctypes.c_int32),
                 ("iters", ctypes.c_int32), ("rule", ctypes.c_int32), ("prec", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("residual_every", ctypes.c_int32),
-                ("reserved0", ctypes.c_int32), ("target_rel_err", ctypes.c_double),
+                ("flags", ctypes.c_int32), ("target_rel_err", ctypes.c_double),
                 ("alpha", ctypes.c_double), ("beta", ctypes.c_double), ("eps", ctypes.c_double)]
 
 
@@ -87,12 +87,15 @@ class NmfError(RuntimeError):
         self.status = status
 
 
+FLAG_STAGED_ITERATE = 1
+
+
 def params(m, n, r, ell, power_iters=2, iters=0, rule="fasthals", prec="fp32", seed=0,
-           residual_every=0, target_rel_err=0.0, alpha=0.0, beta=0.0, eps=0.0):
+           residual_every=0, target_rel_err=0.0, alpha=0.0, beta=0.0, eps=0.0, flags=0):
     """Build an nmf_params struct (names as in include/nmf_rp.h)."""
     return nmf_params(int(m), int(n), int(r), int(ell), int(power_iters), int(iters),
                       RULE.get(rule, rule), PREC.get(prec, prec), int(seed), int(residual_every),
-                      0, float(target_rel_err), float(alpha), float(beta), float(eps))
+                      int(flags), float(target_rel_err), float(alpha), float(beta), float(eps))
 
 
 class Context:

@@ -98,8 +98,12 @@ def test_dual_pass_strided_x_and_single_sides(lib, ctx):
     assert rel(host(Z), X64.T @ U) <= 1e-5
 
 
-@pytest.mark.parametrize("m,n,ell", [(512, 256, 18), (1000, 777, 40), (257, 1025, 70)])
+@pytest.mark.parametrize("m,n,ell", [(512, 256, 18), (1000, 777, 40), (257, 1025, 70),
+                                     (1000, 784, 40), (300, 1032, 70), (129, 136, 18),
+                                     (2000, 520, 128), (5000, 3000, 40), (64, 8, 1),
+                                     (3000, 4096, 100)])
 def test_dual_pass_bf16(lib, ctx, m, n, ell):
+    """BF16 X (n a multiple of 8 goes to the tcgen05/TMA kernel, other n to the SIMT kernel)."""
     rng = np.random.default_rng(11 + m)
     X = rng.uniform(0, 1, (m, n)).astype(np.float32)
     V = rng.standard_normal((n, ell)).astype(np.float32)
@@ -349,3 +353,34 @@ def test_degenerate_square_full_width(lib, ctx):
     for _ in range(3):
         Wo, Ho = O.fasthals_step(Wo, Ho, pr.X)
     assert rel(host(W) @ host(H), Wo @ Ho) <= 1e-4
+
+
+@pytest.mark.parametrize("rule", ["fasthals", "mu"])
+@pytest.mark.parametrize("seed,m,n,r,ell", [(0, 512, 256, 8, 18), (1, 3000, 1777, 20, 40),
+                                            (2, 100, 5001, 32, 48)])
+def test_persistent_and_staged_iterations_agree(lib, ctx, rule, seed, m, n, r, ell):
+    """The one-launch persistent kernel and the one-launch-per-stage kernels run the same
+    arithmetic (they differ only in the order of cross-block sums): 30 iterations agree, and
+    both stay within 1% of the oracle's relative error."""
+    pr, QL, QR, Xhat, Xchk = compressed_state(seed, m, n, r, ell)
+    outs = []
+    for flags in (0, lib.FLAG_STAGED_ITERATE):
+        p = lib.params(m, n, r, ell, rule=rule, flags=flags)
+        W, H = cu(pr.W0), cu(pr.H0)
+        lib.nmf_iterate(ctx, p, cu(QL), cu(QR), cu(Xhat), cu(Xchk), W, H, 30)
+        lib.nmf_sync(ctx)
+        outs.append((host(W), host(H)))
+    (Wp, Hp), (Ws, Hs) = outs
+    assert rel(Wp @ Hp, Ws @ Hs) <= 1e-4
+    Wo, Ho = O.iterate(pr.W0, pr.H0, QL, QR, Xhat, Xchk, 30, rule=rule)
+    ro = O.residual(pr.X, Wo, Ho)[0]
+    for Wg, Hg in outs:
+        assert abs(O.residual(pr.X, Wg, Hg)[0] - ro) <= 0.01 * ro
+
+
+def test_iterate_zero_iterations_is_identity(lib, ctx):
+    pr, QL, QR, Xhat, Xchk = compressed_state(3, 300, 200, 5, 10)
+    p = lib.params(300, 200, 5, 10)
+    W, H = cu(pr.W0), cu(pr.H0)
+    lib.nmf_iterate(ctx, p, cu(QL), cu(QR), cu(Xhat), cu(Xchk), W, H, 0)
+    assert np.array_equal(host(W), pr.W0) and np.array_equal(host(H), pr.H0)
