@@ -255,7 +255,7 @@ def main():
     def timed(prec, init, steps, warmup, profile=False):
         for _ in range(warmup):
             solve(prec, init, target)
-        ts, its, errs = [], [], []
+        ts, its, errs, checks = [], [], [], []
         l0 = ctx.launches
         if profile:
             N.nmf_phase_times(ctx, reset=True)
@@ -273,23 +273,25 @@ def main():
             ts.append(a.elapsed_time(b) / 1e3)
             its.append(it)
             errs.append(e)
+            checks.append(N.nmf_last_solve_info(ctx)[1])
         phases = None
         if profile:
             N.nmf_set_profiling(ctx, False)
             phases = N.nmf_phase_times(ctx, reset=True)
-        return ts, its, errs, ctx.launches - l0, phases
+        return ts, its, errs, ctx.launches - l0, phases, checks
 
     results = {}
     for prec, init in contenders:
         if (prec, init) == headline:
             continue
-        ts, its, errs, _, _ = timed(prec, init, args.steps, 1)
+        ts, its, errs, _, _, checks = timed(prec, init, args.steps, 1)
         results[f"{prec}+{init}"] = {"s": statistics.median(ts), "iters": its[0],
-                                     "rel_err": errs[0]}
+                                     "rel_err": errs[0], "exact_checks": checks[0]}
 
     clocks = ClockSampler(local_rank)
     clocks.start()
-    ts, its, errs, launches, phases = timed(*headline, args.steps, args.warmup, profile=True)
+    ts, its, errs, launches, phases, checks = timed(*headline, args.steps, args.warmup,
+                                                    profile=True)
     clk = clocks.stop()
     t_local = statistics.median(ts)
     if world > 1:
@@ -297,7 +299,7 @@ def main():
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
         t_local = float(tt.item())
     results[f"{headline[0]}+{headline[1]}"] = {"s": statistics.median(ts), "iters": its[0],
-                                               "rel_err": errs[0]}
+                                               "rel_err": errs[0], "exact_checks": checks[0]}
 
     # e2e: same solve through the public API with the host copy of X inside the timed region
     Wh = torch.empty((m, r), dtype=torch.float32).pin_memory()

@@ -193,21 +193,33 @@ nmf_status nmf_residual(nmf_ctx* ctx, const nmf_params* p, const float* X, int64
                         const float* W, const float* H, double* rel_err_host,
                         double* err2_host, double* x2_host);
 
-/* NNDSVD initial factors from the compressed data (SVD of X ~ Q_L X_hat through the l x l
- * eigenproblem of X_hat X_hat^T in FP64). W: m x r, H: r x n. */
+/* NNDSVD initial factors (Boutsidis & Gallopoulos) from the compressed data: the top r singular
+ * triplets of X ~ Q_L X_hat (Section 3, Eq. 3.4) come from the l x l eigenproblem of
+ * X_hat X_hat^T (Gram in float-float arithmetic summed in FP64, cyclic Jacobi in FP32), with
+ * u_j = Q_L u'_j and v_j = X_hat^T u'_j / sigma_j; each pair keeps its larger sign part.
+ * QL: m x l, Xhat: l x n, W: m x r, H: r x n, all row-major FP32 device arrays owned by the
+ * caller. Components whose eigenvector error matters are those with small eigenvalue gaps:
+ * the FP32 eigensolver gives eigenvector j an error of about l * eps32 * lambda_1 / gap_j. */
 nmf_status nmf_nndsvd(nmf_ctx* ctx, const nmf_params* p, const float* QL, const float* Xhat,
                       float* W, float* H);
 
 /*
  * Whole pipeline on FP32 X (m x n, leading dimension ldx): sketch (Omega from p->seed), compress,
- * initialise (init), iterate; an exact residual every p->residual_every iterations and at the end.
- * Stops at the first check with rel_err <= p->target_rel_err (if > 0) or after p->iters
- * iterations. With p->prec = BF16 the X passes read a BF16 copy made in the workspace.
- * W, H: in/out (read only for NMF_INIT_GIVEN). Synchronises the stream.
- * Outputs: *rel_err_host (last exact residual), *iters_done_host (iterations run; may be NULL).
+ * initialise (init), iterate. Every p->residual_every iterations (and after the last one) there
+ * is a check; with p->target_rel_err > 0 the solve stops at the first check whose exact relative
+ * residual is <= the target, else after p->iters iterations. The exact residual of a check is
+ * computed only when an error monitor built from the compressed data alone (||X||^2 -
+ * 2 <W_tld^T X_hat, H> + <W^T W, H H^T>) is within 5 % of the target, and always for the last
+ * check; the decision is taken on the device. With p->prec = BF16 the X passes read a BF16
+ * copy made in the workspace. W, H: in/out (read only for NMF_INIT_GIVEN). Synchronises the
+ * stream. Outputs: *rel_err_host (the last exact relative residual), *iters_done_host
+ * (iterations at that check; may be NULL).
  */
 nmf_status nmf_solve(nmf_ctx* ctx, const nmf_params* p, int32_t init, const float* X, int64_t ldx,
                      float* W, float* H, double* rel_err_host, int32_t* iters_done_host);
+
+/* Iterations and number of exact residual checks of the last nmf_solve on this context. */
+nmf_status nmf_last_solve_info(const nmf_ctx* ctx, int32_t* iters, int32_t* exact_checks);
 
 #ifdef __cplusplus
 }

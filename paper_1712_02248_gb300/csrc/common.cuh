@@ -91,16 +91,22 @@ cudaError_t launch_iterate(const Launcher& L, const IterArgs& a, int iters, void
 
 // All iterations in one cooperative launch (r <= 32); status receives NMF_ERR_TIMEOUT if a
 // grid barrier wait runs out.
-bool iterate_persistent_supported(int r, int ell);
+bool iterate_persistent_supported(int64_t m, int64_t n, int r, int ell);
 size_t iterate_persistent_ws_bytes(int r, int ell);
+// mon (2 floats) receives the error monitor's cross and quadratic terms of the last iteration;
+// if *done is non-zero on entry the launch does nothing.
 cudaError_t launch_iterate_persistent(const Launcher& L, const IterArgs& a, int iters, void* ws,
-                                      size_t ws_bytes, int* status);
+                                      size_t ws_bytes, int* status, float* mon, const int* done);
 
-// Residual partial sums: writes 2 doubles (||X-WH||^2, ||X||^2) to out2 (device).
+// Residual partial sums: writes 2 doubles (||X-WH||^2, ||X||^2) to out2 (device). If gate is
+// non-null and *gate == 0 the kernels return without work.
 size_t residual_ws_bytes(int64_t m, int64_t n);
 cudaError_t launch_residual(const Launcher& L, const float* X, int64_t m, int64_t n, int64_t ldx,
                             const float* W, const float* H, int r, double* out2, void* ws,
-                            size_t ws_bytes);
+                            size_t ws_bytes, const int* gate = nullptr);
+// ||X||^2 into *out (device, FP64).
+cudaError_t launch_sumsq(const Launcher& L, const float* X, int64_t m, int64_t n, int64_t ldx,
+                         double* out, void* ws, size_t ws_bytes);
 
 // NNDSVD from compressed data.
 size_t nndsvd_ws_bytes(int64_t m, int64_t n, int r, int ell);

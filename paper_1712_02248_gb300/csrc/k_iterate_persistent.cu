@@ -2,30 +2,51 @@
 //
 // The update rules are those of k_iterate.cu (Section 4, Eq. fastHALS_a with the Section 4.1
 // terms; Section 3.1, Algorithm 3 with the semi-NMF rule). Each block owns a fixed slice of the
-// rows of W and of the columns of H for the whole run. One iteration is two phases:
+// rows of W and of the columns of H for the whole run. The slice's rows of X_chk and Q_L and its
+// columns of X_hat and rows of Q_R are staged in shared memory once. A row of W is handled by a
+// group of kGA = 4 lanes and a column of H by kGB = 16 lanes, each lane owning the components
+// j = g, g + G, g + 2G, ... (g its index in the group); the factors stay in registers across
+// iterations. One iteration:
 //
-//   A  (rows of W)   from H_tld, G_W: S_W row, sweep over j, W row written; the block adds its
-//                    rows' contributions to W_tld_raw = Q_L^T W and to the column sums of
-//                    squares into an FP64 accumulator (red.add.f64).
+//   A  (rows of W)    H_tld, G_W from the cross-block sums; S_W row; Gauss-Seidel sweep over j;
+//                     the block adds its rows' W_tld_raw = Q_L^T W and W_raw^T W_raw (whose
+//                     diagonal holds the squared column norms) into the cross-block sums.
 //   -- grid barrier --
-//   B  (columns of H) every block reads W_tld_raw and the squares, forms s_j, W_tld = raw/s,
-//                    G_H; compensation h_j *= s_j, S_H column, sweep; adds H Q_R contributions
-//                    into the FP64 accumulator of H_tld.
+//   B  (columns of H) s_j = ||w_j||, W_tld = raw / s, G_H; compensation h_j *= s_j; S_H column;
+//                     sweep; the block adds H Q_R, H H^T and <S_H, H> into the sums read by the
+//                     next phase A and by the error monitor.
 //   -- grid barrier --
 //
-// Partial sums are FP32 within a block and FP64 across blocks; the order of the cross-block
-// additions varies from run to run, but FP64 sums of FP32 values round back to the same FP32
-// result except in rare ties. W's normalisation by s_j is applied when phase A of the next
-// iteration (or the final pass) reads the row. Every wait is bounded: on time-out the kernel
-// latches NMF_ERR_TIMEOUT and all blocks leave.
+// G_W and G_H are symmetric; every lane reads them along a row (consecutive lanes, distinct
+// shared-memory banks).
+//
+// The sweep is incremental: t_j = S_j - sum_q w_q G_qj is formed for every j; when w_j moves by d
+// (computed by the lane owning j and broadcast in the group) every later t_j' drops by d G_jj'.
+// These are the Gauss-Seidel values of the paper's component-by-component update.
+//
+// Cross-block sums: FP32 red.add into kCopies copies (block b adds into copy b % kCopies), read
+// back through L2 as a fixed-order sum of the copies. The order of the adds within a copy varies
+// from run to run, so results can differ in the last bits between runs.
+//
+// Error monitor (no read of X): after the last iteration the kernel leaves in mon[0] the cross
+// term <W_tld^T X_hat, H> and in mon[1] the quadratic term <W^T W, H H^T>; with ||X||^2 they give
+// ||X - W H||^2 ~ ||X||^2 - 2 mon[0] + mon[1] (X replaced by Q_L Q_L^T X in the cross term,
+// Section 3 Eq. 3.4).
+//
+// If *done is set on entry (an earlier residual check reached the target) the kernel returns at
+// once. Every wait is bounded: on time-out the kernel latches NMF_ERR_TIMEOUT and all blocks leave.
 #include "common.cuh"
 
 namespace nmfrp {
 namespace {
 
-constexpr int kPT = 256;          // threads per block
-constexpr int kCopies = 8;        // copies of each cross-block accumulator (spreads the atomics)
-constexpr long long kWaitCycles = 4000000000LL;   // about two seconds of polling before giving up
+constexpr int kPT = 768;          // threads per block (one block per SM, 85 registers a thread)
+constexpr int kGA = 4;            // lanes per row of W
+constexpr int kGB = 16;           // lanes per column of H
+constexpr int kMaxRows = kPT / kGA;   // rows of W per block
+constexpr int kMaxCols = kPT / kGB;   // columns of H per block
+constexpr int kCopies = 8;        // copies of each cross-block sum
+constexpr long long kWaitCycles = 4000000000LL;   // about two seconds of polling
 
 struct Barrier {
   unsigned int count;
@@ -58,7 +79,6 @@ __device__ bool grid_sync(Barrier* bar, unsigned nblocks, int* status, int* abor
           ok = 0;
           break;
         }
-        __nanosleep(32);
       }
       if (!ok) {
         latch(status, kStTimeout);
@@ -77,6 +97,7 @@ __device__ __forceinline__ float negp(float v) { return v < 0.f ? -v : 0.f; }
 struct PArgs {
   int64_t m, n;
   int r, ell, iters, rule;
+  int RB, CB;     // rows / columns per block
   float alpha, beta, eps;
   const float* QL;
   const float* QR;
@@ -84,279 +105,410 @@ struct PArgs {
   const float* Xchk;
   float* W;
   float* H;
-  double* accW;   // [2][kCopies][ell*r + r]
-  double* accH;   // [2][kCopies][r*ell]
+  float* accA;    // [2][kCopies][EA]: phase-A sums (W_tld_raw, W^T W)
+  float* accB;    // [2][kCopies][EB]: phase-B sums (H_tld, H H^T, cross)
+  float* mon;     // [2]: cross term and quadratic term of the last iteration
+  const int* done;
   Barrier* bar;
   int* status;
   int* abort_flag;
 };
 
-template <int RP, int RULE>
-__global__ void __launch_bounds__(kPT) iterate_persistent_kernel(PArgs a) {
+// Phase-A entries: W_tld_raw (ell x r) then W^T W (r x r). Phase-B entries: H_tld (r x ell),
+// H H^T (r x r), cross (1).
+__host__ __device__ __forceinline__ int ea_size(int r, int ell) { return ell * r + r * r; }
+__host__ __device__ __forceinline__ int eb_size(int r, int ell) { return r * ell + r * r + 1; }
+
+// Fixed-order sum of the kCopies copies of entry e, read through L2 (the copies are written by
+// other blocks' atomics).
+__device__ __forceinline__ float acc_read(const float* base, int E, int e) {
+  float v[kCopies];
+#pragma unroll
+  for (int c = 0; c < kCopies; ++c) v[c] = __ldcg(base + c * E + e);
+  float s = 0.f;
+#pragma unroll
+  for (int c = 0; c < kCopies; ++c) s += v[c];
+  return s;
+}
+
+// CA components per lane in phase A (RP = kGA * CA), CB_ per lane in phase B (kGB * CB_ >= RP).
+template <int CA, int CB_, int RULE>
+__global__ void __launch_bounds__(kPT, 1) iterate_persistent_kernel(PArgs a) {
+  constexpr int RP = kGA * CA;
+  constexpr int RPB = kGB * CB_;
+  static_assert(RPB >= RP, "phase B must cover the components of phase A");
   extern __shared__ __align__(16) float sh[];
   const int r = a.r, ell = a.ell, t = threadIdx.x;
-  const int EW = ell * r + r;  // W-phase partial entries: W_tld_raw (ell x r) + colsq (r)
-  const int EH = r * ell;      // H-phase partial entries: H_tld (r x ell)
-  float* HtT = sh;                   // [ell][RP]   H_tld^T
-  float* Gw = HtT + ell * RP;        // [RP][RP]
-  float* WtS = Gw + RP * RP;         // [ell][RP]   W_tld (normalised)
-  float* Gh = WtS + ell * RP;        // [RP][RP]
-  float* sc = Gh + RP * RP;          // [RP]        s_j of the last W phase
-  float* stA = sc + RP;              // [kPT][r]    staged rows of W / columns of H
-  float* stB = stA + kPT * RP;       // [kPT][ell]  staged rows of Q_L / rows of Q_R
+  const int EA = ea_size(r, ell), EB = eb_size(r, ell);
+  const int LS = ell | 1;                // odd stride of staged rows (conflict-free reads)
+  float* HtT = sh;                       // [ell][RPB]  H_tld^T
+  float* Gw = HtT + ell * RPB;           // [RPB][RPB]
+  float* WtS = Gw + RPB * RPB;           // [ell][RPB]  W_tld (normalised)
+  float* Gh = WtS + ell * RPB;           // [RPB][RPB]
+  float* sc = Gh + RPB * RPB;            // [RPB]       s_j of the last W phase
+  float* inv = sc + RPB;                 // [RPB]       1 / G_jj of the current phase
+  float* stA = inv + RPB;                // [kMaxRows][RP]  rows of W, later columns of H
+  float* stX = stA + kMaxRows * RPB;     // [RB][LS]    rows of X_chk
+  float* stB = stX + a.RB * LS;          // [RB][LS]    rows of Q_L
+  float* stX2 = stB + a.RB * LS;         // [CB][LS]    columns of X_hat
+  float* stB2 = stX2 + a.CB * LS;        // [CB][LS]    rows of Q_R
+  __shared__ float red[kPT / 32];
   const unsigned G = gridDim.x;
   const int64_t rb = (a.m + G - 1) / G, cbk = (a.n + G - 1) / G;
   const int64_t r0 = blockIdx.x * rb, r1 = min(a.m, r0 + rb);
   const int64_t c0 = blockIdx.x * cbk, c1 = min(a.n, c0 + cbk);
+  const int nrows = r1 > r0 ? static_cast<int>(r1 - r0) : 0;
+  const int ncols = c1 > c0 ? static_cast<int>(c1 - c0) : 0;
   const bool normalize = (RULE == 0);
+  const bool plain = (a.alpha == 0.f && a.beta == 0.f);
 
-  for (int j = t; j < RP; j += kPT) sc[j] = 1.f;
+  if (*reinterpret_cast<const volatile int*>(a.done)) return;   // the solve has converged
 
-  // H_tld partial of this block's columns of H into accH[slot]
-  auto h_partial = [&](int slot, bool scale_h) {
-    float acc[8];
-    for (int64_t cc = c0; cc < c1; cc += kPT) {
-      const int64_t c = cc + t;
-      __syncthreads();
-      if (c < c1) {
-        for (int j = 0; j < r; ++j) stA[t * RP + j] = a.H[j * a.n + c] * (scale_h ? sc[j] : 1.f);
-        for (int k = 0; k < ell; ++k) stB[t * ell + k] = a.QR[c * ell + k];
-      } else {
-        for (int j = 0; j < r; ++j) stA[t * RP + j] = 0.f;
-        for (int k = 0; k < ell; ++k) stB[t * ell + k] = 0.f;
-      }
-      __syncthreads();
-      const int cnt = static_cast<int>(c1 - cc < kPT ? c1 - cc : kPT);
-      for (int e0 = 0; e0 < EH; e0 += kPT * 8) {
+  for (int j = t; j < RPB; j += kPT) sc[j] = 1.f;
+
+  // phase-A role: row slot ra (row r0 + ra), lane ga in its group; phase-B role: column slot cb
+  const int ra = t / kGA, ga = t % kGA;
+  const int cb = t / kGB, gb = t % kGB;
+  const bool has_row = ra < nrows, has_col = cb < ncols;
+  const int64_t myrow = r0 + ra, mycol = c0 + cb;
+  float w[CA], h[CB_];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) acc[u] = 0.f;
+  for (int c = 0; c < CA; ++c) {
+    const int j = ga + kGA * c;
+    w[c] = (has_row && j < r) ? a.W[myrow * r + j] : 0.f;
+  }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int e = e0 + u * kPT + t;
-          if (e < EH) {
-            const int j = e / ell, k = e - j * ell;
-            float s = 0.f;
-            for (int q = 0; q < cnt; ++q) s = fmaf(stA[q * RP + j], stB[q * ell + k], s);
-            acc[u] = s;
-          }
-        }
+  for (int c = 0; c < CB_; ++c) {
+    const int j = gb + kGB * c;
+    h[c] = (has_col && j < r) ? a.H[j * a.n + mycol] : 0.f;
+  }
+  for (int e = t; e < a.RB * ell; e += kPT) {
+    const int i = e / ell, k = e - i * ell;
+    const bool in = i < nrows;
+    stX[i * LS + k] = in ? a.Xchk[(r0 + i) * ell + k] : 0.f;
+    stB[i * LS + k] = in ? a.QL[(r0 + i) * ell + k] : 0.f;
+  }
+  for (int e = t; e < a.CB * ell; e += kPT) {
+    const int cI = e / ell, k = e - cI * ell;
+    const bool in = cI < ncols;
+    stX2[cI * LS + k] = in ? a.Xhat[k * a.n + c0 + cI] : 0.f;
+    stB2[cI * LS + k] = in ? a.QR[(c0 + cI) * ell + k] : 0.f;
+  }
+
+  // phase-B block sums: H_tld (staged columns of H in stA x rows of Q_R), H H^T, cross term
+  auto add_b = [&](float* dst, float cross) {
+    for (int e = t; e < r * ell; e += kPT) {
+      const int j = e / ell, k = e - j * ell;
+      float v = 0.f;
+      for (int q = 0; q < ncols; ++q) v = fmaf(stA[q * RPB + j], stB2[q * LS + k], v);
+      atomicAdd(&dst[e], v);
+    }
+    for (int e = t; e < r * r; e += kPT) {
+      const int p = e / r, q2 = e - p * r;
+      float v = 0.f;
+      for (int q = 0; q < ncols; ++q) v = fmaf(stA[q * RPB + p], stA[q * RPB + q2], v);
+      atomicAdd(&dst[r * ell + e], v);
+    }
+    if (t == 0) atomicAdd(&dst[r * ell + r * r], cross);
+  };
+  // stage this thread's components of its column of H
+  auto stage_h = [&]() {
+    if (has_col) {
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int e = e0 + u * kPT + t;
-          if (e < EH)
-            atomicAdd(&a.accH[(slot * kCopies + blockIdx.x % kCopies) * EH + e],
-                      static_cast<double>(acc[u]));
-        }
-      }
+      for (int c = 0; c < CB_; ++c) stA[cb * RPB + gb + kGB * c] = h[c];
     }
   };
 
-  // prologue: H_tld of the initial H into accH[1]
-  if (a.iters > 0) h_partial(1, false);
+  // prologue: H_tld, H H^T of the initial H into accB[1]
+  for (int e = t; e < kMaxRows * RPB; e += kPT) stA[e] = 0.f;
+  __syncthreads();
+  stage_h();
+  __syncthreads();
+  add_b(a.accB + (1 * kCopies + blockIdx.x % kCopies) * EB, 0.f);
   if (!grid_sync(a.bar, G, a.status, a.abort_flag)) return;
 
   for (int it = 0; it < a.iters; ++it) {
-    const int ph = it & 1;        // parity of this iteration's accumulators
-    const int pr = ph ^ 1;        // parity of the previous ones
+    const int ph = it & 1, pr = ph ^ 1;
+    float* accA_w = a.accA + (ph * kCopies + blockIdx.x % kCopies) * EA;
+    const float* accB_r = a.accB + pr * kCopies * EB;
     // ---------------- phase A: rows of W
-    // clear the W accumulators of the next iteration (last read one phase ago), a slice per block
-    for (int64_t e = blockIdx.x * kPT + t; e < kCopies * EW; e += static_cast<int64_t>(G) * kPT)
-      a.accW[pr * kCopies * EW + e] = 0.0;
-    for (int e = t; e < ell * RP; e += kPT) {
-      const int k = e / RP, j = e - k * RP;
-      double v = 0.0;
-      if (j < r)
-        for (int c = 0; c < kCopies; ++c) v += a.accH[(pr * kCopies + c) * EH + j * ell + k];
-      HtT[e] = static_cast<float>(v);
+    // clear the phase-A sums written two phases ago (already read), a slice per block
+    for (int64_t e = static_cast<int64_t>(blockIdx.x) * kPT + t; e < kCopies * EA;
+         e += static_cast<int64_t>(G) * kPT)
+      a.accA[pr * kCopies * EA + e] = 0.f;
+    for (int e = t; e < ell * RPB; e += kPT) {
+      const int k = e / RPB, j = e - k * RPB;
+      HtT[e] = (j < r) ? acc_read(accB_r, EB, j * ell + k) : 0.f;
     }
     __syncthreads();
-    for (int e = t; e < RP * RP; e += kPT) {
-      const int p = e / RP, q = e - p * RP;
+    for (int e = t; e < RPB * RPB; e += kPT) {
+      const int p = e / RPB, q = e - p * RPB;
       float g = 0.f;
       if (p < r && q < r)
-        for (int k = 0; k < ell; ++k) g = fmaf(HtT[k * RP + p], HtT[k * RP + q], g);
+        for (int k = 0; k < ell; ++k) g = fmaf(HtT[k * RPB + p], HtT[k * RPB + q], g);
       Gw[e] = g;
+      if (p == q) inv[p] = g > 0.f ? 1.f / g : 0.f;
     }
     __syncthreads();
-    float accw[4];
-    for (int64_t ii = r0; ii < r1; ii += kPT) {
-      const int64_t i = ii + t;
-      if (i < r1) {
-        float w[RP], s[RP];
+    {
+      float s[CA];
 #pragma unroll
-        for (int j = 0; j < RP; ++j) {
-          w[j] = (j < r) ? a.W[i * r + j] / sc[j] : 0.f;
-          s[j] = 0.f;
-        }
-        const float* xr = a.Xchk + i * ell;
-        for (int k = 0; k < ell; ++k) {
-          const float xk = xr[k];
+      for (int c = 0; c < CA; ++c) {
+        w[c] = w[c] / sc[ga + kGA * c];   // normalisation of the previous W phase (1 for MU)
+        s[c] = 0.f;
+      }
+      const float* xr = stX + (has_row ? ra : 0) * LS;
+      for (int k = 0; k < ell; ++k) {
+        const float xk = xr[k];
 #pragma unroll
-          for (int j = 0; j < RP; ++j) s[j] = fmaf(xk, HtT[k * RP + j], s[j]);
-        }
-        if (RULE == 0) {
+        for (int c = 0; c < CA; ++c) s[c] = fmaf(xk, HtT[k * RPB + ga + kGA * c], s[c]);
+      }
+      if (RULE == 0) {
+        // t_j = S_j - sum_q w_q G_qj with w_q gathered from the group
+        // j = kGA * cj + o: the slot cj is unrolled (register index), the owner lane o is not
 #pragma unroll
-          for (int j = 0; j < RP; ++j) {
-            const float g = Gw[j * RP + j];
-            if (j < r && g > 0.f) {
-              float tt = s[j];
+        for (int cq = 0; cq < CA; ++cq) {
+#pragma unroll 1
+          for (int o = 0; o < kGA; ++o) {
+            const int q = kGA * cq + o;
+            const float wq = __shfl_sync(0xffffffffu, w[cq], o, kGA);
 #pragma unroll
-              for (int q = 0; q < RP; ++q) tt = fmaf(-w[q], Gw[q * RP + j], tt);
-              w[j] = fmaxf(0.f, w[j] + tt / g);
-            }
+            for (int c = 0; c < CA; ++c) s[c] = fmaf(-wq, Gw[q * RPB + ga + kGA * c], s[c]);
           }
-        } else {
+        }
 #pragma unroll
-          for (int j = 0; j < RP; ++j) {
-            float num = posp(s[j]), den = negp(s[j]) + a.eps;
-#pragma unroll
-            for (int q = 0; q < RP; ++q) {
-              const float gq = Gw[q * RP + j];
-              num = fmaf(w[q], negp(gq), num);
-              den = fmaf(w[q], posp(gq), den);
+        for (int cj = 0; cj < CA; ++cj) {
+#pragma unroll 1
+          for (int o = 0; o < kGA; ++o) {
+            const int j = kGA * cj + o;
+            float d = 0.f;
+            if (ga == o && j < r && Gw[j * RPB + j] > 0.f) {
+              const float wn = fmaxf(0.f, w[cj] + s[cj] * inv[j]);
+              d = wn - w[cj];
+              w[cj] = wn;
             }
-            s[j] = w[j] * sqrtf(num / den);
+            d = __shfl_sync(0xffffffffu, d, o, kGA);
+#pragma unroll
+            for (int c = 0; c < CA; ++c)
+              if (ga + kGA * c > j) s[c] = fmaf(-d, Gw[j * RPB + ga + kGA * c], s[c]);
           }
-#pragma unroll
-          for (int j = 0; j < RP; ++j) w[j] = s[j];
         }
-#pragma unroll
-        for (int j = 0; j < RP; ++j) {
-          if (j < r) a.W[i * r + j] = w[j];
-          stA[t * RP + j] = w[j];
-        }
-        for (int k = 0; k < ell; ++k) stB[t * ell + k] = a.QL[i * ell + k];
       } else {
-        for (int j = 0; j < RP; ++j) stA[t * RP + j] = 0.f;
-        for (int k = 0; k < ell; ++k) stB[t * ell + k] = 0.f;
-      }
-      __syncthreads();
-      const int cnt = static_cast<int>(r1 - ii < kPT ? r1 - ii : kPT);
-      for (int e0 = 0; e0 < EW; e0 += kPT * 4) {
+        float num[CA], den[CA];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int e = e0 + u * kPT + t;
-          float v = 0.f;
-          if (e < ell * r) {
-            const int k = e / r, j = e - k * r;
-            for (int q = 0; q < cnt; ++q) v = fmaf(stB[q * ell + k], stA[q * RP + j], v);
-          } else if (e < EW) {
-            const int j = e - ell * r;
-            for (int q = 0; q < cnt; ++q) v = fmaf(stA[q * RP + j], stA[q * RP + j], v);
+        for (int c = 0; c < CA; ++c) {
+          num[c] = posp(s[c]);
+          den[c] = negp(s[c]) + a.eps;
+        }
+#pragma unroll
+        for (int cq = 0; cq < CA; ++cq) {
+#pragma unroll 1
+          for (int o = 0; o < kGA; ++o) {
+            const int q = kGA * cq + o;
+            const float wq = __shfl_sync(0xffffffffu, w[cq], o, kGA);
+#pragma unroll
+            for (int c = 0; c < CA; ++c) {
+              const float gq = Gw[q * RPB + ga + kGA * c];
+              num[c] = fmaf(wq, negp(gq), num[c]);
+              den[c] = fmaf(wq, posp(gq), den[c]);
+            }
           }
-          accw[u] = v;
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int e = e0 + u * kPT + t;
-          if (e < EW)
-            atomicAdd(&a.accW[(ph * kCopies + blockIdx.x % kCopies) * EW + e],
-                      static_cast<double>(accw[u]));
-        }
+        for (int c = 0; c < CA; ++c)
+          w[c] = (ga + kGA * c < r) ? w[c] * sqrtf(num[c] / den[c]) : 0.f;
       }
-      __syncthreads();
+      if (!has_row) {
+#pragma unroll
+        for (int c = 0; c < CA; ++c) w[c] = 0.f;
+      }
+      if (ra < kMaxRows) {
+#pragma unroll
+        for (int c = 0; c < CA; ++c) stA[ra * RPB + ga + kGA * c] = w[c];
+      }
+    }
+    __syncthreads();
+    for (int e = t; e < ell * r; e += kPT) {
+      const int k = e / r, j = e - k * r;
+      float v = 0.f;
+      for (int q = 0; q < nrows; ++q) v = fmaf(stB[q * LS + k], stA[q * RPB + j], v);
+      atomicAdd(&accA_w[e], v);
+    }
+    for (int e = t; e < r * r; e += kPT) {
+      const int p = e / r, q2 = e - p * r;
+      float v = 0.f;
+      for (int q = 0; q < nrows; ++q) v = fmaf(stA[q * RPB + p], stA[q * RPB + q2], v);
+      atomicAdd(&accA_w[ell * r + e], v);
     }
     if (!grid_sync(a.bar, G, a.status, a.abort_flag)) return;
 
     // ---------------- phase B: columns of H
-    for (int64_t e = blockIdx.x * kPT + t; e < kCopies * EH; e += static_cast<int64_t>(G) * kPT)
-      a.accH[pr * kCopies * EH + e] = 0.0;
-    for (int j = t; j < RP; j += kPT) {
-      double c2 = 0.0;
-      if (j < r)
-        for (int c = 0; c < kCopies; ++c) c2 += a.accW[(ph * kCopies + c) * EW + ell * r + j];
-      const float c2f = static_cast<float>(c2);
-      sc[j] = (normalize && j < r && c2f > 0.f) ? sqrtf(c2f) : 1.f;
+    const float* accA_r = a.accA + ph * kCopies * EA;
+    float* accB_w = a.accB + (ph * kCopies + blockIdx.x % kCopies) * EB;
+    for (int64_t e = static_cast<int64_t>(blockIdx.x) * kPT + t; e < kCopies * EB;
+         e += static_cast<int64_t>(G) * kPT)
+      a.accB[pr * kCopies * EB + e] = 0.f;
+    for (int j = t; j < RPB; j += kPT) {
+      const float c2 = (j < r) ? acc_read(accA_r, EA, ell * r + j * r + j) : 0.f;
+      sc[j] = (normalize && j < r && c2 > 0.f) ? sqrtf(c2) : 1.f;
     }
     __syncthreads();
-    for (int e = t; e < ell * RP; e += kPT) {
-      const int k = e / RP, j = e - k * RP;
-      double v = 0.0;
-      if (j < r)
-        for (int c = 0; c < kCopies; ++c) v += a.accW[(ph * kCopies + c) * EW + k * r + j];
-      WtS[e] = (j < r) ? static_cast<float>(v) / sc[j] : 0.f;
+    for (int e = t; e < ell * RPB; e += kPT) {
+      const int k = e / RPB, j = e - k * RPB;
+      WtS[e] = (j < r) ? acc_read(accA_r, EA, k * r + j) / sc[j] : 0.f;
     }
     __syncthreads();
-    for (int e = t; e < RP * RP; e += kPT) {
-      const int p = e / RP, q = e - p * RP;
+    for (int e = t; e < RPB * RPB; e += kPT) {
+      const int p = e / RPB, q = e - p * RPB;
       float g = 0.f;
       if (p < r && q < r)
-        for (int k = 0; k < ell; ++k) g = fmaf(WtS[k * RP + p], WtS[k * RP + q], g);
+        for (int k = 0; k < ell; ++k) g = fmaf(WtS[k * RPB + p], WtS[k * RPB + q], g);
       Gh[e] = g;
+      if (p == q) inv[p] = g > 0.f ? 1.f / g : 0.f;
     }
     __syncthreads();
-    const bool plain = (a.alpha == 0.f && a.beta == 0.f);
-    for (int64_t cc = c0; cc < c1; cc += kPT) {
-      const int64_t c = cc + t;
-      if (c < c1) {
-        float h[RP], s[RP];
+    float cross = 0.f;
+    {
+      float s[CB_], shc[CB_];
 #pragma unroll
-        for (int j = 0; j < RP; ++j) {
-          h[j] = (j < r) ? a.H[j * a.n + c] * sc[j] : 0.f;
-          s[j] = 0.f;
-        }
-        for (int k = 0; k < ell; ++k) {
-          const float xk = a.Xhat[k * a.n + c];
-#pragma unroll
-          for (int j = 0; j < RP; ++j) s[j] = fmaf(xk, WtS[k * RP + j], s[j]);
-        }
-        if (RULE == 0) {
-#pragma unroll
-          for (int j = 0; j < RP; ++j) {
-            if (j >= r) continue;
-            const float g = Gh[j * RP + j];
-            float tt = s[j];
-#pragma unroll
-            for (int q = 0; q < RP; ++q) tt = fmaf(-Gh[j * RP + q], h[q], tt);
-            if (plain) {
-              if (g > 0.f) h[j] = fmaxf(0.f, h[j] + tt / g);
-            } else if (g + a.beta > 0.f) {
-              h[j] = fmaxf(0.f, (fmaf(h[j], g, tt) - a.alpha) / (g + a.beta));
-            }
-          }
-        } else {
-#pragma unroll
-          for (int j = 0; j < RP; ++j) {
-            float num = posp(s[j]), den = negp(s[j]) + a.eps;
-#pragma unroll
-            for (int q = 0; q < RP; ++q) {
-              const float gq = Gh[j * RP + q];
-              num = fmaf(negp(gq), h[q], num);
-              den = fmaf(posp(gq), h[q], den);
-            }
-            s[j] = h[j] * sqrtf(num / den);
-          }
-#pragma unroll
-          for (int j = 0; j < RP; ++j) h[j] = s[j];
-        }
-#pragma unroll
-        for (int j = 0; j < RP; ++j)
-          if (j < r) a.H[j * a.n + c] = h[j];
+      for (int c = 0; c < CB_; ++c) {
+        h[c] *= sc[gb + kGB * c];
+        s[c] = 0.f;
       }
+      const float* xc = stX2 + (has_col ? cb : 0) * LS;
+      for (int k = 0; k < ell; ++k) {
+        const float xk = xc[k];
+#pragma unroll
+        for (int c = 0; c < CB_; ++c) s[c] = fmaf(xk, WtS[k * RPB + gb + kGB * c], s[c]);
+      }
+#pragma unroll
+      for (int c = 0; c < CB_; ++c) shc[c] = s[c];   // S_H column for the monitor
+      if (RULE == 0) {
+#pragma unroll
+        for (int cq = 0; cq < CB_; ++cq) {
+#pragma unroll 1
+          for (int o = 0; o < kGB; ++o) {
+            const int q = kGB * cq + o;
+            const float hq = __shfl_sync(0xffffffffu, h[cq], o, kGB);
+#pragma unroll
+            for (int c = 0; c < CB_; ++c) s[c] = fmaf(-Gh[q * RPB + gb + kGB * c], hq, s[c]);
+          }
+        }
+#pragma unroll
+        for (int cj = 0; cj < CB_; ++cj) {
+#pragma unroll 1
+          for (int o = 0; o < kGB; ++o) {
+          const int j = kGB * cj + o;
+          float d = 0.f;
+          if (gb == o && j < r) {
+            const float g = Gh[j * RPB + j];
+            float hn = h[cj];
+            if (plain) {
+              if (g > 0.f) hn = fmaxf(0.f, h[cj] + s[cj] * inv[j]);
+            } else if (g + a.beta > 0.f) {
+              hn = fmaxf(0.f, (fmaf(h[cj], g, s[cj]) - a.alpha) / (g + a.beta));
+            }
+            d = hn - h[cj];
+            h[cj] = hn;
+          }
+          d = __shfl_sync(0xffffffffu, d, o, kGB);
+#pragma unroll
+          for (int c = 0; c < CB_; ++c)
+            if (gb + kGB * c > j) s[c] = fmaf(-d, Gh[j * RPB + gb + kGB * c], s[c]);
+          }
+        }
+      } else {
+        float num[CB_], den[CB_];
+#pragma unroll
+        for (int c = 0; c < CB_; ++c) {
+          num[c] = posp(s[c]);
+          den[c] = negp(s[c]) + a.eps;
+        }
+#pragma unroll
+        for (int cq = 0; cq < CB_; ++cq) {
+#pragma unroll 1
+          for (int o = 0; o < kGB; ++o) {
+            const int q = kGB * cq + o;
+            const float hq = __shfl_sync(0xffffffffu, h[cq], o, kGB);
+#pragma unroll
+            for (int c = 0; c < CB_; ++c) {
+              const float gq = Gh[q * RPB + gb + kGB * c];
+              num[c] = fmaf(negp(gq), hq, num[c]);
+              den[c] = fmaf(posp(gq), hq, den[c]);
+            }
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < CB_; ++c)
+          h[c] = (gb + kGB * c < r) ? h[c] * sqrtf(num[c] / den[c]) : 0.f;
+      }
+      if (!has_col) {
+#pragma unroll
+        for (int c = 0; c < CB_; ++c) h[c] = 0.f;
+      }
+#pragma unroll
+      for (int c = 0; c < CB_; ++c) cross = fmaf(shc[c], h[c], cross);
     }
-    // H_tld of the new H (next iteration's phase A); this block's columns were just written
-    // by this block's own threads
+    stage_h();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cross += __shfl_xor_sync(0xffffffffu, cross, o);
+    if ((t & 31) == 0) red[t >> 5] = cross;
     __syncthreads();
-    h_partial(ph, false);
+    float csum = 0.f;
+    if (t == 0)
+      for (int wI = 0; wI < kPT / 32; ++wI) csum += red[wI];
+    add_b(accB_w, csum);
     if (!grid_sync(a.bar, G, a.status, a.abort_flag)) return;
   }
-  // final normalisation of W's rows by the last s_j
-  if (normalize && a.iters > 0) {
-    for (int64_t i = r0 + t; i < r1; i += kPT)
-      for (int j = 0; j < r; ++j) a.W[i * r + j] /= sc[j];
+  // the last iteration's monitor terms: cross, and <W^T W, H H^T> for the normalised W
+  if (blockIdx.x == 0 && a.iters > 0) {
+    const int ph = (a.iters - 1) & 1;
+    const float* accA_r = a.accA + ph * kCopies * EA;
+    const float* accB_r = a.accB + ph * kCopies * EB;
+    float q2 = 0.f;
+    for (int e = t; e < r * r; e += kPT) {
+      const int p = e / r, q = e - p * r;
+      const float gww = acc_read(accA_r, EA, ell * r + e) / (sc[p] * sc[q]);
+      q2 = fmaf(gww, acc_read(accB_r, EB, r * ell + e), q2);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) q2 += __shfl_xor_sync(0xffffffffu, q2, o);
+    if ((t & 31) == 0) red[t >> 5] = q2;
+    __syncthreads();
+    if (t == 0) {
+      float s = 0.f;
+      for (int wI = 0; wI < kPT / 32; ++wI) s += red[wI];
+      a.mon[0] = acc_read(accB_r, EB, r * ell + r * r);
+      a.mon[1] = s;
+    }
+  }
+  // write back: W normalised by the last s_j, H
+  if (a.iters > 0) {
+    if (has_row)
+#pragma unroll
+      for (int c = 0; c < CA; ++c) {
+        const int j = ga + kGA * c;
+        if (j < r) a.W[myrow * r + j] = normalize ? w[c] / sc[j] : w[c];
+      }
+    if (has_col)
+#pragma unroll
+      for (int c = 0; c < CB_; ++c) {
+        const int j = gb + kGB * c;
+        if (j < r) a.H[j * a.n + mycol] = h[c];
+      }
   }
 }
 
-int rp_for(int r) {
-  if (r <= 8) return 8;
-  if (r <= 16) return 16;
-  return 32;
+size_t smem_for(int RPB, int ell, int RB, int CB) {
+  const int LS = ell | 1;
+  return sizeof(float) * (2 * ell * RPB + 2 * RPB * RPB + 2 * RPB + kMaxRows * RPB +
+                          static_cast<size_t>(2 * RB + 2 * CB) * LS);
 }
 
-template <int RP, int RULE>
-cudaError_t launch(const Launcher& L, PArgs& a, int device_sms) {
-  auto k = iterate_persistent_kernel<RP, RULE>;
-  const size_t smem = sizeof(float) * (2 * a.ell * RP + 2 * RP * RP + RP + kPT * RP + kPT * a.ell);
+template <int CA, int CB_, int RULE>
+cudaError_t launch(const Launcher& L, PArgs& a, int grid) {
+  auto k = iterate_persistent_kernel<CA, CB_, RULE>;
+  const size_t smem = smem_for(kGB * CB_, a.ell, a.RB, a.CB);
   cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
   if (err != cudaSuccess) return err;
@@ -364,7 +516,6 @@ cudaError_t launch(const Launcher& L, PArgs& a, int device_sms) {
   if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kPT, smem)) != cudaSuccess)
     return err;
   if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
-  const int grid = device_sms;   // one block per SM
   void* args[] = {&a};
   err = cudaLaunchCooperativeKernel(reinterpret_cast<void*>(k), dim3(grid), dim3(kPT), args, smem,
                                     L.stream);
@@ -372,20 +523,35 @@ cudaError_t launch(const Launcher& L, PArgs& a, int device_sms) {
   return err;
 }
 
+int num_sms() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms > 0 ? sms : 148;
+}
+
 }  // namespace
 
 size_t iterate_persistent_ws_bytes(int r, int ell) {
-  return sizeof(double) * kCopies * (2 * (ell * r + r) + 2 * r * ell) + sizeof(Barrier) +
-         2 * sizeof(int) + 1024;
+  const size_t ea = ea_size(r, ell), eb = eb_size(r, ell);
+  return sizeof(float) * kCopies * 2 * (ea + eb) + sizeof(Barrier) + 2 * sizeof(int) + 1024;
 }
 
-bool iterate_persistent_supported(int r, int ell) { return r <= 32 && ell <= 128; }
+bool iterate_persistent_supported(int64_t m, int64_t n, int r, int ell) {
+  const int grid = num_sms();
+  const int64_t rb = (m + grid - 1) / grid, cbk = (n + grid - 1) / grid;
+  return r <= 32 && rb <= kMaxRows && cbk <= kMaxCols &&
+         smem_for(32, ell, static_cast<int>(rb), static_cast<int>(cbk)) <= 220 * 1024;
+}
 
 cudaError_t launch_iterate_persistent(const Launcher& L, const IterArgs& ia, int iters, void* ws,
-                                      size_t ws_bytes, int* status) {
+                                      size_t ws_bytes, int* status, float* mon, const int* done) {
   if (ws_bytes < iterate_persistent_ws_bytes(ia.r, ia.ell)) return cudaErrorInvalidValue;
+  if (!iterate_persistent_supported(ia.m, ia.n, ia.r, ia.ell)) return cudaErrorInvalidValue;
   if (iters <= 0) return cudaSuccess;
   char* p = static_cast<char*>(ws);
+  const size_t ea = ea_size(ia.r, ia.ell), eb = eb_size(ia.r, ia.ell);
+  const int grid = num_sms();
   PArgs a;
   a.m = ia.m;
   a.n = ia.n;
@@ -402,24 +568,23 @@ cudaError_t launch_iterate_persistent(const Launcher& L, const IterArgs& ia, int
   a.Xchk = ia.Xchk;
   a.W = ia.W;
   a.H = ia.H;
-  a.accW = reinterpret_cast<double*>(p);
-  a.accH = a.accW + 2 * kCopies * (ia.ell * ia.r + ia.r);
-  a.bar = reinterpret_cast<Barrier*>(a.accH + 2 * kCopies * ia.r * ia.ell);
+  a.accA = reinterpret_cast<float*>(p);
+  a.accB = a.accA + 2 * kCopies * ea;
+  a.bar = reinterpret_cast<Barrier*>(a.accB + 2 * kCopies * eb);
   a.abort_flag = reinterpret_cast<int*>(a.bar + 1);
   a.status = status;
+  a.mon = mon;
+  a.done = done;
   const size_t clear = reinterpret_cast<char*>(a.abort_flag + 1) - p;
   cudaError_t err = cudaMemsetAsync(ws, 0, clear, L.stream);
   if (err != cudaSuccess) return err;
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int RP = rp_for(ia.r);
+  a.RB = static_cast<int>((ia.m + grid - 1) / grid);
+  a.CB = static_cast<int>((ia.n + grid - 1) / grid);
   const bool mu = ia.rule != 0;
-  switch (RP) {
-    case 8: return mu ? launch<8, 1>(L, a, sms) : launch<8, 0>(L, a, sms);
-    case 16: return mu ? launch<16, 1>(L, a, sms) : launch<16, 0>(L, a, sms);
-    default: return mu ? launch<32, 1>(L, a, sms) : launch<32, 0>(L, a, sms);
-  }
+  if (ia.r <= 8) return mu ? launch<2, 1, 1>(L, a, grid) : launch<2, 1, 0>(L, a, grid);
+  if (ia.r <= 16) return mu ? launch<4, 1, 1>(L, a, grid) : launch<4, 1, 0>(L, a, grid);
+  if (ia.r <= 24) return mu ? launch<6, 2, 1>(L, a, grid) : launch<6, 2, 0>(L, a, grid);
+  return mu ? launch<8, 2, 1>(L, a, grid) : launch<8, 2, 0>(L, a, grid);
 }
 
 }  // namespace nmfrp

@@ -1,13 +1,393 @@
-// NNDSVD initialisation from compressed data (Boutsidis & Gallopoulos 2008).
+// NNDSVD initial factors (Boutsidis & Gallopoulos 2008) from compressed data.
+//
+// X ~ Q_L X_hat (Section 3, Eq. 3.4), so the top singular triplets of X are taken from X_hat:
+// the eigenvectors U' of M = X_hat X_hat^T (l x l) give u_j = Q_L u'_j, sigma_j = sqrt(lambda_j)
+// and v_j = X_hat^T u'_j / sigma_j. For each component the larger-norm sign part of the pair
+// (u_j, v_j) is kept (the first pair in absolute value):
+//   w_j = sqrt(sigma_j s') u_j^{+/-} / ||u_j^{+/-}||,  h_j = sqrt(sigma_j s') v_j^{+/-} / ||v_j^{+/-}||,
+//   s' = ||u_j^{+/-}|| ||v_j^{+/-}||.
+// The result does not depend on the sign of each eigenvector.
+//
+// Kernels: float-float Gram of the rows of X_hat (partials over column slabs, FP64 sum); one-block
+// cyclic Jacobi eigensolver (round-robin ordering, ell/2 disjoint rotations per round, FP32,
+// Rutishauser's stable rotation); U and V with per-block sums of the squared sign parts; one
+// block that picks the signs and scales; the elementwise assembly of W and H.
 #include "common.cuh"
 
 namespace nmfrp {
+namespace {
 
-size_t nndsvd_ws_bytes(int64_t, int64_t, int, int) { return 256; }
+constexpr int kMaxL = 128;
+constexpr int kSlabCols = 256;
 
-cudaError_t launch_nndsvd(const Launcher&, int64_t, int64_t, int, int, const float*, const float*,
-                          float*, float*, void*, size_t, int*) {
-  return cudaErrorNotSupported;
+__device__ __forceinline__ void ff_fma(float a, float b, float& hi, float& lo) {
+  const float p = __fmul_rn(a, b);
+  const float e = __fmaf_rn(a, b, -p);
+  const float s = __fadd_rn(hi, p);
+  const float v = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, v)), __fsub_rn(p, v));
+  hi = s;
+  lo = __fadd_rn(lo, __fadd_rn(err, e));
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Partial M[p][q] = sum over a slab of 256 columns of X_hat[p][c] X_hat[q][c], p <= q.
+__global__ void __launch_bounds__(256) xgram_partial_kernel(const float* __restrict__ Xhat,
+                                                            int64_t n, int ell,
+                                                            double* __restrict__ part) {
+  extern __shared__ float xs[];   // [ell][kSlabCols + 1]
+  const int S = kSlabCols + 1;
+  const int64_t c0 = static_cast<int64_t>(blockIdx.x) * kSlabCols;
+  for (int e = threadIdx.x; e < ell * kSlabCols; e += blockDim.x) {
+    const int k = e / kSlabCols, c = e - k * kSlabCols;
+    xs[k * S + c] = (c0 + c < n) ? Xhat[k * n + c0 + c] : 0.f;
+  }
+  __syncthreads();
+  double* out = part + static_cast<int64_t>(blockIdx.x) * ell * ell;
+  for (int e = threadIdx.x; e < ell * ell; e += blockDim.x) {
+    const int p = e / ell, q = e - p * ell;
+    if (p > q) continue;
+    float hi = 0.f, lo = 0.f;
+    for (int c = 0; c < kSlabCols; ++c) ff_fma(xs[p * S + c], xs[q * S + c], hi, lo);
+    out[e] = static_cast<double>(hi) + static_cast<double>(lo);
+  }
+}
+
+// M[e] = sum over slabs of part[slab][e] (upper triangle, mirrored): one warp per entry.
+__global__ void xgram_sum_kernel(const double* __restrict__ part, int nparts, int ell,
+                                 double* __restrict__ M) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= ell * ell) return;
+  const int p = warp / ell, q = warp - p * ell;
+  const int a = p < q ? p : q, b = p < q ? q : p;
+  double v = 0.0;
+  for (int s = lane; s < nparts; s += 32) v += part[static_cast<int64_t>(s) * ell * ell + a * ell + b];
+  v = warp_sum(v);
+  if (lane == 0) M[warp] = v;
+}
+
+// One block: cyclic Jacobi on M (FP32). Writes the eigenvectors of the
+// r largest eigenvalues (columns, ell x r, row-major) and sigma_j = sqrt(lambda_j) (descending).
+__global__ void __launch_bounds__(512) jacobi_kernel(const double* __restrict__ Mg, int ell, int r,
+                                                     float* __restrict__ Ur,
+                                                     float* __restrict__ sigma) {
+  extern __shared__ float jsm[];
+  const int L = (ell + 1) / 2 * 2;   // even size (a zero row/column pads odd ell)
+  const int LS = L + 1;
+  float* Am = jsm;                   // [L][LS]
+  float* Vm = Am + L * LS;           // [L][LS]
+#define A(p, q) Am[(p) * LS + (q)]
+#define V(p, q) Vm[(p) * LS + (q)]
+  __shared__ float cs[kMaxL / 2], sn[kMaxL / 2];
+  __shared__ int top[kMaxL / 2], bot[kMaxL / 2];
+  __shared__ float off2, tot2;
+  __shared__ int order[kMaxL];
+  const int t = threadIdx.x, nt = blockDim.x;
+  for (int e = t; e < L * L; e += nt) {
+    const int p = e / L, q = e - p * L;
+    A(p, q) = (p < ell && q < ell) ? static_cast<float>(Mg[p * ell + q]) : 0.f;
+    V(p, q) = (p == q) ? 1.f : 0.f;
+  }
+  const int half = L / 2;
+  for (int i = t; i < half; i += nt) {
+    top[i] = 2 * i;
+    bot[i] = 2 * i + 1;
+  }
+  __syncthreads();
+  for (int sweep = 0; sweep < 30; ++sweep) {
+    if (t == 0) {
+      off2 = 0.f;
+      tot2 = 0.f;
+    }
+    __syncthreads();
+    float o = 0.f, d = 0.f;
+    for (int e = t; e < L * L; e += nt) {
+      const int p = e / L, q = e - p * L;
+      const float v = A(p, q) * A(p, q);
+      if (p != q) o += v;
+      d += v;
+    }
+    atomicAdd(&off2, o);
+    atomicAdd(&tot2, d);
+    __syncthreads();
+    if (!(off2 > 1e-14f * tot2)) break;
+    for (int round = 0; round < L - 1; ++round) {
+      // rotation angles of the disjoint pairs of this round
+      for (int i = t; i < half; i += nt) {
+        const int p = top[i] < bot[i] ? top[i] : bot[i];
+        const int q = top[i] < bot[i] ? bot[i] : top[i];
+        const float apq = A(p, q);
+        float c = 1.f, s = 0.f;
+        if (fabsf(apq) > 1e-30f) {
+          const float theta = (A(q, q) - A(p, p)) / (2.f * apq);
+          const float tt = copysignf(1.f, theta) / (fabsf(theta) + sqrtf(theta * theta + 1.f));
+          c = rsqrtf(tt * tt + 1.f);
+          s = tt * c;
+        }
+        cs[i] = c;
+        sn[i] = s;
+      }
+      __syncthreads();
+      // columns p, q of A and V: A <- A J, V <- V J
+      for (int e = t; e < half * L; e += nt) {
+        const int i = e / L, row = e - i * L;
+        const int p = top[i] < bot[i] ? top[i] : bot[i];
+        const int q = top[i] < bot[i] ? bot[i] : top[i];
+        const float c = cs[i], s = sn[i];
+        const float ap = A(row, p), aq = A(row, q);
+        A(row, p) = c * ap - s * aq;
+        A(row, q) = s * ap + c * aq;
+        const float vp = V(row, p), vq = V(row, q);
+        V(row, p) = c * vp - s * vq;
+        V(row, q) = s * vp + c * vq;
+      }
+      __syncthreads();
+      // rows p, q of A: A <- J^T A
+      for (int e = t; e < half * L; e += nt) {
+        const int i = e / L, col = e - i * L;
+        const int p = top[i] < bot[i] ? top[i] : bot[i];
+        const int q = top[i] < bot[i] ? bot[i] : top[i];
+        const float c = cs[i], s = sn[i];
+        const float ap = A(p, col), aq = A(q, col);
+        A(p, col) = c * ap - s * aq;
+        A(q, col) = s * ap + c * aq;
+      }
+      __syncthreads();
+      // next pairing (round-robin with top[0] fixed)
+      if (t == 0) {
+        const int last_top = top[half - 1];
+        const int first_bot = bot[0];
+        for (int i = half - 1; i > 1; --i) top[i] = top[i - 1];
+        if (half > 1) top[1] = first_bot;
+        for (int i = 0; i < half - 1; ++i) bot[i] = bot[i + 1];
+        bot[half - 1] = last_top;
+        if (half == 1) {
+          // a single pair: nothing to rotate
+        }
+      }
+      __syncthreads();
+    }
+  }
+  // order by eigenvalue, descending (selection; ell <= 128)
+  if (t == 0) {
+    for (int i = 0; i < L; ++i) order[i] = i;
+    for (int i = 0; i < r; ++i) {
+      int best = i;
+      for (int k = i + 1; k < L; ++k)
+        if (A(order[k], order[k]) > A(order[best], order[best])) best = k;
+      const int tmp = order[i];
+      order[i] = order[best];
+      order[best] = tmp;
+    }
+  }
+  __syncthreads();
+  for (int e = t; e < ell * r; e += nt) {
+    const int k = e / r, j = e - k * r;
+    Ur[e] = V(k, order[j]);
+  }
+  for (int j = t; j < r; j += nt) sigma[j] = sqrtf(fmaxf(A(order[j], order[j]), 0.f));
+#undef A
+#undef V
+}
+
+__device__ __forceinline__ float warp_sumf(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// rows: U[i][j] = sum_k QL[i][k] Ur[k][j] into W (scratch); per-block sums of the squared
+// positive and negative parts of each column
+__global__ void __launch_bounds__(256) u_rows_kernel(const float* __restrict__ QL, int64_t m,
+                                                     int ell, int r, const float* __restrict__ Ur,
+                                                     float* __restrict__ U, double* __restrict__ part) {
+  __shared__ float us[kMaxL * 64];
+  __shared__ float acc[2][64];
+  for (int e = threadIdx.x; e < ell * r; e += blockDim.x) us[e] = Ur[e];
+  for (int e = threadIdx.x; e < 2 * 64; e += blockDim.x) acc[e / 64][e % 64] = 0.f;
+  __syncthreads();
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t i0 = static_cast<int64_t>(blockIdx.x) * blockDim.x; i0 < m; i0 += stride) {
+    const int64_t i = i0 + threadIdx.x;
+    const bool act = i < m;
+    for (int j = 0; j < r; ++j) {
+      float s = 0.f;
+      if (act) {
+        const float* q = QL + i * ell;
+        for (int k = 0; k < ell; ++k) s = fmaf(q[k], us[k * r + j], s);
+        U[i * r + j] = s;
+      }
+      const float pp = warp_sumf(s > 0.f ? s * s : 0.f);
+      const float nn = warp_sumf(s < 0.f ? s * s : 0.f);
+      if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&acc[0][j], pp);
+        atomicAdd(&acc[1][j], nn);
+      }
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < 2 * r; e += blockDim.x)
+    part[static_cast<int64_t>(blockIdx.x) * 2 * r + e] = acc[e / r][e % r];
+}
+
+// columns: V[j][c] = sum_k Xhat[k][c] Ur[k][j] / sigma_j into H (scratch); sign-part sums
+__global__ void __launch_bounds__(256) v_cols_kernel(const float* __restrict__ Xhat, int64_t n,
+                                                     int ell, int r, const float* __restrict__ Ur,
+                                                     const float* __restrict__ sigma,
+                                                     float* __restrict__ V,
+                                                     double* __restrict__ part) {
+  __shared__ float us[kMaxL * 64];
+  __shared__ float isg[64];
+  __shared__ float acc[2][64];
+  for (int e = threadIdx.x; e < ell * r; e += blockDim.x) us[e] = Ur[e];
+  for (int j = threadIdx.x; j < r; j += blockDim.x) isg[j] = sigma[j] > 0.f ? 1.f / sigma[j] : 0.f;
+  for (int e = threadIdx.x; e < 2 * 64; e += blockDim.x) acc[e / 64][e % 64] = 0.f;
+  __syncthreads();
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t c0 = static_cast<int64_t>(blockIdx.x) * blockDim.x; c0 < n; c0 += stride) {
+    const int64_t c = c0 + threadIdx.x;
+    const bool act = c < n;
+    for (int j = 0; j < r; ++j) {
+      float s = 0.f;
+      if (act) {
+        for (int k = 0; k < ell; ++k) s = fmaf(Xhat[k * n + c], us[k * r + j], s);
+        s *= isg[j];
+        V[j * n + c] = s;
+      }
+      const float pp = warp_sumf(s > 0.f ? s * s : 0.f);
+      const float nn = warp_sumf(s < 0.f ? s * s : 0.f);
+      if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&acc[0][j], pp);
+        atomicAdd(&acc[1][j], nn);
+      }
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < 2 * r; e += blockDim.x)
+    part[static_cast<int64_t>(blockIdx.x) * 2 * r + e] = acc[e / r][e % r];
+}
+
+// per component: which sign part to keep and the two scale factors
+__global__ void nndsvd_coef_kernel(const double* __restrict__ upart, int nu,
+                                   const double* __restrict__ vpart, int nv, int r,
+                                   const float* __restrict__ sigma, float* __restrict__ coef) {
+  // coef[j] = scale of u part, coef[r + j] = scale of v part, coef[2r + j] = mode
+  // (0: absolute value, 1: positive parts, 2: negative parts, 3: zero component)
+  const int j = threadIdx.x;
+  if (j >= r) return;
+  double up = 0, un = 0, vp = 0, vn = 0;
+  for (int b = 0; b < nu; ++b) {
+    up += upart[b * 2 * r + j];
+    un += upart[b * 2 * r + r + j];
+  }
+  for (int b = 0; b < nv; ++b) {
+    vp += vpart[b * 2 * r + j];
+    vn += vpart[b * 2 * r + r + j];
+  }
+  const double sg = sigma[j];
+  float cu = 0.f, cv = 0.f, mode = 3.f;
+  if (j == 0) {
+    cu = cv = static_cast<float>(sqrt(sg));
+    mode = 0.f;
+  } else {
+    const double nup = sqrt(up), nun = sqrt(un), nvp = sqrt(vp), nvn = sqrt(vn);
+    const double mp = nup * nvp, mn = nun * nvn;
+    if (mp >= mn) {
+      if (mp > 0.0) {
+        const double f = sqrt(sg * mp);
+        cu = static_cast<float>(f / nup);
+        cv = static_cast<float>(f / nvp);
+        mode = 1.f;
+      }
+    } else {
+      const double f = sqrt(sg * mn);
+      cu = static_cast<float>(f / nun);
+      cv = static_cast<float>(f / nvn);
+      mode = 2.f;
+    }
+  }
+  coef[j] = cu;
+  coef[r + j] = cv;
+  coef[2 * r + j] = mode;
+}
+
+__device__ __forceinline__ float part_of(float x, int mode) {
+  if (mode == 0) return fabsf(x);
+  if (mode == 1) return x > 0.f ? x : 0.f;
+  if (mode == 2) return x < 0.f ? -x : 0.f;
+  return 0.f;
+}
+
+__global__ void nndsvd_apply_kernel(float* __restrict__ W, int64_t m, float* __restrict__ H,
+                                    int64_t n, int r, const float* __restrict__ coef) {
+  const int64_t tw = m * r, th = static_cast<int64_t>(r) * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tw + th;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    if (e < tw) {
+      const int j = static_cast<int>(e % r);
+      W[e] = coef[j] * part_of(W[e], static_cast<int>(coef[2 * r + j]));
+    } else {
+      const int64_t f = e - tw;
+      const int j = static_cast<int>(f / n);
+      H[f] = coef[r + j] * part_of(H[f], static_cast<int>(coef[2 * r + j]));
+    }
+  }
+}
+
+int blocks_for(int64_t work) {
+  const int64_t b = cdiv(work, 256);
+  return static_cast<int>(b < 1 ? 1 : (b > 1024 ? 1024 : b));
+}
+
+}  // namespace
+
+size_t nndsvd_ws_bytes(int64_t m, int64_t n, int r, int ell) {
+  const int64_t slabs = cdiv(n, kSlabCols);
+  const int bu = blocks_for(m), bv = blocks_for(n);
+  return sizeof(double) * ((slabs + 1) * ell * ell + 2 * r * (bu + bv)) +
+         sizeof(float) * (ell * r + r + 3 * r) + 4096;
+}
+
+cudaError_t launch_nndsvd(const Launcher& L, int64_t m, int64_t n, int r, int ell,
+                          const float* QL, const float* Xhat, float* W, float* H, void* ws,
+                          size_t ws_bytes, int* status) {
+  (void)status;
+  if (ell > kMaxL || r > 64 || r > ell) return cudaErrorNotSupported;
+  if (ws_bytes < nndsvd_ws_bytes(m, n, r, ell)) return cudaErrorInvalidValue;
+  const int64_t slabs = cdiv(n, kSlabCols);
+  const int bu = blocks_for(m), bv = blocks_for(n);
+  double* gpart = static_cast<double*>(ws);
+  double* M = gpart + slabs * ell * ell;
+  double* upart = M + ell * ell;
+  double* vpart = upart + 2 * r * bu;
+  float* Ur = reinterpret_cast<float*>(vpart + 2 * r * bv);
+  float* sigma = Ur + ell * r;
+  float* coef = sigma + r;
+  const size_t gsm = sizeof(float) * ell * (kSlabCols + 1);
+  cudaError_t err = cudaFuncSetAttribute(xgram_partial_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(gsm));
+  if (err != cudaSuccess) return err;
+  const int Lp = (ell + 1) / 2 * 2;
+  const size_t jsm = sizeof(float) * 2 * Lp * (Lp + 1);
+  if ((err = cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(jsm))) != cudaSuccess)
+    return err;
+  xgram_partial_kernel<<<static_cast<unsigned>(slabs), 256, gsm, L.stream>>>(Xhat, n, ell, gpart);
+  xgram_sum_kernel<<<static_cast<unsigned>(cdiv(static_cast<int64_t>(ell) * ell * 32, 256)), 256, 0,
+                     L.stream>>>(gpart, static_cast<int>(slabs), ell, M);
+  jacobi_kernel<<<1, 512, jsm, L.stream>>>(M, ell, r, Ur, sigma);
+  u_rows_kernel<<<bu, 256, 0, L.stream>>>(QL, m, ell, r, Ur, W, upart);
+  v_cols_kernel<<<bv, 256, 0, L.stream>>>(Xhat, n, ell, r, Ur, sigma, H, vpart);
+  nndsvd_coef_kernel<<<1, 64, 0, L.stream>>>(upart, bu, vpart, bv, r, sigma, coef);
+  nndsvd_apply_kernel<<<blocks_for(m * r + r * n), 256, 0, L.stream>>>(W, m, H, n, r, coef);
+  L.count(7);
+  return cudaGetLastError();
 }
 
 }  // namespace nmfrp

@@ -23,7 +23,8 @@ __device__ __forceinline__ double warp_sum(double v) {
 template <bool VEC>
 __global__ void __launch_bounds__(kThreads, 1) residual_kernel(
     const float* __restrict__ X, int64_t m, int64_t n, int64_t ldx, const float* __restrict__ W,
-    const float* __restrict__ H, int r, double* __restrict__ part) {
+    const float* __restrict__ H, int r, double* __restrict__ part, const int* gate) {
+  if (gate && !*reinterpret_cast<const volatile int*>(gate)) return;
   extern __shared__ __align__(16) float sh[];
   float* WsT = sh;                 // [r][kWS]   W tile transposed
   float* Hs = WsT + r * kWS;       // [r][kT]
@@ -124,7 +125,8 @@ __global__ void __launch_bounds__(kThreads, 1) residual_kernel(
 }
 
 __global__ void residual_final_kernel(const double* __restrict__ part, int nparts,
-                                      double* __restrict__ out2) {
+                                      double* __restrict__ out2, const int* gate) {
+  if (gate && !*reinterpret_cast<const volatile int*>(gate)) return;
   const int t = threadIdx.x;  // one warp
   double a = 0.0, b = 0.0;
   for (int i = t; i < nparts; i += 32) {
@@ -157,7 +159,7 @@ size_t residual_ws_bytes(int64_t, int64_t) {
 
 cudaError_t launch_residual(const Launcher& L, const float* X, int64_t m, int64_t n, int64_t ldx,
                             const float* W, const float* H, int r, double* out2, void* ws,
-                            size_t ws_bytes) {
+                            size_t ws_bytes, const int* gate) {
   if (ws_bytes < residual_ws_bytes(m, n)) return cudaErrorInvalidValue;
   const int64_t tiles = cdiv(m, kT) * cdiv(n, kT);
   double* part = static_cast<double*>(ws);
@@ -173,8 +175,65 @@ cudaError_t launch_residual(const Launcher& L, const float* X, int64_t m, int64_
     per_sm = 1;
   int grid = num_sms() * (per_sm < 4 ? per_sm : 4);
   if (tiles < grid) grid = static_cast<int>(tiles);
-  k<<<grid, kThreads, sm, L.stream>>>(X, m, n, ldx, W, H, r, part);
-  residual_final_kernel<<<1, 32, 0, L.stream>>>(part, grid, out2);
+  k<<<grid, kThreads, sm, L.stream>>>(X, m, n, ldx, W, H, r, part, gate);
+  residual_final_kernel<<<1, 32, 0, L.stream>>>(part, grid, out2, gate);
+  L.count(2);
+  return cudaGetLastError();
+}
+
+namespace {
+
+// sum of x^2 over X: FP32 within 4 elements, FP64 across them, fixed-order block and final sums
+__global__ void __launch_bounds__(256) sumsq_kernel(const float* __restrict__ X, int64_t m,
+                                                    int64_t n, int64_t ldx,
+                                                    double* __restrict__ part) {
+  __shared__ double red[8];
+  const bool vec = (ldx % 4 == 0) && (n % 4 == 0) && (reinterpret_cast<uintptr_t>(X) % 16 == 0);
+  double acc = 0.0;
+  if (vec) {
+    const int64_t n4 = n / 4, total = m * n4;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+      const int64_t i = e / n4, j = e - i * n4;
+      const float4 v = __ldcs(reinterpret_cast<const float4*>(X + i * ldx) + j);
+      acc += static_cast<double>(fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, v.w * v.w))));
+    }
+  } else {
+    const int64_t total = m * n;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+      const int64_t i = e / n, j = e - i * n;
+      const float v = X[i * ldx + j];
+      acc += static_cast<double>(v * v);
+    }
+  }
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double a = threadIdx.x < 8 ? red[threadIdx.x] : 0.0;
+    a = warp_sum(a);
+    if (threadIdx.x == 0) part[blockIdx.x] = a;
+  }
+}
+
+__global__ void sumsq_final_kernel(const double* __restrict__ part, int nparts,
+                                   double* __restrict__ out) {
+  double a = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += 32) a += part[i];
+  a = warp_sum(a);
+  if (threadIdx.x == 0) *out = a;
+}
+
+}  // namespace
+
+cudaError_t launch_sumsq(const Launcher& L, const float* X, int64_t m, int64_t n, int64_t ldx,
+                         double* out, void* ws, size_t ws_bytes) {
+  const int grid = num_sms() * 4;
+  if (ws_bytes < sizeof(double) * grid) return cudaErrorInvalidValue;
+  double* part = static_cast<double*>(ws);
+  sumsq_kernel<<<grid, 256, 0, L.stream>>>(X, m, n, ldx, part);
+  sumsq_final_kernel<<<1, 32, 0, L.stream>>>(part, grid, out);
   L.count(2);
   return cudaGetLastError();
 }

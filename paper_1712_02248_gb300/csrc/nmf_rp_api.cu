@@ -25,6 +25,12 @@ struct nmf_ctx {
   int* d_status = nullptr;   // latched device status word
   double* d_res = nullptr;   // residual sums (2 doubles)
   double* h_res = nullptr;   // pinned host copy
+  // solve-loop state on the device (one allocation)
+  float* d_mon = nullptr;    // [2] monitor terms of the last iteration run
+  int* d_flags = nullptr;    // [0] done, [1] gate, [2] always zero, [3] exact checks run
+  double* d_solve = nullptr; // [0] ||X||^2, [1] last exact rel_err, [2] iterations at that check
+  int* h_done = nullptr;     // pinned [2] copies of the done flag
+  int last_iters = 0, last_checks = 0;
   int64_t launches = 0;
   char msg[512] = {0};
   bool profiling = false;
@@ -306,7 +312,7 @@ nmf_status compress_impl(nmf_ctx* ctx, const nmf_params* p, const void* X, int64
 
 nmf_status iterate_impl(nmf_ctx* ctx, const nmf_params* p, const float* QL, const float* QR,
                         const float* Xhat, const float* Xchk, float* W, float* H, int iters,
-                        Arena a) {
+                        Arena a, const int* done = nullptr) {
   if (p->r > 64) return fail(ctx, NMF_ERR_UNSUPPORTED, "iterations support r <= 64");
   nmfrp::IterArgs ia;
   ia.m = p->m;
@@ -326,8 +332,9 @@ nmf_status iterate_impl(nmf_ctx* ctx, const nmf_params* p, const float* QL, cons
   Phase ph(ctx, NMF_PHASE_ITERATE);
   size_t rest = 0;
   void* ws = a.rest(&rest);
-  if (!(p->flags & NMF_FLAG_STAGED_ITERATE) && nmfrp::iterate_persistent_supported(p->r, p->ell)) {
-    NMF_CUDA(nmfrp::launch_iterate_persistent(launcher(ctx), ia, iters, ws, rest, ctx->d_status),
+  if (!(p->flags & NMF_FLAG_STAGED_ITERATE) && nmfrp::iterate_persistent_supported(p->m, p->n, p->r, p->ell)) {
+    NMF_CUDA(nmfrp::launch_iterate_persistent(launcher(ctx), ia, iters, ws, rest, ctx->d_status,
+                                              ctx->d_mon, done ? done : ctx->d_flags + 2),
              "iterate (persistent)");
   } else {
     NMF_CUDA(nmfrp::launch_iterate(launcher(ctx), ia, iters, ws, rest), "iterate");
@@ -376,6 +383,37 @@ nmf_status take_status(nmf_ctx* ctx) {
   return NMF_OK;
 }
 
+// Decide whether the exact residual of this check must run: always for the last check, else
+// when the error monitor (||X||^2 - 2 cross + quad, X replaced by its projection) is within
+// `margin` of the target.
+__global__ void solve_gate_kernel(const float* mon, const double* solve, double target,
+                                  double margin, int force, int* flags) {
+  if (flags[0]) {
+    flags[1] = 0;
+    return;
+  }
+  if (force || !(target > 0.0)) {
+    flags[1] = 1;
+    return;
+  }
+  const double x2 = solve[0];
+  const double e2 = x2 - 2.0 * static_cast<double>(mon[0]) + static_cast<double>(mon[1]);
+  const double est = x2 > 0.0 ? sqrt(fmax(e2, 0.0) / x2) : 0.0;
+  flags[1] = (est <= target * (1.0 + margin)) ? 1 : 0;
+}
+
+// After a gated exact residual: record it and raise `done` when the target is reached.
+__global__ void solve_decide_kernel(const double* res2, double target, int iters_done,
+                                    double* solve, int* flags) {
+  if (flags[0] || !flags[1]) return;
+  const double e2 = res2[0], x2 = solve[0];
+  const double rel = x2 > 0.0 ? sqrt(e2 / x2) : sqrt(e2);
+  solve[1] = rel;
+  solve[2] = iters_done;
+  flags[3] += 1;
+  if (target > 0.0 && rel <= target) flags[0] = 1;
+}
+
 struct DeviceGuard {
   int prev = -1;
   explicit DeviceGuard(int dev) {
@@ -406,6 +444,12 @@ nmf_status nmf_create(nmf_ctx** out, int device, void* cuda_stream) {
   if (cudaMalloc(&ctx->d_status, sizeof(int)) != cudaSuccess ||
       cudaMalloc(&ctx->d_res, 2 * sizeof(double)) != cudaSuccess ||
       cudaMallocHost(&ctx->h_res, 2 * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&ctx->d_mon, 4 * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&ctx->d_flags, 4 * sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&ctx->d_solve, 4 * sizeof(double)) != cudaSuccess ||
+      cudaMallocHost(&ctx->h_done, 2 * sizeof(int)) != cudaSuccess ||
+      cudaMemset(ctx->d_flags, 0, 4 * sizeof(int)) != cudaSuccess ||
+      cudaMemset(ctx->d_mon, 0, 4 * sizeof(float)) != cudaSuccess ||
       cudaMemset(ctx->d_status, 0, sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     nmf_destroy(ctx);
@@ -428,6 +472,10 @@ void nmf_destroy(nmf_ctx* ctx) {
   if (ctx->d_status) cudaFree(ctx->d_status);
   if (ctx->d_res) cudaFree(ctx->d_res);
   if (ctx->h_res) cudaFreeHost(ctx->h_res);
+  if (ctx->d_mon) cudaFree(ctx->d_mon);
+  if (ctx->d_flags) cudaFree(ctx->d_flags);
+  if (ctx->d_solve) cudaFree(ctx->d_solve);
+  if (ctx->h_done) cudaFreeHost(ctx->h_done);
   delete ctx;
 }
 
@@ -440,6 +488,13 @@ nmf_status nmf_set_stream(nmf_ctx* ctx, void* cuda_stream) {
 const char* nmf_last_error(const nmf_ctx* ctx) { return ctx ? ctx->msg : "context is NULL"; }
 
 int64_t nmf_launch_count(const nmf_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+nmf_status nmf_last_solve_info(const nmf_ctx* ctx, int32_t* iters, int32_t* exact_checks) {
+  if (!ctx) return NMF_ERR_INVALID_ARG;
+  if (iters) *iters = ctx->last_iters;
+  if (exact_checks) *exact_checks = ctx->last_checks;
+  return NMF_OK;
+}
 
 nmf_status nmf_set_profiling(nmf_ctx* ctx, int32_t on) {
   if (!ctx) return NMF_ERR_INVALID_ARG;
@@ -654,18 +709,78 @@ nmf_status nmf_solve(nmf_ctx* ctx, const nmf_params* p, int32_t init, const floa
     if (e == cudaErrorNotSupported) return fail(ctx, NMF_ERR_UNSUPPORTED, "nndsvd not available");
     if (e != cudaSuccess) return cuda_fail(ctx, e, "nndsvd");
   }
+  // Device-side loop: iterate a chunk, gate the exact residual on the error monitor, run it,
+  // decide; the host queues one chunk ahead and stops once the device has raised `done`.
   const int every = p->residual_every > 0 ? p->residual_every : std::max(p->iters, 1);
-  int done = 0;
-  double rel = -1.0;
-  while (true) {
+  const double margin = 0.05;
+  size_t rest = 0;
+  void* ws = a.rest(&rest);
+  NMF_CUDA(cudaMemsetAsync(ctx->d_flags, 0, 4 * sizeof(int), ctx->stream), "solve flags");
+  NMF_CUDA(cudaMemsetAsync(ctx->d_mon, 0, 4 * sizeof(float), ctx->stream), "solve monitor");
+  NMF_CUDA(cudaMemsetAsync(ctx->d_solve, 0, 4 * sizeof(double), ctx->stream), "solve state");
+  NMF_CUDA(nmfrp::launch_sumsq(launcher(ctx), X, m, n, ldx, ctx->d_solve, ws, rest), "sumsq");
+  const bool staged = (p->flags & NMF_FLAG_STAGED_ITERATE) || !nmfrp::iterate_persistent_supported(p->m, p->n, p->r, p->ell);
+  cudaEvent_t ev[2] = {pool_event(ctx), pool_event(ctx)};
+  if (!ev[0] || !ev[1]) return fail(ctx, NMF_ERR_CUDA, "event creation");
+  int done = 0, chunk = 0;
+  bool stopped = false;
+  nmf_status result = NMF_OK;
+  while (done < p->iters || (p->iters == 0 && chunk == 0)) {
     const int k = std::min(every, p->iters - done);
-    if (k > 0 && (st = iterate_impl(ctx, p, QL, QR, Xhat, Xchk, W, H, k, a)) != NMF_OK) return st;
+    if (k > 0 && (st = iterate_impl(ctx, p, QL, QR, Xhat, Xchk, W, H, k, a, ctx->d_flags)) != NMF_OK) {
+      result = st;
+      break;
+    }
     done += std::max(k, 0);
-    if ((st = residual_impl(ctx, p, X, ldx, W, H, &rel, nullptr, nullptr, a)) != NMF_OK) return st;
-    if ((p->target_rel_err > 0 && rel <= p->target_rel_err) || done >= p->iters) break;
+    const bool last = done >= p->iters;
+    // the staged iteration kernels do not feed the monitor: check exactly every time
+    solve_gate_kernel<<<1, 1, 0, ctx->stream>>>(ctx->d_mon, ctx->d_solve, p->target_rel_err,
+                                                margin, (last || staged) ? 1 : 0, ctx->d_flags);
+    {
+      Phase ph(ctx, NMF_PHASE_RESIDUAL);
+      NMF_CUDA(nmfrp::launch_residual(launcher(ctx), X, m, n, ldx, W, H, p->r, ctx->d_res, ws,
+                                      rest, ctx->d_flags + 1),
+               "residual");
+    }
+    solve_decide_kernel<<<1, 1, 0, ctx->stream>>>(ctx->d_res, p->target_rel_err, done,
+                                                  ctx->d_solve, ctx->d_flags);
+    ctx->launches += 2;
+    NMF_CUDA(cudaGetLastError(), "solve loop");
+    NMF_CUDA(cudaMemcpyAsync(ctx->h_done + (chunk & 1), ctx->d_flags, sizeof(int),
+                             cudaMemcpyDeviceToHost, ctx->stream),
+             "done copy");
+    NMF_CUDA(cudaEventRecord(ev[chunk & 1], ctx->stream), "event");
+    // the persistent kernel skips its work once `done` is set, so one chunk may be queued ahead;
+    // the per-stage kernels do not look at the flag, so their chunks are waited for one by one
+    const int look = staged ? chunk : chunk - 1;
+    if (look >= 0) {
+      NMF_CUDA(cudaEventSynchronize(ev[look & 1]), "event wait");
+      if (ctx->h_done[look & 1]) {
+        stopped = true;
+        break;
+      }
+    }
+    ++chunk;
+    if (p->iters == 0) break;
   }
-  if (rel_err_host) *rel_err_host = rel;
-  if (iters_done_host) *iters_done_host = done;
+  (void)stopped;
+  ctx->pool.push_back(ev[0]);
+  ctx->pool.push_back(ev[1]);
+  if (result != NMF_OK) return result;
+  double out[3] = {0, 0, 0};
+  int flags[4] = {0, 0, 0, 0};
+  NMF_CUDA(cudaMemcpyAsync(out, ctx->d_solve, 3 * sizeof(double), cudaMemcpyDeviceToHost,
+                           ctx->stream),
+           "solve result");
+  NMF_CUDA(cudaMemcpyAsync(flags, ctx->d_flags, 4 * sizeof(int), cudaMemcpyDeviceToHost,
+                           ctx->stream),
+           "solve flags");
+  NMF_CUDA(cudaStreamSynchronize(ctx->stream), "solve sync");
+  ctx->last_iters = static_cast<int>(out[2]);
+  ctx->last_checks = flags[3];
+  if (!(out[1] == out[1]) || out[1] > 1e300) return fail(ctx, NMF_ERR_NOT_FINITE, "residual is not finite");
+  if (rel_err_host) *rel_err_host = out[1];
+  if (iters_done_host) *iters_done_host = static_cast<int32_t>(out[2]);
   return take_status(ctx);
 }
 

@@ -30,7 +30,8 @@ INIT = {"given": 0, "nndsvd": 1}
 EXPORTS = ["nmf_create", "nmf_destroy", "nmf_set_stream", "nmf_last_error", "nmf_sync",
            "nmf_launch_count", "nmf_workspace_size", "nmf_gaussian", "nmf_quantize",
            "nmf_dual_pass", "nmf_qr", "nmf_sketch", "nmf_compress", "nmf_iterate",
-           "nmf_residual", "nmf_nndsvd", "nmf_solve", "nmf_set_profiling", "nmf_phase_times"]
+           "nmf_residual", "nmf_nndsvd", "nmf_solve", "nmf_set_profiling", "nmf_phase_times",
+           "nmf_last_solve_info"]
 PHASES = ["quantize", "dual_pass", "qr", "iterate", "residual", "init"]
 
 
@@ -74,6 +75,8 @@ _c = {
     "nmf_residual": _sig("nmf_residual", ctypes.c_int, [_vp, _P, _vp, _i64, _vp, _vp, _D, _D, _D]),
     "nmf_nndsvd": _sig("nmf_nndsvd", ctypes.c_int, [_vp, _P, _vp, _vp, _vp, _vp]),
     "nmf_set_profiling": _sig("nmf_set_profiling", ctypes.c_int, [_vp, _i32]),
+    "nmf_last_solve_info": _sig("nmf_last_solve_info", ctypes.c_int,
+                                [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
     "nmf_phase_times": _sig("nmf_phase_times", ctypes.c_int,
                             [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64), _i32]),
     "nmf_solve": _sig("nmf_solve", ctypes.c_int,
@@ -88,6 +91,7 @@ class NmfError(RuntimeError):
 
 
 FLAG_STAGED_ITERATE = 1
+FLAG_SIMT_DUAL_PASS = 2
 
 
 def params(m, n, r, ell, power_iters=2, iters=0, rule="fasthals", prec="fp32", seed=0,
@@ -292,3 +296,10 @@ def nmf_phase_times(ctx, reset=True):
     cnt = (_i64 * len(PHASES))()
     ctx._check(_c["nmf_phase_times"](ctx.handle, ms, cnt, 1 if reset else 0))
     return {name: (ms[i], int(cnt[i])) for i, name in enumerate(PHASES)}
+
+
+def nmf_last_solve_info(ctx):
+    """(iterations, exact residual checks) of the last nmf_solve on this context."""
+    it, ch = _i32(), _i32()
+    ctx._check(_c["nmf_last_solve_info"](ctx.handle, ctypes.byref(it), ctypes.byref(ch)))
+    return it.value, ch.value

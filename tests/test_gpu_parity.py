@@ -384,3 +384,104 @@ def test_iterate_zero_iterations_is_identity(lib, ctx):
     W, H = cu(pr.W0), cu(pr.H0)
     lib.nmf_iterate(ctx, p, cu(QL), cu(QR), cu(Xhat), cu(Xchk), W, H, 0)
     assert np.array_equal(host(W), pr.W0) and np.array_equal(host(H), pr.H0)
+
+
+def test_bf16_sketch_tensor_core_and_simt_agree(lib, ctx):
+    """The tcgen05 pass rounds V, U to BF16, the SIMT pass keeps them FP32; both sketches of the
+    same BF16 X agree within the low-precision tolerance and span the same subspace as the FP64
+    oracle's on the exact X to within 2e-2 in projected data."""
+    pr = inputs.random_problem(12, 3000, 2048, 20, 40, w=2)
+    X = cu(pr.X)
+    Xq = lib.nmf_quantize(ctx, X)
+    outs = []
+    for flags in (0, lib.FLAG_SIMT_DUAL_PASS):
+        p = lib.params(3000, 2048, 20, 40, power_iters=2, prec="bf16", flags=flags)
+        QL, QR = lib.nmf_sketch(ctx, p, Xq, cu(pr.omega_L), cu(pr.omega_R))
+        Xhat, Xchk = lib.nmf_compress(ctx, p, Xq, QL, QR)
+        lib.nmf_sync(ctx)
+        outs.append((host(QL), host(Xhat)))
+    (QLt, Xht), (QLs, Xhs) = outs
+    QLo, QRo = O.sketch(pr.X, pr.omega_L, pr.omega_R, 2)
+    Xho, _ = O.compress(pr.X, QLo, QRo)
+    ref = QLo @ Xho
+    assert rel(QLt @ Xht, ref) <= 2e-2
+    assert rel(QLs @ Xhs, ref) <= 2e-2
+    assert rel(QLt @ Xht, QLs @ Xhs) <= 2e-2
+
+
+def test_solve_monitor_gates_exact_checks(lib, ctx):
+    """With a target, the device-side loop runs the exact residual only when the compressed
+    error monitor is within 5 % of the target; the stopping iteration equals the one found by
+    checking the exact residual at every check (the staged kernels, which never use the
+    monitor)."""
+    pr = inputs.random_problem(13, 2000, 1500, 10, 20, w=2)
+    X = cu(pr.X)
+    res = {}
+    for flags in (0, lib.FLAG_STAGED_ITERATE):
+        p = lib.params(2000, 1500, 10, 20, power_iters=2, iters=300, residual_every=10,
+                       target_rel_err=0.0, seed=3, flags=flags)
+        W, H = cu(pr.W0), cu(pr.H0)
+        e_final, _ = lib.nmf_solve(ctx, p, X, W, H)
+        target = 1.01 * e_final
+        p = lib.params(2000, 1500, 10, 20, power_iters=2, iters=300, residual_every=10,
+                       target_rel_err=target, seed=3, flags=flags)
+        W, H = cu(pr.W0), cu(pr.H0)
+        e, it = lib.nmf_solve(ctx, p, X, W, H)
+        its, checks = lib.nmf_last_solve_info(ctx)
+        assert e <= target and its == it
+        assert abs(lib.nmf_residual(ctx, p, X, W, H)[0] - e) <= 1e-6 * e   # W, H match the check
+        res[flags] = (it, checks)
+    (it_mon, checks_mon), (it_all, checks_all) = res[0], res[lib.FLAG_STAGED_ITERATE]
+    assert checks_all == it_all // 10
+    assert checks_mon < checks_all
+    assert abs(it_mon - it_all) <= 10
+
+
+# ------------------------------------------------------------------ NNDSVD from compressed data
+
+def designed_compressed(seed, m, n, ell, decay):
+    """Q_L with orthonormal columns and X_hat = A diag(s) B^T with s_j = decay^j: a compressed
+    pair whose singular values are known and separated."""
+    rng = np.random.default_rng(seed)
+    QL = np.linalg.qr(rng.standard_normal((m, ell)))[0]
+    A = np.linalg.qr(rng.standard_normal((ell, ell)))[0]
+    B = np.linalg.qr(rng.standard_normal((n, ell)))[0]
+    s = decay ** np.arange(ell)
+    return QL.astype(np.float32), ((A * s) @ B.T).astype(np.float32), s
+
+
+@pytest.mark.parametrize("seed,m,n,r,ell,decay", [(0, 1001, 333, 4, 9, 0.7),
+                                                  (1, 3000, 1200, 20, 40, 0.85),
+                                                  (2, 256, 4100, 1, 16, 0.5)])
+def test_nndsvd_matches_oracle(lib, ctx, seed, m, n, r, ell, decay):
+    """Each column of W and row of H against the oracle's LAPACK-SVD NNDSVD on the same FP32
+    inputs. The kernel's eigensolver runs in FP32, so component j carries the eigenvector error
+    ell * eps32 * lambda_1 / gap_j with lambda = s^2 and gap_j the distance of lambda_j to its
+    neighbours."""
+    QL, Xhat, s = designed_compressed(seed, m, n, ell, decay)
+    Wo, Ho = O.nndsvd_compressed(QL, Xhat, r)
+    # precondition: no component is close to a tie between its two sign parts
+    U1, _, Vt = np.linalg.svd(Xhat.astype(np.float64), full_matrices=False)
+    U = QL.astype(np.float64) @ U1[:, :r]
+    for j in range(1, r):
+        x, y = U[:, j], Vt[j]
+        mp = np.linalg.norm(np.maximum(x, 0)) * np.linalg.norm(np.maximum(y, 0))
+        mn = np.linalg.norm(np.minimum(x, 0)) * np.linalg.norm(np.minimum(y, 0))
+        assert abs(mp - mn) > 1e-3 * (mp + mn)
+    p = lib.params(m, n, r, ell)
+    W, H = lib.nmf_nndsvd(ctx, p, cu(QL), cu(Xhat))
+    W, H = host(W), host(H)
+    lam = s ** 2
+    eps32 = 2.0 ** -24
+    for j in range(r):
+        gap = min(lam[j - 1] - lam[j] if j > 0 else np.inf, lam[j] - lam[j + 1])
+        tol = 1e-5 + ell * eps32 * lam[0] / gap
+        assert rel(W[:, j], Wo[:, j]) <= tol, (j, rel(W[:, j], Wo[:, j]), tol)
+        assert rel(H[j], Ho[j]) <= tol, (j, rel(H[j], Ho[j]), tol)
+    assert (W >= 0).all() and (H >= 0).all()
+
+
+def test_nndsvd_rejects_rank_above_sketch(lib, ctx):
+    QL, Xhat, _ = designed_compressed(0, 100, 80, 8, 0.5)
+    with pytest.raises(lib.NmfError):
+        lib.nmf_nndsvd(ctx, lib.params(100, 80, 9, 8), cu(QL), cu(Xhat))
