@@ -193,6 +193,36 @@ nmf_status nmf_residual(nmf_ctx* ctx, const nmf_params* p, const float* X, int64
                         const float* W, const float* H, double* rel_err_host,
                         double* err2_host, double* x2_host);
 
+/*
+ * The residual sums of nmf_residual without a context and without allocating device memory.
+ * The paper has no counterpart: this is a service entry point for callers that cannot allocate
+ * when they need the residual, such as a serving loop whose device memory is all handed to its
+ * own pools, or code that must not stall the device's other streams (cudaFree synchronises the
+ * whole device). The per-block partial sums live in a fixed 32 KB array in the library's global
+ * memory (two doubles per block; the grid is at most 4 blocks per SM, so devices with up to 512
+ * SMs fit) instead of a workspace. Nothing in it has to start at zero.
+ *
+ * device: the CUDA device of X, W, H and out_dev; it is made current for the call.
+ * stream: a cudaStream_t of that device (NULL = legacy default stream).
+ * X: m x n FP32, row-major with leading dimension ldx >= n. W: m x r, H: r x n, contiguous
+ * row-major FP32, 1 <= r <= 128. All device pointers, owned by the caller.
+ * out_dev: 2 doubles of device memory: out_dev[0] = ||X - W H||_F^2, out_dev[1] = ||X||_F^2,
+ * summed as in nmf_residual. The relative error is sqrt(out_dev[0] / out_dev[1]).
+ * The call queues two kernels on `stream` and returns without synchronising.
+ *
+ * The first call on a device does a one-time set-up: it resolves the array's device address,
+ * which can load the library's device code onto the device; make that first call before any
+ * stream capture. Calls on one device share the array, so two calls in flight at the same time
+ * (on different streams, or from different threads) race: order them on one stream or with
+ * events.
+ * Returns NMF_ERR_INVALID_ARG for NULL pointers, bad sizes or a device that cannot be made
+ * current; NMF_ERR_UNSUPPORTED if the device needs more partial-sum slots than the array holds;
+ * NMF_ERR_CUDA if the set-up or a launch fails.
+ */
+nmf_status nmf_residual_static(int32_t device, void* stream, const float* X, int64_t m,
+                               int64_t n, int64_t ldx, int32_t r, const float* W, const float* H,
+                               double* out_dev);
+
 /* NNDSVD initial factors (Boutsidis & Gallopoulos) from the compressed data: the top r singular
  * triplets of X ~ Q_L X_hat (Section 3, Eq. 3.4) come from the l x l eigenproblem of
  * X_hat X_hat^T (Gram in float-float arithmetic summed in FP64, cyclic Jacobi in FP32), with

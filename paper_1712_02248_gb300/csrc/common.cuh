@@ -104,6 +104,10 @@ size_t residual_ws_bytes(int64_t m, int64_t n);
 cudaError_t launch_residual(const Launcher& L, const float* X, int64_t m, int64_t n, int64_t ldx,
                             const float* W, const float* H, int r, double* out2, void* ws,
                             size_t ws_bytes, const int* gate = nullptr);
+// Static scratch for launch_residual: the device address (resolved once per device, which must be
+// current) of a fixed array of residual_static_capacity_bytes() bytes in global memory.
+size_t residual_static_capacity_bytes();
+cudaError_t residual_static_scratch(int device, void** addr);
 // ||X||^2 into *out (device, FP64).
 cudaError_t launch_sumsq(const Launcher& L, const float* X, int64_t m, int64_t n, int64_t ldx,
                          double* out, void* ws, size_t ws_bytes);

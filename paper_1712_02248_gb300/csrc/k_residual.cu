@@ -6,6 +6,8 @@
 // (K = r FMAs each), and adds (x - wh)^2 and x^2 to per-thread sums. Per-tile sums are FP32 (64
 // terms), accumulated across tiles in FP64; block sums and the final sum are FP64 in a fixed
 // order (deterministic).
+#include <mutex>
+
 #include "common.cuh"
 
 namespace nmfrp {
@@ -236,6 +238,43 @@ cudaError_t launch_sumsq(const Launcher& L, const float* X, int64_t m, int64_t n
   sumsq_final_kernel<<<1, 32, 0, L.stream>>>(part, grid, out);
   L.count(2);
   return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- residual with static scratch
+// A caller that cannot allocate device memory when it wants the residual (a serving loop whose
+// device memory is all handed to its own pools, or code that must not stall the device's other
+// streams, as cudaFree does by synchronising the device) gets the per-block partial sums in a
+// fixed array of this module's global memory instead of a context workspace. Each block writes
+// its two slots before the final sum reads them, so the array needs no clearing; two calls in
+// flight on one device at the same time share it and race.
+namespace {
+
+constexpr int kStaticPartialDoubles = 4096;   // 32 KB: two doubles per block, up to 2048 blocks
+__device__ __align__(256) double g_residual_partials[kStaticPartialDoubles];
+
+constexpr int kStaticMaxDevices = 64;
+std::mutex g_static_mu;
+void* g_static_addr[kStaticMaxDevices] = {};
+
+}  // namespace
+
+size_t residual_static_capacity_bytes() { return sizeof(double) * kStaticPartialDoubles; }
+
+cudaError_t residual_static_scratch(int device, void** addr) {
+  if (device < 0 || device >= kStaticMaxDevices) return cudaErrorInvalidDevice;
+  int cur = -1;
+  cudaError_t e = cudaGetDevice(&cur);
+  if (e != cudaSuccess) return e;
+  if (cur != device) return cudaErrorInvalidDevice;   // set-up needs the device current
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_addr[device]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_residual_partials);
+    if (e != cudaSuccess) return e;
+    g_static_addr[device] = p;
+  }
+  *addr = g_static_addr[device];
+  return cudaSuccess;
 }
 
 }  // namespace nmfrp

@@ -656,6 +656,25 @@ nmf_status nmf_residual(nmf_ctx* ctx, const nmf_params* p, const float* X, int64
   return residual_impl(ctx, p, X, ldx, W, H, rel_err_host, err2_host, x2_host, a);
 }
 
+nmf_status nmf_residual_static(int32_t device, void* stream, const float* X, int64_t m,
+                               int64_t n, int64_t ldx, int32_t r, const float* W, const float* H,
+                               double* out_dev) {
+  if (!X || !W || !H || !out_dev || m < 1 || n < 1 || ldx < n || r < 1 || r > 128)
+    return NMF_ERR_INVALID_ARG;
+  DeviceGuard g(device);
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess || cur != device) return NMF_ERR_INVALID_ARG;
+  void* scratch = nullptr;
+  if (nmfrp::residual_static_scratch(device, &scratch) != cudaSuccess) return NMF_ERR_CUDA;
+  const size_t cap = nmfrp::residual_static_capacity_bytes();
+  if (nmfrp::residual_ws_bytes(m, n) > cap) return NMF_ERR_UNSUPPORTED;
+  nmfrp::Launcher L;
+  L.stream = static_cast<cudaStream_t>(stream);
+  if (nmfrp::launch_residual(L, X, m, n, ldx, W, H, r, out_dev, scratch, cap) != cudaSuccess)
+    return NMF_ERR_CUDA;
+  return NMF_OK;
+}
+
 nmf_status nmf_nndsvd(nmf_ctx* ctx, const nmf_params* p, const float* QL, const float* Xhat,
                       float* W, float* H) {
   if (!ctx) return NMF_ERR_INVALID_ARG;

@@ -30,7 +30,7 @@ INIT = {"given": 0, "nndsvd": 1}
 EXPORTS = ["nmf_create", "nmf_destroy", "nmf_set_stream", "nmf_last_error", "nmf_sync",
            "nmf_launch_count", "nmf_workspace_size", "nmf_gaussian", "nmf_quantize",
            "nmf_dual_pass", "nmf_qr", "nmf_sketch", "nmf_compress", "nmf_iterate",
-           "nmf_residual", "nmf_nndsvd", "nmf_solve", "nmf_set_profiling", "nmf_phase_times",
+           "nmf_residual", "nmf_residual_static", "nmf_nndsvd", "nmf_solve", "nmf_set_profiling", "nmf_phase_times",
            "nmf_last_solve_info"]
 PHASES = ["quantize", "dual_pass", "qr", "iterate", "residual", "init"]
 
@@ -74,6 +74,8 @@ _c = {
     "nmf_iterate": _sig("nmf_iterate", ctypes.c_int, [_vp, _P, _vp, _vp, _vp, _vp, _vp, _vp, _i32]),
     "nmf_residual": _sig("nmf_residual", ctypes.c_int, [_vp, _P, _vp, _i64, _vp, _vp, _D, _D, _D]),
     "nmf_nndsvd": _sig("nmf_nndsvd", ctypes.c_int, [_vp, _P, _vp, _vp, _vp, _vp]),
+    "nmf_residual_static": _sig("nmf_residual_static", ctypes.c_int,
+                                [_i32, _vp, _vp, _i64, _i64, _i64, _i32, _vp, _vp, _vp]),
     "nmf_set_profiling": _sig("nmf_set_profiling", ctypes.c_int, [_vp, _i32]),
     "nmf_last_solve_info": _sig("nmf_last_solve_info", ctypes.c_int,
                                 [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
@@ -266,6 +268,29 @@ def nmf_residual(ctx, p, X, W, H):
                                   _ptr(_dev_f32(H, "H")), ctypes.byref(rel), ctypes.byref(e2),
                                   ctypes.byref(x2)))
     return rel.value, e2.value, x2.value
+
+
+_STATIC_ERRORS = {
+    1: "bad pointer, size or device",
+    7: "the device needs more partial-sum slots than the static array holds",
+    2: "set-up or launch failed",
+}
+
+
+def nmf_residual_static(X, W, H, out, stream=None):
+    """||X - W H||^2 and ||X||^2 into `out` (2 float64 on X's device) with no context and no
+    device allocation; queued on `stream` (torch's current stream), not synchronised."""
+    X, ldx = _x_arg(X, 0)
+    W, H = _dev_f32(W, "W"), _dev_f32(H, "H")
+    if not (out.is_cuda and out.dtype == torch.float64 and out.numel() >= 2 and out.is_contiguous()):
+        raise ValueError("out must be a contiguous float64 CUDA tensor of 2 elements")
+    dev = X.device.index
+    s = stream if stream is not None else torch.cuda.current_stream(X.device)
+    st = _c["nmf_residual_static"](dev, _vp(s.cuda_stream), _ptr(X), X.shape[0], X.shape[1], ldx,
+                                   W.shape[1], _ptr(W), _ptr(H), _ptr(out))
+    if st != NMF_OK:
+        raise NmfError(st, "nmf_residual_static: " + _STATIC_ERRORS.get(st, "error"))
+    return out
 
 
 def nmf_nndsvd(ctx, p, QL, Xhat, W=None, H=None):
