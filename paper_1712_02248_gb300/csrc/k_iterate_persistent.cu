@@ -2,31 +2,33 @@
 //
 // The update rules are those of k_iterate.cu (Section 4, Eq. fastHALS_a with the Section 4.1
 // terms; Section 3.1, Algorithm 3 with the semi-NMF rule). Each block owns a fixed slice of the
-// rows of W and of the columns of H for the whole run. The slice's rows of X_chk and Q_L and its
-// columns of X_hat and rows of Q_R are staged in shared memory once. A row of W is handled by a
-// group of kGA = 4 lanes and a column of H by kGB = 16 lanes, each lane owning the components
-// j = g, g + G, g + 2G, ... (g its index in the group); the factors stay in registers across
-// iterations. One iteration:
+// rows of W and of the columns of H for the whole run; the slice's rows of X_chk and Q_L, its
+// columns of X_hat and rows of Q_R, and its rows of W and columns of H live in shared memory
+// across iterations. One iteration:
 //
-//   A  (rows of W)    H_tld, G_W from the cross-block sums; S_W row; Gauss-Seidel sweep over j;
-//                     the block adds its rows' W_tld_raw = Q_L^T W and W_raw^T W_raw (whose
-//                     diagonal holds the squared column norms) into the cross-block sums.
+//   A  (rows of W)    H_tld from the cross-block sums; G_W = H_tld H_tld^T; per row: S_W row,
+//                     Gauss-Seidel sweep over j; then the block's share of
+//                     [Q_L | W]^T W  (W_tld_raw = Q_L^T W and W^T W, whose diagonal holds the
+//                     squared column norms) is added into the cross-block sums.
 //   -- grid barrier --
-//   B  (columns of H) s_j = ||w_j||, W_tld = raw / s, G_H; compensation h_j *= s_j; S_H column;
-//                     sweep; the block adds H Q_R, H H^T and <S_H, H> into the sums read by the
-//                     next phase A and by the error monitor.
+//   B  (columns of H) s_j = ||w_j||, W_tld = raw / s, G_H = W_tld^T W_tld; per column: h_j *= s_j
+//                     (the normalisation moved to H), S_H column, sweep; then the block's share of
+//                     H^T [Q_R | H]  (H_tld and H H^T) and of <S_H, H> is added.
 //   -- grid barrier --
 //
-// G_W and G_H are symmetric; every lane reads them along a row (consecutive lanes, distinct
-// shared-memory banks).
+// A row of W is handled by kGA = 2 lanes and a column of H by kGB = 4 lanes; each lane owns a
+// contiguous run of RP / kGA (RP / kGB) components, so every shared-memory read of a Gram row or
+// of H_tld / W_tld is a broadcast vector load. The sweep is incremental: t_j = S_j - sum_q w_q
+// G_qj is formed for every j; when w_j moves by d (computed by the lane owning j, broadcast in
+// the group) every t_j' drops by d G_jj' (those with j' <= j are never read again, so they are
+// updated too instead of being masked). These are the Gauss-Seidel values of the paper's
+// component-by-component update.
 //
-// The sweep is incremental: t_j = S_j - sum_q w_q G_qj is formed for every j; when w_j moves by d
-// (computed by the lane owning j and broadcast in the group) every later t_j' drops by d G_jj'.
-// These are the Gauss-Seidel values of the paper's component-by-component update.
-//
-// Cross-block sums: FP32 red.add into kCopies copies (block b adds into copy b % kCopies), read
-// back through L2 as a fixed-order sum of the copies. The order of the adds within a copy varies
-// from run to run, so results can differ in the last bits between runs.
+// Block shares of the cross-block sums are register-tiled (4 x 4 outputs a thread, the rows of
+// the slice split over thread groups) and summed in a fixed order in shared memory, then added
+// with vector FP32 atomics into kCopies copies (block b into copy b % kCopies); readers sum the
+// copies in a fixed order through L2. The order of the atomics within a copy varies from run to
+// run, so results can differ in the last bits between runs.
 //
 // Error monitor (no read of X): after the last iteration the kernel leaves in mon[0] the cross
 // term <W_tld^T X_hat, H> and in mon[1] the quadratic term <W^T W, H H^T>; with ||X||^2 they give
@@ -40,12 +42,10 @@
 namespace nmfrp {
 namespace {
 
-constexpr int kPT = 768;          // threads per block (one block per SM, 85 registers a thread)
-constexpr int kGA = 4;            // lanes per row of W
-constexpr int kGB = 16;           // lanes per column of H
-constexpr int kMaxRows = kPT / kGA;   // rows of W per block
-constexpr int kMaxCols = kPT / kGB;   // columns of H per block
-constexpr int kCopies = 8;        // copies of each cross-block sum
+constexpr int kNT = 512;          // threads per block (one block per SM)
+constexpr int kGA = 2;            // lanes per row of W
+constexpr int kGB = 4;            // lanes per column of H
+constexpr int kCopies = 4;        // copies of each cross-block sum
 constexpr long long kWaitCycles = 4000000000LL;   // about two seconds of polling
 
 struct Barrier {
@@ -94,6 +94,17 @@ __device__ bool grid_sync(Barrier* bar, unsigned nblocks, int* status, int* abor
 __device__ __forceinline__ float posp(float v) { return v > 0.f ? v : 0.f; }
 __device__ __forceinline__ float negp(float v) { return v < 0.f ? -v : 0.f; }
 
+// ell padded to a multiple of 4, and the row stride of staged rows (a multiple of 4 whose
+// quarter is odd: rows read as float4 by consecutive threads hit distinct banks).
+__host__ __device__ __forceinline__ int lq_of(int ell) { return (ell + 3) & ~3; }
+__host__ __device__ __forceinline__ int lsx_of(int ell) {
+  const int s = lq_of(ell);
+  return ((s / 4) % 2 == 0) ? s + 4 : s;
+}
+// cross-block sum sizes: phase A [LQ + RP][RP]; phase B [RP][LQ + RP] + cross (padded to 4)
+__host__ __device__ __forceinline__ int ea_size(int RP, int LQ) { return (LQ + RP) * RP; }
+__host__ __device__ __forceinline__ int eb_size(int RP, int LQ) { return RP * (LQ + RP) + 4; }
+
 struct PArgs {
   int64_t m, n;
   int r, ell, iters, rule;
@@ -105,8 +116,8 @@ struct PArgs {
   const float* Xchk;
   float* W;
   float* H;
-  float* accA;    // [2][kCopies][EA]: phase-A sums (W_tld_raw, W^T W)
-  float* accB;    // [2][kCopies][EB]: phase-B sums (H_tld, H H^T, cross)
+  float* accA;    // [2][kCopies][EA]
+  float* accB;    // [2][kCopies][EB]
   float* mon;     // [2]: cross term and quadratic term of the last iteration
   const int* done;
   Barrier* bar;
@@ -114,13 +125,7 @@ struct PArgs {
   int* abort_flag;
 };
 
-// Phase-A entries: W_tld_raw (ell x r) then W^T W (r x r). Phase-B entries: H_tld (r x ell),
-// H H^T (r x r), cross (1).
-__host__ __device__ __forceinline__ int ea_size(int r, int ell) { return ell * r + r * r; }
-__host__ __device__ __forceinline__ int eb_size(int r, int ell) { return r * ell + r * r + 1; }
-
-// Fixed-order sum of the kCopies copies of entry e, read through L2 (the copies are written by
-// other blocks' atomics).
+// Fixed-order sum of the kCopies copies of entry e, read through L2.
 __device__ __forceinline__ float acc_read(const float* base, int E, int e) {
   float v[kCopies];
 #pragma unroll
@@ -131,333 +136,349 @@ __device__ __forceinline__ float acc_read(const float* base, int E, int e) {
   return s;
 }
 
-// CA components per lane in phase A (RP = kGA * CA), CB_ per lane in phase B (kGB * CB_ >= RP).
-template <int CA, int CB_, int RULE>
-__global__ void __launch_bounds__(kPT, 1) iterate_persistent_kernel(PArgs a) {
-  constexpr int RP = kGA * CA;
-  constexpr int RPB = kGB * CB_;
-  static_assert(RPB >= RP, "phase B must cover the components of phase A");
+// out[a][b] += sum_{i < K} A_i[a] B_i[b] (a < NA, b < NB, both multiples of 4), added with vector
+// atomics into `dst` (row-major NA x NB). Row i of A is A1[i * lda1 + a] for a < NA1 and
+// A2[i * lda2 + a - NA1] beyond; B likewise with NB1. `red` holds kNT * 16 floats.
+__device__ void block_share(int K, int NA, int NB, const float* A1, int lda1, const float* A2,
+                            int lda2, int NA1, const float* B1, int ldb1, const float* B2,
+                            int ldb2, int NB1, float* red, float* dst) {
+  const int t = threadIdx.x;
+  const int tb = NB / 4, tiles = (NA / 4) * tb;
+  int ks = kNT / tiles;
+  if (ks < 1) ks = 1;
+  const int chunk = (K + ks - 1) / ks;
+  for (int u = t; u < tiles * ks; u += kNT) {
+    const int tile = u % tiles, kk = u / tiles;
+    const int a0 = 4 * (tile / tb), b0 = 4 * (tile % tb);
+    const float* pa = a0 < NA1 ? A1 + a0 : A2 + (a0 - NA1);
+    const float* pb = b0 < NB1 ? B1 + b0 : B2 + (b0 - NB1);
+    const int lda = a0 < NA1 ? lda1 : lda2, ldb = b0 < NB1 ? ldb1 : ldb2;
+    float acc[4][4];
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) acc[x][y] = 0.f;
+    const int i1 = min(K, (kk + 1) * chunk);
+#pragma unroll 2
+    for (int i = kk * chunk; i < i1; ++i) {
+      const float4 av = *reinterpret_cast<const float4*>(pa + i * lda);
+      const float4 bv = *reinterpret_cast<const float4*>(pb + i * ldb);
+      const float aa[4] = {av.x, av.y, av.z, av.w};
+      const float bb[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(aa[x], bb[y], acc[x][y]);
+    }
+    float* rp = red + (static_cast<size_t>(kk) * NA + a0) * NB + b0;
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+      *reinterpret_cast<float4*>(rp + x * NB) = make_float4(acc[x][0], acc[x][1], acc[x][2], acc[x][3]);
+  }
+  __syncthreads();
+  const int q4 = NA * NB / 4;
+  for (int q = t; q < q4; q += kNT) {
+    float4 s = *reinterpret_cast<const float4*>(red + 4 * q);
+    for (int kk = 1; kk < ks; ++kk) {
+      const float4 v = *reinterpret_cast<const float4*>(red + static_cast<size_t>(kk) * NA * NB + 4 * q);
+      s.x += v.x;
+      s.y += v.y;
+      s.z += v.z;
+      s.w += v.w;
+    }
+    atomicAdd(reinterpret_cast<float4*>(dst + 4 * q), s);
+  }
+}
+
+// G[p][q] = sum_k T[k][p] T[k][q] (RP x RP) from T (LQ x RP), 2 x 2 outputs a thread.
+template <int RP>
+__device__ __forceinline__ void gram_rp(const float* T, int LQ, float* G) {
+  constexpr int H2 = RP / 2;
+  for (int u = threadIdx.x; u < H2 * H2; u += kNT) {
+    const int p0 = 2 * (u / H2), q0 = 2 * (u % H2);
+    float g00 = 0.f, g01 = 0.f, g10 = 0.f, g11 = 0.f;
+#pragma unroll 4
+    for (int k = 0; k < LQ; ++k) {
+      const float2 a = *reinterpret_cast<const float2*>(T + k * RP + p0);
+      const float2 b = *reinterpret_cast<const float2*>(T + k * RP + q0);
+      g00 = fmaf(a.x, b.x, g00);
+      g01 = fmaf(a.x, b.y, g01);
+      g10 = fmaf(a.y, b.x, g10);
+      g11 = fmaf(a.y, b.y, g11);
+    }
+    G[p0 * RP + q0] = g00;
+    G[p0 * RP + q0 + 1] = g01;
+    G[(p0 + 1) * RP + q0] = g10;
+    G[(p0 + 1) * RP + q0 + 1] = g11;
+  }
+}
+
+// C consecutive floats from shared memory (C a multiple of 2; float4 where it can).
+template <int C>
+__device__ __forceinline__ void ld_run(const float* p, float* v) {
+  if constexpr (C % 4 == 0) {
+#pragma unroll
+    for (int c = 0; c < C; c += 4) {
+      const float4 x = *reinterpret_cast<const float4*>(p + c);
+      v[c] = x.x;
+      v[c + 1] = x.y;
+      v[c + 2] = x.z;
+      v[c + 3] = x.w;
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < C; c += 2) {
+      const float2 x = *reinterpret_cast<const float2*>(p + c);
+      v[c] = x.x;
+      v[c + 1] = x.y;
+    }
+  }
+}
+
+// One group of NG lanes updates one factor vector v (RP components, lane g owning
+// [g C, g C + C)) given its cross product s (S_j for the owned j), the Gram G (RP x RP, shared
+// memory) and the rule. For FastHALS-RP on H (reg = true) the Section 4.1 alpha / beta form is
+// used. Components j >= r are zero on entry and stay zero.
+template <int RP, int NG, int RULE>
+__device__ __forceinline__ void update_vec(float* v, float* s, const float* G, int g, int r,
+                                           bool reg, float alpha, float beta, float eps) {
+  constexpr int C = RP / NG;
+  const unsigned full = 0xffffffffu;
+  if (RULE == 0) {
+    // t_j = S_j - sum_q v_q G[q][j]
+#pragma unroll 1
+    for (int o = 0; o < NG; ++o) {
+#pragma unroll
+      for (int cq = 0; cq < C; ++cq) {
+        const float vq = __shfl_sync(full, v[cq], o, NG);
+        float gr[C];
+        ld_run<C>(G + (o * C + cq) * RP + g * C, gr);
+#pragma unroll
+        for (int c = 0; c < C; ++c) s[c] = fmaf(-vq, gr[c], s[c]);
+      }
+    }
+#pragma unroll 1
+    for (int o = 0; o < NG; ++o) {
+#pragma unroll
+      for (int cj = 0; cj < C; ++cj) {
+        const int j = o * C + cj;
+        float d = 0.f;
+        if (g == o && j < r) {
+          const float gjj = G[j * RP + j];
+          float vn = v[cj];
+          if (!reg) {
+            if (gjj > 0.f) vn = fmaxf(0.f, fmaf(s[cj], 1.f / gjj, v[cj]));
+          } else if (gjj + beta > 0.f) {
+            vn = fmaxf(0.f, (fmaf(v[cj], gjj, s[cj]) - alpha) / (gjj + beta));
+          }
+          d = vn - v[cj];
+          v[cj] = vn;
+        }
+        d = __shfl_sync(full, d, o, NG);
+        float gr[C];
+        ld_run<C>(G + j * RP + g * C, gr);
+#pragma unroll
+        for (int c = 0; c < C; ++c) s[c] = fmaf(-d, gr[c], s[c]);
+      }
+    }
+  } else {
+    float num[C], den[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      num[c] = posp(s[c]);
+      den[c] = negp(s[c]) + eps;
+    }
+#pragma unroll 1
+    for (int o = 0; o < NG; ++o) {
+#pragma unroll
+      for (int cq = 0; cq < C; ++cq) {
+        const float vq = __shfl_sync(full, v[cq], o, NG);
+        float gr[C];
+        ld_run<C>(G + (o * C + cq) * RP + g * C, gr);
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          num[c] = fmaf(vq, negp(gr[c]), num[c]);
+          den[c] = fmaf(vq, posp(gr[c]), den[c]);
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < C; ++c) v[c] = (g * C + c < r) ? v[c] * sqrtf(num[c] / den[c]) : 0.f;
+  }
+}
+
+template <int RP, int RULE>
+__global__ void __launch_bounds__(kNT, 1) iterate_persistent_kernel(PArgs a) {
+  constexpr int CA = RP / kGA, CBn = RP / kGB;
   extern __shared__ __align__(16) float sh[];
   const int r = a.r, ell = a.ell, t = threadIdx.x;
-  const int EA = ea_size(r, ell), EB = eb_size(r, ell);
-  const int LS = ell | 1;                // odd stride of staged rows (conflict-free reads)
-  float* HtT = sh;                       // [ell][RPB]  H_tld^T
-  float* Gw = HtT + ell * RPB;           // [RPB][RPB]
-  float* WtS = Gw + RPB * RPB;           // [ell][RPB]  W_tld (normalised)
-  float* Gh = WtS + ell * RPB;           // [RPB][RPB]
-  float* sc = Gh + RPB * RPB;            // [RPB]       s_j of the last W phase
-  float* inv = sc + RPB;                 // [RPB]       1 / G_jj of the current phase
-  float* stA = inv + RPB;                // [kMaxRows][RP]  rows of W, later columns of H
-  float* stX = stA + kMaxRows * RPB;     // [RB][LS]    rows of X_chk
-  float* stB = stX + a.RB * LS;          // [RB][LS]    rows of Q_L
-  float* stX2 = stB + a.RB * LS;         // [CB][LS]    columns of X_hat
-  float* stB2 = stX2 + a.CB * LS;        // [CB][LS]    rows of Q_R
-  __shared__ float red[kPT / 32];
+  const int LQ = lq_of(ell), LS = lsx_of(ell);
+  const int EA = ea_size(RP, LQ), EB = eb_size(RP, LQ);
+  const int RB = a.RB, CB = a.CB;
+  float* HtT = sh;                  // [LQ][RP]   H_tld^T
+  float* Gw = HtT + LQ * RP;        // [RP][RP]
+  float* WtS = Gw + RP * RP;        // [LQ][RP]   W_tld (normalised)
+  float* Gh = WtS + LQ * RP;        // [RP][RP]
+  float* sc = Gh + RP * RP;         // [RP]       s_j of the last W phase
+  float* Ws = sc + RP;              // [RB][RP]   rows of W (unnormalised)
+  float* Hs = Ws + RB * RP;         // [CB][RP]   columns of H
+  float* Xc = Hs + CB * RP;         // [RB][LS]   rows of X_chk
+  float* Ql = Xc + RB * LS;         // [RB][LS]   rows of Q_L
+  float* Xh = Ql + RB * LS;         // [CB][LS]   columns of X_hat
+  float* Qr = Xh + CB * LS;         // [CB][LS]   rows of Q_R
+  float* red = Qr + CB * LS;        // [kNT * 16] block-share scratch
+  __shared__ float wred[kNT / 32];
   const unsigned G = gridDim.x;
-  const int64_t rb = (a.m + G - 1) / G, cbk = (a.n + G - 1) / G;
-  const int64_t r0 = blockIdx.x * rb, r1 = min(a.m, r0 + rb);
-  const int64_t c0 = blockIdx.x * cbk, c1 = min(a.n, c0 + cbk);
-  const int nrows = r1 > r0 ? static_cast<int>(r1 - r0) : 0;
-  const int ncols = c1 > c0 ? static_cast<int>(c1 - c0) : 0;
+  const int64_t r0 = static_cast<int64_t>(blockIdx.x) * RB, c0 = static_cast<int64_t>(blockIdx.x) * CB;
+  const int nrows = r0 < a.m ? static_cast<int>(a.m - r0 < RB ? a.m - r0 : RB) : 0;
+  const int ncols = c0 < a.n ? static_cast<int>(a.n - c0 < CB ? a.n - c0 : CB) : 0;
   const bool normalize = (RULE == 0);
-  const bool plain = (a.alpha == 0.f && a.beta == 0.f);
+  const bool reg = !(a.alpha == 0.f && a.beta == 0.f);
 
   if (*reinterpret_cast<const volatile int*>(a.done)) return;   // the solve has converged
 
-  for (int j = t; j < RPB; j += kPT) sc[j] = 1.f;
-
-  // phase-A role: row slot ra (row r0 + ra), lane ga in its group; phase-B role: column slot cb
-  const int ra = t / kGA, ga = t % kGA;
-  const int cb = t / kGB, gb = t % kGB;
-  const bool has_row = ra < nrows, has_col = cb < ncols;
-  const int64_t myrow = r0 + ra, mycol = c0 + cb;
-  float w[CA], h[CB_];
-#pragma unroll
-  for (int c = 0; c < CA; ++c) {
-    const int j = ga + kGA * c;
-    w[c] = (has_row && j < r) ? a.W[myrow * r + j] : 0.f;
+  // ---- stage the slice (zero-padded) and the factors
+  for (int j = t; j < RP; j += kNT) sc[j] = 1.f;
+  for (int e = t; e < RB * RP; e += kNT) {
+    const int i = e / RP, j = e - i * RP;
+    Ws[e] = (i < nrows && j < r) ? a.W[(r0 + i) * r + j] : 0.f;
   }
-#pragma unroll
-  for (int c = 0; c < CB_; ++c) {
-    const int j = gb + kGB * c;
-    h[c] = (has_col && j < r) ? a.H[j * a.n + mycol] : 0.f;
+  for (int e = t; e < CB * RP; e += kNT) {
+    const int c = e / RP, j = e - c * RP;
+    Hs[e] = (c < ncols && j < r) ? a.H[static_cast<int64_t>(j) * a.n + c0 + c] : 0.f;
   }
-  for (int e = t; e < a.RB * ell; e += kPT) {
-    const int i = e / ell, k = e - i * ell;
-    const bool in = i < nrows;
-    stX[i * LS + k] = in ? a.Xchk[(r0 + i) * ell + k] : 0.f;
-    stB[i * LS + k] = in ? a.QL[(r0 + i) * ell + k] : 0.f;
+  for (int e = t; e < RB * LS; e += kNT) {
+    const int i = e / LS, k = e - i * LS;
+    const bool in = i < nrows && k < ell;
+    Xc[e] = in ? a.Xchk[(r0 + i) * ell + k] : 0.f;
+    Ql[e] = in ? a.QL[(r0 + i) * ell + k] : 0.f;
   }
-  for (int e = t; e < a.CB * ell; e += kPT) {
-    const int cI = e / ell, k = e - cI * ell;
-    const bool in = cI < ncols;
-    stX2[cI * LS + k] = in ? a.Xhat[k * a.n + c0 + cI] : 0.f;
-    stB2[cI * LS + k] = in ? a.QR[(c0 + cI) * ell + k] : 0.f;
+  for (int e = t; e < CB * LS; e += kNT) {
+    const int c = e / LS, k = e - c * LS;
+    const bool in = c < ncols && k < ell;
+    Xh[e] = in ? a.Xhat[static_cast<int64_t>(k) * a.n + c0 + c] : 0.f;
+    Qr[e] = in ? a.QR[(c0 + c) * ell + k] : 0.f;
   }
-
-  // phase-B block sums: H_tld (staged columns of H in stA x rows of Q_R), H H^T, cross term
-  auto add_b = [&](float* dst, float cross) {
-    for (int e = t; e < r * ell; e += kPT) {
-      const int j = e / ell, k = e - j * ell;
-      float v = 0.f;
-      for (int q = 0; q < ncols; ++q) v = fmaf(stA[q * RPB + j], stB2[q * LS + k], v);
-      atomicAdd(&dst[e], v);
-    }
-    for (int e = t; e < r * r; e += kPT) {
-      const int p = e / r, q2 = e - p * r;
-      float v = 0.f;
-      for (int q = 0; q < ncols; ++q) v = fmaf(stA[q * RPB + p], stA[q * RPB + q2], v);
-      atomicAdd(&dst[r * ell + e], v);
-    }
-    if (t == 0) atomicAdd(&dst[r * ell + r * r], cross);
-  };
-  // stage this thread's components of its column of H
-  auto stage_h = [&]() {
-    if (has_col) {
-#pragma unroll
-      for (int c = 0; c < CB_; ++c) stA[cb * RPB + gb + kGB * c] = h[c];
-    }
-  };
-
+  __syncthreads();
   // prologue: H_tld, H H^T of the initial H into accB[1]
-  for (int e = t; e < kMaxRows * RPB; e += kPT) stA[e] = 0.f;
-  __syncthreads();
-  stage_h();
-  __syncthreads();
-  add_b(a.accB + (1 * kCopies + blockIdx.x % kCopies) * EB, 0.f);
+  block_share(CB, RP, LQ + RP, Hs, RP, Hs, RP, RP, Qr, LS, Hs, RP, LQ, red,
+              a.accB + (1 * kCopies + blockIdx.x % kCopies) * EB);
   if (!grid_sync(a.bar, G, a.status, a.abort_flag)) return;
 
   for (int it = 0; it < a.iters; ++it) {
     const int ph = it & 1, pr = ph ^ 1;
-    float* accA_w = a.accA + (ph * kCopies + blockIdx.x % kCopies) * EA;
-    const float* accB_r = a.accB + pr * kCopies * EB;
-    // ---------------- phase A: rows of W
-    // clear the phase-A sums written two phases ago (already read), a slice per block
-    for (int64_t e = static_cast<int64_t>(blockIdx.x) * kPT + t; e < kCopies * EA;
-         e += static_cast<int64_t>(G) * kPT)
+    // ================= phase A: rows of W
+    for (int64_t e = static_cast<int64_t>(blockIdx.x) * kNT + t; e < kCopies * EA;
+         e += static_cast<int64_t>(G) * kNT)
       a.accA[pr * kCopies * EA + e] = 0.f;
-    for (int e = t; e < ell * RPB; e += kPT) {
-      const int k = e / RPB, j = e - k * RPB;
-      HtT[e] = (j < r) ? acc_read(accB_r, EB, j * ell + k) : 0.f;
-    }
-    __syncthreads();
-    for (int e = t; e < RPB * RPB; e += kPT) {
-      const int p = e / RPB, q = e - p * RPB;
-      float g = 0.f;
-      if (p < r && q < r)
-        for (int k = 0; k < ell; ++k) g = fmaf(HtT[k * RPB + p], HtT[k * RPB + q], g);
-      Gw[e] = g;
-      if (p == q) inv[p] = g > 0.f ? 1.f / g : 0.f;
-    }
-    __syncthreads();
     {
-      float s[CA];
+      const float* accB_r = a.accB + pr * kCopies * EB;
+      for (int e = t; e < RP * LQ; e += kNT) {
+        const int j = e / LQ, k = e - j * LQ;
+        HtT[k * RP + j] = acc_read(accB_r, EB, j * (LQ + RP) + k);
+      }
+    }
+    __syncthreads();
+    gram_rp<RP>(HtT, LQ, Gw);
+    __syncthreads();
+    for (int slot = t / kGA; slot < ((nrows + 31) & ~31); slot += kNT / kGA) {
+      // whole warps take part in the shuffles; rows past the slice compute on zeros
+      const int g = t % kGA;
+      const int i = slot < RB ? slot : RB - 1;
+      float w[CA], s[CA];
+      ld_run<CA>(Ws + i * RP + g * CA, w);
 #pragma unroll
       for (int c = 0; c < CA; ++c) {
-        w[c] = w[c] / sc[ga + kGA * c];   // normalisation of the previous W phase (1 for MU)
+        w[c] = w[c] / sc[g * CA + c];   // normalisation of the previous W phase (1 for MU)
         s[c] = 0.f;
       }
-      const float* xr = stX + (has_row ? ra : 0) * LS;
-      for (int k = 0; k < ell; ++k) {
-        const float xk = xr[k];
+      const float* xr = Xc + i * LS;
+      for (int k = 0; k < LQ; k += 4) {
+        const float4 x4 = *reinterpret_cast<const float4*>(xr + k);
+        const float xk[4] = {x4.x, x4.y, x4.z, x4.w};
 #pragma unroll
-        for (int c = 0; c < CA; ++c) s[c] = fmaf(xk, HtT[k * RPB + ga + kGA * c], s[c]);
+        for (int q = 0; q < 4; ++q) {
+          float hr[CA];
+          ld_run<CA>(HtT + (k + q) * RP + g * CA, hr);
+#pragma unroll
+          for (int c = 0; c < CA; ++c) s[c] = fmaf(xk[q], hr[c], s[c]);
+        }
       }
-      if (RULE == 0) {
-        // t_j = S_j - sum_q w_q G_qj with w_q gathered from the group
-        // j = kGA * cj + o: the slot cj is unrolled (register index), the owner lane o is not
+      update_vec<RP, kGA, RULE>(w, s, Gw, g, r, false, 0.f, 0.f, a.eps);
+      if (slot < nrows) {
 #pragma unroll
-        for (int cq = 0; cq < CA; ++cq) {
-#pragma unroll 1
-          for (int o = 0; o < kGA; ++o) {
-            const int q = kGA * cq + o;
-            const float wq = __shfl_sync(0xffffffffu, w[cq], o, kGA);
-#pragma unroll
-            for (int c = 0; c < CA; ++c) s[c] = fmaf(-wq, Gw[q * RPB + ga + kGA * c], s[c]);
-          }
-        }
-#pragma unroll
-        for (int cj = 0; cj < CA; ++cj) {
-#pragma unroll 1
-          for (int o = 0; o < kGA; ++o) {
-            const int j = kGA * cj + o;
-            float d = 0.f;
-            if (ga == o && j < r && Gw[j * RPB + j] > 0.f) {
-              const float wn = fmaxf(0.f, w[cj] + s[cj] * inv[j]);
-              d = wn - w[cj];
-              w[cj] = wn;
-            }
-            d = __shfl_sync(0xffffffffu, d, o, kGA);
-#pragma unroll
-            for (int c = 0; c < CA; ++c)
-              if (ga + kGA * c > j) s[c] = fmaf(-d, Gw[j * RPB + ga + kGA * c], s[c]);
-          }
-        }
-      } else {
-        float num[CA], den[CA];
-#pragma unroll
-        for (int c = 0; c < CA; ++c) {
-          num[c] = posp(s[c]);
-          den[c] = negp(s[c]) + a.eps;
-        }
-#pragma unroll
-        for (int cq = 0; cq < CA; ++cq) {
-#pragma unroll 1
-          for (int o = 0; o < kGA; ++o) {
-            const int q = kGA * cq + o;
-            const float wq = __shfl_sync(0xffffffffu, w[cq], o, kGA);
-#pragma unroll
-            for (int c = 0; c < CA; ++c) {
-              const float gq = Gw[q * RPB + ga + kGA * c];
-              num[c] = fmaf(wq, negp(gq), num[c]);
-              den[c] = fmaf(wq, posp(gq), den[c]);
-            }
-          }
-        }
-#pragma unroll
-        for (int c = 0; c < CA; ++c)
-          w[c] = (ga + kGA * c < r) ? w[c] * sqrtf(num[c] / den[c]) : 0.f;
-      }
-      if (!has_row) {
-#pragma unroll
-        for (int c = 0; c < CA; ++c) w[c] = 0.f;
-      }
-      if (ra < kMaxRows) {
-#pragma unroll
-        for (int c = 0; c < CA; ++c) stA[ra * RPB + ga + kGA * c] = w[c];
+        for (int c = 0; c < CA; c += 2)
+          *reinterpret_cast<float2*>(Ws + i * RP + g * CA + c) = make_float2(w[c], w[c + 1]);
       }
     }
     __syncthreads();
-    for (int e = t; e < ell * r; e += kPT) {
-      const int k = e / r, j = e - k * r;
-      float v = 0.f;
-      for (int q = 0; q < nrows; ++q) v = fmaf(stB[q * LS + k], stA[q * RPB + j], v);
-      atomicAdd(&accA_w[e], v);
-    }
-    for (int e = t; e < r * r; e += kPT) {
-      const int p = e / r, q2 = e - p * r;
-      float v = 0.f;
-      for (int q = 0; q < nrows; ++q) v = fmaf(stA[q * RPB + p], stA[q * RPB + q2], v);
-      atomicAdd(&accA_w[ell * r + e], v);
-    }
+    // [Q_L | W]^T W over the slice
+    block_share(RB, LQ + RP, RP, Ql, LS, Ws, RP, LQ, Ws, RP, Ws, RP, RP, red,
+                a.accA + (ph * kCopies + blockIdx.x % kCopies) * EA);
     if (!grid_sync(a.bar, G, a.status, a.abort_flag)) return;
 
-    // ---------------- phase B: columns of H
-    const float* accA_r = a.accA + ph * kCopies * EA;
-    float* accB_w = a.accB + (ph * kCopies + blockIdx.x % kCopies) * EB;
-    for (int64_t e = static_cast<int64_t>(blockIdx.x) * kPT + t; e < kCopies * EB;
-         e += static_cast<int64_t>(G) * kPT)
+    // ================= phase B: columns of H
+    for (int64_t e = static_cast<int64_t>(blockIdx.x) * kNT + t; e < kCopies * EB;
+         e += static_cast<int64_t>(G) * kNT)
       a.accB[pr * kCopies * EB + e] = 0.f;
-    for (int j = t; j < RPB; j += kPT) {
-      const float c2 = (j < r) ? acc_read(accA_r, EA, ell * r + j * r + j) : 0.f;
-      sc[j] = (normalize && j < r && c2 > 0.f) ? sqrtf(c2) : 1.f;
+    {
+      const float* accA_r = a.accA + ph * kCopies * EA;
+      for (int j = t; j < RP; j += kNT) {
+        const float c2 = acc_read(accA_r, EA, (LQ + j) * RP + j);
+        sc[j] = (normalize && j < r && c2 > 0.f) ? sqrtf(c2) : 1.f;
+      }
+      __syncthreads();
+      for (int e = t; e < LQ * RP; e += kNT) WtS[e] = acc_read(accA_r, EA, e) / sc[e % RP];
     }
     __syncthreads();
-    for (int e = t; e < ell * RPB; e += kPT) {
-      const int k = e / RPB, j = e - k * RPB;
-      WtS[e] = (j < r) ? acc_read(accA_r, EA, k * r + j) / sc[j] : 0.f;
-    }
-    __syncthreads();
-    for (int e = t; e < RPB * RPB; e += kPT) {
-      const int p = e / RPB, q = e - p * RPB;
-      float g = 0.f;
-      if (p < r && q < r)
-        for (int k = 0; k < ell; ++k) g = fmaf(WtS[k * RPB + p], WtS[k * RPB + q], g);
-      Gh[e] = g;
-      if (p == q) inv[p] = g > 0.f ? 1.f / g : 0.f;
-    }
+    gram_rp<RP>(WtS, LQ, Gh);
     __syncthreads();
     float cross = 0.f;
-    {
-      float s[CB_], shc[CB_];
+    for (int slot = t / kGB; slot < ((ncols + 7) & ~7); slot += kNT / kGB) {
+      const int g = t % kGB;
+      const int c = slot < CB ? slot : CB - 1;
+      float h[CBn], s[CBn];
+      ld_run<CBn>(Hs + c * RP + g * CBn, h);
 #pragma unroll
-      for (int c = 0; c < CB_; ++c) {
-        h[c] *= sc[gb + kGB * c];
-        s[c] = 0.f;
+      for (int q = 0; q < CBn; ++q) {
+        h[q] *= sc[g * CBn + q];
+        s[q] = 0.f;
       }
-      const float* xc = stX2 + (has_col ? cb : 0) * LS;
-      for (int k = 0; k < ell; ++k) {
-        const float xk = xc[k];
+      const float* xc = Xh + c * LS;
+      for (int k = 0; k < LQ; k += 4) {
+        const float4 x4 = *reinterpret_cast<const float4*>(xc + k);
+        const float xk[4] = {x4.x, x4.y, x4.z, x4.w};
 #pragma unroll
-        for (int c = 0; c < CB_; ++c) s[c] = fmaf(xk, WtS[k * RPB + gb + kGB * c], s[c]);
+        for (int q = 0; q < 4; ++q) {
+          float wr[CBn];
+          ld_run<CBn>(WtS + (k + q) * RP + g * CBn, wr);
+#pragma unroll
+          for (int z = 0; z < CBn; ++z) s[z] = fmaf(xk[q], wr[z], s[z]);
+        }
       }
+      float shc[CBn];
 #pragma unroll
-      for (int c = 0; c < CB_; ++c) shc[c] = s[c];   // S_H column for the monitor
-      if (RULE == 0) {
+      for (int z = 0; z < CBn; ++z) shc[z] = s[z];   // S_H column for the monitor
+      update_vec<RP, kGB, RULE>(h, s, Gh, g, r, RULE == 0 && reg, a.alpha, a.beta, a.eps);
+      if (slot < ncols) {
 #pragma unroll
-        for (int cq = 0; cq < CB_; ++cq) {
-#pragma unroll 1
-          for (int o = 0; o < kGB; ++o) {
-            const int q = kGB * cq + o;
-            const float hq = __shfl_sync(0xffffffffu, h[cq], o, kGB);
+        for (int z = 0; z < CBn; ++z) cross = fmaf(shc[z], h[z], cross);
 #pragma unroll
-            for (int c = 0; c < CB_; ++c) s[c] = fmaf(-Gh[q * RPB + gb + kGB * c], hq, s[c]);
-          }
-        }
-#pragma unroll
-        for (int cj = 0; cj < CB_; ++cj) {
-#pragma unroll 1
-          for (int o = 0; o < kGB; ++o) {
-          const int j = kGB * cj + o;
-          float d = 0.f;
-          if (gb == o && j < r) {
-            const float g = Gh[j * RPB + j];
-            float hn = h[cj];
-            if (plain) {
-              if (g > 0.f) hn = fmaxf(0.f, h[cj] + s[cj] * inv[j]);
-            } else if (g + a.beta > 0.f) {
-              hn = fmaxf(0.f, (fmaf(h[cj], g, s[cj]) - a.alpha) / (g + a.beta));
-            }
-            d = hn - h[cj];
-            h[cj] = hn;
-          }
-          d = __shfl_sync(0xffffffffu, d, o, kGB);
-#pragma unroll
-          for (int c = 0; c < CB_; ++c)
-            if (gb + kGB * c > j) s[c] = fmaf(-d, Gh[j * RPB + gb + kGB * c], s[c]);
-          }
-        }
-      } else {
-        float num[CB_], den[CB_];
-#pragma unroll
-        for (int c = 0; c < CB_; ++c) {
-          num[c] = posp(s[c]);
-          den[c] = negp(s[c]) + a.eps;
-        }
-#pragma unroll
-        for (int cq = 0; cq < CB_; ++cq) {
-#pragma unroll 1
-          for (int o = 0; o < kGB; ++o) {
-            const int q = kGB * cq + o;
-            const float hq = __shfl_sync(0xffffffffu, h[cq], o, kGB);
-#pragma unroll
-            for (int c = 0; c < CB_; ++c) {
-              const float gq = Gh[q * RPB + gb + kGB * c];
-              num[c] = fmaf(negp(gq), hq, num[c]);
-              den[c] = fmaf(posp(gq), hq, den[c]);
-            }
-          }
-        }
-#pragma unroll
-        for (int c = 0; c < CB_; ++c)
-          h[c] = (gb + kGB * c < r) ? h[c] * sqrtf(num[c] / den[c]) : 0.f;
+        for (int z = 0; z < CBn; z += 2)
+          *reinterpret_cast<float2*>(Hs + c * RP + g * CBn + z) = make_float2(h[z], h[z + 1]);
       }
-      if (!has_col) {
-#pragma unroll
-        for (int c = 0; c < CB_; ++c) h[c] = 0.f;
-      }
-#pragma unroll
-      for (int c = 0; c < CB_; ++c) cross = fmaf(shc[c], h[c], cross);
     }
-    stage_h();
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) cross += __shfl_xor_sync(0xffffffffu, cross, o);
-    if ((t & 31) == 0) red[t >> 5] = cross;
+    if ((t & 31) == 0) wred[t >> 5] = cross;
     __syncthreads();
-    float csum = 0.f;
-    if (t == 0)
-      for (int wI = 0; wI < kPT / 32; ++wI) csum += red[wI];
-    add_b(accB_w, csum);
+    float* accB_w = a.accB + (ph * kCopies + blockIdx.x % kCopies) * EB;
+    block_share(CB, RP, LQ + RP, Hs, RP, Hs, RP, RP, Qr, LS, Hs, RP, LQ, red, accB_w);
+    if (t == 0) {
+      float csum = 0.f;
+      for (int wI = 0; wI < kNT / 32; ++wI) csum += wred[wI];
+      atomicAdd(&accB_w[RP * (LQ + RP)], csum);
+    }
     if (!grid_sync(a.bar, G, a.status, a.abort_flag)) return;
   }
   // the last iteration's monitor terms: cross, and <W^T W, H H^T> for the normalised W
@@ -466,58 +487,57 @@ __global__ void __launch_bounds__(kPT, 1) iterate_persistent_kernel(PArgs a) {
     const float* accA_r = a.accA + ph * kCopies * EA;
     const float* accB_r = a.accB + ph * kCopies * EB;
     float q2 = 0.f;
-    for (int e = t; e < r * r; e += kPT) {
-      const int p = e / r, q = e - p * r;
-      const float gww = acc_read(accA_r, EA, ell * r + e) / (sc[p] * sc[q]);
-      q2 = fmaf(gww, acc_read(accB_r, EB, r * ell + e), q2);
+    for (int e = t; e < RP * RP; e += kNT) {
+      const int p = e / RP, q = e - p * RP;
+      const float gww = acc_read(accA_r, EA, (LQ + p) * RP + q) / (sc[p] * sc[q]);
+      q2 = fmaf(gww, acc_read(accB_r, EB, p * (LQ + RP) + LQ + q), q2);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) q2 += __shfl_xor_sync(0xffffffffu, q2, o);
-    if ((t & 31) == 0) red[t >> 5] = q2;
+    if ((t & 31) == 0) wred[t >> 5] = q2;
     __syncthreads();
     if (t == 0) {
       float s = 0.f;
-      for (int wI = 0; wI < kPT / 32; ++wI) s += red[wI];
-      a.mon[0] = acc_read(accB_r, EB, r * ell + r * r);
+      for (int wI = 0; wI < kNT / 32; ++wI) s += wred[wI];
+      a.mon[0] = acc_read(accB_r, EB, RP * (LQ + RP));
       a.mon[1] = s;
     }
   }
   // write back: W normalised by the last s_j, H
   if (a.iters > 0) {
-    if (has_row)
-#pragma unroll
-      for (int c = 0; c < CA; ++c) {
-        const int j = ga + kGA * c;
-        if (j < r) a.W[myrow * r + j] = normalize ? w[c] / sc[j] : w[c];
-      }
-    if (has_col)
-#pragma unroll
-      for (int c = 0; c < CB_; ++c) {
-        const int j = gb + kGB * c;
-        if (j < r) a.H[j * a.n + mycol] = h[c];
-      }
+    for (int e = t; e < nrows * r; e += kNT) {
+      const int i = e / r, j = e - i * r;
+      const float v = Ws[i * RP + j];
+      a.W[(r0 + i) * r + j] = normalize ? v / sc[j] : v;
+    }
+    for (int e = t; e < ncols * r; e += kNT) {
+      const int j = e / ncols, c = e - j * ncols;
+      a.H[static_cast<int64_t>(j) * a.n + c0 + c] = Hs[c * RP + j];
+    }
   }
 }
 
-size_t smem_for(int RPB, int ell, int RB, int CB) {
-  const int LS = ell | 1;
-  return sizeof(float) * (2 * ell * RPB + 2 * RPB * RPB + 2 * RPB + kMaxRows * RPB +
-                          static_cast<size_t>(2 * RB + 2 * CB) * LS);
+size_t smem_floats(int RP, int ell, int RB, int CB) {
+  const int LQ = lq_of(ell), LS = lsx_of(ell);
+  return static_cast<size_t>(2 * LQ * RP + 2 * RP * RP + RP) + static_cast<size_t>(RB + CB) * RP +
+         static_cast<size_t>(2 * RB + 2 * CB) * LS + kNT * 16;
 }
 
-template <int CA, int CB_, int RULE>
+int rp_of(int r) { return r <= 8 ? 8 : r <= 16 ? 16 : r <= 24 ? 24 : 32; }
+
+template <int RP, int RULE>
 cudaError_t launch(const Launcher& L, PArgs& a, int grid) {
-  auto k = iterate_persistent_kernel<CA, CB_, RULE>;
-  const size_t smem = smem_for(kGB * CB_, a.ell, a.RB, a.CB);
+  auto k = iterate_persistent_kernel<RP, RULE>;
+  const size_t smem = sizeof(float) * smem_floats(RP, a.ell, a.RB, a.CB);
   cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
   if (err != cudaSuccess) return err;
   int per_sm = 0;
-  if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kPT, smem)) != cudaSuccess)
+  if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kNT, smem)) != cudaSuccess)
     return err;
   if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
   void* args[] = {&a};
-  err = cudaLaunchCooperativeKernel(reinterpret_cast<void*>(k), dim3(grid), dim3(kPT), args, smem,
+  err = cudaLaunchCooperativeKernel(reinterpret_cast<void*>(k), dim3(grid), dim3(kNT), args, smem,
                                     L.stream);
   L.count();
   return err;
@@ -533,15 +553,18 @@ int num_sms() {
 }  // namespace
 
 size_t iterate_persistent_ws_bytes(int r, int ell) {
-  const size_t ea = ea_size(r, ell), eb = eb_size(r, ell);
+  const int RP = rp_of(r), LQ = lq_of(ell);
+  const size_t ea = ea_size(RP, LQ), eb = eb_size(RP, LQ);
   return sizeof(float) * kCopies * 2 * (ea + eb) + sizeof(Barrier) + 2 * sizeof(int) + 1024;
 }
 
 bool iterate_persistent_supported(int64_t m, int64_t n, int r, int ell) {
+  if (r < 1 || r > 32 || ell < 1 || ell > 128) return false;
   const int grid = num_sms();
   const int64_t rb = (m + grid - 1) / grid, cbk = (n + grid - 1) / grid;
-  return r <= 32 && rb <= kMaxRows && cbk <= kMaxCols &&
-         smem_for(32, ell, static_cast<int>(rb), static_cast<int>(cbk)) <= 220 * 1024;
+  if (rb > 4096 || cbk > 4096) return false;
+  return sizeof(float) * smem_floats(rp_of(r), ell, static_cast<int>(rb), static_cast<int>(cbk)) <=
+         220 * 1024;
 }
 
 cudaError_t launch_iterate_persistent(const Launcher& L, const IterArgs& ia, int iters, void* ws,
@@ -550,7 +573,8 @@ cudaError_t launch_iterate_persistent(const Launcher& L, const IterArgs& ia, int
   if (!iterate_persistent_supported(ia.m, ia.n, ia.r, ia.ell)) return cudaErrorInvalidValue;
   if (iters <= 0) return cudaSuccess;
   char* p = static_cast<char*>(ws);
-  const size_t ea = ea_size(ia.r, ia.ell), eb = eb_size(ia.r, ia.ell);
+  const int RP = rp_of(ia.r), LQ = lq_of(ia.ell);
+  const size_t ea = ea_size(RP, LQ), eb = eb_size(RP, LQ);
   const int grid = num_sms();
   PArgs a;
   a.m = ia.m;
@@ -568,23 +592,27 @@ cudaError_t launch_iterate_persistent(const Launcher& L, const IterArgs& ia, int
   a.Xchk = ia.Xchk;
   a.W = ia.W;
   a.H = ia.H;
-  a.accA = reinterpret_cast<float*>(p);
+  // 16-byte aligned sums (vector atomics)
+  uintptr_t base = (reinterpret_cast<uintptr_t>(p) + 15) & ~static_cast<uintptr_t>(15);
+  a.accA = reinterpret_cast<float*>(base);
   a.accB = a.accA + 2 * kCopies * ea;
   a.bar = reinterpret_cast<Barrier*>(a.accB + 2 * kCopies * eb);
   a.abort_flag = reinterpret_cast<int*>(a.bar + 1);
   a.status = status;
   a.mon = mon;
   a.done = done;
-  const size_t clear = reinterpret_cast<char*>(a.abort_flag + 1) - p;
-  cudaError_t err = cudaMemsetAsync(ws, 0, clear, L.stream);
+  const size_t clear = reinterpret_cast<char*>(a.abort_flag + 1) - reinterpret_cast<char*>(base);
+  cudaError_t err = cudaMemsetAsync(a.accA, 0, clear, L.stream);
   if (err != cudaSuccess) return err;
   a.RB = static_cast<int>((ia.m + grid - 1) / grid);
   a.CB = static_cast<int>((ia.n + grid - 1) / grid);
   const bool mu = ia.rule != 0;
-  if (ia.r <= 8) return mu ? launch<2, 1, 1>(L, a, grid) : launch<2, 1, 0>(L, a, grid);
-  if (ia.r <= 16) return mu ? launch<4, 1, 1>(L, a, grid) : launch<4, 1, 0>(L, a, grid);
-  if (ia.r <= 24) return mu ? launch<6, 2, 1>(L, a, grid) : launch<6, 2, 0>(L, a, grid);
-  return mu ? launch<8, 2, 1>(L, a, grid) : launch<8, 2, 0>(L, a, grid);
+  switch (RP) {
+    case 8: return mu ? launch<8, 1>(L, a, grid) : launch<8, 0>(L, a, grid);
+    case 16: return mu ? launch<16, 1>(L, a, grid) : launch<16, 0>(L, a, grid);
+    case 24: return mu ? launch<24, 1>(L, a, grid) : launch<24, 0>(L, a, grid);
+    default: return mu ? launch<32, 1>(L, a, grid) : launch<32, 0>(L, a, grid);
+  }
 }
 
 }  // namespace nmfrp
