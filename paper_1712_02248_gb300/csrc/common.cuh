@@ -46,21 +46,30 @@ cudaError_t launch_gaussian(const Launcher& L, int64_t rows, int64_t cols, uint6
 cudaError_t launch_quantize_bf16(const Launcher& L, const float* X, int64_t m, int64_t n,
                                  int64_t ldx, __nv_bfloat16* Xq, int64_t ldq);
 
+// The same copy plus ||X||^2 (into *x2_out) and <X - X_q, X> (into *corr_out), both FP64 on the
+// device; ws holds quantize_stats_ws_bytes() of block partials.
+size_t quantize_stats_ws_bytes();
+cudaError_t launch_quantize_bf16_stats(const Launcher& L, const float* X, int64_t m, int64_t n,
+                                       int64_t ldx, __nv_bfloat16* Xq, int64_t ldq, double* x2_out,
+                                       double* corr_out, void* ws, size_t ws_bytes);
+
 // Dual pass Y = X V (m x ell), Z = X^T U (n x ell). x_bf16 selects the element type of X.
 // ws: workspace for partial sums (size from dual_pass_ws_bytes).
 // BF16 X with both products goes to the tensor-core kernel when TMA can address X (ldx a
 // multiple of 8, X 16-byte aligned) unless force_simt is set.
 size_t dual_pass_ws_bytes(int64_t m, int64_t n, int ell);
+// split: on the tensor-core path, V and U enter as hi + lo BF16 pairs (only X is rounded to
+// BF16), which the compression uses; ignored elsewhere.
 cudaError_t launch_dual_pass(const Launcher& L, const void* X, bool x_bf16, int64_t m, int64_t n,
                              int64_t ldx, int ell, const float* V, const float* U, float* Y,
                              float* Z, void* ws, size_t ws_bytes, int* status,
-                             bool force_simt = false);
+                             bool force_simt = false, bool split = false);
 // tcgen05 + TMA dual pass (BF16 X).
 bool dual_pass_tc_supported(int64_t m, int64_t n, int64_t ldx, int ell, const void* X);
 size_t dual_pass_tc_ws_bytes(int64_t m, int64_t n, int ell);
 cudaError_t launch_dual_pass_tc(const Launcher& L, const __nv_bfloat16* X, int64_t m, int64_t n,
                                 int64_t ldx, int ell, const float* V, const float* U, float* Y,
-                                float* Z, void* ws, size_t ws_bytes, int* status);
+                                float* Z, void* ws, size_t ws_bytes, int* status, bool split);
 
 // Thin QR via CholeskyQR2 with FP64 Gram and Cholesky. Q may alias Y.
 size_t qr_ws_bytes(int64_t rows, int ell);

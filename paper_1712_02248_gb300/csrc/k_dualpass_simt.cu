@@ -222,11 +222,12 @@ size_t dual_pass_ws_bytes(int64_t m, int64_t n, int ell) {
 
 cudaError_t launch_dual_pass(const Launcher& L, const void* X, bool x_bf16, int64_t m, int64_t n,
                              int64_t ldx, int ell, const float* V, const float* U, float* Y,
-                             float* Z, void* ws, size_t ws_bytes, int* status, bool force_simt) {
+                             float* Z, void* ws, size_t ws_bytes, int* status, bool force_simt,
+                             bool split) {
   if (ws_bytes < dual_pass_ws_bytes(m, n, ell)) return cudaErrorInvalidValue;
   if (x_bf16 && V && U && !force_simt && dual_pass_tc_supported(m, n, ldx, ell, X))
     return launch_dual_pass_tc(L, static_cast<const __nv_bfloat16*>(X), m, n, ldx, ell, V, U, Y,
-                               Z, ws, ws_bytes, status);
+                               Z, ws, ws_bytes, status, split);
   if (x_bf16)
     return dispatch(L, static_cast<const __nv_bfloat16*>(X), m, n, ldx, ell, V, U, Y, Z,
                     static_cast<float*>(ws));

@@ -175,22 +175,35 @@ struct TcArgs {
   int ell;
   int n_rowgroups, n_colgroups;   // grid = n_colgroups x n_rowgroups
   int64_t n_rowblocks;            // ceil(m / 128)
-  int tiles_per_group;            // column tiles per column group (<= NCT)
+  int tiles_per_group;            // column tiles per column group (<= the kernel's NCT)
+  int stages;                     // X stages in shared memory (<= kMaxStages)
   int64_t n_coltiles;             // ceil(n / 128)
-  float* Ypart;                   // [n_colgroups][m][ell]
-  float* Zpart;                   // [n_rowgroups][n][ell]
+  float* Ypart;                   // [n_colgroups][ell][m]   (k-major: rows contiguous)
+  float* Zpart;                   // [n_rowgroups][ell][n]
   int* status;
 };
 
-template <int LP, int NCT, int STAGES>
+constexpr int kMaxStages = 4;
+constexpr uint32_t kXStage = 2 * kRows * kHalfCols * 2;   // 32 KB: two 128 x 64 BF16 halves
+constexpr int kSmemCap = 232448 - 1024;   // opt-in shared memory per block, less the static part
+
+// tensor-memory columns of one accumulator and the most column tiles whose Z accumulators fit
+__host__ __device__ constexpr int acc_stride(int LP) { return (LP + 31) / 32 * 32; }
+__host__ __device__ constexpr int nct_max(int LP) {
+  return (512 / acc_stride(LP) - 2) > 14 ? 14 : (512 / acc_stride(LP) - 2);
+}
+
+// SPLIT = 2: V and U enter as hi + lo BF16 pairs (v = hi + lo to about 2^-16 relative), each
+// product is accumulated from both, so only X is rounded to BF16.
+template <int LP, int SPLIT>
 __global__ void __launch_bounds__(kThreads, 1) dual_pass_tc_kernel(
     const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapV,
     const __grid_constant__ CUtensorMap mapU, TcArgs a) {
+  constexpr int NCT = nct_max(LP);
   constexpr uint32_t kXHalf = kRows * kHalfCols * 2;   // 16 KB
   constexpr uint32_t kBBox = LP * kHalfCols * 2;        // LP rows x 128 B
-  constexpr uint32_t kStage = 2 * kXHalf + 4 * kBBox;   // X halves, V boxes, U boxes
-  constexpr uint32_t kTxBytes = kStage;
-  constexpr int AS = (LP + 31) / 32 * 32;               // accumulator stride in TMEM columns
+  constexpr uint32_t kBTile = SPLIT * 2 * kBBox;        // one column tile (or row block) of V (U)
+  constexpr int AS = acc_stride(LP);
   constexpr int kTmemNeed = (2 + NCT) * AS;
   constexpr uint32_t kTmemCols = kTmemNeed <= 32 ? 32 : kTmemNeed <= 64 ? 64 : kTmemNeed <= 128
                                                                                 ? 128
@@ -201,7 +214,12 @@ __global__ void __launch_bounds__(kThreads, 1) dual_pass_tc_kernel(
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-  __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES];
+  const int stages = a.stages;
+  unsigned char* Xs = smem;                              // [stages][32 KB]
+  unsigned char* Us = Xs + stages * kXStage;             // [2][SPLIT][2 halves][kBBox]
+  unsigned char* Vs = Us + 2 * kBTile;                   // [nct][SPLIT][2 halves][kBBox]
+  __shared__ __align__(8) uint64_t full_bar[kMaxStages], empty_bar[kMaxStages];
+  __shared__ __align__(8) uint64_t u_full[2], u_empty[2], v_full;
   __shared__ __align__(8) uint64_t ydone_bar[2], yfree_bar[2], zdone_bar, drain_bar;
   __shared__ uint32_t tmem_base;
   __shared__ volatile int abort_f;
@@ -218,14 +236,17 @@ __global__ void __launch_bounds__(kThreads, 1) dual_pass_tc_kernel(
 
   if (threadIdx.x == 0) {
     abort_f = 0;
-    for (int s = 0; s < STAGES; ++s) {
+    for (int s = 0; s < kMaxStages; ++s) {
       mbar_init(smem_u32(&full_bar[s]), 1);
       mbar_init(smem_u32(&empty_bar[s]), 1);
     }
     for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&u_full[b]), 1);
+      mbar_init(smem_u32(&u_empty[b]), 1);
       mbar_init(smem_u32(&ydone_bar[b]), 1);
       mbar_init(smem_u32(&yfree_bar[b]), 128);
     }
+    mbar_init(smem_u32(&v_full), 1);
     mbar_init(smem_u32(&zdone_bar), 1);
     mbar_init(smem_u32(&drain_bar), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -239,73 +260,99 @@ __global__ void __launch_bounds__(kThreads, 1) dual_pass_tc_kernel(
     // ---------------- TMA producer
     if (lane == 0 && ntiles > 0) {
       const uint64_t pol_x = policy_evict_first(), pol_b = policy_evict_last();
-      int issued = 0;
-      for (int tI = 0; tI < ntiles; ++tI) {
-        const int s = tI % STAGES;
-        const uint32_t ph = (tI / STAGES) & 1;
-        if (!mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1, &abort_f)) break;
-        const int lr = tI / nct, lc = tI - lr * nct;
+      // the CTA's column tiles of V stay resident for the whole rectangle
+      const uint32_t vb = smem_u32(&v_full);
+      mbar_expect_tx(vb, static_cast<uint32_t>(nct) * kBTile);
+      for (int lc = 0; lc < nct; ++lc)
+        for (int sp = 0; sp < SPLIT; ++sp)
+          for (int hf = 0; hf < 2; ++hf)
+            tma_load_2d(smem_u32(Vs + lc * kBTile + (sp * 2 + hf) * kBBox), &mapV,
+                        static_cast<int>((ct0 + lc) * kCols) + hf * kHalfCols, sp * LP, vb, pol_b);
+      int issued = 0, u_issued = 0;
+      bool ok = true;
+      for (int lr = 0; lr < nrb && ok; ++lr) {
+        const int ub = lr & 1;
         const int row0 = static_cast<int>((rb0 + lr) * kRows);
-        const int col0 = static_cast<int>((ct0 + lc) * kCols);
-        unsigned char* st = smem + s * kStage;
-        const uint32_t fb = smem_u32(&full_bar[s]);
-        mbar_expect_tx(fb, kTxBytes);
-        tma_load_2d(smem_u32(st), &mapX, col0, row0, fb, pol_x);
-        tma_load_2d(smem_u32(st + kXHalf), &mapX, col0 + kHalfCols, row0, fb, pol_x);
-        tma_load_2d(smem_u32(st + 2 * kXHalf), &mapV, col0, 0, fb, pol_b);
-        tma_load_2d(smem_u32(st + 2 * kXHalf + kBBox), &mapV, col0 + kHalfCols, 0, fb, pol_b);
-        tma_load_2d(smem_u32(st + 2 * kXHalf + 2 * kBBox), &mapU, row0, 0, fb, pol_b);
-        tma_load_2d(smem_u32(st + 2 * kXHalf + 3 * kBBox), &mapU, row0 + kHalfCols, 0, fb, pol_b);
-        issued = tI + 1;
+        if (!mbar_wait(smem_u32(&u_empty[ub]), ((lr >> 1) & 1) ^ 1, &abort_f)) break;
+        const uint32_t ubar = smem_u32(&u_full[ub]);
+        mbar_expect_tx(ubar, kBTile);
+        for (int sp = 0; sp < SPLIT; ++sp)
+          for (int hf = 0; hf < 2; ++hf)
+            tma_load_2d(smem_u32(Us + ub * kBTile + (sp * 2 + hf) * kBBox), &mapU,
+                        row0 + hf * kHalfCols, sp * LP, ubar, pol_b);
+        u_issued = lr + 1;
+        for (int lc = 0; lc < nct; ++lc) {
+          const int tI = lr * nct + lc;
+          const int s = tI % stages;
+          const uint32_t ph = (tI / stages) & 1;
+          if (!mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1, &abort_f)) {
+            ok = false;
+            break;
+          }
+          const int col0 = static_cast<int>((ct0 + lc) * kCols);
+          unsigned char* st = Xs + s * kXStage;
+          const uint32_t fb = smem_u32(&full_bar[s]);
+          mbar_expect_tx(fb, kXStage);
+          tma_load_2d(smem_u32(st), &mapX, col0, row0, fb, pol_x);
+          tma_load_2d(smem_u32(st + kXHalf), &mapX, col0 + kHalfCols, row0, fb, pol_x);
+          issued = tI + 1;
+        }
       }
-      // the last copy issued on each stage has landed before the CTA may leave
-      for (int tI = issued - STAGES > 0 ? issued - STAGES : 0; tI < issued; ++tI) {
-        mbar_drain(smem_u32(&full_bar[tI % STAGES]), (tI / STAGES) & 1);
-      }
+      // every copy issued has landed before the CTA may leave
+      mbar_drain(vb, 0);
+      for (int lr = u_issued - 2 > 0 ? u_issued - 2 : 0; lr < u_issued; ++lr)
+        mbar_drain(smem_u32(&u_full[lr & 1]), (lr >> 1) & 1);
+      for (int tI = issued - stages > 0 ? issued - stages : 0; tI < issued; ++tI)
+        mbar_drain(smem_u32(&full_bar[tI % stages]), (tI / stages) & 1);
     }
   } else if (warp == 5) {
     // ---------------- MMA issuer
     if (lane == 0 && ntiles > 0) {
       constexpr uint32_t idY = idesc_bf16(LP, 0);   // A = X tile, K-major
       constexpr uint32_t idZ = idesc_bf16(LP, 1);   // A = X tile, MN-major
-      int tI = 0;
-      bool ok = true;
+      bool ok = mbar_wait(smem_u32(&v_full), 0, &abort_f);
       for (int lr = 0; lr < nrb && ok; ++lr) {
-        const int yb = lr & 1;
-        if (!mbar_wait(smem_u32(&yfree_bar[yb]), ((lr >> 1) & 1) ^ 1, &abort_f)) {
+        const int yb = lr & 1, ub = lr & 1;
+        if (!mbar_wait(smem_u32(&yfree_bar[yb]), ((lr >> 1) & 1) ^ 1, &abort_f) ||
+            !mbar_wait(smem_u32(&u_full[ub]), (lr >> 1) & 1, &abort_f)) {
           ok = false;
           break;
         }
         tc_fence_after();
         const uint32_t dY = tmem + static_cast<uint32_t>(yb * AS);
-        for (int lc = 0; lc < nct; ++lc, ++tI) {
-          const int s = tI % STAGES;
-          const uint32_t ph = (tI / STAGES) & 1;
+        const uint32_t ubase = smem_u32(Us + ub * kBTile);
+        for (int lc = 0; lc < nct; ++lc) {
+          const int tI = lr * nct + lc;
+          const int s = tI % stages;
+          const uint32_t ph = (tI / stages) & 1;
           if (!mbar_wait(smem_u32(&full_bar[s]), ph, &abort_f)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          const uint32_t st = smem_u32(smem + s * kStage);
-          const uint32_t xa = st, xb = st + kXHalf;
-          const uint32_t v0 = st + 2 * kXHalf, v1 = v0 + kBBox;
-          const uint32_t u0 = st + 2 * kXHalf + 2 * kBBox, u1 = u0 + kBBox;
+          const uint32_t xa = smem_u32(Xs + s * kXStage), xb = xa + kXHalf;
+          const uint32_t vbase = smem_u32(Vs + lc * kBTile);
           const uint32_t dZ = tmem + static_cast<uint32_t>((2 + lc) * AS);
 #pragma unroll
           for (int kk = 0; kk < 8; ++kk) {
             const uint32_t off = (kk & 3) * 32;
+            const uint32_t hf = kk < 4 ? 0u : 1u;
             // Y: K = columns of the tile
             const uint64_t aY = sdesc((kk < 4 ? xa : xb) + off, 16, 1024);
-            const uint64_t bY = sdesc((kk < 4 ? v0 : v1) + off, 16, 1024);
-            mma_bf16(dY, aY, bY, idY, (lc > 0 || kk > 0) ? 1u : 0u);
             // Z: K = rows of the tile; MN-major A spans both halves (LBO = 16 KB)
             const uint64_t aZ = sdesc(xa + kk * 2048, kXHalf, 1024);
-            const uint64_t bZ = sdesc((kk < 4 ? u0 : u1) + off, 16, 1024);
-            mma_bf16(dZ, aZ, bZ, idZ, (lr > 0 || kk > 0) ? 1u : 0u);
+#pragma unroll
+            for (int sp = 0; sp < SPLIT; ++sp) {
+              const uint64_t bY = sdesc(vbase + (sp * 2 + hf) * kBBox + off, 16, 1024);
+              mma_bf16(dY, aY, bY, idY, (lc > 0 || kk > 0 || sp > 0) ? 1u : 0u);
+              const uint64_t bZ = sdesc(ubase + (sp * 2 + hf) * kBBox + off, 16, 1024);
+              mma_bf16(dZ, aZ, bZ, idZ, (lr > 0 || kk > 0 || sp > 0) ? 1u : 0u);
+            }
           }
           mma_commit(smem_u32(&empty_bar[s]));
         }
         if (!ok) break;
+        mma_commit(smem_u32(&u_empty[ub]));
         mma_commit(smem_u32(&ydone_bar[yb]));
       }
       if (ok) mma_commit(smem_u32(&zdone_bar));
@@ -315,36 +362,40 @@ __global__ void __launch_bounds__(kThreads, 1) dual_pass_tc_kernel(
     }
   } else {
     // ---------------- epilogue: warps 0-3, TMEM lanes 32 warp .. 32 warp + 31
+    // partial sums are k-major, so each store of a warp covers 32 consecutive floats
     const uint32_t lane_base = static_cast<uint32_t>(warp * 32) << 16;
-    float v[LP];
+    float v[16];
     for (int lr = 0; lr < (ntiles > 0 ? nrb : 0); ++lr) {
       const int yb = lr & 1;
       if (!mbar_wait(smem_u32(&ydone_bar[yb]), (lr >> 1) & 1, &abort_f)) break;
       tc_fence_after();
+      const int64_t row = (rb0 + lr) * kRows + warp * 32 + lane;
+      float* dst = a.Ypart + static_cast<int64_t>(cg) * a.ell * a.m + row;
+#pragma unroll 1
+      for (int c = 0; c < LP; c += 16) {
+        tmem_ld16(tmem + lane_base + yb * AS + c, v);
+        if (row < a.m) {
 #pragma unroll
-      for (int c = 0; c < LP; c += 16) tmem_ld16(tmem + lane_base + yb * AS + c, v + c);
+          for (int k = 0; k < 16; ++k)
+            if (c + k < a.ell) __stcg(dst + static_cast<int64_t>(c + k) * a.m, v[k]);
+        }
+      }
       tc_fence_before();
       mbar_arrive(smem_u32(&yfree_bar[yb]));
-      const int64_t row = (rb0 + lr) * kRows + warp * 32 + lane;
-      if (row < a.m) {
-        float* dst = a.Ypart + (static_cast<int64_t>(cg) * a.m + row) * a.ell;
-#pragma unroll
-        for (int k = 0; k < LP; ++k)
-          if (k < a.ell) dst[k] = v[k];
-      }
     }
     if (ntiles > 0 && mbar_wait(smem_u32(&zdone_bar), 0, &abort_f)) {
       tc_fence_after();
       for (int lc = 0; lc < nct; ++lc) {
-#pragma unroll
-        for (int c = 0; c < LP; c += 16)
-          tmem_ld16(tmem + lane_base + (2 + lc) * AS + c, v + c);
         const int64_t col = (ct0 + lc) * kCols + warp * 32 + lane;
-        if (col < a.n) {
-          float* dst = a.Zpart + (static_cast<int64_t>(rg) * a.n + col) * a.ell;
+        float* dst = a.Zpart + static_cast<int64_t>(rg) * a.ell * a.n + col;
+#pragma unroll 1
+        for (int c = 0; c < LP; c += 16) {
+          tmem_ld16(tmem + lane_base + (2 + lc) * AS + c, v);
+          if (col < a.n) {
 #pragma unroll
-          for (int k = 0; k < LP; ++k)
-            if (k < a.ell) dst[k] = v[k];
+            for (int k = 0; k < 16; ++k)
+              if (c + k < a.ell) __stcg(dst + static_cast<int64_t>(c + k) * a.n, v[k]);
+          }
         }
       }
       tc_fence_before();
@@ -358,9 +409,11 @@ __global__ void __launch_bounds__(kThreads, 1) dual_pass_tc_kernel(
   }
 }
 
-// V (rows x ell, FP32) -> Vt (LP x ld, BF16), rows ell..LP-1 and columns rows..ld-1 zero.
+// V (rows x ell, FP32) -> Vt (SPLIT*LP x ld, BF16): rows [0, LP) hold hi = bf16(v), rows
+// [LP, 2 LP) (SPLIT = 2) hold lo = bf16(v - hi); rows ell..LP-1 of each part and columns
+// rows..ld-1 are zero.
 __global__ void transpose_bf16_kernel(const float* __restrict__ V, int64_t rows, int ell, int LP,
-                                      int64_t ld, __nv_bfloat16* __restrict__ Vt) {
+                                      int split, int64_t ld, __nv_bfloat16* __restrict__ Vt) {
   __shared__ float tile[32][33];
   const int64_t r0 = static_cast<int64_t>(blockIdx.x) * 32;
   const int k0 = blockIdx.y * 32;
@@ -373,17 +426,35 @@ __global__ void transpose_bf16_kernel(const float* __restrict__ V, int64_t rows,
   for (int i = threadIdx.y; i < 32; i += blockDim.y) {
     const int k = k0 + i;
     const int64_t r = r0 + threadIdx.x;
-    if (k < LP && r < ld) Vt[static_cast<int64_t>(k) * ld + r] = __float2bfloat16_rn(tile[threadIdx.x][i]);
+    if (k < LP && r < ld) {
+      const float x = tile[threadIdx.x][i];
+      const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+      Vt[static_cast<int64_t>(k) * ld + r] = hi;
+      if (split == 2)
+        Vt[static_cast<int64_t>(LP + k) * ld + r] = __float2bfloat16_rn(x - __bfloat162float(hi));
+    }
   }
 }
 
-__global__ void reduce_slots_tc_kernel(const float* __restrict__ part, int slots, int64_t total,
-                                       float* __restrict__ out) {
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
+// out[row][k] = sum over slots of part[slot][k][row] (fixed slot order), 32 rows a block,
+// transposed through shared memory so that both the reads and the writes are coalesced.
+__global__ void __launch_bounds__(256) reduce_slots_t_kernel(const float* __restrict__ part,
+                                                             int slots, int64_t rows, int ell,
+                                                             float* __restrict__ out) {
+  __shared__ float tile[32][129];
+  const int64_t row0 = static_cast<int64_t>(blockIdx.x) * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int64_t r = row0 + tx;
+  for (int k = ty; k < ell; k += 8) {
     float s = 0.f;
-    for (int k = 0; k < slots; ++k) s += part[k * total + e];
-    out[e] = s;
+    if (r < rows)
+      for (int c = 0; c < slots; ++c) s += __ldcg(part + (static_cast<int64_t>(c) * ell + k) * rows + r);
+    tile[tx][k] = s;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < 32 * ell; e += 256) {
+    const int i = e / ell, k = e - i * ell;
+    if (row0 + i < rows) out[(row0 + i) * ell + k] = tile[i][k];
   }
 }
 
@@ -433,21 +504,46 @@ int num_sms() {
 int lp16(int ell) { return (ell + 15) / 16 * 16; }
 
 struct Plan {
-  int LP, NCT, stages;
+  int LP, split, stages, nct;
+  size_t smem;
   int rowgroups, colgroups, tiles_per_group;
   int64_t rowblocks, coltiles;
 };
 
-Plan plan_for(int64_t m, int64_t n, int ell) {
+size_t smem_bytes(int LP, int split, int stages, int nct) {
+  const size_t btile = static_cast<size_t>(split) * 2 * LP * kHalfCols * 2;
+  return static_cast<size_t>(stages) * kXStage + 2 * btile + static_cast<size_t>(nct) * btile + 1024;
+}
+
+// Deepest X pipeline that still keeps enough resident column tiles (4 stages with
+// min(4, NCT) tiles, else 3 stages with min(2, NCT), else 2 stages with one), then as many
+// resident column tiles as fit. nct = 0 means the configuration does not fit.
+void pick_stages(int LP, int split, int* stages, int* nct) {
+  const int cap = nct_max(LP);
+  for (int s = kMaxStages; s >= 2; --s) {
+    int k = cap;
+    while (k > 0 && smem_bytes(LP, split, s, k) > static_cast<size_t>(kSmemCap)) --k;
+    const int want = s == 4 ? (cap < 4 ? cap : 4) : s == 3 ? (cap < 2 ? cap : 2) : 1;
+    if (k >= want && k > 0) {
+      *stages = s;
+      *nct = k;
+      return;
+    }
+  }
+  *stages = 2;
+  *nct = 0;
+}
+
+Plan plan_for(int64_t m, int64_t n, int ell, int split) {
   Plan p;
   p.LP = lp16(ell);
-  const int as = (p.LP + 31) / 32 * 32;
-  p.NCT = 512 / as - 2;
-  if (p.NCT > 14) p.NCT = 14;
-  p.stages = p.LP <= 64 ? 3 : 2;
+  p.split = split;
+  pick_stages(p.LP, split, &p.stages, &p.nct);
+  p.smem = smem_bytes(p.LP, split, p.stages, p.nct > 0 ? p.nct : 1);
   p.rowblocks = cdiv(m, kRows);
   p.coltiles = cdiv(n, kCols);
-  p.colgroups = static_cast<int>(cdiv(p.coltiles, p.NCT));
+  const int nct = p.nct > 0 ? p.nct : 1;
+  p.colgroups = static_cast<int>(cdiv(p.coltiles, nct));
   p.tiles_per_group = static_cast<int>(cdiv(p.coltiles, p.colgroups));
   int rg = num_sms() / p.colgroups;
   if (rg < 1) rg = 1;
@@ -456,12 +552,10 @@ Plan plan_for(int64_t m, int64_t n, int ell) {
   return p;
 }
 
-template <int LP, int NCT, int STAGES>
+template <int LP, int SPLIT>
 cudaError_t launch_t(const Launcher& L, const CUtensorMap& mx, const CUtensorMap& mv,
-                     const CUtensorMap& mu, const TcArgs& a) {
-  auto k = dual_pass_tc_kernel<LP, NCT, STAGES>;
-  constexpr size_t stage = 2 * kRows * kHalfCols * 2 + 4 * LP * kHalfCols * 2;
-  size_t smem = STAGES * stage + 1024;
+                     const CUtensorMap& mu, const TcArgs& a, size_t smem) {
+  auto k = dual_pass_tc_kernel<LP, SPLIT>;
   if (smem < 120 * 1024) smem = 120 * 1024;   // one CTA per SM: it owns the tensor memory
   cudaError_t err =
       cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
@@ -470,6 +564,22 @@ cudaError_t launch_t(const Launcher& L, const CUtensorMap& mx, const CUtensorMap
   k<<<grid, kThreads, smem, L.stream>>>(mx, mv, mu, a);
   L.count();
   return cudaGetLastError();
+}
+
+template <int SPLIT>
+cudaError_t launch_lp(int LP, const Launcher& L, const CUtensorMap& mx, const CUtensorMap& mv,
+                      const CUtensorMap& mu, const TcArgs& a, size_t smem) {
+  switch (LP) {
+    case 16: return launch_t<16, SPLIT>(L, mx, mv, mu, a, smem);
+    case 32: return launch_t<32, SPLIT>(L, mx, mv, mu, a, smem);
+    case 48: return launch_t<48, SPLIT>(L, mx, mv, mu, a, smem);
+    case 64: return launch_t<64, SPLIT>(L, mx, mv, mu, a, smem);
+    case 80: return launch_t<80, SPLIT>(L, mx, mv, mu, a, smem);
+    case 96: return launch_t<96, SPLIT>(L, mx, mv, mu, a, smem);
+    case 112: return launch_t<112, SPLIT>(L, mx, mv, mu, a, smem);
+    case 128: return launch_t<128, SPLIT>(L, mx, mv, mu, a, smem);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace
@@ -481,18 +591,33 @@ bool dual_pass_tc_supported(int64_t m, int64_t n, int64_t ldx, int ell, const vo
   return encode_fn() != nullptr;
 }
 
+bool dual_pass_tc_split_supported(int ell) {
+  int s = 0, k = 0;
+  pick_stages(lp16(ell), 2, &s, &k);
+  return ell >= 1 && ell <= 128 && k > 0;
+}
+
 size_t dual_pass_tc_ws_bytes(int64_t m, int64_t n, int ell) {
-  const Plan p = plan_for(m, n, ell);
-  const int64_t ldv = (n + 7) / 8 * 8, ldu = (m + 7) / 8 * 8;
-  return sizeof(float) * static_cast<size_t>(p.colgroups * m * ell + p.rowgroups * n * ell) +
-         2 * static_cast<size_t>(p.LP) * (ldv + ldu) + 4096;
+  // the larger of the two layouts (plain and split operands)
+  size_t best = 0;
+  for (int split = 1; split <= 2; ++split) {
+    const Plan p = plan_for(m, n, ell, split);
+    const int64_t ldv = (n + 7) / 8 * 8, ldu = (m + 7) / 8 * 8;
+    const size_t b =
+        sizeof(float) * static_cast<size_t>(p.colgroups * m * ell + p.rowgroups * n * ell) +
+        2 * static_cast<size_t>(split * p.LP) * (ldv + ldu) + 4096;
+    if (b > best) best = b;
+  }
+  return best;
 }
 
 cudaError_t launch_dual_pass_tc(const Launcher& L, const __nv_bfloat16* X, int64_t m, int64_t n,
                                 int64_t ldx, int ell, const float* V, const float* U, float* Y,
-                                float* Z, void* ws, size_t ws_bytes, int* status) {
+                                float* Z, void* ws, size_t ws_bytes, int* status, bool split) {
   if (ws_bytes < dual_pass_tc_ws_bytes(m, n, ell)) return cudaErrorInvalidValue;
-  const Plan p = plan_for(m, n, ell);
+  const int sp = (split && dual_pass_tc_split_supported(ell)) ? 2 : 1;
+  const Plan p = plan_for(m, n, ell, sp);
+  if (p.nct < 1) return cudaErrorInvalidValue;
   const int64_t ldv = (n + 7) / 8 * 8, ldu = (m + 7) / 8 * 8;
   char* w = static_cast<char*>(ws);
   float* Ypart = reinterpret_cast<float*>(w);
@@ -500,22 +625,22 @@ cudaError_t launch_dual_pass_tc(const Launcher& L, const __nv_bfloat16* X, int64
   uintptr_t q = reinterpret_cast<uintptr_t>(Zpart + p.rowgroups * n * ell);
   q = (q + 255) & ~uintptr_t(255);
   __nv_bfloat16* Vt = reinterpret_cast<__nv_bfloat16*>(q);
-  q += 2 * static_cast<size_t>(p.LP) * ldv;
+  q += 2 * static_cast<size_t>(sp * p.LP) * ldv;
   q = (q + 255) & ~uintptr_t(255);
   __nv_bfloat16* Ut = reinterpret_cast<__nv_bfloat16*>(q);
   {
     dim3 gv(static_cast<unsigned>(cdiv(ldv, 32)), static_cast<unsigned>(cdiv(p.LP, 32)));
-    transpose_bf16_kernel<<<gv, dim3(32, 8), 0, L.stream>>>(V, n, ell, p.LP, ldv, Vt);
+    transpose_bf16_kernel<<<gv, dim3(32, 8), 0, L.stream>>>(V, n, ell, p.LP, sp, ldv, Vt);
     dim3 gu(static_cast<unsigned>(cdiv(ldu, 32)), static_cast<unsigned>(cdiv(p.LP, 32)));
-    transpose_bf16_kernel<<<gu, dim3(32, 8), 0, L.stream>>>(U, m, ell, p.LP, ldu, Ut);
+    transpose_bf16_kernel<<<gu, dim3(32, 8), 0, L.stream>>>(U, m, ell, p.LP, sp, ldu, Ut);
     L.count(2);
   }
   CUtensorMap mx, mv, mu;
   if (!make_map(&mx, X, static_cast<uint64_t>(n), static_cast<uint64_t>(m),
                 static_cast<uint64_t>(ldx), kHalfCols, kRows) ||
-      !make_map(&mv, Vt, static_cast<uint64_t>(ldv), static_cast<uint64_t>(p.LP),
+      !make_map(&mv, Vt, static_cast<uint64_t>(ldv), static_cast<uint64_t>(sp * p.LP),
                 static_cast<uint64_t>(ldv), kHalfCols, static_cast<uint32_t>(p.LP)) ||
-      !make_map(&mu, Ut, static_cast<uint64_t>(ldu), static_cast<uint64_t>(p.LP),
+      !make_map(&mu, Ut, static_cast<uint64_t>(ldu), static_cast<uint64_t>(sp * p.LP),
                 static_cast<uint64_t>(ldu), kHalfCols, static_cast<uint32_t>(p.LP)))
     return cudaErrorInvalidValue;
   TcArgs a;
@@ -526,28 +651,19 @@ cudaError_t launch_dual_pass_tc(const Launcher& L, const __nv_bfloat16* X, int64
   a.n_colgroups = p.colgroups;
   a.n_rowblocks = p.rowblocks;
   a.tiles_per_group = p.tiles_per_group;
+  a.stages = p.stages;
   a.n_coltiles = p.coltiles;
   a.Ypart = Ypart;
   a.Zpart = Zpart;
   a.status = status;
-  cudaError_t err;
-  switch (p.LP) {
-    case 16: err = launch_t<16, 14, 3>(L, mx, mv, mu, a); break;
-    case 32: err = launch_t<32, 14, 3>(L, mx, mv, mu, a); break;
-    case 48: err = launch_t<48, 6, 3>(L, mx, mv, mu, a); break;
-    case 64: err = launch_t<64, 6, 3>(L, mx, mv, mu, a); break;
-    case 80: err = launch_t<80, 3, 2>(L, mx, mv, mu, a); break;
-    case 96: err = launch_t<96, 3, 2>(L, mx, mv, mu, a); break;
-    case 112: err = launch_t<112, 2, 2>(L, mx, mv, mu, a); break;
-    case 128: err = launch_t<128, 2, 2>(L, mx, mv, mu, a); break;
-    default: return cudaErrorInvalidValue;
-  }
+  const size_t smem = smem_bytes(p.LP, sp, p.stages, p.tiles_per_group);
+  cudaError_t err = sp == 2 ? launch_lp<2>(p.LP, L, mx, mv, mu, a, smem)
+                            : launch_lp<1>(p.LP, L, mx, mv, mu, a, smem);
   if (err != cudaSuccess) return err;
-  const int64_t ty = m * ell, tz = n * ell;
-  reduce_slots_tc_kernel<<<static_cast<unsigned>(cdiv(ty, 256) < 4096 ? cdiv(ty, 256) : 4096), 256,
-                           0, L.stream>>>(Ypart, p.colgroups, ty, Y);
-  reduce_slots_tc_kernel<<<static_cast<unsigned>(cdiv(tz, 256) < 4096 ? cdiv(tz, 256) : 4096), 256,
-                           0, L.stream>>>(Zpart, p.rowgroups, tz, Z);
+  reduce_slots_t_kernel<<<static_cast<unsigned>(cdiv(m, 32)), 256, 0, L.stream>>>(
+      Ypart, p.colgroups, m, ell, Y);
+  reduce_slots_t_kernel<<<static_cast<unsigned>(cdiv(n, 32)), 256, 0, L.stream>>>(
+      Zpart, p.rowgroups, n, ell, Z);
   L.count(2);
   return cudaGetLastError();
 }

@@ -82,6 +82,83 @@ __global__ void quantize_bf16_vec4_kernel(const float* __restrict__ X, int64_t m
   }
 }
 
+// BF16 copy plus the two sums the compressed error monitor needs: ||X||^2 and <X - X_q, X>
+// (the rounding of X to BF16 enters the monitor's cross term; this sum removes it). Per element
+// in FP32, per thread and block in FP64, block partials summed in a fixed order.
+template <bool VEC>
+__global__ void __launch_bounds__(256) quantize_bf16_stats_kernel(
+    const float* __restrict__ X, int64_t m, int64_t n, int64_t ldx, __nv_bfloat16* __restrict__ Xq,
+    int64_t ldq, double* __restrict__ part) {
+  __shared__ double red[2][8];
+  double x2 = 0.0, corr = 0.0;
+  if (VEC) {
+    const int64_t n4 = n / 4, total = m * n4;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+      const int64_t i = e / n4, j4 = e - i * n4;
+      const float4 v = __ldcs(reinterpret_cast<const float4*>(X + i * ldx) + j4);
+      __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y);
+      __nv_bfloat162 hi = __floats2bfloat162_rn(v.z, v.w);
+      uint2 packed;
+      packed.x = *reinterpret_cast<uint32_t*>(&lo);
+      packed.y = *reinterpret_cast<uint32_t*>(&hi);
+      reinterpret_cast<uint2*>(Xq + i * ldq)[j4] = packed;
+      const float2 ql = __bfloat1622float2(lo), qh = __bfloat1622float2(hi);
+      x2 += static_cast<double>(fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, v.w * v.w))));
+      corr += static_cast<double>(fmaf(v.x, v.x - ql.x, fmaf(v.y, v.y - ql.y,
+                                   fmaf(v.z, v.z - qh.x, v.w * (v.w - qh.y)))));
+    }
+  } else {
+    const int64_t total = m * ldq;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+      const int64_t i = e / ldq, j = e - i * ldq;
+      const float x = j < n ? X[i * ldx + j] : 0.f;
+      const __nv_bfloat16 q = __float2bfloat16_rn(x);
+      Xq[e] = q;
+      x2 += static_cast<double>(x * x);
+      corr += static_cast<double>(x * (x - __bfloat162float(q)));
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    x2 += __shfl_xor_sync(0xffffffffu, x2, o);
+    corr += __shfl_xor_sync(0xffffffffu, corr, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = x2;
+    red[1][threadIdx.x >> 5] = corr;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < 8; ++w) {
+      a += red[0][w];
+      b += red[1][w];
+    }
+    part[2 * blockIdx.x] = a;
+    part[2 * blockIdx.x + 1] = b;
+  }
+}
+
+__global__ void stats_final_kernel(const double* __restrict__ part, int nparts,
+                                   double* __restrict__ x2_out, double* __restrict__ corr_out) {
+  double a = 0.0, b = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += 32) {
+    a += part[2 * i];
+    b += part[2 * i + 1];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  if (threadIdx.x == 0) {
+    *x2_out = a;
+    *corr_out = b;
+  }
+}
+
 int grid_for(int64_t work, int threads) {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -114,6 +191,40 @@ cudaError_t launch_quantize_bf16(const Launcher& L, const float* X, int64_t m, i
   else
     quantize_bf16_kernel<<<grid_for(m * ldq, 256), 256, 0, L.stream>>>(X, m, n, ldx, Xq, ldq);
   L.count();
+  return cudaGetLastError();
+}
+
+size_t quantize_stats_ws_bytes() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (sms <= 0) sms = 148;
+  return sizeof(double) * 2 * static_cast<size_t>(sms) * 8 + 256;
+}
+
+cudaError_t launch_quantize_bf16_stats(const Launcher& L, const float* X, int64_t m, int64_t n,
+                                       int64_t ldx, __nv_bfloat16* Xq, int64_t ldq, double* x2_out,
+                                       double* corr_out, void* ws, size_t ws_bytes) {
+  if (m * n <= 0) return cudaErrorInvalidValue;
+  if (ws_bytes < quantize_stats_ws_bytes()) return cudaErrorInvalidValue;
+  const bool vec = (n % 4 == 0) && (ldx % 4 == 0) && (ldq % 4 == 0) &&
+                   (reinterpret_cast<uintptr_t>(X) % 16 == 0);
+  double* part = static_cast<double*>(ws);
+  int grid;
+  if (vec) {
+    grid = grid_for(m * n / 4, 256);
+    if (ldq != n) {
+      // zero the pad columns first (the vector kernel writes columns [0, n) only)
+      cudaError_t e = cudaMemsetAsync(Xq, 0, sizeof(__nv_bfloat16) * m * ldq, L.stream);
+      if (e != cudaSuccess) return e;
+    }
+    quantize_bf16_stats_kernel<true><<<grid, 256, 0, L.stream>>>(X, m, n, ldx, Xq, ldq, part);
+  } else {
+    grid = grid_for(m * ldq, 256);
+    quantize_bf16_stats_kernel<false><<<grid, 256, 0, L.stream>>>(X, m, n, ldx, Xq, ldq, part);
+  }
+  stats_final_kernel<<<1, 32, 0, L.stream>>>(part, grid, x2_out, corr_out);
+  L.count(2);
   return cudaGetLastError();
 }
 

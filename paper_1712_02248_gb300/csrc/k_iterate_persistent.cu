@@ -16,7 +16,7 @@
 //                     H^T [Q_R | H]  (H_tld and H H^T) and of <S_H, H> is added.
 //   -- grid barrier --
 //
-// A row of W is handled by kGA = 2 lanes and a column of H by kGB = 4 lanes; each lane owns a
+// A row of W is handled by kGA = 2 lanes and a column of H by kGB = 2 lanes; each lane owns a
 // contiguous run of RP / kGA (RP / kGB) components, so every shared-memory read of a Gram row or
 // of H_tld / W_tld is a broadcast vector load. The sweep is incremental: t_j = S_j - sum_q w_q
 // G_qj is formed for every j; when w_j moves by d (computed by the lane owning j, broadcast in
@@ -44,13 +44,13 @@ namespace {
 
 constexpr int kNT = 512;          // threads per block (one block per SM)
 constexpr int kGA = 2;            // lanes per row of W
-constexpr int kGB = 4;            // lanes per column of H
+constexpr int kGB = 2;            // lanes per column of H
 constexpr int kCopies = 4;        // copies of each cross-block sum
 constexpr long long kWaitCycles = 4000000000LL;   // about two seconds of polling
 
 struct Barrier {
-  unsigned int count;
-  unsigned int gen;
+  unsigned int count;   // arrivals so far (never reset within a launch)
+  unsigned int pad;
 };
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
@@ -59,22 +59,28 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
   return v;
 }
 
-// Grid-wide barrier for a co-resident grid. Returns false if the wait ran out.
-__device__ bool grid_sync(Barrier* bar, unsigned nblocks, int* status, int* abort_flag) {
+__device__ __forceinline__ unsigned atom_add_acq_rel(unsigned* p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+
+// Grid-wide barrier for a co-resident grid: the k-th barrier of the launch completes when the
+// arrival counter reaches k * nblocks (one acquire-release add per block after a fence, acquire
+// polling). Returns false if the wait ran out.
+__device__ bool grid_sync(Barrier* bar, unsigned nblocks, unsigned& epoch, int* status,
+                          int* abort_flag) {
   __syncthreads();
   __shared__ int ok;
+  ++epoch;
   if (threadIdx.x == 0) {
     ok = 1;
-    const unsigned g = ld_acquire(&bar->gen);
+    const unsigned target = epoch * nblocks;
     __threadfence();
-    const unsigned arrived = atomicAdd(&bar->count, 1u);
-    if (arrived == nblocks - 1) {
-      bar->count = 0;
-      __threadfence();
-      atomicAdd(&bar->gen, 1u);
-    } else {
+    const unsigned before = atom_add_acq_rel(&bar->count, 1u);
+    if (before + 1 < target) {
       const long long t0 = clock64();
-      while (ld_acquire(&bar->gen) == g) {
+      while (static_cast<int>(ld_acquire(&bar->count) - target) < 0) {
         if (clock64() - t0 > kWaitCycles || *reinterpret_cast<volatile int*>(abort_flag)) {
           ok = 0;
           break;
@@ -190,9 +196,10 @@ __device__ void block_share(int K, int NA, int NB, const float* A1, int lda1, co
   }
 }
 
-// G[p][q] = sum_k T[k][p] T[k][q] (RP x RP) from T (LQ x RP), 2 x 2 outputs a thread.
+// G[p][q] = sum_k T[k][p] T[k][q] (RP x RP) from T (LQ x RP), 2 x 2 outputs a thread;
+// inv[j] = 1 / G[j][j] where G[j][j] > 0, else 0.
 template <int RP>
-__device__ __forceinline__ void gram_rp(const float* T, int LQ, float* G) {
+__device__ __forceinline__ void gram_rp(const float* T, int LQ, float* G, float* inv) {
   constexpr int H2 = RP / 2;
   for (int u = threadIdx.x; u < H2 * H2; u += kNT) {
     const int p0 = 2 * (u / H2), q0 = 2 * (u % H2);
@@ -210,12 +217,17 @@ __device__ __forceinline__ void gram_rp(const float* T, int LQ, float* G) {
     G[p0 * RP + q0 + 1] = g01;
     G[(p0 + 1) * RP + q0] = g10;
     G[(p0 + 1) * RP + q0 + 1] = g11;
+    if (p0 == q0) {
+      inv[p0] = g00 > 0.f ? 1.f / g00 : 0.f;
+      inv[p0 + 1] = g11 > 0.f ? 1.f / g11 : 0.f;
+    }
   }
 }
 
 // C consecutive floats from shared memory (C a multiple of 2; float4 where it can).
 template <int C>
 __device__ __forceinline__ void ld_run(const float* p, float* v) {
+  static_assert(C % 2 == 0, "runs are read as float2 / float4");
   if constexpr (C % 4 == 0) {
 #pragma unroll
     for (int c = 0; c < C; c += 4) {
@@ -240,8 +252,9 @@ __device__ __forceinline__ void ld_run(const float* p, float* v) {
 // memory) and the rule. For FastHALS-RP on H (reg = true) the Section 4.1 alpha / beta form is
 // used. Components j >= r are zero on entry and stay zero.
 template <int RP, int NG, int RULE>
-__device__ __forceinline__ void update_vec(float* v, float* s, const float* G, int g, int r,
-                                           bool reg, float alpha, float beta, float eps) {
+__device__ __forceinline__ void update_vec(float* v, float* s, const float* G, const float* inv,
+                                           int g, int r, bool reg, float alpha, float beta,
+                                           float eps) {
   constexpr int C = RP / NG;
   const unsigned full = 0xffffffffu;
   if (RULE == 0) {
@@ -267,7 +280,7 @@ __device__ __forceinline__ void update_vec(float* v, float* s, const float* G, i
           const float gjj = G[j * RP + j];
           float vn = v[cj];
           if (!reg) {
-            if (gjj > 0.f) vn = fmaxf(0.f, fmaf(s[cj], 1.f / gjj, v[cj]));
+            if (gjj > 0.f) vn = fmaxf(0.f, fmaf(s[cj], inv[j], v[cj]));
           } else if (gjj + beta > 0.f) {
             vn = fmaxf(0.f, (fmaf(v[cj], gjj, s[cj]) - alpha) / (gjj + beta));
           }
@@ -307,9 +320,9 @@ __device__ __forceinline__ void update_vec(float* v, float* s, const float* G, i
   }
 }
 
-template <int RP, int RULE>
+template <int RP, int RULE, int GA, int GB>
 __global__ void __launch_bounds__(kNT, 1) iterate_persistent_kernel(PArgs a) {
-  constexpr int CA = RP / kGA, CBn = RP / kGB;
+  constexpr int CA = RP / GA, CBn = RP / GB;
   extern __shared__ __align__(16) float sh[];
   const int r = a.r, ell = a.ell, t = threadIdx.x;
   const int LQ = lq_of(ell), LS = lsx_of(ell);
@@ -320,7 +333,8 @@ __global__ void __launch_bounds__(kNT, 1) iterate_persistent_kernel(PArgs a) {
   float* WtS = Gw + RP * RP;        // [LQ][RP]   W_tld (normalised)
   float* Gh = WtS + LQ * RP;        // [RP][RP]
   float* sc = Gh + RP * RP;         // [RP]       s_j of the last W phase
-  float* Ws = sc + RP;              // [RB][RP]   rows of W (unnormalised)
+  float* invs = sc + RP;            // [RP]       1 / G_jj of the current phase
+  float* Ws = invs + RP;            // [RB][RP]   rows of W (unnormalised)
   float* Hs = Ws + RB * RP;         // [CB][RP]   columns of H
   float* Xc = Hs + CB * RP;         // [RB][LS]   rows of X_chk
   float* Ql = Xc + RB * LS;         // [RB][LS]   rows of Q_L
@@ -336,6 +350,7 @@ __global__ void __launch_bounds__(kNT, 1) iterate_persistent_kernel(PArgs a) {
   const bool reg = !(a.alpha == 0.f && a.beta == 0.f);
 
   if (*reinterpret_cast<const volatile int*>(a.done)) return;   // the solve has converged
+  unsigned epoch = 0;
 
   // ---- stage the slice (zero-padded) and the factors
   for (int j = t; j < RP; j += kNT) sc[j] = 1.f;
@@ -363,7 +378,7 @@ __global__ void __launch_bounds__(kNT, 1) iterate_persistent_kernel(PArgs a) {
   // prologue: H_tld, H H^T of the initial H into accB[1]
   block_share(CB, RP, LQ + RP, Hs, RP, Hs, RP, RP, Qr, LS, Hs, RP, LQ, red,
               a.accB + (1 * kCopies + blockIdx.x % kCopies) * EB);
-  if (!grid_sync(a.bar, G, a.status, a.abort_flag)) return;
+  if (!grid_sync(a.bar, G, epoch, a.status, a.abort_flag)) return;
 
   for (int it = 0; it < a.iters; ++it) {
     const int ph = it & 1, pr = ph ^ 1;
@@ -379,11 +394,11 @@ __global__ void __launch_bounds__(kNT, 1) iterate_persistent_kernel(PArgs a) {
       }
     }
     __syncthreads();
-    gram_rp<RP>(HtT, LQ, Gw);
+    gram_rp<RP>(HtT, LQ, Gw, invs);
     __syncthreads();
-    for (int slot = t / kGA; slot < ((nrows + 31) & ~31); slot += kNT / kGA) {
+    for (int slot = t / GA; slot < ((nrows + 31) & ~31); slot += kNT / GA) {
       // whole warps take part in the shuffles; rows past the slice compute on zeros
-      const int g = t % kGA;
+      const int g = t % GA;
       const int i = slot < RB ? slot : RB - 1;
       float w[CA], s[CA];
       ld_run<CA>(Ws + i * RP + g * CA, w);
@@ -404,7 +419,7 @@ __global__ void __launch_bounds__(kNT, 1) iterate_persistent_kernel(PArgs a) {
           for (int c = 0; c < CA; ++c) s[c] = fmaf(xk[q], hr[c], s[c]);
         }
       }
-      update_vec<RP, kGA, RULE>(w, s, Gw, g, r, false, 0.f, 0.f, a.eps);
+      update_vec<RP, GA, RULE>(w, s, Gw, invs, g, r, false, 0.f, 0.f, a.eps);
       if (slot < nrows) {
 #pragma unroll
         for (int c = 0; c < CA; c += 2)
@@ -415,7 +430,7 @@ __global__ void __launch_bounds__(kNT, 1) iterate_persistent_kernel(PArgs a) {
     // [Q_L | W]^T W over the slice
     block_share(RB, LQ + RP, RP, Ql, LS, Ws, RP, LQ, Ws, RP, Ws, RP, RP, red,
                 a.accA + (ph * kCopies + blockIdx.x % kCopies) * EA);
-    if (!grid_sync(a.bar, G, a.status, a.abort_flag)) return;
+    if (!grid_sync(a.bar, G, epoch, a.status, a.abort_flag)) return;
 
     // ================= phase B: columns of H
     for (int64_t e = static_cast<int64_t>(blockIdx.x) * kNT + t; e < kCopies * EB;
@@ -431,11 +446,11 @@ __global__ void __launch_bounds__(kNT, 1) iterate_persistent_kernel(PArgs a) {
       for (int e = t; e < LQ * RP; e += kNT) WtS[e] = acc_read(accA_r, EA, e) / sc[e % RP];
     }
     __syncthreads();
-    gram_rp<RP>(WtS, LQ, Gh);
+    gram_rp<RP>(WtS, LQ, Gh, invs);
     __syncthreads();
     float cross = 0.f;
-    for (int slot = t / kGB; slot < ((ncols + 7) & ~7); slot += kNT / kGB) {
-      const int g = t % kGB;
+    for (int slot = t / GB; slot < ((ncols + 31) & ~31); slot += kNT / GB) {
+      const int g = t % GB;
       const int c = slot < CB ? slot : CB - 1;
       float h[CBn], s[CBn];
       ld_run<CBn>(Hs + c * RP + g * CBn, h);
@@ -459,7 +474,7 @@ __global__ void __launch_bounds__(kNT, 1) iterate_persistent_kernel(PArgs a) {
       float shc[CBn];
 #pragma unroll
       for (int z = 0; z < CBn; ++z) shc[z] = s[z];   // S_H column for the monitor
-      update_vec<RP, kGB, RULE>(h, s, Gh, g, r, RULE == 0 && reg, a.alpha, a.beta, a.eps);
+      update_vec<RP, GB, RULE>(h, s, Gh, invs, g, r, RULE == 0 && reg, a.alpha, a.beta, a.eps);
       if (slot < ncols) {
 #pragma unroll
         for (int z = 0; z < CBn; ++z) cross = fmaf(shc[z], h[z], cross);
@@ -479,7 +494,7 @@ __global__ void __launch_bounds__(kNT, 1) iterate_persistent_kernel(PArgs a) {
       for (int wI = 0; wI < kNT / 32; ++wI) csum += wred[wI];
       atomicAdd(&accB_w[RP * (LQ + RP)], csum);
     }
-    if (!grid_sync(a.bar, G, a.status, a.abort_flag)) return;
+    if (!grid_sync(a.bar, G, epoch, a.status, a.abort_flag)) return;
   }
   // the last iteration's monitor terms: cross, and <W^T W, H H^T> for the normalised W
   if (blockIdx.x == 0 && a.iters > 0) {
@@ -519,15 +534,15 @@ __global__ void __launch_bounds__(kNT, 1) iterate_persistent_kernel(PArgs a) {
 
 size_t smem_floats(int RP, int ell, int RB, int CB) {
   const int LQ = lq_of(ell), LS = lsx_of(ell);
-  return static_cast<size_t>(2 * LQ * RP + 2 * RP * RP + RP) + static_cast<size_t>(RB + CB) * RP +
+  return static_cast<size_t>(2 * LQ * RP + 2 * RP * RP + 2 * RP) + static_cast<size_t>(RB + CB) * RP +
          static_cast<size_t>(2 * RB + 2 * CB) * LS + kNT * 16;
 }
 
 int rp_of(int r) { return r <= 8 ? 8 : r <= 16 ? 16 : r <= 24 ? 24 : 32; }
 
-template <int RP, int RULE>
+template <int RP, int RULE, int GA = kGA, int GB = kGB>
 cudaError_t launch(const Launcher& L, PArgs& a, int grid) {
-  auto k = iterate_persistent_kernel<RP, RULE>;
+  auto k = iterate_persistent_kernel<RP, RULE, GA, GB>;
   const size_t smem = sizeof(float) * smem_floats(RP, a.ell, a.RB, a.CB);
   cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));

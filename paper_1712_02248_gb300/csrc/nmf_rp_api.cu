@@ -193,12 +193,13 @@ float eps_of(const nmf_params* p) { return p->eps > 0 ? static_cast<float>(p->ep
 
 // One dual pass with its scratch.
 nmf_status dual(nmf_ctx* ctx, const void* X, bool bf16, int64_t m, int64_t n, int64_t ldx, int ell,
-                const float* V, const float* U, float* Y, float* Z, Arena a, bool simt = false) {
+                const float* V, const float* U, float* Y, float* Z, Arena a, bool simt = false,
+                bool split = false) {
   Phase ph(ctx, NMF_PHASE_DUAL_PASS);
   size_t rest = 0;
   void* ws = a.rest(&rest);
   NMF_CUDA(nmfrp::launch_dual_pass(launcher(ctx), X, bf16, m, n, ldx, ell, V, U, Y, Z, ws, rest,
-                                   ctx->d_status, simt),
+                                   ctx->d_status, simt, split),
            "dual pass");
   return NMF_OK;
 }
@@ -300,8 +301,10 @@ nmf_status compress_impl(nmf_ctx* ctx, const nmf_params* p, const void* X, int64
   const int64_t m = p->m, n = p->n;
   const int l = p->ell;
   float* XhatT = a.take<float>(n * l);
+  // the compressed data feed every iteration and the error monitor: Q_L, Q_R enter the BF16
+  // tensor-core pass as hi + lo pairs so that only X itself is rounded
   nmf_status st = dual(ctx, X, p->prec == NMF_PREC_BF16, m, n, ldx, l, QR, QL, Xchk, XhatT, a,
-                       (p->flags & NMF_FLAG_SIMT_DUAL_PASS) != 0);
+                       (p->flags & NMF_FLAG_SIMT_DUAL_PASS) != 0, true);
   if (st != NMF_OK) return st;
   dim3 grid(static_cast<unsigned>(cdiv(n, 32)), static_cast<unsigned>(cdiv(l, 32)));
   transpose_kernel<<<grid, dim3(32, 8), 0, ctx->stream>>>(XhatT, n, l, Xhat);
@@ -384,8 +387,8 @@ nmf_status take_status(nmf_ctx* ctx) {
 }
 
 // Decide whether the exact residual of this check must run: always for the last check, else
-// when the error monitor (||X||^2 - 2 cross + quad, X replaced by its projection) is within
-// `margin` of the target.
+// when the error monitor (||X||^2 - 2 cross + quad, X replaced by its projection, plus the
+// rounding term of a BF16 copy) is within `margin` of the target.
 __global__ void solve_gate_kernel(const float* mon, const double* solve, double target,
                                   double margin, int force, int* flags) {
   if (flags[0]) {
@@ -396,8 +399,10 @@ __global__ void solve_gate_kernel(const float* mon, const double* solve, double 
     flags[1] = 1;
     return;
   }
+  // solve[3] = <X - X_q, X> when the compressed data come from a BF16 copy X_q (else 0):
+  // <X, W H> ~ <X_hat, W_tld H> + <X - X_q, X>
   const double x2 = solve[0];
-  const double e2 = x2 - 2.0 * static_cast<double>(mon[0]) + static_cast<double>(mon[1]);
+  const double e2 = x2 - 2.0 * (static_cast<double>(mon[0]) + solve[3]) + static_cast<double>(mon[1]);
   const double est = x2 > 0.0 ? sqrt(fmax(e2, 0.0) / x2) : 0.0;
   flags[1] = (est <= target * (1.0 + margin)) ? 1 : 0;
 }
@@ -707,11 +712,17 @@ nmf_status nmf_solve(nmf_ctx* ctx, const nmf_params* p, int32_t init, const floa
   Arena a{static_cast<char*>(ctx->ws), ctx->ws_bytes};
   const void* Xp = X;
   int64_t ldp = ldx;
+  NMF_CUDA(cudaMemsetAsync(ctx->d_solve, 0, 4 * sizeof(double), ctx->stream), "solve state");
   if (p->prec == NMF_PREC_BF16) {
     const int64_t ldq = (n + 7) / 8 * 8;   // row pitch a TMA descriptor can address
     __nv_bfloat16* Xq = a.take<__nv_bfloat16>(m * ldq);
     Phase ph(ctx, NMF_PHASE_QUANTIZE);
-    NMF_CUDA(nmfrp::launch_quantize_bf16(launcher(ctx), X, m, n, ldx, Xq, ldq), "quantize");
+    size_t qrest = 0;
+    void* qws = a.rest(&qrest);
+    // ||X||^2 into solve[0] and the rounding term <X - X_q, X> of the monitor into solve[3]
+    NMF_CUDA(nmfrp::launch_quantize_bf16_stats(launcher(ctx), X, m, n, ldx, Xq, ldq,
+                                               ctx->d_solve, ctx->d_solve + 3, qws, qrest),
+             "quantize");
     Xp = Xq;
     ldp = ldq;
   }
@@ -736,8 +747,8 @@ nmf_status nmf_solve(nmf_ctx* ctx, const nmf_params* p, int32_t init, const floa
   void* ws = a.rest(&rest);
   NMF_CUDA(cudaMemsetAsync(ctx->d_flags, 0, 4 * sizeof(int), ctx->stream), "solve flags");
   NMF_CUDA(cudaMemsetAsync(ctx->d_mon, 0, 4 * sizeof(float), ctx->stream), "solve monitor");
-  NMF_CUDA(cudaMemsetAsync(ctx->d_solve, 0, 4 * sizeof(double), ctx->stream), "solve state");
-  NMF_CUDA(nmfrp::launch_sumsq(launcher(ctx), X, m, n, ldx, ctx->d_solve, ws, rest), "sumsq");
+  if (p->prec != NMF_PREC_BF16)
+    NMF_CUDA(nmfrp::launch_sumsq(launcher(ctx), X, m, n, ldx, ctx->d_solve, ws, rest), "sumsq");
   const bool staged = (p->flags & NMF_FLAG_STAGED_ITERATE) || !nmfrp::iterate_persistent_supported(p->m, p->n, p->r, p->ell);
   cudaEvent_t ev[2] = {pool_event(ctx), pool_event(ctx)};
   if (!ev[0] || !ev[1]) return fail(ctx, NMF_ERR_CUDA, "event creation");
