@@ -83,14 +83,17 @@ __global__ void quantize_bf16_vec4_kernel(const float* __restrict__ X, int64_t m
 }
 
 // BF16 copy plus the two sums the compressed error monitor needs: ||X||^2 and <X - X_q, X>
-// (the rounding of X to BF16 enters the monitor's cross term; this sum removes it). Per element
-// in FP32, per thread and block in FP64, block partials summed in a fixed order.
+// (the rounding of X to BF16 enters the monitor's cross term; this sum removes it). FP32 within
+// runs of 64 elements a thread, FP64 beyond (the FP64 pipe is far narrower than the FP32 one),
+// block partials summed in a fixed order.
 template <bool VEC>
 __global__ void __launch_bounds__(256) quantize_bf16_stats_kernel(
     const float* __restrict__ X, int64_t m, int64_t n, int64_t ldx, __nv_bfloat16* __restrict__ Xq,
     int64_t ldq, double* __restrict__ part) {
   __shared__ double red[2][8];
   double x2 = 0.0, corr = 0.0;
+  float fx2 = 0.f, fcorr = 0.f;
+  int run = 0;
   if (VEC) {
     const int64_t n4 = n / 4, total = m * n4;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
@@ -104,9 +107,15 @@ __global__ void __launch_bounds__(256) quantize_bf16_stats_kernel(
       packed.y = *reinterpret_cast<uint32_t*>(&hi);
       reinterpret_cast<uint2*>(Xq + i * ldq)[j4] = packed;
       const float2 ql = __bfloat1622float2(lo), qh = __bfloat1622float2(hi);
-      x2 += static_cast<double>(fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, v.w * v.w))));
-      corr += static_cast<double>(fmaf(v.x, v.x - ql.x, fmaf(v.y, v.y - ql.y,
-                                   fmaf(v.z, v.z - qh.x, v.w * (v.w - qh.y)))));
+      fx2 = fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, fmaf(v.w, v.w, fx2))));
+      fcorr = fmaf(v.x, v.x - ql.x, fmaf(v.y, v.y - ql.y,
+                   fmaf(v.z, v.z - qh.x, fmaf(v.w, v.w - qh.y, fcorr))));
+      if (++run == 16) {
+        x2 += static_cast<double>(fx2);
+        corr += static_cast<double>(fcorr);
+        fx2 = fcorr = 0.f;
+        run = 0;
+      }
     }
   } else {
     const int64_t total = m * ldq;
@@ -116,10 +125,18 @@ __global__ void __launch_bounds__(256) quantize_bf16_stats_kernel(
       const float x = j < n ? X[i * ldx + j] : 0.f;
       const __nv_bfloat16 q = __float2bfloat16_rn(x);
       Xq[e] = q;
-      x2 += static_cast<double>(x * x);
-      corr += static_cast<double>(x * (x - __bfloat162float(q)));
+      fx2 = fmaf(x, x, fx2);
+      fcorr = fmaf(x, x - __bfloat162float(q), fcorr);
+      if (++run == 64) {
+        x2 += static_cast<double>(fx2);
+        corr += static_cast<double>(fcorr);
+        fx2 = fcorr = 0.f;
+        run = 0;
+      }
     }
   }
+  x2 += static_cast<double>(fx2);
+  corr += static_cast<double>(fcorr);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     x2 += __shfl_xor_sync(0xffffffffu, x2, o);

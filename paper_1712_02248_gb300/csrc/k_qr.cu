@@ -61,9 +61,14 @@ __global__ void __launch_bounds__(kGramThreads) gram_partial_kernel(QrBatch b, i
   __syncthreads();
   constexpr int T2 = LP / 2;
   double* out = Gp + (b.part_off[mat] + blockIdx.x) * LP * LP;
-  for (int tile = t; tile < T2 * T2; tile += kGramThreads) {
-    const int P = tile / T2, Qi = tile - P * T2;
-    if (P > Qi) continue;
+  // upper-triangle tiles only: tile u -> (P, Qi) with P <= Qi, row P holding T2 - P tiles
+  for (int tile = t; tile < T2 * (T2 + 1) / 2; tile += kGramThreads) {
+    int P = 0, u = tile;
+    while (u >= T2 - P) {
+      u -= T2 - P;
+      ++P;
+    }
+    const int Qi = P + u;
     float h00 = 0, h01 = 0, h10 = 0, h11 = 0, l00 = 0, l01 = 0, l10 = 0, l11 = 0;
 #pragma unroll 4
     for (int i = 0; i < kGramRows; ++i) {
