@@ -64,7 +64,7 @@ typedef enum {
 /* nmf_params.flags bits. */
 enum {
   /* run the iterations as one kernel launch per stage instead of one persistent cooperative
-     launch for all iterations (same arithmetic; for comparison and for r > 32, which always
+     launch for all iterations (same arithmetic; for comparison and for r > 48, which always
      uses the per-stage kernels) */
   NMF_FLAG_STAGED_ITERATE = 1,
   /* run BF16 passes over X on the SIMT pipes instead of the tcgen05 tensor-core kernel */
@@ -247,6 +247,32 @@ nmf_status nmf_nndsvd(nmf_ctx* ctx, const nmf_params* p, const float* QL, const 
  */
 nmf_status nmf_solve(nmf_ctx* ctx, const nmf_params* p, int32_t init, const float* X, int64_t ldx,
                      float* W, float* H, double* rel_err_host, int32_t* iters_done_host);
+
+/*
+ * Many independent problems in one call (throughput mode; each problem is the computation of
+ * nmf_solve with a fixed iteration count). Section 2, Eq. 2.2 per problem; Algorithms 3/4 loop.
+ * count >= 1 problems; p[i] their parameters (m, n, r, ell, power_iters, iters, rule, prec,
+ * seed, alpha, beta, eps; residual_every and target_rel_err are not used: every problem runs
+ * p[i].iters iterations). X, ldx, W, H are HOST arrays of count entries holding DEVICE pointers
+ * (X[i]: FP32 m x n, leading dimension ldx[i]; W[i]: m x r, H[i]: r x n in/out, read for
+ * NMF_INIT_GIVEN). init applies to all problems. rows_per_block: rows of W a block of the
+ * iteration kernel takes; each problem runs on ceil(m / rows_per_block) blocks (at least what its
+ * shared-memory slices need, at most the number of SMs), and problems are packed into cooperative
+ * launches that fill the SMs. rows_per_block = 0 lets the autotuner choose among 128, 256, 512
+ * and 1024 rows: on the first call with a given list of (m, n, r, ell, rule) it times 4 iterations
+ * of every candidate on scratch copies of W and H (stream-ordered cudaMallocAsync) and keeps the
+ * fastest for later calls on this context (nmf_last_batch_info reports the choice). rel_err_host[i] receives ||X_i - W_i H_i||_F /
+ * ||X_i||_F after the iterations. The sketch, compression and residuals of different problems
+ * run concurrently on up to 8 internal streams. Synchronises the context stream.
+ * Limits: r <= 48, ell <= 128 per problem. Errors as for nmf_solve; NMF_ERR_UNSUPPORTED if a
+ * problem is outside the limits.
+ */
+nmf_status nmf_solve_batched(nmf_ctx* ctx, int32_t count, const nmf_params* p, int32_t init,
+                             const float* const* X, const int64_t* ldx, float* const* W,
+                             float* const* H, int32_t rows_per_block, double* rel_err_host);
+
+/* Rows per block the last nmf_solve_batched on this context used (autotuned or given). */
+nmf_status nmf_last_batch_info(const nmf_ctx* ctx, int32_t* rows_per_block);
 
 /* Iterations and number of exact residual checks of the last nmf_solve on this context. */
 nmf_status nmf_last_solve_info(const nmf_ctx* ctx, int32_t* iters, int32_t* exact_checks);

@@ -98,7 +98,7 @@ size_t iterate_ws_bytes(int64_t m, int64_t n, int r, int ell);
 cudaError_t launch_iterate(const Launcher& L, const IterArgs& a, int iters, void* ws,
                            size_t ws_bytes);
 
-// All iterations in one cooperative launch (r <= 32); status receives NMF_ERR_TIMEOUT if a
+// All iterations in one cooperative launch (r <= 48); status receives NMF_ERR_TIMEOUT if a
 // grid barrier wait runs out.
 bool iterate_persistent_supported(int64_t m, int64_t n, int r, int ell);
 size_t iterate_persistent_ws_bytes(int r, int ell);
@@ -106,6 +106,15 @@ size_t iterate_persistent_ws_bytes(int r, int ell);
 // if *done is non-zero on entry the launch does nothing.
 cudaError_t launch_iterate_persistent(const Launcher& L, const IterArgs& a, int iters, void* ws,
                                       size_t ws_bytes, int* status, float* mon, const int* done);
+
+// Several independent problems in cooperative launches ("waves" packed into the SMs, one class
+// of padded rank and rule per launch); problem i runs iters[i] iterations on blocks[i] blocks
+// (at least iterate_multi_min_blocks, at most the number of SMs). mon: 2 floats per problem.
+int iterate_multi_min_blocks(int64_t m, int64_t n, int r, int ell);
+size_t iterate_multi_ws_bytes(const IterArgs* ia, int nprob);
+cudaError_t launch_iterate_multi(const Launcher& L, const IterArgs* ia, const int* iters,
+                                 const int* blocks, int nprob, void* ws, size_t ws_bytes,
+                                 int* status, float* mon, const int* done_zero);
 
 // Residual partial sums: writes 2 doubles (||X-WH||^2, ||X||^2) to out2 (device). If gate is
 // non-null and *gate == 0 the kernels return without work.

@@ -37,6 +37,9 @@
 //
 // If *done is set on entry (an earlier residual check reached the target) the kernel returns at
 // once. Every wait is bounded: on time-out the kernel latches NMF_ERR_TIMEOUT and all blocks leave.
+#include <algorithm>
+#include <vector>
+
 #include "common.cuh"
 
 namespace nmfrp {
@@ -320,10 +323,12 @@ __device__ __forceinline__ void update_vec(float* v, float* s, const float* G, c
   }
 }
 
+// The whole run for one problem, executed by `G` co-resident blocks of which this is block
+// `bid` (all blocks of a problem call it with the same arguments).
 template <int RP, int RULE, int GA, int GB>
-__global__ void __launch_bounds__(kNT, 1) iterate_persistent_kernel(PArgs a) {
+__device__ __forceinline__ void iterate_body(const PArgs& a, const unsigned bid, const unsigned G,
+                                             float* sh) {
   constexpr int CA = RP / GA, CBn = RP / GB;
-  extern __shared__ __align__(16) float sh[];
   const int r = a.r, ell = a.ell, t = threadIdx.x;
   const int LQ = lq_of(ell), LS = lsx_of(ell);
   const int EA = ea_size(RP, LQ), EB = eb_size(RP, LQ);
@@ -342,8 +347,7 @@ __global__ void __launch_bounds__(kNT, 1) iterate_persistent_kernel(PArgs a) {
   float* Qr = Xh + CB * LS;         // [CB][LS]   rows of Q_R
   float* red = Qr + CB * LS;        // [kNT * 16] block-share scratch
   __shared__ float wred[kNT / 32];
-  const unsigned G = gridDim.x;
-  const int64_t r0 = static_cast<int64_t>(blockIdx.x) * RB, c0 = static_cast<int64_t>(blockIdx.x) * CB;
+  const int64_t r0 = static_cast<int64_t>(bid) * RB, c0 = static_cast<int64_t>(bid) * CB;
   const int nrows = r0 < a.m ? static_cast<int>(a.m - r0 < RB ? a.m - r0 : RB) : 0;
   const int ncols = c0 < a.n ? static_cast<int>(a.n - c0 < CB ? a.n - c0 : CB) : 0;
   const bool normalize = (RULE == 0);
@@ -377,13 +381,13 @@ __global__ void __launch_bounds__(kNT, 1) iterate_persistent_kernel(PArgs a) {
   __syncthreads();
   // prologue: H_tld, H H^T of the initial H into accB[1]
   block_share(CB, RP, LQ + RP, Hs, RP, Hs, RP, RP, Qr, LS, Hs, RP, LQ, red,
-              a.accB + (1 * kCopies + blockIdx.x % kCopies) * EB);
+              a.accB + (1 * kCopies + bid % kCopies) * EB);
   if (!grid_sync(a.bar, G, epoch, a.status, a.abort_flag)) return;
 
   for (int it = 0; it < a.iters; ++it) {
     const int ph = it & 1, pr = ph ^ 1;
     // ================= phase A: rows of W
-    for (int64_t e = static_cast<int64_t>(blockIdx.x) * kNT + t; e < kCopies * EA;
+    for (int64_t e = static_cast<int64_t>(bid) * kNT + t; e < kCopies * EA;
          e += static_cast<int64_t>(G) * kNT)
       a.accA[pr * kCopies * EA + e] = 0.f;
     {
@@ -429,11 +433,11 @@ __global__ void __launch_bounds__(kNT, 1) iterate_persistent_kernel(PArgs a) {
     __syncthreads();
     // [Q_L | W]^T W over the slice
     block_share(RB, LQ + RP, RP, Ql, LS, Ws, RP, LQ, Ws, RP, Ws, RP, RP, red,
-                a.accA + (ph * kCopies + blockIdx.x % kCopies) * EA);
+                a.accA + (ph * kCopies + bid % kCopies) * EA);
     if (!grid_sync(a.bar, G, epoch, a.status, a.abort_flag)) return;
 
     // ================= phase B: columns of H
-    for (int64_t e = static_cast<int64_t>(blockIdx.x) * kNT + t; e < kCopies * EB;
+    for (int64_t e = static_cast<int64_t>(bid) * kNT + t; e < kCopies * EB;
          e += static_cast<int64_t>(G) * kNT)
       a.accB[pr * kCopies * EB + e] = 0.f;
     {
@@ -487,7 +491,7 @@ __global__ void __launch_bounds__(kNT, 1) iterate_persistent_kernel(PArgs a) {
     for (int o = 16; o > 0; o >>= 1) cross += __shfl_xor_sync(0xffffffffu, cross, o);
     if ((t & 31) == 0) wred[t >> 5] = cross;
     __syncthreads();
-    float* accB_w = a.accB + (ph * kCopies + blockIdx.x % kCopies) * EB;
+    float* accB_w = a.accB + (ph * kCopies + bid % kCopies) * EB;
     block_share(CB, RP, LQ + RP, Hs, RP, Hs, RP, RP, Qr, LS, Hs, RP, LQ, red, accB_w);
     if (t == 0) {
       float csum = 0.f;
@@ -497,7 +501,7 @@ __global__ void __launch_bounds__(kNT, 1) iterate_persistent_kernel(PArgs a) {
     if (!grid_sync(a.bar, G, epoch, a.status, a.abort_flag)) return;
   }
   // the last iteration's monitor terms: cross, and <W^T W, H H^T> for the normalised W
-  if (blockIdx.x == 0 && a.iters > 0) {
+  if (bid == 0 && a.iters > 0) {
     const int ph = (a.iters - 1) & 1;
     const float* accA_r = a.accA + ph * kCopies * EA;
     const float* accB_r = a.accB + ph * kCopies * EB;
@@ -532,15 +536,43 @@ __global__ void __launch_bounds__(kNT, 1) iterate_persistent_kernel(PArgs a) {
   }
 }
 
+template <int RP, int RULE, int GA, int GB>
+__global__ void __launch_bounds__(kNT, 1) iterate_persistent_kernel(PArgs a) {
+  extern __shared__ __align__(16) float sh[];
+  iterate_body<RP, RULE, GA, GB>(a, blockIdx.x, gridDim.x, sh);
+}
+
+// Several independent problems in one cooperative launch: blocks [start[p], start[p + 1]) run
+// problem p with its own sums, barrier counter and abort flag.
+constexpr int kMaxWave = 152;
+struct MultiArgs {
+  int nprob;
+  int start[kMaxWave + 1];
+  PArgs p[kMaxWave];
+};
+
+template <int RP, int RULE, int GA, int GB>
+__global__ void __launch_bounds__(kNT, 1) iterate_multi_kernel(const __grid_constant__ MultiArgs M) {
+  extern __shared__ __align__(16) float sh[];
+  int lo = 0, hi = M.nprob;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (M.start[mid] <= static_cast<int>(blockIdx.x)) lo = mid;
+    else hi = mid;
+  }
+  const PArgs a = M.p[lo];
+  iterate_body<RP, RULE, GA, GB>(a, blockIdx.x - M.start[lo], M.start[lo + 1] - M.start[lo], sh);
+}
+
 size_t smem_floats(int RP, int ell, int RB, int CB) {
   const int LQ = lq_of(ell), LS = lsx_of(ell);
   return static_cast<size_t>(2 * LQ * RP + 2 * RP * RP + 2 * RP) + static_cast<size_t>(RB + CB) * RP +
          static_cast<size_t>(2 * RB + 2 * CB) * LS + kNT * 16;
 }
 
-int rp_of(int r) { return r <= 8 ? 8 : r <= 16 ? 16 : r <= 24 ? 24 : 32; }
+int rp_of(int r) { return r <= 8 ? 8 : r <= 16 ? 16 : r <= 24 ? 24 : r <= 32 ? 32 : 48; }
 
-template <int RP, int RULE, int GA = kGA, int GB = kGB>
+template <int RP, int RULE, int GA = (RP > 32 ? 4 : kGA), int GB = (RP > 32 ? 4 : kGB)>
 cudaError_t launch(const Launcher& L, PArgs& a, int grid) {
   auto k = iterate_persistent_kernel<RP, RULE, GA, GB>;
   const size_t smem = sizeof(float) * smem_floats(RP, a.ell, a.RB, a.CB);
@@ -574,7 +606,7 @@ size_t iterate_persistent_ws_bytes(int r, int ell) {
 }
 
 bool iterate_persistent_supported(int64_t m, int64_t n, int r, int ell) {
-  if (r < 1 || r > 32 || ell < 1 || ell > 128) return false;
+  if (r < 1 || r > 48 || ell < 1 || ell > 128) return false;
   const int grid = num_sms();
   const int64_t rb = (m + grid - 1) / grid, cbk = (n + grid - 1) / grid;
   if (rb > 4096 || cbk > 4096) return false;
@@ -626,8 +658,157 @@ cudaError_t launch_iterate_persistent(const Launcher& L, const IterArgs& ia, int
     case 8: return mu ? launch<8, 1>(L, a, grid) : launch<8, 0>(L, a, grid);
     case 16: return mu ? launch<16, 1>(L, a, grid) : launch<16, 0>(L, a, grid);
     case 24: return mu ? launch<24, 1>(L, a, grid) : launch<24, 0>(L, a, grid);
-    default: return mu ? launch<32, 1>(L, a, grid) : launch<32, 0>(L, a, grid);
+    case 32: return mu ? launch<32, 1>(L, a, grid) : launch<32, 0>(L, a, grid);
+    default: return mu ? launch<48, 1>(L, a, grid) : launch<48, 0>(L, a, grid);
   }
+}
+
+// ---------------------------------------------------------------- several problems at once
+
+namespace {
+
+template <int RP, int RULE, int GA = (RP > 32 ? 4 : kGA), int GB = (RP > 32 ? 4 : kGB)>
+cudaError_t launch_multi(const Launcher& L, const MultiArgs& M, int grid, size_t smem) {
+  auto k = iterate_multi_kernel<RP, RULE, GA, GB>;
+  cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+  if (err != cudaSuccess) return err;
+  int per_sm = 0;
+  if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kNT, smem)) != cudaSuccess)
+    return err;
+  if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
+  void* args[] = {const_cast<MultiArgs*>(&M)};
+  err = cudaLaunchCooperativeKernel(reinterpret_cast<void*>(k), dim3(grid), dim3(kNT), args, smem,
+                                    L.stream);
+  L.count();
+  return err;
+}
+
+cudaError_t launch_multi_rp(int RP, bool mu, const Launcher& L, const MultiArgs& M, int grid,
+                            size_t smem) {
+  switch (RP) {
+    case 8: return mu ? launch_multi<8, 1>(L, M, grid, smem) : launch_multi<8, 0>(L, M, grid, smem);
+    case 16: return mu ? launch_multi<16, 1>(L, M, grid, smem) : launch_multi<16, 0>(L, M, grid, smem);
+    case 24: return mu ? launch_multi<24, 1>(L, M, grid, smem) : launch_multi<24, 0>(L, M, grid, smem);
+    case 32: return mu ? launch_multi<32, 1>(L, M, grid, smem) : launch_multi<32, 0>(L, M, grid, smem);
+    default: return mu ? launch_multi<48, 1>(L, M, grid, smem) : launch_multi<48, 0>(L, M, grid, smem);
+  }
+}
+
+}  // namespace
+
+int iterate_multi_min_blocks(int64_t m, int64_t n, int r, int ell) {
+  if (r < 1 || r > 48 || ell < 1 || ell > 128) return 0;
+  const int sms = num_sms();
+  for (int c = 1; c <= sms; ++c) {
+    const int64_t rb = (m + c - 1) / c, cbk = (n + c - 1) / c;
+    if (rb <= 4096 && cbk <= 4096 &&
+        sizeof(float) * smem_floats(rp_of(r), ell, static_cast<int>(rb), static_cast<int>(cbk)) <=
+            220 * 1024)
+      return c;
+  }
+  return 0;
+}
+
+size_t iterate_multi_ws_bytes(const IterArgs* ia, int nprob) {
+  size_t b = 1024;
+  for (int i = 0; i < nprob; ++i) b += (iterate_persistent_ws_bytes(ia[i].r, ia[i].ell) + 255) / 256 * 256;
+  return b;
+}
+
+cudaError_t launch_iterate_multi(const Launcher& L, const IterArgs* ia, const int* iters,
+                                 const int* blocks, int nprob, void* ws, size_t ws_bytes,
+                                 int* status, float* mon, const int* done_zero) {
+  if (nprob < 1) return cudaSuccess;
+  if (ws_bytes < iterate_multi_ws_bytes(ia, nprob)) return cudaErrorInvalidValue;
+  const int sms = num_sms();
+  // per-problem sums, barrier and abort flag (all zeroed here)
+  std::vector<PArgs> pa(nprob);
+  uintptr_t base = (reinterpret_cast<uintptr_t>(ws) + 255) & ~static_cast<uintptr_t>(255);
+  const uintptr_t first = base;
+  for (int i = 0; i < nprob; ++i) {
+    if (ia[i].r < 1 || ia[i].r > 48 || blocks[i] < iterate_multi_min_blocks(ia[i].m, ia[i].n, ia[i].r, ia[i].ell) ||
+        blocks[i] > sms)
+      return cudaErrorInvalidValue;
+    const int RP = rp_of(ia[i].r), LQ = lq_of(ia[i].ell);
+    const size_t ea = ea_size(RP, LQ), eb = eb_size(RP, LQ);
+    PArgs& a = pa[i];
+    a.m = ia[i].m;
+    a.n = ia[i].n;
+    a.r = ia[i].r;
+    a.ell = ia[i].ell;
+    a.iters = iters[i];
+    a.rule = ia[i].rule;
+    a.alpha = ia[i].alpha;
+    a.beta = ia[i].beta;
+    a.eps = ia[i].eps;
+    a.QL = ia[i].QL;
+    a.QR = ia[i].QR;
+    a.Xhat = ia[i].Xhat;
+    a.Xchk = ia[i].Xchk;
+    a.W = ia[i].W;
+    a.H = ia[i].H;
+    a.accA = reinterpret_cast<float*>(base);
+    a.accB = a.accA + 2 * kCopies * ea;
+    a.bar = reinterpret_cast<Barrier*>(a.accB + 2 * kCopies * eb);
+    a.abort_flag = reinterpret_cast<int*>(a.bar + 1);
+    a.status = status;
+    a.mon = mon + 2 * i;
+    a.done = done_zero;
+    a.RB = static_cast<int>((ia[i].m + blocks[i] - 1) / blocks[i]);
+    a.CB = static_cast<int>((ia[i].n + blocks[i] - 1) / blocks[i]);
+    base += (iterate_persistent_ws_bytes(ia[i].r, ia[i].ell) + 255) / 256 * 256;
+  }
+  cudaError_t err = cudaMemsetAsync(reinterpret_cast<void*>(first), 0, base - first, L.stream);
+  if (err != cudaSuccess) return err;
+  // waves: problems of one (RP, rule) class, largest first, first-fit into the SMs
+  std::vector<int> order(nprob);
+  for (int i = 0; i < nprob; ++i) order[i] = i;
+  std::sort(order.begin(), order.end(), [&](int x, int y) {
+    const int kx = rp_of(ia[x].r) * 2 + ia[x].rule, ky = rp_of(ia[y].r) * 2 + ia[y].rule;
+    if (kx != ky) return kx < ky;
+    return blocks[x] > blocks[y];
+  });
+  size_t at = 0;
+  while (at < order.size()) {
+    const int cls = rp_of(ia[order[at]].r) * 2 + ia[order[at]].rule;
+    size_t end = at;
+    while (end < order.size() && rp_of(ia[order[end]].r) * 2 + ia[order[end]].rule == cls) ++end;
+    // first-fit decreasing over the class
+    std::vector<std::vector<int>> waves;
+    std::vector<int> used;
+    for (size_t q = at; q < end; ++q) {
+      const int i = order[q];
+      size_t w = 0;
+      while (w < waves.size() && (used[w] + blocks[i] > sms || waves[w].size() >= kMaxWave)) ++w;
+      if (w == waves.size()) {
+        waves.emplace_back();
+        used.push_back(0);
+      }
+      waves[w].push_back(i);
+      used[w] += blocks[i];
+    }
+    for (size_t w = 0; w < waves.size(); ++w) {
+      MultiArgs M;
+      M.nprob = static_cast<int>(waves[w].size());
+      int grid = 0;
+      size_t smem = 0;
+      for (int k = 0; k < M.nprob; ++k) {
+        const int i = waves[w][k];
+        M.start[k] = grid;
+        M.p[k] = pa[i];
+        grid += blocks[i];
+        const size_t sm = sizeof(float) * smem_floats(rp_of(ia[i].r), ia[i].ell, pa[i].RB, pa[i].CB);
+        smem = sm > smem ? sm : smem;
+      }
+      M.start[M.nprob] = grid;
+      const int RP = rp_of(ia[waves[w][0]].r);
+      if ((err = launch_multi_rp(RP, ia[waves[w][0]].rule != 0, L, M, grid, smem)) != cudaSuccess)
+        return err;
+    }
+    at = end;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace nmfrp

@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 
+#include <utility>
 #include <vector>
 
 #include "nmf_rp.h"
@@ -38,6 +39,17 @@ struct nmf_ctx {
   std::vector<cudaEvent_t> pool;
   double phase_ms[NMF_PHASE_COUNT] = {0};
   int64_t phase_n[NMF_PHASE_COUNT] = {0};
+  // batched solves: side streams (fork / join through events) and their sizes
+  static constexpr int kSide = 8;
+  cudaStream_t side[kSide] = {};
+  cudaEvent_t side_ev[kSide] = {};
+  cudaEvent_t fork_ev = nullptr;
+  double* d_bres = nullptr;   // 2 doubles per problem
+  double* h_bres = nullptr;
+  int bres_cap = 0;
+  int last_batch_rows_per_block = 0;
+  // autotuned rows per block of the batched iterations, keyed by a hash of the batch's shapes
+  std::vector<std::pair<uint64_t, int>> tuned;
 };
 
 namespace {
@@ -481,6 +493,13 @@ void nmf_destroy(nmf_ctx* ctx) {
   if (ctx->d_flags) cudaFree(ctx->d_flags);
   if (ctx->d_solve) cudaFree(ctx->d_solve);
   if (ctx->h_done) cudaFreeHost(ctx->h_done);
+  for (int i = 0; i < nmf_ctx::kSide; ++i) {
+    if (ctx->side[i]) cudaStreamDestroy(ctx->side[i]);
+    if (ctx->side_ev[i]) cudaEventDestroy(ctx->side_ev[i]);
+  }
+  if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
+  if (ctx->d_bres) cudaFree(ctx->d_bres);
+  if (ctx->h_bres) cudaFreeHost(ctx->h_bres);
   delete ctx;
 }
 
@@ -498,6 +517,12 @@ nmf_status nmf_last_solve_info(const nmf_ctx* ctx, int32_t* iters, int32_t* exac
   if (!ctx) return NMF_ERR_INVALID_ARG;
   if (iters) *iters = ctx->last_iters;
   if (exact_checks) *exact_checks = ctx->last_checks;
+  return NMF_OK;
+}
+
+nmf_status nmf_last_batch_info(const nmf_ctx* ctx, int32_t* rows_per_block) {
+  if (!ctx || !rows_per_block) return NMF_ERR_INVALID_ARG;
+  *rows_per_block = ctx->last_batch_rows_per_block;
   return NMF_OK;
 }
 
@@ -811,6 +836,246 @@ nmf_status nmf_solve(nmf_ctx* ctx, const nmf_params* p, int32_t init, const floa
   if (!(out[1] == out[1]) || out[1] > 1e300) return fail(ctx, NMF_ERR_NOT_FINITE, "residual is not finite");
   if (rel_err_host) *rel_err_host = out[1];
   if (iters_done_host) *iters_done_host = static_cast<int32_t>(out[2]);
+  return take_status(ctx);
+}
+
+nmf_status nmf_solve_batched(nmf_ctx* ctx, int32_t count, const nmf_params* p, int32_t init,
+                             const float* const* X, const int64_t* ldx, float* const* W,
+                             float* const* H, int32_t rows_per_block, double* rel_err_host) {
+  if (!ctx) return NMF_ERR_INVALID_ARG;
+  if (count < 1 || !p || !X || !ldx || !W || !H || !rel_err_host)
+    return fail(ctx, NMF_ERR_INVALID_ARG, "bad batched arguments");
+  if (init != NMF_INIT_GIVEN && init != NMF_INIT_NNDSVD)
+    return fail(ctx, NMF_ERR_INVALID_ARG, "unknown init %d", init);
+  if (rows_per_block < 0) return fail(ctx, NMF_ERR_INVALID_ARG, "rows_per_block < 0");
+  for (int i = 0; i < count; ++i) {
+    nmf_status st = check_params(ctx, &p[i]);
+    if (st != NMF_OK) return st;
+    if (!X[i] || !W[i] || !H[i] || ldx[i] < p[i].n)
+      return fail(ctx, NMF_ERR_INVALID_ARG, "problem %d: bad pointers or ldx", i);
+    if (p[i].iters < 0) return fail(ctx, NMF_ERR_INVALID_ARG, "problem %d: iters < 0", i);
+    if (nmfrp::iterate_multi_min_blocks(p[i].m, p[i].n, p[i].r, p[i].ell) < 1)
+      return fail(ctx, NMF_ERR_UNSUPPORTED, "problem %d: r or ell too large for batching", i);
+  }
+  DeviceGuard g(ctx->device);
+  const int nside = count < nmf_ctx::kSide ? count : nmf_ctx::kSide;
+  for (int k = 0; k < nside; ++k) {
+    if (!ctx->side[k]) {
+      NMF_CUDA(cudaStreamCreateWithFlags(&ctx->side[k], cudaStreamNonBlocking), "side stream");
+      NMF_CUDA(cudaEventCreateWithFlags(&ctx->side_ev[k], cudaEventDisableTiming), "side event");
+    }
+  }
+  if (!ctx->fork_ev) NMF_CUDA(cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming), "fork event");
+  if (ctx->bres_cap < count) {
+    if (ctx->d_bres) cudaFree(ctx->d_bres);
+    if (ctx->h_bres) cudaFreeHost(ctx->h_bres);
+    ctx->d_bres = nullptr;
+    ctx->h_bres = nullptr;
+    ctx->bres_cap = 0;
+    NMF_CUDA(cudaMalloc(&ctx->d_bres, sizeof(double) * 2 * count + sizeof(float) * 2 * count + 64),
+             "batch results");
+    NMF_CUDA(cudaMallocHost(&ctx->h_bres, sizeof(double) * 2 * count), "batch results");
+    ctx->bres_cap = count;
+  }
+  float* d_mon = reinterpret_cast<float*>(ctx->d_bres + 2 * count);
+  // workspace: per problem Q_L, Q_R, X_hat, X_chk; the iteration sums; one scratch per stream
+  std::vector<nmfrp::IterArgs> ia(count);
+  size_t keep = 0, scratch = 0;
+  for (int i = 0; i < count; ++i) {
+    const nmf_params* q = &p[i];
+    keep += sizeof(float) * (2 * (q->m + q->n) * q->ell) + 4 * 256;
+    const int64_t ldq = (q->n + 7) / 8 * 8;
+    size_t s = q->prec == NMF_PREC_BF16 ? 2 * static_cast<size_t>(q->m * ldq) + 256 : 0;
+    size_t rest = sketch_ws(q, true);
+    rest = std::max(rest, sizeof(float) * q->n * q->ell + 1024 + pass_scratch(q->m, q->n, q->ell));
+    rest = std::max(rest, nmfrp::nndsvd_ws_bytes(q->m, q->n, q->r, q->ell));
+    rest = std::max(rest, nmfrp::residual_ws_bytes(q->m, q->n));
+    rest = std::max(rest, nmfrp::quantize_stats_ws_bytes());
+    scratch = std::max(scratch, s + rest + 1024);
+    ia[i].m = q->m;
+    ia[i].n = q->n;
+    ia[i].r = q->r;
+    ia[i].ell = q->ell;
+    ia[i].rule = q->rule;
+    ia[i].alpha = static_cast<float>(q->alpha);
+    ia[i].beta = static_cast<float>(q->beta);
+    ia[i].eps = eps_of(q);
+  }
+  const size_t iter_ws = nmfrp::iterate_multi_ws_bytes(ia.data(), count);
+  nmf_status st = ensure_ws(ctx, keep + iter_ws + nside * scratch + 8192);
+  if (st != NMF_OK) return st;
+  Arena a{static_cast<char*>(ctx->ws), ctx->ws_bytes};
+  for (int i = 0; i < count; ++i) {
+    ia[i].QL = a.take<float>(p[i].m * p[i].ell);
+    ia[i].QR = a.take<float>(p[i].n * p[i].ell);
+    ia[i].Xhat = a.take<float>(p[i].ell * p[i].n);
+    ia[i].Xchk = a.take<float>(p[i].m * p[i].ell);
+    ia[i].W = W[i];
+    ia[i].H = H[i];
+  }
+  char* iter_base = a.take<char>(iter_ws);
+  std::vector<char*> sbase(nside);
+  for (int k = 0; k < nside; ++k) sbase[k] = a.take<char>(scratch);
+  const cudaStream_t main_stream = ctx->stream;
+  auto fork = [&]() -> nmf_status {
+    NMF_CUDA(cudaEventRecord(ctx->fork_ev, main_stream), "fork");
+    for (int k = 0; k < nside; ++k) NMF_CUDA(cudaStreamWaitEvent(ctx->side[k], ctx->fork_ev, 0), "fork");
+    return NMF_OK;
+  };
+  auto join = [&]() -> nmf_status {
+    for (int k = 0; k < nside; ++k) {
+      NMF_CUDA(cudaEventRecord(ctx->side_ev[k], ctx->side[k]), "join");
+      NMF_CUDA(cudaStreamWaitEvent(main_stream, ctx->side_ev[k], 0), "join");
+    }
+    return NMF_OK;
+  };
+  // phase 1: sketch, compression (and NNDSVD) of each problem on its side stream
+  if ((st = fork()) != NMF_OK) return st;
+  for (int i = 0; i < count && st == NMF_OK; ++i) {
+    const int k = i % nside;
+    ctx->stream = ctx->side[k];
+    const nmf_params* q = &p[i];
+    Arena sa{sbase[k], scratch};
+    const void* Xp = X[i];
+    int64_t ldp = ldx[i];
+    if (q->prec == NMF_PREC_BF16) {
+      const int64_t ldq = (q->n + 7) / 8 * 8;
+      __nv_bfloat16* Xq = sa.take<__nv_bfloat16>(q->m * ldq);
+      Phase ph(ctx, NMF_PHASE_QUANTIZE);
+      cudaError_t e = nmfrp::launch_quantize_bf16(launcher(ctx), X[i], q->m, q->n, ldx[i], Xq, ldq);
+      if (e != cudaSuccess) {
+        st = cuda_fail(ctx, e, "quantize");
+        break;
+      }
+      Xp = Xq;
+      ldp = ldq;
+    }
+    if ((st = sketch_impl(ctx, q, Xp, ldp, nullptr, nullptr, const_cast<float*>(ia[i].QL),
+                          const_cast<float*>(ia[i].QR), sa)) != NMF_OK)
+      break;
+    if ((st = compress_impl(ctx, q, Xp, ldp, ia[i].QL, ia[i].QR, const_cast<float*>(ia[i].Xhat),
+                            const_cast<float*>(ia[i].Xchk), sa)) != NMF_OK)
+      break;
+    if (init == NMF_INIT_NNDSVD) {
+      Phase ph(ctx, NMF_PHASE_INIT);
+      size_t rest = 0;
+      void* ws = sa.rest(&rest);
+      cudaError_t e = nmfrp::launch_nndsvd(launcher(ctx), q->m, q->n, q->r, q->ell, ia[i].QL,
+                                           ia[i].Xhat, W[i], H[i], ws, rest, ctx->d_status);
+      if (e != cudaSuccess) st = cuda_fail(ctx, e, "nndsvd");
+    }
+  }
+  ctx->stream = main_stream;
+  if (st != NMF_OK) return st;
+  if ((st = join()) != NMF_OK) return st;
+  // phase 2: every problem's iterations, several problems per cooperative launch
+  {
+    const int sms = [] {
+      int dev = 0, n = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+      return n > 0 ? n : 148;
+    }();
+    std::vector<int> iters(count), blocks(count);
+    auto plan_blocks = [&](int rpb) {
+      for (int i = 0; i < count; ++i) {
+        const int64_t want = (p[i].m + rpb - 1) / rpb;
+        int b = static_cast<int>(want < sms ? want : sms);
+        b = std::max(b, nmfrp::iterate_multi_min_blocks(p[i].m, p[i].n, p[i].r, p[i].ell));
+        blocks[i] = std::max(1, b);
+      }
+    };
+    NMF_CUDA(cudaMemsetAsync(ctx->d_flags + 2, 0, sizeof(int), main_stream), "zero flag");
+    int rpb = rows_per_block;
+    if (rpb == 0) {
+      // autotuner: rows of W per block, timed on a few iterations of scratch copies of W, H
+      uint64_t key = 1469598103934665603ull;
+      for (int i = 0; i < count; ++i)
+        for (int64_t v : {p[i].m, p[i].n, static_cast<int64_t>(p[i].r), static_cast<int64_t>(p[i].ell),
+                          static_cast<int64_t>(p[i].rule)})
+          key = (key ^ static_cast<uint64_t>(v)) * 1099511628211ull;
+      for (const auto& kv : ctx->tuned)
+        if (kv.first == key) rpb = kv.second;
+      if (rpb == 0) {
+        static const int kCand[] = {128, 256, 512, 1024};
+        size_t wh = 0;
+        for (int i = 0; i < count; ++i)
+          wh += (sizeof(float) * p[i].m * p[i].r + 255) / 256 * 256 +
+                (sizeof(float) * p[i].r * p[i].n + 255) / 256 * 256;
+        float* trial = nullptr;
+        NMF_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&trial), wh, main_stream), "tuning copies");
+        std::vector<nmfrp::IterArgs> ta = ia;
+        char* q = reinterpret_cast<char*>(trial);
+        for (int i = 0; i < count; ++i) {
+          ta[i].W = reinterpret_cast<float*>(q);
+          q += (sizeof(float) * p[i].m * p[i].r + 255) / 256 * 256;
+          ta[i].H = reinterpret_cast<float*>(q);
+          q += (sizeof(float) * p[i].r * p[i].n + 255) / 256 * 256;
+        }
+        for (int i = 0; i < count; ++i) iters[i] = std::min(p[i].iters, 4);
+        cudaEvent_t e0 = pool_event(ctx), e1 = pool_event(ctx);
+        float best = 1e30f;
+        for (int c : kCand) {
+          plan_blocks(c);
+          for (int i = 0; i < count; ++i) {
+            NMF_CUDA(cudaMemcpyAsync(ta[i].W, W[i], sizeof(float) * p[i].m * p[i].r,
+                                     cudaMemcpyDeviceToDevice, main_stream), "tuning copy");
+            NMF_CUDA(cudaMemcpyAsync(ta[i].H, H[i], sizeof(float) * p[i].r * p[i].n,
+                                     cudaMemcpyDeviceToDevice, main_stream), "tuning copy");
+          }
+          NMF_CUDA(cudaEventRecord(e0, main_stream), "tuning event");
+          NMF_CUDA(nmfrp::launch_iterate_multi(launcher(ctx), ta.data(), iters.data(),
+                                               blocks.data(), count, iter_base, iter_ws,
+                                               ctx->d_status, d_mon, ctx->d_flags + 2),
+                   "tuning iterations");
+          NMF_CUDA(cudaEventRecord(e1, main_stream), "tuning event");
+          NMF_CUDA(cudaEventSynchronize(e1), "tuning sync");
+          float ms = 0.f;
+          NMF_CUDA(cudaEventElapsedTime(&ms, e0, e1), "tuning time");
+          if (ms < best) {
+            best = ms;
+            rpb = c;
+          }
+        }
+        ctx->pool.push_back(e0);
+        ctx->pool.push_back(e1);
+        NMF_CUDA(cudaFreeAsync(trial, main_stream), "tuning copies");
+        ctx->tuned.emplace_back(key, rpb);
+      }
+    }
+    ctx->last_batch_rows_per_block = rpb;
+    plan_blocks(rpb);
+    for (int i = 0; i < count; ++i) iters[i] = p[i].iters;
+    Phase ph(ctx, NMF_PHASE_ITERATE);
+    NMF_CUDA(nmfrp::launch_iterate_multi(launcher(ctx), ia.data(), iters.data(), blocks.data(),
+                                         count, iter_base, iter_ws, ctx->d_status, d_mon,
+                                         ctx->d_flags + 2),
+             "batched iterations");
+  }
+  // phase 3: exact residual of each problem
+  if ((st = fork()) != NMF_OK) return st;
+  for (int i = 0; i < count && st == NMF_OK; ++i) {
+    const int k = i % nside;
+    ctx->stream = ctx->side[k];
+    Arena sa{sbase[k], scratch};
+    size_t rest = 0;
+    void* ws = sa.rest(&rest);
+    Phase ph(ctx, NMF_PHASE_RESIDUAL);
+    cudaError_t e = nmfrp::launch_residual(launcher(ctx), X[i], p[i].m, p[i].n, ldx[i], W[i], H[i],
+                                           p[i].r, ctx->d_bres + 2 * i, ws, rest);
+    if (e != cudaSuccess) st = cuda_fail(ctx, e, "residual");
+  }
+  ctx->stream = main_stream;
+  if (st != NMF_OK) return st;
+  if ((st = join()) != NMF_OK) return st;
+  NMF_CUDA(cudaMemcpyAsync(ctx->h_bres, ctx->d_bres, sizeof(double) * 2 * count,
+                           cudaMemcpyDeviceToHost, main_stream),
+           "batch results");
+  NMF_CUDA(cudaStreamSynchronize(main_stream), "batch sync");
+  for (int i = 0; i < count; ++i) {
+    const double e2 = ctx->h_bres[2 * i], x2 = ctx->h_bres[2 * i + 1];
+    rel_err_host[i] = x2 > 0 ? std::sqrt(e2 / x2) : std::sqrt(e2);
+  }
   return take_status(ctx);
 }
 

@@ -31,7 +31,7 @@ EXPORTS = ["nmf_create", "nmf_destroy", "nmf_set_stream", "nmf_last_error", "nmf
            "nmf_launch_count", "nmf_workspace_size", "nmf_gaussian", "nmf_quantize",
            "nmf_dual_pass", "nmf_qr", "nmf_sketch", "nmf_compress", "nmf_iterate",
            "nmf_residual", "nmf_residual_static", "nmf_nndsvd", "nmf_solve", "nmf_set_profiling", "nmf_phase_times",
-           "nmf_last_solve_info"]
+           "nmf_last_solve_info", "nmf_solve_batched", "nmf_last_batch_info"]
 PHASES = ["quantize", "dual_pass", "qr", "iterate", "residual", "init"]
 
 
@@ -83,6 +83,10 @@ _c = {
                             [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64), _i32]),
     "nmf_solve": _sig("nmf_solve", ctypes.c_int,
                       [_vp, _P, _i32, _vp, _i64, _vp, _vp, _D, ctypes.POINTER(_i32)]),
+    "nmf_last_batch_info": _sig("nmf_last_batch_info", ctypes.c_int, [_vp, ctypes.POINTER(_i32)]),
+    "nmf_solve_batched": _sig("nmf_solve_batched", ctypes.c_int,
+                              [_vp, _i32, _P, _i32, ctypes.POINTER(_vp), ctypes.POINTER(_i64),
+                               ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i32, _D]),
 }
 
 
@@ -309,6 +313,30 @@ def nmf_solve(ctx, p, X, W, H, init="given"):
                                _ptr(_dev_f32(W, "W")), _ptr(_dev_f32(H, "H")), ctypes.byref(rel),
                                ctypes.byref(it)))
     return rel.value, it.value
+
+
+def nmf_solve_batched(ctx, ps, Xs, Ws, Hs, init="given", rows_per_block=0):
+    """Independent problems in one call: ps, Xs, Ws, Hs are equal-length lists (params structs,
+    FP32 X, in/out W, H CUDA tensors). Returns the list of final relative residuals."""
+    k = len(ps)
+    if not (len(Xs) == len(Ws) == len(Hs) == k) or k == 0:
+        raise ValueError("ps, Xs, Ws, Hs must be non-empty lists of equal length")
+    arr = (nmf_params * k)(*ps)
+    xp = (_vp * k)(*[_vp(_x_arg(x, 0)[0].data_ptr()) for x in Xs])
+    ld = (_i64 * k)(*[x.stride(0) for x in Xs])
+    wp = (_vp * k)(*[_vp(_dev_f32(w, "W").data_ptr()) for w in Ws])
+    hp = (_vp * k)(*[_vp(_dev_f32(h, "H").data_ptr()) for h in Hs])
+    out = (ctypes.c_double * k)()
+    ctx._check(_c["nmf_solve_batched"](ctx.handle, k, arr, INIT.get(init, init), xp, ld, wp, hp,
+                                       int(rows_per_block), out))
+    return list(out)
+
+
+def nmf_last_batch_info(ctx):
+    """Rows of W per block the last batched solve used (autotuned when 0 was passed)."""
+    v = _i32()
+    ctx._check(_c["nmf_last_batch_info"](ctx.handle, ctypes.byref(v)))
+    return v.value
 
 
 def nmf_set_profiling(ctx, on=True):

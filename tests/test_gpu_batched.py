@@ -1,0 +1,145 @@
+"""Batched solves: many independent problems of uneven m, n, r in one call (nmf_solve_batched).
+
+Each problem of a batch is the computation of nmf_solve with a fixed iteration count: the
+batched call must give every problem the relative residual that nmf_solve gives it alone (the
+two differ only in the order of cross-block sums, within 1e-4 relative), and stay within 1 % of
+the FP64 oracle run on the same Omega and initial factors.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_1712_02248_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture
+def ctx(lib):
+    c = lib.Context(0)
+    yield c
+    c.close()
+
+
+def cu(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to("cuda")
+
+
+def make_batch(specs, seed):
+    probs = []
+    for k, (m, n, r, ell) in enumerate(specs):
+        probs.append(inputs.random_problem(seed + k, m, n, r, ell, w=2))
+    return probs
+
+
+SPECS = [(700, 300, 5, 15), (1500, 900, 40, 50), (333, 517, 12, 22), (2048, 256, 8, 18),
+         (900, 1200, 20, 30), (513, 211, 33, 43), (1200, 700, 17, 27), (260, 900, 3, 13),
+         (1800, 1300, 26, 36), (640, 640, 10, 20), (1100, 450, 31, 41), (405, 1999, 24, 34)]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_batched_matches_single_solves(lib, ctx, prec):
+    probs = make_batch(SPECS, 100)
+    iters = 40
+    ps, Xs, Ws, Hs, single = [], [], [], [], []
+    for k, pr in enumerate(probs):
+        m, n = pr.X.shape
+        p = lib.params(m, n, pr.r, pr.ell, power_iters=2, iters=iters, prec=prec, seed=7 + k)
+        X = cu(pr.X)
+        W, H = cu(pr.W0), cu(pr.H0)
+        e, it = lib.nmf_solve(ctx, p, X, W, H)
+        assert it == iters
+        single.append(e)
+        ps.append(p)
+        Xs.append(X)
+        Ws.append(cu(pr.W0))
+        Hs.append(cu(pr.H0))
+    got = lib.nmf_solve_batched(ctx, ps, Xs, Ws, Hs)
+    for k, (g, s) in enumerate(zip(got, single)):
+        assert abs(g - s) <= 1e-4 * s, f"problem {k}: batched {g} vs single {s}"
+        assert (Ws[k] >= 0).all() and (Hs[k] >= 0).all()
+        # the returned factors are the ones the residual was taken on
+        rr = lib.nmf_residual(ctx, ps[k], Xs[k], Ws[k], Hs[k])[0]
+        assert abs(rr - g) <= 1e-6 * g
+
+
+def test_batched_blocks_per_problem_do_not_change_results(lib, ctx):
+    """rows_per_block only changes how many blocks a problem runs on (and so the order of the
+    cross-block sums)."""
+    probs = make_batch(SPECS[:6], 200)
+    outs = []
+    for rpb in (64, 256, 1024):
+        ps, Xs, Ws, Hs = [], [], [], []
+        for k, pr in enumerate(probs):
+            m, n = pr.X.shape
+            ps.append(lib.params(m, n, pr.r, pr.ell, power_iters=2, iters=30, seed=3 + k))
+            Xs.append(cu(pr.X))
+            Ws.append(cu(pr.W0))
+            Hs.append(cu(pr.H0))
+        outs.append(np.array(lib.nmf_solve_batched(ctx, ps, Xs, Ws, Hs, rows_per_block=rpb)))
+    assert np.max(np.abs(outs[0] - outs[1]) / outs[1]) <= 1e-4
+    assert np.max(np.abs(outs[2] - outs[1]) / outs[1]) <= 1e-4
+
+
+def test_batched_against_oracle(lib, ctx):
+    """Two problems of the batch against the FP64 oracle on the same Omega (drawn by the
+    library's generator and handed to the oracle) and initial factors: final relative residual
+    within 1 % after the same iterations."""
+    specs = [(600, 400, 6, 16), (900, 350, 35, 45), (300, 800, 14, 24)]
+    probs = make_batch(specs, 300)
+    iters = 25
+    ps, Xs, Ws, Hs = [], [], [], []
+    for k, pr in enumerate(probs):
+        m, n = pr.X.shape
+        ps.append(lib.params(m, n, pr.r, pr.ell, power_iters=2, iters=iters, seed=11 + k))
+        Xs.append(cu(pr.X))
+        Ws.append(cu(pr.W0))
+        Hs.append(cu(pr.H0))
+    got = lib.nmf_solve_batched(ctx, ps, Xs, Ws, Hs)
+    for k, pr in enumerate(probs):
+        m, n = pr.X.shape
+        oL = lib.nmf_gaussian(ctx, n, pr.ell, 11 + k, 0).double().cpu().numpy()
+        oR = lib.nmf_gaussian(ctx, m, pr.ell, 11 + k, 1).double().cpu().numpy()
+        _, _, _, _, hist = O.solve(pr.X.astype(np.float64), oL, oR, pr.W0, pr.H0, 2, iters)
+        ro = hist[-1][1]
+        assert abs(got[k] - ro) <= 0.01 * ro, f"problem {k}: {got[k]} vs oracle {ro}"
+
+
+def test_batched_rejects_bad_arguments(lib, ctx):
+    pr = inputs.random_problem(5, 300, 200, 4, 10)
+    p = lib.params(300, 200, 4, 10, iters=5)
+    X, W, H = cu(pr.X), cu(pr.W0), cu(pr.H0)
+    with pytest.raises(lib.NmfError):
+        lib.nmf_solve_batched(ctx, [p], [X], [W], [H], rows_per_block=-1)
+    big = lib.params(300, 200, 60, 70, iters=5)    # r above the batched limit of 48
+    W2 = cu(np.random.default_rng(0).random((300, 60), dtype=np.float32))
+    H2 = cu(np.random.default_rng(1).random((60, 200), dtype=np.float32))
+    with pytest.raises(lib.NmfError) as e:
+        lib.nmf_solve_batched(ctx, [big], [X], [W2], [H2])
+    assert e.value.status == 7
+
+
+def test_batched_autotuner_picks_a_candidate_and_keeps_results(lib, ctx):
+    """rows_per_block = 0: the autotuner times the candidates on scratch copies, so the factors
+    it returns are those of a plain run with the chosen setting."""
+    probs = make_batch(SPECS[:5], 400)
+
+    def run(rpb):
+        ps, Xs, Ws, Hs = [], [], [], []
+        for k, pr in enumerate(probs):
+            m, n = pr.X.shape
+            ps.append(lib.params(m, n, pr.r, pr.ell, power_iters=2, iters=20, seed=5 + k))
+            Xs.append(cu(pr.X))
+            Ws.append(cu(pr.W0))
+            Hs.append(cu(pr.H0))
+        return np.array(lib.nmf_solve_batched(ctx, ps, Xs, Ws, Hs, rows_per_block=rpb))
+
+    auto = run(0)
+    chosen = lib.nmf_last_batch_info(ctx)
+    assert chosen in (128, 256, 512, 1024)
+    again = run(0)                      # cached choice
+    assert lib.nmf_last_batch_info(ctx) == chosen
+    fixed = run(chosen)
+    assert np.max(np.abs(auto - fixed) / fixed) <= 1e-4
+    assert np.max(np.abs(again - fixed) / fixed) <= 1e-4
