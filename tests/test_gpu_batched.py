@@ -143,3 +143,31 @@ def test_batched_autotuner_picks_a_candidate_and_keeps_results(lib, ctx):
     fixed = run(chosen)
     assert np.max(np.abs(auto - fixed) / fixed) <= 1e-4
     assert np.max(np.abs(again - fixed) / fixed) <= 1e-4
+
+
+def test_batched_graph_replay_matches_eager_run(lib, ctx):
+    """Without per-phase timing the sketch / compression phase is captured in a CUDA graph and
+    replayed on later calls with the same inputs; with timing on it runs eagerly. All three runs
+    give the same residuals (up to the order of the iterations' cross-block sums)."""
+    probs = make_batch(SPECS[:7], 500)
+
+    def run():
+        ps, Xs, Ws, Hs = [], [], [], []
+        for k, pr in enumerate(probs):
+            m, n = pr.X.shape
+            ps.append(lib.params(m, n, pr.r, pr.ell, power_iters=2, iters=15, prec="bf16",
+                                 seed=9 + k))
+            Xs.append(X_dev[k])
+            Ws.append(cu(pr.W0))
+            Hs.append(cu(pr.H0))
+        return np.array(lib.nmf_solve_batched(ctx, ps, Xs, Ws, Hs, rows_per_block=256))
+
+    X_dev = [cu(pr.X) for pr in probs]
+    lib.nmf_set_profiling(ctx, True)
+    eager = run()
+    lib.nmf_set_profiling(ctx, False)
+    lib.nmf_phase_times(ctx)
+    first = run()       # captures and launches the graph
+    second = run()      # replays it
+    assert np.max(np.abs(first - eager) / eager) <= 1e-4
+    assert np.max(np.abs(second - eager) / eager) <= 1e-4
