@@ -449,3 +449,87 @@ def test_philox_normal_box_muller_pairs():
     u0 = ((x[0] >> 8) + 0.5) * 2.0 ** -24
     assert abs(Z[0] ** 2 + Z[1] ** 2 + 2 * np.log(u0)) <= 1e-12
     assert abs(Z.mean()) < 0.06 and abs(Z.std() - 1) < 0.05
+
+
+# ---------------------------------------------------------------- learned warm start
+
+from oracle import warmstart_oracle as WS  # noqa: E402
+
+
+def test_bf16_round_exact_values():
+    """Round to nearest, ties to even, at the 8-bit significand of bfloat16."""
+    u = 2.0 ** -7    # spacing of bfloat16 in [1, 2)
+    x = np.array([1.0, 1 + u / 2, 1 + 3 * u / 2, 1 + u / 4, 1 + 3 * u / 4, -3.0, 1 + u])
+    want = np.array([1.0, 1.0, 1 + 2 * u, 1.0, 1 + u, -3.0, 1 + u])
+    assert np.array_equal(WS.bf16_round(x), want)
+
+
+def test_mlp_gradient_matches_finite_differences():
+    """Every component of the gradient against a central difference of the loss (on the
+    unrounded network, where the loss is smooth away from ReLU kinks)."""
+    F, Hd, r, B = 5, 7, 3, 6
+    rng = np.random.default_rng(0)
+    p = rng.standard_normal(WS.mlp_param_count(F, Hd, r)) * 0.5
+    X = rng.standard_normal((B, F))
+    T = rng.standard_normal((B, r))
+    _, g = WS.mlp_loss_grad(p, X, T, F, Hd, r, round_weights=False)
+    h = 1e-6
+    fd = np.empty_like(p)
+    for k in range(p.size):
+        e = np.zeros_like(p)
+        e[k] = h
+        lp, _ = WS.mlp_loss_grad(p + e, X, T, F, Hd, r, round_weights=False)
+        lm, _ = WS.mlp_loss_grad(p - e, X, T, F, Hd, r, round_weights=False)
+        fd[k] = (lp - lm) / (2 * h)
+    assert np.max(np.abs(fd - g)) <= 1e-7 * max(1.0, np.max(np.abs(g)))
+
+
+def test_mlp_rounded_gradient_is_gradient_at_rounded_weights():
+    F, Hd, r = 4, 6, 2
+    rng = np.random.default_rng(1)
+    p = rng.standard_normal(WS.mlp_param_count(F, Hd, r))
+    X, T = rng.standard_normal((5, F)), rng.standard_normal((5, r))
+    W1, b1, W2, b2, W3, b3 = WS.mlp_unpack(p, F, Hd, r)
+    q = np.concatenate([WS.bf16_round(W1).ravel(), b1, WS.bf16_round(W2).ravel(), b2,
+                        WS.bf16_round(W3).ravel(), b3])
+    l1, g1 = WS.mlp_loss_grad(p, X, T, F, Hd, r)
+    l2, g2 = WS.mlp_loss_grad(q, X, T, F, Hd, r, round_weights=False)
+    assert l1 == l2 and np.array_equal(g1, g2)
+
+
+def test_adam_first_step_closed_form():
+    """Step 1 of Adam moves every parameter by lr * g / (|g| + eps) (bias correction makes the
+    moment estimates g and g^2)."""
+    rng = np.random.default_rng(2)
+    p, g = rng.standard_normal(9), rng.standard_normal(9)
+    q, m, v = WS.adam_step(p, np.zeros(9), np.zeros(9), g, 1, 1e-3)
+    assert np.allclose(q, p - 1e-3 * g / (np.abs(g) + WS.ADAM_EPS), rtol=0, atol=1e-15)
+    assert np.allclose(m, 0.1 * g) and np.allclose(v, 0.001 * g * g)
+
+
+def test_warmstart_features_reproduce_nndsvd():
+    """W_b has unit (or zero) columns, W_b H_b is the NNDSVD product, and an untrained network
+    (zero last layer) returns exactly W_b, H_b."""
+    rng = np.random.default_rng(3)
+    m, n, ell, r = 300, 200, 12, 5
+    QL = np.linalg.qr(rng.standard_normal((m, ell)))[0]
+    Xhat = rng.standard_normal((ell, n)) * (0.7 ** np.arange(ell))[:, None]
+    Wb, Hb, hs, Fw, Fh = WS.warmstart_features(QL, Xhat, r)
+    Wn, Hn = O.nndsvd_compressed(QL, Xhat, r)
+    norms = np.linalg.norm(Wb, axis=0)
+    assert np.all((np.abs(norms - 1) < 1e-12) | (norms == 0))
+    assert np.allclose(Wb @ Hb, Wn @ Hn, rtol=0, atol=1e-12 * np.abs(Wn @ Hn).max())
+    assert np.allclose(np.linalg.norm(Hb, axis=1), hs)
+    assert Fw.shape == (m, 3 * r) and Fh.shape == (n, 3 * r)
+    F, Hd = 3 * r, 16
+    p = WS.mlp_init(F, Hd, r, seed=4)
+    Dw, _ = WS.mlp_forward(p, Fw, F, Hd, r)
+    Dh, _ = WS.mlp_forward(p, Fh, F, Hd, r)
+    W0, H0 = WS.warmstart_apply(Wb, Hb, hs, Dw, Dh)
+    assert np.array_equal(W0, Wb) and np.array_equal(H0, Hb)
+    # targets invert the map where the solution is positive
+    Ws = np.abs(Wb + 0.01 * rng.standard_normal(Wb.shape)) + 0.1
+    Hs = np.abs(Hb + 0.01 * rng.standard_normal(Hb.shape)) + 0.1
+    Tw, Th = WS.warmstart_targets(Wb, Hb, hs, Ws, Hs)
+    W1, H1 = WS.warmstart_apply(Wb, Hb, hs, Tw, Th)
+    assert np.allclose(W1, Ws) and np.allclose(H1[hs > 0], Hs[hs > 0])
