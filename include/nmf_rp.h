@@ -58,7 +58,8 @@ typedef enum {
 /* Initialisation used by nmf_solve. */
 typedef enum {
   NMF_INIT_GIVEN = 0,        /* W, H hold the caller's initial factors */
-  NMF_INIT_NNDSVD = 1        /* NNDSVD of the compressed data (Boutsidis & Gallopoulos 2008) */
+  NMF_INIT_NNDSVD = 1,       /* NNDSVD of the compressed data (Boutsidis & Gallopoulos 2008) */
+  NMF_INIT_MLP = 2           /* NNDSVD corrected by the learned warm start (nmf_set_warmstart) */
 } nmf_init;
 
 /* nmf_params.flags bits. */
@@ -232,6 +233,58 @@ nmf_status nmf_residual_static(int32_t device, void* stream, const float* X, int
  * the FP32 eigensolver gives eigenvector j an error of about l * eps32 * lambda_1 / gap_j. */
 nmf_status nmf_nndsvd(nmf_ctx* ctx, const nmf_params* p, const float* QL, const float* Xhat,
                       float* W, float* H);
+
+/*
+ * Learned warm start. The paper starts from random factors (Section 5); NNDSVD of the compressed
+ * data (above) corrected row by row by a small network trained on solutions of the compressed NMF
+ * itself is a faster start. Definitions (r components; u_j, v_j, s_j the singular triplets of
+ * X ~ Q_L X_hat; p(x) the part of x NNDSVD keeps: |x| for j = 0, else x+ or x- by the larger
+ * product of norms, or nothing):
+ *   W_b[:, j] = p(u_j) / ||p(u_j)||,  H_b[j, :] = hscale_j p(v_j) / ||p(v_j)||,
+ *   hscale_j = s_j ||p(u_j)|| ||p(v_j)||            (W_b H_b is the NNDSVD product)
+ *   F_w[i] = [sqrt(m) c_j u_ij, sqrt(m) W_b[i, j], s_j / s_0]  (j < r; m x 3r, row-major)
+ *   F_h[c] = [sqrt(n) c_j v_cj, sqrt(n) H_b[j, c] / hscale_j, s_j / s_0]  (n x 3r)
+ *   with c_j u = |u| (j = 0), u (positive part kept), -u (negative part kept), 0 (none)
+ *   W_0 = max(0, W_b + D_w / sqrt(m)),  H_0[j][c] = max(0, H_b[j][c] + hscale_j D_h[c][j] / sqrt(n))
+ *   with D_w = net_W(F_w) (m x r) and D_h = net_H(F_h) (n x r).
+ * A network (F inputs, two hidden ReLU layers of `hidden` units, r outputs) is one FP32 vector
+ * [W1 (F x hidden), b1 (hidden), W2 (hidden x hidden), b2, W3 (hidden x r), b3 (r)], matrices
+ * row-major, owned by the caller (device memory). The weight matrices are rounded to BF16 (round
+ * to nearest even) wherever they enter a product; biases, activations and accumulation are FP32.
+ * Loss: mean squared error over rows x r outputs; gradients are those of the rounded weights,
+ * laid out like the parameters.
+ */
+/* Number of parameters of a network (F inputs, hidden units, r outputs); -1 for bad sizes. */
+int64_t nmf_mlp_param_count(int32_t F, int32_t hidden, int32_t r);
+/* W_b (m x r), H_b (r x n), hscale (r), F_w (m x 3r), F_h (n x 3r) from Q_L (m x l) and
+ * X_hat (l x n); device arrays owned by the caller. r <= 64, l <= 128. */
+nmf_status nmf_warmstart_features(nmf_ctx* ctx, const nmf_params* p, const float* QL,
+                                  const float* Xhat, float* Wb, float* Hb, float* hscale,
+                                  float* Fw, float* Fh);
+/* Y (rows x r) = network(X) for X (rows x F); device arrays. */
+nmf_status nmf_mlp_forward(nmf_ctx* ctx, int32_t F, int32_t hidden, int32_t r,
+                           const float* params, const float* X, int64_t rows, float* Y);
+/* grad (param_count floats, device) of the loss of network(X) against T (rows x r); the loss is
+ * written to *loss_host when it is not NULL (this synchronises). */
+nmf_status nmf_mlp_loss_grad(nmf_ctx* ctx, int32_t F, int32_t hidden, int32_t r,
+                             const float* params, const float* X, const float* T, int64_t rows,
+                             float* grad, double* loss_host);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias correction for step >= 1) on `count`
+ * parameters with moment buffers m, v (device, zero before step 1). */
+nmf_status nmf_mlp_adam(nmf_ctx* ctx, int64_t count, float* params, float* m, float* v,
+                        const float* grad, int32_t step, float lr);
+/* nmf_mlp_loss_grad into `grad` followed by nmf_mlp_adam. */
+nmf_status nmf_mlp_train_step(nmf_ctx* ctx, int32_t F, int32_t hidden, int32_t r, float* params,
+                              float* m, float* v, float* grad, int32_t step, float lr,
+                              const float* X, const float* T, int64_t rows, double* loss_host);
+/* W (m x r), H (r x n) from W_b, H_b, hscale and the two network outputs (definitions above). */
+nmf_status nmf_warmstart_apply(nmf_ctx* ctx, int64_t m, int64_t n, int32_t r, const float* Wb,
+                               const float* Dw, const float* Hb, const float* Dh,
+                               const float* hscale, float* W, float* H);
+/* Copy the two networks (F = 3r inputs, host or device memory) into the context for
+ * NMF_INIT_MLP; problems with another r are refused at solve time. */
+nmf_status nmf_set_warmstart(nmf_ctx* ctx, int32_t hidden, int32_t r, const float* params_w,
+                             const float* params_h);
 
 /*
  * Whole pipeline on FP32 X (m x n, leading dimension ldx): sketch (Omega from p->seed), compress,

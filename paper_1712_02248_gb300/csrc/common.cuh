@@ -136,4 +136,23 @@ cudaError_t launch_nndsvd(const Launcher& L, int64_t m, int64_t n, int r, int el
                           const float* QL, const float* Xhat, float* W, float* H, void* ws,
                           size_t ws_bytes, int* status);
 
+// Learned warm start: NNDSVD-based W_b (m x r), H_b (r x n), hscale (r) and row features F_w
+// (m x 3r), F_h (n x 3r); nndsvd_ws_bytes of workspace.
+cudaError_t launch_warmstart_features(const Launcher& L, int64_t m, int64_t n, int r, int ell,
+                                      const float* QL, const float* Xhat, float* Wb, float* Hb,
+                                      float* hscale, float* Fw, float* Fh, void* ws,
+                                      size_t ws_bytes);
+int64_t mlp_param_count(int F, int Hd, int r);
+size_t mlp_ws_bytes(int64_t rows, int Hd, int r);
+cudaError_t launch_mlp_forward(const Launcher& L, int F, int Hd, int r, const float* params,
+                               const float* X, int64_t rows, float* Y, void* ws, size_t ws_bytes);
+cudaError_t launch_mlp_loss_grad(const Launcher& L, int F, int Hd, int r, const float* params,
+                                 const float* X, const float* T, int64_t rows, float* grad,
+                                 double* loss, void* ws, size_t ws_bytes);
+cudaError_t launch_adam(const Launcher& L, float* p, float* m, float* v, const float* g,
+                        int64_t count, float lr, int step);
+cudaError_t launch_warmstart_apply(const Launcher& L, int64_t m, int64_t n, int r,
+                                   const float* Wb, const float* Dw, const float* Hb,
+                                   const float* Dh, const float* hscale, float* W, float* H);
+
 }  // namespace nmfrp

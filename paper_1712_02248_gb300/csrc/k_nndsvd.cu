@@ -344,13 +344,102 @@ int blocks_for(int64_t work) {
   return static_cast<int>(b < 1 ? 1 : (b > 1024 ? 1024 : b));
 }
 
+// Warm-start features. Per component j (one thread each): the sign part NNDSVD keeps (mode as
+// in nndsvd_coef_kernel), 1 / ||p(u_j)||, 1 / ||p(v_j)||, f2_j = sigma_j ||p(u_j)|| ||p(v_j)||
+// and sigma_j / sigma_0. cw: [mode, inu, inv, f2, ratio] x r.
+__global__ void ws_coef_kernel(const double* __restrict__ upart, int nu,
+                               const double* __restrict__ vpart, int nv, int r,
+                               const float* __restrict__ sigma, float* __restrict__ cw,
+                               float* __restrict__ hscale) {
+  const int j = threadIdx.x;
+  if (j >= r) return;
+  double up = 0, un = 0, vp = 0, vn = 0;
+  for (int b = 0; b < nu; ++b) {
+    up += upart[b * 2 * r + j];
+    un += upart[b * 2 * r + r + j];
+  }
+  for (int b = 0; b < nv; ++b) {
+    vp += vpart[b * 2 * r + j];
+    vn += vpart[b * 2 * r + r + j];
+  }
+  int mode;
+  double nx, ny;
+  if (j == 0) {
+    mode = 0;
+    nx = sqrt(up + un);
+    ny = sqrt(vp + vn);
+  } else {
+    const double mp = sqrt(up) * sqrt(vp), mn = sqrt(un) * sqrt(vn);
+    if (mp >= mn) {
+      mode = mp > 0.0 ? 1 : 3;
+      nx = sqrt(up);
+      ny = sqrt(vp);
+    } else {
+      mode = 2;
+      nx = sqrt(un);
+      ny = sqrt(vn);
+    }
+  }
+  const bool live = mode != 3 && nx > 0.0 && ny > 0.0;
+  const double f2 = live ? static_cast<double>(sigma[j]) * nx * ny : 0.0;
+  cw[j] = static_cast<float>(mode);
+  cw[r + j] = live ? static_cast<float>(1.0 / nx) : 0.f;
+  cw[2 * r + j] = live ? static_cast<float>(1.0 / ny) : 0.f;
+  cw[3 * r + j] = static_cast<float>(f2);
+  cw[4 * r + j] = sigma[0] > 0.f ? sigma[j] / sigma[0] : 0.f;
+  hscale[j] = static_cast<float>(f2);
+}
+
+__device__ __forceinline__ float signed_part(float x, int mode) {
+  if (mode == 0) return fabsf(x);
+  if (mode == 1) return x;
+  if (mode == 2) return -x;
+  return 0.f;
+}
+
+// W side (in place on U -> W_b) and H side (in place on V -> H_b), features F_w (m x 3r),
+// F_h (n x 3r).
+__global__ void ws_feature_kernel(float* __restrict__ Wb, int64_t m, float* __restrict__ Hb,
+                                  int64_t n, int r, const float* __restrict__ cw,
+                                  float* __restrict__ Fw, float* __restrict__ Fh) {
+  const int64_t tw = m * r, th = static_cast<int64_t>(r) * n;
+  const float sm = sqrtf(static_cast<float>(m)), sn = sqrtf(static_cast<float>(n));
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tw + th;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    if (e < tw) {
+      const int64_t i = e / r;
+      const int j = static_cast<int>(e - i * r);
+      const int mode = static_cast<int>(cw[j]);
+      const float x = Wb[e];
+      const float w = part_of(x, mode) * cw[r + j];
+      Wb[e] = w;
+      float* f = Fw + i * 3 * r;
+      f[j] = sm * signed_part(x, mode);
+      f[r + j] = sm * w;
+      f[2 * r + j] = cw[4 * r + j];
+    } else {
+      const int64_t g = e - tw;
+      const int j = static_cast<int>(g / n);
+      const int64_t c = g - static_cast<int64_t>(j) * n;
+      const int mode = static_cast<int>(cw[j]);
+      const float y = Hb[g];
+      const float h = part_of(y, mode) * cw[2 * r + j];
+      Hb[g] = cw[3 * r + j] * h;
+      float* f = Fh + c * 3 * r;
+      f[j] = sn * signed_part(y, mode);
+      f[r + j] = sn * h;
+      f[2 * r + j] = cw[4 * r + j];
+    }
+  }
+}
+
 }  // namespace
 
 size_t nndsvd_ws_bytes(int64_t m, int64_t n, int r, int ell) {
   const int64_t slabs = cdiv(n, kSlabCols);
   const int bu = blocks_for(m), bv = blocks_for(n);
   return sizeof(double) * ((slabs + 1) * ell * ell + 2 * r * (bu + bv)) +
-         sizeof(float) * (ell * r + r + 3 * r) + 4096;
+         sizeof(float) * (ell * r + r + 5 * r) + 4096;
 }
 
 cudaError_t launch_nndsvd(const Launcher& L, int64_t m, int64_t n, int r, int ell,
@@ -386,6 +475,43 @@ cudaError_t launch_nndsvd(const Launcher& L, int64_t m, int64_t n, int r, int el
   v_cols_kernel<<<bv, 256, 0, L.stream>>>(Xhat, n, ell, r, Ur, sigma, H, vpart);
   nndsvd_coef_kernel<<<1, 64, 0, L.stream>>>(upart, bu, vpart, bv, r, sigma, coef);
   nndsvd_apply_kernel<<<blocks_for(m * r + r * n), 256, 0, L.stream>>>(W, m, H, n, r, coef);
+  L.count(7);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_warmstart_features(const Launcher& L, int64_t m, int64_t n, int r, int ell,
+                                      const float* QL, const float* Xhat, float* Wb, float* Hb,
+                                      float* hscale, float* Fw, float* Fh, void* ws,
+                                      size_t ws_bytes) {
+  if (ell > kMaxL || r > 64 || r > ell) return cudaErrorNotSupported;
+  if (ws_bytes < nndsvd_ws_bytes(m, n, r, ell)) return cudaErrorInvalidValue;
+  const int64_t slabs = cdiv(n, kSlabCols);
+  const int bu = blocks_for(m), bv = blocks_for(n);
+  double* gpart = static_cast<double*>(ws);
+  double* M = gpart + slabs * ell * ell;
+  double* upart = M + ell * ell;
+  double* vpart = upart + 2 * r * bu;
+  float* Ur = reinterpret_cast<float*>(vpart + 2 * r * bv);
+  float* sigma = Ur + ell * r;
+  float* cw = sigma + r;
+  const size_t gsm = sizeof(float) * ell * (kSlabCols + 1);
+  cudaError_t err = cudaFuncSetAttribute(xgram_partial_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(gsm));
+  if (err != cudaSuccess) return err;
+  const int Lp = (ell + 1) / 2 * 2;
+  const size_t jsm = sizeof(float) * 2 * Lp * (Lp + 1);
+  if ((err = cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(jsm))) != cudaSuccess)
+    return err;
+  xgram_partial_kernel<<<static_cast<unsigned>(slabs), 256, gsm, L.stream>>>(Xhat, n, ell, gpart);
+  xgram_sum_kernel<<<static_cast<unsigned>(cdiv(static_cast<int64_t>(ell) * ell * 32, 256)), 256, 0,
+                     L.stream>>>(gpart, static_cast<int>(slabs), ell, M);
+  jacobi_kernel<<<1, 512, jsm, L.stream>>>(M, ell, r, Ur, sigma);
+  u_rows_kernel<<<bu, 256, 0, L.stream>>>(QL, m, ell, r, Ur, Wb, upart);
+  v_cols_kernel<<<bv, 256, 0, L.stream>>>(Xhat, n, ell, r, Ur, sigma, Hb, vpart);
+  ws_coef_kernel<<<1, 64, 0, L.stream>>>(upart, bu, vpart, bv, r, sigma, cw, hscale);
+  ws_feature_kernel<<<blocks_for(m * r + r * n), 256, 0, L.stream>>>(Wb, m, Hb, n, r, cw, Fw, Fh);
   L.count(7);
   return cudaGetLastError();
 }

@@ -54,6 +54,10 @@ struct nmf_ctx {
   cudaGraphExec_t batch_graph = nullptr;
   uint64_t batch_key = 0;
   int64_t batch_graph_launches = 0;
+  // learned warm start (NMF_INIT_MLP): the two networks' parameters on the device
+  float* warm = nullptr;      // [W net | H net]
+  int warm_hidden = 0, warm_r = 0;
+  double* d_loss = nullptr;
 };
 
 namespace {
@@ -435,6 +439,48 @@ __global__ void solve_decide_kernel(const double* res2, double target, int iters
   if (target > 0.0 && rel <= target) flags[0] = 1;
 }
 
+// Workspace of the learned warm start for hidden width <= hidden_max: W_b, H_b, hscale, F_w, F_h,
+// the two network outputs and the forward pass activations.
+size_t warm_ws_bytes(const nmf_params* p, int hidden_max) {
+  const int64_t m = p->m, n = p->n, r = p->r;
+  return sizeof(float) * static_cast<size_t>((m + n) * r * 5 + r) + 8 * 256 +
+         std::max(nmfrp::nndsvd_ws_bytes(m, n, p->r, p->ell),
+                  nmfrp::mlp_ws_bytes(std::max(m, n), hidden_max, p->r));
+}
+
+// NNDSVD features, both networks, and the initial factors into W, H.
+nmf_status warm_init(nmf_ctx* ctx, const nmf_params* p, const float* QL, const float* Xhat,
+                     float* W, float* H, Arena a) {
+  if (!ctx->warm || ctx->warm_r != p->r)
+    return fail(ctx, NMF_ERR_INVALID_ARG, "no warm-start network for r = %d (nmf_set_warmstart)", p->r);
+  const int64_t m = p->m, n = p->n;
+  const int r = p->r, F = 3 * r, Hd = ctx->warm_hidden;
+  float* Wb = a.take<float>(m * r);
+  float* Hb = a.take<float>(r * n);
+  float* hs = a.take<float>(r);
+  float* Fw = a.take<float>(m * F);
+  float* Fh = a.take<float>(n * F);
+  float* Dw = a.take<float>(m * r);
+  float* Dh = a.take<float>(n * r);
+  size_t rest = 0;
+  void* ws = a.rest(&rest);
+  NMF_CUDA(nmfrp::launch_warmstart_features(launcher(ctx), m, n, r, p->ell, QL, Xhat, Wb, Hb, hs,
+                                            Fw, Fh, ws, rest),
+           "warm-start features");
+  const int64_t np_ = nmfrp::mlp_param_count(F, Hd, r);
+  NMF_CUDA(nmfrp::launch_mlp_forward(launcher(ctx), F, Hd, r, ctx->warm, Fw, m, Dw, ws, rest),
+           "warm-start network (W)");
+  NMF_CUDA(nmfrp::launch_mlp_forward(launcher(ctx), F, Hd, r, ctx->warm + np_, Fh, n, Dh, ws, rest),
+           "warm-start network (H)");
+  NMF_CUDA(nmfrp::launch_warmstart_apply(launcher(ctx), m, n, r, Wb, Dw, Hb, Dh, hs, W, H),
+           "warm-start factors");
+  return NMF_OK;
+}
+
+bool mlp_shape_ok(int F, int hidden, int r) {
+  return F >= 1 && F <= 4096 && hidden >= 1 && hidden <= 1024 && r >= 1 && r <= 1024;
+}
+
 struct DeviceGuard {
   int prev = -1;
   explicit DeviceGuard(int dev) {
@@ -503,6 +549,8 @@ void nmf_destroy(nmf_ctx* ctx) {
   }
   if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
   if (ctx->batch_graph) cudaGraphExecDestroy(ctx->batch_graph);
+  if (ctx->warm) cudaFree(ctx->warm);
+  if (ctx->d_loss) cudaFree(ctx->d_loss);
   if (ctx->d_bres) cudaFree(ctx->d_bres);
   if (ctx->h_bres) cudaFreeHost(ctx->h_bres);
   delete ctx;
@@ -571,6 +619,7 @@ nmf_status nmf_workspace_size(const nmf_params* p, size_t* bytes) {
   scratch = std::max(scratch, nmfrp::iterate_persistent_ws_bytes(p->r, p->ell));
   scratch = std::max(scratch, nmfrp::residual_ws_bytes(m, n));
   scratch = std::max(scratch, nmfrp::nndsvd_ws_bytes(m, n, p->r, p->ell));
+  scratch = std::max(scratch, warm_ws_bytes(p, 256));
   (void)r;
   *bytes = b + scratch;
   return NMF_OK;
@@ -731,12 +780,16 @@ nmf_status nmf_solve(nmf_ctx* ctx, const nmf_params* p, int32_t init, const floa
   nmf_status st = check_params(ctx, p);
   if (st != NMF_OK) return st;
   if (!X || !W || !H || ldx < p->n) return fail(ctx, NMF_ERR_INVALID_ARG, "bad solve arguments");
-  if (init != NMF_INIT_GIVEN && init != NMF_INIT_NNDSVD)
+  if (init != NMF_INIT_GIVEN && init != NMF_INIT_NNDSVD && init != NMF_INIT_MLP)
     return fail(ctx, NMF_ERR_INVALID_ARG, "unknown init %d", init);
+  if (init == NMF_INIT_MLP && (!ctx->warm || ctx->warm_r != p->r))
+    return fail(ctx, NMF_ERR_INVALID_ARG, "no warm-start network for r = %d (nmf_set_warmstart)", p->r);
   if (p->iters < 0) return fail(ctx, NMF_ERR_INVALID_ARG, "iters < 0");
   DeviceGuard g(ctx->device);
   size_t need = 0;
   nmf_workspace_size(p, &need);
+  if (init == NMF_INIT_MLP && ctx->warm_hidden > 256)
+    need += warm_ws_bytes(p, ctx->warm_hidden);
   if ((st = ensure_ws(ctx, need)) != NMF_OK) return st;
   const int64_t m = p->m, n = p->n, l = p->ell;
   Arena a{static_cast<char*>(ctx->ws), ctx->ws_bytes};
@@ -768,6 +821,9 @@ nmf_status nmf_solve(nmf_ctx* ctx, const nmf_params* p, int32_t init, const floa
                                          need, ctx->d_status);
     if (e == cudaErrorNotSupported) return fail(ctx, NMF_ERR_UNSUPPORTED, "nndsvd not available");
     if (e != cudaSuccess) return cuda_fail(ctx, e, "nndsvd");
+  } else if (init == NMF_INIT_MLP) {
+    Phase ph(ctx, NMF_PHASE_INIT);
+    if ((st = warm_init(ctx, p, QL, Xhat, W, H, a)) != NMF_OK) return st;
   }
   // Device-side loop: iterate a chunk, gate the exact residual on the error monitor, run it,
   // decide; the host queues one chunk ahead and stops once the device has raised `done`.
@@ -844,13 +900,127 @@ nmf_status nmf_solve(nmf_ctx* ctx, const nmf_params* p, int32_t init, const floa
   return take_status(ctx);
 }
 
+int64_t nmf_mlp_param_count(int32_t F, int32_t hidden, int32_t r) {
+  if (!mlp_shape_ok(F, hidden, r)) return -1;
+  return nmfrp::mlp_param_count(F, hidden, r);
+}
+
+nmf_status nmf_warmstart_features(nmf_ctx* ctx, const nmf_params* p, const float* QL,
+                                  const float* Xhat, float* Wb, float* Hb, float* hscale,
+                                  float* Fw, float* Fh) {
+  if (!ctx) return NMF_ERR_INVALID_ARG;
+  nmf_status st = check_params(ctx, p);
+  if (st != NMF_OK) return st;
+  if (!QL || !Xhat || !Wb || !Hb || !hscale || !Fw || !Fh)
+    return fail(ctx, NMF_ERR_INVALID_ARG, "NULL argument");
+  DeviceGuard g(ctx->device);
+  if ((st = ensure_ws(ctx, nmfrp::nndsvd_ws_bytes(p->m, p->n, p->r, p->ell))) != NMF_OK) return st;
+  cudaError_t e = nmfrp::launch_warmstart_features(launcher(ctx), p->m, p->n, p->r, p->ell, QL,
+                                                   Xhat, Wb, Hb, hscale, Fw, Fh, ctx->ws,
+                                                   ctx->ws_bytes);
+  if (e == cudaErrorNotSupported) return fail(ctx, NMF_ERR_UNSUPPORTED, "r or ell too large");
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "warm-start features");
+  return NMF_OK;
+}
+
+nmf_status nmf_mlp_forward(nmf_ctx* ctx, int32_t F, int32_t hidden, int32_t r,
+                           const float* params, const float* X, int64_t rows, float* Y) {
+  if (!ctx) return NMF_ERR_INVALID_ARG;
+  if (!mlp_shape_ok(F, hidden, r) || rows < 1 || rows > (int64_t(1) << 30) || !params || !X || !Y)
+    return fail(ctx, NMF_ERR_INVALID_ARG, "bad network forward arguments");
+  DeviceGuard g(ctx->device);
+  nmf_status st = ensure_ws(ctx, nmfrp::mlp_ws_bytes(rows, hidden, r));
+  if (st != NMF_OK) return st;
+  NMF_CUDA(nmfrp::launch_mlp_forward(launcher(ctx), F, hidden, r, params, X, rows, Y, ctx->ws,
+                                     ctx->ws_bytes),
+           "network forward");
+  return NMF_OK;
+}
+
+nmf_status nmf_mlp_loss_grad(nmf_ctx* ctx, int32_t F, int32_t hidden, int32_t r,
+                             const float* params, const float* X, const float* T, int64_t rows,
+                             float* grad, double* loss_host) {
+  if (!ctx) return NMF_ERR_INVALID_ARG;
+  if (!mlp_shape_ok(F, hidden, r) || rows < 1 || rows > (int64_t(1) << 30) || !params || !X ||
+      !T || !grad)
+    return fail(ctx, NMF_ERR_INVALID_ARG, "bad network gradient arguments");
+  DeviceGuard g(ctx->device);
+  nmf_status st = ensure_ws(ctx, nmfrp::mlp_ws_bytes(rows, hidden, r));
+  if (st != NMF_OK) return st;
+  if (!ctx->d_loss) NMF_CUDA(cudaMalloc(&ctx->d_loss, sizeof(double)), "loss slot");
+  NMF_CUDA(nmfrp::launch_mlp_loss_grad(launcher(ctx), F, hidden, r, params, X, T, rows, grad,
+                                       ctx->d_loss, ctx->ws, ctx->ws_bytes),
+           "network gradient");
+  if (loss_host) {
+    NMF_CUDA(cudaMemcpyAsync(ctx->h_res, ctx->d_loss, sizeof(double), cudaMemcpyDeviceToHost,
+                             ctx->stream),
+             "loss copy");
+    NMF_CUDA(cudaStreamSynchronize(ctx->stream), "loss sync");
+    *loss_host = ctx->h_res[0];
+  }
+  return NMF_OK;
+}
+
+nmf_status nmf_mlp_adam(nmf_ctx* ctx, int64_t count, float* params, float* m, float* v,
+                        const float* grad, int32_t step, float lr) {
+  if (!ctx) return NMF_ERR_INVALID_ARG;
+  if (count < 1 || !params || !m || !v || !grad || step < 1 || !(lr > 0.f))
+    return fail(ctx, NMF_ERR_INVALID_ARG, "bad Adam arguments");
+  DeviceGuard g(ctx->device);
+  NMF_CUDA(nmfrp::launch_adam(launcher(ctx), params, m, v, grad, count, lr, step), "Adam");
+  return NMF_OK;
+}
+
+nmf_status nmf_mlp_train_step(nmf_ctx* ctx, int32_t F, int32_t hidden, int32_t r, float* params,
+                              float* m, float* v, float* grad, int32_t step, float lr,
+                              const float* X, const float* T, int64_t rows, double* loss_host) {
+  nmf_status st = nmf_mlp_loss_grad(ctx, F, hidden, r, params, X, T, rows, grad, loss_host);
+  if (st != NMF_OK) return st;
+  return nmf_mlp_adam(ctx, nmfrp::mlp_param_count(F, hidden, r), params, m, v, grad, step, lr);
+}
+
+nmf_status nmf_warmstart_apply(nmf_ctx* ctx, int64_t m, int64_t n, int32_t r, const float* Wb,
+                               const float* Dw, const float* Hb, const float* Dh,
+                               const float* hscale, float* W, float* H) {
+  if (!ctx) return NMF_ERR_INVALID_ARG;
+  if (m < 1 || n < 1 || r < 1 || !Wb || !Dw || !Hb || !Dh || !hscale || !W || !H)
+    return fail(ctx, NMF_ERR_INVALID_ARG, "bad warm-start arguments");
+  DeviceGuard g(ctx->device);
+  NMF_CUDA(nmfrp::launch_warmstart_apply(launcher(ctx), m, n, r, Wb, Dw, Hb, Dh, hscale, W, H),
+           "warm-start factors");
+  return NMF_OK;
+}
+
+nmf_status nmf_set_warmstart(nmf_ctx* ctx, int32_t hidden, int32_t r, const float* params_w,
+                             const float* params_h) {
+  if (!ctx) return NMF_ERR_INVALID_ARG;
+  if (!mlp_shape_ok(3 * r, hidden, r) || !params_w || !params_h)
+    return fail(ctx, NMF_ERR_INVALID_ARG, "bad warm-start network");
+  DeviceGuard g(ctx->device);
+  const int64_t np_ = nmfrp::mlp_param_count(3 * r, hidden, r);
+  if (ctx->warm) {
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(ctx->warm);
+    ctx->warm = nullptr;
+  }
+  NMF_CUDA(cudaMalloc(&ctx->warm, sizeof(float) * 2 * np_), "warm-start network");
+  NMF_CUDA(cudaMemcpyAsync(ctx->warm, params_w, sizeof(float) * np_, cudaMemcpyDefault, ctx->stream),
+           "warm-start network");
+  NMF_CUDA(cudaMemcpyAsync(ctx->warm + np_, params_h, sizeof(float) * np_, cudaMemcpyDefault,
+                           ctx->stream),
+           "warm-start network");
+  ctx->warm_hidden = hidden;
+  ctx->warm_r = r;
+  return NMF_OK;
+}
+
 nmf_status nmf_solve_batched(nmf_ctx* ctx, int32_t count, const nmf_params* p, int32_t init,
                              const float* const* X, const int64_t* ldx, float* const* W,
                              float* const* H, int32_t rows_per_block, double* rel_err_host) {
   if (!ctx) return NMF_ERR_INVALID_ARG;
   if (count < 1 || !p || !X || !ldx || !W || !H || !rel_err_host)
     return fail(ctx, NMF_ERR_INVALID_ARG, "bad batched arguments");
-  if (init != NMF_INIT_GIVEN && init != NMF_INIT_NNDSVD)
+  if (init != NMF_INIT_GIVEN && init != NMF_INIT_NNDSVD && init != NMF_INIT_MLP)
     return fail(ctx, NMF_ERR_INVALID_ARG, "unknown init %d", init);
   if (rows_per_block < 0) return fail(ctx, NMF_ERR_INVALID_ARG, "rows_per_block < 0");
   for (int i = 0; i < count; ++i) {
@@ -859,6 +1029,8 @@ nmf_status nmf_solve_batched(nmf_ctx* ctx, int32_t count, const nmf_params* p, i
     if (!X[i] || !W[i] || !H[i] || ldx[i] < p[i].n)
       return fail(ctx, NMF_ERR_INVALID_ARG, "problem %d: bad pointers or ldx", i);
     if (p[i].iters < 0) return fail(ctx, NMF_ERR_INVALID_ARG, "problem %d: iters < 0", i);
+    if (init == NMF_INIT_MLP && (!ctx->warm || ctx->warm_r != p[i].r))
+      return fail(ctx, NMF_ERR_INVALID_ARG, "problem %d: no warm-start network for r = %d", i, p[i].r);
     if (nmfrp::iterate_multi_min_blocks(p[i].m, p[i].n, p[i].r, p[i].ell) < 1)
       return fail(ctx, NMF_ERR_UNSUPPORTED, "problem %d: r or ell too large for batching", i);
   }
@@ -896,6 +1068,7 @@ nmf_status nmf_solve_batched(nmf_ctx* ctx, int32_t count, const nmf_params* p, i
     rest = std::max(rest, nmfrp::nndsvd_ws_bytes(q->m, q->n, q->r, q->ell));
     rest = std::max(rest, nmfrp::residual_ws_bytes(q->m, q->n));
     rest = std::max(rest, nmfrp::quantize_stats_ws_bytes());
+    if (init == NMF_INIT_MLP) rest = std::max(rest, warm_ws_bytes(q, std::max(ctx->warm_hidden, 1)));
     scratch = std::max(scratch, s + rest + 1024);
     ia[i].m = q->m;
     ia[i].n = q->n;
@@ -973,6 +1146,9 @@ nmf_status nmf_solve_batched(nmf_ctx* ctx, int32_t count, const nmf_params* p, i
         cudaError_t e = nmfrp::launch_nndsvd(launcher(ctx), q->m, q->n, q->r, q->ell, ia[i].QL,
                                              ia[i].Xhat, W[i], H[i], ws, rest, ctx->d_status);
         if (e != cudaSuccess) r1 = cuda_fail(ctx, e, "nndsvd");
+      } else if (init == NMF_INIT_MLP) {
+        Phase ph(ctx, NMF_PHASE_INIT);
+        r1 = warm_init(ctx, q, ia[i].QL, ia[i].Xhat, W[i], H[i], sa);
       }
     }
     ctx->stream = main_stream;
@@ -995,10 +1171,14 @@ nmf_status nmf_solve_batched(nmf_ctx* ctx, int32_t count, const nmf_params* p, i
       for (size_t b = 0; b < sizeof(nmf_params); ++b) mix(pb[b]);
       mix(reinterpret_cast<uintptr_t>(X[i]));
       mix(static_cast<uint64_t>(ldx[i]));
-      if (init == NMF_INIT_NNDSVD) {
+      if (init != NMF_INIT_GIVEN) {
         mix(reinterpret_cast<uintptr_t>(W[i]));
         mix(reinterpret_cast<uintptr_t>(H[i]));
       }
+    }
+    if (init == NMF_INIT_MLP) {
+      mix(reinterpret_cast<uintptr_t>(ctx->warm));
+      mix(static_cast<uint64_t>(ctx->warm_hidden));
     }
     const cudaStream_t origin = ctx->side[0];
     if (!(ctx->batch_graph && ctx->batch_key == key)) {

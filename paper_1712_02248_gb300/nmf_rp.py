@@ -25,13 +25,16 @@ STATUS = {0: "NMF_OK", 1: "NMF_ERR_INVALID_ARG", 2: "NMF_ERR_CUDA", 3: "NMF_ERR_
           7: "NMF_ERR_UNSUPPORTED"}
 PREC = {"fp32": 0, "bf16": 1, "fp8": 2}
 RULE = {"fasthals": 0, "mu": 1}
-INIT = {"given": 0, "nndsvd": 1}
+INIT = {"given": 0, "nndsvd": 1, "mlp": 2}
 
 EXPORTS = ["nmf_create", "nmf_destroy", "nmf_set_stream", "nmf_last_error", "nmf_sync",
            "nmf_launch_count", "nmf_workspace_size", "nmf_gaussian", "nmf_quantize",
            "nmf_dual_pass", "nmf_qr", "nmf_sketch", "nmf_compress", "nmf_iterate",
            "nmf_residual", "nmf_residual_static", "nmf_nndsvd", "nmf_solve", "nmf_set_profiling", "nmf_phase_times",
-           "nmf_last_solve_info", "nmf_solve_batched", "nmf_last_batch_info"]
+           "nmf_last_solve_info", "nmf_solve_batched", "nmf_last_batch_info",
+           "nmf_mlp_param_count", "nmf_warmstart_features", "nmf_mlp_forward",
+           "nmf_mlp_loss_grad", "nmf_mlp_adam", "nmf_mlp_train_step", "nmf_warmstart_apply",
+           "nmf_set_warmstart"]
 PHASES = ["quantize", "dual_pass", "qr", "iterate", "residual", "init"]
 
 
@@ -83,6 +86,21 @@ _c = {
                             [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64), _i32]),
     "nmf_solve": _sig("nmf_solve", ctypes.c_int,
                       [_vp, _P, _i32, _vp, _i64, _vp, _vp, _D, ctypes.POINTER(_i32)]),
+    "nmf_mlp_param_count": _sig("nmf_mlp_param_count", _i64, [_i32, _i32, _i32]),
+    "nmf_warmstart_features": _sig("nmf_warmstart_features", ctypes.c_int,
+                                   [_vp, _P, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "nmf_mlp_forward": _sig("nmf_mlp_forward", ctypes.c_int,
+                            [_vp, _i32, _i32, _i32, _vp, _vp, _i64, _vp]),
+    "nmf_mlp_loss_grad": _sig("nmf_mlp_loss_grad", ctypes.c_int,
+                              [_vp, _i32, _i32, _i32, _vp, _vp, _vp, _i64, _vp, _D]),
+    "nmf_mlp_adam": _sig("nmf_mlp_adam", ctypes.c_int,
+                         [_vp, _i64, _vp, _vp, _vp, _vp, _i32, ctypes.c_float]),
+    "nmf_mlp_train_step": _sig("nmf_mlp_train_step", ctypes.c_int,
+                               [_vp, _i32, _i32, _i32, _vp, _vp, _vp, _vp, _i32, ctypes.c_float,
+                                _vp, _vp, _i64, _D]),
+    "nmf_warmstart_apply": _sig("nmf_warmstart_apply", ctypes.c_int,
+                                [_vp, _i64, _i64, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "nmf_set_warmstart": _sig("nmf_set_warmstart", ctypes.c_int, [_vp, _i32, _i32, _vp, _vp]),
     "nmf_last_batch_info": _sig("nmf_last_batch_info", ctypes.c_int, [_vp, ctypes.POINTER(_i32)]),
     "nmf_solve_batched": _sig("nmf_solve_batched", ctypes.c_int,
                               [_vp, _i32, _P, _i32, ctypes.POINTER(_vp), ctypes.POINTER(_i64),
@@ -330,6 +348,71 @@ def nmf_solve_batched(ctx, ps, Xs, Ws, Hs, init="given", rows_per_block=0):
     ctx._check(_c["nmf_solve_batched"](ctx.handle, k, arr, INIT.get(init, init), xp, ld, wp, hp,
                                        int(rows_per_block), out))
     return list(out)
+
+
+def nmf_mlp_param_count(F, hidden, r):
+    return int(_c["nmf_mlp_param_count"](F, hidden, r))
+
+
+def nmf_warmstart_features(ctx, p, QL, Xhat):
+    """(W_b, H_b, hscale, F_w, F_h) of include/nmf_rp.h's learned warm start."""
+    dev = QL.device
+    f = lambda *shape: torch.empty(shape, dtype=torch.float32, device=dev)
+    Wb, Hb, hs = f(p.m, p.r), f(p.r, p.n), f(p.r)
+    Fw, Fh = f(p.m, 3 * p.r), f(p.n, 3 * p.r)
+    ctx._check(_c["nmf_warmstart_features"](ctx.handle, ctypes.byref(p), _ptr(_dev_f32(QL, "QL")),
+                                            _ptr(_dev_f32(Xhat, "Xhat")), _ptr(Wb), _ptr(Hb),
+                                            _ptr(hs), _ptr(Fw), _ptr(Fh)))
+    return Wb, Hb, hs, Fw, Fh
+
+
+def nmf_mlp_forward(ctx, params, X, hidden, r, Y=None):
+    _dev_f32(params, "params")
+    _dev_f32(X, "X")
+    Y = Y if Y is not None else torch.empty((X.shape[0], r), dtype=torch.float32, device=X.device)
+    ctx._check(_c["nmf_mlp_forward"](ctx.handle, X.shape[1], hidden, r, _ptr(params), _ptr(X),
+                                      X.shape[0], _ptr(Y)))
+    return Y
+
+
+def nmf_mlp_loss_grad(ctx, params, X, T, hidden, r, grad=None):
+    """(loss, grad) of the mean squared error of network(X) against T."""
+    _dev_f32(params, "params")
+    grad = grad if grad is not None else torch.empty_like(params)
+    loss = ctypes.c_double()
+    ctx._check(_c["nmf_mlp_loss_grad"](ctx.handle, X.shape[1], hidden, r, _ptr(params),
+                                        _ptr(_dev_f32(X, "X")), _ptr(_dev_f32(T, "T")), X.shape[0],
+                                        _ptr(grad), ctypes.byref(loss)))
+    return loss.value, grad
+
+
+def nmf_mlp_adam(ctx, params, m, v, grad, step, lr):
+    ctx._check(_c["nmf_mlp_adam"](ctx.handle, params.numel(), _ptr(params), _ptr(m), _ptr(v),
+                                   _ptr(grad), int(step), float(lr)))
+
+
+def nmf_mlp_train_step(ctx, params, m, v, grad, step, lr, X, T, hidden, r, want_loss=False):
+    loss = ctypes.c_double()
+    ctx._check(_c["nmf_mlp_train_step"](ctx.handle, X.shape[1], hidden, r, _ptr(params), _ptr(m),
+                                         _ptr(v), _ptr(grad), int(step), float(lr),
+                                         _ptr(_dev_f32(X, "X")), _ptr(_dev_f32(T, "T")),
+                                         X.shape[0], ctypes.byref(loss) if want_loss else None))
+    return loss.value if want_loss else None
+
+
+def nmf_warmstart_apply(ctx, Wb, Dw, Hb, Dh, hscale, W=None, H=None):
+    W = W if W is not None else torch.empty_like(Wb)
+    H = H if H is not None else torch.empty_like(Hb)
+    m, r = Wb.shape
+    n = Hb.shape[1]
+    ctx._check(_c["nmf_warmstart_apply"](ctx.handle, m, n, r, _ptr(Wb), _ptr(Dw), _ptr(Hb),
+                                          _ptr(Dh), _ptr(hscale), _ptr(W), _ptr(H)))
+    return W, H
+
+
+def nmf_set_warmstart(ctx, hidden, r, params_w, params_h):
+    ctx._check(_c["nmf_set_warmstart"](ctx.handle, hidden, r, _ptr(_dev_f32(params_w, "params_w")),
+                                        _ptr(_dev_f32(params_h, "params_h"))))
 
 
 def nmf_last_batch_info(ctx):
