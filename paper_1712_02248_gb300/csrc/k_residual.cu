@@ -1,11 +1,14 @@
 // Full-size residual of Eq. 2.2: ||X - W H||_F^2 and ||X||_F^2 in one read of X.
 //
-// A block walks 128 x 128 tiles of X. For each tile it stages the 128 rows of W (transposed) and
-// the 128 columns of H in shared memory, issues its X loads first (16 x 128-bit per thread, so
-// the HBM latency overlaps the W H arithmetic), rebuilds its 8 x 8 outputs of W H in registers
-// (K = r FMAs each), and adds (x - wh)^2 and x^2 to per-thread sums. Per-tile sums are FP32 (64
-// terms), accumulated across tiles in FP64; block sums and the final sum are FP64 in a fixed
-// order (deterministic).
+// Streaming kernel (X rows 16-byte aligned): one persistent block per SM walks a contiguous range
+// of 128 x 64 tiles of X in row-block-major order. X tiles and the matching 64 columns of H arrive through a 2-stage
+// cp.async pipeline in shared memory (two blocks per SM); the 128 rows of W (transposed) are staged once per row
+// block. Each thread rebuilds 8 x 4 outputs of W H in registers (K = r FMAs each) and adds
+// (x - wh)^2 and x^2 to per-thread sums. Per-tile sums are FP32 (32 terms), accumulated across
+// tiles in FP64; block sums and the final sum are FP64 in a fixed order (deterministic).
+//
+// General kernel (any ldx): a block walks 128 x 128 tiles, staging W and H per tile, with its X
+// loads issued first so that their latency overlaps the W H arithmetic.
 #include <mutex>
 
 #include "common.cuh"
@@ -126,6 +129,148 @@ __global__ void __launch_bounds__(kThreads, 1) residual_kernel(
   }
 }
 
+// ---------------------------------------------------------------- streaming kernel
+
+constexpr int kSR = 128, kSC = 64, kSThreads = 256, kSStages = 2;
+constexpr int kXS = kSC + 4;   // padded X tile row (floats): rows 16 B apart mod 128 B
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const uint32_t s = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+struct StreamGeom {
+  int64_t m, n, ldx;
+  int r, RS;                 // RS: stride of a staged H row (64 floats)
+  int64_t tiles_c, tiles;    // column tiles per row block, all tiles
+};
+
+// Issue the cp.async copies of tile `tile` into stage buffers xs (kSR x kXS) and hs (r x kSC).
+// Out-of-range rows / columns are not copied; the compute masks them.
+__device__ __forceinline__ void stream_issue(const float* __restrict__ X, const float* __restrict__ H,
+                                             const StreamGeom& g, int64_t tile, float* xs,
+                                             float* hs) {
+  const int64_t r0 = (tile / g.tiles_c) * kSR, c0 = (tile % g.tiles_c) * kSC;
+  for (int e = threadIdx.x; e < kSR * (kSC / 4); e += kSThreads) {
+    const int i = e / (kSC / 4), c4 = e % (kSC / 4);
+    const int64_t gr = r0 + i, gc = c0 + 4 * c4;
+    if (gr < g.m && gc + 3 < g.n) cp_async16(xs + i * kXS + 4 * c4, X + gr * g.ldx + gc);
+  }
+  for (int e = threadIdx.x; e < g.r * (kSC / 4); e += kSThreads) {
+    const int k = e / (kSC / 4), c4 = e % (kSC / 4);
+    const int64_t gc = c0 + 4 * c4;
+    if (gc + 3 < g.n) cp_async16(hs + k * g.RS + 4 * c4, H + static_cast<int64_t>(k) * g.n + gc);
+  }
+}
+
+__global__ void __launch_bounds__(kSThreads, 2) residual_stream_kernel(
+    const float* __restrict__ X, const float* __restrict__ W, const float* __restrict__ H,
+    StreamGeom g, double* __restrict__ part, const int* gate) {
+  if (gate && !*reinterpret_cast<const volatile int*>(gate)) return;
+  extern __shared__ __align__(16) float sh[];
+  const int r = g.r;
+  const int stage_f = kSR * kXS + r * kSC;     // floats per stage
+  float* WsT = sh + kSStages * stage_f;         // [r][kSR + 4]
+  const int WS = kSR + 4;
+  __shared__ double red[2][kSThreads / 32];
+  const int t = threadIdx.x, ty = t >> 4, tx = t & 15;   // rows 8 ty + a, columns 4 tx + b
+  double e2 = 0.0, x2 = 0.0;
+  // tiles of this block: a contiguous range (W is staged again only when the range crosses
+  // into the next row block)
+  const int64_t first = blockIdx.x * g.tiles / gridDim.x;
+  const int64_t mine = (blockIdx.x + 1) * g.tiles / gridDim.x - first;
+  const int64_t step = 1;
+  // prologue: stages 0 .. kSStages - 2
+  for (int s = 0; s < kSStages - 1; ++s) {
+    if (s < mine) stream_issue(X, H, g, first + s * step, sh + s * stage_f, sh + s * stage_f + kSR * kXS);
+    cp_async_commit();
+  }
+  int64_t cur_rb = -1;
+  for (int64_t k = 0; k < mine; ++k) {
+    // keep kSStages - 1 tiles in flight: issue tile k + kSStages - 1 into the stage freed last
+    {
+      const int64_t nk = k + kSStages - 1;
+      const int s = static_cast<int>(nk % kSStages);
+      if (nk < mine) stream_issue(X, H, g, first + nk * step, sh + s * stage_f, sh + s * stage_f + kSR * kXS);
+      cp_async_commit();
+    }
+    const int64_t tile = first + k * step;
+    const int64_t rb = tile / g.tiles_c, r0 = rb * kSR, c0 = (tile % g.tiles_c) * kSC;
+    if (rb != cur_rb) {
+      // W rows of this row block, transposed (plain loads: once per row block)
+      __syncthreads();
+      for (int e = t; e < kSR * r; e += kSThreads) {
+        const int i = e / r, kk = e - i * r;
+        const int64_t gr = r0 + i;
+        WsT[kk * WS + i] = gr < g.m ? W[gr * r + kk] : 0.f;
+      }
+      cur_rb = rb;
+    }
+    cp_async_wait<kSStages - 1>();
+    __syncthreads();
+    const float* xs = sh + (k % kSStages) * stage_f;
+    const float* hs = xs + kSR * kXS;
+    float acc[8][4];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+#pragma unroll 4
+    for (int kk = 0; kk < r; ++kk) {
+      const float4 w0 = *reinterpret_cast<const float4*>(&WsT[kk * WS + 8 * ty]);
+      const float4 w1 = *reinterpret_cast<const float4*>(&WsT[kk * WS + 8 * ty + 4]);
+      const float4 h0 = *reinterpret_cast<const float4*>(&hs[kk * g.RS + 4 * tx]);
+      const float wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+      const float hv[4] = {h0.x, h0.y, h0.z, h0.w};
+#pragma unroll
+      for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(wv[a], hv[b], acc[a][b]);
+    }
+    float te = 0.f, tx2 = 0.f;
+    const bool cols_in = c0 + 4 * tx + 3 < g.n;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      const bool in = cols_in && (r0 + 8 * ty + a < g.m);
+      const float4 x4 = *reinterpret_cast<const float4*>(&xs[(8 * ty + a) * kXS + 4 * tx]);
+      const float xv[4] = {x4.x, x4.y, x4.z, x4.w};
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const float xb = in ? xv[b] : 0.f;
+        const float d = in ? xb - acc[a][b] : 0.f;
+        te = fmaf(d, d, te);
+        tx2 = fmaf(xb, xb, tx2);
+      }
+    }
+    e2 += te;
+    x2 += tx2;
+    __syncthreads();   // the stage is reused by the copies issued at the next step
+  }
+  cp_async_wait<0>();
+  e2 = warp_sum(e2);
+  x2 = warp_sum(x2);
+  if ((t & 31) == 0) {
+    red[0][t >> 5] = e2;
+    red[1][t >> 5] = x2;
+  }
+  __syncthreads();
+  if (t < 32) {
+    double a = (t < kSThreads / 32) ? red[0][t] : 0.0;
+    double b = (t < kSThreads / 32) ? red[1][t] : 0.0;
+    a = warp_sum(a);
+    b = warp_sum(b);
+    if (t == 0) {
+      part[2 * blockIdx.x] = a;
+      part[2 * blockIdx.x + 1] = b;
+    }
+  }
+}
+
 __global__ void residual_final_kernel(const double* __restrict__ part, int nparts,
                                       double* __restrict__ out2, const int* gate) {
   if (gate && !*reinterpret_cast<const volatile int*>(gate)) return;
@@ -163,8 +308,37 @@ cudaError_t launch_residual(const Launcher& L, const float* X, int64_t m, int64_
                             const float* W, const float* H, int r, double* out2, void* ws,
                             size_t ws_bytes, const int* gate) {
   if (ws_bytes < residual_ws_bytes(m, n)) return cudaErrorInvalidValue;
-  const int64_t tiles = cdiv(m, kT) * cdiv(n, kT);
   double* part = static_cast<double*>(ws);
+  // streaming kernel: rows 16-byte aligned, columns a multiple of 4 (the ragged tail of a row
+  // would need element copies), W H rank small enough for the shared-memory stages (r <= 48)
+  if (ldx % 4 == 0 && n % 4 == 0 && reinterpret_cast<uintptr_t>(X) % 16 == 0 &&
+      reinterpret_cast<uintptr_t>(H) % 16 == 0 && r <= 48) {
+    StreamGeom g;
+    g.m = m;
+    g.n = n;
+    g.ldx = ldx;
+    g.r = r;
+    g.RS = kSC;
+    g.tiles_c = cdiv(n, kSC);
+    g.tiles = cdiv(m, kSR) * g.tiles_c;
+    const size_t sm = sizeof(float) * (static_cast<size_t>(kSStages) * (kSR * kXS + r * kSC) +
+                                       static_cast<size_t>(r) * (kSR + 4));
+    cudaError_t err = cudaFuncSetAttribute(residual_stream_kernel,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           static_cast<int>(sm));
+    if (err != cudaSuccess) return err;
+    int per_sm = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, residual_stream_kernel, kSThreads,
+                                                      sm) != cudaSuccess || per_sm < 1)
+      per_sm = 1;
+    int grid = num_sms() * (per_sm < 2 ? per_sm : 2);
+    if (g.tiles < grid) grid = static_cast<int>(g.tiles);
+    residual_stream_kernel<<<grid, kSThreads, sm, L.stream>>>(X, W, H, g, part, gate);
+    residual_final_kernel<<<1, 32, 0, L.stream>>>(part, grid, out2, gate);
+    L.count(2);
+    return cudaGetLastError();
+  }
+  const int64_t tiles = cdiv(m, kT) * cdiv(n, kT);
   const size_t sm = sizeof(float) * (r * kWS + r * kT);
   const bool vec = (ldx % 4 == 0) && (reinterpret_cast<uintptr_t>(X) % 16 == 0);
   auto k = vec ? residual_kernel<true> : residual_kernel<false>;
