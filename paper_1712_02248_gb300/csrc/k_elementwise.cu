@@ -96,6 +96,7 @@ __global__ void __launch_bounds__(256) quantize_bf16_stats_kernel(
   int run = 0;
   if (VEC) {
     const int64_t n4 = n / 4, total = m * n4;
+#pragma unroll 4
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
       const int64_t i = e / n4, j4 = e - i * n4;

@@ -16,9 +16,9 @@
 //                     H^T [Q_R | H]  (H_tld and H H^T) and of <S_H, H> is added.
 //   -- grid barrier --
 //
-// A row of W is handled by kGA = 2 lanes and a column of H by kGB = 2 lanes; each lane owns a
-// contiguous run of RP / kGA (RP / kGB) components, so every shared-memory read of a Gram row or
-// of H_tld / W_tld is a broadcast vector load. The sweep is incremental: t_j = S_j - sum_q w_q
+// A group of lanes handles one or more rows of W (columns of H); each lane owns a contiguous run
+// of the components, so every shared-memory read of a Gram row or of H_tld / W_tld is a
+// broadcast vector load that serves all the group's rows (Lanes<RP> below). The sweep is incremental: t_j = S_j - sum_q w_q
 // G_qj is formed for every j; when w_j moves by d (computed by the lane owning j, broadcast in
 // the group) every t_j' drops by d G_jj' (those with j' <= j are never read again, so they are
 // updated too instead of being masked). These are the Gauss-Seidel values of the paper's
@@ -46,8 +46,6 @@ namespace nmfrp {
 namespace {
 
 constexpr int kNT = 512;          // threads per block (one block per SM)
-constexpr int kGA = 2;            // lanes per row of W
-constexpr int kGB = 2;            // lanes per column of H
 constexpr int kCopies = 4;        // copies of each cross-block sum
 constexpr long long kWaitCycles = 4000000000LL;   // about two seconds of polling
 
@@ -250,14 +248,15 @@ __device__ __forceinline__ void ld_run(const float* p, float* v) {
   }
 }
 
-// One group of NG lanes updates one factor vector v (RP components, lane g owning
-// [g C, g C + C)) given its cross product s (S_j for the owned j), the Gram G (RP x RP, shared
-// memory) and the rule. For FastHALS-RP on H (reg = true) the Section 4.1 alpha / beta form is
-// used. Components j >= r are zero on entry and stay zero.
-template <int RP, int NG, int RULE>
-__device__ __forceinline__ void update_vec(float* v, float* s, const float* G, const float* inv,
-                                           int g, int r, bool reg, float alpha, float beta,
-                                           float eps) {
+// One group of NG lanes updates R factor vectors at once (rows of W, or columns of H): vector rho
+// has RP components, lane g owning [g C, g C + C), its cross products in s[rho] (S_j for the
+// owned j). Every Gram row read from shared memory serves the R vectors. For FastHALS-RP on H
+// (reg = true) the Section 4.1 alpha / beta form is used. Components j >= r are zero on entry
+// and stay zero.
+template <int RP, int NG, int R, int RULE>
+__device__ __forceinline__ void update_rows(float (&v)[R][RP / NG], float (&s)[R][RP / NG],
+                                            const float* G, const float* inv, int g, int r,
+                                            bool reg, float alpha, float beta, float eps) {
   constexpr int C = RP / NG;
   const unsigned full = 0xffffffffu;
   if (RULE == 0) {
@@ -266,11 +265,14 @@ __device__ __forceinline__ void update_vec(float* v, float* s, const float* G, c
     for (int o = 0; o < NG; ++o) {
 #pragma unroll
       for (int cq = 0; cq < C; ++cq) {
-        const float vq = __shfl_sync(full, v[cq], o, NG);
         float gr[C];
         ld_run<C>(G + (o * C + cq) * RP + g * C, gr);
 #pragma unroll
-        for (int c = 0; c < C; ++c) s[c] = fmaf(-vq, gr[c], s[c]);
+        for (int rho = 0; rho < R; ++rho) {
+          const float vq = __shfl_sync(full, v[rho][cq], o, NG);
+#pragma unroll
+          for (int c = 0; c < C; ++c) s[rho][c] = fmaf(-vq, gr[c], s[rho][c]);
+        }
       }
     }
 #pragma unroll 1
@@ -278,54 +280,70 @@ __device__ __forceinline__ void update_vec(float* v, float* s, const float* G, c
 #pragma unroll
       for (int cj = 0; cj < C; ++cj) {
         const int j = o * C + cj;
-        float d = 0.f;
+        float d[R];
+#pragma unroll
+        for (int rho = 0; rho < R; ++rho) d[rho] = 0.f;
         if (g == o && j < r) {
-          const float gjj = G[j * RP + j];
-          float vn = v[cj];
-          if (!reg) {
-            if (gjj > 0.f) vn = fmaxf(0.f, fmaf(s[cj], inv[j], v[cj]));
-          } else if (gjj + beta > 0.f) {
-            vn = fmaxf(0.f, (fmaf(v[cj], gjj, s[cj]) - alpha) / (gjj + beta));
+          const float gjj = G[j * RP + j], ij = inv[j];
+#pragma unroll
+          for (int rho = 0; rho < R; ++rho) {
+            float vn = v[rho][cj];
+            if (!reg) {
+              if (gjj > 0.f) vn = fmaxf(0.f, fmaf(s[rho][cj], ij, v[rho][cj]));
+            } else if (gjj + beta > 0.f) {
+              vn = fmaxf(0.f, (fmaf(v[rho][cj], gjj, s[rho][cj]) - alpha) / (gjj + beta));
+            }
+            d[rho] = vn - v[rho][cj];
+            v[rho][cj] = vn;
           }
-          d = vn - v[cj];
-          v[cj] = vn;
         }
-        d = __shfl_sync(full, d, o, NG);
         float gr[C];
         ld_run<C>(G + j * RP + g * C, gr);
 #pragma unroll
-        for (int c = 0; c < C; ++c) s[c] = fmaf(-d, gr[c], s[c]);
+        for (int rho = 0; rho < R; ++rho) {
+          const float dd = __shfl_sync(full, d[rho], o, NG);
+#pragma unroll
+          for (int c = 0; c < C; ++c) s[rho][c] = fmaf(-dd, gr[c], s[rho][c]);
+        }
       }
     }
   } else {
-    float num[C], den[C];
+    float num[R][C], den[R][C];
 #pragma unroll
-    for (int c = 0; c < C; ++c) {
-      num[c] = posp(s[c]);
-      den[c] = negp(s[c]) + eps;
-    }
+    for (int rho = 0; rho < R; ++rho)
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        num[rho][c] = posp(s[rho][c]);
+        den[rho][c] = negp(s[rho][c]) + eps;
+      }
 #pragma unroll 1
     for (int o = 0; o < NG; ++o) {
 #pragma unroll
       for (int cq = 0; cq < C; ++cq) {
-        const float vq = __shfl_sync(full, v[cq], o, NG);
         float gr[C];
         ld_run<C>(G + (o * C + cq) * RP + g * C, gr);
 #pragma unroll
-        for (int c = 0; c < C; ++c) {
-          num[c] = fmaf(vq, negp(gr[c]), num[c]);
-          den[c] = fmaf(vq, posp(gr[c]), den[c]);
+        for (int rho = 0; rho < R; ++rho) {
+          const float vq = __shfl_sync(full, v[rho][cq], o, NG);
+#pragma unroll
+          for (int c = 0; c < C; ++c) {
+            num[rho][c] = fmaf(vq, negp(gr[c]), num[rho][c]);
+            den[rho][c] = fmaf(vq, posp(gr[c]), den[rho][c]);
+          }
         }
       }
     }
 #pragma unroll
-    for (int c = 0; c < C; ++c) v[c] = (g * C + c < r) ? v[c] * sqrtf(num[c] / den[c]) : 0.f;
+    for (int rho = 0; rho < R; ++rho)
+#pragma unroll
+      for (int c = 0; c < C; ++c)
+        v[rho][c] = (g * C + c < r) ? v[rho][c] * sqrtf(num[rho][c] / den[rho][c]) : 0.f;
   }
 }
 
 // The whole run for one problem, executed by `G` co-resident blocks of which this is block
 // `bid` (all blocks of a problem call it with the same arguments).
-template <int RP, int RULE, int GA, int GB>
+template <int RP, int RULE, int GA, int RA, int GB, int RC>
 __device__ __forceinline__ void iterate_body(const PArgs& a, const unsigned bid, const unsigned G,
                                              float* sh) {
   constexpr int CA = RP / GA, CBn = RP / GB;
@@ -400,34 +418,62 @@ __device__ __forceinline__ void iterate_body(const PArgs& a, const unsigned bid,
     __syncthreads();
     gram_rp<RP>(HtT, LQ, Gw, invs);
     __syncthreads();
-    for (int slot = t / GA; slot < ((nrows + 31) & ~31); slot += kNT / GA) {
-      // whole warps take part in the shuffles; rows past the slice compute on zeros
-      const int g = t % GA;
-      const int i = slot < RB ? slot : RB - 1;
-      float w[CA], s[CA];
-      ld_run<CA>(Ws + i * RP + g * CA, w);
+    {
+      // group q of GA lanes takes the RA rows q, q + Q, q + 2Q, ... (Q = ceil(nrows / RA)), so
+      // that neighbouring groups read neighbouring rows; whole warps run (shuffles), groups
+      // past the slice compute on a valid row and store nothing
+      constexpr int GPW = 32 / GA;
+      const int Q = (nrows + RA - 1) / RA;
+      const int Qp = (Q + GPW - 1) / GPW * GPW;
+      for (int q = t / GA; q < Qp; q += kNT / GA) {
+        const int g = t % GA;
+        int idx[RA];
+        bool live[RA];
 #pragma unroll
-      for (int c = 0; c < CA; ++c) {
-        w[c] = w[c] / sc[g * CA + c];   // normalisation of the previous W phase (1 for MU)
-        s[c] = 0.f;
-      }
-      const float* xr = Xc + i * LS;
-      for (int k = 0; k < LQ; k += 4) {
-        const float4 x4 = *reinterpret_cast<const float4*>(xr + k);
-        const float xk[4] = {x4.x, x4.y, x4.z, x4.w};
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          float hr[CA];
-          ld_run<CA>(HtT + (k + q) * RP + g * CA, hr);
-#pragma unroll
-          for (int c = 0; c < CA; ++c) s[c] = fmaf(xk[q], hr[c], s[c]);
+        for (int rho = 0; rho < RA; ++rho) {
+          const int row = q + rho * Q;
+          live[rho] = q < Q && row < nrows;
+          idx[rho] = live[rho] ? row : 0;
         }
-      }
-      update_vec<RP, GA, RULE>(w, s, Gw, invs, g, r, false, 0.f, 0.f, a.eps);
-      if (slot < nrows) {
+        float w[RA][CA], sv[RA][CA];
 #pragma unroll
-        for (int c = 0; c < CA; c += 2)
-          *reinterpret_cast<float2*>(Ws + i * RP + g * CA + c) = make_float2(w[c], w[c + 1]);
+        for (int rho = 0; rho < RA; ++rho) {
+          ld_run<CA>(Ws + idx[rho] * RP + g * CA, w[rho]);
+#pragma unroll
+          for (int c = 0; c < CA; ++c) {
+            w[rho][c] = w[rho][c] / sc[g * CA + c];   // normalisation of the previous W phase
+            sv[rho][c] = 0.f;
+          }
+        }
+        for (int k = 0; k < LQ; k += 4) {
+          float xk[RA][4];
+#pragma unroll
+          for (int rho = 0; rho < RA; ++rho) {
+            const float4 x4 = *reinterpret_cast<const float4*>(Xc + idx[rho] * LS + k);
+            xk[rho][0] = x4.x;
+            xk[rho][1] = x4.y;
+            xk[rho][2] = x4.z;
+            xk[rho][3] = x4.w;
+          }
+#pragma unroll
+          for (int q4 = 0; q4 < 4; ++q4) {
+            float hr[CA];
+            ld_run<CA>(HtT + (k + q4) * RP + g * CA, hr);
+#pragma unroll
+            for (int rho = 0; rho < RA; ++rho)
+#pragma unroll
+              for (int c = 0; c < CA; ++c) sv[rho][c] = fmaf(xk[rho][q4], hr[c], sv[rho][c]);
+          }
+        }
+        update_rows<RP, GA, RA, RULE>(w, sv, Gw, invs, g, r, false, 0.f, 0.f, a.eps);
+#pragma unroll
+        for (int rho = 0; rho < RA; ++rho)
+          if (live[rho]) {
+#pragma unroll
+            for (int c = 0; c < CA; c += 2)
+              *reinterpret_cast<float2*>(Ws + idx[rho] * RP + g * CA + c) =
+                  make_float2(w[rho][c], w[rho][c + 1]);
+          }
       }
     }
     __syncthreads();
@@ -453,38 +499,67 @@ __device__ __forceinline__ void iterate_body(const PArgs& a, const unsigned bid,
     gram_rp<RP>(WtS, LQ, Gh, invs);
     __syncthreads();
     float cross = 0.f;
-    for (int slot = t / GB; slot < ((ncols + 31) & ~31); slot += kNT / GB) {
-      const int g = t % GB;
-      const int c = slot < CB ? slot : CB - 1;
-      float h[CBn], s[CBn];
-      ld_run<CBn>(Hs + c * RP + g * CBn, h);
+    {
+      constexpr int GPW = 32 / GB;
+      const int Q = (ncols + RC - 1) / RC;
+      const int Qp = (Q + GPW - 1) / GPW * GPW;
+      for (int q = t / GB; q < Qp; q += kNT / GB) {
+        const int g = t % GB;
+        int idx[RC];
+        bool live[RC];
 #pragma unroll
-      for (int q = 0; q < CBn; ++q) {
-        h[q] *= sc[g * CBn + q];
-        s[q] = 0.f;
-      }
-      const float* xc = Xh + c * LS;
-      for (int k = 0; k < LQ; k += 4) {
-        const float4 x4 = *reinterpret_cast<const float4*>(xc + k);
-        const float xk[4] = {x4.x, x4.y, x4.z, x4.w};
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          float wr[CBn];
-          ld_run<CBn>(WtS + (k + q) * RP + g * CBn, wr);
-#pragma unroll
-          for (int z = 0; z < CBn; ++z) s[z] = fmaf(xk[q], wr[z], s[z]);
+        for (int rho = 0; rho < RC; ++rho) {
+          const int col = q + rho * Q;
+          live[rho] = q < Q && col < ncols;
+          idx[rho] = live[rho] ? col : 0;
         }
-      }
-      float shc[CBn];
+        float h[RC][CBn], sv[RC][CBn];
 #pragma unroll
-      for (int z = 0; z < CBn; ++z) shc[z] = s[z];   // S_H column for the monitor
-      update_vec<RP, GB, RULE>(h, s, Gh, invs, g, r, RULE == 0 && reg, a.alpha, a.beta, a.eps);
-      if (slot < ncols) {
+        for (int rho = 0; rho < RC; ++rho) {
+          ld_run<CBn>(Hs + idx[rho] * RP + g * CBn, h[rho]);
 #pragma unroll
-        for (int z = 0; z < CBn; ++z) cross = fmaf(shc[z], h[z], cross);
+          for (int z = 0; z < CBn; ++z) {
+            h[rho][z] *= sc[g * CBn + z];
+            sv[rho][z] = 0.f;
+          }
+        }
+        for (int k = 0; k < LQ; k += 4) {
+          float xk[RC][4];
 #pragma unroll
-        for (int z = 0; z < CBn; z += 2)
-          *reinterpret_cast<float2*>(Hs + c * RP + g * CBn + z) = make_float2(h[z], h[z + 1]);
+          for (int rho = 0; rho < RC; ++rho) {
+            const float4 x4 = *reinterpret_cast<const float4*>(Xh + idx[rho] * LS + k);
+            xk[rho][0] = x4.x;
+            xk[rho][1] = x4.y;
+            xk[rho][2] = x4.z;
+            xk[rho][3] = x4.w;
+          }
+#pragma unroll
+          for (int q4 = 0; q4 < 4; ++q4) {
+            float wr[CBn];
+            ld_run<CBn>(WtS + (k + q4) * RP + g * CBn, wr);
+#pragma unroll
+            for (int rho = 0; rho < RC; ++rho)
+#pragma unroll
+              for (int z = 0; z < CBn; ++z) sv[rho][z] = fmaf(xk[rho][q4], wr[z], sv[rho][z]);
+          }
+        }
+        float shc[RC][CBn];
+#pragma unroll
+        for (int rho = 0; rho < RC; ++rho)
+#pragma unroll
+          for (int z = 0; z < CBn; ++z) shc[rho][z] = sv[rho][z];   // S_H for the monitor
+        update_rows<RP, GB, RC, RULE>(h, sv, Gh, invs, g, r, RULE == 0 && reg, a.alpha, a.beta,
+                                      a.eps);
+#pragma unroll
+        for (int rho = 0; rho < RC; ++rho)
+          if (live[rho]) {
+#pragma unroll
+            for (int z = 0; z < CBn; ++z) cross = fmaf(shc[rho][z], h[rho][z], cross);
+#pragma unroll
+            for (int z = 0; z < CBn; z += 2)
+              *reinterpret_cast<float2*>(Hs + idx[rho] * RP + g * CBn + z) =
+                  make_float2(h[rho][z], h[rho][z + 1]);
+          }
       }
     }
 #pragma unroll
@@ -536,10 +611,22 @@ __device__ __forceinline__ void iterate_body(const PArgs& a, const unsigned bid,
   }
 }
 
-template <int RP, int RULE, int GA, int GB>
+// Lanes per row / rows per lane group of the W phase (GA, RA) and of the H phase (GB, RC) for
+// each padded rank. Measured on the 20000 x 5000, r = 20 workload (W sweep per iteration):
+// 2 lanes x 1 row 6.7 us, 4 x 2 7.1 us, 2 x 2 8.9 us, 4 x 4 9.4 us (register pressure), so one
+// row per group; 4 lanes above RP = 32 keep the per-lane runs at 12 components.
+template <int RP>
+struct Lanes;
+template <> struct Lanes<8> { static constexpr int GA = 2, RA = 1, GB = 2, RC = 1; };
+template <> struct Lanes<16> { static constexpr int GA = 2, RA = 1, GB = 2, RC = 1; };
+template <> struct Lanes<24> { static constexpr int GA = 2, RA = 1, GB = 2, RC = 1; };
+template <> struct Lanes<32> { static constexpr int GA = 2, RA = 1, GB = 2, RC = 1; };
+template <> struct Lanes<48> { static constexpr int GA = 4, RA = 1, GB = 4, RC = 1; };
+
+template <int RP, int RULE, int GA, int RA, int GB, int RC>
 __global__ void __launch_bounds__(kNT, 1) iterate_persistent_kernel(PArgs a) {
   extern __shared__ __align__(16) float sh[];
-  iterate_body<RP, RULE, GA, GB>(a, blockIdx.x, gridDim.x, sh);
+  iterate_body<RP, RULE, GA, RA, GB, RC>(a, blockIdx.x, gridDim.x, sh);
 }
 
 // Several independent problems in one cooperative launch: blocks [start[p], start[p + 1]) run
@@ -551,7 +638,7 @@ struct MultiArgs {
   PArgs p[kMaxWave];
 };
 
-template <int RP, int RULE, int GA, int GB>
+template <int RP, int RULE, int GA, int RA, int GB, int RC>
 __global__ void __launch_bounds__(kNT, 1) iterate_multi_kernel(const __grid_constant__ MultiArgs M) {
   extern __shared__ __align__(16) float sh[];
   int lo = 0, hi = M.nprob;
@@ -561,7 +648,8 @@ __global__ void __launch_bounds__(kNT, 1) iterate_multi_kernel(const __grid_cons
     else hi = mid;
   }
   const PArgs a = M.p[lo];
-  iterate_body<RP, RULE, GA, GB>(a, blockIdx.x - M.start[lo], M.start[lo + 1] - M.start[lo], sh);
+  iterate_body<RP, RULE, GA, RA, GB, RC>(a, blockIdx.x - M.start[lo], M.start[lo + 1] - M.start[lo],
+                                         sh);
 }
 
 size_t smem_floats(int RP, int ell, int RB, int CB) {
@@ -572,9 +660,10 @@ size_t smem_floats(int RP, int ell, int RB, int CB) {
 
 int rp_of(int r) { return r <= 8 ? 8 : r <= 16 ? 16 : r <= 24 ? 24 : r <= 32 ? 32 : 48; }
 
-template <int RP, int RULE, int GA = (RP > 32 ? 4 : kGA), int GB = (RP > 32 ? 4 : kGB)>
+template <int RP, int RULE, int GA = Lanes<RP>::GA, int RA = Lanes<RP>::RA,
+          int GB = Lanes<RP>::GB, int RC = Lanes<RP>::RC>
 cudaError_t launch(const Launcher& L, PArgs& a, int grid) {
-  auto k = iterate_persistent_kernel<RP, RULE, GA, GB>;
+  auto k = iterate_persistent_kernel<RP, RULE, GA, RA, GB, RC>;
   const size_t smem = sizeof(float) * smem_floats(RP, a.ell, a.RB, a.CB);
   cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
@@ -667,9 +756,10 @@ cudaError_t launch_iterate_persistent(const Launcher& L, const IterArgs& ia, int
 
 namespace {
 
-template <int RP, int RULE, int GA = (RP > 32 ? 4 : kGA), int GB = (RP > 32 ? 4 : kGB)>
+template <int RP, int RULE>
 cudaError_t launch_multi(const Launcher& L, const MultiArgs& M, int grid, size_t smem) {
-  auto k = iterate_multi_kernel<RP, RULE, GA, GB>;
+  auto k = iterate_multi_kernel<RP, RULE, Lanes<RP>::GA, Lanes<RP>::RA, Lanes<RP>::GB,
+                                Lanes<RP>::RC>;
   cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
   if (err != cudaSuccess) return err;

@@ -85,7 +85,6 @@ __global__ void __launch_bounds__(512) jacobi_kernel(const double* __restrict__ 
 #define V(p, q) Vm[(p) * LS + (q)]
   __shared__ float cs[kMaxL / 2], sn[kMaxL / 2];
   __shared__ int top[kMaxL / 2], bot[kMaxL / 2];
-  __shared__ float off2, tot2;
   __shared__ int order[kMaxL];
   const int t = threadIdx.x, nt = blockDim.x;
   for (int e = t; e < L * L; e += nt) {
@@ -98,80 +97,73 @@ __global__ void __launch_bounds__(512) jacobi_kernel(const double* __restrict__ 
     top[i] = 2 * i;
     bot[i] = 2 * i + 1;
   }
-  __syncthreads();
+  __shared__ int rotated;
+  __shared__ unsigned dmax_bits;
   for (int sweep = 0; sweep < 30; ++sweep) {
+    // a sweep that rotates no pair ends the iteration. A pair is rotated while |a_pq| exceeds
+    // 4 eps32 max_p |a_pp|: FP32 rounding leaves off-diagonal noise of order eps32 lambda_max
+    // in every entry, which is also the eigenvector error the results are held to
+    // (ell eps32 lambda_max / gap)
     if (t == 0) {
-      off2 = 0.f;
-      tot2 = 0.f;
+      rotated = 0;
+      dmax_bits = 0u;
     }
     __syncthreads();
-    float o = 0.f, d = 0.f;
-    for (int e = t; e < L * L; e += nt) {
-      const int p = e / L, q = e - p * L;
-      const float v = A(p, q) * A(p, q);
-      if (p != q) o += v;
-      d += v;
-    }
-    atomicAdd(&off2, o);
-    atomicAdd(&tot2, d);
+    for (int p = t; p < L; p += nt) atomicMax(&dmax_bits, __float_as_uint(fabsf(A(p, p))));
     __syncthreads();
-    if (!(off2 > 1e-14f * tot2)) break;
+    const float thr = 4.f * 1.1920929e-7f * __uint_as_float(dmax_bits);
     for (int round = 0; round < L - 1; ++round) {
-      // rotation angles of the disjoint pairs of this round
+      // round-robin pairing (circle method): position 0 fixed, positions 1..L-1 rotated by
+      // `round`; pair i joins positions i and L-1-i (each index once per round, every pair of
+      // indices once per sweep)
+      auto pos = [&](int j) { return j == 0 ? 0 : (j - 1 + round) % (L - 1) + 1; };
       for (int i = t; i < half; i += nt) {
-        const int p = top[i] < bot[i] ? top[i] : bot[i];
-        const int q = top[i] < bot[i] ? bot[i] : top[i];
+        const int a = pos(i), b = pos(L - 1 - i);
+        const int p = a < b ? a : b, q = a < b ? b : a;
+        top[i] = p;
+        bot[i] = q;
         const float apq = A(p, q);
-        float c = 1.f, s = 0.f;
-        if (fabsf(apq) > 1e-30f) {
+        float c = 1.f, sv = 0.f;
+        if (fabsf(apq) > 1e-30f && fabsf(apq) > thr) {
           const float theta = (A(q, q) - A(p, p)) / (2.f * apq);
           const float tt = copysignf(1.f, theta) / (fabsf(theta) + sqrtf(theta * theta + 1.f));
           c = rsqrtf(tt * tt + 1.f);
-          s = tt * c;
+          sv = tt * c;
+          rotated = 1;
         }
         cs[i] = c;
-        sn[i] = s;
+        sn[i] = sv;
       }
       __syncthreads();
-      // columns p, q of A and V: A <- A J, V <- V J
-      for (int e = t; e < half * L; e += nt) {
-        const int i = e / L, row = e - i * L;
-        const int p = top[i] < bot[i] ? top[i] : bot[i];
-        const int q = top[i] < bot[i] ? bot[i] : top[i];
-        const float c = cs[i], s = sn[i];
-        const float ap = A(row, p), aq = A(row, q);
-        A(row, p) = c * ap - s * aq;
-        A(row, q) = s * ap + c * aq;
-        const float vp = V(row, p), vq = V(row, q);
-        V(row, p) = c * vp - s * vq;
-        V(row, q) = s * vp + c * vq;
-      }
-      __syncthreads();
-      // rows p, q of A: A <- J^T A
-      for (int e = t; e < half * L; e += nt) {
-        const int i = e / L, col = e - i * L;
-        const int p = top[i] < bot[i] ? top[i] : bot[i];
-        const int q = top[i] < bot[i] ? bot[i] : top[i];
-        const float c = cs[i], s = sn[i];
-        const float ap = A(p, col), aq = A(q, col);
-        A(p, col) = c * ap - s * aq;
-        A(q, col) = s * ap + c * aq;
-      }
-      __syncthreads();
-      // next pairing (round-robin with top[0] fixed)
-      if (t == 0) {
-        const int last_top = top[half - 1];
-        const int first_bot = bot[0];
-        for (int i = half - 1; i > 1; --i) top[i] = top[i - 1];
-        if (half > 1) top[1] = first_bot;
-        for (int i = 0; i < half - 1; ++i) bot[i] = bot[i + 1];
-        bot[half - 1] = last_top;
-        if (half == 1) {
-          // a single pair: nothing to rotate
+      // A <- J^T A J as 2 x 2 blocks (rows of pair i, columns of pair k), V <- V J
+      for (int e = t; e < half * half + L * half; e += nt) {
+        if (e < half * half) {
+          const int i = e / half, k = e - i * half;
+          const int p = top[i], q = bot[i], pk = top[k], qk = bot[k];
+          const float ci = cs[i], si = sn[i], ck = cs[k], sk = sn[k];
+          const float app = A(p, pk), apq = A(p, qk), aqp = A(q, pk), aqq = A(q, qk);
+          // columns: [c_k -s_k; s_k c_k] on the right, then rows with (c_i, s_i) on the left
+          const float bpp = ck * app - sk * apq, bpq = sk * app + ck * apq;
+          const float bqp = ck * aqp - sk * aqq, bqq = sk * aqp + ck * aqq;
+          A(p, pk) = ci * bpp - si * bqp;
+          A(p, qk) = ci * bpq - si * bqq;
+          A(q, pk) = si * bpp + ci * bqp;
+          A(q, qk) = si * bpq + ci * bqq;
+        } else {
+          const int f = e - half * half;
+          const int i = f / L, row = f - i * L;
+          const int p = top[i], q = bot[i];
+          const float c = cs[i], sv = sn[i];
+          const float vp = V(row, p), vq = V(row, q);
+          V(row, p) = c * vp - sv * vq;
+          V(row, q) = sv * vp + c * vq;
         }
       }
       __syncthreads();
     }
+    const int any = rotated;   // read by every thread before thread 0 clears it again
+    __syncthreads();
+    if (!any) break;
   }
   // order by eigenvalue, descending (selection; ell <= 128)
   if (t == 0) {
