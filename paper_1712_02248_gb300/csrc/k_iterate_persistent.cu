@@ -24,6 +24,9 @@
 // updated too instead of being masked). These are the Gauss-Seidel values of the paper's
 // component-by-component update.
 //
+// The per-element scalings use reciprocals formed once per phase (an IEEE division per element of
+// a row cost as much as the row's whole S product).
+//
 // Block shares of the cross-block sums are register-tiled (4 x 4 outputs a thread, the rows of
 // the slice split over thread groups) and summed in a fixed order in shared memory, then added
 // with vector FP32 atomics into kCopies copies (block b into copy b % kCopies); readers sum the
@@ -357,7 +360,8 @@ __device__ __forceinline__ void iterate_body(const PArgs& a, const unsigned bid,
   float* Gh = WtS + LQ * RP;        // [RP][RP]
   float* sc = Gh + RP * RP;         // [RP]       s_j of the last W phase
   float* invs = sc + RP;            // [RP]       1 / G_jj of the current phase
-  float* Ws = invs + RP;            // [RB][RP]   rows of W (unnormalised)
+  float* rsc = invs + RP;           // [RP]       1 / s_j
+  float* Ws = rsc + RP;             // [RB][RP]   rows of W (unnormalised)
   float* Hs = Ws + RB * RP;         // [CB][RP]   columns of H
   float* Xc = Hs + CB * RP;         // [RB][LS]   rows of X_chk
   float* Ql = Xc + RB * LS;         // [RB][LS]   rows of Q_L
@@ -375,7 +379,10 @@ __device__ __forceinline__ void iterate_body(const PArgs& a, const unsigned bid,
   unsigned epoch = 0;
 
   // ---- stage the slice (zero-padded) and the factors
-  for (int j = t; j < RP; j += kNT) sc[j] = 1.f;
+  for (int j = t; j < RP; j += kNT) {
+    sc[j] = 1.f;
+    rsc[j] = 1.f;
+  }
   for (int e = t; e < RB * RP; e += kNT) {
     const int i = e / RP, j = e - i * RP;
     Ws[e] = (i < nrows && j < r) ? a.W[(r0 + i) * r + j] : 0.f;
@@ -441,7 +448,7 @@ __device__ __forceinline__ void iterate_body(const PArgs& a, const unsigned bid,
           ld_run<CA>(Ws + idx[rho] * RP + g * CA, w[rho]);
 #pragma unroll
           for (int c = 0; c < CA; ++c) {
-            w[rho][c] = w[rho][c] / sc[g * CA + c];   // normalisation of the previous W phase
+            w[rho][c] *= rsc[g * CA + c];   // normalisation of the previous W phase
             sv[rho][c] = 0.f;
           }
         }
@@ -490,10 +497,12 @@ __device__ __forceinline__ void iterate_body(const PArgs& a, const unsigned bid,
       const float* accA_r = a.accA + ph * kCopies * EA;
       for (int j = t; j < RP; j += kNT) {
         const float c2 = acc_read(accA_r, EA, (LQ + j) * RP + j);
-        sc[j] = (normalize && j < r && c2 > 0.f) ? sqrtf(c2) : 1.f;
+        const float sj = (normalize && j < r && c2 > 0.f) ? sqrtf(c2) : 1.f;
+        sc[j] = sj;
+        rsc[j] = 1.f / sj;
       }
       __syncthreads();
-      for (int e = t; e < LQ * RP; e += kNT) WtS[e] = acc_read(accA_r, EA, e) / sc[e % RP];
+      for (int e = t; e < LQ * RP; e += kNT) WtS[e] = acc_read(accA_r, EA, e) * rsc[e % RP];
     }
     __syncthreads();
     gram_rp<RP>(WtS, LQ, Gh, invs);
@@ -654,7 +663,7 @@ __global__ void __launch_bounds__(kNT, 1) iterate_multi_kernel(const __grid_cons
 
 size_t smem_floats(int RP, int ell, int RB, int CB) {
   const int LQ = lq_of(ell), LS = lsx_of(ell);
-  return static_cast<size_t>(2 * LQ * RP + 2 * RP * RP + 2 * RP) + static_cast<size_t>(RB + CB) * RP +
+  return static_cast<size_t>(2 * LQ * RP + 2 * RP * RP + 3 * RP) + static_cast<size_t>(RB + CB) * RP +
          static_cast<size_t>(2 * RB + 2 * CB) * LS + kNT * 16;
 }
 
