@@ -5,10 +5,11 @@
 // Precision. Sweep 1 sees cond(G) = cond(Y)^2, so its Gram matrix is accumulated in float-float
 // arithmetic (error-free products by FMA and Knuth's TwoSum; about 48 significant bits, relative
 // error near 1e-12 over a 128-row slab) and summed across slabs in FP64; its Cholesky factor and
-// R^{-1} are formed in FP64 (an l x l problem) and R^{-1} is applied in float-float, since its
-// entries reach cond(Y) and their products cancel. The FP64 pipe of this GPU runs at 1/58 of the
-// FP32 rate, so the X-sized Gram and application run on the FP32 pipes. Sweep 2 starts from a
-// nearly orthonormal matrix: its Gram is float-float, its Cholesky and application FP32. The
+// R^{-1} are formed in float-float too (an l x l problem, ~44 bits) and R^{-1} is applied in
+// float-float, since its entries reach cond(Y) and their products cancel. The FP64 pipe of this
+// GPU runs at 1/58 of the FP32 rate (a warp-wide FP64 instruction holds its scheduler's FP64
+// pipe for ~67 cycles), so everything runs on the FP32 pipes. Sweep 2 starts from a nearly
+// orthonormal matrix: its Gram and factor are float-float as well, its application FP32. The
 // result is the Q of the QR factorisation whose R has a positive diagonal.
 //
 // Up to two independent matrices (the two chains of the sketch) go through each kernel in one
@@ -104,81 +105,152 @@ __global__ void sum_parts_kernel(const double* __restrict__ Gp, QrBatch b, int e
   if (lane == 0) G[mat * entries + warp] = s;
 }
 
-__device__ __forceinline__ double rsqrt_any(double v) { return rsqrt(v); }
-__device__ __forceinline__ float rsqrt_any(float v) { return rsqrtf(v); }
+// ---- float-float arithmetic (a value is hi + lo, |lo| <= ulp(hi) / 2; about 44 significant
+// bits): Knuth's TwoSum, the FMA-based exact product, and Newton-corrected square root and
+// reciprocal. Used for the l x l Cholesky factor and its inverse, which need more than FP32 when
+// the sketch is ill-conditioned; the FP64 pipe of this GPU runs at 1/58 of the FP32 rate.
+struct FF {
+  float hi, lo;
+};
 
-// One CTA per matrix: Cholesky G = R^T R in precision F (in place on the upper triangle), then
-// T = R^{-1}, whose strictly upper part is kept transposed in the lower triangle of the same
-// array. Writes T split as T_hi + T_lo (two FP32 arrays, ell x ell row-major).
-template <int LP, typename F>
-__global__ void __launch_bounds__(256) chol_inv_kernel(const double* __restrict__ Gin, QrBatch b,
-                                                       int ell, float* __restrict__ Thi,
-                                                       float* __restrict__ Tlo, int* status) {
+__device__ __forceinline__ FF ff_quick(float a, float b) {   // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ FF ff_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float v = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, v)), __fsub_rn(b, v))};
+}
+__device__ __forceinline__ FF ff_add(FF x, FF y) {
+  FF s = ff_two_sum(x.hi, y.hi);
+  const FF t = ff_two_sum(x.lo, y.lo);
+  s.lo = __fadd_rn(s.lo, t.hi);
+  s = ff_quick(s.hi, s.lo);
+  s.lo = __fadd_rn(s.lo, t.lo);
+  return ff_quick(s.hi, s.lo);
+}
+__device__ __forceinline__ FF ff_neg(FF x) { return {-x.hi, -x.lo}; }
+__device__ __forceinline__ FF ff_mul(FF x, FF y) {
+  const float p = __fmul_rn(x.hi, y.hi);
+  float e = __fmaf_rn(x.hi, y.hi, -p);
+  e = __fmaf_rn(x.hi, y.lo, e);
+  e = __fmaf_rn(x.lo, y.hi, e);
+  return ff_quick(p, e);
+}
+// 1 / x: FP32 estimate, one Newton step in float-float (r + r (1 - x r))
+__device__ __forceinline__ FF ff_recip(FF x) {
+  const float r = __frcp_rn(x.hi);
+  const FF e = ff_add({1.f, 0.f}, ff_neg(ff_mul(x, {r, 0.f})));
+  return ff_add({r, 0.f}, ff_mul({r, 0.f}, e));
+}
+// sqrt(x): FP32 estimate q, one correction (x - q^2) / (2 q)
+__device__ __forceinline__ FF ff_sqrt(FF x) {
+  const float q = __fsqrt_rn(x.hi);
+  const FF d = ff_add(x, ff_neg(ff_mul({q, 0.f}, {q, 0.f})));
+  return ff_quick(q, __fdiv_rn(d.hi, __fmul_rn(2.f, q)));
+}
+
+// One block per matrix: Cholesky G = R^T R in float-float (in place on the upper triangle; G
+// arrives in FP64), then T = R^{-1} by back substitution, one column per thread (T[k][c] for
+// k < c kept transposed in the lower triangle), four partial sums a column for latency. Writes T
+// as T_hi + T_lo (two FP32 arrays, ell x ell row-major).
+template <int LP>
+__global__ void __launch_bounds__(256) chol_inv_ff_kernel(const double* __restrict__ Gin,
+                                                          QrBatch b, int ell,
+                                                          float* __restrict__ Thi,
+                                                          float* __restrict__ Tlo, int* status) {
   constexpr int S = LP + 1;
-  extern __shared__ __align__(16) unsigned char chol_sm[];
-  F* A = reinterpret_cast<F*>(chol_sm);   // [LP][S]
-  F* dinv = A + LP * S;                     // [LP]   1 / R[j][j]
+  extern __shared__ __align__(16) float chol_ff_sm[];
+  float* Ah = chol_ff_sm;         // [LP][S]
+  float* Al = Ah + LP * S;        // [LP][S]
+  float* dh = Al + LP * S;        // [LP]  1 / R[j][j]
+  float* dl = dh + LP;
   __shared__ int bad;
   const int mat = blockIdx.x;
   if (mat >= b.nmat) return;
   const double* G = Gin + static_cast<int64_t>(mat) * LP * LP;
   const int t = threadIdx.x, nt = blockDim.x;
   if (t == 0) bad = 0;
-  for (int e = t; e < LP * LP; e += nt) {
-    const int p = e / LP, q = e - p * LP;
-    A[p * S + q] = (p <= q && q < ell) ? static_cast<F>(G[p * LP + q]) : F(0);
-  }
+  for (int p = t >> 5; p < LP; p += nt >> 5)
+    for (int q = t & 31; q < LP; q += 32) {
+      const double g = (p <= q && q < ell) ? G[p * LP + q] : 0.0;
+      const float hi = static_cast<float>(g);
+      Ah[p * S + q] = hi;
+      Al[p * S + q] = static_cast<float>(g - static_cast<double>(hi));
+    }
   __syncthreads();
   for (int j = 0; j < ell; ++j) {
     if (t == 0) {
-      F d = A[j * S + j];
+      FF d = {Ah[j * S + j], Al[j * S + j]};
       // a non-positive pivot: the sketch is numerically rank deficient
-      if (!(d > F(0))) {
+      if (!(d.hi > 0.f)) {
         bad = 1;
-        d = F(1e-30);
+        d = {1e-30f, 0.f};
       }
-      const F inv = rsqrt_any(d);
-      A[j * S + j] = d * inv;
-      dinv[j] = inv;
+      const FF r = ff_sqrt(d);
+      const FF ri = ff_recip(r);
+      Ah[j * S + j] = r.hi;
+      Al[j * S + j] = r.lo;
+      dh[j] = ri.hi;
+      dl[j] = ri.lo;
     }
     __syncthreads();
-    const F inv = dinv[j];
-    for (int q = j + 1 + t; q < ell; q += nt) A[j * S + q] *= inv;
+    const FF ri = {dh[j], dl[j]};
+    for (int q = j + 1 + t; q < ell; q += nt) {
+      const FF v = ff_mul({Ah[j * S + q], Al[j * S + q]}, ri);
+      Ah[j * S + q] = v.hi;
+      Al[j * S + q] = v.lo;
+    }
     __syncthreads();
-    const int w = ell - j - 1;
-    for (int e = t; e < w * w; e += nt) {
-      const int p = j + 1 + e / w, q = j + 1 + e % w;
-      if (p <= q) A[p * S + q] -= A[j * S + p] * A[j * S + q];
+    for (int p = j + 1 + (t >> 5); p < ell; p += nt >> 5) {
+      const FF ajp = {Ah[j * S + p], Al[j * S + p]};
+      for (int q = p + (t & 31); q < ell; q += 32) {
+        const FF v = ff_add({Ah[p * S + q], Al[p * S + q]},
+                            ff_neg(ff_mul(ajp, {Ah[j * S + q], Al[j * S + q]})));
+        Ah[p * S + q] = v.hi;
+        Al[p * S + q] = v.lo;
+      }
     }
     __syncthreads();
   }
   // T[c][c] = 1 / R[c][c];  T[i][c] = -(sum_{k=i+1..c} R[i][k] T[k][c]) / R[i][i]
-  // (one warp per column; T[k][c] for k < c lives at A[c][k])
-  const int warp = t >> 5, lane = t & 31, nw = nt >> 5;
-  for (int c = warp; c < ell; c += nw) {
-    const F tcc = dinv[c];
+  for (int c = t; c < ell; c += nt) {
+    const FF tcc = {dh[c], dl[c]};
     for (int i = c - 1; i >= 0; --i) {
-      F s = F(0);
-      for (int k = i + 1 + lane; k <= c; k += 32)
-        s += A[i * S + k] * ((k == c) ? tcc : A[c * S + k]);
+      FF acc[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+      acc[0] = ff_mul({Ah[i * S + c], Al[i * S + c]}, tcc);
+      int k = i + 1;
+      for (; k + 3 < c; k += 4) {
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) A[c * S + i] = -s * dinv[i];
-      __syncwarp();
+        for (int u = 0; u < 4; ++u)
+          acc[u] = ff_add(acc[u], ff_mul({Ah[i * S + k + u], Al[i * S + k + u]},
+                                         {Ah[c * S + k + u], Al[c * S + k + u]}));
+      }
+      for (; k < c; ++k)
+        acc[0] = ff_add(acc[0], ff_mul({Ah[i * S + k], Al[i * S + k]}, {Ah[c * S + k], Al[c * S + k]}));
+      const FF sum = ff_add(ff_add(acc[0], acc[1]), ff_add(acc[2], acc[3]));
+      const FF v = ff_neg(ff_mul(sum, {dh[i], dl[i]}));
+      Ah[c * S + i] = v.hi;
+      Al[c * S + i] = v.lo;
     }
   }
   __syncthreads();
   float* th = Thi + static_cast<int64_t>(mat) * ell * ell;
   float* tl = Tlo + static_cast<int64_t>(mat) * ell * ell;
-  for (int e = t; e < ell * ell; e += nt) {
-    const int p = e / ell, q = e - p * ell;
-    F v = F(0);
-    if (p == q) v = dinv[p];
-    else if (p < q) v = A[q * S + p];
-    const float hi = static_cast<float>(v);
-    th[e] = hi;
-    tl[e] = static_cast<float>(v - static_cast<F>(hi));
-  }
+  for (int p = t >> 5; p < ell; p += nt >> 5)
+    for (int q = t & 31; q < ell; q += 32) {
+      float hi = 0.f, lo = 0.f;
+      if (p == q) {
+        hi = dh[p];
+        lo = dl[p];
+      } else if (p < q) {
+        hi = Ah[q * S + p];
+        lo = Al[q * S + p];
+      }
+      th[p * ell + q] = hi;
+      tl[p * ell + q] = lo;
+    }
   if (t == 0 && bad) latch(status, kStQrBreakdown);
 }
 
@@ -279,15 +351,12 @@ cudaError_t run(const Launcher& L, QrBatch b, int ell, char* ws, int* status) {
   }
   const size_t gram_smem = sizeof(float) * kGramRows * LP;
   const size_t apply_smem = sizeof(float) * 2 * LP * LP;
-  const size_t chol_smem64 = sizeof(double) * (LP * (LP + 1) + LP);
-  const size_t chol_smem32 = sizeof(float) * (LP * (LP + 1) + LP);
+  const size_t chol_smemff = sizeof(float) * (2 * LP * (LP + 1) + 2 * LP);
   cudaError_t err;
-  if ((err = cudaFuncSetAttribute(chol_inv_kernel<LP, double>,
+  if ((err = cudaFuncSetAttribute(chol_inv_ff_kernel<LP>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  static_cast<int>(chol_smem64))) != cudaSuccess ||
-      (err = cudaFuncSetAttribute(chol_inv_kernel<LP, float>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  static_cast<int>(chol_smem32))) != cudaSuccess ||
+                                  static_cast<int>(chol_smemff))) != cudaSuccess ||
+
       (err = cudaFuncSetAttribute(gram_partial_kernel<LP>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   static_cast<int>(gram_smem))) != cudaSuccess ||
@@ -313,13 +382,11 @@ cudaError_t run(const Launcher& L, QrBatch b, int ell, char* ws, int* status) {
                               gram_smem, L.stream>>>(bb, ell, Gp);
     sum_parts_kernel<<<dim3(sum_grid, nmat), 256, 0, L.stream>>>(Gp, bb, LP * LP, G);
     if (sweep == 0) {
-      chol_inv_kernel<LP, double><<<nmat, 256, chol_smem64, L.stream>>>(G, bb, ell, Thi, Tlo,
-                                                                       status);
+      chol_inv_ff_kernel<LP><<<nmat, 256, chol_smemff, L.stream>>>(G, bb, ell, Thi, Tlo, status);
       apply_tri_kernel<LP, true><<<dim3(apply_grid, nmat), 256, apply_smem, L.stream>>>(
           bb, ell, Thi, Tlo);
     } else {
-      chol_inv_kernel<LP, float><<<nmat, 256, chol_smem32, L.stream>>>(G, bb, ell, Thi, Tlo,
-                                                                      status);
+      chol_inv_ff_kernel<LP><<<nmat, 256, chol_smemff, L.stream>>>(G, bb, ell, Thi, Tlo, status);
       apply_tri_kernel<LP, false><<<dim3(apply_grid, nmat), 256, apply_smem, L.stream>>>(
           bb, ell, Thi, Tlo);
     }
