@@ -12,8 +12,8 @@ produces. Definitions (r components, X ~ Q_L X_hat with X_hat = U' S V^T, u_j = 
                2 = negative parts, 3 = none (both products zero)
   p(x)         that part of x (|x|, x+, x-, 0)
   W_b[:, j]    p(u_j) / ||p(u_j)||            (unit columns)
-  H_b[j, :]    f_j^2 p(v_j) / ||p(v_j)||      f_j^2 = s_j ||p(u_j)|| ||p(v_j)|| (s_0 for j = 0),
-               so that W_b H_b equals the NNDSVD product
+  H_b[j, :]    f_j^2 p(v_j) / ||p(v_j)||      f_j^2 = s_j ||p(u_j)|| ||p(v_j)|| (for j = 0 the
+               norms are those of |u_0|, |v_0|, i.e. 1), so that W_b H_b is the NNDSVD product
   hscale_j     ||H_b[j, :]|| = f_j^2
   F_w[i]       [sqrt(m) c_j u_ij (j < r), sqrt(m) W_b[i, j] (j < r), s_j / s_0 (j < r)]
   F_h[c]       [sqrt(n) c_j v_cj, sqrt(n) H_b[j, c] / hscale_j, s_j / s_0]
@@ -156,7 +156,7 @@ def warmstart_features(QL, Xhat, r):
         px, py = _part(x, mode), _part(y, mode)
         nx, ny = np.linalg.norm(px), np.linalg.norm(py)
         if mode != 3 and nx > 0 and ny > 0:
-            f2 = s[j] * (nx * ny if j > 0 else 1.0)
+            f2 = s[j] * nx * ny
             Wb[:, j] = px / nx
             Hb[j, :] = f2 * py / ny
             hscale[j] = f2

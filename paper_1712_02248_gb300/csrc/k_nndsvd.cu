@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(512) jacobi_kernel(const double* __restrict__ 
       // A <- J^T A J as 2 x 2 blocks (rows of pair i, columns of pair k), V <- V J
       for (int e = t; e < half * half + L * half; e += nt) {
         if (e < half * half) {
-          const int i = e / half, k = e - i * half;
+          const int i = e / half, k = e - i * half;   // one division a task (few tasks a thread)
           const int p = top[i], q = bot[i], pk = top[k], qk = bot[k];
           const float ci = cs[i], si = sn[i], ck = cs[k], sk = sn[k];
           const float app = A(p, pk), apq = A(p, qk), aqp = A(q, pk), aqq = A(q, qk);
