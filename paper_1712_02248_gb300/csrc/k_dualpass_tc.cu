@@ -436,26 +436,36 @@ __global__ void transpose_bf16_kernel(const float* __restrict__ V, int64_t rows,
   }
 }
 
-// out[row][k] = sum over slots of part[slot][k][row] (fixed slot order), 32 rows a block,
-// transposed through shared memory so that both the reads and the writes are coalesced.
+// out[row][k] = sum over slots of part[slot][k][row] (fixed slot order). A block takes 32 rows x
+// 8 values of k, one sum a thread with eight slot loads in flight (coalesced over rows), and
+// writes its 32 x 8 tile transposed through shared memory.
 __global__ void __launch_bounds__(256) reduce_slots_t_kernel(const float* __restrict__ part,
                                                              int slots, int64_t rows, int ell,
                                                              float* __restrict__ out) {
-  __shared__ float tile[32][129];
+  __shared__ float tile[8][33];
   const int64_t row0 = static_cast<int64_t>(blockIdx.x) * 32;
+  const int k0 = blockIdx.y * 8;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int64_t r = row0 + tx;
-  for (int k = ty; k < ell; k += 8) {
-    float s = 0.f;
-    if (r < rows)
-      for (int c = 0; c < slots; ++c) s += __ldcg(part + (static_cast<int64_t>(c) * ell + k) * rows + r);
-    tile[tx][k] = s;
+  const int k = k0 + ty;
+  float s = 0.f;
+  if (r < rows && k < ell) {
+    const float* p = part + static_cast<int64_t>(k) * rows + r;
+    const int64_t slot_stride = static_cast<int64_t>(ell) * rows;
+    int c = 0;
+    for (; c + 8 <= slots; c += 8) {
+      float v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = __ldcg(p + (c + u) * slot_stride);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) s += v[u];
+    }
+    for (; c < slots; ++c) s += __ldcg(p + c * slot_stride);
   }
+  tile[ty][tx] = s;
   __syncthreads();
-  for (int e = threadIdx.x; e < 32 * ell; e += 256) {
-    const int i = e / ell, k = e - i * ell;
-    if (row0 + i < rows) out[(row0 + i) * ell + k] = tile[i][k];
-  }
+  const int i = threadIdx.x >> 3, j = threadIdx.x & 7;
+  if (row0 + i < rows && k0 + j < ell) out[(row0 + i) * ell + k0 + j] = tile[j][i];
 }
 
 // ------------------------------------------------------------------ host side
@@ -660,9 +670,10 @@ cudaError_t launch_dual_pass_tc(const Launcher& L, const __nv_bfloat16* X, int64
   cudaError_t err = sp == 2 ? launch_lp<2>(p.LP, L, mx, mv, mu, a, smem)
                             : launch_lp<1>(p.LP, L, mx, mv, mu, a, smem);
   if (err != cudaSuccess) return err;
-  reduce_slots_t_kernel<<<static_cast<unsigned>(cdiv(m, 32)), 256, 0, L.stream>>>(
+  const unsigned kg = static_cast<unsigned>(cdiv(ell, 8));
+  reduce_slots_t_kernel<<<dim3(static_cast<unsigned>(cdiv(m, 32)), kg), 256, 0, L.stream>>>(
       Ypart, p.colgroups, m, ell, Y);
-  reduce_slots_t_kernel<<<static_cast<unsigned>(cdiv(n, 32)), 256, 0, L.stream>>>(
+  reduce_slots_t_kernel<<<dim3(static_cast<unsigned>(cdiv(n, 32)), kg), 256, 0, L.stream>>>(
       Zpart, p.rowgroups, n, ell, Z);
   L.count(2);
   return cudaGetLastError();

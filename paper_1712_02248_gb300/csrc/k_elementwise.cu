@@ -95,18 +95,28 @@ __global__ void __launch_bounds__(256) quantize_bf16_stats_kernel(
   float fx2 = 0.f, fcorr = 0.f;
   int run = 0;
   if (VEC) {
-    const int64_t n4 = n / 4, total = m * n4;
-#pragma unroll 4
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
-      const int64_t i = e / n4, j4 = e - i * n4;
-      const float4 v = __ldcs(reinterpret_cast<const float4*>(X + i * ldx) + j4);
+    // grid-stride over the float4s of the m x n/4 array; the (row, float4) position advances by
+    // a fixed (di, dj) each step (one division a thread), two loads in flight a step
+    const int64_t n4 = n / 4;
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    const int64_t di = stride / n4, dj = stride - di * n4;
+    const int64_t e0 = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    int64_t i = e0 / n4, j4 = e0 - i * n4;
+    auto advance = [&](int64_t& ii, int64_t& jj) {
+      ii += di;
+      jj += dj;
+      if (jj >= n4) {
+        jj -= n4;
+        ++ii;
+      }
+    };
+    auto consume = [&](const float4 v, int64_t ii, int64_t jj) {
       __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y);
       __nv_bfloat162 hi = __floats2bfloat162_rn(v.z, v.w);
       uint2 packed;
       packed.x = *reinterpret_cast<uint32_t*>(&lo);
       packed.y = *reinterpret_cast<uint32_t*>(&hi);
-      reinterpret_cast<uint2*>(Xq + i * ldq)[j4] = packed;
+      reinterpret_cast<uint2*>(Xq + ii * ldq)[jj] = packed;
       const float2 ql = __bfloat1622float2(lo), qh = __bfloat1622float2(hi);
       fx2 = fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, fmaf(v.w, v.w, fx2))));
       fcorr = fmaf(v.x, v.x - ql.x, fmaf(v.y, v.y - ql.y,
@@ -117,6 +127,19 @@ __global__ void __launch_bounds__(256) quantize_bf16_stats_kernel(
         fx2 = fcorr = 0.f;
         run = 0;
       }
+    };
+    while (i < m) {
+      int64_t i2 = i, j2 = j4;
+      advance(i2, j2);
+      const float4 v = __ldcs(reinterpret_cast<const float4*>(X + i * ldx) + j4);
+      const bool two = i2 < m;
+      const float4 w = two ? __ldcs(reinterpret_cast<const float4*>(X + i2 * ldx) + j2)
+                           : make_float4(0.f, 0.f, 0.f, 0.f);
+      consume(v, i, j4);
+      if (two) consume(w, i2, j2);
+      i = i2;
+      j4 = j2;
+      advance(i, j4);
     }
   } else {
     const int64_t total = m * ldq;

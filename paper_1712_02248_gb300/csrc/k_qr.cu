@@ -4,30 +4,39 @@
 //
 // Precision. Sweep 1 sees cond(G) = cond(Y)^2, so its Gram matrix is accumulated in float-float
 // arithmetic (error-free products by FMA and Knuth's TwoSum; about 48 significant bits, relative
-// error near 1e-12 over a 128-row slab) and summed across slabs in FP64; its Cholesky factor and
-// R^{-1} are formed in float-float too (an l x l problem, ~44 bits) and R^{-1} is applied in
-// float-float, since its entries reach cond(Y) and their products cancel. The FP64 pipe of this
-// GPU runs at 1/58 of the FP32 rate (a warp-wide FP64 instruction holds its scheduler's FP64
-// pipe for ~67 cycles), so everything runs on the FP32 pipes. Sweep 2 starts from a nearly
-// orthonormal matrix: its Gram and factor are float-float as well, its application FP32. The
-// result is the Q of the QR factorisation whose R has a positive diagonal.
+// error near 1e-12 over a slab) and summed across slabs in float-float; R^{-1} is formed in
+// float-float too (an l x l problem, ~44 bits) and applied in float-float, since its entries
+// reach cond(Y) and their products cancel. The FP64 pipe of this GPU runs at 1/58 of the FP32
+// rate (a warp-wide FP64 instruction holds its scheduler's FP64 pipe for ~67 cycles), so
+// everything runs on the FP32 pipes. Sweep 2 starts from a nearly orthonormal matrix: its Gram
+// and factor are float-float as well, its application FP32. The result is the Q of the QR
+// factorisation whose R has a positive diagonal.
 //
-// Up to two independent matrices (the two chains of the sketch) go through each kernel in one
-// launch: blockIdx.y (blockIdx.x for the Cholesky) selects the matrix.
+// R^{-1} without a triangular solve: symmetric Gaussian elimination of G carried along on an
+// identity block, [G | I] -> [D L^T | L^{-1}] with G = L D L^T (L unit lower triangular), one
+// barrier a pivot and every trailing entry updated in parallel; then R = D^{1/2} L^T and
+// R^{-1} = L^{-T} D^{-1/2}, i.e. R^{-1}[k][c] = L^{-1}[c][k] / sqrt(D_c).
+//
+// The Gram and apply kernels run two blocks an SM, each on an equal contiguous range of rows,
+// taken in chunks of up to 64 rows (one contiguous run of floats) staged in shared memory with
+// every global load in flight before the first store. Up to two independent matrices (the two
+// chains of the sketch) go through each kernel in one launch: the blocks of matrix 0 come first,
+// then those of matrix 1, split in proportion to their rows (blockIdx.x for the Cholesky).
 #include "common.cuh"
 
 namespace nmfrp {
 namespace {
 
-constexpr int kGramRows = 128;   // rows per Gram block
-constexpr int kGramThreads = 256;
+constexpr int kSlab = 64;          // rows a Gram / apply chunk
+constexpr int kQrThreads = 256;
 constexpr int kMaxMats = 2;
 
 struct QrBatch {
   const float* Y[kMaxMats];     // inputs of this sweep
   float* Q[kMaxMats];           // outputs of this sweep
   int64_t rows[kMaxMats];
-  int64_t part_off[kMaxMats];   // first Gram-partial slot of each matrix
+  int64_t part_off[kMaxMats];   // first block (and Gram-partial slot) of each matrix
+  int nblk[kMaxMats];           // blocks of each matrix
   int nmat;
 };
 
@@ -40,69 +49,6 @@ __device__ __forceinline__ void ff_fma(float a, float b, float& hi, float& lo) {
   const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, v)), __fsub_rn(p, v));
   hi = s;
   lo = __fadd_rn(lo, __fadd_rn(err, e));
-}
-
-// Partial Gram of a 128-row slab in float-float: Gp[slot][p][q] (FP64) for p <= q.
-template <int LP>
-__global__ void __launch_bounds__(kGramThreads) gram_partial_kernel(QrBatch b, int ell,
-                                                                    double* __restrict__ Gp) {
-  extern __shared__ __align__(16) float Ysm[];   // [kGramRows][LP]
-  const int mat = blockIdx.y;
-  if (mat >= b.nmat) return;
-  const int64_t rows = b.rows[mat];
-  const int64_t r0 = static_cast<int64_t>(blockIdx.x) * kGramRows;
-  if (r0 >= rows) return;
-  const float* Y = b.Y[mat];
-  const int t = threadIdx.x;
-  for (int e = t; e < kGramRows * LP; e += kGramThreads) {
-    const int i = e / LP, k = e - i * LP;
-    const int64_t gr = r0 + i;
-    Ysm[e] = (gr < rows && k < ell) ? Y[gr * ell + k] : 0.f;
-  }
-  __syncthreads();
-  constexpr int T2 = LP / 2;
-  double* out = Gp + (b.part_off[mat] + blockIdx.x) * LP * LP;
-  // upper-triangle tiles only: tile u -> (P, Qi) with P <= Qi, row P holding T2 - P tiles
-  for (int tile = t; tile < T2 * (T2 + 1) / 2; tile += kGramThreads) {
-    int P = 0, u = tile;
-    while (u >= T2 - P) {
-      u -= T2 - P;
-      ++P;
-    }
-    const int Qi = P + u;
-    float h00 = 0, h01 = 0, h10 = 0, h11 = 0, l00 = 0, l01 = 0, l10 = 0, l11 = 0;
-#pragma unroll 4
-    for (int i = 0; i < kGramRows; ++i) {
-      const float2 a = *reinterpret_cast<const float2*>(&Ysm[i * LP + 2 * P]);
-      const float2 c = *reinterpret_cast<const float2*>(&Ysm[i * LP + 2 * Qi]);
-      ff_fma(a.x, c.x, h00, l00);
-      ff_fma(a.x, c.y, h01, l01);
-      ff_fma(a.y, c.x, h10, l10);
-      ff_fma(a.y, c.y, h11, l11);
-    }
-    out[(2 * P) * LP + 2 * Qi] = static_cast<double>(h00) + static_cast<double>(l00);
-    out[(2 * P) * LP + 2 * Qi + 1] = static_cast<double>(h01) + static_cast<double>(l01);
-    out[(2 * P + 1) * LP + 2 * Qi] = static_cast<double>(h10) + static_cast<double>(l10);
-    out[(2 * P + 1) * LP + 2 * Qi + 1] = static_cast<double>(h11) + static_cast<double>(l11);
-  }
-}
-
-// G[mat][e] = sum over the matrix's slabs of Gp[slot][e]: one warp per entry, lanes stride the
-// slabs, then a fixed shuffle tree (deterministic).
-__global__ void sum_parts_kernel(const double* __restrict__ Gp, QrBatch b, int entries,
-                                 double* __restrict__ G) {
-  const int mat = blockIdx.y;
-  if (mat >= b.nmat) return;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (warp >= entries) return;
-  const int64_t nparts = cdiv(b.rows[mat], kGramRows);
-  const double* base = Gp + b.part_off[mat] * entries;
-  double s = 0.0;
-  for (int64_t k = lane; k < nparts; k += 32) s += base[k * entries + warp];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) G[mat * entries + warp] = s;
 }
 
 // ---- float-float arithmetic (a value is hi + lo, |lo| <= ulp(hi) / 2; about 44 significant
@@ -138,9 +84,21 @@ __device__ __forceinline__ FF ff_mul(FF x, FF y) {
   e = __fmaf_rn(x.lo, y.hi, e);
   return ff_quick(p, e);
 }
-// 1 / x: FP32 estimate, one Newton step in float-float (r + r (1 - x r))
+// x - a b with one renormalisation (the low parts of x and of the product combined by a plain
+// add: error about 2^-44 (|x| + |a b|), the bound a backward-stable elimination step needs)
+__device__ __forceinline__ FF ff_fms(FF x, FF a, FF b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  FF s = ff_two_sum(x.hi, -p);
+  s.lo = __fadd_rn(s.lo, __fsub_rn(x.lo, e));
+  return ff_quick(s.hi, s.lo);
+}
+// 1 / x: FP32 estimate (the fast approximate reciprocal: one Newton step squares its ~1e-7
+// relative error), one Newton step in float-float (r + r (1 - x r))
 __device__ __forceinline__ FF ff_recip(FF x) {
-  const float r = __frcp_rn(x.hi);
+  const float r = __fdividef(1.f, x.hi);
   const FF e = ff_add({1.f, 0.f}, ff_neg(ff_mul(x, {r, 0.f})));
   return ff_add({r, 0.f}, ff_mul({r, 0.f}, e));
 }
@@ -151,161 +109,363 @@ __device__ __forceinline__ FF ff_sqrt(FF x) {
   return ff_quick(q, __fdiv_rn(d.hi, __fmul_rn(2.f, q)));
 }
 
-// One block per matrix: Cholesky G = R^T R in float-float (in place on the upper triangle; G
-// arrives in FP64), then T = R^{-1} by back substitution, one column per thread (T[k][c] for
-// k < c kept transposed in the lower triangle), four partial sums a column for latency. Writes T
-// as T_hi + T_lo (two FP32 arrays, ell x ell row-major).
+// b.x[mat] without a local-memory copy of the by-value struct (mat is 0 or 1).
+template <class T>
+__device__ __forceinline__ T pick(const T (&a)[kMaxMats], int mat) {
+  return mat ? a[1] : a[0];
+}
+
+// Block -> (matrix, block within it, its rows [r0, r1)); equal ranges, never empty.
+__device__ __forceinline__ void range_of(const QrBatch& b, int& mat, int& blk, int64_t& r0,
+                                         int64_t& r1) {
+  int bb = blockIdx.x;
+  mat = 0;
+  if (b.nmat > 1 && bb >= b.nblk[0]) {
+    bb -= b.nblk[0];
+    mat = 1;
+  }
+  const int64_t rows = pick(b.rows, mat), nb = pick(b.nblk, mat);
+  blk = bb;
+  r0 = rows * bb / nb;
+  r1 = rows * (bb + 1) / nb;
+}
+
+// sm[i * (LP + 1) + k] = Y[r0 + i][k] for rows r0 + i < r1 (at most 64) and k < ell, zero
+// elsewhere (columns ell .. LP - 1, rows past r1). The rows are the contiguous run Y + r0 * ell,
+// read as float4 when it is 16-byte aligned, all loads of a thread issued before its stores.
+// The odd row stride spreads a column read by 32 consecutive rows over all banks.
 template <int LP>
-__global__ void __launch_bounds__(256) chol_inv_ff_kernel(const double* __restrict__ Gin,
+__device__ __forceinline__ void stage_slab(const float* __restrict__ Y, int64_t r1, int ell,
+                                           int64_t r0, float* __restrict__ sm) {
+  constexpr int S = LP + 1;
+  constexpr int kV = (kSlab * LP / 4 + kQrThreads - 1) / kQrThreads;
+  const int t = threadIdx.x;
+  const int nrows = static_cast<int>(r1 - r0 < kSlab ? r1 - r0 : kSlab);
+  const int count = nrows * ell;
+  const float* src = Y + r0 * ell;
+  for (int e = t; e < kSlab * S; e += kQrThreads) {   // padding (disjoint from the data)
+    const int i = e / S, k = e - i * S;
+    if (i >= nrows || k >= ell) sm[e] = 0.f;
+  }
+  int nv = 0;
+  if ((reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+    nv = count >> 2;
+    float4 buf[kV];
+#pragma unroll
+    for (int u = 0; u < kV; ++u) {
+      const int v = t + u * kQrThreads;
+      if (v < nv) buf[u] = reinterpret_cast<const float4*>(src)[v];
+    }
+#pragma unroll
+    for (int u = 0; u < kV; ++u) {
+      const int v = t + u * kQrThreads;
+      if (v < nv) {
+        int i = (4 * v) / ell, k = 4 * v - i * ell;
+        const float x[4] = {buf[u].x, buf[u].y, buf[u].z, buf[u].w};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          sm[i * S + k] = x[c];
+          if (++k == ell) {
+            k = 0;
+            ++i;
+          }
+        }
+      }
+    }
+  }
+  for (int f = 4 * nv + t; f < count; f += kQrThreads) {
+    const int i = f / ell;
+    sm[i * S + f - i * ell] = src[f];
+  }
+}
+
+// Partial Gram of a block's rows in float-float: Gp[slot][p][q] = (hi, lo) for p <= q < ell
+// (2 x 2 tiles of the upper triangle of the ell x ell block, each thread's tiles accumulated
+// in registers over the block's chunks; other entries are not written).
+template <int LP>
+__global__ void __launch_bounds__(kQrThreads) gram_partial_kernel(QrBatch b, int ell,
+                                                                  float2* __restrict__ Gp) {
+  constexpr int S = LP + 1;
+  constexpr int kT = ((LP / 2) * (LP / 2 + 1) / 2 + kQrThreads - 1) / kQrThreads;
+  extern __shared__ float Ysm[];   // [kSlab][S]
+  int mat, blk;
+  int64_t r0, r1;
+  range_of(b, mat, blk, r0, r1);
+  const float* Y = pick(b.Y, mat);
+  const int T2 = (ell + 1) >> 1, ntiles = T2 * (T2 + 1) / 2;
+  int a0[kT], c0[kT];
+#pragma unroll
+  for (int v = 0; v < kT; ++v) {   // tile u -> (P, Qi), P <= Qi, row P holding T2 - P tiles
+    int P = 0, u = threadIdx.x + v * kQrThreads;
+    a0[v] = -1;
+    if (u < ntiles) {
+      while (u >= T2 - P) {
+        u -= T2 - P;
+        ++P;
+      }
+      a0[v] = 2 * P;
+      c0[v] = 2 * (P + u);
+    }
+  }
+  float h[kT][4], l[kT][4];
+#pragma unroll
+  for (int v = 0; v < kT; ++v)
+#pragma unroll
+    for (int x = 0; x < 4; ++x) h[v][x] = l[v][x] = 0.f;
+  // equal chunks of at most 64 rows
+  const int64_t nch = (r1 - r0 + kSlab - 1) / kSlab;
+  for (int64_t ch = 0; ch < nch; ++ch) {
+    const int64_t c = r0 + (r1 - r0) * ch / nch, c1 = r0 + (r1 - r0) * (ch + 1) / nch;
+    if (ch > 0) __syncthreads();   // the previous chunk is consumed
+    stage_slab<LP>(Y, c1, ell, c, Ysm);
+    __syncthreads();
+    const int nrows = static_cast<int>(c1 - c);
+#pragma unroll
+    for (int v = 0; v < kT; ++v) {
+      if (a0[v] < 0) continue;
+      const float* ya = Ysm + a0[v];
+      const float* yc = Ysm + c0[v];
+#pragma unroll 4
+      for (int i = 0; i < nrows; ++i) {
+        const float ax = ya[i * S], ay = ya[i * S + 1];
+        const float cx = yc[i * S], cy = yc[i * S + 1];
+        ff_fma(ax, cx, h[v][0], l[v][0]);
+        ff_fma(ax, cy, h[v][1], l[v][1]);
+        ff_fma(ay, cx, h[v][2], l[v][2]);
+        ff_fma(ay, cy, h[v][3], l[v][3]);
+      }
+    }
+  }
+  float2* out = Gp + (pick(b.part_off, mat) + blk) * LP * LP;
+#pragma unroll
+  for (int v = 0; v < kT; ++v) {
+    if (a0[v] < 0) continue;
+    const int p = a0[v], q = c0[v];
+#pragma unroll
+    for (int x = 0; x < 4; ++x) {
+      const FF f = ff_quick(h[v][x], l[v][x]);
+      out[(p + (x >> 1)) * LP + q + (x & 1)] = make_float2(f.hi, f.lo);
+    }
+  }
+}
+
+// G[mat][p][q] = sum over the matrix's blocks of Gp[slot][p][q] in float-float for p <= q < ell.
+// A block takes 8 consecutive entries of row p (coalesced reads) and 32 groups over the slots,
+// 8 loads in flight a thread, then a fixed-order tree (deterministic). Blocks holding no entry
+// of the upper triangle return.
+template <int LP>
+__global__ void __launch_bounds__(256) sum_parts_kernel(const float2* __restrict__ Gp, QrBatch b,
+                                                        int ell, float2* __restrict__ G) {
+  constexpr int E = LP * LP;
+  __shared__ FF red[32][8];
+  const int mat = blockIdx.z;
+  if (mat >= b.nmat) return;
+  const int p = blockIdx.y, q0 = blockIdx.x * 8;
+  if (p >= ell || q0 >= ell || q0 + 7 < p) return;
+  const int x = threadIdx.x & 7, g = threadIdx.x >> 3;
+  const int nparts = pick(b.nblk, mat);
+  const float2* base = Gp + pick(b.part_off, mat) * E + p * LP + q0 + x;
+  FF s = {0.f, 0.f};
+  for (int k0 = g; k0 < nparts; k0 += 32 * 8) {
+    float2 v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int k = k0 + 32 * u;
+      v[u] = k < nparts ? base[static_cast<int64_t>(k) * E] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) s = ff_add(s, {v[u].x, v[u].y});
+  }
+  red[g][x] = s;
+  __syncthreads();
+  for (int w = 16; w > 0; w >>= 1) {
+    if (g < w) red[g][x] = ff_add(red[g][x], red[g + w][x]);
+    __syncthreads();
+  }
+  if (g == 0) G[mat * E + p * LP + q0 + x] = make_float2(red[0][x].hi, red[0][x].lo);
+}
+
+// One block per matrix: T = R^{-1} (G = R^T R) by the elimination of [G | I] described at the
+// top, in float-float. M holds the upper triangle of the trailing matrix (k >= i) and the strict
+// lower triangle of L^{-1} (k < i; its unit diagonal is implicit). Step j reads row j and
+// updates the rows below it: M[i][k] -= (M[j][i] / M[j][j]) * y_k with y_k = M[j][k] (k != j)
+// and y_j = 1. The thread that updates the next pivot M[j + 1][j + 1] also forms its reciprocal
+// (double-buffered in shared memory), so each step has one barrier. Writes T as T_hi + T_lo
+// (two FP32 arrays, ell x ell row-major).
+template <int LP>
+__global__ void __launch_bounds__(512) chol_inv_ff_kernel(const float2* __restrict__ Gin,
                                                           QrBatch b, int ell,
                                                           float* __restrict__ Thi,
                                                           float* __restrict__ Tlo, int* status) {
   constexpr int S = LP + 1;
+  constexpr int kNT = 512, kPer = (LP * LP + kNT - 1) / kNT;
   extern __shared__ __align__(16) float chol_ff_sm[];
-  float* Ah = chol_ff_sm;         // [LP][S]
-  float* Al = Ah + LP * S;        // [LP][S]
-  float* dh = Al + LP * S;        // [LP]  1 / R[j][j]
-  float* dl = dh + LP;
-  __shared__ int bad;
+  float* Mh = chol_ff_sm;         // [LP][S]
+  float* Ml = Mh + LP * S;        // [LP][S]
+  float* rh = Ml + LP * S;        // [LP]  1 / sqrt(D_c)
+  float* rl = rh + LP;
+  __shared__ FF pinv[2];          // 1 / M[j][j] of the current and the next pivot
   const int mat = blockIdx.x;
   if (mat >= b.nmat) return;
-  const double* G = Gin + static_cast<int64_t>(mat) * LP * LP;
-  const int t = threadIdx.x, nt = blockDim.x;
-  if (t == 0) bad = 0;
-  for (int p = t >> 5; p < LP; p += nt >> 5)
-    for (int q = t & 31; q < LP; q += 32) {
-      const double g = (p <= q && q < ell) ? G[p * LP + q] : 0.0;
-      const float hi = static_cast<float>(g);
-      Ah[p * S + q] = hi;
-      Al[p * S + q] = static_cast<float>(g - static_cast<double>(hi));
+  const float2* G = Gin + static_cast<int64_t>(mat) * LP * LP;
+  const int t = threadIdx.x;
+  for (int e = t; e < LP * LP; e += kNT) {
+    const int i = e / LP, k = e - i * LP;
+    const float2 g = (i <= k && k < ell) ? G[e] : make_float2(0.f, 0.f);
+    Mh[i * S + k] = g.x;
+    Ml[i * S + k] = g.y;
+  }
+  // this thread's entries (i, k) of the ell x ell block, fixed for all pivots
+  int ei[kPer], ek[kPer];
+#pragma unroll
+  for (int u = 0; u < kPer; ++u) {
+    const int e = t + u * kNT;
+    ei[u] = e / ell;
+    ek[u] = e - ei[u] * ell;
+    if (e >= ell * ell) ei[u] = -1;
+  }
+  // a non-positive pivot: the sketch is numerically rank deficient
+  bool bad = false;
+  auto pivot_inv = [&](FF d) {
+    if (!(d.hi > 0.f)) {
+      bad = true;
+      d = {1e-30f, 0.f};
     }
+    return ff_recip(d);
+  };
+  if (t == 0) pinv[0] = pivot_inv({static_cast<float>(G[0].x), G[0].y});
   __syncthreads();
   for (int j = 0; j < ell; ++j) {
-    if (t == 0) {
-      FF d = {Ah[j * S + j], Al[j * S + j]};
-      // a non-positive pivot: the sketch is numerically rank deficient
-      if (!(d.hi > 0.f)) {
-        bad = 1;
-        d = {1e-30f, 0.f};
-      }
-      const FF r = ff_sqrt(d);
-      const FF ri = ff_recip(r);
-      Ah[j * S + j] = r.hi;
-      Al[j * S + j] = r.lo;
-      dh[j] = ri.hi;
-      dl[j] = ri.lo;
-    }
-    __syncthreads();
-    const FF ri = {dh[j], dl[j]};
-    for (int q = j + 1 + t; q < ell; q += nt) {
-      const FF v = ff_mul({Ah[j * S + q], Al[j * S + q]}, ri);
-      Ah[j * S + q] = v.hi;
-      Al[j * S + q] = v.lo;
-    }
-    __syncthreads();
-    for (int p = j + 1 + (t >> 5); p < ell; p += nt >> 5) {
-      const FF ajp = {Ah[j * S + p], Al[j * S + p]};
-      for (int q = p + (t & 31); q < ell; q += 32) {
-        const FF v = ff_add({Ah[p * S + q], Al[p * S + q]},
-                            ff_neg(ff_mul(ajp, {Ah[j * S + q], Al[j * S + q]})));
-        Ah[p * S + q] = v.hi;
-        Al[p * S + q] = v.lo;
-      }
-    }
-    __syncthreads();
-  }
-  // T[c][c] = 1 / R[c][c];  T[i][c] = -(sum_{k=i+1..c} R[i][k] T[k][c]) / R[i][i]
-  for (int c = t; c < ell; c += nt) {
-    const FF tcc = {dh[c], dl[c]};
-    for (int i = c - 1; i >= 0; --i) {
-      FF acc[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-      acc[0] = ff_mul({Ah[i * S + c], Al[i * S + c]}, tcc);
-      int k = i + 1;
-      for (; k + 3 < c; k += 4) {
+    const FF inv = pinv[j & 1];
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
-          acc[u] = ff_add(acc[u], ff_mul({Ah[i * S + k + u], Al[i * S + k + u]},
-                                         {Ah[c * S + k + u], Al[c * S + k + u]}));
+    for (int u = 0; u < kPer; ++u) {
+      const int i = ei[u], k = ek[u];
+      if (i > j && (k <= j || k >= i)) {
+        const FF l = ff_mul({Mh[j * S + i], Ml[j * S + i]}, inv);
+        const FF y = k == j ? FF{1.f, 0.f} : FF{Mh[j * S + k], Ml[j * S + k]};
+        const FF v = ff_fms({Mh[i * S + k], Ml[i * S + k]}, l, y);
+        Mh[i * S + k] = v.hi;
+        Ml[i * S + k] = v.lo;
+        if (i == j + 1 && k == i) pinv[(j + 1) & 1] = pivot_inv(v);
       }
-      for (; k < c; ++k)
-        acc[0] = ff_add(acc[0], ff_mul({Ah[i * S + k], Al[i * S + k]}, {Ah[c * S + k], Al[c * S + k]}));
-      const FF sum = ff_add(ff_add(acc[0], acc[1]), ff_add(acc[2], acc[3]));
-      const FF v = ff_neg(ff_mul(sum, {dh[i], dl[i]}));
-      Ah[c * S + i] = v.hi;
-      Al[c * S + i] = v.lo;
     }
+    __syncthreads();
   }
-  __syncthreads();
+  for (int c = t; c < ell; c += kNT) {
+    FF d = {Mh[c * S + c], Ml[c * S + c]};
+    if (!(d.hi > 0.f)) d = {1e-30f, 0.f};
+    const FF r = ff_recip(ff_sqrt(d));
+    rh[c] = r.hi;
+    rl[c] = r.lo;
+  }
+  bad = __syncthreads_or(bad);
   float* th = Thi + static_cast<int64_t>(mat) * ell * ell;
   float* tl = Tlo + static_cast<int64_t>(mat) * ell * ell;
-  for (int p = t >> 5; p < ell; p += nt >> 5)
-    for (int q = t & 31; q < ell; q += 32) {
-      float hi = 0.f, lo = 0.f;
-      if (p == q) {
-        hi = dh[p];
-        lo = dl[p];
-      } else if (p < q) {
-        hi = Ah[q * S + p];
-        lo = Al[q * S + p];
-      }
-      th[p * ell + q] = hi;
-      tl[p * ell + q] = lo;
-    }
+  for (int e = t; e < LP * LP; e += kNT) {
+    const int p = e / LP, q = e - p * LP;
+    if (p >= ell || q >= ell) continue;
+    FF v = {0.f, 0.f};
+    if (p == q) v = {rh[q], rl[q]};
+    else if (p < q) v = ff_mul({Mh[q * S + p], Ml[q * S + p]}, {rh[q], rl[q]});
+    th[p * ell + q] = v.hi;
+    tl[p * ell + q] = v.lo;
+  }
   if (t == 0 && bad) latch(status, kStQrBreakdown);
 }
 
-// Q = Y (T_hi + T_lo), T upper triangular. FF: float-float accumulation of the T_hi part.
-// One thread per (row, block of 8 columns).
-template <int LP, bool FF>
-__global__ void __launch_bounds__(256) apply_tri_kernel(QrBatch b, int ell,
-                                                        const float* __restrict__ Thi,
-                                                        const float* __restrict__ Tlo) {
+// Q = Y (T_hi + T_lo), T upper triangular, over a block's rows in 64-row chunks. FFA:
+// float-float accumulation of the T_hi part. A task is (8-column block cb, row i) with cb
+// uniform across a warp (so is the length of its inner loop) and the longest blocks first.
+template <int LP, bool FFA>
+__global__ void __launch_bounds__(kQrThreads) apply_tri_kernel(QrBatch b, int ell,
+                                                               const float* __restrict__ Thi,
+                                                               const float* __restrict__ Tlo) {
+  constexpr int S = LP + 1;
   extern __shared__ __align__(16) float tsm[];
-  float* Th = tsm;             // [LP][LP]
-  float* Tl = tsm + LP * LP;   // [LP][LP]
-  const int mat = blockIdx.y;
-  if (mat >= b.nmat) return;
+  float* Th = tsm;                             // [LP][LP]
+  float* Tl = Th + LP * LP;                    // [LP][LP] (FFA only)
+  float* Ysm = Tl + (FFA ? LP * LP : 0);       // [kSlab][S]
+  int mat, blk;
+  int64_t r0, r1;
+  range_of(b, mat, blk, r0, r1);
   const float* th = Thi + static_cast<int64_t>(mat) * ell * ell;
   const float* tl = Tlo + static_cast<int64_t>(mat) * ell * ell;
-  for (int e = threadIdx.x; e < LP * LP; e += blockDim.x) {
+#pragma unroll 8
+  for (int e = threadIdx.x; e < LP * LP; e += kQrThreads) {
     const int p = e / LP, q = e - p * LP;
     const bool in = p < ell && q < ell;
     Th[e] = in ? th[p * ell + q] : 0.f;
-    Tl[e] = (FF && in) ? tl[p * ell + q] : 0.f;
+    if (FFA) Tl[e] = in ? tl[p * ell + q] : 0.f;
   }
-  __syncthreads();
-  const float* Y = b.Y[mat];
-  float* Q = b.Q[mat];
-  const int64_t rows = b.rows[mat];
-  constexpr int CB = 8, NCB = LP / CB;
-  const int64_t total = rows * NCB;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e / NCB;
-    const int cb = static_cast<int>(e - i * NCB);
-    float hi[CB], lo[CB];
+  const float* Y = pick(b.Y, mat);
+  float* Q = pick(b.Q, mat);
+  const int ncb = (ell + 7) >> 3;
+  // equal chunks of at most 64 rows
+  const int64_t nch = (r1 - r0 + kSlab - 1) / kSlab;
+  for (int64_t ch = 0; ch < nch; ++ch) {
+    const int64_t c = r0 + (r1 - r0) * ch / nch, c1 = r0 + (r1 - r0) * (ch + 1) / nch;
+    if (ch > 0) __syncthreads();   // the previous chunk is consumed
+    stage_slab<LP>(Y, c1, ell, c, Ysm);
+    __syncthreads();
+    const int nrows = static_cast<int>(c1 - c);
+    for (int e = threadIdx.x; e < ncb * nrows; e += kQrThreads) {
+      const int cb = ncb - 1 - e / nrows, i = e - (ncb - 1 - cb) * nrows;
+      float hi[8], lo[8];
 #pragma unroll
-    for (int q = 0; q < CB; ++q) hi[q] = lo[q] = 0.f;
-    const float* yr = Y + i * ell;
-    const int kmax = min(ell, (cb + 1) * CB);
-    for (int k = 0; k < kmax; ++k) {
-      const float y = yr[k];
+      for (int q = 0; q < 8; ++q) hi[q] = lo[q] = 0.f;
+      const int kmax = min(ell, (cb + 1) * 8);
+      const float* yr = Ysm + i * S;
+      for (int k = 0; k < kmax; ++k) {
+        const float y = yr[k];
+        const float4 a0 = *reinterpret_cast<const float4*>(Th + k * LP + cb * 8);
+        const float4 a1 = *reinterpret_cast<const float4*>(Th + k * LP + cb * 8 + 4);
+        const float ta[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+        if (FFA) {
+          const float4 b0 = *reinterpret_cast<const float4*>(Tl + k * LP + cb * 8);
+          const float4 b1 = *reinterpret_cast<const float4*>(Tl + k * LP + cb * 8 + 4);
+          const float tb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
-      for (int q = 0; q < CB; ++q) {
-        if (FF) {
-          ff_fma(y, Th[k * LP + cb * CB + q], hi[q], lo[q]);
-          lo[q] = fmaf(y, Tl[k * LP + cb * CB + q], lo[q]);
+          for (int q = 0; q < 8; ++q) {
+            ff_fma(y, ta[q], hi[q], lo[q]);
+            lo[q] = fmaf(y, tb[q], lo[q]);
+          }
         } else {
-          hi[q] = fmaf(y, Th[k * LP + cb * CB + q], hi[q]);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) hi[q] = fmaf(y, ta[q], hi[q]);
         }
       }
-    }
+      float* qr = Q + (c + i) * ell + cb * 8;
 #pragma unroll
-    for (int q = 0; q < CB; ++q) {
-      const int c = cb * CB + q;
-      if (c < ell) Q[i * ell + c] = FF ? __fadd_rn(hi[q], lo[q]) : hi[q];
+      for (int q = 0; q < 8; ++q)
+        if (cb * 8 + q < ell) qr[q] = FFA ? __fadd_rn(hi[q], lo[q]) : hi[q];
     }
   }
+}
+
+int qr_sms() {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    sms = v > 0 ? v : 148;
+  }
+  return sms;
+}
+
+// Blocks of each matrix: two an SM in all (never more), split in proportion to the rows, none
+// without rows.
+void split_blocks(const int64_t* rows, int nmat, int* nblk) {
+  const int64_t total = 2 * static_cast<int64_t>(qr_sms());
+  int64_t want[kMaxMats] = {total, 0};
+  if (nmat == 2) {
+    int64_t n0 = (total * rows[0] + (rows[0] + rows[1]) / 2) / (rows[0] + rows[1]);
+    n0 = n0 < 1 ? 1 : n0 > total - 1 ? total - 1 : n0;
+    want[0] = n0;
+    want[1] = total - n0;
+  }
+  for (int i = 0; i < nmat; ++i)
+    nblk[i] = static_cast<int>(want[i] < rows[i] ? want[i] : rows[i]);
 }
 
 int lp_for(int ell) {
@@ -319,9 +479,11 @@ int lp_for(int ell) {
 
 size_t ws_bytes_for(const int64_t* rows, int nmat, int ell) {
   const int LP = lp_for(ell);
-  size_t slabs = 0;
-  for (int i = 0; i < nmat; ++i) slabs += cdiv(rows[i], kGramRows);
-  size_t b = sizeof(double) * (slabs + nmat) * LP * LP;
+  int nblk[kMaxMats] = {0, 0};
+  split_blocks(rows, nmat, nblk);
+  size_t parts = 0;
+  for (int i = 0; i < nmat; ++i) parts += nblk[i];
+  size_t b = sizeof(float2) * (parts + nmat) * LP * LP;
   b += 2 * sizeof(float) * nmat * ell * ell + 256;
   for (int i = 0; i < nmat; ++i) b += sizeof(float) * rows[i] * ell + 256;
   return b + 4096;
@@ -330,16 +492,14 @@ size_t ws_bytes_for(const int64_t* rows, int nmat, int ell) {
 template <int LP>
 cudaError_t run(const Launcher& L, QrBatch b, int ell, char* ws, int* status) {
   const int nmat = b.nmat;
-  int64_t slabs = 0, max_slabs = 0, max_rows = 0;
+  split_blocks(b.rows, nmat, b.nblk);
+  int64_t parts = 0;
   for (int i = 0; i < nmat; ++i) {
-    b.part_off[i] = slabs;
-    const int64_t s = cdiv(b.rows[i], kGramRows);
-    slabs += s;
-    max_slabs = s > max_slabs ? s : max_slabs;
-    max_rows = b.rows[i] > max_rows ? b.rows[i] : max_rows;
+    b.part_off[i] = parts;
+    parts += b.nblk[i];
   }
-  double* Gp = reinterpret_cast<double*>(ws);
-  double* G = Gp + slabs * LP * LP;
+  float2* Gp = reinterpret_cast<float2*>(ws);
+  float2* G = Gp + parts * LP * LP;
   float* Thi = reinterpret_cast<float*>(G + nmat * LP * LP);
   float* Tlo = Thi + nmat * ell * ell;
   char* p = reinterpret_cast<char*>(Tlo + nmat * ell * ell);
@@ -349,28 +509,25 @@ cudaError_t run(const Launcher& L, QrBatch b, int ell, char* ws, int* status) {
     Q1[i] = reinterpret_cast<float*>(p);
     p += sizeof(float) * b.rows[i] * ell;
   }
-  const size_t gram_smem = sizeof(float) * kGramRows * LP;
-  const size_t apply_smem = sizeof(float) * 2 * LP * LP;
-  const size_t chol_smemff = sizeof(float) * (2 * LP * (LP + 1) + 2 * LP);
+  const size_t slab_smem = sizeof(float) * kSlab * (LP + 1);
+  const size_t apply_ff_smem = sizeof(float) * 2 * LP * LP + slab_smem;
+  const size_t apply_smem = sizeof(float) * LP * LP + slab_smem;
+  const size_t chol_smem = sizeof(float) * (2 * LP * (LP + 1) + 2 * LP);
   cudaError_t err;
   if ((err = cudaFuncSetAttribute(chol_inv_ff_kernel<LP>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  static_cast<int>(chol_smemff))) != cudaSuccess ||
-
+                                  static_cast<int>(chol_smem))) != cudaSuccess ||
       (err = cudaFuncSetAttribute(gram_partial_kernel<LP>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  static_cast<int>(gram_smem))) != cudaSuccess ||
+                                  static_cast<int>(slab_smem))) != cudaSuccess ||
       (err = cudaFuncSetAttribute(apply_tri_kernel<LP, true>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  static_cast<int>(apply_smem))) != cudaSuccess ||
+                                  static_cast<int>(apply_ff_smem))) != cudaSuccess ||
       (err = cudaFuncSetAttribute(apply_tri_kernel<LP, false>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   static_cast<int>(apply_smem))) != cudaSuccess)
     return err;
-  const int64_t apply_work = max_rows * (LP / 8);
-  const unsigned apply_grid =
-      static_cast<unsigned>(cdiv(apply_work, 256) < 2048 ? cdiv(apply_work, 256) : 2048);
-  const unsigned sum_grid = static_cast<unsigned>(cdiv(static_cast<int64_t>(LP) * LP * 32, 256));
+  const unsigned grid = static_cast<unsigned>(parts);
   for (int sweep = 0; sweep < 2; ++sweep) {
     // sweep 0 reads Y and writes the scratch Q1; sweep 1 reads Q1 and writes Q (Q may alias Y)
     QrBatch bb = b;
@@ -378,18 +535,13 @@ cudaError_t run(const Launcher& L, QrBatch b, int ell, char* ws, int* status) {
       bb.Y[i] = sweep == 0 ? b.Y[i] : Q1[i];
       bb.Q[i] = sweep == 0 ? Q1[i] : b.Q[i];
     }
-    gram_partial_kernel<LP><<<dim3(static_cast<unsigned>(max_slabs), nmat), kGramThreads,
-                              gram_smem, L.stream>>>(bb, ell, Gp);
-    sum_parts_kernel<<<dim3(sum_grid, nmat), 256, 0, L.stream>>>(Gp, bb, LP * LP, G);
-    if (sweep == 0) {
-      chol_inv_ff_kernel<LP><<<nmat, 256, chol_smemff, L.stream>>>(G, bb, ell, Thi, Tlo, status);
-      apply_tri_kernel<LP, true><<<dim3(apply_grid, nmat), 256, apply_smem, L.stream>>>(
-          bb, ell, Thi, Tlo);
-    } else {
-      chol_inv_ff_kernel<LP><<<nmat, 256, chol_smemff, L.stream>>>(G, bb, ell, Thi, Tlo, status);
-      apply_tri_kernel<LP, false><<<dim3(apply_grid, nmat), 256, apply_smem, L.stream>>>(
-          bb, ell, Thi, Tlo);
-    }
+    gram_partial_kernel<LP><<<grid, kQrThreads, slab_smem, L.stream>>>(bb, ell, Gp);
+    sum_parts_kernel<LP><<<dim3(LP / 8, ell, nmat), 256, 0, L.stream>>>(Gp, bb, ell, G);
+    chol_inv_ff_kernel<LP><<<nmat, 512, chol_smem, L.stream>>>(G, bb, ell, Thi, Tlo, status);
+    if (sweep == 0)
+      apply_tri_kernel<LP, true><<<grid, kQrThreads, apply_ff_smem, L.stream>>>(bb, ell, Thi, Tlo);
+    else
+      apply_tri_kernel<LP, false><<<grid, kQrThreads, apply_smem, L.stream>>>(bb, ell, Thi, Tlo);
     L.count(4);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
