@@ -16,6 +16,28 @@ enum : int {
   kStTimeout = 6,
 };
 
+// Running sum held as an unevaluated pair hi + lo of FP32 values, each addition by Knuth's
+// TwoSum (about 48 significant bits). Long sums stay off the FP64 pipe, which on this GPU is so
+// narrow that one FP64 add per 64 streamed elements halved the bandwidth of a streaming kernel.
+struct FSum {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float v) {
+    const float s = __fadd_rn(hi, v);
+    const float b = __fsub_rn(s, hi);
+    lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(hi, __fsub_rn(s, b)), __fsub_rn(v, b)));
+    hi = s;
+  }
+  // += a * b with the product's rounding error kept (FMA)
+  __device__ __forceinline__ void add_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    lo = __fadd_rn(lo, __fmaf_rn(a, b, -p));
+    add(p);
+  }
+  __device__ __forceinline__ double value() const {
+    return static_cast<double>(hi) + static_cast<double>(lo);
+  }
+};
+
 // Record the first failure only.
 __device__ __forceinline__ void latch(int* status, int code) {
   if (status) atomicCAS(status, 0, code);

@@ -84,14 +84,14 @@ __global__ void quantize_bf16_vec4_kernel(const float* __restrict__ X, int64_t m
 
 // BF16 copy plus the two sums the compressed error monitor needs: ||X||^2 and <X - X_q, X>
 // (the rounding of X to BF16 enters the monitor's cross term; this sum removes it). FP32 within
-// runs of 64 elements a thread, FP64 beyond (the FP64 pipe is far narrower than the FP32 one),
-// block partials summed in a fixed order.
+// runs of 64 elements a thread, float-float (FSum) beyond, FP64 only for the block partials,
+// summed in a fixed order.
 template <bool VEC>
 __global__ void __launch_bounds__(256) quantize_bf16_stats_kernel(
     const float* __restrict__ X, int64_t m, int64_t n, int64_t ldx, __nv_bfloat16* __restrict__ Xq,
     int64_t ldq, double* __restrict__ part) {
   __shared__ double red[2][8];
-  double x2 = 0.0, corr = 0.0;
+  FSum sx2, scorr;
   float fx2 = 0.f, fcorr = 0.f;
   int run = 0;
   if (VEC) {
@@ -122,8 +122,8 @@ __global__ void __launch_bounds__(256) quantize_bf16_stats_kernel(
       fcorr = fmaf(v.x, v.x - ql.x, fmaf(v.y, v.y - ql.y,
                    fmaf(v.z, v.z - qh.x, fmaf(v.w, v.w - qh.y, fcorr))));
       if (++run == 16) {
-        x2 += static_cast<double>(fx2);
-        corr += static_cast<double>(fcorr);
+        sx2.add(fx2);
+        scorr.add(fcorr);
         fx2 = fcorr = 0.f;
         run = 0;
       }
@@ -152,15 +152,16 @@ __global__ void __launch_bounds__(256) quantize_bf16_stats_kernel(
       fx2 = fmaf(x, x, fx2);
       fcorr = fmaf(x, x - __bfloat162float(q), fcorr);
       if (++run == 64) {
-        x2 += static_cast<double>(fx2);
-        corr += static_cast<double>(fcorr);
+        sx2.add(fx2);
+        scorr.add(fcorr);
         fx2 = fcorr = 0.f;
         run = 0;
       }
     }
   }
-  x2 += static_cast<double>(fx2);
-  corr += static_cast<double>(fcorr);
+  sx2.add(fx2);
+  scorr.add(fcorr);
+  double x2 = sx2.value(), corr = scorr.value();
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     x2 += __shfl_xor_sync(0xffffffffu, x2, o);

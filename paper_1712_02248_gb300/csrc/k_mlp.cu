@@ -104,19 +104,21 @@ __global__ void __launch_bounds__(kThreads) mlp_gemm_kernel(int M, int N, int K,
   }
 }
 
-// E = Y - T; G = 2 E / (rows r); per-block partial sums of E^2 (FP64) for the loss.
+// E = Y - T; G = 2 E / (rows r); per-block partial sums of E^2 for the loss (float-float with
+// exact products within a thread, FP64 across threads).
 __global__ void __launch_bounds__(256) mse_grad_kernel(const float* __restrict__ Y,
                                                        const float* __restrict__ T, int64_t total,
                                                        float scale, float* __restrict__ G,
                                                        double* __restrict__ part) {
   __shared__ double red[8];
-  double s = 0.0;
+  FSum fs;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     const float d = Y[e] - T[e];
     G[e] = scale * d;
-    s += static_cast<double>(d) * d;
+    fs.add_prod(d, d);
   }
+  double s = fs.value();
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;

@@ -5,7 +5,8 @@
 // cp.async pipeline in shared memory (two blocks per SM); the 128 rows of W (transposed) are staged once per row
 // block. Each thread rebuilds 8 x 4 outputs of W H in registers (K = r FMAs each) and adds
 // (x - wh)^2 and x^2 to per-thread sums. Per-tile sums are FP32 (32 terms), accumulated across
-// tiles in FP64; block sums and the final sum are FP64 in a fixed order (deterministic).
+// tiles in float-float (FSum: the FP64 pipe of this GPU is too narrow for a per-tile FP64 add);
+// block sums and the final sum are FP64 in a fixed order (deterministic).
 //
 // General kernel (any ldx): a block walks 128 x 128 tiles, staging W and H per tile, with its X
 // loads issued first so that their latency overlaps the W H arithmetic.
@@ -36,7 +37,7 @@ __global__ void __launch_bounds__(kThreads, 1) residual_kernel(
   __shared__ double red[2][kThreads / 32];
   const int t = threadIdx.x, ty = t >> 4, tx = t & 15;
   const int64_t tiles_c = cdiv(n, kT), tiles = cdiv(m, kT) * tiles_c;
-  double e2 = 0.0, x2 = 0.0;
+  FSum se2, sx2;
   for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const int64_t r0 = (tile / tiles_c) * kT, c0 = (tile % tiles_c) * kT;
     // X loads for this thread's 8 x 8 outputs: rows r0 + 8 ty + a, columns c0 + 4 tx + {0..3}
@@ -107,11 +108,10 @@ __global__ void __launch_bounds__(kThreads, 1) residual_kernel(
         te = fmaf(d, d, te);
         tx2 = fmaf(xv[a][b], xv[a][b], tx2);
       }
-    e2 += te;
-    x2 += tx2;
+    se2.add(te);
+    sx2.add(tx2);
   }
-  e2 = warp_sum(e2);
-  x2 = warp_sum(x2);
+  const double e2 = warp_sum(se2.value()), x2 = warp_sum(sx2.value());
   if ((t & 31) == 0) {
     red[0][t >> 5] = e2;
     red[1][t >> 5] = x2;
@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(kSThreads, 2) residual_stream_kernel(
   const int WS = kSR + 4;
   __shared__ double red[2][kSThreads / 32];
   const int t = threadIdx.x, ty = t >> 4, tx = t & 15;   // rows 8 ty + a, columns 4 tx + b
-  double e2 = 0.0, x2 = 0.0;
+  FSum se2, sx2;
   // tiles of this block: a contiguous range (W is staged again only when the range crosses
   // into the next row block)
   const int64_t first = blockIdx.x * g.tiles / gridDim.x;
@@ -247,13 +247,12 @@ __global__ void __launch_bounds__(kSThreads, 2) residual_stream_kernel(
         tx2 = fmaf(xb, xb, tx2);
       }
     }
-    e2 += te;
-    x2 += tx2;
+    se2.add(te);
+    sx2.add(tx2);
     __syncthreads();   // the stage is reused by the copies issued at the next step
   }
   cp_async_wait<0>();
-  e2 = warp_sum(e2);
-  x2 = warp_sum(x2);
+  const double e2 = warp_sum(se2.value()), x2 = warp_sum(sx2.value());
   if ((t & 31) == 0) {
     red[0][t >> 5] = e2;
     red[1][t >> 5] = x2;
@@ -359,20 +358,21 @@ cudaError_t launch_residual(const Launcher& L, const float* X, int64_t m, int64_
 
 namespace {
 
-// sum of x^2 over X: FP32 within 4 elements, FP64 across them, fixed-order block and final sums
+// sum of x^2 over X: FP32 within 4 elements, float-float across them, fixed-order FP64 block and
+// final sums
 __global__ void __launch_bounds__(256) sumsq_kernel(const float* __restrict__ X, int64_t m,
                                                     int64_t n, int64_t ldx,
                                                     double* __restrict__ part) {
   __shared__ double red[8];
   const bool vec = (ldx % 4 == 0) && (n % 4 == 0) && (reinterpret_cast<uintptr_t>(X) % 16 == 0);
-  double acc = 0.0;
+  FSum sacc;
   if (vec) {
     const int64_t n4 = n / 4, total = m * n4;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
       const int64_t i = e / n4, j = e - i * n4;
       const float4 v = __ldcs(reinterpret_cast<const float4*>(X + i * ldx) + j);
-      acc += static_cast<double>(fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, v.w * v.w))));
+      sacc.add(fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, v.w * v.w))));
     }
   } else {
     const int64_t total = m * n;
@@ -380,10 +380,10 @@ __global__ void __launch_bounds__(256) sumsq_kernel(const float* __restrict__ X,
          e += (int64_t)gridDim.x * blockDim.x) {
       const int64_t i = e / n, j = e - i * n;
       const float v = X[i * ldx + j];
-      acc += static_cast<double>(v * v);
+      sacc.add(v * v);
     }
   }
-  acc = warp_sum(acc);
+  const double acc = warp_sum(sacc.value());
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
   __syncthreads();
   if (threadIdx.x < 32) {
