@@ -262,7 +262,57 @@ __device__ __forceinline__ void update_rows(float (&v)[R][RP / NG], float (&s)[R
                                             bool reg, float alpha, float beta, float eps) {
   constexpr int C = RP / NG;
   const unsigned full = 0xffffffffu;
-  if (RULE == 0) {
+  if (RULE == 0 && NG == 2) {
+    // Two lanes a vector (lane g owns components g C .. g C + C - 1). Each step's update is
+    // formed by both lanes from their own component cj and kept by the owner only (no divergent
+    // branch on the dependency chain: the diagonal loads do not wait for it), and one XOR
+    // shuffle hands the partner's values over. Steps j >= r are skipped.
+    // t_j = S_j - sum_q v_q G[q][j]: own q from registers, the partner's by one shuffle each
+#pragma unroll 1
+    for (int half = 0; half < 2; ++half) {   // own component rows, then the partner's
+      const int src = half ? (g ^ 1) : g;
+#pragma unroll
+      for (int q = 0; q < C; ++q) {
+        float gr[C];
+        ld_run<C>(G + (src * C + q) * RP + g * C, gr);
+#pragma unroll
+        for (int rho = 0; rho < R; ++rho) {
+          const float vm = v[rho][q];
+          const float vq = half ? __shfl_xor_sync(full, vm, 1) : vm;
+#pragma unroll
+          for (int c = 0; c < C; ++c) s[rho][c] = fmaf(-vq, gr[c], s[rho][c]);
+        }
+      }
+    }
+#pragma unroll 1
+    for (int o = 0; o < 2; ++o) {
+      const bool own = g == o;
+#pragma unroll
+      for (int cj = 0; cj < C; ++cj) {
+        const int j = o * C + cj;
+        if (j >= r) break;
+        const int jm = g * C + cj;   // this lane's component at step position cj
+        const float gjj = G[jm * RP + jm], ij = inv[jm];
+        float gr[C];
+        ld_run<C>(G + j * RP + g * C, gr);
+#pragma unroll
+        for (int rho = 0; rho < R; ++rho) {
+          const float vo = v[rho][cj];
+          float vn = vo;
+          if (!reg) {
+            if (gjj > 0.f) vn = fmaxf(0.f, fmaf(s[rho][cj], ij, vo));
+          } else if (gjj + beta > 0.f) {
+            vn = fmaxf(0.f, (fmaf(vo, gjj, s[rho][cj]) - alpha) / (gjj + beta));
+          }
+          const float dl = own ? vn - vo : 0.f;
+          v[rho][cj] = own ? vn : vo;
+          const float dd = dl + __shfl_xor_sync(full, dl, 1);
+#pragma unroll
+          for (int c = 0; c < C; ++c) s[rho][c] = fmaf(-dd, gr[c], s[rho][c]);
+        }
+      }
+    }
+  } else if (RULE == 0) {
     // t_j = S_j - sum_q v_q G[q][j]
 #pragma unroll 1
     for (int o = 0; o < NG; ++o) {

@@ -411,9 +411,9 @@ def test_bf16_sketch_tensor_core_and_simt_agree(lib, ctx):
 
 def test_solve_monitor_gates_exact_checks(lib, ctx):
     """With a target, the device-side loop runs the exact residual only when the compressed
-    error monitor is within 5 % of the target; the stopping iteration equals the one found by
-    checking the exact residual at every check (the staged kernels, which never use the
-    monitor)."""
+    error monitor is within 5 % of the target (0.2 % once an exact check has calibrated it); the
+    stopping iteration equals the one found by checking the exact residual at every check (the
+    staged kernels, which never use the monitor)."""
     pr = inputs.random_problem(13, 2000, 1500, 10, 20, w=2)
     X = cu(pr.X)
     res = {}
