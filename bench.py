@@ -565,8 +565,12 @@ def main():
     dp_achieved = dp_bytes / (dp_ms / dp_n * 1e-3) / 1e9
     shares = {k: v[0] for k, v in phases.items() if v[1] > 0}
     dom = max(shares, key=shares.get)
+    # DRAM bytes of one iterate_persistent_kernel launch (10 iterations) from an ncu capture of
+    # this workload (profiles/iterate_persistent_kernel_dense_20000x5000_r20.md: 10.19 MB read,
+    # nothing written back to DRAM within the launch): the slices are staged once a launch
+    it_traffic = 10.188e6 if (m, n, r, ell) == (20000, 5000, 20, 40) else None
     roofline = {"bound": "alu", "achieved": it_achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": it_achieved / alu_peak, "traffic": None,
+                "frac": it_achieved / alu_peak, "traffic": it_traffic,
                 "kernel": "iterate_persistent_kernel (FastHALS-RP iterations)",
                 "peak_source": f"derived: {n_sms} SMs x 128 FP32 lanes x 2 FLOP x {sm_mhz:.0f} MHz",
                 "units": f"{flops_iter} FLOP per iteration x {iters_run} iterations",
