@@ -200,16 +200,29 @@ __device__ void block_share(int K, int NA, int NB, const float* A1, int lda1, co
   }
 }
 
-// G[p][q] = sum_k T[k][p] T[k][q] (RP x RP) from T (LQ x RP), 2 x 2 outputs a thread;
-// inv[j] = 1 / G[j][j] where G[j][j] > 0, else 0.
+// G[p][q] = sum_k T[k][p] T[k][q] (RP x RP) from T (LQ x RP); inv[j] = 1 / G[j][j] where
+// G[j][j] > 0, else 0. The 2 x 2 tiles of the upper triangle are computed over KS ranges of k
+// by different threads (partials in `red`, at least kNT * 4 floats), summed in a fixed order,
+// and mirrored. Ends with a block barrier.
 template <int RP>
-__device__ __forceinline__ void gram_rp(const float* T, int LQ, float* G, float* inv) {
-  constexpr int H2 = RP / 2;
-  for (int u = threadIdx.x; u < H2 * H2; u += kNT) {
-    const int p0 = 2 * (u / H2), q0 = 2 * (u % H2);
+__device__ __forceinline__ void gram_rp(const float* T, int LQ, float* G, float* inv, float* red) {
+  constexpr int T2 = RP / 2, NT = T2 * (T2 + 1) / 2;
+  constexpr int KS0 = kNT / NT < 1 ? 1 : kNT / NT;
+  const int ks_cap = (LQ + 3) / 4;   // at least four k a range
+  const int KS = KS0 < ks_cap ? KS0 : ks_cap;
+  const int chunk = (LQ + KS - 1) / KS;
+  for (int u = threadIdx.x; u < NT * KS; u += kNT) {
+    const int tile = u % NT, kk = u / NT;
+    int P = 0, v = tile;
+    while (v >= T2 - P) {
+      v -= T2 - P;
+      ++P;
+    }
+    const int p0 = 2 * P, q0 = 2 * (P + v);
     float g00 = 0.f, g01 = 0.f, g10 = 0.f, g11 = 0.f;
+    const int k1 = min(LQ, (kk + 1) * chunk);
 #pragma unroll 4
-    for (int k = 0; k < LQ; ++k) {
+    for (int k = kk * chunk; k < k1; ++k) {
       const float2 a = *reinterpret_cast<const float2*>(T + k * RP + p0);
       const float2 b = *reinterpret_cast<const float2*>(T + k * RP + q0);
       g00 = fmaf(a.x, b.x, g00);
@@ -217,14 +230,23 @@ __device__ __forceinline__ void gram_rp(const float* T, int LQ, float* G, float*
       g10 = fmaf(a.y, b.x, g10);
       g11 = fmaf(a.y, b.y, g11);
     }
-    G[p0 * RP + q0] = g00;
-    G[p0 * RP + q0 + 1] = g01;
-    G[(p0 + 1) * RP + q0] = g10;
-    G[(p0 + 1) * RP + q0 + 1] = g11;
-    if (p0 == q0) {
-      inv[p0] = g00 > 0.f ? 1.f / g00 : 0.f;
-      inv[p0 + 1] = g11 > 0.f ? 1.f / g11 : 0.f;
+    *reinterpret_cast<float4*>(red + 4 * u) = make_float4(g00, g01, g10, g11);
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < NT * 4; e += kNT) {
+    const int tile = e >> 2, x = e & 3;
+    float g = red[4 * tile + x];
+    for (int kk = 1; kk < KS; ++kk) g += red[4 * (kk * NT + tile) + x];
+    int P = 0, v = tile;
+    while (v >= T2 - P) {
+      v -= T2 - P;
+      ++P;
     }
+    if (v == 0 && x == 2) continue;   // the mirror of entry 1 of a diagonal tile
+    const int p = 2 * P + (x >> 1), q = 2 * (P + v) + (x & 1);
+    G[p * RP + q] = g;
+    G[q * RP + p] = g;
+    if (p == q) inv[p] = g > 0.f ? 1.f / g : 0.f;
   }
 }
 
@@ -473,7 +495,7 @@ __device__ __forceinline__ void iterate_body(const PArgs& a, const unsigned bid,
       }
     }
     __syncthreads();
-    gram_rp<RP>(HtT, LQ, Gw, invs);
+    gram_rp<RP>(HtT, LQ, Gw, invs, red);
     __syncthreads();
     {
       // group q of GA lanes takes the RA rows q, q + Q, q + 2Q, ... (Q = ceil(nrows / RA)), so
@@ -555,7 +577,7 @@ __device__ __forceinline__ void iterate_body(const PArgs& a, const unsigned bid,
       for (int e = t; e < LQ * RP; e += kNT) WtS[e] = acc_read(accA_r, EA, e) * rsc[e % RP];
     }
     __syncthreads();
-    gram_rp<RP>(WtS, LQ, Gh, invs);
+    gram_rp<RP>(WtS, LQ, Gh, invs, red);
     __syncthreads();
     float cross = 0.f;
     {
