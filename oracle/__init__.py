@@ -10,3 +10,4 @@ primitives (matmul, LAPACK QR/SVD) as single steps, no blocking or fusion beyond
 equations state. Functions whose result the paper does not fix are marked "parity unpinned".
 """
 from .nmf_oracle import *  # noqa: F401,F403
+from .fp8_oracle import *  # noqa: F401,F403

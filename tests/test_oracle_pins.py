@@ -533,3 +533,63 @@ def test_warmstart_features_reproduce_nndsvd():
     Tw, Th = WS.warmstart_targets(Wb, Hb, hs, Ws, Hs)
     W1, H1 = WS.warmstart_apply(Wb, Hb, hs, Tw, Th)
     assert np.allclose(W1, Ws) and np.allclose(H1[hs > 0], Hs[hs > 0])
+
+
+# ------------------------------------------------------------------ FP8 E4M3 copy of X
+
+def test_e4m3_decode_matches_the_format_definition():
+    """Codes the OCP E4M3 definition names: 1.0 = 0 0111 000, the largest finite 448 =
+    0 1111 110, the smallest normal 2^-6 = 0 0001 000, the smallest subnormal 2^-9 = 0 0000 001,
+    NaN = s 1111 111, and the sign bit."""
+    d = O.e4m3_decode
+    assert d(np.uint8(0x38)) == 1.0 and d(np.uint8(0xB8)) == -1.0
+    assert d(np.uint8(0x7E)) == 448.0 and d(np.uint8(0x08)) == 2.0 ** -6
+    assert d(np.uint8(0x01)) == 2.0 ** -9 and d(np.uint8(0x07)) == 7 / 8 * 2.0 ** -6
+    assert d(np.uint8(0x00)) == 0.0 and d(np.uint8(0x3C)) == 1.5
+    assert np.isnan(d(np.uint8(0x7F))) and np.isnan(d(np.uint8(0xFF)))
+    v = d(np.arange(127, dtype=np.uint8))
+    assert np.all(np.diff(v) > 0)                       # 127 increasing finite magnitudes
+    assert np.isfinite(d(np.arange(256, dtype=np.uint8))).sum() == 254
+
+
+def test_e4m3_encode_rounds_to_nearest_even_and_saturates():
+    e = O.e4m3_encode
+    assert e(1.0 + 1 / 16) == 0x38            # tie between 1 (mantissa 000) and 1.125: even
+    assert e(1.0 + 3 / 16) == 0x3A            # tie between 1.125 and 1.25 (mantissa 010)
+    assert e(1.0 + 1 / 16 + 1e-9) == 0x39     # just above the tie
+    assert e(2.0 ** -10) == 0x00              # tie between 0 and 2^-9: zero (even)
+    assert e(3 * 2.0 ** -10) == 0x02          # tie between 2^-9 and 2^-8: 2^-8 (even)
+    assert e(500.0) == 0x7E and e(-1e6) == 0xFE
+    assert e(-0.0) == 0x80 and e(-1e-6) == 0x80   # sign bit kept when rounding to zero
+    rng = np.random.default_rng(0)
+    v = np.exp(rng.uniform(np.log(2.0 ** -6), np.log(448.0), 100000))
+    q = O.e4m3_decode(e(v))
+    assert np.max(np.abs(q - v) / v) <= 2.0 ** -4   # half an ulp of a 3-bit mantissa
+    # nearest: no other finite code is closer
+    grid = O.e4m3_decode(np.arange(127, dtype=np.uint8))
+    w = rng.uniform(0, 448, 2000)
+    best = np.min(np.abs(grid[None, :] - w[:, None]), axis=1)
+    assert np.all(np.abs(O.e4m3_decode(e(w)) - w) <= best)
+
+
+def test_e8m0_tile_scale_is_the_smallest_power_of_two_that_fits():
+    rng = np.random.default_rng(1)
+    X = rng.exponential(1.0, (70, 45)) * np.exp(rng.uniform(-20, 20, (70, 45)))
+    X[32:64, 32:45] = 0.0                                # an all-zero edge tile
+    k = O.e8m0_tile_exponents(X)
+    assert k.shape == (3, 2) and k[1, 1] == 0
+    for a in range(3):
+        for b in range(2):
+            amax = np.abs(X[32 * a:32 * a + 32, 32 * b:32 * b + 32]).max()
+            if amax > 0:
+                assert amax / 2.0 ** k[a, b] <= 448.0 < amax / 2.0 ** (k[a, b] - 1)
+    codes, kk = O.fp8_quantize(X)
+    Xq = O.fp8_dequantize(codes, kk)
+    big = X >= 2.0 ** -6 * 2.0 ** np.repeat(np.repeat(kk, 32, 0), 32, 1)[:70, :45]
+    assert np.max(np.abs(Xq - X)[big] / X[big]) <= 2.0 ** -4
+    assert np.all(np.abs(Xq) <= 448.0 * 2.0 ** np.repeat(np.repeat(kk, 32, 0), 32, 1)[:70, :45])
+
+
+def test_fp8_layout_pads_rows_to_16_bytes():
+    assert O.fp8_layout(100, 5000) == (5008, 500992, 500992 + 4 * 157)
+    assert O.fp8_layout(64, 32) == (32, 2048, 2048 + 2)
