@@ -46,7 +46,8 @@ typedef enum {
 typedef enum {
   NMF_PREC_FP32 = 0,         /* X read as FP32 */
   NMF_PREC_BF16 = 1,         /* X read as BF16, tensor cores, FP32 accumulation */
-  NMF_PREC_FP8_E4M3 = 2      /* reserved */
+  NMF_PREC_FP8_E4M3 = 2      /* X read as the FP8 copy of nmf_quantize (E4M3 codes, one E8M0
+                                scale a 32 x 32 tile); nmf_solve compresses from the FP32 X */
 } nmf_precision;
 
 /* Update rule of the iterations. */
@@ -133,18 +134,29 @@ nmf_status nmf_gaussian(nmf_ctx* ctx, int64_t rows, int64_t cols, uint64_t seed,
                         uint32_t stream_id, float* out);
 
 /*
- * Copy X (FP32, m x n, leading dimension ldx) to BF16 (round to nearest even), dense m x n:
- * `Xq` holds m*n uint16 BF16 codes. The low-precision copy the BF16 sketch and compression read.
+ * Low-precision copy of X (FP32, m x n, leading dimension ldx) that the sketch and compression
+ * read. `Xq` (device) must hold nmf_quantized_bytes(prec, m, n) bytes.
+ *   prec = NMF_PREC_BF16: m*n BF16 codes, dense m x n, round to nearest even.
+ *   prec = NMF_PREC_FP8_E4M3: OCP FP8 E4M3 codes, row pitch ldq = n rounded up to 16 bytes (the
+ *     pad columns are zero), then, at byte offset ceil(m * ldq / 256) * 256, one E8M0 byte
+ *     k + 127 for every 32 x 32 tile (ceil(m/32) rows of ceil(n/32), row-major). 2^k is the
+ *     smallest power of two with amax / 2^k <= 448 over the tile (k = 0 for an all-zero tile,
+ *     clamped to [-127, 127]); each code is round-to-nearest-even of x / 2^k, saturating, and
+ *     the copy's value of x is code * 2^k.
  */
 nmf_status nmf_quantize(nmf_ctx* ctx, int32_t prec, const float* X, int64_t m, int64_t n,
                         int64_t ldx, void* Xq);
+
+/* Bytes of the nmf_quantize copy of an m x n matrix (0 for an unknown precision). */
+size_t nmf_quantized_bytes(int32_t prec, int64_t m, int64_t n);
 
 /*
  * One fused pass over X (the building block of every sketch and compression step):
  *   Y = X V   (m x l, reduction over n)   and   Z = X^T U   (n x l, reduction over m),
  * reading X once. V is n x l, U is m x l, all FP32 row-major; Y, Z are written (not accumulated).
- * `X` is FP32 (prec = NMF_PREC_FP32, leading dimension ldx) or the dense BF16 copy from
- * nmf_quantize (prec = NMF_PREC_BF16, ldx must equal n). Either of V/Y or U/Z may be NULL
+ * `X` is FP32 (prec = NMF_PREC_FP32, leading dimension ldx) or the BF16 / FP8 copy from
+ * nmf_quantize (prec = NMF_PREC_BF16 / NMF_PREC_FP8_E4M3, ldx must equal n; the FP8 copy's
+ * values are code * 2^k of its tile scale). Either of V/Y or U/Z may be NULL
  * (both of a pair) to skip that product. 1 <= l <= 128.
  */
 nmf_status nmf_dual_pass(nmf_ctx* ctx, int32_t prec, const void* X, int64_t m, int64_t n,
@@ -154,8 +166,9 @@ nmf_status nmf_dual_pass(nmf_ctx* ctx, int32_t prec, const void* X, int64_t m, i
 /*
  * Thin QR of a tall FP32 matrix Y (rows x l, rows >= l): writes Q (rows x l, FP32, orthonormal
  * columns, the unique Q whose R has a positive diagonal; Section 3, Eq. 3.4-3.5). CholeskyQR2
- * (Fukaya et al. 2014): the Gram matrix Y^T Y and its Cholesky factor are formed in FP64; a
- * non-positive pivot latches NMF_ERR_QR_BREAKDOWN. Q may alias Y.
+ * (Fukaya et al. 2014): the Gram matrix Y^T Y, its factor and R^-1 are formed in float-float
+ * arithmetic (about 44 significant bits) on the FP32 pipes; a non-positive pivot latches
+ * NMF_ERR_QR_BREAKDOWN. Q may alias Y.
  */
 nmf_status nmf_qr(nmf_ctx* ctx, const float* Y, int64_t rows, int32_t ell, float* Q);
 
@@ -164,7 +177,8 @@ nmf_status nmf_qr(nmf_ctx* ctx, const float* Y, int64_t rows, int32_t ell, float
  * (X^T X)^w X^T Omega_R, orthonormalised after every application of X or X^T, both chains
  * advancing together so that 2w + 1 passes over X serve both. omega_L (n x l) / omega_R (m x l)
  * may be NULL: drawn with nmf_gaussian(seed = p->seed, stream_id 0 / 1).
- * `X` is FP32 with leading dimension ldx (p->prec = FP32), or the nmf_quantize copy (BF16, ldx = n).
+ * `X` is FP32 with leading dimension ldx (p->prec = FP32), or the nmf_quantize copy of the
+ * precision p->prec (BF16 or FP8, ldx = n).
  */
 nmf_status nmf_sketch(nmf_ctx* ctx, const nmf_params* p, const void* X, int64_t ldx,
                       const float* omega_L, const float* omega_R, float* QL, float* QR);

@@ -14,8 +14,9 @@ choice on top of the method (the sketch and compression contractions read X only
                the sign bit of v is kept, also when the magnitude rounds to zero.
   tile scale   for the 32 x 32 tile T (edge tiles cover what is left), amax = max |x| over T;
                2^k with k the smallest integer such that amax / 2^k <= 448 (amax = f 2^e with
-               f in [0.5, 1): k = e - 9 if f <= 0.875, else e - 8); k = 0 for an all-zero tile.
-               Stored as the E8M0 byte k + 127.
+               f in [0.5, 1): k = e - 9 if f <= 0.875, else e - 8), clamped to the E8M0 range
+               [-127, 127] (codes then saturate); k = 0 for an all-zero tile. Stored as the
+               E8M0 byte k + 127.
   X_q          encode(x / 2^k) * 2^k entry by entry.
   sums         ||X||^2 and <X - X_q, X> (the BF16 path's monitor correction, with X_q the FP8 copy).
 
@@ -78,7 +79,7 @@ def e8m0_tile_exponents(X):
             if amax == 0.0:
                 continue
             f, e = np.frexp(amax)
-            k[a, b] = (e - 9) if f <= 0.875 else (e - 8)
+            k[a, b] = min(127, max(-127, (e - 9) if f <= 0.875 else (e - 8)))
     return k
 
 

@@ -75,14 +75,28 @@ cudaError_t launch_quantize_bf16_stats(const Launcher& L, const float* X, int64_
                                        int64_t ldx, __nv_bfloat16* Xq, int64_t ldq, double* x2_out,
                                        double* corr_out, void* ws, size_t ws_bytes);
 
-// Dual pass Y = X V (m x ell), Z = X^T U (n x ell). x_bf16 selects the element type of X.
+// Element type of X in the dual pass: FP32 (ldx any), BF16 (dense), or the FP8 copy made by
+// launch_quantize_fp8_stats (ldx ignored: the copy's own row pitch and tile scales are used).
+enum : int { kXFp32 = 0, kXBf16 = 1, kXFp8 = 2 };
+
+// Bytes of the FP8 copy of an m x n matrix: E4M3 codes with row pitch ldq = n rounded up to 16
+// (pad columns zero), then at byte scale_off (a multiple of 256) one E8M0 byte a 32 x 32 tile,
+// ceil(m / 32) rows of ceil(n / 32).
+size_t fp8_copy_bytes(int64_t m, int64_t n, int64_t* ldq = nullptr, int64_t* scale_off = nullptr);
+// FP32 X -> the FP8 copy (codes and scales), plus ||X||^2 and <X - X_q, X> (either output may
+// be null). ws: quantize_stats_ws_bytes() + 64 bytes.
+cudaError_t launch_quantize_fp8_stats(const Launcher& L, const float* X, int64_t m, int64_t n,
+                                      int64_t ldx, uint8_t* Xq, double* x2_out, double* corr_out,
+                                      void* ws, size_t ws_bytes);
+
+// Dual pass Y = X V (m x ell), Z = X^T U (n x ell). x_type selects the element type of X.
 // ws: workspace for partial sums (size from dual_pass_ws_bytes).
 // BF16 X with both products goes to the tensor-core kernel when TMA can address X (ldx a
 // multiple of 8, X 16-byte aligned) unless force_simt is set.
 size_t dual_pass_ws_bytes(int64_t m, int64_t n, int ell);
 // split: on the tensor-core path, V and U enter as hi + lo BF16 pairs (only X is rounded to
 // BF16), which the compression uses; ignored elsewhere.
-cudaError_t launch_dual_pass(const Launcher& L, const void* X, bool x_bf16, int64_t m, int64_t n,
+cudaError_t launch_dual_pass(const Launcher& L, const void* X, int x_type, int64_t m, int64_t n,
                              int64_t ldx, int ell, const float* V, const float* U, float* Y,
                              float* Z, void* ws, size_t ws_bytes, int* status,
                              bool force_simt = false, bool split = false);

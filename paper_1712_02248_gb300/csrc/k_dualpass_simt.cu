@@ -8,6 +8,8 @@
 // in registers across the CTA's rows; Y for the CTA's rows is carried in shared memory across its
 // columns. Partial sums go to per-rectangle slots and a second kernel adds them in a fixed order
 // (deterministic results, no atomics).
+#include <cuda_fp8.h>
+
 #include "common.cuh"
 
 namespace nmfrp {
@@ -18,14 +20,28 @@ constexpr int kChunkRows = 32;
 constexpr int kChunkCols = 128;
 constexpr int kXsStride = kChunkCols + 4;
 
-__device__ __forceinline__ float load_x(const float* p) { return __ldcs(p); }
-__device__ __forceinline__ float load_x(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+// X element (gr, gc): FP32, BF16, or an FP8 copy (E4M3 code times the E8M0 scale 2^(S - 127) of
+// its 32 x 32 tile, S row-major over tiles with tn tiles a row)
+__device__ __forceinline__ float load_x(const float* X, int64_t gr, int64_t gc, int64_t ldx,
+                                        const uint8_t*, int64_t) {
+  return __ldcs(X + gr * ldx + gc);
+}
+__device__ __forceinline__ float load_x(const __nv_bfloat16* X, int64_t gr, int64_t gc,
+                                        int64_t ldx, const uint8_t*, int64_t) {
+  return __bfloat162float(X[gr * ldx + gc]);
+}
+__device__ __forceinline__ float load_x(const uint8_t* X, int64_t gr, int64_t gc, int64_t ldx,
+                                        const uint8_t* S, int64_t tn) {
+  const __nv_fp8_storage_t q = X[gr * ldx + gc];
+  const int k = static_cast<int>(S[(gr >> 5) * tn + (gc >> 5)]) - 127;
+  return ldexpf(__half2float(__half(__nv_cvt_fp8_to_halfraw(q, __NV_E4M3))), k);
+}
 
 template <int LP, typename XT>
 __global__ void __launch_bounds__(kThreads) dual_pass_simt_kernel(
     const XT* __restrict__ X, int64_t m, int64_t n, int64_t ldx, int ell,
     const float* __restrict__ V, const float* __restrict__ U, float* __restrict__ Ypart,
-    float* __restrict__ Zpart, int RC, int CC) {
+    float* __restrict__ Zpart, int RC, int CC, const uint8_t* __restrict__ S, int64_t tn) {
   constexpr int KZ = LP / 4;   // Z accumulators per column per thread
   constexpr int KY = LP / 8;   // Y outputs per thread per chunk
   extern __shared__ __align__(16) float smem[];
@@ -67,7 +83,7 @@ __global__ void __launch_bounds__(kThreads) dual_pass_simt_kernel(
       for (int e = t; e < kChunkRows * kChunkCols; e += kThreads) {
         const int i = e >> 7, c = e & 127;
         const int64_t gr = rbase + i, gc = cbase + c;
-        Xs[i * kXsStride + c] = (gr < m && gc < n) ? load_x(X + gr * ldx + gc) : 0.f;
+        Xs[i * kXsStride + c] = (gr < m && gc < n) ? load_x(X, gr, gc, ldx, S, tn) : 0.f;
       }
       for (int e = t; e < kChunkRows * LP; e += kThreads) {
         const int i = e / LP, k = e - i * LP;
@@ -169,7 +185,8 @@ size_t smem_bytes(int LP, int RC) {
 
 template <int LP, typename XT>
 cudaError_t run(const Launcher& L, const XT* X, int64_t m, int64_t n, int64_t ldx, int ell,
-                const float* V, const float* U, float* Y, float* Z, float* ws) {
+                const float* V, const float* U, float* Y, float* Z, float* ws,
+                const uint8_t* S, int64_t tn) {
   const Split s = choose_split(m, n, LP);
   float* Ypart = ws;
   float* Zpart = ws + s.nb * m * ell;
@@ -180,7 +197,7 @@ cudaError_t run(const Launcher& L, const XT* X, int64_t m, int64_t n, int64_t ld
   if (err != cudaSuccess) return err;
   dim3 grid(static_cast<unsigned>(s.nb), static_cast<unsigned>(s.na));
   dual_pass_simt_kernel<LP, XT><<<grid, kThreads, sm, L.stream>>>(
-      X, m, n, ldx, ell, V, U, V ? Ypart : nullptr, U ? Zpart : nullptr, s.RC, s.CC);
+      X, m, n, ldx, ell, V, U, V ? Ypart : nullptr, U ? Zpart : nullptr, s.RC, s.CC, S, tn);
   L.count();
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
   if (V) {
@@ -200,14 +217,15 @@ cudaError_t run(const Launcher& L, const XT* X, int64_t m, int64_t n, int64_t ld
 
 template <typename XT>
 cudaError_t dispatch(const Launcher& L, const XT* X, int64_t m, int64_t n, int64_t ldx, int ell,
-                     const float* V, const float* U, float* Y, float* Z, float* ws) {
+                     const float* V, const float* U, float* Y, float* Z, float* ws,
+                     const uint8_t* S = nullptr, int64_t tn = 0) {
   switch (lp_for(ell)) {
-    case 16: return run<16>(L, X, m, n, ldx, ell, V, U, Y, Z, ws);
-    case 32: return run<32>(L, X, m, n, ldx, ell, V, U, Y, Z, ws);
-    case 48: return run<48>(L, X, m, n, ldx, ell, V, U, Y, Z, ws);
-    case 64: return run<64>(L, X, m, n, ldx, ell, V, U, Y, Z, ws);
-    case 96: return run<96>(L, X, m, n, ldx, ell, V, U, Y, Z, ws);
-    default: return run<128>(L, X, m, n, ldx, ell, V, U, Y, Z, ws);
+    case 16: return run<16>(L, X, m, n, ldx, ell, V, U, Y, Z, ws, S, tn);
+    case 32: return run<32>(L, X, m, n, ldx, ell, V, U, Y, Z, ws, S, tn);
+    case 48: return run<48>(L, X, m, n, ldx, ell, V, U, Y, Z, ws, S, tn);
+    case 64: return run<64>(L, X, m, n, ldx, ell, V, U, Y, Z, ws, S, tn);
+    case 96: return run<96>(L, X, m, n, ldx, ell, V, U, Y, Z, ws, S, tn);
+    default: return run<128>(L, X, m, n, ldx, ell, V, U, Y, Z, ws, S, tn);
   }
 }
 
@@ -220,11 +238,20 @@ size_t dual_pass_ws_bytes(int64_t m, int64_t n, int ell) {
   return simt > tc ? simt : tc;
 }
 
-cudaError_t launch_dual_pass(const Launcher& L, const void* X, bool x_bf16, int64_t m, int64_t n,
+cudaError_t launch_dual_pass(const Launcher& L, const void* X, int x_type, int64_t m, int64_t n,
                              int64_t ldx, int ell, const float* V, const float* U, float* Y,
                              float* Z, void* ws, size_t ws_bytes, int* status, bool force_simt,
                              bool split) {
   if (ws_bytes < dual_pass_ws_bytes(m, n, ell)) return cudaErrorInvalidValue;
+  if (x_type == kXFp8) {
+    // the FP8 copy: codes with row pitch ldq, then the tile scales (fp8_copy_bytes)
+    int64_t ldq = 0, off = 0;
+    fp8_copy_bytes(m, n, &ldq, &off);
+    const uint8_t* q = static_cast<const uint8_t*>(X);
+    return dispatch(L, q, m, n, ldq, ell, V, U, Y, Z, static_cast<float*>(ws), q + off,
+                    (n + 31) / 32);
+  }
+  const bool x_bf16 = x_type == kXBf16;
   if (x_bf16 && V && U && !force_simt && dual_pass_tc_supported(m, n, ldx, ell, X))
     return launch_dual_pass_tc(L, static_cast<const __nv_bfloat16*>(X), m, n, ldx, ell, V, U, Y,
                                Z, ws, ws_bytes, status, split);

@@ -1,4 +1,6 @@
 // Gaussian test matrix (Section 3: Omega ~ N(0,1)) and the FP32 -> BF16 copy of X.
+#include <cuda_fp8.h>
+
 #include "common.cuh"
 
 namespace nmfrp {
@@ -183,6 +185,78 @@ __global__ void __launch_bounds__(256) quantize_bf16_stats_kernel(
   }
 }
 
+// FP8 copy of X: OCP E4M3 codes at Xq[i * ldq + j] (ldq = n rounded up to 16, pad columns zero)
+// and one E8M0 scale byte k + 127 a 32 x 32 tile at S[(i / 32) * tn + j / 32], where 2^k is the
+// smallest power of two with amax / 2^k <= 448 over the tile (amax = f 2^e, f in [0.5, 1):
+// k = e - 9 if f <= 0.875 else e - 8; k = 0 for an all-zero tile; clamped to [-127, 127]).
+// Codes are round-to-nearest-even of x / 2^k, saturating. One warp a tile (lane = column, the
+// tile's 32 loads in flight), plus the monitor sums ||X||^2 and <X - X_q, X> in float-float.
+__global__ void __launch_bounds__(256) quantize_fp8_stats_kernel(
+    const float* __restrict__ X, int64_t m, int64_t n, int64_t ldx, uint8_t* __restrict__ Xq,
+    int64_t ldq, uint8_t* __restrict__ S, double* __restrict__ part) {
+  __shared__ double red[2][8];
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t tn = (n + 31) / 32, tiles = ((m + 31) / 32) * tn;
+  FSum sx2, scorr;
+  for (int64_t tile = static_cast<int64_t>(blockIdx.x) * 8 + wib; tile < tiles;
+       tile += static_cast<int64_t>(gridDim.x) * 8) {
+    const int64_t ti = tile / tn, tj = tile - ti * tn;
+    const int64_t r0 = ti * 32, c = tj * 32 + lane;
+    const int nr = m - r0 < 32 ? static_cast<int>(m - r0) : 32;
+    const bool colv = c < n;
+    float x[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) x[i] = (i < nr && colv) ? __ldcs(X + (r0 + i) * ldx + c) : 0.f;
+    float amax = 0.f;
+#pragma unroll
+    for (int i = 0; i < 32; ++i) amax = fmaxf(amax, fabsf(x[i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(full, amax, o));
+    int k = 0;
+    if (amax > 0.f) {
+      int e;
+      const float f = frexpf(amax, &e);
+      k = f <= 0.875f ? e - 9 : e - 8;
+      k = k < -127 ? -127 : (k > 127 ? 127 : k);
+    }
+    const float sinv = ldexpf(1.f, -k), sc = ldexpf(1.f, k);
+    float tx2 = 0.f, tcorr = 0.f;
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      const __nv_fp8_storage_t q = __nv_cvt_float_to_fp8(__fmul_rn(x[i], sinv), __NV_SATFINITE,
+                                                         __NV_E4M3);
+      const float xq = __half2float(__half(__nv_cvt_fp8_to_halfraw(q, __NV_E4M3))) * sc;
+      if (i < nr && c < ldq) Xq[(r0 + i) * ldq + c] = colv ? static_cast<uint8_t>(q) : uint8_t(0);
+      tx2 = fmaf(x[i], x[i], tx2);
+      tcorr = fmaf(x[i], x[i] - xq, tcorr);
+    }
+    sx2.add(tx2);
+    scorr.add(tcorr);
+    if (lane == 0) S[tile] = static_cast<uint8_t>(k + 127);
+  }
+  double x2 = sx2.value(), corr = scorr.value();
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    x2 += __shfl_xor_sync(full, x2, o);
+    corr += __shfl_xor_sync(full, corr, o);
+  }
+  if (lane == 0) {
+    red[0][wib] = x2;
+    red[1][wib] = corr;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < 8; ++w) {
+      a += red[0][w];
+      b += red[1][w];
+    }
+    part[2 * blockIdx.x] = a;
+    part[2 * blockIdx.x + 1] = b;
+  }
+}
+
 __global__ void stats_final_kernel(const double* __restrict__ part, int nparts,
                                    double* __restrict__ x2_out, double* __restrict__ corr_out) {
   double a = 0.0, b = 0.0;
@@ -233,6 +307,33 @@ cudaError_t launch_quantize_bf16(const Launcher& L, const float* X, int64_t m, i
   else
     quantize_bf16_kernel<<<grid_for(m * ldq, 256), 256, 0, L.stream>>>(X, m, n, ldx, Xq, ldq);
   L.count();
+  return cudaGetLastError();
+}
+
+size_t fp8_copy_bytes(int64_t m, int64_t n, int64_t* ldq, int64_t* scale_off) {
+  const int64_t q = (n + 15) / 16 * 16;
+  const int64_t off = (m * q + 255) / 256 * 256;
+  if (ldq) *ldq = q;
+  if (scale_off) *scale_off = off;
+  return static_cast<size_t>(off + ((m + 31) / 32) * ((n + 31) / 32));
+}
+
+cudaError_t launch_quantize_fp8_stats(const Launcher& L, const float* X, int64_t m, int64_t n,
+                                      int64_t ldx, uint8_t* Xq, double* x2_out, double* corr_out,
+                                      void* ws, size_t ws_bytes) {
+  if (m <= 0 || n <= 0 || ldx < n) return cudaErrorInvalidValue;
+  if (ws_bytes < quantize_stats_ws_bytes() + 64) return cudaErrorInvalidValue;
+  int64_t ldq = 0, off = 0;
+  fp8_copy_bytes(m, n, &ldq, &off);
+  double* part = static_cast<double*>(ws);
+  const int64_t tiles = ((m + 31) / 32) * ((n + 31) / 32);
+  const int grid = grid_for((tiles + 7) / 8, 1);
+  quantize_fp8_stats_kernel<<<grid, 256, 0, L.stream>>>(X, m, n, ldx, Xq, ldq, Xq + off, part);
+  // without destinations the sums land in the scratch just past the partials
+  double* sink = part + 2 * grid;
+  stats_final_kernel<<<1, 32, 0, L.stream>>>(part, grid, x2_out ? x2_out : sink,
+                                             corr_out ? corr_out : sink + 1);
+  L.count(2);
   return cudaGetLastError();
 }
 

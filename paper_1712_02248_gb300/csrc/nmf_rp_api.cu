@@ -196,9 +196,8 @@ nmf_status check_params(nmf_ctx* ctx, const nmf_params* p) {
     return fail(ctx, NMF_ERR_INVALID_ARG, "power_iters must be in [0, 32]");
   if (p->rule != NMF_RULE_FASTHALS_RP && p->rule != NMF_RULE_MU_RP)
     return fail(ctx, NMF_ERR_INVALID_ARG, "unknown rule %d", p->rule);
-  if (p->prec != NMF_PREC_FP32 && p->prec != NMF_PREC_BF16)
-    return fail(ctx, p->prec == NMF_PREC_FP8_E4M3 ? NMF_ERR_UNSUPPORTED : NMF_ERR_INVALID_ARG,
-                "precision %d not available", p->prec);
+  if (p->prec != NMF_PREC_FP32 && p->prec != NMF_PREC_BF16 && p->prec != NMF_PREC_FP8_E4M3)
+    return fail(ctx, NMF_ERR_INVALID_ARG, "precision %d not available", p->prec);
   if (p->alpha < 0 || p->beta < 0) return fail(ctx, NMF_ERR_INVALID_ARG, "alpha, beta must be >= 0");
   return NMF_OK;
 }
@@ -207,20 +206,24 @@ nmf_status check_x(nmf_ctx* ctx, const nmf_params* p, const void* X, int64_t ldx
   if (!X) return fail(ctx, NMF_ERR_INVALID_ARG, "X is NULL");
   if (p->prec == NMF_PREC_BF16 && ldx != p->n)
     return fail(ctx, NMF_ERR_INVALID_ARG, "BF16 X must be dense (ldx == n)");
+  if (p->prec == NMF_PREC_FP8_E4M3 && ldx != p->n)
+    return fail(ctx, NMF_ERR_INVALID_ARG, "FP8 X is the nmf_quantize layout (pass ldx == n)");
   if (ldx < p->n) return fail(ctx, NMF_ERR_INVALID_ARG, "ldx < n");
   return NMF_OK;
 }
 
 float eps_of(const nmf_params* p) { return p->eps > 0 ? static_cast<float>(p->eps) : 1e-12f; }
 
-// One dual pass with its scratch.
-nmf_status dual(nmf_ctx* ctx, const void* X, bool bf16, int64_t m, int64_t n, int64_t ldx, int ell,
+// One dual pass with its scratch; prec (nmf_precision) names the element type of X.
+nmf_status dual(nmf_ctx* ctx, const void* X, int prec, int64_t m, int64_t n, int64_t ldx, int ell,
                 const float* V, const float* U, float* Y, float* Z, Arena a, bool simt = false,
                 bool split = false) {
   Phase ph(ctx, NMF_PHASE_DUAL_PASS);
   size_t rest = 0;
   void* ws = a.rest(&rest);
-  NMF_CUDA(nmfrp::launch_dual_pass(launcher(ctx), X, bf16, m, n, ldx, ell, V, U, Y, Z, ws, rest,
+  const int xt = prec == NMF_PREC_BF16 ? nmfrp::kXBf16
+                 : prec == NMF_PREC_FP8_E4M3 ? nmfrp::kXFp8 : nmfrp::kXFp32;
+  NMF_CUDA(nmfrp::launch_dual_pass(launcher(ctx), X, xt, m, n, ldx, ell, V, U, Y, Z, ws, rest,
                                    ctx->d_status, simt, split),
            "dual pass");
   return NMF_OK;
@@ -265,7 +268,7 @@ nmf_status sketch_impl(nmf_ctx* ctx, const nmf_params* p, const void* X, int64_t
                        const float* omega_L, const float* omega_R, float* QL, float* QR, Arena a) {
   const int64_t m = p->m, n = p->n;
   const int l = p->ell;
-  const bool bf16 = p->prec == NMF_PREC_BF16;
+  const int bf16 = p->prec;   // element type of X for every pass
   const bool simt = (p->flags & NMF_FLAG_SIMT_DUAL_PASS) != 0;
   float* mR = a.take<float>(m * l);   // right chain, m-side
   float* nL = a.take<float>(n * l);   // left chain, n-side
@@ -325,7 +328,7 @@ nmf_status compress_impl(nmf_ctx* ctx, const nmf_params* p, const void* X, int64
   float* XhatT = a.take<float>(n * l);
   // the compressed data feed every iteration and the error monitor: Q_L, Q_R enter the BF16
   // tensor-core pass as hi + lo pairs so that only X itself is rounded
-  nmf_status st = dual(ctx, X, p->prec == NMF_PREC_BF16, m, n, ldx, l, QR, QL, Xchk, XhatT, a,
+  nmf_status st = dual(ctx, X, p->prec, m, n, ldx, l, QR, QL, Xchk, XhatT, a,
                        (p->flags & NMF_FLAG_SIMT_DUAL_PASS) != 0, true);
   if (st != NMF_OK) return st;
   dim3 grid(static_cast<unsigned>(cdiv(n, 32)), static_cast<unsigned>(cdiv(l, 32)));
@@ -623,6 +626,7 @@ nmf_status nmf_workspace_size(const nmf_params* p, size_t* bytes) {
   const int64_t m = p->m, n = p->n, l = p->ell, r = p->r;
   size_t b = 0;
   if (p->prec == NMF_PREC_BF16) b += 2 * static_cast<size_t>(m * ((n + 7) / 8 * 8)) + 1024;
+  if (p->prec == NMF_PREC_FP8_E4M3) b += nmfrp::fp8_copy_bytes(m, n) + 1024;
   b += sizeof(float) * (2 * (m * l + n * l) + l * n + m * l) + 4096;  // QL QR Xhat Xchk + omega
   size_t scratch = sketch_ws(p, true);
   scratch = std::max(scratch, sizeof(float) * n * l + 1024 + pass_scratch(m, n, p->ell));
@@ -646,15 +650,31 @@ nmf_status nmf_gaussian(nmf_ctx* ctx, int64_t rows, int64_t cols, uint64_t seed,
   return NMF_OK;
 }
 
+size_t nmf_quantized_bytes(int32_t prec, int64_t m, int64_t n) {
+  if (m < 1 || n < 1) return 0;
+  if (prec == NMF_PREC_BF16) return 2 * static_cast<size_t>(m * n);
+  if (prec == NMF_PREC_FP8_E4M3) return nmfrp::fp8_copy_bytes(m, n);
+  if (prec == NMF_PREC_FP32) return 4 * static_cast<size_t>(m * n);
+  return 0;
+}
+
 nmf_status nmf_quantize(nmf_ctx* ctx, int32_t prec, const float* X, int64_t m, int64_t n,
                         int64_t ldx, void* Xq) {
   if (!ctx) return NMF_ERR_INVALID_ARG;
-  if (prec != NMF_PREC_BF16)
-    return fail(ctx, prec == NMF_PREC_FP8_E4M3 ? NMF_ERR_UNSUPPORTED : NMF_ERR_INVALID_ARG,
-                "quantize supports BF16");
+  if (prec != NMF_PREC_BF16 && prec != NMF_PREC_FP8_E4M3)
+    return fail(ctx, NMF_ERR_INVALID_ARG, "quantize makes a BF16 or an FP8 copy");
   if (!X || !Xq || m < 1 || n < 1 || ldx < n)
     return fail(ctx, NMF_ERR_INVALID_ARG, "bad quantize arguments");
   DeviceGuard g(ctx->device);
+  if (prec == NMF_PREC_FP8_E4M3) {
+    nmf_status st = ensure_ws(ctx, nmfrp::quantize_stats_ws_bytes() + 4096);
+    if (st != NMF_OK) return st;
+    NMF_CUDA(nmfrp::launch_quantize_fp8_stats(launcher(ctx), X, m, n, ldx,
+                                              static_cast<uint8_t*>(Xq), nullptr, nullptr,
+                                              ctx->ws, ctx->ws_bytes),
+             "quantize");
+    return NMF_OK;
+  }
   NMF_CUDA(nmfrp::launch_quantize_bf16(launcher(ctx), X, m, n, ldx,
                                        static_cast<__nv_bfloat16*>(Xq), n),
            "quantize");
@@ -667,17 +687,17 @@ nmf_status nmf_dual_pass(nmf_ctx* ctx, int32_t prec, const void* X, int64_t m, i
   if (!ctx) return NMF_ERR_INVALID_ARG;
   if (!X || m < 1 || n < 1 || ell < 1 || ell > 128 || ldx < n)
     return fail(ctx, NMF_ERR_INVALID_ARG, "bad dual pass sizes");
-  if (prec != NMF_PREC_FP32 && prec != NMF_PREC_BF16)
+  if (prec != NMF_PREC_FP32 && prec != NMF_PREC_BF16 && prec != NMF_PREC_FP8_E4M3)
     return fail(ctx, NMF_ERR_INVALID_ARG, "bad precision %d", prec);
-  if (prec == NMF_PREC_BF16 && ldx != n)
-    return fail(ctx, NMF_ERR_INVALID_ARG, "BF16 X must be dense (ldx == n)");
+  if (prec != NMF_PREC_FP32 && ldx != n)
+    return fail(ctx, NMF_ERR_INVALID_ARG, "BF16 / FP8 X must be the dense copy (ldx == n)");
   if ((V == nullptr) != (Y == nullptr) || (U == nullptr) != (Z == nullptr) || (!V && !U))
     return fail(ctx, NMF_ERR_INVALID_ARG, "V/Y and U/Z must be given in pairs");
   DeviceGuard g(ctx->device);
   nmf_status st = ensure_ws(ctx, nmfrp::dual_pass_ws_bytes(m, n, ell) + 4096);
   if (st != NMF_OK) return st;
   Arena a{static_cast<char*>(ctx->ws), ctx->ws_bytes};
-  return dual(ctx, X, prec == NMF_PREC_BF16, m, n, ldx, ell, V, U, Y, Z, a);
+  return dual(ctx, X, prec, m, n, ldx, ell, V, U, Y, Z, a);
 }
 
 nmf_status nmf_qr(nmf_ctx* ctx, const float* Y, int64_t rows, int32_t ell, float* Q) {
@@ -819,13 +839,33 @@ nmf_status nmf_solve(nmf_ctx* ctx, const nmf_params* p, int32_t init, const floa
              "quantize");
     Xp = Xq;
     ldp = ldq;
+  } else if (p->prec == NMF_PREC_FP8_E4M3) {
+    uint8_t* Xq = a.take<uint8_t>(static_cast<int64_t>(nmfrp::fp8_copy_bytes(m, n)));
+    Phase ph(ctx, NMF_PHASE_QUANTIZE);
+    size_t qrest = 0;
+    void* qws = a.rest(&qrest);
+    // ||X||^2 into solve[0]; the compression reads the FP32 X (below), so the monitor needs no
+    // rounding term and solve[3] stays 0
+    NMF_CUDA(nmfrp::launch_quantize_fp8_stats(launcher(ctx), X, m, n, ldx, Xq, ctx->d_solve,
+                                              nullptr, qws, qrest),
+             "quantize");
+    Xp = Xq;
+    ldp = n;
   }
   float* QL = a.take<float>(m * l);
   float* QR = a.take<float>(n * l);
   float* Xhat = a.take<float>(l * n);
   float* Xchk = a.take<float>(m * l);
   if ((st = sketch_impl(ctx, p, Xp, ldp, nullptr, nullptr, QL, QR, a)) != NMF_OK) return st;
-  if ((st = compress_impl(ctx, p, Xp, ldp, QL, QR, Xhat, Xchk, a)) != NMF_OK) return st;
+  if (p->prec == NMF_PREC_FP8_E4M3) {
+    // precision recovery: the E4M3 rounding of X (relative error up to 2^-4) would set the
+    // floor of the compressed problem, so the compression reads the FP32 X with the final Q
+    nmf_params p32 = *p;
+    p32.prec = NMF_PREC_FP32;
+    if ((st = compress_impl(ctx, &p32, X, ldx, QL, QR, Xhat, Xchk, a)) != NMF_OK) return st;
+  } else if ((st = compress_impl(ctx, p, Xp, ldp, QL, QR, Xhat, Xchk, a)) != NMF_OK) {
+    return st;
+  }
   if (init == NMF_INIT_NNDSVD) {
     Phase ph(ctx, NMF_PHASE_INIT);
     cudaError_t e = nmfrp::launch_nndsvd(launcher(ctx), m, n, p->r, p->ell, QL, Xhat, W, H, a.rest(&need),
@@ -844,7 +884,7 @@ nmf_status nmf_solve(nmf_ctx* ctx, const nmf_params* p, int32_t init, const floa
   void* ws = a.rest(&rest);
   NMF_CUDA(cudaMemsetAsync(ctx->d_flags, 0, 4 * sizeof(int), ctx->stream), "solve flags");
   NMF_CUDA(cudaMemsetAsync(ctx->d_mon, 0, 4 * sizeof(float), ctx->stream), "solve monitor");
-  if (p->prec != NMF_PREC_BF16)
+  if (p->prec == NMF_PREC_FP32)
     NMF_CUDA(nmfrp::launch_sumsq(launcher(ctx), X, m, n, ldx, ctx->d_solve, ws, rest), "sumsq");
   const bool staged = (p->flags & NMF_FLAG_STAGED_ITERATE) || !nmfrp::iterate_persistent_supported(p->m, p->n, p->r, p->ell);
   cudaEvent_t ev[2] = {pool_event(ctx), pool_event(ctx)};
@@ -1038,6 +1078,8 @@ nmf_status nmf_solve_batched(nmf_ctx* ctx, int32_t count, const nmf_params* p, i
   for (int i = 0; i < count; ++i) {
     nmf_status st = check_params(ctx, &p[i]);
     if (st != NMF_OK) return st;
+    if (p[i].prec == NMF_PREC_FP8_E4M3)
+      return fail(ctx, NMF_ERR_UNSUPPORTED, "problem %d: FP8 copies are single-solve only", i);
     if (!X[i] || !W[i] || !H[i] || ldx[i] < p[i].n)
       return fail(ctx, NMF_ERR_INVALID_ARG, "problem %d: bad pointers or ldx", i);
     if (p[i].iters < 0) return fail(ctx, NMF_ERR_INVALID_ARG, "problem %d: iters < 0", i);

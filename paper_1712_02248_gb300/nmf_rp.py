@@ -34,7 +34,7 @@ EXPORTS = ["nmf_create", "nmf_destroy", "nmf_set_stream", "nmf_last_error", "nmf
            "nmf_last_solve_info", "nmf_solve_batched", "nmf_last_batch_info",
            "nmf_mlp_param_count", "nmf_warmstart_features", "nmf_mlp_forward",
            "nmf_mlp_loss_grad", "nmf_mlp_adam", "nmf_mlp_train_step", "nmf_warmstart_apply",
-           "nmf_set_warmstart"]
+           "nmf_set_warmstart", "nmf_quantized_bytes"]
 PHASES = ["quantize", "dual_pass", "qr", "iterate", "residual", "init"]
 
 
@@ -69,6 +69,7 @@ _c = {
     "nmf_workspace_size": _sig("nmf_workspace_size", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_size_t)]),
     "nmf_gaussian": _sig("nmf_gaussian", ctypes.c_int, [_vp, _i64, _i64, _u64, _u32, _vp]),
     "nmf_quantize": _sig("nmf_quantize", ctypes.c_int, [_vp, _i32, _vp, _i64, _i64, _i64, _vp]),
+    "nmf_quantized_bytes": _sig("nmf_quantized_bytes", ctypes.c_size_t, [_i32, _i64, _i64]),
     "nmf_dual_pass": _sig("nmf_dual_pass", ctypes.c_int,
                           [_vp, _i32, _vp, _i64, _i64, _i64, _i32, _vp, _vp, _vp, _vp]),
     "nmf_qr": _sig("nmf_qr", ctypes.c_int, [_vp, _vp, _i64, _i32, _vp]),
@@ -183,9 +184,29 @@ def _dev_f32(t, name):
     return t
 
 
+class Fp8Copy:
+    """The FP8 copy of an m x n matrix made by nmf_quantize: `buf` holds the library's byte layout
+    (E4M3 codes with rows padded to 16 bytes, then one E8M0 scale byte a 32 x 32 tile)."""
+
+    def __init__(self, buf, m, n):
+        self.buf, self.shape = buf, (m, n)
+        self.is_cuda, self.device = buf.is_cuda, buf.device
+
+    def data_ptr(self):
+        return self.buf.data_ptr()
+
+
+def nmf_quantized_bytes(prec, m, n):
+    return int(_c["nmf_quantized_bytes"](PREC.get(prec, prec), m, n))
+
+
 def _x_arg(X, prec):
     if not X.is_cuda:
         raise ValueError("X must be a CUDA tensor")
+    if prec == PREC["fp8"]:
+        if not isinstance(X, Fp8Copy):
+            raise ValueError("FP8 X must be the nmf_quantize copy (Fp8Copy)")
+        return X, X.shape[1]
     if prec == PREC["bf16"]:
         if X.dtype != torch.bfloat16 or not X.is_contiguous():
             raise ValueError("BF16 X must be a contiguous bfloat16 tensor (see nmf_quantize)")
@@ -219,13 +240,22 @@ def nmf_gaussian(ctx, rows, cols, seed, stream_id, out=None):
 
 
 def nmf_quantize(ctx, X, prec="bf16", out=None):
+    """BF16 copy (a bfloat16 tensor) or FP8 copy (an Fp8Copy) of the FP32 matrix X."""
     m, n = X.shape
-    if out is None:
-        out = torch.empty((m, n), dtype=torch.bfloat16, device=X.device)
+    pr = PREC.get(prec, prec)
     if X.dtype != torch.float32 or X.stride(1) != 1:
         raise ValueError("X must be float32 with unit column stride")
-    ctx._check(_c["nmf_quantize"](ctx.handle, PREC.get(prec, prec), _ptr(X), m, n, X.stride(0),
-                                  _ptr(out)))
+    if pr == PREC["fp8"]:
+        nb = nmf_quantized_bytes(pr, m, n)
+        buf = out.buf if isinstance(out, Fp8Copy) else torch.empty(nb, dtype=torch.uint8,
+                                                                   device=X.device)
+        if buf.numel() < nb:
+            raise ValueError("FP8 buffer too small")
+        ctx._check(_c["nmf_quantize"](ctx.handle, pr, _ptr(X), m, n, X.stride(0), _ptr(buf)))
+        return Fp8Copy(buf, m, n)
+    if out is None:
+        out = torch.empty((m, n), dtype=torch.bfloat16, device=X.device)
+    ctx._check(_c["nmf_quantize"](ctx.handle, pr, _ptr(X), m, n, X.stride(0), _ptr(out)))
     return out
 
 
