@@ -100,6 +100,11 @@ cudaError_t launch_dual_pass(const Launcher& L, const void* X, int x_type, int64
                              int64_t ldx, int ell, const float* V, const float* U, float* Y,
                              float* Z, void* ws, size_t ws_bytes, int* status,
                              bool force_simt = false, bool split = false);
+// tcgen05 + TMA dual pass on the FP8 copy (codes converted to BF16 in shared memory).
+bool dual_pass_tc_fp8_supported(int64_t m, int64_t n, int ell, const void* Xq);
+cudaError_t launch_dual_pass_tc_fp8(const Launcher& L, const uint8_t* Xq, int64_t m, int64_t n,
+                                    int ell, const float* V, const float* U, float* Y, float* Z,
+                                    void* ws, size_t ws_bytes, int* status);
 // tcgen05 + TMA dual pass (BF16 X).
 bool dual_pass_tc_supported(int64_t m, int64_t n, int64_t ldx, int ell, const void* X);
 size_t dual_pass_tc_ws_bytes(int64_t m, int64_t n, int ell);

@@ -244,6 +244,9 @@ cudaError_t launch_dual_pass(const Launcher& L, const void* X, int x_type, int64
                              bool split) {
   if (ws_bytes < dual_pass_ws_bytes(m, n, ell)) return cudaErrorInvalidValue;
   if (x_type == kXFp8) {
+    if (V && U && !force_simt && dual_pass_tc_fp8_supported(m, n, ell, X))
+      return launch_dual_pass_tc_fp8(L, static_cast<const uint8_t*>(X), m, n, ell, V, U, Y, Z, ws,
+                                     ws_bytes, status);
     // the FP8 copy: codes with row pitch ldq, then the tile scales (fp8_copy_bytes)
     int64_t ldq = 0, off = 0;
     fp8_copy_bytes(m, n, &ldq, &off);

@@ -13,11 +13,16 @@
 // are BF16 copies made by a small preparation kernel (rows l..LP-1 zero).
 //
 // Warp roles (192 threads): warps 0-3 drain TMEM (each its 32-lane sub-partition) and write the
-// partial sums, warp 4 issues the TMA loads, warp 5 allocates TMEM and issues the MMAs. Partial
+// partial sums, warp 4 issues the TMA loads, warp 5 allocates TMEM and issues the MMAs.
+// FP8 X (E4M3 codes, one E8M0 scale a 32 x 32 tile): TMA brings each 128 x 128 tile of codes
+// (16 KB, 128B-swizzled) into its own ring, and warps 6-9 rewrite it as the BF16 tile the MMAs
+// read, code times 2^k (exact in BF16), in the same swizzled layout, before signalling the MMA
+// issuer; the HBM stream is half that of BF16 X. Partial
 // sums of Y (one per column group) and Z (one per row group) are added by the fixed-order slot
 // reduction of the SIMT path. Every mbarrier wait is bounded; on time-out the kernel latches
 // NMF_ERR_TIMEOUT, drains what it issued and frees its tensor memory.
 #include <cuda.h>
+#include <cuda_fp8.h>
 
 #include "common.cuh"
 
@@ -28,6 +33,9 @@ constexpr int kRows = 128;          // rows per block (MMA M for Y)
 constexpr int kCols = 128;          // columns per tile (MMA M for Z)
 constexpr int kHalfCols = 64;       // 128-byte swizzle atom: 64 BF16 columns
 constexpr int kThreads = 192;
+constexpr int kThreadsF8 = 320;     // + warps 6-9: FP8 -> BF16 converters
+constexpr int kF8Stages = 4;        // ring of FP8 tiles
+constexpr uint32_t kX8Stage = 128 * 128;   // one 128 x 128 E4M3 tile (16 KB)
 constexpr long long kWaitCycles = 4000000000LL;   // every mbarrier wait gives up after ~2 s
 
 // ------------------------------------------------------------------ PTX wrappers
@@ -181,7 +189,18 @@ struct TcArgs {
   float* Ypart;                   // [n_colgroups][ell][m]   (k-major: rows contiguous)
   float* Zpart;                   // [n_rowgroups][ell][n]
   int* status;
+  const uint8_t* S;               // FP8 X: E8M0 tile scales (row-major, tn a row)
+  int64_t tn;
 };
+
+// Two E4M3 codes (low byte = first element) times 2^k (exact) as a BF16 pair (low half first).
+__device__ __forceinline__ uint32_t e4m3x2_to_bf16x2(uint32_t pair, float sc) {
+  const __half2_raw h =
+      __nv_cvt_fp8x2_to_halfraw2(static_cast<__nv_fp8x2_storage_t>(pair & 0xFFFFu), __NV_E4M3);
+  const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&h));
+  const __nv_bfloat162 b = __floats2bfloat162_rn(f.x * sc, f.y * sc);
+  return *reinterpret_cast<const uint32_t*>(&b);
+}
 
 constexpr int kMaxStages = 4;
 constexpr uint32_t kXStage = 2 * kRows * kHalfCols * 2;   // 32 KB: two 128 x 64 BF16 halves
@@ -195,8 +214,8 @@ __host__ __device__ constexpr int nct_max(int LP) {
 
 // SPLIT = 2: V and U enter as hi + lo BF16 pairs (v = hi + lo to about 2^-16 relative), each
 // product is accumulated from both, so only X is rounded to BF16.
-template <int LP, int SPLIT>
-__global__ void __launch_bounds__(kThreads, 1) dual_pass_tc_kernel(
+template <int LP, int SPLIT, bool F8>
+__global__ void __launch_bounds__(F8 ? kThreadsF8 : kThreads, 1) dual_pass_tc_kernel(
     const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapV,
     const __grid_constant__ CUtensorMap mapU, TcArgs a) {
   constexpr int NCT = nct_max(LP);
@@ -216,11 +235,13 @@ __global__ void __launch_bounds__(kThreads, 1) dual_pass_tc_kernel(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   const int stages = a.stages;
   unsigned char* Xs = smem;                              // [stages][32 KB]
-  unsigned char* Us = Xs + stages * kXStage;             // [2][SPLIT][2 halves][kBBox]
+  unsigned char* X8 = Xs + stages * kXStage;             // [kF8Stages][16 KB] (F8 only)
+  unsigned char* Us = X8 + (F8 ? kF8Stages * kX8Stage : 0u);   // [2][SPLIT][2 halves][kBBox]
   unsigned char* Vs = Us + 2 * kBTile;                   // [nct][SPLIT][2 halves][kBBox]
   __shared__ __align__(8) uint64_t full_bar[kMaxStages], empty_bar[kMaxStages];
   __shared__ __align__(8) uint64_t u_full[2], u_empty[2], v_full;
   __shared__ __align__(8) uint64_t ydone_bar[2], yfree_bar[2], zdone_bar, drain_bar;
+  __shared__ __align__(8) uint64_t f8_full[kF8Stages], f8_empty[kF8Stages];
   __shared__ uint32_t tmem_base;
   __shared__ volatile int abort_f;
 
@@ -237,8 +258,12 @@ __global__ void __launch_bounds__(kThreads, 1) dual_pass_tc_kernel(
   if (threadIdx.x == 0) {
     abort_f = 0;
     for (int s = 0; s < kMaxStages; ++s) {
-      mbar_init(smem_u32(&full_bar[s]), 1);
+      mbar_init(smem_u32(&full_bar[s]), F8 ? 128 : 1);   // FP8: the 128 converter threads
       mbar_init(smem_u32(&empty_bar[s]), 1);
+    }
+    for (int s = 0; s < kF8Stages; ++s) {
+      mbar_init(smem_u32(&f8_full[s]), 1);
+      mbar_init(smem_u32(&f8_empty[s]), 128);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(smem_u32(&u_full[b]), 1);
@@ -283,18 +308,29 @@ __global__ void __launch_bounds__(kThreads, 1) dual_pass_tc_kernel(
         u_issued = lr + 1;
         for (int lc = 0; lc < nct; ++lc) {
           const int tI = lr * nct + lc;
-          const int s = tI % stages;
-          const uint32_t ph = (tI / stages) & 1;
-          if (!mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1, &abort_f)) {
-            ok = false;
-            break;
-          }
           const int col0 = static_cast<int>((ct0 + lc) * kCols);
-          unsigned char* st = Xs + s * kXStage;
-          const uint32_t fb = smem_u32(&full_bar[s]);
-          mbar_expect_tx(fb, kXStage);
-          tma_load_2d(smem_u32(st), &mapX, col0, row0, fb, pol_x);
-          tma_load_2d(smem_u32(st + kXHalf), &mapX, col0 + kHalfCols, row0, fb, pol_x);
+          if constexpr (F8) {
+            const int s8 = tI % kF8Stages;
+            if (!mbar_wait(smem_u32(&f8_empty[s8]), ((tI / kF8Stages) & 1) ^ 1, &abort_f)) {
+              ok = false;
+              break;
+            }
+            const uint32_t fb = smem_u32(&f8_full[s8]);
+            mbar_expect_tx(fb, kX8Stage);
+            tma_load_2d(smem_u32(X8 + s8 * kX8Stage), &mapX, col0, row0, fb, pol_x);
+          } else {
+            const int s = tI % stages;
+            const uint32_t ph = (tI / stages) & 1;
+            if (!mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1, &abort_f)) {
+              ok = false;
+              break;
+            }
+            unsigned char* st = Xs + s * kXStage;
+            const uint32_t fb = smem_u32(&full_bar[s]);
+            mbar_expect_tx(fb, kXStage);
+            tma_load_2d(smem_u32(st), &mapX, col0, row0, fb, pol_x);
+            tma_load_2d(smem_u32(st + kXHalf), &mapX, col0 + kHalfCols, row0, fb, pol_x);
+          }
           issued = tI + 1;
         }
       }
@@ -302,8 +338,9 @@ __global__ void __launch_bounds__(kThreads, 1) dual_pass_tc_kernel(
       mbar_drain(vb, 0);
       for (int lr = u_issued - 2 > 0 ? u_issued - 2 : 0; lr < u_issued; ++lr)
         mbar_drain(smem_u32(&u_full[lr & 1]), (lr >> 1) & 1);
-      for (int tI = issued - stages > 0 ? issued - stages : 0; tI < issued; ++tI)
-        mbar_drain(smem_u32(&full_bar[tI % stages]), (tI / stages) & 1);
+      const int ring = F8 ? kF8Stages : stages;
+      for (int tI = issued - ring > 0 ? issued - ring : 0; tI < issued; ++tI)
+        mbar_drain(smem_u32(F8 ? &f8_full[tI % ring] : &full_bar[tI % ring]), (tI / ring) & 1);
     }
   } else if (warp == 5) {
     // ---------------- MMA issuer
@@ -359,6 +396,53 @@ __global__ void __launch_bounds__(kThreads, 1) dual_pass_tc_kernel(
       // drain: all MMAs issued by this thread complete before tensor memory is freed
       mma_commit(smem_u32(&drain_bar));
       mbar_drain(smem_u32(&drain_bar), 0);
+    }
+  } else if (warp >= 6) {
+    // ---------------- FP8 converters (warps 6-9): thread ct rewrites row ct of each tile
+    if constexpr (F8) {
+      const int ct = threadIdx.x - 192, sw = ct & 7;
+      bool ok = true;
+      for (int lr = 0; lr < nrb && ok; ++lr) {
+        const int64_t row = (rb0 + lr) * kRows + ct;
+        for (int lc = 0; lc < nct; ++lc) {
+          const int tI = lr * nct + lc;
+          const int s8 = tI % kF8Stages, s = tI % stages;
+          if (!mbar_wait(smem_u32(&f8_full[s8]), (tI / kF8Stages) & 1, &abort_f) ||
+              !mbar_wait(smem_u32(&empty_bar[s]), ((tI / stages) & 1) ^ 1, &abort_f)) {
+            ok = false;
+            break;
+          }
+          const int64_t col0 = (ct0 + lc) * kCols;
+          const unsigned char* src = X8 + s8 * kX8Stage + ct * 128;
+          unsigned char* dst = Xs + s * kXStage + ct * 128;
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            // codes of columns col0 + 16 c .. + 15 (chunk c of the row, swizzled)
+            const uint4 w = *reinterpret_cast<const uint4*>(src + ((c ^ sw) << 4));
+            const int64_t col = col0 + 16 * c;
+            int k = 0;   // rows / columns past the matrix hold zero codes (TMA fill)
+            if (row < a.m && col < a.n) k = static_cast<int>(a.S[(row >> 5) * a.tn + (col >> 5)]) - 127;
+            const float sc = ldexpf(1.f, k);
+            const uint32_t wv[4] = {w.x, w.y, w.z, w.w};
+            uint32_t o[8];
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+              o[2 * h] = e4m3x2_to_bf16x2(wv[h], sc);
+              o[2 * h + 1] = e4m3x2_to_bf16x2(wv[h] >> 16, sc);
+            }
+            // BF16 columns 16 c .. 16 c + 15: half c / 4, 16-byte chunks 2 (c % 4) and + 1
+            unsigned char* hb = dst + (c >> 2) * kXHalf;
+            const int j0 = (c & 3) * 2;
+            *reinterpret_cast<uint4*>(hb + ((j0 ^ sw) << 4)) = make_uint4(o[0], o[1], o[2], o[3]);
+            *reinterpret_cast<uint4*>(hb + (((j0 + 1) ^ sw) << 4)) =
+                make_uint4(o[4], o[5], o[6], o[7]);
+          }
+          // the MMAs read the tile through the async proxy
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          mbar_arrive(smem_u32(&full_bar[s]));
+          mbar_arrive(smem_u32(&f8_empty[s8]));
+        }
+      }
     }
   } else {
     // ---------------- epilogue: warps 0-3, TMEM lanes 32 warp .. 32 warp + 31
@@ -504,6 +588,21 @@ bool make_map(CUtensorMap* map, const void* base, uint64_t inner, uint64_t outer
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// 2-D map of E4M3 codes: `inner` columns (row pitch `pitch` bytes, a multiple of 16), `outer`
+// rows, box 128 x 128 (128-byte rows: the 128B swizzle atom); reads past the edges give zero.
+bool make_map8(CUtensorMap* map, const void* base, uint64_t inner, uint64_t outer, uint64_t pitch) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {inner, outer};
+  const cuuint64_t strides[1] = {pitch};
+  const cuuint32_t box[2] = {128, 128};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void*>(base), dims, strides, box,
+            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 int num_sms() {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -520,19 +619,20 @@ struct Plan {
   int64_t rowblocks, coltiles;
 };
 
-size_t smem_bytes(int LP, int split, int stages, int nct) {
+size_t smem_bytes(int LP, int split, int stages, int nct, bool f8 = false) {
   const size_t btile = static_cast<size_t>(split) * 2 * LP * kHalfCols * 2;
-  return static_cast<size_t>(stages) * kXStage + 2 * btile + static_cast<size_t>(nct) * btile + 1024;
+  return static_cast<size_t>(stages) * kXStage + (f8 ? kF8Stages * kX8Stage : 0) + 2 * btile +
+         static_cast<size_t>(nct) * btile + 1024;
 }
 
 // Deepest X pipeline that still keeps enough resident column tiles (4 stages with
 // min(4, NCT) tiles, else 3 stages with min(2, NCT), else 2 stages with one), then as many
 // resident column tiles as fit. nct = 0 means the configuration does not fit.
-void pick_stages(int LP, int split, int* stages, int* nct) {
+void pick_stages(int LP, int split, int* stages, int* nct, bool f8 = false) {
   const int cap = nct_max(LP);
   for (int s = kMaxStages; s >= 2; --s) {
     int k = cap;
-    while (k > 0 && smem_bytes(LP, split, s, k) > static_cast<size_t>(kSmemCap)) --k;
+    while (k > 0 && smem_bytes(LP, split, s, k, f8) > static_cast<size_t>(kSmemCap)) --k;
     const int want = s == 4 ? (cap < 4 ? cap : 4) : s == 3 ? (cap < 2 ? cap : 2) : 1;
     if (k >= want && k > 0) {
       *stages = s;
@@ -544,12 +644,12 @@ void pick_stages(int LP, int split, int* stages, int* nct) {
   *nct = 0;
 }
 
-Plan plan_for(int64_t m, int64_t n, int ell, int split) {
+Plan plan_for(int64_t m, int64_t n, int ell, int split, bool f8 = false) {
   Plan p;
   p.LP = lp16(ell);
   p.split = split;
-  pick_stages(p.LP, split, &p.stages, &p.nct);
-  p.smem = smem_bytes(p.LP, split, p.stages, p.nct > 0 ? p.nct : 1);
+  pick_stages(p.LP, split, &p.stages, &p.nct, f8);
+  p.smem = smem_bytes(p.LP, split, p.stages, p.nct > 0 ? p.nct : 1, f8);
   p.rowblocks = cdiv(m, kRows);
   p.coltiles = cdiv(n, kCols);
   const int nct = p.nct > 0 ? p.nct : 1;
@@ -562,32 +662,32 @@ Plan plan_for(int64_t m, int64_t n, int ell, int split) {
   return p;
 }
 
-template <int LP, int SPLIT>
+template <int LP, int SPLIT, bool F8>
 cudaError_t launch_t(const Launcher& L, const CUtensorMap& mx, const CUtensorMap& mv,
                      const CUtensorMap& mu, const TcArgs& a, size_t smem) {
-  auto k = dual_pass_tc_kernel<LP, SPLIT>;
+  auto k = dual_pass_tc_kernel<LP, SPLIT, F8>;
   if (smem < 120 * 1024) smem = 120 * 1024;   // one CTA per SM: it owns the tensor memory
   cudaError_t err =
       cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (err != cudaSuccess) return err;
   dim3 grid(a.n_colgroups, a.n_rowgroups);
-  k<<<grid, kThreads, smem, L.stream>>>(mx, mv, mu, a);
+  k<<<grid, F8 ? kThreadsF8 : kThreads, smem, L.stream>>>(mx, mv, mu, a);
   L.count();
   return cudaGetLastError();
 }
 
-template <int SPLIT>
+template <int SPLIT, bool F8>
 cudaError_t launch_lp(int LP, const Launcher& L, const CUtensorMap& mx, const CUtensorMap& mv,
                       const CUtensorMap& mu, const TcArgs& a, size_t smem) {
   switch (LP) {
-    case 16: return launch_t<16, SPLIT>(L, mx, mv, mu, a, smem);
-    case 32: return launch_t<32, SPLIT>(L, mx, mv, mu, a, smem);
-    case 48: return launch_t<48, SPLIT>(L, mx, mv, mu, a, smem);
-    case 64: return launch_t<64, SPLIT>(L, mx, mv, mu, a, smem);
-    case 80: return launch_t<80, SPLIT>(L, mx, mv, mu, a, smem);
-    case 96: return launch_t<96, SPLIT>(L, mx, mv, mu, a, smem);
-    case 112: return launch_t<112, SPLIT>(L, mx, mv, mu, a, smem);
-    case 128: return launch_t<128, SPLIT>(L, mx, mv, mu, a, smem);
+    case 16: return launch_t<16, SPLIT, F8>(L, mx, mv, mu, a, smem);
+    case 32: return launch_t<32, SPLIT, F8>(L, mx, mv, mu, a, smem);
+    case 48: return launch_t<48, SPLIT, F8>(L, mx, mv, mu, a, smem);
+    case 64: return launch_t<64, SPLIT, F8>(L, mx, mv, mu, a, smem);
+    case 80: return launch_t<80, SPLIT, F8>(L, mx, mv, mu, a, smem);
+    case 96: return launch_t<96, SPLIT, F8>(L, mx, mv, mu, a, smem);
+    case 112: return launch_t<112, SPLIT, F8>(L, mx, mv, mu, a, smem);
+    case 128: return launch_t<128, SPLIT, F8>(L, mx, mv, mu, a, smem);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -608,10 +708,11 @@ bool dual_pass_tc_split_supported(int ell) {
 }
 
 size_t dual_pass_tc_ws_bytes(int64_t m, int64_t n, int ell) {
-  // the larger of the two layouts (plain and split operands)
+  // the largest of the layouts (plain and split operands, BF16 and FP8 X)
   size_t best = 0;
-  for (int split = 1; split <= 2; ++split) {
-    const Plan p = plan_for(m, n, ell, split);
+  for (int v = 0; v < 3; ++v) {
+    const int split = v == 1 ? 2 : 1;
+    const Plan p = plan_for(m, n, ell, split, v == 2);
     const int64_t ldv = (n + 7) / 8 * 8, ldu = (m + 7) / 8 * 8;
     const size_t b =
         sizeof(float) * static_cast<size_t>(p.colgroups * m * ell + p.rowgroups * n * ell) +
@@ -621,12 +722,14 @@ size_t dual_pass_tc_ws_bytes(int64_t m, int64_t n, int ell) {
   return best;
 }
 
-cudaError_t launch_dual_pass_tc(const Launcher& L, const __nv_bfloat16* X, int64_t m, int64_t n,
-                                int64_t ldx, int ell, const float* V, const float* U, float* Y,
-                                float* Z, void* ws, size_t ws_bytes, int* status, bool split) {
-  if (ws_bytes < dual_pass_tc_ws_bytes(m, n, ell)) return cudaErrorInvalidValue;
-  const int sp = (split && dual_pass_tc_split_supported(ell)) ? 2 : 1;
-  const Plan p = plan_for(m, n, ell, sp);
+namespace {
+
+// Operand preparation, the kernel and the slot sums for one dual pass; mx maps X (BF16 halves of
+// 128 x 64, or FP8 tiles of 128 x 128), S / tn the FP8 tile scales.
+cudaError_t run_tc(const Launcher& L, const CUtensorMap& mx, bool f8, const uint8_t* S, int64_t tn,
+                   int64_t m, int64_t n, int ell, const float* V, const float* U, float* Y,
+                   float* Z, void* ws, int* status, int sp) {
+  const Plan p = plan_for(m, n, ell, sp, f8);
   if (p.nct < 1) return cudaErrorInvalidValue;
   const int64_t ldv = (n + 7) / 8 * 8, ldu = (m + 7) / 8 * 8;
   char* w = static_cast<char*>(ws);
@@ -645,10 +748,8 @@ cudaError_t launch_dual_pass_tc(const Launcher& L, const __nv_bfloat16* X, int64
     transpose_bf16_kernel<<<gu, dim3(32, 8), 0, L.stream>>>(U, m, ell, p.LP, sp, ldu, Ut);
     L.count(2);
   }
-  CUtensorMap mx, mv, mu;
-  if (!make_map(&mx, X, static_cast<uint64_t>(n), static_cast<uint64_t>(m),
-                static_cast<uint64_t>(ldx), kHalfCols, kRows) ||
-      !make_map(&mv, Vt, static_cast<uint64_t>(ldv), static_cast<uint64_t>(sp * p.LP),
+  CUtensorMap mv, mu;
+  if (!make_map(&mv, Vt, static_cast<uint64_t>(ldv), static_cast<uint64_t>(sp * p.LP),
                 static_cast<uint64_t>(ldv), kHalfCols, static_cast<uint32_t>(p.LP)) ||
       !make_map(&mu, Ut, static_cast<uint64_t>(ldu), static_cast<uint64_t>(sp * p.LP),
                 static_cast<uint64_t>(ldu), kHalfCols, static_cast<uint32_t>(p.LP)))
@@ -666,9 +767,12 @@ cudaError_t launch_dual_pass_tc(const Launcher& L, const __nv_bfloat16* X, int64
   a.Ypart = Ypart;
   a.Zpart = Zpart;
   a.status = status;
-  const size_t smem = smem_bytes(p.LP, sp, p.stages, p.tiles_per_group);
-  cudaError_t err = sp == 2 ? launch_lp<2>(p.LP, L, mx, mv, mu, a, smem)
-                            : launch_lp<1>(p.LP, L, mx, mv, mu, a, smem);
+  a.S = S;
+  a.tn = tn;
+  const size_t smem = smem_bytes(p.LP, sp, p.stages, p.tiles_per_group, f8);
+  cudaError_t err = f8 ? launch_lp<1, true>(p.LP, L, mx, mv, mu, a, smem)
+                    : sp == 2 ? launch_lp<2, false>(p.LP, L, mx, mv, mu, a, smem)
+                              : launch_lp<1, false>(p.LP, L, mx, mv, mu, a, smem);
   if (err != cudaSuccess) return err;
   const unsigned kg = static_cast<unsigned>(cdiv(ell, 8));
   reduce_slots_t_kernel<<<dim3(static_cast<unsigned>(cdiv(m, 32)), kg), 256, 0, L.stream>>>(
@@ -677,6 +781,42 @@ cudaError_t launch_dual_pass_tc(const Launcher& L, const __nv_bfloat16* X, int64
       Zpart, p.rowgroups, n, ell, Z);
   L.count(2);
   return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_dual_pass_tc(const Launcher& L, const __nv_bfloat16* X, int64_t m, int64_t n,
+                                int64_t ldx, int ell, const float* V, const float* U, float* Y,
+                                float* Z, void* ws, size_t ws_bytes, int* status, bool split) {
+  if (ws_bytes < dual_pass_tc_ws_bytes(m, n, ell)) return cudaErrorInvalidValue;
+  const int sp = (split && dual_pass_tc_split_supported(ell)) ? 2 : 1;
+  CUtensorMap mx;
+  if (!make_map(&mx, X, static_cast<uint64_t>(n), static_cast<uint64_t>(m),
+                static_cast<uint64_t>(ldx), kHalfCols, kRows))
+    return cudaErrorInvalidValue;
+  return run_tc(L, mx, false, nullptr, 0, m, n, ell, V, U, Y, Z, ws, status, sp);
+}
+
+bool dual_pass_tc_fp8_supported(int64_t m, int64_t n, int ell, const void* Xq) {
+  if (ell < 1 || ell > 128 || (reinterpret_cast<uintptr_t>(Xq) & 15) != 0) return false;
+  if (m < kRows || n < kCols) return false;   // the 128 x 128 box stays within the tensor
+  if (m > (int64_t(1) << 31) - kRows || n > (int64_t(1) << 31) - kCols) return false;
+  int s = 0, k = 0;
+  pick_stages(lp16(ell), 1, &s, &k, true);
+  return k > 0 && encode_fn() != nullptr;
+}
+
+cudaError_t launch_dual_pass_tc_fp8(const Launcher& L, const uint8_t* Xq, int64_t m, int64_t n,
+                                    int ell, const float* V, const float* U, float* Y, float* Z,
+                                    void* ws, size_t ws_bytes, int* status) {
+  if (ws_bytes < dual_pass_tc_ws_bytes(m, n, ell)) return cudaErrorInvalidValue;
+  int64_t ldq = 0, off = 0;
+  fp8_copy_bytes(m, n, &ldq, &off);
+  CUtensorMap mx;
+  if (!make_map8(&mx, Xq, static_cast<uint64_t>(n), static_cast<uint64_t>(m),
+                 static_cast<uint64_t>(ldq)))
+    return cudaErrorInvalidValue;
+  return run_tc(L, mx, true, Xq + off, (n + 31) / 32, m, n, ell, V, U, Y, Z, ws, status, 1);
 }
 
 }  // namespace nmfrp

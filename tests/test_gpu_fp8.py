@@ -2,11 +2,14 @@
 
 The quantization is integer work decided in FP32 on both sides (the scale exponent from frexp of
 the tile maximum, the code by round-to-nearest-even of an exact power-of-two scaling), so the
-codes, the pad bytes and the scale bytes are compared bit for bit with the oracle. The dual pass,
-sketch and compression on the FP8 copy are compared with the FP64 oracle applied to the
-dequantised values (the only difference is the library's FP32 arithmetic: 1e-5 relative). The
-solve with an FP8 sketch compresses from the FP32 X and must end within 1 % of the oracle's error
-on X after the same iterations.
+codes, the pad bytes and the scale bytes are compared bit for bit with the oracle. The dual pass
+on the FP8 copy is compared with the FP64 oracle applied to the dequantised values: exactly
+(1e-5, the library's FP32 accumulation) once the basis operands are rounded to BF16 as the
+tensor-core pass rounds them (RNE, relative error <= 2^-9; the SIMT pass keeps them in FP32).
+The sketch and compression through the SIMT pass match the oracle on the dequantised copy to
+1e-4; through the tensor cores, whose bases are BF16, to the 2e-2 of the BF16 sketch. The solve
+with an FP8 sketch compresses from the FP32 X and must end within 1 % of the oracle taking the
+same steps.
 """
 import numpy as np
 import pytest
@@ -42,6 +45,13 @@ def split_copy(q, m, n):
     rows = buf[:m * ldq].reshape(m, ldq)
     tm, tn = -(-m // 32), -(-n // 32)
     return rows[:, :n], rows[:, n:], buf[off:off + tm * tn].reshape(tm, tn)
+
+
+def bf16(a):
+    """Round to the nearest BF16 (ties to even), as the tensor-core pass rounds V and U."""
+    u = np.ascontiguousarray(a, np.float32).view(np.uint32).astype(np.uint64)
+    u = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
 def varied_matrix(seed, m, n):
@@ -100,28 +110,87 @@ def test_fp8_dual_pass_matches_the_dequantised_oracle(lib, ctx):
     V = rng.standard_normal((n, ell)).astype(np.float32)
     U = rng.standard_normal((m, ell)).astype(np.float32)
     q = lib.nmf_quantize(ctx, cu(X), prec="fp8")
+    Y, Z = lib.nmf_dual_pass(ctx, q, cu(V), cu(U), prec="fp8")   # tensor cores (m, n >= 128)
+    codes, _, scales = split_copy(q, m, n)
+    Xq = O.fp8_dequantize(codes, scales.astype(np.int64) - 127)
+    assert rel(Y.cpu().numpy(), Xq @ bf16(V)) <= 1e-5
+    assert rel(Z.cpu().numpy(), Xq.T @ bf16(U)) <= 1e-5
+    # small enough for the SIMT pass only (fewer than 128 columns): FP32 bases
+    Xs = X[:, :100]
+    q2 = lib.nmf_quantize(ctx, cu(Xs), prec="fp8")
+    Y2, Z2 = lib.nmf_dual_pass(ctx, q2, cu(V[:100]), cu(U), prec="fp8")
+    codes2, _, scales2 = split_copy(q2, m, 100)
+    Xq2 = O.fp8_dequantize(codes2, scales2.astype(np.int64) - 127)
+    assert rel(Y2.cpu().numpy(), Xq2 @ V[:100]) <= 1e-5
+    assert rel(Z2.cpu().numpy(), Xq2.T @ U) <= 1e-5
+
+
+@pytest.mark.parametrize("m,n,ell", [(1000, 3001, 40), (4096, 700, 70), (256, 128, 16)])
+def test_fp8_tensor_core_pass_matches_simt_and_oracle(lib, ctx, m, n, ell):
+    """The tensor-core pass (codes converted to BF16 in shared memory, exact) against the SIMT
+    pass on the same copy (the sketch with the SIMT flag) and against the FP64 oracle applied
+    to the dequantised values."""
+    rng = np.random.default_rng(m + n)
+    X = (rng.exponential(1.0, (m, n)) * np.exp(rng.uniform(-3, 3, (m, 1)))).astype(np.float32)
+    V = rng.standard_normal((n, ell)).astype(np.float32)
+    U = rng.standard_normal((m, ell)).astype(np.float32)
+    q = lib.nmf_quantize(ctx, cu(X), prec="fp8")
     Y, Z = lib.nmf_dual_pass(ctx, q, cu(V), cu(U), prec="fp8")
     codes, _, scales = split_copy(q, m, n)
     Xq = O.fp8_dequantize(codes, scales.astype(np.int64) - 127)
-    assert rel(Y.cpu().numpy(), Xq @ V) <= 1e-5
-    assert rel(Z.cpu().numpy(), Xq.T @ U) <= 1e-5
+    assert rel(Y.cpu().numpy(), Xq @ bf16(V)) <= 1e-5
+    assert rel(Z.cpu().numpy(), Xq.T @ bf16(U)) <= 1e-5
+    pr = inputs.random_problem(9, m, n, min(10, ell - 4), ell, w=1)
+    q2 = lib.nmf_quantize(ctx, cu(pr.X), prec="fp8")
+    out = []
+    for flags in (0, lib.FLAG_SIMT_DUAL_PASS):
+        p = lib.params(m, n, pr.r, ell, power_iters=1, prec="fp8", flags=flags)
+        QL, QR = lib.nmf_sketch(ctx, p, q2, cu(pr.omega_L), cu(pr.omega_R))
+        out.append((QL.double().cpu().numpy(), QR.double().cpu().numpy()))
+    (a, b), (c, d) = out     # BF16 bases on the tensor cores, FP32 on the SIMT pass
+    assert rel(a @ a.T, c @ c.T) <= 2e-2 and rel(b @ b.T, d @ d.T) <= 2e-2
+
+
+def test_fp8_tensor_core_pass_full_size_sampled(lib, ctx):
+    """The dense 20000 x 5000 workload at its sketch width: Y = X_q V on 300 sampled rows and
+    Z = X_q^T U on 300 sampled columns against the dequantised oracle."""
+    pr = inputs.dense_20k_5k(seed=4)
+    X = pr.X
+    m, n = X.shape
+    ell = 40
+    rng = np.random.default_rng(5)
+    V = rng.standard_normal((n, ell)).astype(np.float32)
+    U = rng.standard_normal((m, ell)).astype(np.float32)
+    q = lib.nmf_quantize(ctx, cu(X), prec="fp8")
+    Y, Z = lib.nmf_dual_pass(ctx, q, cu(V), cu(U), prec="fp8")
+    codes, _, scales = split_copy(q, m, n)
+    k = scales.astype(np.int64) - 127
+    rows = rng.choice(m, 300, replace=False)
+    cols = rng.choice(n, 300, replace=False)
+    kr = np.repeat(k, 32, axis=1)[:, :n]                 # tile exponent of every column
+    Xr = O.e4m3_decode(codes[rows]) * 2.0 ** kr[rows // 32]
+    assert rel(Y.cpu().numpy()[rows], Xr @ bf16(V)) <= 1e-5
+    kc = np.repeat(k, 32, axis=0)[:m]                    # tile exponent of every row
+    Xc = O.e4m3_decode(codes[:, cols]) * 2.0 ** kc[:, cols // 32]
+    assert rel(Z.cpu().numpy()[cols], Xc.T @ bf16(U)) <= 1e-5
 
 
 def test_fp8_sketch_and_compression_match_the_dequantised_oracle(lib, ctx):
     pr = inputs.random_problem(21, 1200, 900, 10, 20, w=2)
     m, n = pr.X.shape
-    p = lib.params(m, n, pr.r, pr.ell, power_iters=2, prec="fp8")
     q = lib.nmf_quantize(ctx, cu(pr.X), prec="fp8")
-    QL, QR = lib.nmf_sketch(ctx, p, q, cu(pr.omega_L), cu(pr.omega_R))
-    Xhat, Xchk = lib.nmf_compress(ctx, p, q, QL, QR)
     codes, _, scales = split_copy(q, m, n)
     Xq = O.fp8_dequantize(codes, scales.astype(np.int64) - 127)
     QLo, QRo = O.sketch(Xq, pr.omega_L, pr.omega_R, 2)
     Xho, Xco = O.compress(Xq, QLo, QRo)
-    # basis-free forms: Q_L X_hat = Q_L Q_L^T X_q and X_chk Q_R^T = X_q Q_R Q_R^T
-    QLh, QRh = QL.double().cpu().numpy(), QR.double().cpu().numpy()
-    assert rel(QLh @ Xhat.double().cpu().numpy(), QLo @ Xho) <= 1e-4
-    assert rel(Xchk.double().cpu().numpy() @ QRh.T, Xco @ QRo.T) <= 1e-4
+    for flags, tol in ((lib.FLAG_SIMT_DUAL_PASS, 1e-4), (0, 2e-2)):
+        p = lib.params(m, n, pr.r, pr.ell, power_iters=2, prec="fp8", flags=flags)
+        QL, QR = lib.nmf_sketch(ctx, p, q, cu(pr.omega_L), cu(pr.omega_R))
+        Xhat, Xchk = lib.nmf_compress(ctx, p, q, QL, QR)
+        # basis-free forms: Q_L X_hat = Q_L Q_L^T X_q and X_chk Q_R^T = X_q Q_R Q_R^T
+        QLh, QRh = QL.double().cpu().numpy(), QR.double().cpu().numpy()
+        assert rel(QLh @ Xhat.double().cpu().numpy(), QLo @ Xho) <= tol
+        assert rel(Xchk.double().cpu().numpy() @ QRh.T, Xco @ QRo.T) <= tol
 
 
 def test_fp8_solve_ends_within_one_percent_of_the_oracle(lib, ctx):
