@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", choices=["fp32", "bf16"], default=None,
                     help="run one short solve (20 iterations) for a profiler's launch list")
-    ap.add_argument("--config", choices=["dense", "batched", "images", "warmstart"],
+    ap.add_argument("--config", choices=["dense", "batched", "images", "warmstart", "passes"],
                     default="dense",
                     help="batched: 256 uneven problems through nmf_solve_batched against one "
                          "nmf_solve per problem; images: 4096 x 100000 image-like data, r = 50, "
@@ -321,6 +321,69 @@ def run_images(args):
     ctx.close()
 
 
+def run_passes(args):
+    """One fused dual pass over X (Y = X V and Z = X^T U) per element type of X: FP32 (SIMT),
+    BF16 and FP8 E4M3 with per-tile scales (tensor cores), at the dense workload's shape
+    (20000 x 5000, l = 40) and the image workload's (4096 x 100000, l = 70). X is uniform
+    [0, 1) (a bandwidth measurement: the values do not change the work); time per pass with
+    CUDA events on the library's stream, median of --steps passes after --warmup."""
+    import torch
+    from paper_1712_02248_gb300 import nmf_rp as N
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    ctx = N.Context(0)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(args.seed)
+    out = {}
+    for name, m, n, ell in (("dense 20000x5000 l=40", 20000, 5000, 40),
+                            ("images 4096x100000 l=70", 4096, 100000, 70)):
+        X = torch.rand((m, n), device=dev, generator=gen)
+        V = torch.randn((n, ell), device=dev, generator=gen)
+        U = torch.randn((m, ell), device=dev, generator=gen)
+        Y = torch.empty((m, ell), device=dev)
+        Z = torch.empty((n, ell), device=dev)
+        copies = {"fp32": X, "bf16": N.nmf_quantize(ctx, X, prec="bf16"),
+                  "fp8": N.nmf_quantize(ctx, X, prec="fp8")}
+        xbytes = {"fp32": 4 * m * n, "bf16": 2 * m * n,
+                  "fp8": N.nmf_quantized_bytes("fp8", m, n)}
+        row = {}
+        for prec, Xp in copies.items():
+            for _ in range(args.warmup):
+                N.nmf_dual_pass(ctx, Xp, V, U, prec=prec, Y=Y, Z=Z)
+            ts = []
+            for _ in range(args.steps):
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(ctx.stream)
+                N.nmf_dual_pass(ctx, Xp, V, U, prec=prec, Y=Y, Z=Z)
+                b.record(ctx.stream)
+                b.synchronize()
+                ts.append(a.elapsed_time(b) / 1e3)
+            t = statistics.median(ts)
+            algo = xbytes[prec] + 8 * ell * (m + n)     # X once, V and U read, Y and Z written
+            row[prec] = {"ms": t * 1e3, "algorithmic_bytes": algo,
+                         "achieved_gbs": algo / t / 1e9, "frac_hbm": algo / t / 1e9 / hbm}
+        out[name] = row
+        del X, copies
+        torch.cuda.empty_cache()
+    print(json.dumps({
+        "metric": "fused dual pass over X (sketch / compression pass) by element type of X",
+        "value": out["images 4096x100000 l=70"]["fp8"]["ms"] / 1e3, "unit": "s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": False,
+        "dtype": "fp8", "data": "synthetic (uniform X)",
+        "config": {"workload": "one dual pass (Y = X V, Z = X^T U) at the dense and image shapes",
+                   "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback",
+                   "hbm_peak_gbs": hbm},
+        "passes": out}))
+    ctx.close()
+
+
 def run_warmstart(args):
     """Learned warm start on planted 8192 x 2048 matrices (r = 16, l = 32, 2 % noise, Exp(1)
     factors): train on --train-count matrices, then on --heldout others report iterations and
@@ -388,7 +451,8 @@ def main():
         return
     if args.config != "dense":
         if int(os.environ.get("RANK", 0)) == 0:
-            {"batched": run_batched, "images": run_images, "warmstart": run_warmstart}[args.config](args)
+            {"batched": run_batched, "images": run_images, "warmstart": run_warmstart,
+             "passes": run_passes}[args.config](args)
         return
     import torch
     rank, local_rank, world = dist_env()
@@ -466,9 +530,10 @@ def main():
                  "target_var_h": winfo["target_var_h"]}
 
     # contenders; the headline is the faster of the two warm starts (NNDSVD, learned)
-    contenders = [("fp32", "given"), ("bf16", "given"), ("bf16", "nndsvd"), ("bf16", "mlp")]
+    contenders = [("fp32", "given"), ("bf16", "given"), ("bf16", "nndsvd"), ("bf16", "mlp"),
+                  ("fp8", "mlp")]
     pre = {}
-    for prec, init in contenders[2:]:
+    for prec, init in contenders[2:4]:
         solve(prec, init, target)
         t0 = time.perf_counter()
         solve(prec, init, target)

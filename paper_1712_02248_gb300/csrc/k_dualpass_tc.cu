@@ -15,7 +15,7 @@
 // Warp roles (192 threads): warps 0-3 drain TMEM (each its 32-lane sub-partition) and write the
 // partial sums, warp 4 issues the TMA loads, warp 5 allocates TMEM and issues the MMAs.
 // FP8 X (E4M3 codes, one E8M0 scale a 32 x 32 tile): TMA brings each 128 x 128 tile of codes
-// (16 KB, 128B-swizzled) into its own ring, and warps 6-9 rewrite it as the BF16 tile the MMAs
+// (16 KB, 128B-swizzled) into its own ring, and warps 6-13 rewrite it as the BF16 tile the MMAs
 // read, code times 2^k (exact in BF16), in the same swizzled layout, before signalling the MMA
 // issuer; the HBM stream is half that of BF16 X. Partial
 // sums of Y (one per column group) and Z (one per row group) are added by the fixed-order slot
@@ -33,7 +33,8 @@ constexpr int kRows = 128;          // rows per block (MMA M for Y)
 constexpr int kCols = 128;          // columns per tile (MMA M for Z)
 constexpr int kHalfCols = 64;       // 128-byte swizzle atom: 64 BF16 columns
 constexpr int kThreads = 192;
-constexpr int kThreadsF8 = 320;     // + warps 6-9: FP8 -> BF16 converters
+constexpr int kThreadsF8 = 448;     // + warps 6-13: FP8 -> BF16 converters (two a row)
+constexpr int kConv = kThreadsF8 - kThreads;
 constexpr int kF8Stages = 4;        // ring of FP8 tiles
 constexpr uint32_t kX8Stage = 128 * 128;   // one 128 x 128 E4M3 tile (16 KB)
 constexpr long long kWaitCycles = 4000000000LL;   // every mbarrier wait gives up after ~2 s
@@ -258,12 +259,12 @@ __global__ void __launch_bounds__(F8 ? kThreadsF8 : kThreads, 1) dual_pass_tc_ke
   if (threadIdx.x == 0) {
     abort_f = 0;
     for (int s = 0; s < kMaxStages; ++s) {
-      mbar_init(smem_u32(&full_bar[s]), F8 ? 128 : 1);   // FP8: the 128 converter threads
+      mbar_init(smem_u32(&full_bar[s]), F8 ? kConv : 1);   // FP8: the converter threads
       mbar_init(smem_u32(&empty_bar[s]), 1);
     }
     for (int s = 0; s < kF8Stages; ++s) {
       mbar_init(smem_u32(&f8_full[s]), 1);
-      mbar_init(smem_u32(&f8_empty[s]), 128);
+      mbar_init(smem_u32(&f8_empty[s]), kConv);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(smem_u32(&u_full[b]), 1);
@@ -398,9 +399,10 @@ __global__ void __launch_bounds__(F8 ? kThreadsF8 : kThreads, 1) dual_pass_tc_ke
       mbar_drain(smem_u32(&drain_bar), 0);
     }
   } else if (warp >= 6) {
-    // ---------------- FP8 converters (warps 6-9): thread ct rewrites row ct of each tile
+    // ---------------- FP8 converters (warps 6-13): thread t rewrites half `part` of row ct
     if constexpr (F8) {
-      const int ct = threadIdx.x - 192, sw = ct & 7;
+      const int ct = (threadIdx.x - kThreads) & 127, part = (threadIdx.x - kThreads) >> 7;
+      const int sw = ct & 7;
       bool ok = true;
       for (int lr = 0; lr < nrb && ok; ++lr) {
         const int64_t row = (rb0 + lr) * kRows + ct;
@@ -415,14 +417,18 @@ __global__ void __launch_bounds__(F8 ? kThreadsF8 : kThreads, 1) dual_pass_tc_ke
           const int64_t col0 = (ct0 + lc) * kCols;
           const unsigned char* src = X8 + s8 * kX8Stage + ct * 128;
           unsigned char* dst = Xs + s * kXStage + ct * 128;
+          // scale bytes of this row's tiles from column col0 on (rows / columns past the
+          // matrix hold zero codes from the TMA fill: any scale serves)
+          const bool rin = row < a.m;
+          const uint8_t* srow = a.S + (rin ? (row >> 5) * a.tn : 0) + (col0 >> 5);
 #pragma unroll
-          for (int c = 0; c < 8; ++c) {
+          for (int cc = 0; cc < 4; ++cc) {
+            const int c = 4 * part + cc;
             // codes of columns col0 + 16 c .. + 15 (chunk c of the row, swizzled)
             const uint4 w = *reinterpret_cast<const uint4*>(src + ((c ^ sw) << 4));
-            const int64_t col = col0 + 16 * c;
-            int k = 0;   // rows / columns past the matrix hold zero codes (TMA fill)
-            if (row < a.m && col < a.n) k = static_cast<int>(a.S[(row >> 5) * a.tn + (col >> 5)]) - 127;
-            const float sc = ldexpf(1.f, k);
+            // the E8M0 byte is the biased exponent of 2^k (byte 0: 2^-127, a subnormal)
+            const uint32_t eb = (rin && col0 + 16 * c < a.n) ? srow[c >> 1] : 127u;
+            const float sc = eb ? __uint_as_float(eb << 23) : __uint_as_float(0x00400000u);
             const uint32_t wv[4] = {w.x, w.y, w.z, w.w};
             uint32_t o[8];
 #pragma unroll
