@@ -69,8 +69,13 @@ enum {
      launch for all iterations (same arithmetic; for comparison and for r > 48, which always
      uses the per-stage kernels) */
   NMF_FLAG_STAGED_ITERATE = 1,
-  /* run BF16 passes over X on the SIMT pipes instead of the tcgen05 tensor-core kernel */
-  NMF_FLAG_SIMT_DUAL_PASS = 2
+  /* run BF16 / FP8 passes over X on the SIMT pipes instead of the tcgen05 tensor-core kernel */
+  NMF_FLAG_SIMT_DUAL_PASS = 2,
+  /* nmf_sketch: orthonormalise rank-deficient pass outputs by replacing the columns whose
+     Cholesky pivot falls below 1e-12 of their diagonal with Gaussian draws (seeded by p->seed)
+     and repeating CholeskyQR2, instead of latching NMF_ERR_QR_BREAKDOWN; synchronises after
+     every QR. nmf_solve does this by itself when a first run meets a breakdown. */
+  NMF_FLAG_ROBUST_QR = 4
 };
 
 typedef struct {

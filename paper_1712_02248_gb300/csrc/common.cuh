@@ -117,10 +117,15 @@ size_t qr_ws_bytes(int64_t rows, int ell);
 cudaError_t launch_qr(const Launcher& L, const float* Y, int64_t rows, int ell, float* Q,
                       void* ws, size_t ws_bytes, int* status);
 // Up to two independent QRs (same ell) through one set of launches; qr_ws_bytes(max rows, ell)
-// of workspace suffices.
+// of workspace suffices. bad_cols (4 words a matrix, may be null) receives the columns whose
+// Cholesky pivot fell below the rank tolerance (those runs also latch kStQrBreakdown).
 cudaError_t launch_qr_batch(const Launcher& L, int nmat, const float* const* Y,
                             const int64_t* rows, int ell, float* const* Q, void* ws,
-                            size_t ws_bytes, int* status);
+                            size_t ws_bytes, int* status, uint32_t* bad_cols = nullptr);
+// Y (rows x ell) column j <- N(0, 1) draws (Philox4x32-10, key = seed, counter stream stream_id)
+// for every bit j set in mask[0..3].
+cudaError_t launch_replace_columns(const Launcher& L, float* Y, int64_t rows, int ell,
+                                   const uint32_t* mask, uint64_t seed, uint32_t stream_id);
 
 // Iterations of FastHALS-RP (rule 0) or MU-RP (rule 1).
 struct IterArgs {

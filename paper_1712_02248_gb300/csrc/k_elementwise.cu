@@ -57,6 +57,34 @@ __global__ void gaussian_kernel(int64_t total, uint2 key, uint32_t stream_id, fl
   }
 }
 
+// Y[i][j] = N(0, 1) for every column j whose bit is set in mask[j / 32] (rows x ell, row-major):
+// the Philox4x32-10 / Box-Muller draws of the Gaussian kernel, counter (element / 4, stream_id).
+__global__ void replace_columns_kernel(float* __restrict__ Y, int64_t rows, int ell, uint4 mask,
+                                       uint2 key, uint32_t stream_id) {
+  const uint32_t mw[4] = {mask.x, mask.y, mask.z, mask.w};
+  const int64_t total = rows * ell, nblk = (total + 3) / 4;
+  for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nblk;
+       b += (int64_t)gridDim.x * blockDim.x) {
+    const uint4 x = philox4x32_10(
+        make_uint4(static_cast<uint32_t>(b), static_cast<uint32_t>(b >> 32), stream_id, 0u), key);
+    const uint32_t u[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+    for (int t = 0; t < 4; t += 2) {
+      const float rad = sqrtf(-2.0f * logf(to_unit(u[t])));
+      float sn, cs;
+      sincospif(2.0f * to_unit(u[t + 1]), &sn, &cs);
+      const float z[2] = {rad * cs, rad * sn};
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int64_t e = 4 * b + t + q;
+        if (e >= total) continue;
+        const int j = static_cast<int>(e % ell);
+        if ((mw[j >> 5] >> (j & 31)) & 1u) Y[e] = z[q];
+      }
+    }
+  }
+}
+
 __global__ void quantize_bf16_kernel(const float* __restrict__ X, int64_t m, int64_t n, int64_t ldx,
                                      __nv_bfloat16* __restrict__ Xq, int64_t ldq) {
   const int64_t total = m * ldq;
@@ -293,6 +321,16 @@ cudaError_t launch_gaussian(const Launcher& L, int64_t rows, int64_t cols, uint6
   if (total <= 0) return cudaSuccess;
   const uint2 key = make_uint2(static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32));
   gaussian_kernel<<<grid_for((total + 3) / 4, 256), 256, 0, L.stream>>>(total, key, stream_id, out);
+  L.count();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_replace_columns(const Launcher& L, float* Y, int64_t rows, int ell,
+                                   const uint32_t* mask, uint64_t seed, uint32_t stream_id) {
+  if (rows <= 0 || ell <= 0 || ell > 128) return cudaErrorInvalidValue;
+  const uint2 key = make_uint2(static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32));
+  replace_columns_kernel<<<grid_for((rows * ell + 3) / 4, 256), 256, 0, L.stream>>>(
+      Y, rows, ell, make_uint4(mask[0], mask[1], mask[2], mask[3]), key, stream_id);
   L.count();
   return cudaGetLastError();
 }

@@ -291,12 +291,18 @@ __global__ void __launch_bounds__(256) sum_parts_kernel(const float2* __restrict
 // updates the rows below it: M[i][k] -= (M[j][i] / M[j][j]) * y_k with y_k = M[j][k] (k != j)
 // and y_j = 1. The thread that updates the next pivot M[j + 1][j + 1] also forms its reciprocal
 // (double-buffered in shared memory), so each step has one barrier. Writes T as T_hi + T_lo
-// (two FP32 arrays, ell x ell row-major).
+// (two FP32 arrays, ell x ell row-major). A pivot below kPivotTol times its column's original
+// diagonal (beyond what the float-float factor resolves: the column depends on the ones before
+// it) is replaced by that bound, latches kStQrBreakdown and sets the column's bit in bad_cols
+// (4 words a matrix, may be null).
+constexpr float kPivotTol = 1e-12f;
+
 template <int LP>
 __global__ void __launch_bounds__(512) chol_inv_ff_kernel(const float2* __restrict__ Gin,
                                                           QrBatch b, int ell,
                                                           float* __restrict__ Thi,
-                                                          float* __restrict__ Tlo, int* status) {
+                                                          float* __restrict__ Tlo, int* status,
+                                                          uint32_t* bad_cols) {
   constexpr int S = LP + 1;
   constexpr int kNT = 512, kPer = (LP * LP + kNT - 1) / kNT;
   extern __shared__ __align__(16) float chol_ff_sm[];
@@ -304,6 +310,7 @@ __global__ void __launch_bounds__(512) chol_inv_ff_kernel(const float2* __restri
   float* Ml = Mh + LP * S;        // [LP][S]
   float* rh = Ml + LP * S;        // [LP]  1 / sqrt(D_c)
   float* rl = rh + LP;
+  float* d0 = rl + LP;            // [LP]  original diagonal G[c][c]
   __shared__ FF pinv[2];          // 1 / M[j][j] of the current and the next pivot
   const int mat = blockIdx.x;
   if (mat >= b.nmat) return;
@@ -314,6 +321,7 @@ __global__ void __launch_bounds__(512) chol_inv_ff_kernel(const float2* __restri
     const float2 g = (i <= k && k < ell) ? G[e] : make_float2(0.f, 0.f);
     Mh[i * S + k] = g.x;
     Ml[i * S + k] = g.y;
+    if (i == k) d0[i] = g.x;
   }
   // this thread's entries (i, k) of the ell x ell block, fixed for all pivots
   int ei[kPer], ek[kPer];
@@ -324,16 +332,19 @@ __global__ void __launch_bounds__(512) chol_inv_ff_kernel(const float2* __restri
     ek[u] = e - ei[u] * ell;
     if (e >= ell * ell) ei[u] = -1;
   }
-  // a non-positive pivot: the sketch is numerically rank deficient
+  // a pivot below kPivotTol of its original diagonal: the sketch is numerically rank deficient
   bool bad = false;
-  auto pivot_inv = [&](FF d) {
-    if (!(d.hi > 0.f)) {
+  auto floor_of = [&](int c) { return fmaxf(kPivotTol * d0[c], 1e-30f); };
+  auto pivot_inv = [&](FF d, int c) {
+    if (!(d.hi > floor_of(c))) {
       bad = true;
-      d = {1e-30f, 0.f};
+      if (bad_cols) atomicOr(&bad_cols[4 * mat + (c >> 5)], 1u << (c & 31));
+      d = {floor_of(c), 0.f};
     }
     return ff_recip(d);
   };
-  if (t == 0) pinv[0] = pivot_inv({static_cast<float>(G[0].x), G[0].y});
+  __syncthreads();
+  if (t == 0) pinv[0] = pivot_inv({G[0].x, G[0].y}, 0);
   __syncthreads();
   for (int j = 0; j < ell; ++j) {
     const FF inv = pinv[j & 1];
@@ -346,14 +357,14 @@ __global__ void __launch_bounds__(512) chol_inv_ff_kernel(const float2* __restri
         const FF v = ff_fms({Mh[i * S + k], Ml[i * S + k]}, l, y);
         Mh[i * S + k] = v.hi;
         Ml[i * S + k] = v.lo;
-        if (i == j + 1 && k == i) pinv[(j + 1) & 1] = pivot_inv(v);
+        if (i == j + 1 && k == i) pinv[(j + 1) & 1] = pivot_inv(v, i);
       }
     }
     __syncthreads();
   }
   for (int c = t; c < ell; c += kNT) {
     FF d = {Mh[c * S + c], Ml[c * S + c]};
-    if (!(d.hi > 0.f)) d = {1e-30f, 0.f};
+    if (!(d.hi > floor_of(c))) d = {floor_of(c), 0.f};
     const FF r = ff_recip(ff_sqrt(d));
     rh[c] = r.hi;
     rl[c] = r.lo;
@@ -490,7 +501,7 @@ size_t ws_bytes_for(const int64_t* rows, int nmat, int ell) {
 }
 
 template <int LP>
-cudaError_t run(const Launcher& L, QrBatch b, int ell, char* ws, int* status) {
+cudaError_t run(const Launcher& L, QrBatch b, int ell, char* ws, int* status, uint32_t* bad_cols) {
   const int nmat = b.nmat;
   split_blocks(b.rows, nmat, b.nblk);
   int64_t parts = 0;
@@ -512,7 +523,7 @@ cudaError_t run(const Launcher& L, QrBatch b, int ell, char* ws, int* status) {
   const size_t slab_smem = sizeof(float) * kSlab * (LP + 1);
   const size_t apply_ff_smem = sizeof(float) * 2 * LP * LP + slab_smem;
   const size_t apply_smem = sizeof(float) * LP * LP + slab_smem;
-  const size_t chol_smem = sizeof(float) * (2 * LP * (LP + 1) + 2 * LP);
+  const size_t chol_smem = sizeof(float) * (2 * LP * (LP + 1) + 3 * LP);
   cudaError_t err;
   if ((err = cudaFuncSetAttribute(chol_inv_ff_kernel<LP>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -537,7 +548,8 @@ cudaError_t run(const Launcher& L, QrBatch b, int ell, char* ws, int* status) {
     }
     gram_partial_kernel<LP><<<grid, kQrThreads, slab_smem, L.stream>>>(bb, ell, Gp);
     sum_parts_kernel<LP><<<dim3(LP / 8, ell, nmat), 256, 0, L.stream>>>(Gp, bb, ell, G);
-    chol_inv_ff_kernel<LP><<<nmat, 512, chol_smem, L.stream>>>(G, bb, ell, Thi, Tlo, status);
+    chol_inv_ff_kernel<LP><<<nmat, 512, chol_smem, L.stream>>>(G, bb, ell, Thi, Tlo, status,
+                                                               bad_cols);
     if (sweep == 0)
       apply_tri_kernel<LP, true><<<grid, kQrThreads, apply_ff_smem, L.stream>>>(bb, ell, Thi, Tlo);
     else
@@ -557,7 +569,7 @@ size_t qr_ws_bytes(int64_t rows, int ell) {
 
 cudaError_t launch_qr_batch(const Launcher& L, int nmat, const float* const* Y,
                             const int64_t* rows, int ell, float* const* Q, void* ws,
-                            size_t ws_bytes, int* status) {
+                            size_t ws_bytes, int* status, uint32_t* bad_cols) {
   if (nmat < 1 || nmat > kMaxMats) return cudaErrorInvalidValue;
   if (ws_bytes < ws_bytes_for(rows, nmat, ell)) return cudaErrorInvalidValue;
   QrBatch b{};
@@ -569,18 +581,18 @@ cudaError_t launch_qr_batch(const Launcher& L, int nmat, const float* const* Y,
   }
   char* w = static_cast<char*>(ws);
   switch (lp_for(ell)) {
-    case 16: return run<16>(L, b, ell, w, status);
-    case 32: return run<32>(L, b, ell, w, status);
-    case 48: return run<48>(L, b, ell, w, status);
-    case 64: return run<64>(L, b, ell, w, status);
-    case 96: return run<96>(L, b, ell, w, status);
-    default: return run<128>(L, b, ell, w, status);
+    case 16: return run<16>(L, b, ell, w, status, bad_cols);
+    case 32: return run<32>(L, b, ell, w, status, bad_cols);
+    case 48: return run<48>(L, b, ell, w, status, bad_cols);
+    case 64: return run<64>(L, b, ell, w, status, bad_cols);
+    case 96: return run<96>(L, b, ell, w, status, bad_cols);
+    default: return run<128>(L, b, ell, w, status, bad_cols);
   }
 }
 
 cudaError_t launch_qr(const Launcher& L, const float* Y, int64_t rows, int ell, float* Q,
                       void* ws, size_t ws_bytes, int* status) {
-  return launch_qr_batch(L, 1, &Y, &rows, ell, &Q, ws, ws_bytes, status);
+  return launch_qr_batch(L, 1, &Y, &rows, ell, &Q, ws, ws_bytes, status, nullptr);
 }
 
 }  // namespace nmfrp

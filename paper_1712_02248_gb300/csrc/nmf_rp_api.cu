@@ -24,6 +24,9 @@ struct nmf_ctx {
   void* ws = nullptr;
   size_t ws_bytes = 0;
   int* d_status = nullptr;   // latched device status word
+  uint32_t* d_qrbad = nullptr;   // [8] columns the sketch QRs found dependent (2 matrices x 128 bits)
+  float* d_wh0 = nullptr;        // initial W, H kept for a rerun of nmf_solve
+  size_t wh0_cap = 0;
   double* d_res = nullptr;   // residual sums (2 doubles)
   double* h_res = nullptr;   // pinned host copy
   // solve-loop state on the device (one allocation)
@@ -250,6 +253,57 @@ nmf_status qr2(nmf_ctx* ctx, float* Ym, int64_t m, float* Yn, int64_t n, int ell
   return NMF_OK;
 }
 
+// qr2 that repairs a numerically rank-deficient pass output: Y is kept; when a Cholesky pivot
+// falls below the rank tolerance, the columns it names are replaced by Gaussian draws (a column
+// that depends on the ones before it adds nothing to range(Y), so the span keeps range(Y) and
+// gains a random direction) and CholeskyQR2 runs again. Every update of the method depends on Q
+// only through Q Q^T X, which is X on range(Y) either way. Synchronises after each attempt.
+nmf_status qr2_robust(nmf_ctx* ctx, float* Ym, int64_t m, float* Yn, int64_t n, int ell,
+                      uint64_t seed, Arena a) {
+  Phase ph(ctx, NMF_PHASE_QR);
+  float* keep_m = a.take<float>(m * ell);
+  float* keep_n = a.take<float>(n * ell);
+  NMF_CUDA(cudaMemcpyAsync(keep_m, Ym, sizeof(float) * m * ell, cudaMemcpyDeviceToDevice,
+                           ctx->stream), "qr copy");
+  NMF_CUDA(cudaMemcpyAsync(keep_n, Yn, sizeof(float) * n * ell, cudaMemcpyDeviceToDevice,
+                           ctx->stream), "qr copy");
+  size_t rest = 0;
+  void* ws = a.rest(&rest);
+  const float* ys[2] = {Ym, Yn};
+  float* qs[2] = {Ym, Yn};
+  const int64_t rows[2] = {m, n};
+  for (int attempt = 0; attempt < 4; ++attempt) {
+    uint32_t bad[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int st = 0;
+    NMF_CUDA(cudaMemsetAsync(ctx->d_qrbad, 0, sizeof(bad), ctx->stream), "qr mask");
+    NMF_CUDA(nmfrp::launch_qr_batch(launcher(ctx), 2, ys, rows, ell, qs, ws, rest, ctx->d_status,
+                                    ctx->d_qrbad),
+             "qr");
+    NMF_CUDA(cudaMemcpyAsync(bad, ctx->d_qrbad, sizeof(bad), cudaMemcpyDeviceToHost, ctx->stream),
+             "qr mask");
+    NMF_CUDA(cudaMemcpyAsync(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream),
+             "qr status");
+    NMF_CUDA(cudaStreamSynchronize(ctx->stream), "qr sync");
+    if (st != NMF_ERR_QR_BREAKDOWN) return NMF_OK;   // other statuses stay latched
+    NMF_CUDA(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream), "status reset");
+    // restore Y, replace the named columns, keep the repaired copy for the next attempt
+    float* Ys[2] = {Ym, Yn};
+    float* keeps[2] = {keep_m, keep_n};
+    for (int k = 0; k < 2; ++k) {
+      NMF_CUDA(cudaMemcpyAsync(Ys[k], keeps[k], sizeof(float) * rows[k] * ell,
+                               cudaMemcpyDeviceToDevice, ctx->stream), "qr restore");
+      if (bad[4 * k] | bad[4 * k + 1] | bad[4 * k + 2] | bad[4 * k + 3]) {
+        NMF_CUDA(nmfrp::launch_replace_columns(launcher(ctx), Ys[k], rows[k], ell, bad + 4 * k,
+                                               seed, 0x52430000u + 2u * attempt + k),
+                 "qr repair");
+        NMF_CUDA(cudaMemcpyAsync(keeps[k], Ys[k], sizeof(float) * rows[k] * ell,
+                                 cudaMemcpyDeviceToDevice, ctx->stream), "qr copy");
+      }
+    }
+  }
+  return fail(ctx, NMF_ERR_QR_BREAKDOWN, "sketch QR still rank deficient after column repair");
+}
+
 size_t pass_scratch(int64_t m, int64_t n, int ell) {
   return std::max(nmfrp::dual_pass_ws_bytes(m, n, ell),
                   std::max(nmfrp::qr_ws_bytes(m, ell), nmfrp::qr_ws_bytes(n, ell))) + 4096;
@@ -259,13 +313,15 @@ size_t sketch_ws(const nmf_params* p, bool need_omega) {
   const int64_t m = p->m, n = p->n, l = p->ell;
   size_t b = sizeof(float) * (m * l + n * l) + 1024;         // other chain's m- and n-side bases
   if (need_omega) b += sizeof(float) * (m * l + n * l) + 1024;
+  b += sizeof(float) * (m * l + n * l) + 1024;               // pass outputs kept by qr2_robust
   return b + pass_scratch(m, n, p->ell);
 }
 
 // Both chains of Eq. 3.5 advance together: pass 0 applies X to Omega_L and X^T to Omega_R; pass
 // p >= 1 applies X to one chain's n-side basis and X^T to the other chain's m-side basis.
 nmf_status sketch_impl(nmf_ctx* ctx, const nmf_params* p, const void* X, int64_t ldx,
-                       const float* omega_L, const float* omega_R, float* QL, float* QR, Arena a) {
+                       const float* omega_L, const float* omega_R, float* QL, float* QR, Arena a,
+                       bool robust = false) {
   const int64_t m = p->m, n = p->n;
   const int l = p->ell;
   const int bf16 = p->prec;   // element type of X for every pass
@@ -285,18 +341,22 @@ nmf_status sketch_impl(nmf_ctx* ctx, const nmf_params* p, const void* X, int64_t
     }
   }
   nmf_status st;
+  auto orth = [&](float* Ym, float* Yn, int pass) {
+    return robust ? qr2_robust(ctx, Ym, m, Yn, n, l, p->seed + 0x9E37u * (pass + 1), a)
+                  : qr2(ctx, Ym, m, Yn, n, l, a);
+  };
   // pass 0
   if ((st = dual(ctx, X, bf16, m, n, ldx, l, omega_L, omega_R, QL, QR, a, simt)) != NMF_OK)
     return st;
-  if ((st = qr2(ctx, QL, m, QR, n, l, a)) != NMF_OK) return st;
+  if ((st = orth(QL, QR, 0)) != NMF_OK) return st;
   for (int pass = 1; pass <= 2 * p->power_iters; ++pass) {
     if (pass & 1) {
       // right chain: X * (n-side) -> m-side; left chain: X^T * (m-side) -> n-side
       if ((st = dual(ctx, X, bf16, m, n, ldx, l, QR, QL, mR, nL, a, simt)) != NMF_OK) return st;
-      if ((st = qr2(ctx, mR, m, nL, n, l, a)) != NMF_OK) return st;
+      if ((st = orth(mR, nL, pass)) != NMF_OK) return st;
     } else {
       if ((st = dual(ctx, X, bf16, m, n, ldx, l, nL, mR, QL, QR, a, simt)) != NMF_OK) return st;
-      if ((st = qr2(ctx, QL, m, QR, n, l, a)) != NMF_OK) return st;
+      if ((st = orth(QL, QR, pass)) != NMF_OK) return st;
     }
   }
   return NMF_OK;
@@ -523,6 +583,7 @@ nmf_status nmf_create(nmf_ctx** out, int device, void* cuda_stream) {
   ctx->stream = static_cast<cudaStream_t>(cuda_stream);
   DeviceGuard g(device);
   if (cudaMalloc(&ctx->d_status, sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&ctx->d_qrbad, 8 * sizeof(uint32_t)) != cudaSuccess ||
       cudaMalloc(&ctx->d_res, 2 * sizeof(double)) != cudaSuccess ||
       cudaMallocHost(&ctx->h_res, 2 * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&ctx->d_mon, 4 * sizeof(float)) != cudaSuccess ||
@@ -551,6 +612,8 @@ void nmf_destroy(nmf_ctx* ctx) {
   for (cudaEvent_t e : ctx->pool) cudaEventDestroy(e);
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->d_status) cudaFree(ctx->d_status);
+  if (ctx->d_qrbad) cudaFree(ctx->d_qrbad);
+  if (ctx->d_wh0) cudaFree(ctx->d_wh0);
   if (ctx->d_res) cudaFree(ctx->d_res);
   if (ctx->h_res) cudaFreeHost(ctx->h_res);
   if (ctx->d_mon) cudaFree(ctx->d_mon);
@@ -723,7 +786,8 @@ nmf_status nmf_sketch(nmf_ctx* ctx, const nmf_params* p, const void* X, int64_t 
   DeviceGuard g(ctx->device);
   if ((st = ensure_ws(ctx, sketch_ws(p, !omega_L || !omega_R))) != NMF_OK) return st;
   Arena a{static_cast<char*>(ctx->ws), ctx->ws_bytes};
-  return sketch_impl(ctx, p, X, ldx, omega_L, omega_R, QL, QR, a);
+  return sketch_impl(ctx, p, X, ldx, omega_L, omega_R, QL, QR, a,
+                     (p->flags & NMF_FLAG_ROBUST_QR) != 0);
 }
 
 nmf_status nmf_compress(nmf_ctx* ctx, const nmf_params* p, const void* X, int64_t ldx,
@@ -805,18 +869,11 @@ nmf_status nmf_nndsvd(nmf_ctx* ctx, const nmf_params* p, const float* QL, const 
   return NMF_OK;
 }
 
-nmf_status nmf_solve(nmf_ctx* ctx, const nmf_params* p, int32_t init, const float* X, int64_t ldx,
-                     float* W, float* H, double* rel_err_host, int32_t* iters_done_host) {
-  if (!ctx) return NMF_ERR_INVALID_ARG;
-  nmf_status st = check_params(ctx, p);
-  if (st != NMF_OK) return st;
-  if (!X || !W || !H || ldx < p->n) return fail(ctx, NMF_ERR_INVALID_ARG, "bad solve arguments");
-  if (init != NMF_INIT_GIVEN && init != NMF_INIT_NNDSVD && init != NMF_INIT_MLP)
-    return fail(ctx, NMF_ERR_INVALID_ARG, "unknown init %d", init);
-  if (init == NMF_INIT_MLP && (!ctx->warm || ctx->warm_r != p->r))
-    return fail(ctx, NMF_ERR_INVALID_ARG, "no warm-start network for r = %d (nmf_set_warmstart)", p->r);
-  if (p->iters < 0) return fail(ctx, NMF_ERR_INVALID_ARG, "iters < 0");
-  DeviceGuard g(ctx->device);
+// One run of the whole pipeline; robust: sketch QRs repair rank-deficient pass outputs.
+nmf_status solve_impl(nmf_ctx* ctx, const nmf_params* p, int32_t init, const float* X,
+                      int64_t ldx, float* W, float* H, double* rel_err_host,
+                      int32_t* iters_done_host, bool robust) {
+  nmf_status st = NMF_OK;
   size_t need = 0;
   nmf_workspace_size(p, &need);
   if (init == NMF_INIT_MLP && ctx->warm_hidden > 256)
@@ -856,7 +913,8 @@ nmf_status nmf_solve(nmf_ctx* ctx, const nmf_params* p, int32_t init, const floa
   float* QR = a.take<float>(n * l);
   float* Xhat = a.take<float>(l * n);
   float* Xchk = a.take<float>(m * l);
-  if ((st = sketch_impl(ctx, p, Xp, ldp, nullptr, nullptr, QL, QR, a)) != NMF_OK) return st;
+  if ((st = sketch_impl(ctx, p, Xp, ldp, nullptr, nullptr, QL, QR, a, robust)) != NMF_OK)
+    return st;
   if (p->prec == NMF_PREC_FP8_E4M3) {
     // precision recovery: the E4M3 rounding of X (relative error up to 2^-4) would set the
     // floor of the compressed problem, so the compression reads the FP32 X with the final Q
@@ -946,10 +1004,53 @@ nmf_status nmf_solve(nmf_ctx* ctx, const nmf_params* p, int32_t init, const floa
   NMF_CUDA(cudaStreamSynchronize(ctx->stream), "solve sync");
   ctx->last_iters = static_cast<int>(out[2]);
   ctx->last_checks = flags[3];
+  if ((st = take_status(ctx)) != NMF_OK) return st;   // a QR breakdown is reported as such
   if (!(out[1] == out[1]) || out[1] > 1e300) return fail(ctx, NMF_ERR_NOT_FINITE, "residual is not finite");
   if (rel_err_host) *rel_err_host = out[1];
   if (iters_done_host) *iters_done_host = static_cast<int32_t>(out[2]);
-  return take_status(ctx);
+  return NMF_OK;
+}
+
+nmf_status nmf_solve(nmf_ctx* ctx, const nmf_params* p, int32_t init, const float* X, int64_t ldx,
+                     float* W, float* H, double* rel_err_host, int32_t* iters_done_host) {
+  if (!ctx) return NMF_ERR_INVALID_ARG;
+  nmf_status st = check_params(ctx, p);
+  if (st != NMF_OK) return st;
+  if (!X || !W || !H || ldx < p->n) return fail(ctx, NMF_ERR_INVALID_ARG, "bad solve arguments");
+  if (init != NMF_INIT_GIVEN && init != NMF_INIT_NNDSVD && init != NMF_INIT_MLP)
+    return fail(ctx, NMF_ERR_INVALID_ARG, "unknown init %d", init);
+  if (init == NMF_INIT_MLP && (!ctx->warm || ctx->warm_r != p->r))
+    return fail(ctx, NMF_ERR_INVALID_ARG, "no warm-start network for r = %d (nmf_set_warmstart)", p->r);
+  if (p->iters < 0) return fail(ctx, NMF_ERR_INVALID_ARG, "iters < 0");
+  DeviceGuard g(ctx->device);
+  // given initial factors are kept so that a rank-deficient sketch can run again with repaired
+  // QRs (the first run updates W, H in place)
+  const size_t wh = static_cast<size_t>(p->m * p->r + p->r * p->n);
+  if (init == NMF_INIT_GIVEN) {
+    if (ctx->wh0_cap < wh) {
+      if (ctx->d_wh0) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(ctx->d_wh0);
+        ctx->d_wh0 = nullptr;
+        ctx->wh0_cap = 0;
+      }
+      NMF_CUDA(cudaMalloc(&ctx->d_wh0, sizeof(float) * wh), "initial factors");
+      ctx->wh0_cap = wh;
+    }
+    NMF_CUDA(cudaMemcpyAsync(ctx->d_wh0, W, sizeof(float) * p->m * p->r,
+                             cudaMemcpyDeviceToDevice, ctx->stream), "initial factors");
+    NMF_CUDA(cudaMemcpyAsync(ctx->d_wh0 + p->m * p->r, H, sizeof(float) * p->r * p->n,
+                             cudaMemcpyDeviceToDevice, ctx->stream), "initial factors");
+  }
+  st = solve_impl(ctx, p, init, X, ldx, W, H, rel_err_host, iters_done_host, false);
+  if (st != NMF_ERR_QR_BREAKDOWN) return st;
+  if (init == NMF_INIT_GIVEN) {
+    NMF_CUDA(cudaMemcpyAsync(W, ctx->d_wh0, sizeof(float) * p->m * p->r,
+                             cudaMemcpyDeviceToDevice, ctx->stream), "initial factors");
+    NMF_CUDA(cudaMemcpyAsync(H, ctx->d_wh0 + p->m * p->r, sizeof(float) * p->r * p->n,
+                             cudaMemcpyDeviceToDevice, ctx->stream), "initial factors");
+  }
+  return solve_impl(ctx, p, init, X, ldx, W, H, rel_err_host, iters_done_host, true);
 }
 
 int64_t nmf_mlp_param_count(int32_t F, int32_t hidden, int32_t r) {

@@ -144,6 +144,63 @@ def test_qr_breakdown_is_reported(lib, ctx):
     lib.nmf_sync(ctx)   # status cleared after being reported
 
 
+def exact_rank_problem(seed, m, n, r, ell):
+    """X = W0 H0 exactly (no noise, Exp(1) factors): rank r < ell, so every pass output of the
+    sketch is numerically rank deficient."""
+    rng = np.random.default_rng(seed)
+    W0 = rng.exponential(1.0, (m, r))
+    H0 = rng.exponential(1.0, (r, n))
+    X = (W0 @ H0).astype(np.float32)
+    return X, rng.standard_normal((n, ell)), rng.standard_normal((m, ell))
+
+
+def test_sketch_of_exact_low_rank_x_breaks_down_without_repair(lib, ctx):
+    X, oL, oR = exact_rank_problem(3, 600, 400, 5, 12)
+    p = lib.params(600, 400, 5, 12, power_iters=2)
+    lib.nmf_sketch(ctx, p, cu(X), cu(oL), cu(oR))
+    with pytest.raises(lib.NmfError) as e:
+        lib.nmf_sync(ctx)
+    assert e.value.status == 4
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_robust_sketch_repairs_rank_deficient_passes(lib, ctx, prec):
+    """With NMF_FLAG_ROBUST_QR the dependent columns of each pass output are replaced by Gaussian
+    draws and CholeskyQR2 repeated: Q_L, Q_R orthonormal, and (closed form for exact rank
+    r <= ell) the projections reproduce X: Q_L Q_L^T X = X = X Q_R Q_R^T."""
+    m, n, r, ell = 600, 400, 5, 12
+    X, oL, oR = exact_rank_problem(3, m, n, r, ell)
+    p = lib.params(m, n, r, ell, power_iters=2, prec=prec, flags=lib.FLAG_ROBUST_QR)
+    Xd = cu(X)
+    Xp = lib.nmf_quantize(ctx, Xd) if prec == "bf16" else Xd
+    QL, QR = lib.nmf_sketch(ctx, p, Xp, cu(oL), cu(oR))
+    lib.nmf_sync(ctx)
+    QL, QR, Xh = host(QL), host(QR), X.astype(np.float64)
+    assert np.abs(QL.T @ QL - np.eye(ell)).max() <= 1e-5
+    assert np.abs(QR.T @ QR - np.eye(ell)).max() <= 1e-5
+    tol = 1e-5 if prec == "fp32" else 2e-2      # BF16: the rounding of X moves its range
+    assert rel(QL @ (QL.T @ Xh), Xh) <= tol
+    assert rel((Xh @ QR) @ QR.T, Xh) <= tol
+
+
+def test_solve_reruns_with_repaired_qr(lib, ctx):
+    """nmf_solve on an exactly low-rank X: the first run meets the breakdown, the library
+    restores the given factors and runs again with the repairing QR; the result is the solve of
+    the rank-r problem (finite, non-negative, error far below the start's)."""
+    m, n, r, ell = 600, 400, 5, 12
+    X, _, _ = exact_rank_problem(4, m, n, r, ell)
+    rng = np.random.default_rng(5)
+    W0, H0 = rng.random((m, r)), rng.random((r, n))
+    e0 = O.residual(X.astype(np.float64), W0, H0)[0]
+    p = lib.params(m, n, r, ell, power_iters=2, iters=200, seed=8)
+    W, H = cu(W0), cu(H0)
+    e, it = lib.nmf_solve(ctx, p, cu(X), W, H)
+    assert it == 200 and np.isfinite(e)
+    assert (W >= 0).all() and (H >= 0).all()
+    assert e <= 0.05 * e0
+    assert abs(lib.nmf_residual(ctx, p, cu(X), W, H)[0] - e) <= 1e-6 * max(e, 1e-12)
+
+
 # ------------------------------------------------------------------ sketch and compression
 
 def proj_diff(QL, QLo, X):
