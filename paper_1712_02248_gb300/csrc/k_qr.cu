@@ -16,6 +16,12 @@
 // identity block, [G | I] -> [D L^T | L^{-1}] with G = L D L^T (L unit lower triangular), one
 // barrier a pivot and every trailing entry updated in parallel; then R = D^{1/2} L^T and
 // R^{-1} = L^{-T} D^{-1/2}, i.e. R^{-1}[k][c] = L^{-1}[c][k] / sqrt(D_c).
+// Sweep 2 sees G = I + E with E small (the orthogonality error of sweep 1). There, with
+// R = I + N (N upper triangular), R^T R = G reads N + N^T = E - N^T N: N is the upper triangle
+// of E - N^T N with its diagonal halved, a fixed point reached from N = 0 with error of order
+// |E|^(k+1) after k steps, and R^{-1} = I - N + N^2 - ... (Horner). When a = l max |E_ij| (a
+// bound on the 2-norm of E) is at most 1e-3, a few steps and terms (the first is N = triu(E),
+// no product) give R^{-1} to 1e-8 with matrix products only; otherwise the elimination runs.
 //
 // The Gram and apply kernels run two blocks an SM, each on an equal contiguous range of rows,
 // taken in chunks of up to 64 rows (one contiguous run of floats) staged in shared memory with
@@ -297,7 +303,7 @@ __global__ void __launch_bounds__(256) sum_parts_kernel(const float2* __restrict
 // (4 words a matrix, may be null).
 constexpr float kPivotTol = 1e-12f;
 
-template <int LP>
+template <int LP, bool NEAR_I>
 __global__ void __launch_bounds__(512) chol_inv_ff_kernel(const float2* __restrict__ Gin,
                                                           QrBatch b, int ell,
                                                           float* __restrict__ Thi,
@@ -311,6 +317,7 @@ __global__ void __launch_bounds__(512) chol_inv_ff_kernel(const float2* __restri
   float* rh = Ml + LP * S;        // [LP]  1 / sqrt(D_c)
   float* rl = rh + LP;
   float* d0 = rl + LP;            // [LP]  original diagonal G[c][c]
+  float* Mx = d0 + LP;            // [LP][S] (sweep 2's product path)
   __shared__ FF pinv[2];          // 1 / M[j][j] of the current and the next pivot
   const int mat = blockIdx.x;
   if (mat >= b.nmat) return;
@@ -322,6 +329,99 @@ __global__ void __launch_bounds__(512) chol_inv_ff_kernel(const float2* __restri
     Mh[i * S + k] = g.x;
     Ml[i * S + k] = g.y;
     if (i == k) d0[i] = g.x;
+  }
+  if constexpr (NEAR_I) {
+    __shared__ unsigned emax_bits;
+    if (t == 0) emax_bits = 0u;
+    __syncthreads();
+    // E = G - I (FP32; the float-float Gram rounded once), in Mh (upper triangle, mirrored)
+    unsigned mine = 0u;
+    for (int e = t; e < ell * ell; e += kNT) {
+      const int i = e / ell, k = e - i * ell;
+      if (i > k) continue;
+      const float v = __fadd_rn(__fadd_rn(Mh[i * S + k], -(i == k ? 1.f : 0.f)), Ml[i * S + k]);
+      mine = max(mine, __float_as_uint(fabsf(v)));
+      Mx[i * S + k] = v;
+      Mx[k * S + i] = v;
+    }
+    atomicMax(&emax_bits, mine);
+    __syncthreads();
+    const float a2 = static_cast<float>(ell) * __uint_as_float(emax_bits);   // >= |E|_2
+    if (a2 <= 1e-3f) {
+      // error budget 1e-8: N after `steps` fixed-point steps is off by a2^(steps+1), the series
+      // cut after N^terms by a2^(terms+1)
+      const int steps = a2 <= 1e-4f ? 1 : 2, terms = a2 <= 1e-4f ? 2 : 3;
+      float* E = Mx;
+      float* N = Ml;
+      float* Nn = Mh;
+      // four partial sums: the dot products are latency-bound chains through shared memory
+      auto dot = [&](const float* x, int xs, const float* y, int ys, int u0, int u1) {
+        float q0 = 0.f, q1 = 0.f, q2 = 0.f, q3 = 0.f;
+        int u = u0;
+        for (; u + 3 < u1; u += 4) {
+          q0 = fmaf(x[u * xs], y[u * ys], q0);
+          q1 = fmaf(x[(u + 1) * xs], y[(u + 1) * ys], q1);
+          q2 = fmaf(x[(u + 2) * xs], y[(u + 2) * ys], q2);
+          q3 = fmaf(x[(u + 3) * xs], y[(u + 3) * ys], q3);
+        }
+        for (; u < u1; ++u) q0 = fmaf(x[u * xs], y[u * ys], q0);
+        return (q0 + q1) + (q2 + q3);
+      };
+      // first step from N = 0: N = triu(E), diagonal halved
+      for (int e = t; e < LP * S; e += kNT) {
+        const int i = e / S, k = e - i * S;
+        N[e] = (i < ell && k < ell && i <= k) ? (i == k ? 0.5f : 1.f) * E[e] : 0.f;
+      }
+      __syncthreads();
+      for (int step = 1; step < steps; ++step) {   // N <- triu(E - N^T N), diagonal halved
+        for (int e = t; e < ell * ell; e += kNT) {
+          const int i = e / ell, k = e - i * ell;
+          float v = 0.f;
+          if (i <= k) {
+            v = E[i * S + k] - dot(N + i, S, N + k, S, 0, i + 1);   // (N^T N)_ik
+            if (i == k) v *= 0.5f;
+          }
+          Nn[i * S + k] = v;
+        }
+        __syncthreads();
+        for (int e = t; e < ell * ell; e += kNT) {
+          const int i = e / ell, k = e - i * ell;
+          N[i * S + k] = Nn[i * S + k];
+        }
+        __syncthreads();
+      }
+      // T = (I + N)^{-1} = I - N (I - N (I - ...)): P = I - N, then P <- I - N P
+      float* P = Mx;
+      float* Pn = Mh;
+      for (int e = t; e < ell * ell; e += kNT) {
+        const int i = e / ell, k = e - i * ell;
+        P[i * S + k] = (i == k ? 1.f : 0.f) - N[i * S + k];
+      }
+      __syncthreads();
+      for (int term = 1; term < terms; ++term) {
+        for (int e = t; e < ell * ell; e += kNT) {
+          const int i = e / ell, k = e - i * ell;
+          float v = 0.f;
+          if (i <= k) v = (i == k ? 1.f : 0.f) - dot(N + i * S, 1, P + k, S, i, k + 1);   // (N P)_ik
+          Pn[i * S + k] = v;
+        }
+        __syncthreads();
+        for (int e = t; e < ell * ell; e += kNT) {
+          const int i = e / ell, k = e - i * ell;
+          P[i * S + k] = Pn[i * S + k];
+        }
+        __syncthreads();
+      }
+      float* th = Thi + static_cast<int64_t>(mat) * ell * ell;
+      float* tl = Tlo + static_cast<int64_t>(mat) * ell * ell;
+      for (int e = t; e < ell * ell; e += kNT) {
+        const int i = e / ell, k = e - i * ell;
+        th[e] = P[i * S + k];
+        tl[e] = 0.f;
+      }
+      return;
+    }
+    __syncthreads();
   }
   // this thread's entries (i, k) of the ell x ell block, fixed for all pivots
   int ei[kPer], ek[kPer];
@@ -524,10 +624,14 @@ cudaError_t run(const Launcher& L, QrBatch b, int ell, char* ws, int* status, ui
   const size_t apply_ff_smem = sizeof(float) * 2 * LP * LP + slab_smem;
   const size_t apply_smem = sizeof(float) * LP * LP + slab_smem;
   const size_t chol_smem = sizeof(float) * (2 * LP * (LP + 1) + 3 * LP);
+  const size_t chol_smem2 = chol_smem + sizeof(float) * LP * (LP + 1);
   cudaError_t err;
-  if ((err = cudaFuncSetAttribute(chol_inv_ff_kernel<LP>,
+  if ((err = cudaFuncSetAttribute(chol_inv_ff_kernel<LP, false>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   static_cast<int>(chol_smem))) != cudaSuccess ||
+      (err = cudaFuncSetAttribute(chol_inv_ff_kernel<LP, true>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(chol_smem2))) != cudaSuccess ||
       (err = cudaFuncSetAttribute(gram_partial_kernel<LP>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   static_cast<int>(slab_smem))) != cudaSuccess ||
@@ -548,8 +652,12 @@ cudaError_t run(const Launcher& L, QrBatch b, int ell, char* ws, int* status, ui
     }
     gram_partial_kernel<LP><<<grid, kQrThreads, slab_smem, L.stream>>>(bb, ell, Gp);
     sum_parts_kernel<LP><<<dim3(LP / 8, ell, nmat), 256, 0, L.stream>>>(Gp, bb, ell, G);
-    chol_inv_ff_kernel<LP><<<nmat, 512, chol_smem, L.stream>>>(G, bb, ell, Thi, Tlo, status,
-                                                               bad_cols);
+    if (sweep == 0)
+      chol_inv_ff_kernel<LP, false><<<nmat, 512, chol_smem, L.stream>>>(G, bb, ell, Thi, Tlo,
+                                                                        status, bad_cols);
+    else
+      chol_inv_ff_kernel<LP, true><<<nmat, 512, chol_smem2, L.stream>>>(G, bb, ell, Thi, Tlo,
+                                                                        status, bad_cols);
     if (sweep == 0)
       apply_tri_kernel<LP, true><<<grid, kQrThreads, apply_ff_smem, L.stream>>>(bb, ell, Thi, Tlo);
     else
