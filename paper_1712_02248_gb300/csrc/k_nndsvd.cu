@@ -18,7 +18,10 @@ namespace nmfrp {
 namespace {
 
 constexpr int kMaxL = 128;
-constexpr int kSlabCols = 256;
+constexpr int kSlabCols = 32;      // Gram blocks take multiples of 32 columns of X_hat ...
+constexpr int kMaxSlabs = 256;     // ... wide enough to need at most 256 blocks
+constexpr int kRowThreads = 128;   // threads (rows of U) a u_rows block
+constexpr int kColThreads = 64;    // threads (columns of V) a v_cols block
 
 __device__ __forceinline__ void ff_fma(float a, float b, float& hi, float& lo) {
   const float p = __fmul_rn(a, b);
@@ -36,15 +39,15 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Partial M[p][q] = sum over a slab of 256 columns of X_hat[p][c] X_hat[q][c], p <= q.
+// Partial M[p][q] = sum over a slab of `width` columns of X_hat[p][c] X_hat[q][c], p <= q.
 __global__ void __launch_bounds__(256) xgram_partial_kernel(const float* __restrict__ Xhat,
-                                                            int64_t n, int ell,
+                                                            int64_t n, int ell, int width,
                                                             double* __restrict__ part) {
-  extern __shared__ float xs[];   // [ell][kSlabCols + 1]
-  const int S = kSlabCols + 1;
-  const int64_t c0 = static_cast<int64_t>(blockIdx.x) * kSlabCols;
-  for (int e = threadIdx.x; e < ell * kSlabCols; e += blockDim.x) {
-    const int k = e / kSlabCols, c = e - k * kSlabCols;
+  extern __shared__ float xs[];   // [ell][width + 1]
+  const int S = width + 1;
+  const int64_t c0 = static_cast<int64_t>(blockIdx.x) * width;
+  for (int e = threadIdx.x; e < ell * width; e += blockDim.x) {
+    const int k = e / width, c = e - k * width;
     xs[k * S + c] = (c0 + c < n) ? Xhat[k * n + c0 + c] : 0.f;
   }
   __syncthreads();
@@ -53,7 +56,7 @@ __global__ void __launch_bounds__(256) xgram_partial_kernel(const float* __restr
     const int p = e / ell, q = e - p * ell;
     if (p > q) continue;
     float hi = 0.f, lo = 0.f;
-    for (int c = 0; c < kSlabCols; ++c) ff_fma(xs[p * S + c], xs[q * S + c], hi, lo);
+    for (int c = 0; c < width; ++c) ff_fma(xs[p * S + c], xs[q * S + c], hi, lo);
     out[e] = static_cast<double>(hi) + static_cast<double>(lo);
   }
 }
@@ -194,45 +197,65 @@ __device__ __forceinline__ float warp_sumf(float v) {
 }
 
 // rows: U[i][j] = sum_k QL[i][k] Ur[k][j] into W (scratch); per-block sums of the squared
-// positive and negative parts of each column
-__global__ void __launch_bounds__(256) u_rows_kernel(const float* __restrict__ QL, int64_t m,
-                                                     int ell, int r, const float* __restrict__ Ur,
-                                                     float* __restrict__ U, double* __restrict__ part) {
+// positive and negative parts of each column. A thread takes one row: the row is read once and
+// the r outputs accumulate side by side (independent chains).
+template <int RM>   // RM >= r: the register arrays of a thread
+__global__ void __launch_bounds__(kRowThreads) u_rows_kernel(const float* __restrict__ QL,
+                                                             int64_t m, int ell, int r,
+                                                             const float* __restrict__ Ur,
+                                                             float* __restrict__ U,
+                                                             double* __restrict__ part) {
   __shared__ float us[kMaxL * 64];
   __shared__ float acc[2][64];
   for (int e = threadIdx.x; e < ell * r; e += blockDim.x) us[e] = Ur[e];
   for (int e = threadIdx.x; e < 2 * 64; e += blockDim.x) acc[e / 64][e % 64] = 0.f;
   __syncthreads();
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-  for (int64_t i0 = static_cast<int64_t>(blockIdx.x) * blockDim.x; i0 < m; i0 += stride) {
-    const int64_t i = i0 + threadIdx.x;
-    const bool act = i < m;
-    for (int j = 0; j < r; ++j) {
-      float s = 0.f;
-      if (act) {
-        const float* q = QL + i * ell;
-        for (int k = 0; k < ell; ++k) s = fmaf(q[k], us[k * r + j], s);
-        U[i * r + j] = s;
+  float pp[RM], nn[RM];
+#pragma unroll
+  for (int j = 0; j < RM; ++j) pp[j] = nn[j] = 0.f;
+  for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < m; i += stride) {
+    float s[RM];
+#pragma unroll
+    for (int j = 0; j < RM; ++j) s[j] = 0.f;
+    const float* q = QL + i * ell;
+    for (int k = 0; k < ell; ++k) {
+      const float qk = q[k];
+#pragma unroll
+      for (int j = 0; j < RM; ++j)
+        if (j < r) s[j] = fmaf(qk, us[k * r + j], s[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < RM; ++j)
+      if (j < r) {
+        U[i * r + j] = s[j];
+        pp[j] = fmaf(s[j] > 0.f ? s[j] : 0.f, s[j], pp[j]);
+        nn[j] = fmaf(s[j] < 0.f ? s[j] : 0.f, s[j], nn[j]);
       }
-      const float pp = warp_sumf(s > 0.f ? s * s : 0.f);
-      const float nn = warp_sumf(s < 0.f ? s * s : 0.f);
+  }
+#pragma unroll
+  for (int j = 0; j < RM; ++j)
+    if (j < r) {
+      const float a = warp_sumf(pp[j]), b = warp_sumf(nn[j]);
       if ((threadIdx.x & 31) == 0) {
-        atomicAdd(&acc[0][j], pp);
-        atomicAdd(&acc[1][j], nn);
+        atomicAdd(&acc[0][j], a);
+        atomicAdd(&acc[1][j], b);
       }
     }
-  }
   __syncthreads();
   for (int e = threadIdx.x; e < 2 * r; e += blockDim.x)
     part[static_cast<int64_t>(blockIdx.x) * 2 * r + e] = acc[e / r][e % r];
 }
 
-// columns: V[j][c] = sum_k Xhat[k][c] Ur[k][j] / sigma_j into H (scratch); sign-part sums
-__global__ void __launch_bounds__(256) v_cols_kernel(const float* __restrict__ Xhat, int64_t n,
-                                                     int ell, int r, const float* __restrict__ Ur,
-                                                     const float* __restrict__ sigma,
-                                                     float* __restrict__ V,
-                                                     double* __restrict__ part) {
+// columns: V[j][c] = sum_k Xhat[k][c] Ur[k][j] / sigma_j into H (scratch); sign-part sums. A
+// thread takes one column (coalesced over the block), read once.
+template <int RM>
+__global__ void __launch_bounds__(kColThreads) v_cols_kernel(const float* __restrict__ Xhat,
+                                                             int64_t n, int ell, int r,
+                                                             const float* __restrict__ Ur,
+                                                             const float* __restrict__ sigma,
+                                                             float* __restrict__ V,
+                                                             double* __restrict__ part) {
   __shared__ float us[kMaxL * 64];
   __shared__ float isg[64];
   __shared__ float acc[2][64];
@@ -241,27 +264,52 @@ __global__ void __launch_bounds__(256) v_cols_kernel(const float* __restrict__ X
   for (int e = threadIdx.x; e < 2 * 64; e += blockDim.x) acc[e / 64][e % 64] = 0.f;
   __syncthreads();
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-  for (int64_t c0 = static_cast<int64_t>(blockIdx.x) * blockDim.x; c0 < n; c0 += stride) {
-    const int64_t c = c0 + threadIdx.x;
-    const bool act = c < n;
-    for (int j = 0; j < r; ++j) {
-      float s = 0.f;
-      if (act) {
-        for (int k = 0; k < ell; ++k) s = fmaf(Xhat[k * n + c], us[k * r + j], s);
-        s *= isg[j];
-        V[j * n + c] = s;
+  float pp[RM], nn[RM];
+#pragma unroll
+  for (int j = 0; j < RM; ++j) pp[j] = nn[j] = 0.f;
+  for (int64_t c = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; c < n; c += stride) {
+    float s[RM];
+#pragma unroll
+    for (int j = 0; j < RM; ++j) s[j] = 0.f;
+    for (int k = 0; k < ell; ++k) {
+      const float x = Xhat[k * n + c];
+#pragma unroll
+      for (int j = 0; j < RM; ++j)
+        if (j < r) s[j] = fmaf(x, us[k * r + j], s[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < RM; ++j)
+      if (j < r) {
+        const float v = s[j] * isg[j];
+        V[j * n + c] = v;
+        pp[j] = fmaf(v > 0.f ? v : 0.f, v, pp[j]);
+        nn[j] = fmaf(v < 0.f ? v : 0.f, v, nn[j]);
       }
-      const float pp = warp_sumf(s > 0.f ? s * s : 0.f);
-      const float nn = warp_sumf(s < 0.f ? s * s : 0.f);
+  }
+#pragma unroll
+  for (int j = 0; j < RM; ++j)
+    if (j < r) {
+      const float a = warp_sumf(pp[j]), b = warp_sumf(nn[j]);
       if ((threadIdx.x & 31) == 0) {
-        atomicAdd(&acc[0][j], pp);
-        atomicAdd(&acc[1][j], nn);
+        atomicAdd(&acc[0][j], a);
+        atomicAdd(&acc[1][j], b);
       }
     }
-  }
   __syncthreads();
   for (int e = threadIdx.x; e < 2 * r; e += blockDim.x)
     part[static_cast<int64_t>(blockIdx.x) * 2 * r + e] = acc[e / r][e % r];
+}
+
+// out[e] = sum over the nb blocks of part[b][e] (e < 2 r): one warp a sum, lanes over the blocks,
+// so the coefficient kernels read a single partial.
+__global__ void part_sum_kernel(const double* __restrict__ part, int nb, int r,
+                                double* __restrict__ out) {
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (w >= 2 * r) return;
+  double v = 0.0;
+  for (int b = lane; b < nb; b += 32) v += part[static_cast<int64_t>(b) * 2 * r + w];
+  v = warp_sum(v);
+  if (lane == 0) out[w] = v;
 }
 
 // per component: which sign part to keep and the two scale factors
@@ -331,8 +379,14 @@ __global__ void nndsvd_apply_kernel(float* __restrict__ W, int64_t m, float* __r
   }
 }
 
-int blocks_for(int64_t work) {
-  const int64_t b = cdiv(work, 256);
+// columns a Gram block takes: a multiple of 32, at most kMaxSlabs blocks
+int slab_width(int64_t n) {
+  const int64_t w = (cdiv(n, kMaxSlabs) + kSlabCols - 1) / kSlabCols * kSlabCols;
+  return static_cast<int>(w < kSlabCols ? kSlabCols : w);
+}
+
+int blocks_for(int64_t work, int threads = 256) {
+  const int64_t b = cdiv(work, threads);
   return static_cast<int>(b < 1 ? 1 : (b > 1024 ? 1024 : b));
 }
 
@@ -428,9 +482,9 @@ __global__ void ws_feature_kernel(float* __restrict__ Wb, int64_t m, float* __re
 }  // namespace
 
 size_t nndsvd_ws_bytes(int64_t m, int64_t n, int r, int ell) {
-  const int64_t slabs = cdiv(n, kSlabCols);
-  const int bu = blocks_for(m), bv = blocks_for(n);
-  return sizeof(double) * ((slabs + 1) * ell * ell + 2 * r * (bu + bv)) +
+  const int64_t slabs = cdiv(n, slab_width(n));
+  const int bu = blocks_for(m, kRowThreads), bv = blocks_for(n, kColThreads);
+  return sizeof(double) * ((slabs + 1) * ell * ell + 2 * r * (bu + bv) + 4 * r) +
          sizeof(float) * (ell * r + r + 5 * r) + 4096;
 }
 
@@ -440,16 +494,19 @@ cudaError_t launch_nndsvd(const Launcher& L, int64_t m, int64_t n, int r, int el
   (void)status;
   if (ell > kMaxL || r > 64 || r > ell) return cudaErrorNotSupported;
   if (ws_bytes < nndsvd_ws_bytes(m, n, r, ell)) return cudaErrorInvalidValue;
-  const int64_t slabs = cdiv(n, kSlabCols);
-  const int bu = blocks_for(m), bv = blocks_for(n);
+  const int width = slab_width(n);
+  const int64_t slabs = cdiv(n, width);
+  const int bu = blocks_for(m, kRowThreads), bv = blocks_for(n, kColThreads);
   double* gpart = static_cast<double*>(ws);
   double* M = gpart + slabs * ell * ell;
   double* upart = M + ell * ell;
   double* vpart = upart + 2 * r * bu;
-  float* Ur = reinterpret_cast<float*>(vpart + 2 * r * bv);
+  double* usum = vpart + 2 * r * bv;   // [2 r] sums over the u blocks, then [2 r] over the v blocks
+  double* vsum = usum + 2 * r;
+  float* Ur = reinterpret_cast<float*>(vsum + 2 * r);
   float* sigma = Ur + ell * r;
   float* coef = sigma + r;
-  const size_t gsm = sizeof(float) * ell * (kSlabCols + 1);
+  const size_t gsm = sizeof(float) * ell * (width + 1);
   cudaError_t err = cudaFuncSetAttribute(xgram_partial_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(gsm));
@@ -459,15 +516,28 @@ cudaError_t launch_nndsvd(const Launcher& L, int64_t m, int64_t n, int r, int el
   if ((err = cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   static_cast<int>(jsm))) != cudaSuccess)
     return err;
-  xgram_partial_kernel<<<static_cast<unsigned>(slabs), 256, gsm, L.stream>>>(Xhat, n, ell, gpart);
+  xgram_partial_kernel<<<static_cast<unsigned>(slabs), 256, gsm, L.stream>>>(Xhat, n, ell, width,
+                                                                            gpart);
   xgram_sum_kernel<<<static_cast<unsigned>(cdiv(static_cast<int64_t>(ell) * ell * 32, 256)), 256, 0,
                      L.stream>>>(gpart, static_cast<int>(slabs), ell, M);
   jacobi_kernel<<<1, 512, jsm, L.stream>>>(M, ell, r, Ur, sigma);
-  u_rows_kernel<<<bu, 256, 0, L.stream>>>(QL, m, ell, r, Ur, W, upart);
-  v_cols_kernel<<<bv, 256, 0, L.stream>>>(Xhat, n, ell, r, Ur, sigma, H, vpart);
-  nndsvd_coef_kernel<<<1, 64, 0, L.stream>>>(upart, bu, vpart, bv, r, sigma, coef);
+  if (r <= 16) {
+    u_rows_kernel<16><<<bu, kRowThreads, 0, L.stream>>>(QL, m, ell, r, Ur, W, upart);
+    v_cols_kernel<16><<<bv, kColThreads, 0, L.stream>>>(Xhat, n, ell, r, Ur, sigma, H, vpart);
+  } else if (r <= 32) {
+    u_rows_kernel<32><<<bu, kRowThreads, 0, L.stream>>>(QL, m, ell, r, Ur, W, upart);
+    v_cols_kernel<32><<<bv, kColThreads, 0, L.stream>>>(Xhat, n, ell, r, Ur, sigma, H, vpart);
+  } else {
+    u_rows_kernel<64><<<bu, kRowThreads, 0, L.stream>>>(QL, m, ell, r, Ur, W, upart);
+    v_cols_kernel<64><<<bv, kColThreads, 0, L.stream>>>(Xhat, n, ell, r, Ur, sigma, H, vpart);
+  }
+  part_sum_kernel<<<static_cast<unsigned>(cdiv(2 * r * 32, 256)), 256, 0, L.stream>>>(upart, bu, r,
+                                                                                    usum);
+  part_sum_kernel<<<static_cast<unsigned>(cdiv(2 * r * 32, 256)), 256, 0, L.stream>>>(vpart, bv, r,
+                                                                                    vsum);
+  nndsvd_coef_kernel<<<1, 64, 0, L.stream>>>(usum, 1, vsum, 1, r, sigma, coef);
   nndsvd_apply_kernel<<<blocks_for(m * r + r * n), 256, 0, L.stream>>>(W, m, H, n, r, coef);
-  L.count(7);
+  L.count(9);
   return cudaGetLastError();
 }
 
@@ -477,16 +547,19 @@ cudaError_t launch_warmstart_features(const Launcher& L, int64_t m, int64_t n, i
                                       size_t ws_bytes) {
   if (ell > kMaxL || r > 64 || r > ell) return cudaErrorNotSupported;
   if (ws_bytes < nndsvd_ws_bytes(m, n, r, ell)) return cudaErrorInvalidValue;
-  const int64_t slabs = cdiv(n, kSlabCols);
-  const int bu = blocks_for(m), bv = blocks_for(n);
+  const int width = slab_width(n);
+  const int64_t slabs = cdiv(n, width);
+  const int bu = blocks_for(m, kRowThreads), bv = blocks_for(n, kColThreads);
   double* gpart = static_cast<double*>(ws);
   double* M = gpart + slabs * ell * ell;
   double* upart = M + ell * ell;
   double* vpart = upart + 2 * r * bu;
-  float* Ur = reinterpret_cast<float*>(vpart + 2 * r * bv);
+  double* usum = vpart + 2 * r * bv;   // [2 r] sums over the u blocks, then [2 r] over the v blocks
+  double* vsum = usum + 2 * r;
+  float* Ur = reinterpret_cast<float*>(vsum + 2 * r);
   float* sigma = Ur + ell * r;
   float* cw = sigma + r;
-  const size_t gsm = sizeof(float) * ell * (kSlabCols + 1);
+  const size_t gsm = sizeof(float) * ell * (width + 1);
   cudaError_t err = cudaFuncSetAttribute(xgram_partial_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(gsm));
@@ -496,15 +569,28 @@ cudaError_t launch_warmstart_features(const Launcher& L, int64_t m, int64_t n, i
   if ((err = cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   static_cast<int>(jsm))) != cudaSuccess)
     return err;
-  xgram_partial_kernel<<<static_cast<unsigned>(slabs), 256, gsm, L.stream>>>(Xhat, n, ell, gpart);
+  xgram_partial_kernel<<<static_cast<unsigned>(slabs), 256, gsm, L.stream>>>(Xhat, n, ell, width,
+                                                                            gpart);
   xgram_sum_kernel<<<static_cast<unsigned>(cdiv(static_cast<int64_t>(ell) * ell * 32, 256)), 256, 0,
                      L.stream>>>(gpart, static_cast<int>(slabs), ell, M);
   jacobi_kernel<<<1, 512, jsm, L.stream>>>(M, ell, r, Ur, sigma);
-  u_rows_kernel<<<bu, 256, 0, L.stream>>>(QL, m, ell, r, Ur, Wb, upart);
-  v_cols_kernel<<<bv, 256, 0, L.stream>>>(Xhat, n, ell, r, Ur, sigma, Hb, vpart);
-  ws_coef_kernel<<<1, 64, 0, L.stream>>>(upart, bu, vpart, bv, r, sigma, cw, hscale);
+  if (r <= 16) {
+    u_rows_kernel<16><<<bu, kRowThreads, 0, L.stream>>>(QL, m, ell, r, Ur, Wb, upart);
+    v_cols_kernel<16><<<bv, kColThreads, 0, L.stream>>>(Xhat, n, ell, r, Ur, sigma, Hb, vpart);
+  } else if (r <= 32) {
+    u_rows_kernel<32><<<bu, kRowThreads, 0, L.stream>>>(QL, m, ell, r, Ur, Wb, upart);
+    v_cols_kernel<32><<<bv, kColThreads, 0, L.stream>>>(Xhat, n, ell, r, Ur, sigma, Hb, vpart);
+  } else {
+    u_rows_kernel<64><<<bu, kRowThreads, 0, L.stream>>>(QL, m, ell, r, Ur, Wb, upart);
+    v_cols_kernel<64><<<bv, kColThreads, 0, L.stream>>>(Xhat, n, ell, r, Ur, sigma, Hb, vpart);
+  }
+  part_sum_kernel<<<static_cast<unsigned>(cdiv(2 * r * 32, 256)), 256, 0, L.stream>>>(upart, bu, r,
+                                                                                    usum);
+  part_sum_kernel<<<static_cast<unsigned>(cdiv(2 * r * 32, 256)), 256, 0, L.stream>>>(vpart, bv, r,
+                                                                                    vsum);
+  ws_coef_kernel<<<1, 64, 0, L.stream>>>(usum, 1, vsum, 1, r, sigma, cw, hscale);
   ws_feature_kernel<<<blocks_for(m * r + r * n), 256, 0, L.stream>>>(Wb, m, Hb, n, r, cw, Fw, Fh);
-  L.count(7);
+  L.count(9);
   return cudaGetLastError();
 }
 
