@@ -74,6 +74,21 @@ __global__ void xgram_sum_kernel(const double* __restrict__ part, int nparts, in
   if (lane == 0) M[warp] = v;
 }
 
+// One Jacobi task: a column rotation (c_k, s_k) of a 1 x 2 or 2 x 2 block of A or V, then for a
+// 2 x 2 block of A the row rotation (c_i, s_i). The entries are loaded first and stored later so
+// that the loads of two tasks overlap (the tasks of one round touch disjoint entries).
+struct JTask {
+  int o0, o1, o2, o3;   // offsets into the shared A | V storage
+  float x0, x1, x2, x3;
+  float ci, si, ck, sk;
+  bool two, live;
+};
+
+// floor(e / d) for e < 2^14 and 1 <= d <= 128: e * ceil(2^32 / d) / 2^32 is exact there
+__device__ __forceinline__ int div_small(int e, unsigned long long magic) {
+  return static_cast<int>((static_cast<unsigned long long>(e) * magic) >> 32);
+}
+
 // One block: cyclic Jacobi on M (FP32). Writes the eigenvectors of the
 // r largest eigenvalues (columns, ell x r, row-major) and sigma_j = sqrt(lambda_j) (descending).
 __global__ void __launch_bounds__(512) jacobi_kernel(const double* __restrict__ Mg, int ell, int r,
@@ -81,104 +96,149 @@ __global__ void __launch_bounds__(512) jacobi_kernel(const double* __restrict__ 
                                                      float* __restrict__ sigma) {
   extern __shared__ float jsm[];
   const int L = (ell + 1) / 2 * 2;   // even size (a zero row/column pads odd ell)
-  const int LS = L + 1;
+  const int LS = L + 1, L1 = L - 1, half = L / 2;
   float* Am = jsm;                   // [L][LS]
   float* Vm = Am + L * LS;           // [L][LS]
+  const int voff = L * LS;
 #define A(p, q) Am[(p) * LS + (q)]
 #define V(p, q) Vm[(p) * LS + (q)]
   __shared__ float cs[kMaxL / 2], sn[kMaxL / 2];
-  __shared__ int top[kMaxL / 2], bot[kMaxL / 2];
   __shared__ int order[kMaxL];
+  __shared__ int rflag[2];           // "some pair rotates" of the current and the next round
+  __shared__ unsigned dmax_bits;
   const int t = threadIdx.x, nt = blockDim.x;
   for (int e = t; e < L * L; e += nt) {
     const int p = e / L, q = e - p * L;
     A(p, q) = (p < ell && q < ell) ? static_cast<float>(Mg[p * ell + q]) : 0.f;
     V(p, q) = (p == q) ? 1.f : 0.f;
   }
-  const int half = L / 2;
-  for (int i = t; i < half; i += nt) {
-    top[i] = 2 * i;
-    bot[i] = 2 * i + 1;
-  }
-  __shared__ int rotated;
-  __shared__ unsigned dmax_bits;
+  if (t == 0) rflag[0] = rflag[1] = 0;
+  const unsigned long long mag_half = ((1ull << 32) + half - 1) / half;
+  const unsigned long long mag_L = ((1ull << 32) + L - 1) / L;
+  const int nblk = half * half, ntask = nblk + L * half;
+  int g = 0;   // rounds so far (over all sweeps): selects the round's flag
   for (int sweep = 0; sweep < 30; ++sweep) {
     // a sweep that rotates no pair ends the iteration. A pair is rotated while |a_pq| exceeds
     // 4 eps32 max_p |a_pp|: FP32 rounding leaves off-diagonal noise of order eps32 lambda_max
     // in every entry, which is also the eigenvector error the results are held to
     // (ell eps32 lambda_max / gap)
-    if (t == 0) {
-      rotated = 0;
-      dmax_bits = 0u;
-    }
+    if (t == 0) dmax_bits = 0u;
     __syncthreads();
     for (int p = t; p < L; p += nt) atomicMax(&dmax_bits, __float_as_uint(fabsf(A(p, p))));
     __syncthreads();
     const float thr = 4.f * 1.1920929e-7f * __uint_as_float(dmax_bits);
-    for (int round = 0; round < L - 1; ++round) {
+    int sweep_rot = 0;
+    for (int round = 0; round < L1; ++round, ++g) {
       // round-robin pairing (circle method): position 0 fixed, positions 1..L-1 rotated by
       // `round`; pair i joins positions i and L-1-i (each index once per round, every pair of
       // indices once per sweep)
-      auto pos = [&](int j) { return j == 0 ? 0 : (j - 1 + round) % (L - 1) + 1; };
+      auto pos = [&](int j) {
+        const int u = j - 1 + round;
+        return j == 0 ? 0 : (u >= L1 ? u - L1 : u) + 1;
+      };
+      auto pair = [&](int i, int& p, int& q) {
+        const int a = pos(i), b = pos(L1 - i);
+        p = a < b ? a : b;
+        q = a < b ? b : a;
+      };
+      // the next round's flag is free: its last readers passed this round's first barrier
+      if (t == 0) rflag[(g + 1) & 1] = 0;
       for (int i = t; i < half; i += nt) {
-        const int a = pos(i), b = pos(L - 1 - i);
-        const int p = a < b ? a : b, q = a < b ? b : a;
-        top[i] = p;
-        bot[i] = q;
+        int p, q;
+        pair(i, p, q);
         const float apq = A(p, q);
         float c = 1.f, sv = 0.f;
         if (fabsf(apq) > 1e-30f && fabsf(apq) > thr) {
-          const float theta = (A(q, q) - A(p, p)) / (2.f * apq);
-          const float tt = copysignf(1.f, theta) / (fabsf(theta) + sqrtf(theta * theta + 1.f));
-          c = rsqrtf(tt * tt + 1.f);
+          // Rutishauser's rotation: t = sign(theta) / (|theta| + sqrt(theta^2 + 1))
+          const float theta = __fdividef(A(q, q) - A(p, p), 2.f * apq);
+          const float tt =
+              copysignf(__frcp_rn(fabsf(theta) + sqrtf(fmaf(theta, theta, 1.f))), theta);
+          c = rsqrtf(fmaf(tt, tt, 1.f));
           sv = tt * c;
-          rotated = 1;
+          rflag[g & 1] = 1;
         }
         cs[i] = c;
         sn[i] = sv;
       }
       __syncthreads();
+      if (!rflag[g & 1]) continue;   // no pair rotates: A and V stay as they are
+      sweep_rot = 1;
       // A <- J^T A J as 2 x 2 blocks (rows of pair i, columns of pair k), V <- V J
-      for (int e = t; e < half * half + L * half; e += nt) {
-        if (e < half * half) {
-          const int i = e / half, k = e - i * half;   // one division a task (few tasks a thread)
-          const int p = top[i], q = bot[i], pk = top[k], qk = bot[k];
-          const float ci = cs[i], si = sn[i], ck = cs[k], sk = sn[k];
-          const float app = A(p, pk), apq = A(p, qk), aqp = A(q, pk), aqq = A(q, qk);
-          // columns: [c_k -s_k; s_k c_k] on the right, then rows with (c_i, s_i) on the left
-          const float bpp = ck * app - sk * apq, bpq = sk * app + ck * apq;
-          const float bqp = ck * aqp - sk * aqq, bqq = sk * aqp + ck * aqq;
-          A(p, pk) = ci * bpp - si * bqp;
-          A(p, qk) = ci * bpq - si * bqq;
-          A(q, pk) = si * bpp + ci * bqp;
-          A(q, qk) = si * bpq + ci * bqq;
+      auto load = [&](int e, JTask& k) {
+        k.live = false;
+        if (e >= ntask) return;
+        if (e < nblk) {
+          const int i = div_small(e, mag_half), kk = e - i * half;
+          k.ci = cs[i];
+          k.si = sn[i];
+          k.ck = cs[kk];
+          k.sk = sn[kk];
+          if (k.si == 0.f && k.sk == 0.f) return;
+          int p, q, pk, qk;
+          pair(i, p, q);
+          pair(kk, pk, qk);
+          k.o0 = p * LS + pk;
+          k.o1 = p * LS + qk;
+          k.o2 = q * LS + pk;
+          k.o3 = q * LS + qk;
+          k.x0 = jsm[k.o0];
+          k.x1 = jsm[k.o1];
+          k.x2 = jsm[k.o2];
+          k.x3 = jsm[k.o3];
+          k.two = true;
         } else {
-          const int f = e - half * half;
-          const int i = f / L, row = f - i * L;
-          const int p = top[i], q = bot[i];
-          const float c = cs[i], sv = sn[i];
-          const float vp = V(row, p), vq = V(row, q);
-          V(row, p) = c * vp - sv * vq;
-          V(row, q) = sv * vp + c * vq;
+          const int f = e - nblk;
+          const int i = div_small(f, mag_L), row = f - i * L;
+          k.ck = cs[i];
+          k.sk = sn[i];
+          if (k.sk == 0.f) return;
+          int p, q;
+          pair(i, p, q);
+          k.o0 = voff + row * LS + p;
+          k.o1 = voff + row * LS + q;
+          k.x0 = jsm[k.o0];
+          k.x1 = jsm[k.o1];
+          k.two = false;
         }
+        k.live = true;
+      };
+      auto store = [&](const JTask& k) {
+        if (!k.live) return;
+        // columns: [c_k -s_k; s_k c_k] on the right, then rows with (c_i, s_i) on the left
+        const float b0 = k.ck * k.x0 - k.sk * k.x1, b1 = k.sk * k.x0 + k.ck * k.x1;
+        if (k.two) {
+          const float b2 = k.ck * k.x2 - k.sk * k.x3, b3 = k.sk * k.x2 + k.ck * k.x3;
+          jsm[k.o0] = k.ci * b0 - k.si * b2;
+          jsm[k.o1] = k.ci * b1 - k.si * b3;
+          jsm[k.o2] = k.si * b0 + k.ci * b2;
+          jsm[k.o3] = k.si * b1 + k.ci * b3;
+        } else {
+          jsm[k.o0] = b0;
+          jsm[k.o1] = b1;
+        }
+      };
+      for (int e = t; e < ntask; e += 2 * nt) {
+        JTask k0, k1;
+        load(e, k0);
+        load(e + nt, k1);
+        store(k0);
+        store(k1);
       }
       __syncthreads();
     }
-    const int any = rotated;   // read by every thread before thread 0 clears it again
-    __syncthreads();
-    if (!any) break;
+    if (!sweep_rot) break;
   }
-  // order by eigenvalue, descending (selection; ell <= 128)
-  if (t == 0) {
-    for (int i = 0; i < L; ++i) order[i] = i;
-    for (int i = 0; i < r; ++i) {
-      int best = i;
-      for (int k = i + 1; k < L; ++k)
-        if (A(order[k], order[k]) > A(order[best], order[best])) best = k;
-      const int tmp = order[i];
-      order[i] = order[best];
-      order[best] = tmp;
+  // order by eigenvalue, descending: the rank of each diagonal entry (ties by index)
+  for (int j = t; j < L; j += nt) order[j] = j;
+  __syncthreads();
+  for (int j = t; j < L; j += nt) {
+    const float dj = A(j, j);
+    int rank = 0;
+    for (int k = 0; k < L; ++k) {
+      const float dk = A(k, k);
+      rank += (dk > dj || (dk == dj && k < j)) ? 1 : 0;
     }
+    if (rank < r) order[rank] = j;
   }
   __syncthreads();
   for (int e = t; e < ell * r; e += nt) {
