@@ -444,6 +444,19 @@ def run_warmstart(args):
     ctx.close()
 
 
+def nvtx_mark(push):
+    """Open (push) or close the NVTX range "timed" around the timed steps; a no-op where this
+    PyTorch build has no NVTX."""
+    import torch
+    try:
+        if push:
+            torch.cuda.nvtx.range_push("timed")
+        else:
+            torch.cuda.nvtx.range_pop()
+    except (RuntimeError, AttributeError):
+        pass
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -548,6 +561,7 @@ def main():
         if profile:
             N.nmf_phase_times(ctx, reset=True)
             N.nmf_set_profiling(ctx, True)
+            nvtx_mark(True)   # the timed region, for `ncu --nvtx --nvtx-include timed/`
         for _ in range(steps):
             if world > 1:
                 torch.distributed.barrier()
@@ -564,6 +578,7 @@ def main():
             checks.append(N.nmf_last_solve_info(ctx)[1])
         phases = None
         if profile:
+            nvtx_mark(False)
             N.nmf_set_profiling(ctx, False)
             phases = N.nmf_phase_times(ctx, reset=True)
         return ts, its, errs, ctx.launches - l0, phases, checks
