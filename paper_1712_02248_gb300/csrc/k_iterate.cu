@@ -530,16 +530,20 @@ __device__ __forceinline__ void axpy16x2(float xa, float xb, const float* __rest
   }
 }
 
-// tab[k][qpos(j)] = src(k, j) for j < r, 0 elsewhere (pads included), k < rows
+// tab[k][20 (j / 16) + j % 16] = src(k, j) for j < r, 0 elsewhere (pads included), k < rows;
+// the loads are batched (a block fills ~10^4 entries from L2 before its first pass)
 template <typename Src>
 __device__ __forceinline__ void fill_quarter_table(float* __restrict__ tab, int rows, int r,
                                                    Src src) {
-  for (int e = threadIdx.x; e < rows * kQP; e += blockDim.x) {
-    const int k = e / kQP, pos = e - k * kQP;
-    const int quarter = pos / 20, within = pos - quarter * 20;
-    const int j = quarter * 16 + within;
-    tab[e] = (within < 16 && j < r) ? src(k, j) : 0.f;
-  }
+  batched_copy(
+      rows * kQP,
+      [&](int e) {
+        const int k = e / kQP, pos = e - k * kQP;
+        const int quarter = pos / 20, within = pos - quarter * 20;
+        const int j = quarter * 16 + within;
+        return (within < 16 && j < r) ? src(k, j) : 0.f;
+      },
+      [&](int e, float v) { tab[e] = v; });
 }
 
 template <int RULE>
@@ -854,6 +858,20 @@ cudaError_t run(const Launcher& L, const IterArgs& a, int iters, void* ws) {
   if ((err = cudaFuncSetAttribute(K.h, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   static_cast<int>(K.sh_h))) != cudaSuccess)
     return err;
+  // update grids: one wave of resident blocks at most, so that a block fills its shared tables
+  // once for several passes
+  int dev = 0, sms = 0, occ_w = 0, occ_h = 0;
+  if ((err = cudaGetDevice(&dev)) != cudaSuccess) return err;
+  if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+    return err;
+  if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_w, K.w, K.threads, K.sh_w)) !=
+      cudaSuccess)
+    return err;
+  if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_h, K.h, K.threads, K.sh_h)) !=
+      cudaSuccess)
+    return err;
+  const unsigned grid_w = grid_cap(a.m, K.rows, (occ_w > 0 ? occ_w : 1) * sms);
+  const unsigned grid_h = grid_cap(a.n, K.rows, (occ_h > 0 ? occ_h : 1) * sms);
   const int normalize = (a.rule == 0) ? 1 : 0;
   for (int it = 0; it < iters; ++it) {
     // W half-step
@@ -861,7 +879,7 @@ cudaError_t run(const Launcher& L, const IterArgs& a, int iters, void* ws) {
     sum_slots_kernel<<<grid_cap(static_cast<int64_t>(r) * ell * 32, 256, 1 << 20), 256, 0,
                        L.stream>>>(w.Hpart, static_cast<int>(nb_n), r * ell, w.Ht);
     gram_rows_kernel<<<1, 512, sh_gram, L.stream>>>(w.Ht, r, ell, w.G);
-    K.w<<<grid_cap(a.m, K.rows, 4096), K.threads, K.sh_w, L.stream>>>(a.Xchk, w.Ht, w.G, a.m,
+    K.w<<<grid_w, K.threads, K.sh_w, L.stream>>>(a.Xchk, w.Ht, w.G, a.m,
                                                                           r, ell, a.eps, a.W);
     // H half-step
     wt_k<<<static_cast<unsigned>(nb_m), 256, sh_wt, L.stream>>>(a.QL, a.W, a.m, r, ell, w.Wpart);
@@ -869,7 +887,7 @@ cudaError_t run(const Launcher& L, const IterArgs& a, int iters, void* ws) {
                        L.stream>>>(w.Wpart, static_cast<int>(nb_m), ell * r + r, w.Wraw);
     finish_wt_kernel<<<1, 512, sh_fin, L.stream>>>(w.Wraw, r, ell, normalize, w.Wt, w.GH,
                                                    w.scale);
-    K.h<<<grid_cap(a.n, K.rows, 4096), K.threads, K.sh_h, L.stream>>>(
+    K.h<<<grid_h, K.threads, K.sh_h, L.stream>>>(
         a.Xhat, w.Wt, w.GH, w.scale, a.n, r, ell, a.alpha, a.beta, a.eps, a.H);
     L.count(8);
     if (normalize) {
