@@ -44,12 +44,15 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", choices=["fp32", "bf16"], default=None,
                     help="run one short solve (20 iterations) for a profiler's launch list")
-    ap.add_argument("--config", choices=["dense", "batched", "images", "warmstart", "passes"],
+    ap.add_argument("--config", choices=["dense", "batched", "images", "warmstart", "passes",
+                                         "iterate"],
                     default="dense",
                     help="batched: 256 uneven problems through nmf_solve_batched against one "
                          "nmf_solve per problem; images: 4096 x 100000 image-like data, r = 50, "
                          "BF16 against FP32; warmstart: learned warm start on 8192 x 2048, "
-                         "r = 16 (separate JSON lines; not the headline)")
+                         "r = 16; passes: one dual pass per element type of X; iterate: "
+                         "nmf_iterate alone on image-shaped operands (separate JSON lines; "
+                         "not the headline)")
     ap.add_argument("--train-count", type=int, default=256,
                     help="warmstart: planted training matrices (the full recipe uses 10000)")
     ap.add_argument("--heldout", type=int, default=32,
@@ -321,6 +324,57 @@ def run_images(args):
     ctx.close()
 
 
+def run_iterate(args):
+    """nmf_iterate alone (FastHALS-RP) on operands of the image workload's shape: m = 4096,
+    n = 100000 with (r, l) = (50, 70) and (64, 64), both above the persistent kernel's r <= 48
+    and so on the per-stage kernels, and (20, 40) on the persistent kernel. Q_L, Q_R are scaled
+    Gaussian draws and X_hat, X_chk the projections of a U[0, 1) X (the values do not change the
+    work); W, H U[0, 1). Milliseconds per iteration: CUDA events on the library's stream around
+    20 iterations after --warmup calls of 5."""
+    import torch
+    from paper_1712_02248_gb300 import nmf_rp as N
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    ctx = N.Context(0)
+    m, n, timed = 4096, 100000, 20
+    out = {}
+    for r, ell in ((50, 70), (64, 64), (20, 40)):
+        g = torch.Generator(device=dev)
+        g.manual_seed(args.seed + 3)
+        QL = torch.randn(m, ell, device=dev, generator=g) / m ** 0.5
+        QR = torch.randn(n, ell, device=dev, generator=g) / n ** 0.5
+        X = torch.rand(m, n, device=dev, generator=g)
+        Xhat = (QL.T @ X).contiguous()
+        Xchk = (X @ QR).contiguous()
+        del X
+        W0 = torch.rand(m, r, device=dev, generator=g)
+        H0 = torch.rand(r, n, device=dev, generator=g)
+        p = N.params(m, n, r, ell, power_iters=3, prec="fp32", seed=args.seed + 5)
+        W, H = W0.clone(), H0.clone()
+        for _ in range(max(1, args.warmup)):
+            N.nmf_iterate(ctx, p, QL, QR, Xhat, Xchk, W, H, 5)
+        with torch.cuda.stream(ctx.stream):
+            W.copy_(W0)
+            H.copy_(H0)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(ctx.stream)
+        N.nmf_iterate(ctx, p, QL, QR, Xhat, Xchk, W, H, timed)
+        b.record(ctx.stream)
+        b.synchronize()
+        out[f"r{r}_l{ell}"] = {"ms_per_iter": a.elapsed_time(b) / timed,
+                               "path": "per-stage" if r > 48 else "persistent"}
+        del QL, QR, Xhat, Xchk, W0, H0, W, H
+    print(json.dumps({
+        "metric": "nmf_iterate time per FastHALS-RP iteration at 4096 x 100000",
+        "value": out["r50_l70"]["ms_per_iter"], "unit": "ms", "n_gpus": 1,
+        "higher_is_better": False, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "image-shaped iteration operands", "m": m, "n": n,
+                   "iterations_timed": timed},
+        "cases": out}))
+    ctx.close()
+
+
 def run_passes(args):
     """One fused dual pass over X (Y = X V and Z = X^T U) per element type of X: FP32 (SIMT),
     BF16 and FP8 E4M3 with per-tile scales (tensor cores), at the dense workload's shape
@@ -465,7 +519,7 @@ def main():
     if args.config != "dense":
         if int(os.environ.get("RANK", 0)) == 0:
             {"batched": run_batched, "images": run_images, "warmstart": run_warmstart,
-             "passes": run_passes}[args.config](args)
+             "passes": run_passes, "iterate": run_iterate}[args.config](args)
         return
     import torch
     rank, local_rank, world = dist_env()
