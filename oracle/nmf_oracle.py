@@ -336,7 +336,8 @@ def residual(X, W, H):
 def compressed_sq_error(x2, QL, Xhat, W, H):
     """Estimate of ||X - W H||_F^2 from compressed data only (a monitor, no X read):
     ||X||^2 - 2 <W_tld^T X_hat, H> + <W^T W, H H^T>, using X ~ Q_L X_hat (Section 3, Eq. 3.4).
-    Exact when Q_L Q_L^T X = X. Parity unpinned beyond that special case."""
+    With P = Q_L Q_L^T it equals ||X - W H||^2 + 2 <(I - P) X, W H> for any inputs (the cross
+    term sees only P X), hence exact when P X = X; both are pinned."""
     W = np.asarray(W, np.float64)
     H = np.asarray(H, np.float64)
     Wt = np.asarray(QL, np.float64).T @ W

@@ -386,6 +386,23 @@ def test_compressed_error_estimate_is_exact_with_square_projection():
     assert abs(O.compressed_sq_error(x2, QL, Xhat, W, H) - e2) <= 1e-10 * x2
 
 
+def test_compressed_error_estimate_identity_for_any_projection():
+    """For any orthonormal Q_L (P = Q_L Q_L^T) the compressed estimate is
+    ||X||^2 - 2 <P X, W H> + ||W H||^2 = ||X - W H||^2 + 2 <(I - P) X, W H>: the cross term sees
+    only the projected data. Checked against the exact residual of the full X and the
+    complementary projector, with l well below the rank of X so that the correction is large."""
+    rng = _rng(14)
+    m, n, ell, r = 50, 30, 8, 4
+    X = rng.uniform(0, 1, (m, n))
+    QL, _ = np.linalg.qr(rng.standard_normal((m, ell)))
+    Xhat = QL.T @ X
+    W, H = rng.uniform(0, 1, (m, r)), rng.uniform(0, 1, (r, n))
+    _, e2, x2 = O.residual(X, W, H)
+    corr = 2.0 * float(np.sum((X - QL @ (QL.T @ X)) * (W @ H)))
+    assert abs(corr) > 1e-3 * x2
+    assert abs(O.compressed_sq_error(x2, QL, Xhat, W, H) - (e2 + corr)) <= 1e-10 * x2
+
+
 def test_nndsvd_rank_one_and_nonnegative():
     """NNDSVD of a positive rank-1 matrix reproduces it with its first component."""
     rng = _rng(14)
