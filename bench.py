@@ -65,6 +65,18 @@ def dist_env():
             int(os.environ.get("WORLD_SIZE", 1)))
 
 
+def max_over_ranks(x, device):
+    """The largest of the ranks' values, on every rank (the job takes as long as its slowest
+    replica); x itself without an initialised process group of more than one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def workload_config(init, prec):
     w = WORKLOAD
     return {"workload": f"dense planted X {w['m']}x{w['n']} (Exp(1) factors, 1% noise), "
@@ -650,11 +662,7 @@ def main():
     ts, its, errs, launches, phases, checks = timed(*headline, args.steps, args.warmup,
                                                     profile=True)
     clk = clocks.stop()
-    t_local = statistics.median(ts)
-    if world > 1:
-        tt = torch.tensor([t_local], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_local = float(tt.item())
+    t_local = max_over_ranks(statistics.median(ts), dev)
     results[f"{headline[0]}+{headline[1]}"] = {"s": statistics.median(ts), "iters": its[0],
                                                "rel_err": errs[0], "exact_checks": checks[0]}
 
@@ -677,6 +685,7 @@ def main():
         stream.synchronize()
         if i > 0:
             e2e.append(a.elapsed_time(b) / 1e3)
+    e2e_value = max_over_ranks(statistics.median(e2e), dev)
 
     # rooflines (CUDA events on the launching stream around every phase, timed region above)
     peaks = {}
@@ -732,7 +741,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": t_local * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": headline[0], "data": "synthetic",
             "config": workload_config(headline[1], headline[0]),
-            "e2e": {"value": statistics.median(e2e), "unit": "s", "h2d_bytes_per_step": 4 * m * n,
+            "e2e": {"value": e2e_value, "unit": "s", "h2d_bytes_per_step": 4 * m * n,
                     "d2h_bytes_per_step": 4 * (m * r + r * n)},
             "gpu_launches": launches, "gpu_launches_per_step": launches // args.steps,
             "roofline": roofline, "roofline_hbm": roofline_hbm, "cpu_baseline": cpu, "clocks": clk,
