@@ -720,10 +720,10 @@ def main():
                 "dominant_phase": dom,
                 "phase_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in phases.items()},
                 "phase_spans_per_step": {k: v[1] // args.steps for k, v in phases.items()}}
-    # DRAM bytes of one dual_pass_tc_kernel launch from an ncu capture of this workload
+    # DRAM bytes of the dual pass: none current. The last capture of the BF16 launch
     # (profiles/dual_pass_tc_kernel_dense_20000x5000_l40_bf16.md: 203.58 MB read, 6.04 MB
-    # written); per launch like `achieved`
-    dp_traffic = 203.58e6 + 6.04e6 if headline[0] == "bf16" else None
+    # written, no re-reads) predates the FP8 variant's changes to the kernel's source
+    dp_traffic = None
     roofline_hbm = {"bound": "hbm", "achieved": dp_achieved, "peak": hbm_peak, "unit": "GB/s",
                     "frac": dp_achieved / hbm_peak, "traffic": dp_traffic,
                     "kernel": "dual pass over X (dual_pass_tc_kernel + operand prep + slot sums)",
