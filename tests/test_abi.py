@@ -64,3 +64,21 @@ def test_create_without_gpu_fails_cleanly(N):
     st = N._c["nmf_create"](ctypes.byref(h), 0, None)
     assert st == 2 and not h.value    # NMF_ERR_CUDA, no context
     assert N._c["nmf_sync"](None) == 1
+
+
+@pytest.mark.parametrize("m,n", [(1, 1), (31, 17), (32, 32), (33, 100), (20000, 5000),
+                                 (4096, 100000), (7, 16)])
+def test_quantized_bytes_match_the_copy_layouts(N, m, n):
+    """Size query of the low-precision copies (host arithmetic, no GPU): BF16 2mn, FP32 4mn;
+    FP8 codes with rows padded to 16 bytes, then the E8M0 bytes from a 256-byte boundary, one
+    per 32 x 32 tile (the layout the oracle states in fp8_layout)."""
+    import oracle as O
+    assert N.nmf_quantized_bytes("bf16", m, n) == 2 * m * n
+    assert N.nmf_quantized_bytes("fp32", m, n) == 4 * m * n
+    assert N.nmf_quantized_bytes("fp8", m, n) == O.fp8_layout(m, n)[2]
+
+
+def test_quantized_bytes_of_invalid_requests_is_zero(N):
+    assert N.nmf_quantized_bytes("fp8", 0, 10) == 0
+    assert N.nmf_quantized_bytes("bf16", 10, 0) == 0
+    assert N.nmf_quantized_bytes(9, 10, 10) == 0
