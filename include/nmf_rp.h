@@ -199,6 +199,11 @@ nmf_status nmf_compress(nmf_ctx* ctx, const nmf_params* p, const void* X, int64_
  * components j = 1..r (Gauss-Seidel), normalisation of the columns of W with the scale moved to
  * the rows of H, then the whole H sweep. MU-RP (Algorithm 3): the semi-NMF multiplicative rule on
  * W, then on H. Never reads X.
+ * Device arrays owned by the caller, row-major: QL (m x l), QR (n x l), Xhat (l x n), Xchk
+ * (m x l), W (m x r), H (r x n). Asynchronous on the context's stream. r <= 48 with the
+ * problem's slices fitting on chip runs as one persistent launch per call; otherwise (or with
+ * NMF_FLAG_STAGED_ITERATE) one launch per stage and iteration. r > 64: NMF_ERR_UNSUPPORTED;
+ * Invalid parameters (r > l, l > 128 or > min(m, n), ...): NMF_ERR_INVALID_ARG.
  */
 nmf_status nmf_iterate(nmf_ctx* ctx, const nmf_params* p, const float* QL, const float* QR,
                        const float* Xhat, const float* Xchk, float* W, float* H, int32_t iters);
