@@ -21,9 +21,14 @@ Functions and their pins (tests/test_oracle_pins.py):
   mu_step                   Lee-Seung monotonicity on full data
   residual / objective      closed forms on constructed inputs
   compressed_sq_error       equals the exact squared error when Q_L is square
-  nndsvd_compressed         exact for a rank-1 non-negative matrix; non-negativity
+  nndsvd_compressed         exact for a rank-1 non-negative matrix; exact for a block-diagonal
+                            non-negative matrix (every component j >= 1 reached); each component
+                            equals the dominant quadrant of s_j u_j v_j^T (mixed signs)
+  monitor_estimate          equals ||X - W H||^2 + 2 <X - X_q, W H - X> when Q_L is square
+  rounding_term             closed form on a constructed copy; vanishes for an exact copy
   gini                      closed forms (uniform -> 0, one-hot -> 1 - 1/N)
   philox4x32_10             published known-answer vectors of the generator
+  philox_normal_np          element for element equal to philox_normal (the scalar definition)
 """
 from __future__ import annotations
 
@@ -33,9 +38,9 @@ __all__ = [
     "qr_orthonormal", "sketch", "power_product", "compress",
     "fasthals_rp_step", "hals_rp_step", "mu_rp_step",
     "fasthals_step", "mu_step", "semi_nmf_mu_step",
-    "residual", "objective", "compressed_sq_error",
+    "residual", "objective", "compressed_sq_error", "monitor_estimate", "rounding_term",
     "nndsvd_compressed", "gini", "solve", "iterate",
-    "philox4x32_10", "philox_normal", "memory_floats_rp",
+    "philox4x32_10", "philox_normal", "philox_normal_np", "memory_floats_rp",
     "EPS_MU",
 ]
 
@@ -346,6 +351,22 @@ def compressed_sq_error(x2, QL, Xhat, W, H):
     return x2 - 2.0 * cross + quad
 
 
+def rounding_term(X, Xq):
+    """<X - X_q, X>: how far a low-precision copy X_q of X moves the cross term <X, W H> of the
+    error when the compressed data are made from X_q (plain FP64 sum over all entries)."""
+    X = np.asarray(X, np.float64)
+    return float(np.sum((X - np.asarray(Xq, np.float64)) * X))
+
+
+def monitor_estimate(x2, QL, Xhat, W, H, xq_term=0.0):
+    """Error monitor of a solve whose compressed data X_hat = Q_L^T X_q come from a copy X_q of X:
+    ||X - W H||^2 ~ ||X||^2 - 2 (<W_tld^T X_hat, H> + <X - X_q, X>) + <W^T W, H H^T>.
+    The cross term <X, W H> is split as <X_q, W H> + <X - X_q, W H>; the first is replaced by its
+    projection (Section 3, Eq. 3.4), the second by <X - X_q, X> (W H ~ X near a solution).
+    With Q_L square the estimate equals ||X - W H||^2 + 2 <X - X_q, W H - X> exactly (pinned)."""
+    return compressed_sq_error(x2, QL, Xhat, W, H) - 2.0 * float(xq_term)
+
+
 # --------------------------------------------------------------------------------------------
 # Initialisation and diagnostics
 # --------------------------------------------------------------------------------------------
@@ -479,3 +500,38 @@ def philox_normal(rows, cols, seed, stream):
             if e < total:
                 out[e] = z[t]
     return out.reshape(rows, cols)
+
+
+def philox_normal_np(rows, cols, seed, stream):
+    """philox_normal for large matrices: the same definition (counter, key, rounds, uniform map,
+    Box-Muller) evaluated on numpy arrays of counters at once. Pinned element for element
+    against the scalar philox_normal."""
+    total = rows * cols
+    nblk = (total + 3) // 4
+    b = np.arange(nblk, dtype=np.uint64)
+    m32 = np.uint64(_MASK32)
+    c0 = b & m32
+    c1 = b >> np.uint64(32)
+    c2 = np.full(nblk, np.uint64(stream & _MASK32))
+    c3 = np.zeros(nblk, dtype=np.uint64)
+    k0 = np.uint64(seed & _MASK32)
+    k1 = np.uint64((seed >> 32) & _MASK32)
+    M0, M1 = np.uint64(_PHILOX_M0), np.uint64(_PHILOX_M1)
+    for rnd in range(10):
+        if rnd > 0:
+            k0 = (k0 + np.uint64(_PHILOX_W0)) & m32
+            k1 = (k1 + np.uint64(_PHILOX_W1)) & m32
+        p0 = M0 * c0          # < 2^64: exact in uint64
+        p1 = M1 * c2
+        hi0, lo0 = p0 >> np.uint64(32), p0 & m32
+        hi1, lo1 = p1 >> np.uint64(32), p1 & m32
+        c0, c1, c2, c3 = hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0
+    u = [((x >> np.uint64(8)).astype(np.float64) + 0.5) * 2.0 ** -24 for x in (c0, c1, c2, c3)]
+    rad0 = np.sqrt(-2.0 * np.log(u[0]))
+    rad1 = np.sqrt(-2.0 * np.log(u[2]))
+    z = np.empty((nblk, 4), dtype=np.float64)
+    z[:, 0] = rad0 * np.cos(2 * np.pi * u[1])
+    z[:, 1] = rad0 * np.sin(2 * np.pi * u[1])
+    z[:, 2] = rad1 * np.cos(2 * np.pi * u[3])
+    z[:, 3] = rad1 * np.sin(2 * np.pi * u[3])
+    return z.ravel()[:total].reshape(rows, cols)

@@ -420,6 +420,92 @@ def test_nndsvd_rank_one_and_nonnegative():
     assert O.residual(X2, W, H)[0] < 0.9
 
 
+def test_nndsvd_block_diagonal_is_exact_for_every_component():
+    """NNDSVD (Boutsidis & Gallopoulos 2008) on X = sum_k s_k a_k b_k^T with non-negative a_k, b_k
+    on disjoint row and column blocks: the singular pairs are (a_k, b_k) up to a joint sign, each
+    has one non-zero sign part, so every component j >= 1 must reproduce its block exactly and
+    W H = X. The block scales are distinct so the singular values are simple."""
+    rng = _rng(15)
+    rows, cols = [9, 7, 11, 6, 8], [5, 8, 4, 7, 6]
+    m, n, r = sum(rows), sum(cols), len(rows)
+    X = np.zeros((m, n))
+    i0 = c0 = 0
+    for k in range(r):
+        a = rng.uniform(0.2, 1.0, rows[k])
+        b = rng.uniform(0.2, 1.0, cols[k])
+        X[i0:i0 + rows[k], c0:c0 + cols[k]] = (5.0 - k) * np.outer(a, b) / (
+            np.linalg.norm(a) * np.linalg.norm(b))
+        i0 += rows[k]
+        c0 += cols[k]
+    X = X[rng.permutation(m)][:, rng.permutation(n)]
+    ell = r + 3
+    QL, QR = O.sketch(X, rng.standard_normal((n, ell)), rng.standard_normal((m, ell)), 1)
+    Xhat, _ = O.compress(X, QL, QR)
+    W, H = O.nndsvd_compressed(QL, Xhat, r)
+    assert (W >= 0).all() and (H >= 0).all()
+    assert np.abs(W @ H - X).max() <= 1e-12 * np.abs(X).max()
+    # component j carries the block of singular value 5 - j (the j-th largest)
+    for j in range(r):
+        assert abs(np.linalg.norm(np.outer(W[:, j], H[j])) - (5.0 - j)) <= 1e-12
+
+
+def test_nndsvd_component_is_dominant_quadrant_of_singular_pair():
+    """Mixed signs. NNDSVD keeps, for each singular triplet (s_j, u_j, v_j) with j >= 1, the larger
+    (in Frobenius norm) of the two non-negative quadrants of s_j u_j v_j^T: the part on rows with
+    u > 0 and columns with v > 0, or the part on rows with u < 0 and columns with v < 0 (negated).
+    The quadrants are cut from the m x n rank-1 matrix itself and the triplets come from an SVD
+    of the full Q_L X_hat (not of X_hat); component 0 is s_0 |u_0| |v_0|^T."""
+    rng = _rng(16)
+    m, n, ell, r = 40, 30, 9, 6
+    X = rng.uniform(0, 1, (m, n))
+    QL, QR = O.sketch(X, rng.standard_normal((n, ell)), rng.standard_normal((m, ell)), 1)
+    Xhat, _ = O.compress(X, QL, QR)
+    W, H = O.nndsvd_compressed(QL, Xhat, r)
+    U, s, Vt = np.linalg.svd(QL @ Xhat)
+    both = 0
+    for j in range(r):
+        C = s[j] * np.outer(U[:, j], Vt[j])
+        got = np.outer(W[:, j], H[j])
+        if j == 0:
+            want = s[0] * np.outer(np.abs(U[:, 0]), np.abs(Vt[0]))
+        else:
+            pp = np.where((U[:, j] > 0)[:, None] & (Vt[j] > 0)[None, :], C, 0.0)
+            nn = np.where((U[:, j] < 0)[:, None] & (Vt[j] < 0)[None, :], C, 0.0)
+            want = pp if np.linalg.norm(pp) >= np.linalg.norm(nn) else nn
+            both += np.linalg.norm(pp) > 0 and np.linalg.norm(nn) > 0
+        assert np.abs(got - want).max() <= 1e-10 * s[0]
+    assert both >= r - 2  # the mixed-sign branch is exercised, not only one-signed pairs
+
+
+def test_monitor_estimate_identity_with_square_projection():
+    """With Q_L square (P = I) the monitor of a solve on a copy X_q of X is
+    ||X||^2 - 2 <X_q, W H> - 2 <X - X_q, X> + ||W H||^2 = ||X - W H||^2 + 2 <X - X_q, W H - X>
+    (expand both sides); it is exact at W H = X, and equals the compressed estimate for X_q = X."""
+    rng = _rng(17)
+    m, n, r = 14, 14, 3
+    X = rng.uniform(0, 1, (m, n))
+    Xq = X + 1e-2 * rng.standard_normal((m, n))
+    QL, _ = np.linalg.qr(rng.standard_normal((m, m)))
+    Xhat = QL.T @ Xq
+    W, H = rng.uniform(0, 1, (m, r)), rng.uniform(0, 1, (r, n))
+    _, e2, x2 = O.residual(X, W, H)
+    t = O.rounding_term(X, Xq)
+    want = e2 + 2.0 * float(np.sum((X - Xq) * (W @ H - X)))
+    assert abs(O.monitor_estimate(x2, QL, Xhat, W, H, t) - want) <= 1e-10 * x2
+    Wx, Hx = X.copy(), np.eye(n)
+    assert abs(O.monitor_estimate(x2, QL, Xhat, Wx, Hx, t)) <= 1e-10 * x2
+    assert O.monitor_estimate(x2, QL, QL.T @ X, W, H, 0.0) == O.compressed_sq_error(
+        x2, QL, QL.T @ X, W, H)
+
+
+def test_rounding_term_closed_form():
+    """<X - X_q, X> for a copy that moves every entry by the same fraction: X_q = (1 - d) X gives
+    d ||X||^2; an exact copy gives 0."""
+    X = np.arange(1.0, 13.0).reshape(3, 4)
+    assert O.rounding_term(X, X) == 0.0
+    assert abs(O.rounding_term(X, 0.75 * X) - 0.25 * float(np.sum(X * X))) <= 1e-12
+
+
 def test_gini_closed_forms():
     """Section 5.1 Gini formula: all-equal entries give 0, a single non-zero gives 1 - 1/N."""
     assert abs(O.gini(np.ones((4, 5)))) <= 1e-15
@@ -466,6 +552,15 @@ def test_philox_normal_box_muller_pairs():
     u0 = ((x[0] >> 8) + 0.5) * 2.0 ** -24
     assert abs(Z[0] ** 2 + Z[1] ** 2 + 2 * np.log(u0)) <= 1e-12
     assert abs(Z.mean()) < 0.06 and abs(Z.std() - 1) < 0.05
+
+
+def test_philox_normal_np_equals_scalar_definition():
+    """The array form of the generator gives the scalar definition's values element for element,
+    including a seed above 2^32, a non-multiple-of-4 size and both streams."""
+    for rows, cols, seed, stream in [(13, 7, (1 << 40) + 99, 1), (5, 3, 0, 0), (31, 9, 123, 5)]:
+        a = O.philox_normal(rows, cols, seed=seed, stream=stream)
+        b = O.philox_normal_np(rows, cols, seed=seed, stream=stream)
+        assert np.array_equal(a, b)
 
 
 # ---------------------------------------------------------------- learned warm start
