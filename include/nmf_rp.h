@@ -124,6 +124,27 @@ enum {
   NMF_PHASE_COUNT = 6
 };
 nmf_status nmf_set_profiling(nmf_ctx* ctx, int32_t on);
+/*
+ * Polling budget, in SM clock cycles, of each grid-barrier wait of the persistent iteration
+ * kernel in later launches on this context (0 restores the default of about two seconds; < 0 is
+ * NMF_ERR_INVALID_ARG). A wait that runs out latches NMF_ERR_TIMEOUT, raises the launch's abort
+ * flag and every block leaves the kernel (no copies are in flight in that kernel); the next
+ * synchronising call returns the status and clears it, and W, H then hold partial updates.
+ * For testing the time-out path: a budget of a few cycles makes the first barrier run out.
+ * The tensor-core pass keeps its own fixed budget (its waits guard asynchronous copies).
+ */
+nmf_status nmf_set_wait_limit(nmf_ctx* ctx, int64_t cycles);
+/*
+ * Terms of the error monitor (no read of X) that the last persistent nmf_iterate / nmf_solve
+ * left on this context, and the sums the last nmf_solve took of X. Synchronises the stream.
+ *   terms[0] = <W_tld^T X_hat, H> (FP32; W_tld = Q_L^T W) at the last iteration's W, H
+ *   terms[1] = <W^T W, H H^T>     (FP32) at the same W, H
+ *   terms[2] = ||X||_F^2          (FP64) of the last nmf_solve
+ *   terms[3] = <X - X_q, X>       (FP64) of the last nmf_solve with a BF16 copy X_q (else 0)
+ * The solve's estimate of ||X - W H||^2 is terms[2] - 2 (terms[0] + terms[3]) + terms[1]
+ * (Section 3, Eq. 3.4: X replaced by Q_L Q_L^T X in the cross term).
+ */
+nmf_status nmf_monitor_terms(nmf_ctx* ctx, double* terms);
 nmf_status nmf_phase_times(nmf_ctx* ctx, double* ms, int64_t* counts, int32_t reset);
 /* Bytes of device workspace nmf_solve needs for these parameters (other calls need less). */
 nmf_status nmf_workspace_size(const nmf_params* p, size_t* bytes);
@@ -223,9 +244,10 @@ nmf_status nmf_residual(nmf_ctx* ctx, const nmf_params* p, const float* X, int64
  * The paper has no counterpart: this is a service entry point for callers that cannot allocate
  * when they need the residual, such as a serving loop whose device memory is all handed to its
  * own pools, or code that must not stall the device's other streams (cudaFree synchronises the
- * whole device). The per-block partial sums live in a fixed 32 KB array in the library's global
- * memory (two doubles per block; the grid is at most 4 blocks per SM, so devices with up to 512
- * SMs fit) instead of a workspace. Nothing in it has to start at zero.
+ * whole device). The per-block partial sums live in a fixed array of 33,024 bytes in the
+ * library's global memory (two doubles per block plus 256 bytes of alignment slack; the grid is
+ * at most 4 blocks per SM, so devices with up to 512 SMs fit) instead of a workspace. Nothing in
+ * it has to start at zero.
  *
  * device: the CUDA device of X, W, H and out_dev; it is made current for the call.
  * stream: a cudaStream_t of that device (NULL = legacy default stream).
@@ -237,7 +259,8 @@ nmf_status nmf_residual(nmf_ctx* ctx, const nmf_params* p, const float* X, int64
  *
  * The first call on a device does a one-time set-up: it resolves the array's device address,
  * which can load the library's device code onto the device; make that first call before any
- * stream capture. Calls on one device share the array, so two calls in flight at the same time
+ * stream capture. The address is kept for the life of the process: after cudaDeviceReset on
+ * that device it is stale, so do not call this entry point on a device that has been reset. Calls on one device share the array, so two calls in flight at the same time
  * (on different streams, or from different threads) race: order them on one stream or with
  * events.
  * Returns NMF_ERR_INVALID_ARG for NULL pointers, bad sizes or a device that cannot be made

@@ -29,6 +29,7 @@ Functions and their pins (tests/test_oracle_pins.py):
   gini                      closed forms (uniform -> 0, one-hot -> 1 - 1/N)
   philox4x32_10             published known-answer vectors of the generator
   philox_normal_np          element for element equal to philox_normal (the scalar definition)
+  solve_to_target           stops at the same check as `solve` with a residual at every check
 """
 from __future__ import annotations
 
@@ -39,7 +40,7 @@ __all__ = [
     "fasthals_rp_step", "hals_rp_step", "mu_rp_step",
     "fasthals_step", "mu_step", "semi_nmf_mu_step",
     "residual", "objective", "compressed_sq_error", "monitor_estimate", "rounding_term",
-    "nndsvd_compressed", "gini", "solve", "iterate",
+    "nndsvd_compressed", "gini", "solve", "solve_to_target", "iterate",
     "philox4x32_10", "philox_normal", "philox_normal_np", "memory_floats_rp",
     "EPS_MU",
 ]
@@ -446,6 +447,37 @@ def solve(X, omega_L, omega_R, W0, H0, w, iters, rule="fasthals", residual_every
         done += k
         hist.append((done, residual(X, W, H)[0]))
     return W, H, QL, QR, hist
+
+
+def solve_to_target(X, omega_L, omega_R, W0, H0, w, iters, target, check_every=10,
+                    rule="fasthals", margin=0.05):
+    """Whole solve with the stopping rule of a timed run (the paper leaves the convergence
+    criterion undefined; reading: stop at the first check whose exact relative residual is at or
+    below `target`). Sketch and compression as in `solve`; every `check_every` iterations the
+    compressed error estimate (`compressed_sq_error`, no read of X) is formed, and the exact
+    residual of X is computed only when that estimate is within `margin` of the target, or at the
+    last check. The estimate only decides whether the exact residual is worth computing; the stop
+    itself is decided by the exact residual alone.
+
+    Returns (W, H, iters_done, rel_err, exact_checks); rel_err is the last exact residual (at
+    iters_done when the target was met)."""
+    X = np.asarray(X, np.float64)
+    QL, QR = sketch(X, omega_L, omega_R, w)
+    Xhat, Xchk = compress(X, QL, QR)
+    x2 = float(np.sum(X * X))
+    W, H = _f64(W0), _f64(H0)
+    done, checks, rel = 0, 0, float("nan")
+    while done < iters:
+        k = min(check_every, iters - done)
+        W, H = iterate(W, H, QL, QR, Xhat, Xchk, k, rule=rule)
+        done += k
+        est = np.sqrt(max(compressed_sq_error(x2, QL, Xhat, W, H), 0.0) / x2)
+        if done >= iters or est <= target * (1.0 + margin):
+            rel = residual(X, W, H)[0]
+            checks += 1
+            if rel <= target:
+                break
+    return W, H, done, rel, checks
 
 
 # --------------------------------------------------------------------------------------------

@@ -139,6 +139,7 @@ struct IterArgs {
   const float* Xchk;  // m x ell
   float* W;           // m x r
   float* H;           // r x n
+  long long wait_cycles = 0;   // persistent kernel: polling budget of a grid barrier (0: default)
 };
 size_t iterate_ws_bytes(int64_t m, int64_t n, int r, int ell);
 cudaError_t launch_iterate(const Launcher& L, const IterArgs& a, int iters, void* ws,

@@ -73,7 +73,7 @@ __device__ __forceinline__ unsigned atom_add_acq_rel(unsigned* p, unsigned v) {
 // arrival counter reaches k * nblocks (one acquire-release add per block after a fence, acquire
 // polling). Returns false if the wait ran out.
 __device__ bool grid_sync(Barrier* bar, unsigned nblocks, unsigned& epoch, int* status,
-                          int* abort_flag) {
+                          int* abort_flag, long long wait_cycles) {
   __syncthreads();
   __shared__ int ok;
   ++epoch;
@@ -85,7 +85,7 @@ __device__ bool grid_sync(Barrier* bar, unsigned nblocks, unsigned& epoch, int* 
     if (before + 1 < target) {
       const long long t0 = clock64();
       while (static_cast<int>(ld_acquire(&bar->count) - target) < 0) {
-        if (clock64() - t0 > kWaitCycles || *reinterpret_cast<volatile int*>(abort_flag)) {
+        if (clock64() - t0 > wait_cycles || *reinterpret_cast<volatile int*>(abort_flag)) {
           ok = 0;
           break;
         }
@@ -133,6 +133,7 @@ struct PArgs {
   Barrier* bar;
   int* status;
   int* abort_flag;
+  long long wait_cycles;   // polling budget of each grid barrier wait (SM clock cycles)
 };
 
 // Fixed-order sum of the kCopies copies of entry e, read through L2.
@@ -479,7 +480,7 @@ __device__ __forceinline__ void iterate_body(const PArgs& a, const unsigned bid,
   // prologue: H_tld, H H^T of the initial H into accB[1]
   block_share(CB, RP, LQ + RP, Hs, RP, Hs, RP, RP, Qr, LS, Hs, RP, LQ, red,
               a.accB + (1 * kCopies + bid % kCopies) * EB);
-  if (!grid_sync(a.bar, G, epoch, a.status, a.abort_flag)) return;
+  if (!grid_sync(a.bar, G, epoch, a.status, a.abort_flag, a.wait_cycles)) return;
 
   for (int it = 0; it < a.iters; ++it) {
     const int ph = it & 1, pr = ph ^ 1;
@@ -559,7 +560,7 @@ __device__ __forceinline__ void iterate_body(const PArgs& a, const unsigned bid,
     // [Q_L | W]^T W over the slice
     block_share(RB, LQ + RP, RP, Ql, LS, Ws, RP, LQ, Ws, RP, Ws, RP, RP, red,
                 a.accA + (ph * kCopies + bid % kCopies) * EA);
-    if (!grid_sync(a.bar, G, epoch, a.status, a.abort_flag)) return;
+    if (!grid_sync(a.bar, G, epoch, a.status, a.abort_flag, a.wait_cycles)) return;
 
     // ================= phase B: columns of H
     for (int64_t e = static_cast<int64_t>(bid) * kNT + t; e < kCopies * EB;
@@ -654,7 +655,7 @@ __device__ __forceinline__ void iterate_body(const PArgs& a, const unsigned bid,
       for (int wI = 0; wI < kNT / 32; ++wI) csum += wred[wI];
       atomicAdd(&accB_w[RP * (LQ + RP)], csum);
     }
-    if (!grid_sync(a.bar, G, epoch, a.status, a.abort_flag)) return;
+    if (!grid_sync(a.bar, G, epoch, a.status, a.abort_flag, a.wait_cycles)) return;
   }
   // the last iteration's monitor terms: cross, and <W^T W, H H^T> for the normalised W
   if (bid == 0 && a.iters > 0) {
@@ -818,6 +819,7 @@ cudaError_t launch_iterate_persistent(const Launcher& L, const IterArgs& ia, int
   a.status = status;
   a.mon = mon;
   a.done = done;
+  a.wait_cycles = ia.wait_cycles > 0 ? ia.wait_cycles : kWaitCycles;
   const size_t clear = reinterpret_cast<char*>(a.abort_flag + 1) - reinterpret_cast<char*>(base);
   cudaError_t err = cudaMemsetAsync(a.accA, 0, clear, L.stream);
   if (err != cudaSuccess) return err;
@@ -926,6 +928,7 @@ cudaError_t launch_iterate_multi(const Launcher& L, const IterArgs* ia, const in
     a.status = status;
     a.mon = mon + 2 * i;
     a.done = done_zero;
+    a.wait_cycles = ia[i].wait_cycles > 0 ? ia[i].wait_cycles : kWaitCycles;
     a.RB = static_cast<int>((ia[i].m + blocks[i] - 1) / blocks[i]);
     a.CB = static_cast<int>((ia[i].n + blocks[i] - 1) / blocks[i]);
     base += (iterate_persistent_ws_bytes(ia[i].r, ia[i].ell) + 255) / 256 * 256;

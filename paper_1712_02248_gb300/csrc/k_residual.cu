@@ -423,7 +423,9 @@ cudaError_t launch_sumsq(const Launcher& L, const float* X, int64_t m, int64_t n
 // flight on one device at the same time share it and race.
 namespace {
 
-constexpr int kStaticPartialDoubles = 4096;   // 32 KB: two doubles per block, up to 2048 blocks
+// two doubles for each of up to 2048 blocks (4 a multiprocessor on devices of up to 512) plus the
+// 256-byte alignment slack residual_ws_bytes counts: 33,024 bytes
+constexpr int kStaticPartialDoubles = 2 * 4 * 512 + 32;
 __device__ __align__(256) double g_residual_partials[kStaticPartialDoubles];
 
 constexpr int kStaticMaxDevices = 64;

@@ -37,6 +37,7 @@ struct nmf_ctx {
                              // [5] exact / estimate there (0 before the first exact check)
   int* h_done = nullptr;     // pinned [2] copies of the done flag
   int last_iters = 0, last_checks = 0;
+  int64_t wait_cycles = 0;   // grid-barrier polling budget of the persistent kernel (0: default)
   int64_t launches = 0;
   char msg[512] = {0};
   bool profiling = false;
@@ -417,6 +418,7 @@ nmf_status iterate_impl(nmf_ctx* ctx, const nmf_params* p, const float* QL, cons
   ia.Xchk = Xchk;
   ia.W = W;
   ia.H = H;
+  ia.wait_cycles = ctx->wait_cycles;
   Phase ph(ctx, NMF_PHASE_ITERATE);
   size_t rest = 0;
   void* ws = a.rest(&rest);
@@ -653,6 +655,30 @@ nmf_status nmf_last_solve_info(const nmf_ctx* ctx, int32_t* iters, int32_t* exac
 nmf_status nmf_last_batch_info(const nmf_ctx* ctx, int32_t* rows_per_block) {
   if (!ctx || !rows_per_block) return NMF_ERR_INVALID_ARG;
   *rows_per_block = ctx->last_batch_rows_per_block;
+  return NMF_OK;
+}
+
+nmf_status nmf_set_wait_limit(nmf_ctx* ctx, int64_t cycles) {
+  if (!ctx || cycles < 0) return NMF_ERR_INVALID_ARG;
+  ctx->wait_cycles = cycles;
+  return NMF_OK;
+}
+
+nmf_status nmf_monitor_terms(nmf_ctx* ctx, double* terms) {
+  if (!ctx || !terms) return NMF_ERR_INVALID_ARG;
+  DeviceGuard g(ctx->device);
+  float mon[2] = {0.f, 0.f};
+  double solve[4] = {0, 0, 0, 0};
+  NMF_CUDA(cudaMemcpyAsync(mon, ctx->d_mon, sizeof(mon), cudaMemcpyDeviceToHost, ctx->stream),
+           "monitor copy");
+  NMF_CUDA(cudaMemcpyAsync(solve, ctx->d_solve, sizeof(solve), cudaMemcpyDeviceToHost,
+                           ctx->stream),
+           "monitor copy");
+  NMF_CUDA(cudaStreamSynchronize(ctx->stream), "monitor sync");
+  terms[0] = mon[0];
+  terms[1] = mon[1];
+  terms[2] = solve[0];
+  terms[3] = solve[3];
   return NMF_OK;
 }
 
@@ -1004,6 +1030,12 @@ nmf_status solve_impl(nmf_ctx* ctx, const nmf_params* p, int32_t init, const flo
   NMF_CUDA(cudaStreamSynchronize(ctx->stream), "solve sync");
   ctx->last_iters = static_cast<int>(out[2]);
   ctx->last_checks = flags[3];
+  if (!std::isfinite(out[0])) {
+    // a NaN or an infinity in X: every later quantity is meaningless, whatever else the device
+    // latched on the way (a QR breakdown from a NaN pivot, say), so clear it and report X
+    take_status(ctx);
+    return fail(ctx, NMF_ERR_NOT_FINITE, "X holds a NaN or an infinity (||X||^2 is not finite)");
+  }
   if ((st = take_status(ctx)) != NMF_OK) return st;   // a QR breakdown is reported as such
   if (!(out[1] == out[1]) || out[1] > 1e300) return fail(ctx, NMF_ERR_NOT_FINITE, "residual is not finite");
   if (rel_err_host) *rel_err_host = out[1];

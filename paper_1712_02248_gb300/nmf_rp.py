@@ -34,7 +34,8 @@ EXPORTS = ["nmf_create", "nmf_destroy", "nmf_set_stream", "nmf_last_error", "nmf
            "nmf_last_solve_info", "nmf_solve_batched", "nmf_last_batch_info",
            "nmf_mlp_param_count", "nmf_warmstart_features", "nmf_mlp_forward",
            "nmf_mlp_loss_grad", "nmf_mlp_adam", "nmf_mlp_train_step", "nmf_warmstart_apply",
-           "nmf_set_warmstart", "nmf_quantized_bytes"]
+           "nmf_set_warmstart", "nmf_quantized_bytes", "nmf_set_wait_limit",
+           "nmf_monitor_terms"]
 PHASES = ["quantize", "dual_pass", "qr", "iterate", "residual", "init"]
 
 
@@ -81,6 +82,8 @@ _c = {
     "nmf_residual_static": _sig("nmf_residual_static", ctypes.c_int,
                                 [_i32, _vp, _vp, _i64, _i64, _i64, _i32, _vp, _vp, _vp]),
     "nmf_set_profiling": _sig("nmf_set_profiling", ctypes.c_int, [_vp, _i32]),
+    "nmf_set_wait_limit": _sig("nmf_set_wait_limit", ctypes.c_int, [_vp, _i64]),
+    "nmf_monitor_terms": _sig("nmf_monitor_terms", ctypes.c_int, [_vp, _D]),
     "nmf_last_solve_info": _sig("nmf_last_solve_info", ctypes.c_int,
                                 [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
     "nmf_phase_times": _sig("nmf_phase_times", ctypes.c_int,
@@ -337,6 +340,13 @@ def nmf_residual_static(X, W, H, out, stream=None):
     W, H = _dev_f32(W, "W"), _dev_f32(H, "H")
     if not (out.is_cuda and out.dtype == torch.float64 and out.numel() >= 2 and out.is_contiguous()):
         raise ValueError("out must be a contiguous float64 CUDA tensor of 2 elements")
+    # the C entry point receives bare pointers and cannot see these: a mismatch would make its
+    # kernels read past the end of W or H
+    if W.dim() != 2 or H.dim() != 2 or W.shape[0] != X.shape[0] or H.shape != (W.shape[1], X.shape[1]):
+        raise ValueError(f"W must be ({X.shape[0]}, r) and H (r, {X.shape[1]}); got "
+                         f"{tuple(W.shape)} and {tuple(H.shape)}")
+    if not (W.device == X.device and H.device == X.device and out.device == X.device):
+        raise ValueError("X, W, H and out must be on the same CUDA device")
     dev = X.device.index
     s = stream if stream is not None else torch.cuda.current_stream(X.device)
     st = _c["nmf_residual_static"](dev, _vp(s.cuda_stream), _ptr(X), X.shape[0], X.shape[1], ldx,
@@ -455,6 +465,18 @@ def nmf_last_batch_info(ctx):
 
 def nmf_set_profiling(ctx, on=True):
     ctx._check(_c["nmf_set_profiling"](ctx.handle, 1 if on else 0))
+
+
+def nmf_set_wait_limit(ctx, cycles=0):
+    """Polling budget (SM clock cycles) of the persistent kernel's grid-barrier waits; 0 = default."""
+    ctx._check(_c["nmf_set_wait_limit"](ctx.handle, int(cycles)))
+
+
+def nmf_monitor_terms(ctx):
+    """(cross, quad, ||X||^2, <X - X_q, X>) of the error monitor; synchronises the stream."""
+    t = (ctypes.c_double * 4)()
+    ctx._check(_c["nmf_monitor_terms"](ctx.handle, t))
+    return tuple(t)
 
 
 def nmf_phase_times(ctx, reset=True):

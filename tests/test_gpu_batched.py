@@ -101,8 +101,8 @@ def test_batched_against_oracle(lib, ctx):
     got = lib.nmf_solve_batched(ctx, ps, Xs, Ws, Hs)
     for k, pr in enumerate(probs):
         m, n = pr.X.shape
-        oL = lib.nmf_gaussian(ctx, n, pr.ell, 11 + k, 0).double().cpu().numpy()
-        oR = lib.nmf_gaussian(ctx, m, pr.ell, 11 + k, 1).double().cpu().numpy()
+        oL = O.philox_normal_np(n, pr.ell, 11 + k, 0)
+        oR = O.philox_normal_np(m, pr.ell, 11 + k, 1)
         _, _, _, _, hist = O.solve(pr.X.astype(np.float64), oL, oR, pr.W0, pr.H0, 2, iters)
         ro = hist[-1][1]
         assert abs(got[k] - ro) <= 0.01 * ro, f"problem {k}: {got[k]} vs oracle {ro}"

@@ -393,9 +393,10 @@ def test_solve_matches_stepwise_path(lib, ctx):
     W, H = cu(pr.W0), cu(pr.H0)
     relg, it = lib.nmf_solve(ctx, p, X, W, H)
     assert it == 60
-    oL = lib.nmf_gaussian(ctx, 600, 20, 5, 0)
-    oR = lib.nmf_gaussian(ctx, 800, 20, 5, 1)
-    _, _, _, _, hist = O.solve(pr.X, host(oL), host(oR), pr.W0, pr.H0, 2, 60)
+    # Omega from the oracle's own generator (same definition as the library's, seed 5)
+    oL = O.philox_normal_np(600, 20, 5, 0)
+    oR = O.philox_normal_np(800, 20, 5, 1)
+    _, _, _, _, hist = O.solve(pr.X, oL, oR, pr.W0, pr.H0, 2, 60)
     assert abs(relg - hist[-1][1]) <= 0.01 * hist[-1][1]
 
 

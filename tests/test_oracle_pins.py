@@ -506,6 +506,25 @@ def test_rounding_term_closed_form():
     assert abs(O.rounding_term(X, 0.75 * X) - 0.25 * float(np.sum(X * X))) <= 1e-12
 
 
+def test_solve_to_target_stops_where_every_check_is_exact():
+    """The estimate only skips exact residuals that cannot meet the target: the stop is the first
+    check of `solve` (an exact residual at every check) whose error is at or below the target,
+    with the same factors; a target no check meets runs all iterations."""
+    rng = _rng(18)
+    X, _, _ = _planted(rng, 60, 45, 4, 0.05)
+    oL, oR = rng.standard_normal((45, 10)), rng.standard_normal((60, 10))
+    W0, H0 = rng.uniform(0, 1, (60, 4)), rng.uniform(0, 1, (4, 45))
+    _, _, _, _, hist = O.solve(X, oL, oR, W0, H0, 2, 200, residual_every=10)
+    target = hist[6][1] * 1.0000001
+    it_ref = next(i for i, e in hist if e <= target)
+    W, H, it, rel, checks = O.solve_to_target(X, oL, oR, W0, H0, 2, 200, target)
+    assert it == it_ref and rel <= target and checks < it // 10
+    Wr, Hr, _, _, _ = O.solve(X, oL, oR, W0, H0, 2, it, residual_every=0)
+    assert np.array_equal(W, Wr) and np.array_equal(H, Hr)
+    _, _, it, rel, checks = O.solve_to_target(X, oL, oR, W0, H0, 2, 50, 1e-9)
+    assert it == 50 and checks == 1 and rel == O.solve(X, oL, oR, W0, H0, 2, 50)[4][-1][1]
+
+
 def test_gini_closed_forms():
     """Section 5.1 Gini formula: all-equal entries give 0, a single non-zero gives 1 - 1/N."""
     assert abs(O.gini(np.ones((4, 5)))) <= 1e-15

@@ -50,3 +50,17 @@ def test_static_residual_rejects_bad_arguments(lib):
     with pytest.raises(lib.NmfError):
         lib.nmf_residual_static(torch.ones(0, 4, device="cuda"), torch.ones(0, 2, device="cuda"),
                                 torch.ones(2, 4, device="cuda"), out)
+    # W and H whose shapes do not match X: refused by the binding before the call (the C entry
+    # point sees only pointers)
+    X = torch.ones(6, 5, device="cuda")
+    with pytest.raises(ValueError):
+        lib.nmf_residual_static(X, torch.ones(5, 2, device="cuda"), torch.ones(2, 5, device="cuda"),
+                                out)
+    with pytest.raises(ValueError):
+        lib.nmf_residual_static(X, torch.ones(6, 2, device="cuda"), torch.ones(3, 5, device="cuda"),
+                                out)
+    with pytest.raises(ValueError):
+        lib.nmf_residual_static(X, torch.ones(6, 2, device="cuda"), torch.ones(2, 4, device="cuda"),
+                                out)
+    with pytest.raises(ValueError):
+        lib.nmf_residual_static(X, torch.ones(6, 2, device="cuda"), torch.ones(2, 5), out)
