@@ -271,6 +271,60 @@ nmf_status nmf_residual_static(int32_t device, void* stream, const float* X, int
                                int64_t n, int64_t ldx, int32_t r, const float* W, const float* H,
                                double* out_dev);
 
+/*
+ * `iters` iterations of the uncompressed methods on the full data X, the baselines the paper
+ * compares against (Section 5, Tables 5.2 and 5.3), in place on W (m x r) and H (r x n):
+ *   p->rule = NMF_RULE_FASTHALS_RP: FastHALS (Section 2.2): S_W = X H^T, G_W = H H^T, the W sweep
+ *     w_j <- [w_j + (S_W[:,j] - W G_W[:,j]) / G_W[j,j]]_+ over j = 1..r (Gauss-Seidel), the
+ *     normalisation w_j /= ||w_j|| with h_j *= ||w_j||, then S_H = W^T X, G_H = W^T W and the H
+ *     sweep (Section 4.1 alpha / beta form; plain at alpha = beta = 0).
+ *   p->rule = NMF_RULE_MU_RP: Lee-Seung multiplicative updates (Section 2.1, Algorithm 1):
+ *     W <- W o (X H^T) / (W H H^T + eps), then H <- H o (W^T X) / (W^T W H + eps).
+ * Two passes over X an iteration (the H step needs this iteration's W). X as for nmf_sketch:
+ * FP32 with leading dimension ldx (p->prec = FP32), or the nmf_quantize copy of p->prec (ldx = n;
+ * the BF16 / FP8 tensor-core pass keeps W and H as hi + lo BF16 pairs, so only X is rounded).
+ * Uses p->m, n, r (1 <= r <= 64), rule, prec, alpha, beta, eps, flags; p->ell is not used.
+ * Device arrays owned by the caller. Asynchronous on the context's stream.
+ * Errors: NMF_ERR_INVALID_ARG (sizes, pointers, ldx, enums), NMF_ERR_UNSUPPORTED (r > 64).
+ */
+nmf_status nmf_iterate_full(nmf_ctx* ctx, const nmf_params* p, const void* X, int64_t ldx,
+                            float* W, float* H, int32_t iters);
+
+/*
+ * Singular values of the compressed data X_hat (ell x n, row-major FP32 device array owned by the
+ * caller), descending, into sigma_host[0..ell). With X ~ Q_L X_hat (Section 3, Eq. 3.4) they are
+ * the estimates the sketch gives of sigma_1..sigma_ell of X, whose decay sets how many power
+ * iterations w the sketch needs (Section 5.2). Computed as sqrt(lambda_j(X_hat X_hat^T)) from a
+ * float-float Gram and a cyclic Jacobi eigensolver in FP32: each lambda_j carries an absolute
+ * error of about ell * 1.2e-7 * lambda_1. Synchronises the stream.
+ * Errors: NMF_ERR_INVALID_ARG for NULL pointers or sizes outside 1 <= ell <= min(n, 128).
+ */
+nmf_status nmf_spectrum(nmf_ctx* ctx, int64_t n, int32_t ell, const float* Xhat,
+                        double* sigma_host);
+/*
+ * Decay rate p of a singular-value spectrum (host arrays, no device work). Section 5.2 relates
+ * the best number of power iterations to the decay rate p of the spectrum, which it writes as
+ * sigma_j(X)^-p; the rates it reports (0.0012 and 0.0053 over spectra of 1000 and 400 values,
+ * the slower decay needing more power iterations) fit an exponential decay sigma_j ~ C e^(-p j),
+ * so p is taken as minus the least-squares slope of log sigma_j against j over the entries
+ * with sigma_j > rel_floor * sigma_1 (sigma[0] = sigma_1 > 0, descending).
+ * Errors: NMF_ERR_INVALID_ARG for NULL pointers, count < 2, sigma[0] <= 0, rel_floor < 0, or
+ * fewer than two entries above the floor.
+ */
+nmf_status nmf_decay_rate(const double* sigma, int32_t count, double rel_floor, double* p_out);
+
+/*
+ * Gini coefficient of the `count` entries of B (Section 5.1, the sparsity measure of the factor
+ * B = H^T in Figures 5.4 and 5.7): G = sum_{i=1..N} (2 i - N - 1) b_(i) / (N sum_i b_(i)) with
+ * b_(1) <= ... <= b_(N) the entries in ascending order, N = count. B: device array of count
+ * FP32 values (any layout: only the multiset of values matters), owned by the caller. The
+ * entries are sorted on the device (bitonic network over order-preserving integer keys) and the
+ * sums taken in FP64. G = 0 when the entries sum to zero. Synchronises the stream.
+ * Errors: NMF_ERR_INVALID_ARG for NULL pointers or count < 1; NMF_ERR_NOT_FINITE if B holds a
+ * NaN or an infinity.
+ */
+nmf_status nmf_gini(nmf_ctx* ctx, const float* B, int64_t count, double* gini_host);
+
 /* NNDSVD initial factors (Boutsidis & Gallopoulos) from the compressed data: the top r singular
  * triplets of X ~ Q_L X_hat (Section 3, Eq. 3.4) come from the l x l eigenproblem of
  * X_hat X_hat^T (Gram in float-float arithmetic summed in FP64, cyclic Jacobi in FP32), with

@@ -96,21 +96,26 @@ cudaError_t launch_quantize_fp8_stats(const Launcher& L, const float* X, int64_t
 size_t dual_pass_ws_bytes(int64_t m, int64_t n, int ell);
 // split: on the tensor-core path, V and U enter as hi + lo BF16 pairs (only X is rounded to
 // BF16), which the compression uses; ignored elsewhere.
+// z_kmajor: Z is written ell x n (the layout of X_hat) instead of n x ell; only the tensor-core
+// path does this (dual_pass_uses_tc tells which path a pass takes).
 cudaError_t launch_dual_pass(const Launcher& L, const void* X, int x_type, int64_t m, int64_t n,
                              int64_t ldx, int ell, const float* V, const float* U, float* Y,
                              float* Z, void* ws, size_t ws_bytes, int* status,
-                             bool force_simt = false, bool split = false);
+                             bool force_simt = false, bool split = false, bool z_kmajor = false);
+bool dual_pass_uses_tc(const void* X, int x_type, int64_t m, int64_t n, int64_t ldx, int ell,
+                       bool both, bool force_simt);
 // tcgen05 + TMA dual pass on the FP8 copy (codes converted to BF16 in shared memory).
 bool dual_pass_tc_fp8_supported(int64_t m, int64_t n, int ell, const void* Xq);
 cudaError_t launch_dual_pass_tc_fp8(const Launcher& L, const uint8_t* Xq, int64_t m, int64_t n,
                                     int ell, const float* V, const float* U, float* Y, float* Z,
-                                    void* ws, size_t ws_bytes, int* status);
+                                    void* ws, size_t ws_bytes, int* status, bool z_kmajor = false);
 // tcgen05 + TMA dual pass (BF16 X).
 bool dual_pass_tc_supported(int64_t m, int64_t n, int64_t ldx, int ell, const void* X);
 size_t dual_pass_tc_ws_bytes(int64_t m, int64_t n, int ell);
 cudaError_t launch_dual_pass_tc(const Launcher& L, const __nv_bfloat16* X, int64_t m, int64_t n,
                                 int64_t ldx, int ell, const float* V, const float* U, float* Y,
-                                float* Z, void* ws, size_t ws_bytes, int* status, bool split);
+                                float* Z, void* ws, size_t ws_bytes, int* status, bool split,
+                                bool z_kmajor = false);
 
 // Thin QR via CholeskyQR2 with FP64 Gram and Cholesky. Q may alias Y.
 size_t qr_ws_bytes(int64_t rows, int ell);
@@ -162,6 +167,25 @@ size_t iterate_multi_ws_bytes(const IterArgs* ia, int nprob);
 cudaError_t launch_iterate_multi(const Launcher& L, const IterArgs* ia, const int* iters,
                                  const int* blocks, int nprob, void* ws, size_t ws_bytes,
                                  int* status, float* mon, const int* done_zero);
+
+// Singular values of X_hat (ell x n, ell <= 128), descending, into sigma (ell floats, device).
+size_t spectrum_ws_bytes(int64_t n, int ell);
+cudaError_t launch_spectrum(const Launcher& L, int64_t n, int ell, const float* Xhat, void* ws,
+                            size_t ws_bytes, float* sigma);
+
+// Iterations on the full data X (FastHALS, rule 0; Lee-Seung MU, rule 1), r <= 64: two passes
+// over X an iteration (X H^T, then X^T W with the new W). x_type and ldx as for the dual pass.
+size_t iterate_full_ws_bytes(int64_t m, int64_t n, int r);
+cudaError_t launch_iterate_full(const Launcher& L, const void* X, int x_type, int64_t m, int64_t n,
+                                int64_t ldx, int r, int rule, float alpha, float beta, float eps,
+                                float* W, float* H, int iters, void* ws, size_t ws_bytes,
+                                int* status, bool force_simt);
+
+// Gini coefficient sums of `count` floats (Section 5.1): out2[0] = sum (2 i - N - 1) b_(i),
+// out2[1] = sum b_(i) over the ascending order (device, FP64). ws: gini_ws_bytes(count).
+size_t gini_ws_bytes(int64_t count);
+cudaError_t launch_gini(const Launcher& L, const float* B, int64_t count, void* ws,
+                        size_t ws_bytes, double* out2);
 
 // Residual partial sums: writes 2 doubles (||X-WH||^2, ||X||^2) to out2 (device). If gate is
 // non-null and *gate == 0 the kernels return without work.

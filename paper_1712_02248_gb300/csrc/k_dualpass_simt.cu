@@ -238,15 +238,24 @@ size_t dual_pass_ws_bytes(int64_t m, int64_t n, int ell) {
   return simt > tc ? simt : tc;
 }
 
+bool dual_pass_uses_tc(const void* X, int x_type, int64_t m, int64_t n, int64_t ldx, int ell,
+                       bool both, bool force_simt) {
+  if (!both || force_simt) return false;
+  if (x_type == kXFp8) return dual_pass_tc_fp8_supported(m, n, ell, X);
+  return x_type == kXBf16 && dual_pass_tc_supported(m, n, ldx, ell, X);
+}
+
 cudaError_t launch_dual_pass(const Launcher& L, const void* X, int x_type, int64_t m, int64_t n,
                              int64_t ldx, int ell, const float* V, const float* U, float* Y,
                              float* Z, void* ws, size_t ws_bytes, int* status, bool force_simt,
-                             bool split) {
+                             bool split, bool z_kmajor) {
   if (ws_bytes < dual_pass_ws_bytes(m, n, ell)) return cudaErrorInvalidValue;
+  const bool tc = dual_pass_uses_tc(X, x_type, m, n, ldx, ell, V && U, force_simt);
+  if (z_kmajor && !tc) return cudaErrorInvalidValue;
   if (x_type == kXFp8) {
-    if (V && U && !force_simt && dual_pass_tc_fp8_supported(m, n, ell, X))
+    if (tc)
       return launch_dual_pass_tc_fp8(L, static_cast<const uint8_t*>(X), m, n, ell, V, U, Y, Z, ws,
-                                     ws_bytes, status);
+                                     ws_bytes, status, z_kmajor);
     // the FP8 copy: codes with row pitch ldq, then the tile scales (fp8_copy_bytes)
     int64_t ldq = 0, off = 0;
     fp8_copy_bytes(m, n, &ldq, &off);
@@ -255,9 +264,9 @@ cudaError_t launch_dual_pass(const Launcher& L, const void* X, int x_type, int64
                     (n + 31) / 32);
   }
   const bool x_bf16 = x_type == kXBf16;
-  if (x_bf16 && V && U && !force_simt && dual_pass_tc_supported(m, n, ldx, ell, X))
+  if (tc)
     return launch_dual_pass_tc(L, static_cast<const __nv_bfloat16*>(X), m, n, ldx, ell, V, U, Y,
-                               Z, ws, ws_bytes, status, split);
+                               Z, ws, ws_bytes, status, split, z_kmajor);
   if (x_bf16)
     return dispatch(L, static_cast<const __nv_bfloat16*>(X), m, n, ldx, ell, V, U, Y, Z,
                     static_cast<float*>(ws));

@@ -18,10 +18,13 @@
 // (16 KB, 128B-swizzled) into its own ring, and warps 6-13 rewrite it as the BF16 tile the MMAs
 // read, code times 2^k (exact in BF16), in the same swizzled layout, before signalling the MMA
 // issuer; the HBM stream is half that of BF16 X. Partial
-// sums of Y (one per column group) and Z (one per row group) are added by the fixed-order slot
-// reduction of the SIMT path. Every mbarrier wait is bounded; on time-out the kernel latches
-// NMF_ERR_TIMEOUT, drains what it issued and frees its tensor memory.
+// sums of Y (one per column group) and Z (one per row group) are summed in a fixed slot order
+// by one slot-sum launch for both. Every mbarrier wait is bounded; on time-out the kernel
+// latches NMF_ERR_TIMEOUT, drains what it issued and frees its tensor memory.
 #include <cuda.h>
+
+#include <algorithm>
+#include <vector>
 #include <cuda_fp8.h>
 
 #include "common.cuh"
@@ -179,16 +182,28 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int N, int a_mn_major) {
 
 // ------------------------------------------------------------------ kernel
 
+constexpr int kMaxGroups = 160;    // column groups whose row-group counts a table holds
+
+// Row groups of each column group: CTAs [cta0[g], cta0[g + 1]) take column group g, each a
+// contiguous share of the row blocks. Narrower groups get fewer row groups, so every CTA streams
+// about the same number of bytes. Without a table (more column groups than it holds) every
+// group has n_rowgroups row groups.
+struct GroupTable {
+  int table;                      // 1: cta0 is valid
+  int cta0[kMaxGroups + 1];
+};
+
 struct TcArgs {
   int64_t m, n;
   int ell;
-  int n_rowgroups, n_colgroups;   // grid = n_colgroups x n_rowgroups
+  int n_rowgroups, n_colgroups;   // n_rowgroups: the most row groups of any column group
   int64_t n_rowblocks;            // ceil(m / 128)
   int tiles_per_group;            // column tiles per column group (<= the kernel's NCT)
   int stages;                     // X stages in shared memory (<= kMaxStages)
   int64_t n_coltiles;             // ceil(n / 128)
   float* Ypart;                   // [n_colgroups][ell][m]   (k-major: rows contiguous)
   float* Zpart;                   // [n_rowgroups][ell][n]
+  GroupTable gt;
   int* status;
   const uint8_t* S;               // FP8 X: E8M0 tile scales (row-major, tn a row)
   int64_t tn;
@@ -247,10 +262,20 @@ __global__ void __launch_bounds__(F8 ? kThreadsF8 : kThreads, 1) dual_pass_tc_ke
   __shared__ volatile int abort_f;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int cg = blockIdx.x, rg = blockIdx.y;
+  int cg, rg, nrg;
+  if (a.gt.table) {
+    cg = 0;
+    while (cg + 1 < a.n_colgroups && a.gt.cta0[cg + 1] <= static_cast<int>(blockIdx.x)) ++cg;
+    rg = blockIdx.x - a.gt.cta0[cg];
+    nrg = a.gt.cta0[cg + 1] - a.gt.cta0[cg];
+  } else {
+    cg = blockIdx.x / a.n_rowgroups;
+    rg = blockIdx.x - cg * a.n_rowgroups;
+    nrg = a.n_rowgroups;
+  }
   // this CTA's row blocks [rb0, rb1) and column tiles [ct0, ct1)
-  const int64_t rb0 = rg * a.n_rowblocks / a.n_rowgroups;
-  const int64_t rb1 = (rg + 1) * a.n_rowblocks / a.n_rowgroups;
+  const int64_t rb0 = rg * a.n_rowblocks / nrg;
+  const int64_t rb1 = (rg + 1) * a.n_rowblocks / nrg;
   const int64_t ct0 = static_cast<int64_t>(cg) * a.tiles_per_group;
   const int64_t ct1 = min(a.n_coltiles, ct0 + a.tiles_per_group);
   const int nrb = static_cast<int>(rb1 - rb0), nct = static_cast<int>(ct1 - ct0);
@@ -499,18 +524,25 @@ __global__ void __launch_bounds__(F8 ? kThreadsF8 : kThreads, 1) dual_pass_tc_ke
   }
 }
 
-// V (rows x ell, FP32) -> Vt (SPLIT*LP x ld, BF16): rows [0, LP) hold hi = bf16(v), rows
-// [LP, 2 LP) (SPLIT = 2) hold lo = bf16(v - hi); rows ell..LP-1 of each part and columns
-// rows..ld-1 are zero.
-__global__ void transpose_bf16_kernel(const float* __restrict__ V, int64_t rows, int ell, int LP,
-                                      int split, int64_t ld, __nv_bfloat16* __restrict__ Vt) {
+// Operand preparation of one pass in one launch: V (n x ell, FP32) -> Vt and U (m x ell) -> Ut
+// (SPLIT*LP x ld, BF16): rows [0, LP) hold hi = bf16(v), rows [LP, 2 LP) (SPLIT = 2) hold
+// lo = bf16(v - hi); rows ell..LP-1 of each part and columns rows..ld-1 are zero. Blocks
+// [0, nbv) of grid.x take V, the rest U.
+__global__ void prep_operands_kernel(const float* __restrict__ V, int64_t n, int64_t ldv,
+                                     __nv_bfloat16* __restrict__ Vt, const float* __restrict__ U,
+                                     int64_t m, int64_t ldu, __nv_bfloat16* __restrict__ Ut,
+                                     int ell, int LP, int split, int nbv) {
   __shared__ float tile[32][33];
-  const int64_t r0 = static_cast<int64_t>(blockIdx.x) * 32;
+  const bool isv = static_cast<int>(blockIdx.x) < nbv;
+  const float* src = isv ? V : U;
+  const int64_t rows = isv ? n : m, ld = isv ? ldv : ldu;
+  __nv_bfloat16* dst = isv ? Vt : Ut;
+  const int64_t r0 = static_cast<int64_t>(isv ? blockIdx.x : blockIdx.x - nbv) * 32;
   const int k0 = blockIdx.y * 32;
   for (int i = threadIdx.y; i < 32; i += blockDim.y) {
     const int64_t r = r0 + i;
     const int k = k0 + threadIdx.x;
-    tile[i][threadIdx.x] = (r < rows && k < ell) ? V[r * ell + k] : 0.f;
+    tile[i][threadIdx.x] = (r < rows && k < ell) ? src[r * ell + k] : 0.f;
   }
   __syncthreads();
   for (int i = threadIdx.y; i < 32; i += blockDim.y) {
@@ -519,43 +551,92 @@ __global__ void transpose_bf16_kernel(const float* __restrict__ V, int64_t rows,
     if (k < LP && r < ld) {
       const float x = tile[threadIdx.x][i];
       const __nv_bfloat16 hi = __float2bfloat16_rn(x);
-      Vt[static_cast<int64_t>(k) * ld + r] = hi;
+      dst[static_cast<int64_t>(k) * ld + r] = hi;
       if (split == 2)
-        Vt[static_cast<int64_t>(LP + k) * ld + r] = __float2bfloat16_rn(x - __bfloat162float(hi));
+        dst[static_cast<int64_t>(LP + k) * ld + r] = __float2bfloat16_rn(x - __bfloat162float(hi));
     }
   }
 }
 
-// out[row][k] = sum over slots of part[slot][k][row] (fixed slot order). A block takes 32 rows x
-// 8 values of k, one sum a thread with eight slot loads in flight (coalesced over rows), and
-// writes its 32 x 8 tile transposed through shared memory.
-__global__ void __launch_bounds__(256) reduce_slots_t_kernel(const float* __restrict__ part,
-                                                             int slots, int64_t rows, int ell,
-                                                             float* __restrict__ out) {
-  __shared__ float tile[8][33];
-  const int64_t row0 = static_cast<int64_t>(blockIdx.x) * 32;
-  const int k0 = blockIdx.y * 8;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  const int64_t r = row0 + tx;
-  const int k = k0 + ty;
-  float s = 0.f;
-  if (r < rows && k < ell) {
-    const float* p = part + static_cast<int64_t>(k) * rows + r;
-    const int64_t slot_stride = static_cast<int64_t>(ell) * rows;
-    int c = 0;
-    for (; c + 8 <= slots; c += 8) {
-      float v[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) v[u] = __ldcg(p + (c + u) * slot_stride);
-#pragma unroll
-      for (int u = 0; u < 8; ++u) s += v[u];
-    }
-    for (; c < slots; ++c) s += __ldcg(p + c * slot_stride);
+// Slot sums of one pass in one launch: Y[row][k] = sum over ys slots of Yp[slot][k][row] and
+// Z[col][k] (or Z[k][col] when z_kmajor) = sum over zs slots of Zp[slot][k][col], in slot order.
+// A block takes 128 rows (or columns) x 8 values of k: a thread sums four consecutive rows of
+// one k with 16-byte loads, eight slots in flight, and the block writes its tile transposed
+// through shared memory (or straight, k-major). Blocks [0, by) of grid.x take Y, the rest Z.
+constexpr int kRedRows = 128;
+__global__ void __launch_bounds__(256) reduce_pass_kernel(const float* __restrict__ Yp, int ys,
+                                                          int64_t m, float* __restrict__ Y,
+                                                          const float* __restrict__ Zp, int zs,
+                                                          int64_t n, float* __restrict__ Z,
+                                                          int ell, int z_kmajor, int by, int tpg,
+                                                          const __grid_constant__ GroupTable gt) {
+  __shared__ float tile[8][kRedRows + 4];
+  const bool isy = static_cast<int>(blockIdx.x) < by;
+  const float* part = isy ? Yp : Zp;
+  // a block of Z is one column tile: its slots are the row groups of its column group
+  int slots = isy ? ys : zs;
+  if (!isy && gt.table) {
+    const int g = static_cast<int>(blockIdx.x - by) / tpg;
+    slots = gt.cta0[g + 1] - gt.cta0[g];
   }
-  tile[ty][tx] = s;
+  const int64_t rows = isy ? m : n;
+  float* out = isy ? Y : Z;
+  const bool kmajor = !isy && z_kmajor;
+  const int64_t row0 = static_cast<int64_t>(isy ? blockIdx.x : blockIdx.x - by) * kRedRows;
+  const int k0 = blockIdx.y * 8;
+  const int t = threadIdx.x, kq = t >> 5, q = t & 31;   // k = k0 + kq, rows row0 + 4q .. + 3
+  const int k = k0 + kq;
+  const int64_t r = row0 + 4 * q;
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (k < ell && r < rows) {
+    const int64_t sstride = static_cast<int64_t>(ell) * rows;
+    const float* pp = part + static_cast<int64_t>(k) * rows + r;
+    if (r + 4 <= rows && (rows & 3) == 0) {
+      int c = 0;
+      for (; c + 8 <= slots; c += 8) {
+        float4 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = __ldcg(reinterpret_cast<const float4*>(pp + (c + u) * sstride));
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          acc.x += v[u].x;
+          acc.y += v[u].y;
+          acc.z += v[u].z;
+          acc.w += v[u].w;
+        }
+      }
+      for (; c < slots; ++c) {
+        const float4 v = __ldcg(reinterpret_cast<const float4*>(pp + c * sstride));
+        acc.x += v.x;
+        acc.y += v.y;
+        acc.z += v.z;
+        acc.w += v.w;
+      }
+    } else {
+      // ragged tail (or rows not a multiple of 4: no 16-byte alignment): element loads
+      float a4[4] = {0.f, 0.f, 0.f, 0.f};
+      for (int c = 0; c < slots; ++c)
+        for (int e = 0; e < 4; ++e)
+          if (r + e < rows) a4[e] += __ldcg(pp + c * sstride + e);
+      acc = make_float4(a4[0], a4[1], a4[2], a4[3]);
+    }
+  }
+  if (kmajor) {
+    if (k < ell)
+      for (int e = 0; e < 4; ++e)
+        if (r + e < rows) out[static_cast<int64_t>(k) * rows + r + e] = (&acc.x)[e];
+    return;
+  }
+  tile[kq][4 * q] = acc.x;
+  tile[kq][4 * q + 1] = acc.y;
+  tile[kq][4 * q + 2] = acc.z;
+  tile[kq][4 * q + 3] = acc.w;
   __syncthreads();
-  const int i = threadIdx.x >> 3, j = threadIdx.x & 7;
-  if (row0 + i < rows && k0 + j < ell) out[(row0 + i) * ell + k0 + j] = tile[j][i];
+  // out rows row0 .. row0 + 127, columns k0 .. k0 + 7: thread t writes (row t / 8 * 4 + i ...)
+  for (int e = t; e < kRedRows * 8; e += 256) {
+    const int i = e >> 3, j = e & 7;
+    if (row0 + i < rows && k0 + j < ell) out[(row0 + i) * ell + k0 + j] = tile[j][i];
+  }
 }
 
 // ------------------------------------------------------------------ host side
@@ -621,8 +702,10 @@ int lp16(int ell) { return (ell + 15) / 16 * 16; }
 struct Plan {
   int LP, split, stages, nct;
   size_t smem;
-  int rowgroups, colgroups, tiles_per_group;
+  int rowgroups, colgroups, tiles_per_group;   // rowgroups: the most of any column group
+  int ctas;
   int64_t rowblocks, coltiles;
+  GroupTable gt;
 };
 
 size_t smem_bytes(int LP, int split, int stages, int nct, bool f8 = false) {
@@ -661,10 +744,55 @@ Plan plan_for(int64_t m, int64_t n, int ell, int split, bool f8 = false) {
   const int nct = p.nct > 0 ? p.nct : 1;
   p.colgroups = static_cast<int>(cdiv(p.coltiles, nct));
   p.tiles_per_group = static_cast<int>(cdiv(p.coltiles, p.colgroups));
-  int rg = num_sms() / p.colgroups;
-  if (rg < 1) rg = 1;
-  if (rg > p.rowblocks) rg = static_cast<int>(p.rowblocks);
-  p.rowgroups = rg;
+  const int sms = num_sms();
+  p.gt.table = 0;
+  if (p.colgroups > sms || p.colgroups > kMaxGroups) {
+    // more column groups than CTAs at a time: one row group each
+    p.rowgroups = 1;
+    p.ctas = p.colgroups;
+    return p;
+  }
+  // row groups in proportion to each column group's cost, then one more at a time to the group
+  // whose CTAs carry the most, while CTAs are left. A tile costs its bytes plus a fixed part (its
+  // MMAs, conversion and barriers, taken as half of a full tile), so the partial last tile of a
+  // row costs 1/2 + 1/2 of its fraction of 128 columns (in half-tile units below)
+  std::vector<int64_t> width(p.colgroups);
+  std::vector<int> R(p.colgroups);
+  int used = 0;
+  const int64_t tail = n - (p.coltiles - 1) * kCols;   // columns of the last tile
+  const int64_t total = 2 * (p.coltiles - 1) * kCols + kCols + tail;
+  for (int g = 0; g < p.colgroups; ++g) {
+    const int64_t t1 = std::min<int64_t>(p.coltiles, (g + 1) * p.tiles_per_group);
+    const int64_t full = t1 - g * p.tiles_per_group - (t1 == p.coltiles ? 1 : 0);
+    width[g] = 2 * full * kCols + (t1 == p.coltiles ? kCols + tail : 0);
+    int r = static_cast<int>(static_cast<double>(sms) * width[g] / total);
+    r = std::max(1, std::min<int>(r, static_cast<int>(p.rowblocks)));
+    R[g] = r;
+    used += r;
+  }
+  while (used > sms) {   // rounding can only overshoot through the max(1, .)
+    int g = static_cast<int>(std::max_element(R.begin(), R.end()) - R.begin());
+    if (R[g] <= 1) break;
+    --R[g];
+    --used;
+  }
+  auto load = [&](int g) { return cdiv(p.rowblocks, R[g]) * width[g]; };
+  while (used < sms) {
+    int best = -1;
+    for (int g = 0; g < p.colgroups; ++g)
+      if (R[g] < p.rowblocks && (best < 0 || load(g) > load(best))) best = g;
+    if (best < 0) break;
+    ++R[best];
+    ++used;
+  }
+  p.gt.table = 1;
+  p.gt.cta0[0] = 0;
+  p.rowgroups = 0;
+  for (int g = 0; g < p.colgroups; ++g) {
+    p.gt.cta0[g + 1] = p.gt.cta0[g] + R[g];
+    p.rowgroups = std::max(p.rowgroups, R[g]);
+  }
+  p.ctas = p.gt.cta0[p.colgroups];
   return p;
 }
 
@@ -676,7 +804,7 @@ cudaError_t launch_t(const Launcher& L, const CUtensorMap& mx, const CUtensorMap
   cudaError_t err =
       cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (err != cudaSuccess) return err;
-  dim3 grid(a.n_colgroups, a.n_rowgroups);
+  dim3 grid(a.gt.table ? a.gt.cta0[a.n_colgroups] : a.n_colgroups * a.n_rowgroups);
   k<<<grid, F8 ? kThreadsF8 : kThreads, smem, L.stream>>>(mx, mv, mu, a);
   L.count();
   return cudaGetLastError();
@@ -734,25 +862,27 @@ namespace {
 // 128 x 64, or FP8 tiles of 128 x 128), S / tn the FP8 tile scales.
 cudaError_t run_tc(const Launcher& L, const CUtensorMap& mx, bool f8, const uint8_t* S, int64_t tn,
                    int64_t m, int64_t n, int ell, const float* V, const float* U, float* Y,
-                   float* Z, void* ws, int* status, int sp) {
+                   float* Z, void* ws, int* status, int sp, bool z_kmajor) {
   const Plan p = plan_for(m, n, ell, sp, f8);
   if (p.nct < 1) return cudaErrorInvalidValue;
   const int64_t ldv = (n + 7) / 8 * 8, ldu = (m + 7) / 8 * 8;
   char* w = static_cast<char*>(ws);
   float* Ypart = reinterpret_cast<float*>(w);
-  float* Zpart = Ypart + p.colgroups * m * ell;
-  uintptr_t q = reinterpret_cast<uintptr_t>(Zpart + p.rowgroups * n * ell);
+  uintptr_t q = reinterpret_cast<uintptr_t>(Ypart + p.colgroups * m * ell);
+  q = (q + 255) & ~uintptr_t(255);   // 16-byte loads of the slot sums
+  float* Zpart = reinterpret_cast<float*>(q);
+  q = reinterpret_cast<uintptr_t>(Zpart + p.rowgroups * n * ell);
   q = (q + 255) & ~uintptr_t(255);
   __nv_bfloat16* Vt = reinterpret_cast<__nv_bfloat16*>(q);
   q += 2 * static_cast<size_t>(sp * p.LP) * ldv;
   q = (q + 255) & ~uintptr_t(255);
   __nv_bfloat16* Ut = reinterpret_cast<__nv_bfloat16*>(q);
   {
-    dim3 gv(static_cast<unsigned>(cdiv(ldv, 32)), static_cast<unsigned>(cdiv(p.LP, 32)));
-    transpose_bf16_kernel<<<gv, dim3(32, 8), 0, L.stream>>>(V, n, ell, p.LP, sp, ldv, Vt);
-    dim3 gu(static_cast<unsigned>(cdiv(ldu, 32)), static_cast<unsigned>(cdiv(p.LP, 32)));
-    transpose_bf16_kernel<<<gu, dim3(32, 8), 0, L.stream>>>(U, m, ell, p.LP, sp, ldu, Ut);
-    L.count(2);
+    const int nbv = static_cast<int>(cdiv(ldv, 32));
+    dim3 g(static_cast<unsigned>(nbv + cdiv(ldu, 32)), static_cast<unsigned>(cdiv(p.LP, 32)));
+    prep_operands_kernel<<<g, dim3(32, 8), 0, L.stream>>>(V, n, ldv, Vt, U, m, ldu, Ut, ell, p.LP,
+                                                          sp, nbv);
+    L.count();
   }
   CUtensorMap mv, mu;
   if (!make_map(&mv, Vt, static_cast<uint64_t>(ldv), static_cast<uint64_t>(sp * p.LP),
@@ -772,6 +902,7 @@ cudaError_t run_tc(const Launcher& L, const CUtensorMap& mx, bool f8, const uint
   a.n_coltiles = p.coltiles;
   a.Ypart = Ypart;
   a.Zpart = Zpart;
+  a.gt = p.gt;
   a.status = status;
   a.S = S;
   a.tn = tn;
@@ -780,12 +911,11 @@ cudaError_t run_tc(const Launcher& L, const CUtensorMap& mx, bool f8, const uint
                     : sp == 2 ? launch_lp<2, false>(p.LP, L, mx, mv, mu, a, smem)
                               : launch_lp<1, false>(p.LP, L, mx, mv, mu, a, smem);
   if (err != cudaSuccess) return err;
-  const unsigned kg = static_cast<unsigned>(cdiv(ell, 8));
-  reduce_slots_t_kernel<<<dim3(static_cast<unsigned>(cdiv(m, 32)), kg), 256, 0, L.stream>>>(
-      Ypart, p.colgroups, m, ell, Y);
-  reduce_slots_t_kernel<<<dim3(static_cast<unsigned>(cdiv(n, 32)), kg), 256, 0, L.stream>>>(
-      Zpart, p.rowgroups, n, ell, Z);
-  L.count(2);
+  const int by = static_cast<int>(cdiv(m, kRedRows));
+  dim3 gr(static_cast<unsigned>(by + cdiv(n, kRedRows)), static_cast<unsigned>(cdiv(ell, 8)));
+  reduce_pass_kernel<<<gr, 256, 0, L.stream>>>(Ypart, p.colgroups, m, Y, Zpart, p.rowgroups, n, Z,
+                                               ell, z_kmajor ? 1 : 0, by, p.tiles_per_group, p.gt);
+  L.count();
   return cudaGetLastError();
 }
 
@@ -793,14 +923,15 @@ cudaError_t run_tc(const Launcher& L, const CUtensorMap& mx, bool f8, const uint
 
 cudaError_t launch_dual_pass_tc(const Launcher& L, const __nv_bfloat16* X, int64_t m, int64_t n,
                                 int64_t ldx, int ell, const float* V, const float* U, float* Y,
-                                float* Z, void* ws, size_t ws_bytes, int* status, bool split) {
+                                float* Z, void* ws, size_t ws_bytes, int* status, bool split,
+                                bool z_kmajor) {
   if (ws_bytes < dual_pass_tc_ws_bytes(m, n, ell)) return cudaErrorInvalidValue;
   const int sp = (split && dual_pass_tc_split_supported(ell)) ? 2 : 1;
   CUtensorMap mx;
   if (!make_map(&mx, X, static_cast<uint64_t>(n), static_cast<uint64_t>(m),
                 static_cast<uint64_t>(ldx), kHalfCols, kRows))
     return cudaErrorInvalidValue;
-  return run_tc(L, mx, false, nullptr, 0, m, n, ell, V, U, Y, Z, ws, status, sp);
+  return run_tc(L, mx, false, nullptr, 0, m, n, ell, V, U, Y, Z, ws, status, sp, z_kmajor);
 }
 
 bool dual_pass_tc_fp8_supported(int64_t m, int64_t n, int ell, const void* Xq) {
@@ -814,7 +945,7 @@ bool dual_pass_tc_fp8_supported(int64_t m, int64_t n, int ell, const void* Xq) {
 
 cudaError_t launch_dual_pass_tc_fp8(const Launcher& L, const uint8_t* Xq, int64_t m, int64_t n,
                                     int ell, const float* V, const float* U, float* Y, float* Z,
-                                    void* ws, size_t ws_bytes, int* status) {
+                                    void* ws, size_t ws_bytes, int* status, bool z_kmajor) {
   if (ws_bytes < dual_pass_tc_ws_bytes(m, n, ell)) return cudaErrorInvalidValue;
   int64_t ldq = 0, off = 0;
   fp8_copy_bytes(m, n, &ldq, &off);
@@ -822,7 +953,8 @@ cudaError_t launch_dual_pass_tc_fp8(const Launcher& L, const uint8_t* Xq, int64_
   if (!make_map8(&mx, Xq, static_cast<uint64_t>(n), static_cast<uint64_t>(m),
                  static_cast<uint64_t>(ldq)))
     return cudaErrorInvalidValue;
-  return run_tc(L, mx, true, Xq + off, (n + 31) / 32, m, n, ell, V, U, Y, Z, ws, status, 1);
+  return run_tc(L, mx, true, Xq + off, (n + 31) / 32, m, n, ell, V, U, Y, Z, ws, status, 1,
+                z_kmajor);
 }
 
 }  // namespace nmfrp

@@ -601,6 +601,42 @@ cudaError_t launch_nndsvd(const Launcher& L, int64_t m, int64_t n, int r, int el
   return cudaGetLastError();
 }
 
+size_t spectrum_ws_bytes(int64_t n, int ell) {
+  const int64_t slabs = cdiv(n, slab_width(n));
+  return sizeof(double) * ((slabs + 1) * ell * ell) + sizeof(float) * (ell * ell + ell) + 1024;
+}
+
+// Singular values of X_hat (ell x n): sigma_j = sqrt(lambda_j(X_hat X_hat^T)), descending, from
+// the float-float Gram and the FP32 Jacobi eigensolver of the NNDSVD start (an eigenvalue's
+// absolute error is about ell eps32 lambda_1).
+cudaError_t launch_spectrum(const Launcher& L, int64_t n, int ell, const float* Xhat, void* ws,
+                            size_t ws_bytes, float* sigma) {
+  if (ell > kMaxL) return cudaErrorNotSupported;
+  if (ws_bytes < spectrum_ws_bytes(n, ell)) return cudaErrorInvalidValue;
+  const int width = slab_width(n);
+  const int64_t slabs = cdiv(n, width);
+  double* gpart = static_cast<double*>(ws);
+  double* M = gpart + slabs * ell * ell;
+  float* Ur = reinterpret_cast<float*>(M + ell * ell);
+  const size_t gsm = sizeof(float) * ell * (width + 1);
+  cudaError_t err = cudaFuncSetAttribute(xgram_partial_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(gsm));
+  if (err != cudaSuccess) return err;
+  const int Lp = (ell + 1) / 2 * 2;
+  const size_t jsm = sizeof(float) * 2 * Lp * (Lp + 1);
+  if ((err = cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(jsm))) != cudaSuccess)
+    return err;
+  xgram_partial_kernel<<<static_cast<unsigned>(slabs), 256, gsm, L.stream>>>(Xhat, n, ell, width,
+                                                                            gpart);
+  xgram_sum_kernel<<<static_cast<unsigned>(cdiv(static_cast<int64_t>(ell) * ell * 32, 256)), 256, 0,
+                     L.stream>>>(gpart, static_cast<int>(slabs), ell, M);
+  jacobi_kernel<<<1, 512, jsm, L.stream>>>(M, ell, ell, Ur, sigma);
+  L.count(3);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_warmstart_features(const Launcher& L, int64_t m, int64_t n, int r, int ell,
                                       const float* QL, const float* Xhat, float* Wb, float* Hb,
                                       float* hscale, float* Fw, float* Fh, void* ws,

@@ -219,16 +219,19 @@ nmf_status check_x(nmf_ctx* ctx, const nmf_params* p, const void* X, int64_t ldx
 float eps_of(const nmf_params* p) { return p->eps > 0 ? static_cast<float>(p->eps) : 1e-12f; }
 
 // One dual pass with its scratch; prec (nmf_precision) names the element type of X.
+int x_type_of(int prec) {
+  return prec == NMF_PREC_BF16 ? nmfrp::kXBf16 : prec == NMF_PREC_FP8_E4M3 ? nmfrp::kXFp8
+                                                                           : nmfrp::kXFp32;
+}
+
 nmf_status dual(nmf_ctx* ctx, const void* X, int prec, int64_t m, int64_t n, int64_t ldx, int ell,
                 const float* V, const float* U, float* Y, float* Z, Arena a, bool simt = false,
-                bool split = false) {
+                bool split = false, bool z_kmajor = false) {
   Phase ph(ctx, NMF_PHASE_DUAL_PASS);
   size_t rest = 0;
   void* ws = a.rest(&rest);
-  const int xt = prec == NMF_PREC_BF16 ? nmfrp::kXBf16
-                 : prec == NMF_PREC_FP8_E4M3 ? nmfrp::kXFp8 : nmfrp::kXFp32;
-  NMF_CUDA(nmfrp::launch_dual_pass(launcher(ctx), X, xt, m, n, ldx, ell, V, U, Y, Z, ws, rest,
-                                   ctx->d_status, simt, split),
+  NMF_CUDA(nmfrp::launch_dual_pass(launcher(ctx), X, x_type_of(prec), m, n, ldx, ell, V, U, Y, Z,
+                                   ws, rest, ctx->d_status, simt, split, z_kmajor),
            "dual pass");
   return NMF_OK;
 }
@@ -386,11 +389,14 @@ nmf_status compress_impl(nmf_ctx* ctx, const nmf_params* p, const void* X, int64
                          const float* QL, const float* QR, float* Xhat, float* Xchk, Arena a) {
   const int64_t m = p->m, n = p->n;
   const int l = p->ell;
-  float* XhatT = a.take<float>(n * l);
+  const bool simt = (p->flags & NMF_FLAG_SIMT_DUAL_PASS) != 0;
   // the compressed data feed every iteration and the error monitor: Q_L, Q_R enter the BF16
-  // tensor-core pass as hi + lo pairs so that only X itself is rounded
-  nmf_status st = dual(ctx, X, p->prec, m, n, ldx, l, QR, QL, Xchk, XhatT, a,
-                       (p->flags & NMF_FLAG_SIMT_DUAL_PASS) != 0, true);
+  // tensor-core pass as hi + lo pairs so that only X itself is rounded. The tensor-core pass
+  // writes X_hat = Q_L^T X directly in its l x n layout; the SIMT pass writes its transpose
+  if (nmfrp::dual_pass_uses_tc(X, x_type_of(p->prec), m, n, ldx, l, true, simt))
+    return dual(ctx, X, p->prec, m, n, ldx, l, QR, QL, Xchk, Xhat, a, simt, true, true);
+  float* XhatT = a.take<float>(n * l);
+  nmf_status st = dual(ctx, X, p->prec, m, n, ldx, l, QR, QL, Xchk, XhatT, a, simt, true);
   if (st != NMF_OK) return st;
   dim3 grid(static_cast<unsigned>(cdiv(n, 32)), static_cast<unsigned>(cdiv(l, 32)));
   transpose_kernel<<<grid, dim3(32, 8), 0, ctx->stream>>>(XhatT, n, l, Xhat);
@@ -655,6 +661,97 @@ nmf_status nmf_last_solve_info(const nmf_ctx* ctx, int32_t* iters, int32_t* exac
 nmf_status nmf_last_batch_info(const nmf_ctx* ctx, int32_t* rows_per_block) {
   if (!ctx || !rows_per_block) return NMF_ERR_INVALID_ARG;
   *rows_per_block = ctx->last_batch_rows_per_block;
+  return NMF_OK;
+}
+
+nmf_status nmf_iterate_full(nmf_ctx* ctx, const nmf_params* p, const void* X, int64_t ldx,
+                            float* W, float* H, int32_t iters) {
+  if (!ctx) return NMF_ERR_INVALID_ARG;
+  if (!p) return fail(ctx, NMF_ERR_INVALID_ARG, "NULL params");
+  if (p->m < 1 || p->n < 1 || p->r < 1 || p->r > std::min<int64_t>(p->m, p->n))
+    return fail(ctx, NMF_ERR_INVALID_ARG, "bad sizes (m, n >= 1, 1 <= r <= min(m, n))");
+  if (p->r > 64) return fail(ctx, NMF_ERR_UNSUPPORTED, "full-data iterations support r <= 64");
+  if (p->rule != NMF_RULE_FASTHALS_RP && p->rule != NMF_RULE_MU_RP)
+    return fail(ctx, NMF_ERR_INVALID_ARG, "unknown rule %d", p->rule);
+  if (p->prec < NMF_PREC_FP32 || p->prec > NMF_PREC_FP8_E4M3)
+    return fail(ctx, NMF_ERR_INVALID_ARG, "unknown precision %d", p->prec);
+  if (!X || !W || !H || iters < 0) return fail(ctx, NMF_ERR_INVALID_ARG, "bad arguments");
+  if (p->prec == NMF_PREC_FP32 ? ldx < p->n : ldx != p->n)
+    return fail(ctx, NMF_ERR_INVALID_ARG, "ldx must be >= n (FP32 X) or n (BF16 / FP8 copy)");
+  DeviceGuard g(ctx->device);
+  nmf_status st = ensure_ws(ctx, nmfrp::iterate_full_ws_bytes(p->m, p->n, p->r));
+  if (st != NMF_OK) return st;
+  Phase ph(ctx, NMF_PHASE_ITERATE);
+  const cudaError_t e = nmfrp::launch_iterate_full(
+      launcher(ctx), X, x_type_of(p->prec), p->m, p->n, ldx, p->r, p->rule,
+      static_cast<float>(p->alpha), static_cast<float>(p->beta), eps_of(p), W, H, iters, ctx->ws,
+      ctx->ws_bytes, ctx->d_status, (p->flags & NMF_FLAG_SIMT_DUAL_PASS) != 0);
+  if (e == cudaErrorNotSupported) return fail(ctx, NMF_ERR_UNSUPPORTED, "full-data iterations");
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "full-data iterations");
+  return NMF_OK;
+}
+
+nmf_status nmf_spectrum(nmf_ctx* ctx, int64_t n, int32_t ell, const float* Xhat,
+                        double* sigma_host) {
+  if (!ctx) return NMF_ERR_INVALID_ARG;
+  if (!Xhat || !sigma_host || n < 1 || ell < 1 || ell > 128 || ell > n)
+    return fail(ctx, NMF_ERR_INVALID_ARG, "bad spectrum arguments (1 <= ell <= min(n, 128))");
+  DeviceGuard g(ctx->device);
+  const size_t need = nmfrp::spectrum_ws_bytes(n, ell) + sizeof(float) * 128 + 256;
+  nmf_status st = ensure_ws(ctx, need);
+  if (st != NMF_OK) return st;
+  char* base = static_cast<char*>(ctx->ws);
+  float* sig = reinterpret_cast<float*>(base);
+  void* rest = base + 1024;
+  NMF_CUDA(nmfrp::launch_spectrum(launcher(ctx), n, ell, Xhat, rest, ctx->ws_bytes - 1024, sig),
+           "spectrum");
+  float h[128];
+  NMF_CUDA(cudaMemcpyAsync(h, sig, sizeof(float) * ell, cudaMemcpyDeviceToHost, ctx->stream),
+           "spectrum copy");
+  NMF_CUDA(cudaStreamSynchronize(ctx->stream), "spectrum sync");
+  for (int j = 0; j < ell; ++j) sigma_host[j] = h[j];
+  return NMF_OK;
+}
+
+nmf_status nmf_decay_rate(const double* sigma, int32_t count, double rel_floor, double* p_out) {
+  if (!sigma || !p_out || count < 2 || !(rel_floor >= 0.0)) return NMF_ERR_INVALID_ARG;
+  // least-squares slope of log sigma_j against j over the values above rel_floor * sigma_1
+  const double top = sigma[0];
+  if (!(top > 0.0)) return NMF_ERR_INVALID_ARG;
+  double sj = 0, sl = 0, sjj = 0, sjl = 0;
+  int k = 0;
+  for (int j = 0; j < count; ++j) {
+    if (!(sigma[j] > rel_floor * top) || !(sigma[j] > 0.0)) continue;
+    const double x = j, y = std::log(sigma[j]);
+    sj += x;
+    sl += y;
+    sjj += x * x;
+    sjl += x * y;
+    ++k;
+  }
+  if (k < 2) return NMF_ERR_INVALID_ARG;
+  const double den = k * sjj - sj * sj;
+  if (!(den > 0.0)) return NMF_ERR_INVALID_ARG;
+  *p_out = -(k * sjl - sj * sl) / den;
+  return NMF_OK;
+}
+
+nmf_status nmf_gini(nmf_ctx* ctx, const float* B, int64_t count, double* gini_host) {
+  if (!ctx) return NMF_ERR_INVALID_ARG;
+  if (!B || count < 1 || !gini_host) return fail(ctx, NMF_ERR_INVALID_ARG, "bad gini arguments");
+  DeviceGuard g(ctx->device);
+  nmf_status st = ensure_ws(ctx, nmfrp::gini_ws_bytes(count));
+  if (st != NMF_OK) return st;
+  NMF_CUDA(nmfrp::launch_gini(launcher(ctx), B, count, ctx->ws, ctx->ws_bytes, ctx->d_res),
+           "gini");
+  NMF_CUDA(cudaMemcpyAsync(ctx->h_res, ctx->d_res, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                           ctx->stream),
+           "gini copy");
+  NMF_CUDA(cudaStreamSynchronize(ctx->stream), "gini sync");
+  const double num = ctx->h_res[0], tot = ctx->h_res[1];
+  if (!std::isfinite(num) || !std::isfinite(tot))
+    return fail(ctx, NMF_ERR_NOT_FINITE, "gini sums are not finite");
+  *gini_host = tot != 0.0 ? num / (static_cast<double>(count) * tot) : 0.0;
   return NMF_OK;
 }
 

@@ -35,7 +35,8 @@ EXPORTS = ["nmf_create", "nmf_destroy", "nmf_set_stream", "nmf_last_error", "nmf
            "nmf_mlp_param_count", "nmf_warmstart_features", "nmf_mlp_forward",
            "nmf_mlp_loss_grad", "nmf_mlp_adam", "nmf_mlp_train_step", "nmf_warmstart_apply",
            "nmf_set_warmstart", "nmf_quantized_bytes", "nmf_set_wait_limit",
-           "nmf_monitor_terms"]
+           "nmf_monitor_terms", "nmf_gini", "nmf_iterate_full", "nmf_spectrum",
+           "nmf_decay_rate"]
 PHASES = ["quantize", "dual_pass", "qr", "iterate", "residual", "init"]
 
 
@@ -84,6 +85,10 @@ _c = {
     "nmf_set_profiling": _sig("nmf_set_profiling", ctypes.c_int, [_vp, _i32]),
     "nmf_set_wait_limit": _sig("nmf_set_wait_limit", ctypes.c_int, [_vp, _i64]),
     "nmf_monitor_terms": _sig("nmf_monitor_terms", ctypes.c_int, [_vp, _D]),
+    "nmf_gini": _sig("nmf_gini", ctypes.c_int, [_vp, _vp, _i64, _D]),
+    "nmf_iterate_full": _sig("nmf_iterate_full", ctypes.c_int, [_vp, _P, _vp, _i64, _vp, _vp, _i32]),
+    "nmf_spectrum": _sig("nmf_spectrum", ctypes.c_int, [_vp, _i64, _i32, _vp, _D]),
+    "nmf_decay_rate": _sig("nmf_decay_rate", ctypes.c_int, [_D, _i32, ctypes.c_double, _D]),
     "nmf_last_solve_info": _sig("nmf_last_solve_info", ctypes.c_int,
                                 [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
     "nmf_phase_times": _sig("nmf_phase_times", ctypes.c_int,
@@ -465,6 +470,46 @@ def nmf_last_batch_info(ctx):
 
 def nmf_set_profiling(ctx, on=True):
     ctx._check(_c["nmf_set_profiling"](ctx.handle, 1 if on else 0))
+
+
+def nmf_iterate_full(ctx, p, X, W, H, iters):
+    """Full-data FastHALS (p.rule fasthals) or Lee-Seung MU (p.rule mu) on X (FP32, or the BF16 /
+    FP8 nmf_quantize copy of p.prec); W, H updated in place."""
+    X, ldx = _x_arg(X, p.prec)
+    for t, nm in ((W, "W"), (H, "H")):
+        _dev_f32(t, nm)
+    if W.shape != (p.m, p.r) or H.shape != (p.r, p.n):
+        raise ValueError(f"W must be ({p.m}, {p.r}) and H ({p.r}, {p.n})")
+    ctx._check(_c["nmf_iterate_full"](ctx.handle, ctypes.byref(p), _ptr(X), ldx, _ptr(W),
+                                      _ptr(H), int(iters)))
+    return W, H
+
+
+def nmf_spectrum(ctx, Xhat):
+    """Singular values of X_hat (ell x n CUDA float32), descending, as a list of floats."""
+    _dev_f32(Xhat, "Xhat")
+    ell, n = Xhat.shape
+    out = (ctypes.c_double * ell)()
+    ctx._check(_c["nmf_spectrum"](ctx.handle, n, ell, _ptr(Xhat), out))
+    return list(out)
+
+
+def nmf_decay_rate(sigma, rel_floor=1e-3):
+    """Exponential decay rate p of a descending spectrum (host computation in the library)."""
+    arr = (ctypes.c_double * len(sigma))(*[float(v) for v in sigma])
+    p = ctypes.c_double()
+    st = _c["nmf_decay_rate"](arr, len(sigma), float(rel_floor), ctypes.byref(p))
+    if st != NMF_OK:
+        raise NmfError(st, "nmf_decay_rate: invalid spectrum or floor")
+    return p.value
+
+
+def nmf_gini(ctx, B):
+    """Gini coefficient of the entries of the CUDA float32 tensor B (Section 5.1)."""
+    _dev_f32(B, "B")
+    g = ctypes.c_double()
+    ctx._check(_c["nmf_gini"](ctx.handle, _ptr(B), B.numel(), ctypes.byref(g)))
+    return g.value
 
 
 def nmf_set_wait_limit(ctx, cycles=0):

@@ -9,6 +9,8 @@ import re
 
 import pytest
 
+import oracle as O
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "nmf_rp.h")
 
@@ -82,3 +84,19 @@ def test_quantized_bytes_of_invalid_requests_is_zero(N):
     assert N.nmf_quantized_bytes("fp8", 0, 10) == 0
     assert N.nmf_quantized_bytes("bf16", 10, 0) == 0
     assert N.nmf_quantized_bytes(9, 10, 10) == 0
+
+
+def test_decay_rate_host_function_matches_oracle(N):
+    """nmf_decay_rate is host code of the library (no device): it fits the same exponential decay
+    as the oracle's decay_rate, and refuses spectra it cannot fit."""
+    import numpy as np
+    rng = np.random.default_rng(5)
+    for _ in range(5):
+        p = rng.uniform(1e-3, 0.3)
+        s = np.exp(-p * np.arange(60)) * (1 + 0.05 * rng.standard_normal(60)) * 3.0
+        s = np.sort(np.abs(s))[::-1]
+        assert abs(N.nmf_decay_rate(s, 1e-3) - O.decay_rate(s, 1e-3)) <= 1e-10
+    with pytest.raises(N.NmfError):
+        N.nmf_decay_rate([1.0], 0.0)
+    with pytest.raises(N.NmfError):
+        N.nmf_decay_rate([1.0, 1e-9, 1e-9], 1e-3)

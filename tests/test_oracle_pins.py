@@ -525,6 +525,30 @@ def test_solve_to_target_stops_where_every_check_is_exact():
     assert it == 50 and checks == 1 and rel == O.solve(X, oL, oR, W0, H0, 2, 50)[4][-1][1]
 
 
+def test_spectrum_of_exact_rank_sketch_equals_singular_values():
+    """For X of exact rank r <= l the sketch captures range(X), so X_hat = Q_L^T X has the nonzero
+    singular values of X (Section 3, Eq. 3.4 holds with equality); the rest are zero."""
+    rng = _rng(19)
+    X, _, _ = _planted(rng, 60, 45, 5)
+    QL, QR = O.sketch(X, rng.standard_normal((45, 9)), rng.standard_normal((60, 9)), 1)
+    Xhat, _ = O.compress(X, QL, QR)
+    s = O.spectrum(Xhat)
+    want = np.linalg.svd(X, compute_uv=False)
+    assert np.allclose(s[:5], want[:5], rtol=1e-12)
+    assert np.all(np.abs(s[5:]) <= 1e-10 * s[0])
+
+
+def test_decay_rate_recovers_exponential_spectrum():
+    """sigma_j = C exp(-p j) is fitted exactly, for any C; entries below the floor are ignored."""
+    j = np.arange(40)
+    for p, C in ((0.0053, 7.0), (0.0012, 0.3), (0.25, 1e4)):
+        s = C * np.exp(-p * j)
+        assert abs(O.decay_rate(s, 0.0) - p) <= 1e-12 * max(1.0, p)
+    s = np.exp(-0.1 * j)
+    s[30:] = 1e-9                       # a noise floor the fit must skip
+    assert abs(O.decay_rate(s, 1e-3) - 0.1) <= 1e-12
+
+
 def test_gini_closed_forms():
     """Section 5.1 Gini formula: all-equal entries give 0, a single non-zero gives 1 - 1/N."""
     assert abs(O.gini(np.ones((4, 5)))) <= 1e-15
