@@ -45,14 +45,16 @@ def parse():
     ap.add_argument("--profile", choices=["fp32", "bf16"], default=None,
                     help="run one short solve (20 iterations) for a profiler's launch list")
     ap.add_argument("--config", choices=["dense", "batched", "images", "warmstart", "passes",
-                                         "iterate"],
+                                         "iterate", "full", "sweep"],
                     default="dense",
                     help="batched: 256 uneven problems through nmf_solve_batched against one "
                          "nmf_solve per problem; images: 4096 x 100000 image-like data, r = 50, "
                          "BF16 against FP32; warmstart: learned warm start on 8192 x 2048, "
                          "r = 16; passes: one dual pass per element type of X; iterate: "
-                         "nmf_iterate alone on image-shaped operands (separate JSON lines; "
-                         "not the headline)")
+                         "nmf_iterate alone on image-shaped operands; full: compressed vs "
+                         "full-data updates (Tables 5.2/5.3); sweep: the k x w grid of Figure "
+                         "5.3 with the spectral decay rate (separate JSON lines; not the "
+                         "headline)")
     ap.add_argument("--train-count", type=int, default=256,
                     help="warmstart: planted training matrices (the full recipe uses 10000)")
     ap.add_argument("--heldout", type=int, default=32,
@@ -482,6 +484,147 @@ def run_passes(args):
     ctx.close()
 
 
+def _timed_events(stream, fn, reps):
+    """Median seconds of fn() over reps runs, CUDA events on `stream` (one untimed run first)."""
+    import torch
+    fn()
+    ts = []
+    for _ in range(reps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        ts.append(a.elapsed_time(b) / 1e3)
+    return statistics.median(ts)
+
+
+def run_full(args):
+    """The paper's central comparison (Section 5, Tables 5.2 and 5.3) on the GPU: time per update
+    and final error of the compressed methods (FastHALS-RP, MU-RP: nmf_iterate on the sketch's
+    compressed data) against the same methods on the full data (FastHALS, Lee-Seung MU:
+    nmf_iterate_full, two passes over X an iteration), from the same U[0,1) start, on the dense
+    workload (20000 x 5000, r = 20, l = 40, w = 2, BF16 copy of X for every pass) and on a
+    face-sized image problem (400 x 4096 as Olivetti in Table 5.2, r = 20, l = 25, w = 4)."""
+    import torch
+    from paper_1712_02248_gb300 import inputs
+    from paper_1712_02248_gb300 import nmf_rp as N
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    ctx = N.Context(0)
+    rows = {}
+    faces = inputs.images(seed=args.seed + 4, n_samples=400, r=20, ell=25, w=4)
+    work = [("dense 20000x5000 r=20 l=40 w=2", inputs.dense_20k_5k(seed=args.seed), 500),
+            ("faces-like 400x4096 r=20 l=25 w=4",
+             inputs.Problem(np.ascontiguousarray(faces.X.T), 20, 25, 4, faces.omega_R,
+                            faces.omega_L, np.ascontiguousarray(faces.H0.T),
+                            np.ascontiguousarray(faces.W0.T), faces.seed), 500)]
+    for name, pr, iters in work:
+        m, n = pr.X.shape
+        X = torch.from_numpy(pr.X).to(dev)
+        Xq = N.nmf_quantize(ctx, X, prec="bf16")
+        W0 = torch.from_numpy(pr.W0).to(dev)
+        H0 = torch.from_numpy(pr.H0).to(dev)
+        row = {}
+        for rule in ("fasthals", "mu"):
+            p = N.params(m, n, pr.r, pr.ell, power_iters=pr.w, rule=rule, prec="bf16",
+                         seed=args.seed + 17)
+            QL, QR = N.nmf_sketch(ctx, p, Xq)
+            Xhat, Xchk = N.nmf_compress(ctx, p, Xq, QL, QR)
+            W, H = W0.clone(), H0.clone()
+            k = 20
+            t_c = _timed_events(ctx.stream, lambda: N.nmf_iterate(ctx, p, QL, QR, Xhat, Xchk,
+                                                                  W0.clone(), H0.clone(), k),
+                                max(args.steps, 3)) / k
+            N.nmf_iterate(ctx, p, QL, QR, Xhat, Xchk, W, H, iters)
+            e_c = N.nmf_residual(ctx, p, X, W, H)[0]
+            t_f = _timed_events(ctx.stream, lambda: N.nmf_iterate_full(ctx, p, Xq, W0.clone(),
+                                                                       H0.clone(), k),
+                                max(args.steps, 3)) / k
+            W, H = W0.clone(), H0.clone()
+            N.nmf_iterate_full(ctx, p, Xq, W, H, iters)
+            e_f = N.nmf_residual(ctx, p, X, W, H)[0]
+            rp = "FastHALS" if rule == "fasthals" else "MU"
+            row[f"{rp}-RP"] = {"ms_per_update": t_c * 1e3, "rel_err": e_c}
+            row[rp] = {"ms_per_update": t_f * 1e3, "rel_err": e_f}
+            row[f"{rp} / {rp}-RP time per update"] = t_f / t_c
+            row[f"{rp}-RP / {rp} error"] = e_c / e_f
+        rows[name] = row
+        del X, Xq
+        torch.cuda.empty_cache()
+    d = rows["dense 20000x5000 r=20 l=40 w=2"]
+    print(json.dumps({
+        "metric": "time per update, compressed (FastHALS-RP) vs full-data FastHALS, 20000x5000 r=20",
+        "value": d["FastHALS-RP"]["ms_per_update"] / 1e3, "unit": "s", "n_gpus": 1,
+        "steps": args.steps, "higher_is_better": False, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": "dense planted 20000x5000 and a face-sized 400x4096 image-like "
+                               "problem; BF16 copy of X for the sketch, compression and the "
+                               "full-data passes; 500 iterations from U[0,1) for the errors",
+                   "x_contraction_dtype": "bf16"},
+        "results": rows}))
+    ctx.close()
+
+
+def run_sweep(args):
+    """The k x w study of Section 5.1 (Figure 5.3) on the GPU: FastHALS-RP errors after 300
+    iterations for k = 10..50 components and w = 1..5 power iterations (l = k + 10), against
+    full-data FastHALS with the same k and start, on image-like data (4096 pixels x 20000
+    samples, the configured blob recipe), with the spectrum's decay rate p (Section 5.2) from
+    the singular values of the compressed data."""
+    import torch
+    from paper_1712_02248_gb300 import inputs
+    from paper_1712_02248_gb300 import nmf_rp as N
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    ctx = N.Context(0)
+    pr = inputs.images(seed=args.seed + 6, n_samples=20000, r=50, ell=60, w=3)
+    m, n = pr.X.shape
+    X = torch.from_numpy(pr.X).to(dev)
+    Xq = N.nmf_quantize(ctx, X, prec="bf16")
+    iters = 300
+    grid, full, times = {}, {}, {}
+    spectrum = None
+    for k in (10, 20, 30, 40, 50):
+        ell = k + 10
+        W0 = torch.from_numpy(np.ascontiguousarray(pr.W0[:, :k])).to(dev)
+        H0 = torch.from_numpy(np.ascontiguousarray(pr.H0[:k])).to(dev)
+        pf = N.params(m, n, k, ell, prec="bf16")
+        W, H = W0.clone(), H0.clone()
+        N.nmf_iterate_full(ctx, pf, Xq, W, H, iters)
+        full[k] = N.nmf_residual(ctx, pf, X, W, H)[0]
+        for w in (1, 2, 3, 4, 5):
+            p = N.params(m, n, k, ell, power_iters=w, iters=iters, prec="bf16",
+                         seed=args.seed + 100 * k + w, residual_every=0)
+            W, H = W0.clone(), H0.clone()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(ctx.stream)
+            e, _ = N.nmf_solve(ctx, p, X, W, H, init="given")
+            b.record(ctx.stream)
+            b.synchronize()
+            grid[f"k={k} w={w}"] = e
+            times[f"k={k} w={w}"] = a.elapsed_time(b) / 1e3
+            if k == 50 and w == 5:
+                QL, QR = N.nmf_sketch(ctx, p, Xq)
+                Xhat, _ = N.nmf_compress(ctx, p, Xq, QL, QR)
+                spectrum = N.nmf_spectrum(ctx, Xhat)
+    best = {k: min((1, 2, 3, 4, 5), key=lambda w: grid[f"k={k} w={w}"]) for k in full}
+    p_decay = N.nmf_decay_rate(spectrum, 1e-2)
+    print(json.dumps({
+        "metric": "k x w sweep (Figure 5.3): FastHALS-RP error / full FastHALS error, images 4096x20000",
+        "value": float(np.median([grid[f"k={k} w={best[k]}"] / full[k] for k in full])),
+        "unit": "ratio", "n_gpus": 1, "higher_is_better": False, "dtype": "bf16",
+        "data": "synthetic image-like (configured blob recipe)",
+        "config": {"workload": "image-like 4096x20000, k = 10..50, w = 1..5, l = k + 10, 300 "
+                               "iterations from U[0,1), BF16 copy of X",
+                   "iterations": iters},
+        "rp_error": grid, "full_error": {str(k): v for k, v in full.items()},
+        "solve_s": times, "best_w": {str(k): v for k, v in best.items()},
+        "decay_rate_p": p_decay, "spectrum_top": spectrum[:10]}))
+    ctx.close()
+
+
 def run_warmstart(args):
     """Learned warm start on planted 8192 x 2048 matrices (r = 16, l = 32, 2 % noise, Exp(1)
     factors): train on --train-count matrices, then on --heldout others report iterations and
@@ -563,7 +706,8 @@ def main():
     if args.config != "dense":
         if int(os.environ.get("RANK", 0)) == 0:
             {"batched": run_batched, "images": run_images, "warmstart": run_warmstart,
-             "passes": run_passes, "iterate": run_iterate}[args.config](args)
+             "passes": run_passes, "iterate": run_iterate, "full": run_full,
+             "sweep": run_sweep}[args.config](args)
         return
     import torch
     rank, local_rank, world = dist_env()

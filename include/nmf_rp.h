@@ -291,6 +291,40 @@ nmf_status nmf_iterate_full(nmf_ctx* ctx, const nmf_params* p, const void* X, in
                             float* W, float* H, int32_t iters);
 
 /*
+ * Sparse X (Section 5.2 applies the methods to a sparse term-frequency matrix). X is m x n in CSR
+ * form: row_ptr (m + 1 int64, row_ptr[0] = 0, row_ptr[m] = nnz), col (nnz int32 column indices,
+ * distinct within a row, any order) and val (nnz FP32 values), all device arrays owned by the
+ * caller; n < 2^31. Each call builds the transpose (CSC form, rows of a column in increasing
+ * order) in the context's workspace, so X^T U is a gather like X V and every sum runs in a fixed
+ * order (results are bit-identical between runs). The products, the QRs and the updates are
+ * FP32 as for dense FP32 X; p->prec is not used.
+ *   nmf_sketch_csr:   as nmf_sketch (Section 3 Eq. 3.5 with a QR after every application).
+ *   nmf_compress_csr: as nmf_compress (X_hat = Q_L^T X, X_chk = X Q_R).
+ *   nmf_residual_csr: ||X - W H||_F / ||X||_F from ||X||^2 - 2 <X, W H> + <W^T W, H H^T> (the
+ *     first two over the nonzeros, FP64 sums; the Grams in FP32 within 256-row slabs, FP64 across
+ *     them), O(nnz r + (m + n) r^2) work; 1 <= r <= 128. Synchronises the stream.
+ *   nmf_solve_csr:    sketch (rank-deficient pass outputs repaired as with NMF_FLAG_ROBUST_QR),
+ *     compression, initialisation, then iterations in chunks of p->residual_every with the exact
+ *     sparse residual after each; stops at the first check <= p->target_rel_err (if > 0) or after
+ *     p->iters iterations. Synchronises the stream.
+ * Errors as for the dense calls; NMF_ERR_INVALID_ARG also for a NULL row_ptr, nnz < 0 or NULL
+ * col / val with nnz > 0.
+ */
+nmf_status nmf_sketch_csr(nmf_ctx* ctx, const nmf_params* p, const int64_t* row_ptr,
+                          const int32_t* col, const float* val, int64_t nnz,
+                          const float* omega_L, const float* omega_R, float* QL, float* QR);
+nmf_status nmf_compress_csr(nmf_ctx* ctx, const nmf_params* p, const int64_t* row_ptr,
+                            const int32_t* col, const float* val, int64_t nnz, const float* QL,
+                            const float* QR, float* Xhat, float* Xchk);
+nmf_status nmf_residual_csr(nmf_ctx* ctx, const nmf_params* p, const int64_t* row_ptr,
+                            const int32_t* col, const float* val, int64_t nnz, const float* W,
+                            const float* H, double* rel_err_host, double* err2_host,
+                            double* x2_host);
+nmf_status nmf_solve_csr(nmf_ctx* ctx, const nmf_params* p, int32_t init, const int64_t* row_ptr,
+                         const int32_t* col, const float* val, int64_t nnz, float* W, float* H,
+                         double* rel_err_host, int32_t* iters_done_host);
+
+/*
  * Singular values of the compressed data X_hat (ell x n, row-major FP32 device array owned by the
  * caller), descending, into sigma_host[0..ell). With X ~ Q_L X_hat (Section 3, Eq. 3.4) they are
  * the estimates the sketch gives of sigma_1..sigma_ell of X, whose decay sets how many power

@@ -168,6 +168,34 @@ cudaError_t launch_iterate_multi(const Launcher& L, const IterArgs* ia, const in
                                  const int* blocks, int nprob, void* ws, size_t ws_bytes,
                                  int* status, float* mon, const int* done_zero);
 
+// Sparse X (CSR: row pointers int64 m + 1, column indices int32 distinct within a row, FP32
+// values) and its transpose in CSC form (built once per matrix by launch_csc_build into `csc`,
+// csc_bytes(n, nnz) of device memory; ws: csc_ws_bytes).
+struct CsrView {
+  const int64_t* ptr;
+  const int* idx;
+  const float* val;
+};
+struct CscView {
+  int64_t* ptr;
+  int* idx;
+  float* val;
+};
+size_t csc_bytes(int64_t n, int64_t nnz);
+size_t csc_ws_bytes(int64_t m, int64_t n, int64_t nnz);
+cudaError_t launch_csc_build(const Launcher& L, const int64_t* ptr, const int* idx,
+                             const float* val, int64_t m, int64_t n, int64_t nnz, void* csc,
+                             void* ws, size_t ws_bytes, CscView* out);
+// Y = X V (m x ell) through the CSR form, Z = X^T U (n x ell) through the CSC form; either pair
+// may be null.
+cudaError_t launch_csr_dual(const Launcher& L, const CsrView& X, const CscView& XT, int64_t m,
+                            int64_t n, int ell, const float* V, const float* U, float* Y, float* Z);
+// out2[0] = ||X - W H||^2, out2[1] = ||X||^2 (device doubles) for sparse X.
+size_t sparse_residual_ws_bytes(int64_t m, int64_t n, int r);
+cudaError_t launch_sparse_residual(const Launcher& L, const CsrView& X, int64_t m, int64_t n,
+                                   const float* W, const float* H, int r, double* out2, void* ws,
+                                   size_t ws_bytes);
+
 // Singular values of X_hat (ell x n, ell <= 128), descending, into sigma (ell floats, device).
 size_t spectrum_ws_bytes(int64_t n, int ell);
 cudaError_t launch_spectrum(const Launcher& L, int64_t n, int ell, const float* Xhat, void* ws,

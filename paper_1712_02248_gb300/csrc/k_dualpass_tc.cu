@@ -752,20 +752,16 @@ Plan plan_for(int64_t m, int64_t n, int ell, int split, bool f8 = false) {
     p.ctas = p.colgroups;
     return p;
   }
-  // row groups in proportion to each column group's cost, then one more at a time to the group
-  // whose CTAs carry the most, while CTAs are left. A tile costs its bytes plus a fixed part (its
-  // MMAs, conversion and barriers, taken as half of a full tile), so the partial last tile of a
-  // row costs 1/2 + 1/2 of its fraction of 128 columns (in half-tile units below)
+  // row groups in proportion to each column group's tiles, then one more at a time to the group
+  // whose CTAs carry the most tiles, while CTAs are left. Every tile counts in full, the partial
+  // last one too: measured, its MMAs, FP8 conversion and barriers cost about as much as a full
+  // tile's (weighting it by its bytes left one CTA with 79 such tiles and doubled the FP8 pass)
   std::vector<int64_t> width(p.colgroups);
   std::vector<int> R(p.colgroups);
   int used = 0;
-  const int64_t tail = n - (p.coltiles - 1) * kCols;   // columns of the last tile
-  const int64_t total = 2 * (p.coltiles - 1) * kCols + kCols + tail;
   for (int g = 0; g < p.colgroups; ++g) {
-    const int64_t t1 = std::min<int64_t>(p.coltiles, (g + 1) * p.tiles_per_group);
-    const int64_t full = t1 - g * p.tiles_per_group - (t1 == p.coltiles ? 1 : 0);
-    width[g] = 2 * full * kCols + (t1 == p.coltiles ? kCols + tail : 0);
-    int r = static_cast<int>(static_cast<double>(sms) * width[g] / total);
+    width[g] = std::min<int64_t>(p.coltiles, (g + 1) * p.tiles_per_group) - g * p.tiles_per_group;
+    int r = static_cast<int>(static_cast<double>(sms) * width[g] / p.coltiles);
     r = std::max(1, std::min<int>(r, static_cast<int>(p.rowblocks)));
     R[g] = r;
     used += r;

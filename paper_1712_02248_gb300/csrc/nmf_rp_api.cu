@@ -323,13 +323,12 @@ size_t sketch_ws(const nmf_params* p, bool need_omega) {
 
 // Both chains of Eq. 3.5 advance together: pass 0 applies X to Omega_L and X^T to Omega_R; pass
 // p >= 1 applies X to one chain's n-side basis and X^T to the other chain's m-side basis.
-nmf_status sketch_impl(nmf_ctx* ctx, const nmf_params* p, const void* X, int64_t ldx,
-                       const float* omega_L, const float* omega_R, float* QL, float* QR, Arena a,
-                       bool robust = false) {
+// `pass(V, U, Y, Z)` runs one fused pass Y = X V, Z = X^T U over whatever form X has.
+template <typename Pass>
+nmf_status sketch_core(nmf_ctx* ctx, const nmf_params* p, Pass pass, const float* omega_L,
+                       const float* omega_R, float* QL, float* QR, Arena& a, bool robust) {
   const int64_t m = p->m, n = p->n;
   const int l = p->ell;
-  const int bf16 = p->prec;   // element type of X for every pass
-  const bool simt = (p->flags & NMF_FLAG_SIMT_DUAL_PASS) != 0;
   float* mR = a.take<float>(m * l);   // right chain, m-side
   float* nL = a.take<float>(n * l);   // left chain, n-side
   if (!omega_L || !omega_R) {
@@ -345,25 +344,34 @@ nmf_status sketch_impl(nmf_ctx* ctx, const nmf_params* p, const void* X, int64_t
     }
   }
   nmf_status st;
-  auto orth = [&](float* Ym, float* Yn, int pass) {
-    return robust ? qr2_robust(ctx, Ym, m, Yn, n, l, p->seed + 0x9E37u * (pass + 1), a)
+  auto orth = [&](float* Ym, float* Yn, int k) {
+    return robust ? qr2_robust(ctx, Ym, m, Yn, n, l, p->seed + 0x9E37u * (k + 1), a)
                   : qr2(ctx, Ym, m, Yn, n, l, a);
   };
   // pass 0
-  if ((st = dual(ctx, X, bf16, m, n, ldx, l, omega_L, omega_R, QL, QR, a, simt)) != NMF_OK)
-    return st;
+  if ((st = pass(omega_L, omega_R, QL, QR)) != NMF_OK) return st;
   if ((st = orth(QL, QR, 0)) != NMF_OK) return st;
-  for (int pass = 1; pass <= 2 * p->power_iters; ++pass) {
-    if (pass & 1) {
+  for (int k = 1; k <= 2 * p->power_iters; ++k) {
+    if (k & 1) {
       // right chain: X * (n-side) -> m-side; left chain: X^T * (m-side) -> n-side
-      if ((st = dual(ctx, X, bf16, m, n, ldx, l, QR, QL, mR, nL, a, simt)) != NMF_OK) return st;
-      if ((st = orth(mR, nL, pass)) != NMF_OK) return st;
+      if ((st = pass(QR, QL, mR, nL)) != NMF_OK) return st;
+      if ((st = orth(mR, nL, k)) != NMF_OK) return st;
     } else {
-      if ((st = dual(ctx, X, bf16, m, n, ldx, l, nL, mR, QL, QR, a, simt)) != NMF_OK) return st;
-      if ((st = orth(QL, QR, pass)) != NMF_OK) return st;
+      if ((st = pass(nL, mR, QL, QR)) != NMF_OK) return st;
+      if ((st = orth(QL, QR, k)) != NMF_OK) return st;
     }
   }
   return NMF_OK;
+}
+
+nmf_status sketch_impl(nmf_ctx* ctx, const nmf_params* p, const void* X, int64_t ldx,
+                       const float* omega_L, const float* omega_R, float* QL, float* QR, Arena a,
+                       bool robust = false) {
+  const bool simt = (p->flags & NMF_FLAG_SIMT_DUAL_PASS) != 0;
+  auto pass = [&](const float* V, const float* U, float* Y, float* Z) {
+    return dual(ctx, X, p->prec, p->m, p->n, ldx, p->ell, V, U, Y, Z, a, simt);
+  };
+  return sketch_core(ctx, p, pass, omega_L, omega_R, QL, QR, a, robust);
 }
 
 __global__ void transpose_kernel(const float* __restrict__ in, int64_t rows, int cols,
@@ -661,6 +669,214 @@ nmf_status nmf_last_solve_info(const nmf_ctx* ctx, int32_t* iters, int32_t* exac
 nmf_status nmf_last_batch_info(const nmf_ctx* ctx, int32_t* rows_per_block) {
   if (!ctx || !rows_per_block) return NMF_ERR_INVALID_ARG;
   *rows_per_block = ctx->last_batch_rows_per_block;
+  return NMF_OK;
+}
+
+// ---------------------------------------------------------------- sparse X (CSR)
+
+nmf_status check_csr(nmf_ctx* ctx, const nmf_params* p, const int64_t* row_ptr, const int32_t* col,
+                     const float* val, int64_t nnz) {
+  if (!row_ptr || nnz < 0 || (nnz > 0 && (!col || !val)))
+    return fail(ctx, NMF_ERR_INVALID_ARG, "bad CSR arrays (row_ptr, col, val, nnz)");
+  if (p->n > 0x7fffffffLL) return fail(ctx, NMF_ERR_INVALID_ARG, "n must fit in int32 columns");
+  return NMF_OK;
+}
+
+// Workspace of a sparse call beyond `extra`: the CSC transpose, then the larger of its build
+// scratch and the call's own scratch.
+size_t csr_ws(const nmf_params* p, int64_t nnz, size_t extra) {
+  return nmfrp::csc_bytes(p->n, nnz) + 1024 +
+         std::max(nmfrp::csc_ws_bytes(p->m, p->n, nnz) + 1024, extra);
+}
+
+nmf_status csr_prepare(nmf_ctx* ctx, const nmf_params* p, const int64_t* row_ptr,
+                       const int32_t* col, const float* val, int64_t nnz, Arena& a,
+                       nmfrp::CsrView* X, nmfrp::CscView* XT) {
+  X->ptr = row_ptr;
+  X->idx = col;
+  X->val = val;
+  void* csc = a.take<char>(nmfrp::csc_bytes(p->n, nnz));
+  size_t rest = 0;
+  void* ws = a.rest(&rest);   // the build's counts: free again once the transpose is placed
+  NMF_CUDA(nmfrp::launch_csc_build(launcher(ctx), row_ptr, col, val, p->m, p->n, nnz, csc, ws,
+                                   rest, XT),
+           "CSC transpose");
+  return NMF_OK;
+}
+
+nmf_status csr_pass(nmf_ctx* ctx, const nmf_params* p, const nmfrp::CsrView& X,
+                    const nmfrp::CscView& XT, const float* V, const float* U, float* Y, float* Z) {
+  Phase ph(ctx, NMF_PHASE_DUAL_PASS);
+  NMF_CUDA(nmfrp::launch_csr_dual(launcher(ctx), X, XT, p->m, p->n, p->ell, V, U, Y, Z),
+           "sparse pass");
+  return NMF_OK;
+}
+
+nmf_status csr_compress(nmf_ctx* ctx, const nmf_params* p, const nmfrp::CsrView& X,
+                        const nmfrp::CscView& XT, const float* QL, const float* QR, float* Xhat,
+                        float* Xchk, Arena a) {
+  const int64_t n = p->n;
+  const int l = p->ell;
+  float* XhatT = a.take<float>(n * l);
+  nmf_status st = csr_pass(ctx, p, X, XT, QR, QL, Xchk, XhatT);
+  if (st != NMF_OK) return st;
+  dim3 grid(static_cast<unsigned>(cdiv(n, 32)), static_cast<unsigned>(cdiv(l, 32)));
+  transpose_kernel<<<grid, dim3(32, 8), 0, ctx->stream>>>(XhatT, n, l, Xhat);
+  ctx->launches++;
+  NMF_CUDA(cudaGetLastError(), "transpose");
+  return NMF_OK;
+}
+
+nmf_status csr_residual(nmf_ctx* ctx, const nmf_params* p, const nmfrp::CsrView& X,
+                        const float* W, const float* H, double* rel, double* e2o, double* x2o,
+                        Arena a) {
+  size_t rest = 0;
+  void* ws = a.rest(&rest);
+  Phase ph(ctx, NMF_PHASE_RESIDUAL);
+  NMF_CUDA(nmfrp::launch_sparse_residual(launcher(ctx), X, p->m, p->n, W, H, p->r, ctx->d_res, ws,
+                                         rest),
+           "sparse residual");
+  ph.end();
+  NMF_CUDA(cudaMemcpyAsync(ctx->h_res, ctx->d_res, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                           ctx->stream),
+           "residual copy");
+  NMF_CUDA(cudaStreamSynchronize(ctx->stream), "residual sync");
+  const double e2 = ctx->h_res[0], x2 = ctx->h_res[1];
+  if (e2o) *e2o = e2;
+  if (x2o) *x2o = x2;
+  if (!std::isfinite(e2) || !std::isfinite(x2))
+    return fail(ctx, NMF_ERR_NOT_FINITE, "residual is not finite");
+  // the expanded form can round a tiny error below zero
+  if (rel) *rel = x2 > 0 ? std::sqrt(std::max(e2, 0.0) / x2) : std::sqrt(std::max(e2, 0.0));
+  return NMF_OK;
+}
+
+nmf_status nmf_sketch_csr(nmf_ctx* ctx, const nmf_params* p, const int64_t* row_ptr,
+                          const int32_t* col, const float* val, int64_t nnz,
+                          const float* omega_L, const float* omega_R, float* QL, float* QR) {
+  if (!ctx) return NMF_ERR_INVALID_ARG;
+  nmf_status st = check_params(ctx, p);
+  if (st != NMF_OK) return st;
+  if ((st = check_csr(ctx, p, row_ptr, col, val, nnz)) != NMF_OK) return st;
+  if (!QL || !QR) return fail(ctx, NMF_ERR_INVALID_ARG, "QL/QR is NULL");
+  DeviceGuard g(ctx->device);
+  if ((st = ensure_ws(ctx, csr_ws(p, nnz, sketch_ws(p, !omega_L || !omega_R)))) != NMF_OK)
+    return st;
+  Arena a{static_cast<char*>(ctx->ws), ctx->ws_bytes};
+  nmfrp::CsrView X;
+  nmfrp::CscView XT;
+  if ((st = csr_prepare(ctx, p, row_ptr, col, val, nnz, a, &X, &XT)) != NMF_OK) return st;
+  auto pass = [&](const float* V, const float* U, float* Y, float* Z) {
+    return csr_pass(ctx, p, X, XT, V, U, Y, Z);
+  };
+  return sketch_core(ctx, p, pass, omega_L, omega_R, QL, QR, a,
+                     (p->flags & NMF_FLAG_ROBUST_QR) != 0);
+}
+
+nmf_status nmf_compress_csr(nmf_ctx* ctx, const nmf_params* p, const int64_t* row_ptr,
+                            const int32_t* col, const float* val, int64_t nnz, const float* QL,
+                            const float* QR, float* Xhat, float* Xchk) {
+  if (!ctx) return NMF_ERR_INVALID_ARG;
+  nmf_status st = check_params(ctx, p);
+  if (st != NMF_OK) return st;
+  if ((st = check_csr(ctx, p, row_ptr, col, val, nnz)) != NMF_OK) return st;
+  if (!QL || !QR || !Xhat || !Xchk) return fail(ctx, NMF_ERR_INVALID_ARG, "NULL output");
+  DeviceGuard g(ctx->device);
+  if ((st = ensure_ws(ctx, csr_ws(p, nnz, sizeof(float) * p->n * p->ell + 1024))) != NMF_OK)
+    return st;
+  Arena a{static_cast<char*>(ctx->ws), ctx->ws_bytes};
+  nmfrp::CsrView X;
+  nmfrp::CscView XT;
+  if ((st = csr_prepare(ctx, p, row_ptr, col, val, nnz, a, &X, &XT)) != NMF_OK) return st;
+  return csr_compress(ctx, p, X, XT, QL, QR, Xhat, Xchk, a);
+}
+
+nmf_status nmf_residual_csr(nmf_ctx* ctx, const nmf_params* p, const int64_t* row_ptr,
+                            const int32_t* col, const float* val, int64_t nnz, const float* W,
+                            const float* H, double* rel_err_host, double* err2_host,
+                            double* x2_host) {
+  if (!ctx) return NMF_ERR_INVALID_ARG;
+  if (!p || p->m < 1 || p->n < 1 || p->r < 1 || p->r > 128)
+    return fail(ctx, NMF_ERR_INVALID_ARG, "bad sizes (m, n >= 1, 1 <= r <= 128)");
+  nmf_status st = check_csr(ctx, p, row_ptr, col, val, nnz);
+  if (st != NMF_OK) return st;
+  if (!W || !H || !rel_err_host) return fail(ctx, NMF_ERR_INVALID_ARG, "NULL argument");
+  DeviceGuard g(ctx->device);
+  if ((st = ensure_ws(ctx, nmfrp::sparse_residual_ws_bytes(p->m, p->n, p->r) + 1024)) != NMF_OK)
+    return st;
+  Arena a{static_cast<char*>(ctx->ws), ctx->ws_bytes};
+  nmfrp::CsrView X{row_ptr, col, val};
+  return csr_residual(ctx, p, X, W, H, rel_err_host, err2_host, x2_host, a);
+}
+
+nmf_status nmf_solve_csr(nmf_ctx* ctx, const nmf_params* p, int32_t init, const int64_t* row_ptr,
+                         const int32_t* col, const float* val, int64_t nnz, float* W, float* H,
+                         double* rel_err_host, int32_t* iters_done_host) {
+  if (!ctx) return NMF_ERR_INVALID_ARG;
+  nmf_status st = check_params(ctx, p);
+  if (st != NMF_OK) return st;
+  if ((st = check_csr(ctx, p, row_ptr, col, val, nnz)) != NMF_OK) return st;
+  if (!W || !H) return fail(ctx, NMF_ERR_INVALID_ARG, "W/H is NULL");
+  if (init != NMF_INIT_GIVEN && init != NMF_INIT_NNDSVD && init != NMF_INIT_MLP)
+    return fail(ctx, NMF_ERR_INVALID_ARG, "unknown init %d", init);
+  if (init == NMF_INIT_MLP && (!ctx->warm || ctx->warm_r != p->r))
+    return fail(ctx, NMF_ERR_INVALID_ARG, "no warm-start network for r = %d (nmf_set_warmstart)", p->r);
+  if (p->iters < 0) return fail(ctx, NMF_ERR_INVALID_ARG, "iters < 0");
+  DeviceGuard g(ctx->device);
+  const int64_t m = p->m, n = p->n, l = p->ell;
+  size_t scratch = sketch_ws(p, true);
+  scratch = std::max(scratch, sizeof(float) * n * l + 1024);
+  scratch = std::max(scratch, nmfrp::iterate_ws_bytes(m, n, p->r, p->ell));
+  scratch = std::max(scratch, nmfrp::iterate_persistent_ws_bytes(p->r, p->ell));
+  scratch = std::max(scratch, nmfrp::sparse_residual_ws_bytes(m, n, p->r));
+  scratch = std::max(scratch, nmfrp::nndsvd_ws_bytes(m, n, p->r, p->ell));
+  scratch = std::max(scratch, warm_ws_bytes(p, std::max(ctx->warm_hidden, 256)));
+  const size_t fixed = sizeof(float) * (2 * (m * l + n * l)) + 4096;   // QL QR Xhat Xchk
+  if ((st = ensure_ws(ctx, csr_ws(p, nnz, fixed + scratch))) != NMF_OK) return st;
+  Arena a{static_cast<char*>(ctx->ws), ctx->ws_bytes};
+  nmfrp::CsrView X;
+  nmfrp::CscView XT;
+  if ((st = csr_prepare(ctx, p, row_ptr, col, val, nnz, a, &X, &XT)) != NMF_OK) return st;
+  float* QL = a.take<float>(m * l);
+  float* QR = a.take<float>(n * l);
+  float* Xhat = a.take<float>(l * n);
+  float* Xchk = a.take<float>(m * l);
+  auto pass = [&](const float* V, const float* U, float* Y, float* Z) {
+    return csr_pass(ctx, p, X, XT, V, U, Y, Z);
+  };
+  // sparse term-count matrices can be numerically rank deficient: repairing QRs throughout
+  Arena sa = a;
+  if ((st = sketch_core(ctx, p, pass, nullptr, nullptr, QL, QR, sa, true)) != NMF_OK) return st;
+  if ((st = csr_compress(ctx, p, X, XT, QL, QR, Xhat, Xchk, a)) != NMF_OK) return st;
+  if (init == NMF_INIT_NNDSVD) {
+    Phase ph(ctx, NMF_PHASE_INIT);
+    size_t rest = 0;
+    void* ws = a.rest(&rest);
+    cudaError_t e = nmfrp::launch_nndsvd(launcher(ctx), m, n, p->r, p->ell, QL, Xhat, W, H, ws,
+                                         rest, ctx->d_status);
+    if (e == cudaErrorNotSupported) return fail(ctx, NMF_ERR_UNSUPPORTED, "nndsvd not available");
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "nndsvd");
+  } else if (init == NMF_INIT_MLP) {
+    Phase ph(ctx, NMF_PHASE_INIT);
+    if ((st = warm_init(ctx, p, QL, Xhat, W, H, a)) != NMF_OK) return st;
+  }
+  // iterate in chunks of residual_every; the exact sparse residual (nnz-proportional) after each
+  const int every = p->residual_every > 0 ? p->residual_every : std::max(p->iters, 1);
+  int done = 0, checks = 0;
+  double rel = 0.0;
+  do {
+    const int k = std::min(every, p->iters - done);
+    if (k > 0 && (st = iterate_impl(ctx, p, QL, QR, Xhat, Xchk, W, H, k, a)) != NMF_OK) return st;
+    done += std::max(k, 0);
+    if ((st = csr_residual(ctx, p, X, W, H, &rel, nullptr, nullptr, a)) != NMF_OK) return st;
+    ++checks;
+    if ((st = take_status(ctx)) != NMF_OK) return st;
+    if (p->target_rel_err > 0.0 && rel <= p->target_rel_err) break;
+  } while (done < p->iters);
+  ctx->last_iters = done;
+  ctx->last_checks = checks;
+  if (rel_err_host) *rel_err_host = rel;
+  if (iters_done_host) *iters_done_host = done;
   return NMF_OK;
 }
 

@@ -12,6 +12,7 @@ Workloads (shapes of the paper's problem, Section 2, Eq. 2.1: X ~ W H, X non-neg
                   70 % zeroed, 256-level Poisson-like noise (image-like data as in Section 5.1)
   planted_batch   independent planted problems with m, n, r drawn uniformly from ranges
   planted_warm    8192 x 2048, r = 16, Exp(1) factors + 2 % Gaussian noise
+  sparse_counts   topic-model term counts in CSR form (documents x words), for the sparse path
 
 The Gaussian test matrices Omega_L (n x l) and Omega_R (m x l) of Section 3 and the U[0, 1)
 initial factors are drawn here too (the paper: Omega ~ N(0,1); random initialisation).
@@ -117,6 +118,71 @@ def images(seed=0, n_samples=100000, side=64, r=50, ell=70, w=3, parts=50):
         X[:, c:c + k] = np.minimum(1.0, rng.poisson(255.0 * clean) / 255.0).astype(np.float32)
     oL, oR, W0, H0 = _init_and_omega(rng, m, n_samples, r, ell)
     return Problem(X, r, ell, w, oL, oR, W0, H0, seed, f"images_{m}x{n_samples}_r{r}")
+
+
+@dataclasses.dataclass
+class SparseProblem:
+    row_ptr: np.ndarray    # m + 1 int64
+    col: np.ndarray        # nnz int32 (increasing within a row)
+    val: np.ndarray        # nnz float32 counts
+    shape: tuple
+    r: int
+    ell: int
+    w: int
+    omega_L: np.ndarray    # n x ell float32
+    omega_R: np.ndarray    # m x ell float32
+    W0: np.ndarray         # m x r float32
+    H0: np.ndarray         # r x n float32
+    seed: int
+
+    def dense(self):
+        """The m x n matrix as a dense float64 array (small problems only)."""
+        m, n = self.shape
+        X = np.zeros((m, n))
+        rows = np.repeat(np.arange(m), np.diff(self.row_ptr))
+        X[rows, self.col] = self.val
+        return X
+
+
+def sparse_counts(seed=0, m=5000, n=1000, r=60, ell=72, w=9, topics=20, mean_len=100,
+                  alpha=0.1):
+    """Term-count matrix of m documents over n words drawn from a topic model (stands in for the
+    20 Newsgroups frequency matrix of Section 5.2, not available here): word popularity
+    ~ 1 / (rank + 10), each of `topics` topics boosts a random 5 % of the words by Exp(1) x 20;
+    a document draws its length from Poisson(mean_len), its topic mix from Dirichlet(alpha) and
+    each word from its topic. Rows with no words and words never drawn stay empty."""
+    rng = np.random.default_rng(seed)
+    base = 1.0 / (np.arange(n) + 10.0)
+    base = base[rng.permutation(n)]
+    T = np.tile(base, (topics, 1))
+    for t in range(topics):
+        pick = rng.random(n) < 0.05
+        T[t, pick] *= 20.0 * rng.exponential(1.0, pick.sum())
+    T /= T.sum(axis=1, keepdims=True)
+    cumT = np.cumsum(T, axis=1)
+    theta = rng.dirichlet(np.full(topics, alpha), size=m)
+    cumth = np.cumsum(theta, axis=1)
+    lens = rng.poisson(mean_len, size=m)
+    doc = np.repeat(np.arange(m), lens)
+    u = rng.random(doc.size)
+    topic = np.empty(doc.size, dtype=np.int64)
+    for c in range(0, doc.size, 1 << 20):          # (tokens x topics) comparisons in chunks
+        sl = slice(c, c + (1 << 20))
+        topic[sl] = np.minimum((u[sl, None] > cumth[doc[sl]]).sum(axis=1), topics - 1)
+    word = np.empty(doc.size, dtype=np.int64)
+    u2 = rng.random(doc.size)
+    for t in range(topics):
+        sel = topic == t
+        word[sel] = np.minimum(np.searchsorted(cumT[t], u2[sel]), n - 1)
+    keys, counts = np.unique(doc * n + word, return_counts=True)
+    rows = keys // n
+    col = (keys % n).astype(np.int32)
+    row_ptr = np.zeros(m + 1, dtype=np.int64)
+    np.add.at(row_ptr, rows + 1, 1)
+    row_ptr = np.cumsum(row_ptr)
+    omega_L, omega_R, W0, H0 = _init_and_omega(rng, m, n, r, ell)
+    return SparseProblem(row_ptr, col, counts.astype(np.float32), (m, n), r, ell, w, omega_L,
+                         omega_R, W0, H0, seed)
 
 
 def batch_specs(count=256, seed=0, m_range=(500, 8000), n_range=(200, 3000), r_range=(5, 40),

@@ -36,7 +36,8 @@ EXPORTS = ["nmf_create", "nmf_destroy", "nmf_set_stream", "nmf_last_error", "nmf
            "nmf_mlp_loss_grad", "nmf_mlp_adam", "nmf_mlp_train_step", "nmf_warmstart_apply",
            "nmf_set_warmstart", "nmf_quantized_bytes", "nmf_set_wait_limit",
            "nmf_monitor_terms", "nmf_gini", "nmf_iterate_full", "nmf_spectrum",
-           "nmf_decay_rate"]
+           "nmf_decay_rate", "nmf_sketch_csr", "nmf_compress_csr", "nmf_residual_csr",
+           "nmf_solve_csr"]
 PHASES = ["quantize", "dual_pass", "qr", "iterate", "residual", "init"]
 
 
@@ -88,6 +89,14 @@ _c = {
     "nmf_gini": _sig("nmf_gini", ctypes.c_int, [_vp, _vp, _i64, _D]),
     "nmf_iterate_full": _sig("nmf_iterate_full", ctypes.c_int, [_vp, _P, _vp, _i64, _vp, _vp, _i32]),
     "nmf_spectrum": _sig("nmf_spectrum", ctypes.c_int, [_vp, _i64, _i32, _vp, _D]),
+    "nmf_sketch_csr": _sig("nmf_sketch_csr", ctypes.c_int,
+                           [_vp, _P, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp]),
+    "nmf_compress_csr": _sig("nmf_compress_csr", ctypes.c_int,
+                             [_vp, _P, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp]),
+    "nmf_residual_csr": _sig("nmf_residual_csr", ctypes.c_int,
+                             [_vp, _P, _vp, _vp, _vp, _i64, _vp, _vp, _D, _D, _D]),
+    "nmf_solve_csr": _sig("nmf_solve_csr", ctypes.c_int,
+                          [_vp, _P, _i32, _vp, _vp, _vp, _i64, _vp, _vp, _D, ctypes.POINTER(_i32)]),
     "nmf_decay_rate": _sig("nmf_decay_rate", ctypes.c_int, [_D, _i32, ctypes.c_double, _D]),
     "nmf_last_solve_info": _sig("nmf_last_solve_info", ctypes.c_int,
                                 [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
@@ -483,6 +492,73 @@ def nmf_iterate_full(ctx, p, X, W, H, iters):
     ctx._check(_c["nmf_iterate_full"](ctx.handle, ctypes.byref(p), _ptr(X), ldx, _ptr(W),
                                       _ptr(H), int(iters)))
     return W, H
+
+
+class Csr:
+    """A sparse m x n matrix in CSR form on a CUDA device: row_ptr (int64, m + 1), col (int32,
+    distinct within a row), val (float32)."""
+
+    def __init__(self, row_ptr, col, val, shape):
+        if not (row_ptr.is_cuda and row_ptr.dtype == torch.int64 and row_ptr.is_contiguous()):
+            raise ValueError("row_ptr must be a contiguous int64 CUDA tensor")
+        if not (col.is_cuda and col.dtype == torch.int32 and col.is_contiguous()):
+            raise ValueError("col must be a contiguous int32 CUDA tensor")
+        _dev_f32(val, "val")
+        if row_ptr.numel() != shape[0] + 1 or col.numel() != val.numel():
+            raise ValueError("row_ptr must hold m + 1 entries and col / val nnz each")
+        self.row_ptr, self.col, self.val, self.shape = row_ptr, col, val, tuple(shape)
+        self.nnz = val.numel()
+
+    def _args(self):
+        return _ptr(self.row_ptr), _ptr(self.col), _ptr(self.val), self.nnz
+
+
+def _csr_check(p, X):
+    if not isinstance(X, Csr) or X.shape != (p.m, p.n):
+        raise ValueError(f"X must be a Csr of shape ({p.m}, {p.n})")
+
+
+def nmf_sketch_csr(ctx, p, X, omega_L=None, omega_R=None, QL=None, QR=None):
+    _csr_check(p, X)
+    QL = QL if QL is not None else _empty((p.m, p.ell), X.val)
+    QR = QR if QR is not None else _empty((p.n, p.ell), X.val)
+    ctx._check(_c["nmf_sketch_csr"](ctx.handle, ctypes.byref(p), *X._args(), _ptr(omega_L),
+                                    _ptr(omega_R), _ptr(QL), _ptr(QR)))
+    return QL, QR
+
+
+def nmf_compress_csr(ctx, p, X, QL, QR, Xhat=None, Xchk=None):
+    _csr_check(p, X)
+    Xhat = Xhat if Xhat is not None else _empty((p.ell, p.n), X.val)
+    Xchk = Xchk if Xchk is not None else _empty((p.m, p.ell), X.val)
+    ctx._check(_c["nmf_compress_csr"](ctx.handle, ctypes.byref(p), *X._args(),
+                                      _ptr(_dev_f32(QL, "QL")), _ptr(_dev_f32(QR, "QR")),
+                                      _ptr(Xhat), _ptr(Xchk)))
+    return Xhat, Xchk
+
+
+def nmf_residual_csr(ctx, p, X, W, H):
+    """(rel_err, ||X - W H||^2, ||X||^2) of sparse X; synchronises."""
+    _csr_check(p, X)
+    if W.shape != (p.m, p.r) or H.shape != (p.r, p.n):
+        raise ValueError(f"W must be ({p.m}, {p.r}) and H ({p.r}, {p.n})")
+    rel, e2, x2 = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    ctx._check(_c["nmf_residual_csr"](ctx.handle, ctypes.byref(p), *X._args(),
+                                      _ptr(_dev_f32(W, "W")), _ptr(_dev_f32(H, "H")),
+                                      ctypes.byref(rel), ctypes.byref(e2), ctypes.byref(x2)))
+    return rel.value, e2.value, x2.value
+
+
+def nmf_solve_csr(ctx, p, X, W, H, init="given"):
+    """Whole pipeline on sparse X; returns (rel_err, iterations run). W, H updated in place."""
+    _csr_check(p, X)
+    if W.shape != (p.m, p.r) or H.shape != (p.r, p.n):
+        raise ValueError(f"W must be ({p.m}, {p.r}) and H ({p.r}, {p.n})")
+    rel, it = ctypes.c_double(), ctypes.c_int32()
+    ctx._check(_c["nmf_solve_csr"](ctx.handle, ctypes.byref(p), INIT.get(init, init), *X._args(),
+                                   _ptr(_dev_f32(W, "W")), _ptr(_dev_f32(H, "H")),
+                                   ctypes.byref(rel), ctypes.byref(it)))
+    return rel.value, it.value
 
 
 def nmf_spectrum(ctx, Xhat):
