@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--profile", choices=["fp32", "bf16"], default=None,
                     help="run one short solve (20 iterations) for a profiler's launch list")
     ap.add_argument("--config", choices=["dense", "batched", "images", "warmstart", "passes",
-                                         "iterate", "full", "sweep"],
+                                         "iterate", "full", "sweep", "sparse"],
                     default="dense",
                     help="batched: 256 uneven problems through nmf_solve_batched against one "
                          "nmf_solve per problem; images: 4096 x 100000 image-like data, r = 50, "
@@ -53,8 +53,8 @@ def parse():
                          "r = 16; passes: one dual pass per element type of X; iterate: "
                          "nmf_iterate alone on image-shaped operands; full: compressed vs "
                          "full-data updates (Tables 5.2/5.3); sweep: the k x w grid of Figure "
-                         "5.3 with the spectral decay rate (separate JSON lines; not the "
-                         "headline)")
+                         "5.3 with the spectral decay rate; sparse: CSR term counts, "
+                         "200000 x 20000 (separate JSON lines; not the headline)")
     ap.add_argument("--train-count", type=int, default=256,
                     help="warmstart: planted training matrices (the full recipe uses 10000)")
     ap.add_argument("--heldout", type=int, default=32,
@@ -625,6 +625,68 @@ def run_sweep(args):
     ctx.close()
 
 
+def run_sparse(args):
+    """Sparse X (Section 5.2's setting scaled up: term counts of 200000 documents over 20000
+    words from the topic model of the inputs module, about 17 M nonzeros): nmf_solve_csr with
+    k = 60, r + r_ov = 72, w = 9 and 150 FastHALS-RP iterations from U[0,1), the exact sparse
+    residual every 50 iterations; phase times from the library's CUDA events, and the CSR pass's
+    throughput (row pointers, indices and values of the CSR and CSC forms read, l gathered FP32
+    values a nonzero on each side, Y and Z written)."""
+    import torch
+    from paper_1712_02248_gb300 import inputs
+    from paper_1712_02248_gb300 import nmf_rp as N
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    t0 = time.perf_counter()
+    sp = inputs.sparse_counts(args.seed + 8, m=200000, n=20000, r=60, ell=72, w=9)
+    t_gen = time.perf_counter() - t0
+    m, n = sp.shape
+    X = N.Csr(torch.from_numpy(sp.row_ptr).to(dev), torch.from_numpy(sp.col).to(dev),
+              torch.from_numpy(sp.val).to(dev), sp.shape)
+    ctx = N.Context(0)
+    p = N.params(m, n, 60, 72, power_iters=9, iters=150, seed=args.seed + 31, residual_every=50)
+    W0 = torch.from_numpy(sp.W0).to(dev)
+    H0 = torch.from_numpy(sp.H0).to(dev)
+    W, H = W0.clone(), H0.clone()
+    N.nmf_solve_csr(ctx, p, X, W, H)
+    ts = []
+    for _ in range(max(args.steps, 1)):
+        W.copy_(W0)
+        H.copy_(H0)
+        N.nmf_phase_times(ctx, reset=True)
+        N.nmf_set_profiling(ctx, True)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(ctx.stream)
+        e, it = N.nmf_solve_csr(ctx, p, X, W, H)
+        b.record(ctx.stream)
+        b.synchronize()
+        N.nmf_set_profiling(ctx, False)
+        ph = N.nmf_phase_times(ctx, reset=True)
+        ts.append(a.elapsed_time(b) / 1e3)
+    nnz, ell = X.nnz, 72
+    per_pass = 2 * (8 * nnz + 8 * (m + n)) + 2 * 4 * ell * nnz + 4 * ell * (m + n)
+    dp_ms, dp_n = ph["dual_pass"]
+    g = N.nmf_gini(ctx, H)
+    t_g = _timed_events(ctx.stream, lambda: N.nmf_gini(ctx, H), 3)
+    print(json.dumps({
+        "metric": "sparse 200000x20000 (17M nonzeros) k=60: nmf_solve_csr, 150 FastHALS-RP iterations",
+        "value": statistics.median(ts), "unit": "s", "n_gpus": 1, "steps": args.steps,
+        "higher_is_better": False, "dtype": "fp32", "data": "synthetic topic-model term counts",
+        "config": {"workload": "documents x words term counts (Section 5.2 stand-in, scaled up), "
+                               "k=60, l=72, w=9, 150 iterations, residual every 50",
+                   "m": m, "n": n, "nnz": nnz, "generation_s": t_gen},
+        "rel_err": e, "iters": it,
+        "phase_ms": {k: v[0] for k, v in ph.items()},
+        "phase_spans": {k: v[1] for k, v in ph.items()},
+        "csr_pass": {"bytes_per_pass": per_pass, "ms_per_pass": dp_ms / max(dp_n, 1),
+                     "achieved_gbs": per_pass / (dp_ms / max(dp_n, 1) * 1e-3) / 1e9,
+                     "note": "bytes counted as touched; the gathers hit L2 (V, U of 20000 x 72 "
+                             "and 200000 x 72 FP32 are 5.8 MB and 58 MB)"},
+        "gini_H": {"value": g, "entries": 60 * n, "ms": t_g * 1e3}}))
+    ctx.close()
+
+
 def run_warmstart(args):
     """Learned warm start on planted 8192 x 2048 matrices (r = 16, l = 32, 2 % noise, Exp(1)
     factors): train on --train-count matrices, then on --heldout others report iterations and
@@ -707,7 +769,7 @@ def main():
         if int(os.environ.get("RANK", 0)) == 0:
             {"batched": run_batched, "images": run_images, "warmstart": run_warmstart,
              "passes": run_passes, "iterate": run_iterate, "full": run_full,
-             "sweep": run_sweep}[args.config](args)
+             "sweep": run_sweep, "sparse": run_sparse}[args.config](args)
         return
     import torch
     rank, local_rank, world = dist_env()
@@ -879,10 +941,10 @@ def main():
     dp_achieved = dp_bytes / (dp_ms / dp_n * 1e-3) / 1e9
     shares = {k: v[0] for k, v in phases.items() if v[1] > 0}
     dom = max(shares, key=shares.get)
-    # DRAM bytes of one iterate_persistent_kernel launch (10 iterations) from an ncu capture of
-    # this workload (profiles/iterate_persistent_kernel_dense_20000x5000_r20.md: 10.19 MB read,
-    # nothing written back to DRAM within the launch): the slices are staged once a launch
-    it_traffic = 10.192e6 if (m, n, r, ell) == (20000, 5000, 20, 40) else None
+    # DRAM bytes of one iterate_persistent_kernel launch (10 iterations): none current. The
+    # capture in profiles/iterate_persistent_kernel_dense_20000x5000_r20.md (10.19 MB read) predates
+    # the kernel's settable grid-barrier budget
+    it_traffic = None
     roofline = {"bound": "alu", "achieved": it_achieved, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": it_achieved / alu_peak, "traffic": it_traffic,
                 "kernel": "iterate_persistent_kernel (FastHALS-RP iterations)",
@@ -891,10 +953,11 @@ def main():
                 "dominant_phase": dom,
                 "phase_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in phases.items()},
                 "phase_spans_per_step": {k: v[1] // args.steps for k, v in phases.items()}}
-    # DRAM bytes of the dual pass: none current. The last capture of the BF16 launch
-    # (profiles/dual_pass_tc_kernel_dense_20000x5000_l40_bf16.md: 203.58 MB read, 6.04 MB
-    # written, no re-reads) predates the FP8 variant's changes to the kernel's source
-    dp_traffic = None
+    # DRAM bytes of one BF16 pass launch at this workload from an ncu capture of the current
+    # kernel (profiles/dual_pass_tc_kernel_dense_20000x5000_l40_bf16.md: 207.92 MB read, 6.09 MB
+    # written: X and the operand copies read once)
+    dp_traffic = (207.92e6 + 6.09e6) if ((m, n, ell) == (20000, 5000, 40) and
+                                         headline[0] == "bf16") else None
     roofline_hbm = {"bound": "hbm", "achieved": dp_achieved, "peak": hbm_peak, "unit": "GB/s",
                     "frac": dp_achieved / hbm_peak, "traffic": dp_traffic,
                     "kernel": "dual pass over X (dual_pass_tc_kernel + operand prep + slot sums)",

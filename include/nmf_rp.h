@@ -416,6 +416,14 @@ nmf_status nmf_mlp_train_step(nmf_ctx* ctx, int32_t F, int32_t hidden, int32_t r
 nmf_status nmf_warmstart_apply(nmf_ctx* ctx, int64_t m, int64_t n, int32_t r, const float* Wb,
                                const float* Dw, const float* Hb, const float* Dh,
                                const float* hscale, float* W, float* H);
+/* Training targets of the two networks, the inverse of nmf_warmstart_apply where the solution is
+ * positive: Tw = sqrt(m) (W* - W_b) (m x r) and Th (n x r) with Th[c][j] = sqrt(n) (H*[j][c] -
+ * H_b[j][c]) / hscale_j (a zero hscale_j taken as 1). W_b, H_b, hscale as from
+ * nmf_warmstart_features, (W*, H*) the solution the networks learn to reach; device arrays owned
+ * by the caller. */
+nmf_status nmf_warmstart_targets(nmf_ctx* ctx, int64_t m, int64_t n, int32_t r, const float* Wb,
+                                 const float* Hb, const float* hscale, const float* Wstar,
+                                 const float* Hstar, float* Tw, float* Th);
 /* Copy the two networks (F = 3r inputs, host or device memory) into the context for
  * NMF_INIT_MLP; problems with another r are refused at solve time. */
 nmf_status nmf_set_warmstart(nmf_ctx* ctx, int32_t hidden, int32_t r, const float* params_w,

@@ -253,5 +253,9 @@ cudaError_t launch_adam(const Launcher& L, float* p, float* m, float* v, const f
 cudaError_t launch_warmstart_apply(const Launcher& L, int64_t m, int64_t n, int r,
                                    const float* Wb, const float* Dw, const float* Hb,
                                    const float* Dh, const float* hscale, float* W, float* H);
+cudaError_t launch_warmstart_targets(const Launcher& L, int64_t m, int64_t n, int r,
+                                     const float* Wb, const float* Hb, const float* hscale,
+                                     const float* Wstar, const float* Hstar, float* Tw,
+                                     float* Th);
 
 }  // namespace nmfrp

@@ -309,6 +309,40 @@ cudaError_t launch_adam(const Launcher& L, float* p, float* m, float* v, const f
   return cudaGetLastError();
 }
 
+// Training targets (the inverse of the apply map where the solution is positive):
+// Tw = sqrt(m) (W* - W_b) (m x r); Th[c][j] = sqrt(n) (H*[j][c] - H_b[j][c]) / hscale_j (n x r,
+// a zero scale taken as 1).
+__global__ void ws_targets_kernel(const float* __restrict__ Wb, const float* __restrict__ Ws,
+                                  int64_t m, const float* __restrict__ Hb,
+                                  const float* __restrict__ Hs, const float* __restrict__ hscale,
+                                  int64_t n, int r, float* __restrict__ Tw,
+                                  float* __restrict__ Th) {
+  const float sm = sqrtf(static_cast<float>(m)), sn = sqrtf(static_cast<float>(n));
+  const int64_t tw = m * r, tot = tw + n * r;
+  for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < tot;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    if (e < tw) {
+      Tw[e] = sm * (Ws[e] - Wb[e]);
+    } else {
+      const int64_t f = e - tw, c = f / r;
+      const int j = static_cast<int>(f - c * r);
+      const float h = hscale[j] > 0.f ? hscale[j] : 1.f;
+      const int64_t src = static_cast<int64_t>(j) * n + c;
+      Th[f] = sn * (Hs[src] - Hb[src]) / h;
+    }
+  }
+}
+
+cudaError_t launch_warmstart_targets(const Launcher& L, int64_t m, int64_t n, int r,
+                                     const float* Wb, const float* Hb, const float* hscale,
+                                     const float* Wstar, const float* Hstar, float* Tw,
+                                     float* Th) {
+  ws_targets_kernel<<<grid_1d(m * r + r * n), 256, 0, L.stream>>>(Wb, Wstar, m, Hb, Hstar, hscale,
+                                                                   n, r, Tw, Th);
+  L.count();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_warmstart_apply(const Launcher& L, int64_t m, int64_t n, int r,
                                    const float* Wb, const float* Dw, const float* Hb,
                                    const float* Dh, const float* hscale, float* W, float* H) {

@@ -19,6 +19,7 @@ namespace nmfrp {
 namespace {
 
 constexpr int kSpThreads = 256;     // 8 warps a block, one row a warp
+constexpr int kUnroll = 8;          // nonzeros whose gathers a warp issues together
 constexpr int kRowsPerBlockCount = 512;
 constexpr int kResThreads = 256;
 constexpr int kResBlocks = 1024;
@@ -41,20 +42,31 @@ __global__ void __launch_bounds__(kSpThreads) csr_spmm_kernel(const int64_t* __r
     for (int q = 0; q < KPL; ++q) acc[q] = 0.f;
     const int64_t e0 = ptr[i], e1 = ptr[i + 1];
     for (int64_t b = e0; b < e1; b += 32) {
-      // the warp fetches up to 32 nonzeros, then walks them one by one (broadcast by shuffle)
+      // the warp fetches up to 32 nonzeros, then walks them in groups of kUnroll (broadcast by
+      // shuffle): the group's gathers of V are issued before its FMAs, so kUnroll rows of V
+      // are in flight per lane; the FMAs still run in storage order
       const int64_t e = b + lane;
       const int c = e < e1 ? idx[e] : 0;
       const float x = e < e1 ? val[e] : 0.f;
       const int cnt = static_cast<int>(e1 - b < 32 ? e1 - b : 32);
-      for (int t = 0; t < cnt; ++t) {
-        const int ct = __shfl_sync(0xffffffffu, c, t);
-        const float xt = __shfl_sync(0xffffffffu, x, t);
-        const float* vr = V + static_cast<int64_t>(ct) * ell;
+      for (int t0 = 0; t0 < cnt; t0 += kUnroll) {
+        float v[kUnroll][KPL], xs[kUnroll];
 #pragma unroll
-        for (int q = 0; q < KPL; ++q) {
-          const int k = lane + 32 * q;
-          if (k < ell) acc[q] = fmaf(xt, __ldg(vr + k), acc[q]);
+        for (int u = 0; u < kUnroll; ++u) {
+          const int t = t0 + u < cnt ? t0 + u : cnt - 1;   // padded steps reuse a valid index
+          const int ct = __shfl_sync(0xffffffffu, c, t);
+          xs[u] = t0 + u < cnt ? __shfl_sync(0xffffffffu, x, t) : 0.f;
+          const float* vr = V + static_cast<int64_t>(ct) * ell;
+#pragma unroll
+          for (int q = 0; q < KPL; ++q) {
+            const int k = lane + 32 * q;
+            v[u][q] = k < ell ? __ldg(vr + k) : 0.f;
+          }
         }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u)
+#pragma unroll
+          for (int q = 0; q < KPL; ++q) acc[q] = fmaf(xs[u], v[u][q], acc[q]);
       }
     }
 #pragma unroll

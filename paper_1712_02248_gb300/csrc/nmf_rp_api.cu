@@ -1489,6 +1489,19 @@ nmf_status nmf_warmstart_apply(nmf_ctx* ctx, int64_t m, int64_t n, int32_t r, co
   return NMF_OK;
 }
 
+nmf_status nmf_warmstart_targets(nmf_ctx* ctx, int64_t m, int64_t n, int32_t r, const float* Wb,
+                                 const float* Hb, const float* hscale, const float* Wstar,
+                                 const float* Hstar, float* Tw, float* Th) {
+  if (!ctx) return NMF_ERR_INVALID_ARG;
+  if (m < 1 || n < 1 || r < 1 || !Wb || !Hb || !hscale || !Wstar || !Hstar || !Tw || !Th)
+    return fail(ctx, NMF_ERR_INVALID_ARG, "bad warm-start target arguments");
+  DeviceGuard g(ctx->device);
+  NMF_CUDA(nmfrp::launch_warmstart_targets(launcher(ctx), m, n, r, Wb, Hb, hscale, Wstar, Hstar,
+                                           Tw, Th),
+           "warm-start targets");
+  return NMF_OK;
+}
+
 nmf_status nmf_set_warmstart(nmf_ctx* ctx, int32_t hidden, int32_t r, const float* params_w,
                              const float* params_h) {
   if (!ctx) return NMF_ERR_INVALID_ARG;

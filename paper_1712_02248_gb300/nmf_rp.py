@@ -37,7 +37,7 @@ EXPORTS = ["nmf_create", "nmf_destroy", "nmf_set_stream", "nmf_last_error", "nmf
            "nmf_set_warmstart", "nmf_quantized_bytes", "nmf_set_wait_limit",
            "nmf_monitor_terms", "nmf_gini", "nmf_iterate_full", "nmf_spectrum",
            "nmf_decay_rate", "nmf_sketch_csr", "nmf_compress_csr", "nmf_residual_csr",
-           "nmf_solve_csr"]
+           "nmf_solve_csr", "nmf_warmstart_targets"]
 PHASES = ["quantize", "dual_pass", "qr", "iterate", "residual", "init"]
 
 
@@ -119,6 +119,8 @@ _c = {
     "nmf_warmstart_apply": _sig("nmf_warmstart_apply", ctypes.c_int,
                                 [_vp, _i64, _i64, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "nmf_set_warmstart": _sig("nmf_set_warmstart", ctypes.c_int, [_vp, _i32, _i32, _vp, _vp]),
+    "nmf_warmstart_targets": _sig("nmf_warmstart_targets", ctypes.c_int,
+                                  [_vp, _i64, _i64, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "nmf_last_batch_info": _sig("nmf_last_batch_info", ctypes.c_int, [_vp, ctypes.POINTER(_i32)]),
     "nmf_solve_batched": _sig("nmf_solve_batched", ctypes.c_int,
                               [_vp, _i32, _P, _i32, ctypes.POINTER(_vp), ctypes.POINTER(_i64),
@@ -453,6 +455,21 @@ def nmf_mlp_train_step(ctx, params, m, v, grad, step, lr, X, T, hidden, r, want_
                                          _ptr(_dev_f32(X, "X")), _ptr(_dev_f32(T, "T")),
                                          X.shape[0], ctypes.byref(loss) if want_loss else None))
     return loss.value if want_loss else None
+
+
+def nmf_warmstart_targets(ctx, Wb, Hb, hscale, Wstar, Hstar):
+    """Network targets (Tw m x r, Th n x r) that map (W_b, H_b) onto (W*, H*)."""
+    m, r = Wb.shape
+    n = Hb.shape[1]
+    for t, nm in ((Wb, "Wb"), (Hb, "Hb"), (hscale, "hscale"), (Wstar, "Wstar"), (Hstar, "Hstar")):
+        _dev_f32(t, nm)
+    if Wstar.shape != (m, r) or Hb.shape != (r, n) or Hstar.shape != (r, n) or hscale.numel() != r:
+        raise ValueError("shapes of W_b, H_b, hscale, W*, H* disagree")
+    Tw = _empty((m, r), Wb)
+    Th = _empty((n, r), Wb)
+    ctx._check(_c["nmf_warmstart_targets"](ctx.handle, m, n, r, _ptr(Wb), _ptr(Hb), _ptr(hscale),
+                                           _ptr(Wstar), _ptr(Hstar), _ptr(Tw), _ptr(Th)))
+    return Tw, Th
 
 
 def nmf_warmstart_apply(ctx, Wb, Dw, Hb, Dh, hscale, W=None, H=None):

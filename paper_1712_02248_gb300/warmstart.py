@@ -79,9 +79,7 @@ def _make_training_set(ctx, cfg, count, seed):
         W, H = Wb.clone(), Hb.clone()
         N.nmf_iterate(ctx, p, QL, QR, Xhat, Xchk, W, H, cfg.target_iters)
         N.nmf_sync(ctx)   # a latched device error surfaces with the matrix that raised it
-        Tw = (W - Wb) * (cfg.m ** 0.5)
-        hsafe = torch.where(hs > 0, hs, torch.ones_like(hs))
-        Th = ((H - Hb) * (cfg.n ** 0.5) / hsafe[:, None]).t().contiguous()
+        Tw, Th = N.nmf_warmstart_targets(ctx, Wb, Hb, hs, W, H)
         iw = torch.randint(0, cfg.m, (k,), device=dev, generator=gen)
         ih = torch.randint(0, cfg.n, (k,), device=dev, generator=gen)
         Fws.append(Fw[iw])

@@ -118,6 +118,26 @@ def test_apply_matches_oracle(lib, ctx):
     assert rel(host(W), Wo) <= 1e-6 and rel(host(H), Ho) <= 1e-6
 
 
+def test_targets_match_oracle_and_invert_apply(lib, ctx):
+    """nmf_warmstart_targets against the oracle's warmstart_targets (a zero scale included), and
+    apply(targets) returns the solution where it is positive (the targets invert the map)."""
+    rng = np.random.default_rng(9)
+    m, n, r = 900, 333, 7
+    Wb, Hb = rng.random((m, r)), rng.random((r, n))
+    hs = rng.random(r) + 0.5
+    hs[3] = 0.0
+    Ws, Hs = rng.random((m, r)) + 0.1, rng.random((r, n)) + 0.1
+    f = [a.astype(np.float32) for a in (Wb, Hb, hs, Ws, Hs)]
+    Tw, Th = lib.nmf_warmstart_targets(ctx, *[cu(a) for a in f])
+    Two, Tho = WS.warmstart_targets(*f)
+    assert rel(host(Tw), Two) <= 1e-6 and rel(host(Th), Tho) <= 1e-6
+    keep = np.ones(r, bool)
+    keep[3] = False                     # a zero scale maps the correction to nothing
+    W, H = lib.nmf_warmstart_apply(ctx, cu(f[0]), Tw, cu(f[1]), Th, cu(f[2]))
+    assert rel(host(W), f[3]) <= 1e-6
+    assert rel(host(H)[keep], f[4][keep]) <= 1e-6
+
+
 def test_untrained_network_solve_equals_nndsvd_solve(lib, ctx):
     """A zero output layer returns (W_b, H_b), which differ from NNDSVD's factors only by a
     scaling of each component; the FastHALS-RP sweep is equivariant to that scaling, so whole
@@ -149,8 +169,7 @@ def test_trained_warm_start_gain_over_nndsvd(lib, ctx):
     kernels; on 12 held-out matrices report iterations to 1.01 x the error of a 600-iteration
     NNDSVD-started solve for random, NNDSVD and learned starts. The training loss must fall
     below the targets' variance (the networks explain part of the correction), the learned start
-    must begin closer than NNDSVD, and it may not need clearly more iterations (10 %) than
-    NNDSVD on average."""
+    must begin closer than NNDSVD and need fewer iterations than NNDSVD on average."""
     from paper_1712_02248_gb300 import warmstart as WSM
     cfg = WSM.WarmStartConfig(m=1024, n=256, r=8, ell=16, noise=0.02, steps=800)
     pw, ph, info = WSM.train_warmstart(ctx, cfg, count=48, seed=5)
@@ -182,4 +201,4 @@ def test_trained_warm_start_gain_over_nndsvd(lib, ctx):
     summary = {k: (float(np.median(e0[k])), float(np.mean(v))) for k, v in its.items()}
     print("initial error (median), iterations to target (mean):", summary)
     assert summary["mlp"][0] < summary["nndsvd"][0]
-    assert summary["mlp"][1] <= summary["nndsvd"][1] * 1.10
+    assert summary["mlp"][1] < summary["nndsvd"][1]
