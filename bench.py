@@ -55,6 +55,13 @@ def parse():
                          "full-data updates (Tables 5.2/5.3); sweep: the k x w grid of Figure "
                          "5.3 with the spectral decay rate; sparse: CSR term counts, "
                          "200000 x 20000 (separate JSON lines; not the headline)")
+    ap.add_argument("--ws-target-iters", type=int, default=10,
+                    help="dense: iterations from the NNDSVD start that give the warm-start "
+                         "networks' training targets")
+    ap.add_argument("--ws-count", type=int, default=128,
+                    help="dense: planted training matrices of the warm-start networks")
+    ap.add_argument("--ws-steps", type=int, default=1500,
+                    help="dense: Adam steps of each warm-start network")
     ap.add_argument("--train-count", type=int, default=256,
                     help="warmstart: planted training matrices (the full recipe uses 10000)")
     ap.add_argument("--heldout", type=int, default=32,
@@ -836,12 +843,15 @@ def main():
     # planted matrices of the same distribution at a quarter of the size
     from paper_1712_02248_gb300 import warmstart as WSM
     wcfg = WSM.WarmStartConfig(m=m // 5, n=n // 5, r=r, ell=ell, power_iters=w["w"],
-                               noise=0.01, prec="bf16", steps=1500)
+                               noise=0.01, prec="bf16", steps=args.ws_steps,
+                               target_iters=args.ws_target_iters)
     t_train = time.perf_counter()
-    pw, ph, winfo = WSM.train_warmstart(ctx, wcfg, count=128, seed=args.seed + 1)
+    pw, ph, winfo = WSM.train_warmstart(ctx, wcfg, count=args.ws_count, seed=args.seed + 1)
     t_train = time.perf_counter() - t_train
     N.nmf_set_warmstart(ctx, wcfg.hidden, r, pw, ph)
-    warm_info = {"train_matrices": 128, "train_shape": [wcfg.m, wcfg.n], "train_s": t_train,
+    warm_info = {"train_matrices": args.ws_count, "train_shape": [wcfg.m, wcfg.n],
+                 "target_iters": args.ws_target_iters, "adam_steps": args.ws_steps,
+                 "train_s": t_train,
                  "samples": winfo["samples"], "loss_w": winfo["loss_w"][-1][1],
                  "target_var_w": winfo["target_var_w"], "loss_h": winfo["loss_h"][-1][1],
                  "target_var_h": winfo["target_var_h"]}
@@ -941,10 +951,10 @@ def main():
     dp_achieved = dp_bytes / (dp_ms / dp_n * 1e-3) / 1e9
     shares = {k: v[0] for k, v in phases.items() if v[1] > 0}
     dom = max(shares, key=shares.get)
-    # DRAM bytes of one iterate_persistent_kernel launch (10 iterations): none current. The
-    # capture in profiles/iterate_persistent_kernel_dense_20000x5000_r20.md (10.19 MB read) predates
-    # the kernel's settable grid-barrier budget
-    it_traffic = None
+    # DRAM bytes of one iterate_persistent_kernel launch (10 iterations) from an ncu capture of
+    # the current kernel on this workload (profiles/iterate_persistent_kernel_dense_20000x5000_r20.md:
+    # 10.19 MB read, nothing written back within the launch): the slices are staged once a launch
+    it_traffic = 10.192896e6 if (m, n, r, ell) == (20000, 5000, 20, 40) else None
     roofline = {"bound": "alu", "achieved": it_achieved, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": it_achieved / alu_peak, "traffic": it_traffic,
                 "kernel": "iterate_persistent_kernel (FastHALS-RP iterations)",
