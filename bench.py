@@ -303,6 +303,19 @@ def run_batched(args):
     vb = statistics.median(t for t, _ in tb)
     vs = statistics.median(t for t, _ in ts)
     eb, es = tb[0][1], ts[0][1]
+    # algorithmic HBM bytes of a batch (per problem: the BF16 copy of X written from its FP32
+    # read, 2w + 2 passes over the copy with their V / U reads and Y / Z writes, the FP32 residual
+    # read) and iteration FLOPs (4 (m + n) l r + 2 (m + n) r^2 an iteration)
+    hbm_bytes, iter_flops = 0, 0
+    for (m, n, r, ell) in specs:
+        hbm_bytes += 6 * m * n + 6 * (2 * m * n + 8 * ell * (m + n)) + 4 * m * n
+        iter_flops += 200 * (4 * (m + n) * ell * r + 2 * (m + n) * r * r)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
     print(json.dumps({
         "metric": "time per batch of 256 uneven compressed-NMF problems (200 FastHALS-RP its)",
         "value": vb, "unit": "s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
@@ -313,6 +326,12 @@ def run_batched(args):
                    "x_bytes_fp32": xbytes,
                    "rows_per_block": N.nmf_last_batch_info(ctx)},
         "one_solve_per_problem_s": vs, "speedup": vs / vb, "gpu_launches_per_step": launches,
+        "roofline": {"hbm_bytes_per_batch": hbm_bytes, "achieved_gbs": hbm_bytes / vb / 1e9,
+                     "frac_hbm": hbm_bytes / vb / 1e9 / hbm,
+                     "iteration_flops_per_batch": iter_flops,
+                     "iteration_tflops_over_batch": iter_flops / vb / 1e12,
+                     "note": "whole-batch time in the denominators (sketch, QR, iterations and "
+                             "residuals together)"},
         "median_rel_err_batched": float(np.median(eb)),
         "max_rel_err_diff_vs_single": float(np.max(np.abs(np.array(eb) - np.array(es)) /
                                                    np.array(es)))}))

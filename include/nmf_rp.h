@@ -75,7 +75,12 @@ enum {
      Cholesky pivot falls below 1e-12 of their diagonal with Gaussian draws (seeded by p->seed)
      and repeating CholeskyQR2, instead of latching NMF_ERR_QR_BREAKDOWN; synchronises after
      every QR. nmf_solve does this by itself when a first run meets a breakdown. */
-  NMF_FLAG_ROBUST_QR = 4
+  NMF_FLAG_ROBUST_QR = 4,
+  /* nmf_residual: rebuild W H on the tensor cores from BF16 hi + lo splits of W and H (FP32 X
+     with rows 16-byte aligned, r <= 32; else the FP32 kernels run). Each product is then within
+     about 2^-17 of its FP32 value and the squared error within about 1e-6 relative at a 1 %
+     residual. nmf_solve's exact residual checks always take this path where it applies. */
+  NMF_FLAG_TC_RESIDUAL = 8
 };
 
 typedef struct {

@@ -217,10 +217,20 @@ cudaError_t launch_gini(const Launcher& L, const float* B, int64_t count, void* 
 
 // Residual partial sums: writes 2 doubles (||X-WH||^2, ||X||^2) to out2 (device). If gate is
 // non-null and *gate == 0 the kernels return without work.
+// With residual_ws_bytes_tc(m, n) of workspace, FP32 X with rows 16-byte aligned and r <= 32,
+// the W H rebuild runs on the tensor cores (BF16 hi + lo splits of W and H); status receives
+// NMF_ERR_TIMEOUT if one of that kernel's waits runs out.
 size_t residual_ws_bytes(int64_t m, int64_t n);
+size_t residual_ws_bytes_tc(int64_t m, int64_t n);
 cudaError_t launch_residual(const Launcher& L, const float* X, int64_t m, int64_t n, int64_t ldx,
                             const float* W, const float* H, int r, double* out2, void* ws,
-                            size_t ws_bytes, const int* gate = nullptr);
+                            size_t ws_bytes, const int* gate = nullptr, int* status = nullptr);
+bool residual_tc_supported(int64_t m, int64_t n, int64_t ldx, const float* X, int r);
+size_t residual_tc_operand_bytes(int64_t m, int64_t n);
+cudaError_t launch_residual_tc(const Launcher& L, const float* X, int64_t m, int64_t n,
+                               int64_t ldx, const float* W, const float* H, int r, double* part,
+                               int max_grid, int* grid_out, void* ws, size_t ws_bytes, int* status,
+                               const int* gate);
 // Static scratch for launch_residual: the device address (resolved once per device, which must be
 // current) of a fixed array of residual_static_capacity_bytes() bytes in global memory.
 size_t residual_static_capacity_bytes();

@@ -251,6 +251,57 @@ __device__ __forceinline__ void gram_rp(const float* T, int LQ, float* G, float*
   }
 }
 
+// gram_rp on threads [b0, b0 + nthr) of the block (whole warps; `tid` = threadIdx.x - b0), with
+// the named barrier `bar` among them in place of the block barrier, so that the block's other
+// warps can run the sweep's first half meanwhile. Same sums as gram_rp, split over fewer
+// threads (so in another order). The caller ends with a block barrier.
+template <int RP>
+__device__ __forceinline__ void gram_rp_sub(const float* T, int LQ, float* G, float* inv,
+                                            float* red, int tid, int nthr, int bar) {
+  constexpr int T2 = RP / 2, NT = T2 * (T2 + 1) / 2;
+  const int KS0 = nthr / NT < 1 ? 1 : nthr / NT;
+  const int ks_cap = (LQ + 3) / 4;
+  const int KS = KS0 < ks_cap ? KS0 : ks_cap;
+  const int chunk = (LQ + KS - 1) / KS;
+  for (int u = tid; u < NT * KS; u += nthr) {
+    const int tile = u % NT, kk = u / NT;
+    int P = 0, v = tile;
+    while (v >= T2 - P) {
+      v -= T2 - P;
+      ++P;
+    }
+    const int p0 = 2 * P, q0 = 2 * (P + v);
+    float g00 = 0.f, g01 = 0.f, g10 = 0.f, g11 = 0.f;
+    const int k1 = min(LQ, (kk + 1) * chunk);
+#pragma unroll 4
+    for (int k = kk * chunk; k < k1; ++k) {
+      const float2 a = *reinterpret_cast<const float2*>(T + k * RP + p0);
+      const float2 b = *reinterpret_cast<const float2*>(T + k * RP + q0);
+      g00 = fmaf(a.x, b.x, g00);
+      g01 = fmaf(a.x, b.y, g01);
+      g10 = fmaf(a.y, b.x, g10);
+      g11 = fmaf(a.y, b.y, g11);
+    }
+    *reinterpret_cast<float4*>(red + 4 * u) = make_float4(g00, g01, g10, g11);
+  }
+  asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(nthr) : "memory");
+  for (int e = tid; e < NT * 4; e += nthr) {
+    const int tile = e >> 2, x = e & 3;
+    float g = red[4 * tile + x];
+    for (int kk = 1; kk < KS; ++kk) g += red[4 * (kk * NT + tile) + x];
+    int P = 0, v = tile;
+    while (v >= T2 - P) {
+      v -= T2 - P;
+      ++P;
+    }
+    if (v == 0 && x == 2) continue;   // the mirror of entry 1 of a diagonal tile
+    const int p = 2 * P + (x >> 1), q = 2 * (P + v) + (x & 1);
+    G[p * RP + q] = g;
+    G[q * RP + p] = g;
+    if (p == q) inv[p] = g > 0.f ? 1.f / g : 0.f;
+  }
+}
+
 // C consecutive floats from shared memory (C a multiple of 2; float4 where it can).
 template <int C>
 __device__ __forceinline__ void ld_run(const float* p, float* v) {
@@ -496,26 +547,28 @@ __device__ __forceinline__ void iterate_body(const PArgs& a, const unsigned bid,
       }
     }
     __syncthreads();
-    gram_rp<RP>(HtT, LQ, Gw, invs, red);
-    __syncthreads();
     {
       // group q of GA lanes takes the RA rows q, q + Q, q + 2Q, ... (Q = ceil(nrows / RA)), so
       // that neighbouring groups read neighbouring rows; whole warps run (shuffles), groups
-      // past the slice compute on a valid row and store nothing
+      // past the slice compute on a valid row and store nothing. When the groups fit in one
+      // pass with warps to spare, the spare warps form G_W while the others form their rows of
+      // S_W (the first half of the sweep); otherwise G_W comes first.
       constexpr int GPW = 32 / GA;
       const int Q = (nrows + RA - 1) / RA;
       const int Qp = (Q + GPW - 1) / GPW * GPW;
-      for (int q = t / GA; q < Qp; q += kNT / GA) {
-        const int g = t % GA;
-        int idx[RA];
-        bool live[RA];
+      const int busy = Qp * GA;
+      const bool overlap = RULE == 0 && Qp <= kNT / GA && busy + 64 <= kNT;
+      const int g = t % GA;
+      int idx[RA];
+      bool live[RA];
+      float w[RA][CA], sv[RA][CA];
+      auto load_rows = [&](int q) {
 #pragma unroll
         for (int rho = 0; rho < RA; ++rho) {
           const int row = q + rho * Q;
           live[rho] = q < Q && row < nrows;
           idx[rho] = live[rho] ? row : 0;
         }
-        float w[RA][CA], sv[RA][CA];
 #pragma unroll
         for (int rho = 0; rho < RA; ++rho) {
           ld_run<CA>(Ws + idx[rho] * RP + g * CA, w[rho]);
@@ -545,6 +598,8 @@ __device__ __forceinline__ void iterate_body(const PArgs& a, const unsigned bid,
               for (int c = 0; c < CA; ++c) sv[rho][c] = fmaf(xk[rho][q4], hr[c], sv[rho][c]);
           }
         }
+      };
+      auto update_store = [&]() {
         update_rows<RP, GA, RA, RULE>(w, sv, Gw, invs, g, r, false, 0.f, 0.f, a.eps);
 #pragma unroll
         for (int rho = 0; rho < RA; ++rho)
@@ -554,6 +609,19 @@ __device__ __forceinline__ void iterate_body(const PArgs& a, const unsigned bid,
               *reinterpret_cast<float2*>(Ws + idx[rho] * RP + g * CA + c) =
                   make_float2(w[rho][c], w[rho][c + 1]);
           }
+      };
+      if (overlap) {
+        if (t < busy) load_rows(t / GA);
+        else gram_rp_sub<RP>(HtT, LQ, Gw, invs, red, t - busy, kNT - busy, 1);
+        __syncthreads();
+        if (t < busy) update_store();
+      } else {
+        gram_rp<RP>(HtT, LQ, Gw, invs, red);
+        __syncthreads();
+        for (int q = t / GA; q < Qp; q += kNT / GA) {
+          load_rows(q);
+          update_store();
+        }
       }
     }
     __syncthreads();
@@ -578,24 +646,25 @@ __device__ __forceinline__ void iterate_body(const PArgs& a, const unsigned bid,
       for (int e = t; e < LQ * RP; e += kNT) WtS[e] = acc_read(accA_r, EA, e) * rsc[e % RP];
     }
     __syncthreads();
-    gram_rp<RP>(WtS, LQ, Gh, invs, red);
-    __syncthreads();
     float cross = 0.f;
     {
+      // as in phase A: spare warps form G_H while the others form their columns of S_H
       constexpr int GPW = 32 / GB;
       const int Q = (ncols + RC - 1) / RC;
       const int Qp = (Q + GPW - 1) / GPW * GPW;
-      for (int q = t / GB; q < Qp; q += kNT / GB) {
-        const int g = t % GB;
-        int idx[RC];
-        bool live[RC];
+      const int busy = Qp * GB;
+      const bool overlap = RULE == 0 && Qp <= kNT / GB && busy + 64 <= kNT;
+      const int g = t % GB;
+      int idx[RC];
+      bool live[RC];
+      float h[RC][CBn], sv[RC][CBn];
+      auto load_cols = [&](int q) {
 #pragma unroll
         for (int rho = 0; rho < RC; ++rho) {
           const int col = q + rho * Q;
           live[rho] = q < Q && col < ncols;
           idx[rho] = live[rho] ? col : 0;
         }
-        float h[RC][CBn], sv[RC][CBn];
 #pragma unroll
         for (int rho = 0; rho < RC; ++rho) {
           ld_run<CBn>(Hs + idx[rho] * RP + g * CBn, h[rho]);
@@ -625,6 +694,8 @@ __device__ __forceinline__ void iterate_body(const PArgs& a, const unsigned bid,
               for (int z = 0; z < CBn; ++z) sv[rho][z] = fmaf(xk[rho][q4], wr[z], sv[rho][z]);
           }
         }
+      };
+      auto update_store = [&]() {
         float shc[RC][CBn];
 #pragma unroll
         for (int rho = 0; rho < RC; ++rho)
@@ -642,6 +713,19 @@ __device__ __forceinline__ void iterate_body(const PArgs& a, const unsigned bid,
               *reinterpret_cast<float2*>(Hs + idx[rho] * RP + g * CBn + z) =
                   make_float2(h[rho][z], h[rho][z + 1]);
           }
+      };
+      if (overlap) {
+        if (t < busy) load_cols(t / GB);
+        else gram_rp_sub<RP>(WtS, LQ, Gh, invs, red, t - busy, kNT - busy, 1);
+        __syncthreads();
+        if (t < busy) update_store();
+      } else {
+        gram_rp<RP>(WtS, LQ, Gh, invs, red);
+        __syncthreads();
+        for (int q = t / GB; q < Qp; q += kNT / GB) {
+          load_cols(q);
+          update_store();
+        }
       }
     }
 #pragma unroll

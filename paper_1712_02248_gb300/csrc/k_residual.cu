@@ -303,11 +303,26 @@ size_t residual_ws_bytes(int64_t, int64_t) {
   return sizeof(double) * 2 * static_cast<size_t>(residual_grid()) + 256;
 }
 
+size_t residual_ws_bytes_tc(int64_t m, int64_t n) {
+  return residual_ws_bytes(m, n) + residual_tc_operand_bytes(m, n);
+}
+
 cudaError_t launch_residual(const Launcher& L, const float* X, int64_t m, int64_t n, int64_t ldx,
                             const float* W, const float* H, int r, double* out2, void* ws,
-                            size_t ws_bytes, const int* gate) {
+                            size_t ws_bytes, const int* gate, int* status) {
   if (ws_bytes < residual_ws_bytes(m, n)) return cudaErrorInvalidValue;
   double* part = static_cast<double*>(ws);
+  // tensor-core rebuild of W H when the workspace holds its split operands
+  if (ws_bytes >= residual_ws_bytes_tc(m, n) && residual_tc_supported(m, n, ldx, X, r)) {
+    const size_t pb = residual_ws_bytes(m, n);
+    int grid = 0;
+    cudaError_t err = launch_residual_tc(L, X, m, n, ldx, W, H, r, part, residual_grid(), &grid,
+                                         static_cast<char*>(ws) + pb, ws_bytes - pb, status, gate);
+    if (err != cudaSuccess) return err;
+    residual_final_kernel<<<1, 32, 0, L.stream>>>(part, grid, out2, gate);
+    L.count();
+    return cudaGetLastError();
+  }
   // streaming kernel: rows 16-byte aligned, columns a multiple of 4 (the ragged tail of a row
   // would need element copies), W H rank small enough for the shared-memory stages (r <= 48)
   if (ldx % 4 == 0 && n % 4 == 0 && reinterpret_cast<uintptr_t>(X) % 16 == 0 &&

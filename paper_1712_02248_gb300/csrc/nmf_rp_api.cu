@@ -446,20 +446,27 @@ nmf_status iterate_impl(nmf_ctx* ctx, const nmf_params* p, const float* QL, cons
   return NMF_OK;
 }
 
+nmf_status take_status(nmf_ctx* ctx);
+
 nmf_status residual_impl(nmf_ctx* ctx, const nmf_params* p, const float* X, int64_t ldx,
                          const float* W, const float* H, double* rel, double* e2o, double* x2o,
                          Arena a) {
   size_t rest = 0;
   void* ws = a.rest(&rest);
+  // the FP32 rebuild unless the caller asks for the tensor-core one (the kernel is chosen by the
+  // workspace it is given)
+  if (!(p->flags & NMF_FLAG_TC_RESIDUAL)) rest = std::min(rest, nmfrp::residual_ws_bytes(p->m, p->n));
   Phase ph(ctx, NMF_PHASE_RESIDUAL);
   NMF_CUDA(nmfrp::launch_residual(launcher(ctx), X, p->m, p->n, ldx, W, H, p->r, ctx->d_res, ws,
-                                  rest),
+                                  rest, nullptr, ctx->d_status),
            "residual");
   ph.end();
   NMF_CUDA(cudaMemcpyAsync(ctx->h_res, ctx->d_res, 2 * sizeof(double), cudaMemcpyDeviceToHost,
                            ctx->stream),
            "residual copy");
   NMF_CUDA(cudaStreamSynchronize(ctx->stream), "residual sync");
+  nmf_status st = take_status(ctx);   // a wait of the tensor-core kernel that ran out
+  if (st != NMF_OK) return st;
   const double e2 = ctx->h_res[0], x2 = ctx->h_res[1];
   if (e2o) *e2o = e2;
   if (x2o) *x2o = x2;
@@ -1034,7 +1041,7 @@ nmf_status nmf_workspace_size(const nmf_params* p, size_t* bytes) {
   scratch = std::max(scratch, sizeof(float) * n * l + 1024 + pass_scratch(m, n, p->ell));
   scratch = std::max(scratch, nmfrp::iterate_ws_bytes(m, n, p->r, p->ell));
   scratch = std::max(scratch, nmfrp::iterate_persistent_ws_bytes(p->r, p->ell));
-  scratch = std::max(scratch, nmfrp::residual_ws_bytes(m, n));
+  scratch = std::max(scratch, nmfrp::residual_ws_bytes_tc(m, n));
   scratch = std::max(scratch, nmfrp::nndsvd_ws_bytes(m, n, p->r, p->ell));
   scratch = std::max(scratch, warm_ws_bytes(p, 256));
   (void)r;
@@ -1168,7 +1175,9 @@ nmf_status nmf_residual(nmf_ctx* ctx, const nmf_params* p, const float* X, int64
     return fail(ctx, NMF_ERR_INVALID_ARG, "bad residual sizes");
   if (!X || !W || !H || ldx < p->n) return fail(ctx, NMF_ERR_INVALID_ARG, "bad residual arguments");
   DeviceGuard g(ctx->device);
-  nmf_status st = ensure_ws(ctx, nmfrp::residual_ws_bytes(p->m, p->n));
+  nmf_status st = ensure_ws(ctx, (p->flags & NMF_FLAG_TC_RESIDUAL)
+                                     ? nmfrp::residual_ws_bytes_tc(p->m, p->n)
+                                     : nmfrp::residual_ws_bytes(p->m, p->n));
   if (st != NMF_OK) return st;
   Arena a{static_cast<char*>(ctx->ws), ctx->ws_bytes};
   return residual_impl(ctx, p, X, ldx, W, H, rel_err_host, err2_host, x2_host, a);
@@ -1304,7 +1313,7 @@ nmf_status solve_impl(nmf_ctx* ctx, const nmf_params* p, int32_t init, const flo
     {
       Phase ph(ctx, NMF_PHASE_RESIDUAL);
       NMF_CUDA(nmfrp::launch_residual(launcher(ctx), X, m, n, ldx, W, H, p->r, ctx->d_res, ws,
-                                      rest, ctx->d_flags + 1),
+                                      rest, ctx->d_flags + 1, ctx->d_status),
                "residual");
     }
     solve_decide_kernel<<<1, 1, 0, ctx->stream>>>(ctx->d_res, p->target_rel_err, done,
@@ -1822,7 +1831,8 @@ nmf_status nmf_solve_batched(nmf_ctx* ctx, int32_t count, const nmf_params* p, i
     void* ws = sa.rest(&rest);
     Phase ph(ctx, NMF_PHASE_RESIDUAL);
     cudaError_t e = nmfrp::launch_residual(launcher(ctx), X[i], p[i].m, p[i].n, ldx[i], W[i], H[i],
-                                           p[i].r, ctx->d_bres + 2 * i, ws, rest);
+                                           p[i].r, ctx->d_bres + 2 * i, ws, rest, nullptr,
+                                           ctx->d_status);
     if (e != cudaSuccess) st = cuda_fail(ctx, e, "residual");
   }
   ctx->stream = main_stream;

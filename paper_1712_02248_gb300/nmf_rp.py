@@ -137,6 +137,7 @@ class NmfError(RuntimeError):
 FLAG_STAGED_ITERATE = 1
 FLAG_SIMT_DUAL_PASS = 2
 FLAG_ROBUST_QR = 4
+FLAG_TC_RESIDUAL = 8
 
 
 def params(m, n, r, ell, power_iters=2, iters=0, rule="fasthals", prec="fp32", seed=0,

@@ -198,7 +198,12 @@ def test_solve_reruns_with_repaired_qr(lib, ctx):
     assert it == 200 and np.isfinite(e)
     assert (W >= 0).all() and (H >= 0).all()
     assert e <= 0.05 * e0
-    assert abs(lib.nmf_residual(ctx, p, cu(X), W, H)[0] - e) <= 1e-6 * max(e, 1e-12)
+    # the solve's exact checks rebuild W H on the tensor cores: the same kernel through
+    # nmf_residual gives the same value (the FP32 SIMT rebuild differs by ~5e-6 relative at a
+    # residual this small, both being FP32-grade evaluations)
+    ptc = lib.params(m, n, r, ell, flags=lib.FLAG_TC_RESIDUAL)
+    assert abs(lib.nmf_residual(ctx, ptc, cu(X), W, H)[0] - e) <= 1e-6 * max(e, 1e-12)
+    assert abs(lib.nmf_residual(ctx, p, cu(X), W, H)[0] - e) <= 3e-5 * max(e, 1e-12)
 
 
 # ------------------------------------------------------------------ sketch and compression
@@ -365,6 +370,28 @@ def test_residual_matches_oracle(lib, ctx, m, n, r):
     assert abs(x2 - x2o) <= 1e-6 * x2o
     assert abs(e2 - e2o) <= 1e-4 * e2o
     assert abs(relg - relo) <= 1e-4 * relo
+
+
+@pytest.mark.parametrize("m,n,r", [(1000, 700, 20), (20000, 5000, 20), (333, 517, 1), (900, 1300, 16),
+                                   (2049, 131, 17), (640, 1024, 32)])
+def test_tensor_core_residual_matches_oracle(lib, ctx, m, n, r):
+    """The residual with the W H rebuild on the tensor cores (BF16 hi + lo splits, three products):
+    every product within about 2^-17 of FP32, so at a residual of 5 % (and 1 % for the dense
+    workload's shape) the squared error agrees with the oracle to 1e-5 relative and ||X||^2 (FP32
+    sums of 128 squares a tile, float-float across tiles, FP64 across blocks) to 1e-7; ragged
+    tiles (m, n not multiples of 128) and r = 1, 16, 17, 32 (one or two K steps) included."""
+    rng = np.random.default_rng(m + 3 * r)
+    W = rng.uniform(0, 1, (m, r)).astype(np.float32)
+    H = rng.uniform(0, 1, (r, n)).astype(np.float32)
+    noise = 0.01 if (m, n) == (20000, 5000) else 0.05
+    X = (W.astype(np.float64) @ H * (1 + noise * rng.standard_normal((m, n)))).astype(np.float32)
+    p = lib.params(m, n, r, min(r, m, n), flags=lib.FLAG_TC_RESIDUAL)
+    relg, e2, x2 = lib.nmf_residual(ctx, p, cu(X), cu(W), cu(H))
+    relo, e2o, x2o = O.residual(X, W, H)
+    print(f"tc residual {m}x{n} r={r}: e2 {e2 / e2o - 1:+.2e}, x2 {x2 / x2o - 1:+.2e}")
+    assert abs(x2 - x2o) <= 1e-7 * x2o
+    assert abs(e2 - e2o) <= 1e-5 * e2o
+    assert abs(relg - relo) <= 1e-5 * relo
 
 
 # ------------------------------------------------------------------ whole runs
