@@ -92,7 +92,8 @@ cudaError_t launch_quantize_fp8_stats(const Launcher& L, const float* X, int64_t
 // Dual pass Y = X V (m x ell), Z = X^T U (n x ell). x_type selects the element type of X.
 // ws: workspace for partial sums (size from dual_pass_ws_bytes).
 // BF16 X with both products goes to the tensor-core kernel when TMA can address X (ldx a
-// multiple of 8, X 16-byte aligned) unless force_simt is set.
+// multiple of 8, X 16-byte aligned) unless force_simt is set; FP32 X likewise (ldx a multiple
+// of 4, ell <= 80), FP8 X always when its copy is at least one 128 x 128 tile.
 size_t dual_pass_ws_bytes(int64_t m, int64_t n, int ell);
 // split: on the tensor-core path, V and U enter as hi + lo BF16 pairs (only X is rounded to
 // BF16), which the compression uses; ignored elsewhere.
@@ -109,6 +110,13 @@ bool dual_pass_tc_fp8_supported(int64_t m, int64_t n, int ell, const void* Xq);
 cudaError_t launch_dual_pass_tc_fp8(const Launcher& L, const uint8_t* Xq, int64_t m, int64_t n,
                                     int ell, const float* V, const float* U, float* Y, float* Z,
                                     void* ws, size_t ws_bytes, int* status, bool z_kmajor = false);
+// tcgen05 + TMA dual pass on FP32 X (hi + lo BF16 split in shared memory, split V and U), for
+// ell <= 80, ldx a multiple of 4 and X 16-byte aligned.
+bool dual_pass_tc_f32_supported(int64_t m, int64_t n, int64_t ldx, int ell, const void* X);
+cudaError_t launch_dual_pass_tc_f32(const Launcher& L, const float* X, int64_t m, int64_t n,
+                                    int64_t ldx, int ell, const float* V, const float* U, float* Y,
+                                    float* Z, void* ws, size_t ws_bytes, int* status,
+                                    bool z_kmajor = false);
 // tcgen05 + TMA dual pass (BF16 X).
 bool dual_pass_tc_supported(int64_t m, int64_t n, int64_t ldx, int ell, const void* X);
 size_t dual_pass_tc_ws_bytes(int64_t m, int64_t n, int ell);

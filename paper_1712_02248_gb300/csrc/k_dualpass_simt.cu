@@ -242,6 +242,7 @@ bool dual_pass_uses_tc(const void* X, int x_type, int64_t m, int64_t n, int64_t 
                        bool both, bool force_simt) {
   if (!both || force_simt) return false;
   if (x_type == kXFp8) return dual_pass_tc_fp8_supported(m, n, ell, X);
+  if (x_type == kXFp32) return dual_pass_tc_f32_supported(m, n, ldx, ell, X);
   return x_type == kXBf16 && dual_pass_tc_supported(m, n, ldx, ell, X);
 }
 
@@ -264,6 +265,9 @@ cudaError_t launch_dual_pass(const Launcher& L, const void* X, int x_type, int64
                     (n + 31) / 32);
   }
   const bool x_bf16 = x_type == kXBf16;
+  if (tc && x_type == kXFp32)
+    return launch_dual_pass_tc_f32(L, static_cast<const float*>(X), m, n, ldx, ell, V, U, Y, Z,
+                                   ws, ws_bytes, status, z_kmajor);
   if (tc)
     return launch_dual_pass_tc(L, static_cast<const __nv_bfloat16*>(X), m, n, ldx, ell, V, U, Y,
                                Z, ws, ws_bytes, status, split, z_kmajor);

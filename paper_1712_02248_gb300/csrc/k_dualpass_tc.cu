@@ -17,7 +17,12 @@
 // FP8 X (E4M3 codes, one E8M0 scale a 32 x 32 tile): TMA brings each 128 x 128 tile of codes
 // (16 KB, 128B-swizzled) into its own ring, and warps 6-13 rewrite it as the BF16 tile the MMAs
 // read, code times 2^k (exact in BF16), in the same swizzled layout, before signalling the MMA
-// issuer; the HBM stream is half that of BF16 X. Partial
+// issuer; the HBM stream is half that of BF16 X.
+// FP32 X: TMA brings each tile as four 128-row x 32-column boxes (16 KB, 128B-swizzled) into a
+// ring of boxes; warps 6-13 split every element into hi = bf16(x) and lo = bf16(x - hi) (x to
+// about 2^-18 relative) and write a BF16 hi tile and a BF16 lo tile. With V and U also entering
+// as hi + lo pairs, each product accumulates x_hi v_hi + x_hi v_lo + x_lo v_hi: FP32-grade sums
+// on the BF16 tensor cores from one FP32 stream of X. Partial
 // sums of Y (one per column group) and Z (one per row group) are summed in a fixed slot order
 // by one slot-sum launch for both. Every mbarrier wait is bounded; on time-out the kernel
 // latches NMF_ERR_TIMEOUT, drains what it issued and frees its tensor memory.
@@ -43,6 +48,12 @@ constexpr int kThreadsF8 = 448;     // + warps 6-13: FP8 -> BF16 converters (two
 constexpr int kConv = kThreadsF8 - kThreads;
 constexpr int kF8Stages = 4;        // ring of FP8 tiles
 constexpr uint32_t kX8Stage = 128 * 128;   // one 128 x 128 E4M3 tile (16 KB)
+constexpr int kRingMax = 4;         // ring slots of the converted element types (FP8 tiles, FP32 boxes)
+constexpr uint32_t kF32Box = 128 * 128;    // one 128-row x 32-column FP32 box (16 KB)
+
+// Element type of X inside the kernel: BF16 read by the MMAs directly, or FP8 / FP32 converted
+// to BF16 in shared memory first.
+enum : int { kXkBf16 = 0, kXkF8 = 1, kXkF32 = 2 };
 
 // Instruction descriptor, kind::f16: D = F32, A = B = BF16, M = 128, N = LP.
 __host__ __device__ constexpr uint32_t idesc_bf16(int N, int a_mn_major) {
@@ -77,6 +88,7 @@ struct TcArgs {
   int* status;
   const uint8_t* S;               // FP8 X: E8M0 tile scales (row-major, tn a row)
   int64_t tn;
+  int ring;                       // FP32 X: boxes in the ring (<= kRingMax)
 };
 
 // Two E4M3 codes (low byte = first element) times 2^k (exact) as a BF16 pair (low half first).
@@ -97,19 +109,29 @@ __host__ __device__ constexpr int acc_stride(int LP) { return (LP + 31) / 32 * 3
 __host__ __device__ constexpr int nct_max(int LP) {
   return (512 / acc_stride(LP) - 2) > 14 ? 14 : (512 / acc_stride(LP) - 2);
 }
+// FP32 X: each row block's Z contribution is drained from tensor memory into FP32 registers of
+// the epilogue (double-buffered with Y), so the resident column tiles are bounded by the
+// registers (96 sums a thread) and by two Z buffers in tensor memory.
+constexpr int kZRegs = 96;
+__host__ __device__ constexpr int nct_f32_max(int LP) {
+  return kZRegs / LP < 1 ? 1 : kZRegs / LP;
+}
 
 // SPLIT = 2: V and U enter as hi + lo BF16 pairs (v = hi + lo to about 2^-16 relative), each
-// product is accumulated from both, so only X is rounded to BF16.
-template <int LP, int SPLIT, bool F8>
-__global__ void __launch_bounds__(F8 ? kThreadsF8 : kThreads, 1) dual_pass_tc_kernel(
+// product is accumulated from both, so only X is rounded to BF16 (FP32 X: split too).
+template <int LP, int SPLIT, int XK>
+__global__ void __launch_bounds__(XK != kXkBf16 ? kThreadsF8 : kThreads, 1) dual_pass_tc_kernel(
     const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapV,
     const __grid_constant__ CUtensorMap mapU, TcArgs a) {
-  constexpr int NCT = nct_max(LP);
+  constexpr bool F8 = XK == kXkF8, F32 = XK == kXkF32, CONV = F8 || F32;
+  static_assert(!F32 || SPLIT == 2, "FP32 X takes split bases");
+  constexpr int NCT = F32 ? nct_f32_max(LP) : nct_max(LP);
   constexpr uint32_t kXHalf = kRows * kHalfCols * 2;   // 16 KB
+  constexpr uint32_t kXStg = F32 ? 2 * kXStage : kXStage;   // FP32: hi tile, then lo tile
   constexpr uint32_t kBBox = LP * kHalfCols * 2;        // LP rows x 128 B
   constexpr uint32_t kBTile = SPLIT * 2 * kBBox;        // one column tile (or row block) of V (U)
   constexpr int AS = acc_stride(LP);
-  constexpr int kTmemNeed = (2 + NCT) * AS;
+  constexpr int kTmemNeed = (2 + (F32 ? 2 : 1) * NCT) * AS;
   constexpr uint32_t kTmemCols = kTmemNeed <= 32 ? 32 : kTmemNeed <= 64 ? 64 : kTmemNeed <= 128
                                                                                 ? 128
                                                                                 : kTmemNeed <= 256
@@ -120,14 +142,15 @@ __global__ void __launch_bounds__(F8 ? kThreadsF8 : kThreads, 1) dual_pass_tc_ke
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   const int stages = a.stages;
-  unsigned char* Xs = smem;                              // [stages][32 KB]
-  unsigned char* X8 = Xs + stages * kXStage;             // [kF8Stages][16 KB] (F8 only)
-  unsigned char* Us = X8 + (F8 ? kF8Stages * kX8Stage : 0u);   // [2][SPLIT][2 halves][kBBox]
+  const int ring = F8 ? kF8Stages : a.ring;               // converted ring: FP8 tiles or FP32 boxes
+  unsigned char* Xs = smem;                              // [stages][kXStg]
+  unsigned char* X8 = Xs + stages * kXStg;               // FP8: [kF8Stages][16 KB]; FP32: [ring][16 KB]
+  unsigned char* Us = X8 + (F8 ? kF8Stages * kX8Stage : F32 ? ring * kF32Box : 0u);   // [2][SPLIT][2 halves][kBBox]
   unsigned char* Vs = Us + 2 * kBTile;                   // [nct][SPLIT][2 halves][kBBox]
   __shared__ __align__(8) uint64_t full_bar[kMaxStages], empty_bar[kMaxStages];
   __shared__ __align__(8) uint64_t u_full[2], u_empty[2], v_full;
   __shared__ __align__(8) uint64_t ydone_bar[2], yfree_bar[2], zdone_bar, drain_bar;
-  __shared__ __align__(8) uint64_t f8_full[kF8Stages], f8_empty[kF8Stages];
+  __shared__ __align__(8) uint64_t f8_full[kRingMax], f8_empty[kRingMax];
   __shared__ uint32_t tmem_base;
   __shared__ volatile int abort_f;
 
@@ -154,10 +177,10 @@ __global__ void __launch_bounds__(F8 ? kThreadsF8 : kThreads, 1) dual_pass_tc_ke
   if (threadIdx.x == 0) {
     abort_f = 0;
     for (int s = 0; s < kMaxStages; ++s) {
-      mbar_init(smem_u32(&full_bar[s]), F8 ? kConv : 1);   // FP8: the converter threads
+      mbar_init(smem_u32(&full_bar[s]), CONV ? kConv : 1);   // FP8 / FP32: the converters
       mbar_init(smem_u32(&empty_bar[s]), 1);
     }
-    for (int s = 0; s < kF8Stages; ++s) {
+    for (int s = 0; s < kRingMax; ++s) {
       mbar_init(smem_u32(&f8_full[s]), 1);
       mbar_init(smem_u32(&f8_empty[s]), kConv);
     }
@@ -214,6 +237,21 @@ __global__ void __launch_bounds__(F8 ? kThreadsF8 : kThreads, 1) dual_pass_tc_ke
             const uint32_t fb = smem_u32(&f8_full[s8]);
             mbar_expect_tx(fb, kX8Stage);
             tma_load_2d(smem_u32(X8 + s8 * kX8Stage), &mapX, col0, row0, fb, pol_x);
+          } else if constexpr (F32) {
+            // four boxes of 32 columns; `issued` counts boxes
+            for (int q = 0; q < 4 && ok; ++q) {
+              const int b = 4 * tI + q, sl = b % ring;
+              if (!mbar_wait(smem_u32(&f8_empty[sl]), ((b / ring) & 1) ^ 1, &abort_f)) {
+                ok = false;
+                break;
+              }
+              const uint32_t fb = smem_u32(&f8_full[sl]);
+              mbar_expect_tx(fb, kF32Box);
+              tma_load_2d(smem_u32(X8 + sl * kF32Box), &mapX, col0 + 32 * q, row0, fb, pol_x);
+              issued = b + 1;
+            }
+            if (!ok) break;
+            continue;
           } else {
             const int s = tI % stages;
             const uint32_t ph = (tI / stages) & 1;
@@ -221,7 +259,7 @@ __global__ void __launch_bounds__(F8 ? kThreadsF8 : kThreads, 1) dual_pass_tc_ke
               ok = false;
               break;
             }
-            unsigned char* st = Xs + s * kXStage;
+            unsigned char* st = Xs + s * kXStg;
             const uint32_t fb = smem_u32(&full_bar[s]);
             mbar_expect_tx(fb, kXStage);
             tma_load_2d(smem_u32(st), &mapX, col0, row0, fb, pol_x);
@@ -234,9 +272,9 @@ __global__ void __launch_bounds__(F8 ? kThreadsF8 : kThreads, 1) dual_pass_tc_ke
       mbar_drain(vb, 0);
       for (int lr = u_issued - 2 > 0 ? u_issued - 2 : 0; lr < u_issued; ++lr)
         mbar_drain(smem_u32(&u_full[lr & 1]), (lr >> 1) & 1);
-      const int ring = F8 ? kF8Stages : stages;
-      for (int tI = issued - ring > 0 ? issued - ring : 0; tI < issued; ++tI)
-        mbar_drain(smem_u32(F8 ? &f8_full[tI % ring] : &full_bar[tI % ring]), (tI / ring) & 1);
+      const int rn = CONV ? ring : stages;   // units: FP8 tiles, FP32 boxes, BF16 tiles
+      for (int tI = issued - rn > 0 ? issued - rn : 0; tI < issued; ++tI)
+        mbar_drain(smem_u32(CONV ? &f8_full[tI % rn] : &full_bar[tI % rn]), (tI / rn) & 1);
     }
   } else if (warp == 5) {
     // ---------------- MMA issuer
@@ -263,9 +301,11 @@ __global__ void __launch_bounds__(F8 ? kThreadsF8 : kThreads, 1) dual_pass_tc_ke
             break;
           }
           tc_fence_after();
-          const uint32_t xa = smem_u32(Xs + s * kXStage), xb = xa + kXHalf;
+          const uint32_t xa = smem_u32(Xs + s * kXStg), xb = xa + kXHalf;
           const uint32_t vbase = smem_u32(Vs + lc * kBTile);
-          const uint32_t dZ = tmem + static_cast<uint32_t>((2 + lc) * AS);
+          // FP32 X: Z of this row block in buffer yb (drained with Y), else resident per tile
+          const uint32_t dZ = tmem + static_cast<uint32_t>((2 + (F32 ? yb * NCT : 0) + lc) * AS);
+          const bool zacc = !F32 && lr > 0;
 #pragma unroll
           for (int kk = 0; kk < 8; ++kk) {
             const uint32_t off = (kk & 3) * 32;
@@ -279,7 +319,14 @@ __global__ void __launch_bounds__(F8 ? kThreadsF8 : kThreads, 1) dual_pass_tc_ke
               const uint64_t bY = sdesc(vbase + (sp * 2 + hf) * kBBox + off, 16, 1024);
               mma_bf16(dY, aY, bY, idY, (lc > 0 || kk > 0 || sp > 0) ? 1u : 0u);
               const uint64_t bZ = sdesc(ubase + (sp * 2 + hf) * kBBox + off, 16, 1024);
-              mma_bf16(dZ, aZ, bZ, idZ, (lr > 0 || kk > 0 || sp > 0) ? 1u : 0u);
+              mma_bf16(dZ, aZ, bZ, idZ, (zacc || kk > 0 || sp > 0) ? 1u : 0u);
+            }
+            if constexpr (F32) {
+              // x_lo times the hi parts of V and U (the lo tile sits kXStage past the hi tile)
+              const uint64_t aYl = sdesc((kk < 4 ? xa : xb) + kXStage + off, 16, 1024);
+              const uint64_t aZl = sdesc(xa + kXStage + kk * 2048, kXHalf, 1024);
+              mma_bf16(dY, aYl, sdesc(vbase + hf * kBBox + off, 16, 1024), idY, 1u);
+              mma_bf16(dZ, aZl, sdesc(ubase + hf * kBBox + off, 16, 1024), idZ, 1u);
             }
           }
           mma_commit(smem_u32(&empty_bar[s]));
@@ -344,12 +391,67 @@ __global__ void __launch_bounds__(F8 ? kThreadsF8 : kThreads, 1) dual_pass_tc_ke
           mbar_arrive(smem_u32(&f8_empty[s8]));
         }
       }
+    } else if constexpr (F32) {
+      // thread t splits columns 16 part .. 16 part + 15 of every box of row ct
+      const int ct = (threadIdx.x - kThreads) & 127, part = (threadIdx.x - kThreads) >> 7;
+      const int sw = ct & 7;
+      bool ok = true;
+      for (int tI = 0; tI < ntiles && ok; ++tI) {
+        const int s = tI % stages;
+        if (!mbar_wait(smem_u32(&empty_bar[s]), ((tI / stages) & 1) ^ 1, &abort_f)) break;
+        unsigned char* dst = Xs + s * kXStg + ct * 128;
+        for (int q = 0; q < 4; ++q) {
+          const int b = 4 * tI + q, sl = b % ring;
+          if (!mbar_wait(smem_u32(&f8_full[sl]), (b / ring) & 1, &abort_f)) {
+            ok = false;
+            break;
+          }
+          // FP32 chunk c (columns 4c .. 4c + 3 of the box) of row ct sits at 16-byte slot c ^ sw
+          const unsigned char* src = X8 + sl * kF32Box + ct * 128;
+          float x[16];
+#pragma unroll
+          for (int cc = 0; cc < 4; ++cc) {
+            const float4 v = *reinterpret_cast<const float4*>(src + (((4 * part + cc) ^ sw) << 4));
+            x[4 * cc] = v.x;
+            x[4 * cc + 1] = v.y;
+            x[4 * cc + 2] = v.z;
+            x[4 * cc + 3] = v.w;
+          }
+          uint32_t hi[8], lo[8];
+#pragma unroll
+          for (int h = 0; h < 8; ++h) {
+            const __nv_bfloat162 hb = __floats2bfloat162_rn(x[2 * h], x[2 * h + 1]);
+            const float2 hf = __bfloat1622float2(hb);
+            const __nv_bfloat162 lb = __floats2bfloat162_rn(x[2 * h] - hf.x, x[2 * h + 1] - hf.y);
+            hi[h] = *reinterpret_cast<const uint32_t*>(&hb);
+            lo[h] = *reinterpret_cast<const uint32_t*>(&lb);
+          }
+          mbar_arrive(smem_u32(&f8_empty[sl]));   // the box may be refilled
+          // tile columns 32 q + 16 part .. + 15: half q / 2, BF16 chunks j0 and j0 + 1
+          unsigned char* hrow = dst + (q >> 1) * kXHalf;
+          const int j0 = (q & 1) * 4 + 2 * part;
+          *reinterpret_cast<uint4*>(hrow + ((j0 ^ sw) << 4)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+          *reinterpret_cast<uint4*>(hrow + (((j0 + 1) ^ sw) << 4)) =
+              make_uint4(hi[4], hi[5], hi[6], hi[7]);
+          *reinterpret_cast<uint4*>(hrow + kXStage + ((j0 ^ sw) << 4)) =
+              make_uint4(lo[0], lo[1], lo[2], lo[3]);
+          *reinterpret_cast<uint4*>(hrow + kXStage + (((j0 + 1) ^ sw) << 4)) =
+              make_uint4(lo[4], lo[5], lo[6], lo[7]);
+        }
+        if (!ok) break;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(smem_u32(&full_bar[s]));
+      }
     }
   } else {
     // ---------------- epilogue: warps 0-3, TMEM lanes 32 warp .. 32 warp + 31
     // partial sums are k-major, so each store of a warp covers 32 consecutive floats
     const uint32_t lane_base = static_cast<uint32_t>(warp * 32) << 16;
     float v[16];
+    // FP32 X: this thread's column (one a tile) summed over the row blocks, round-to-nearest
+    float zsum[F32 ? NCT * LP : 1];
+#pragma unroll
+    for (int i = 0; i < (F32 ? NCT * LP : 1); ++i) zsum[i] = 0.f;
     for (int lr = 0; lr < (ntiles > 0 ? nrb : 0); ++lr) {
       const int yb = lr & 1;
       if (!mbar_wait(smem_u32(&ydone_bar[yb]), (lr >> 1) & 1, &abort_f)) break;
@@ -365,10 +467,34 @@ __global__ void __launch_bounds__(F8 ? kThreadsF8 : kThreads, 1) dual_pass_tc_ke
             if (c + k < a.ell) __stcg(dst + static_cast<int64_t>(c + k) * a.m, v[k]);
         }
       }
+      if constexpr (F32) {
+#pragma unroll
+        for (int lc = 0; lc < NCT; ++lc) {
+          if (lc < nct) {
+#pragma unroll
+            for (int c = 0; c < LP; c += 16) {
+              tmem_ld16(tmem + lane_base + (2 + yb * NCT + lc) * AS + c, v);
+#pragma unroll
+              for (int k = 0; k < 16; ++k) zsum[lc * LP + c + k] += v[k];
+            }
+          }
+        }
+      }
       tc_fence_before();
       mbar_arrive(smem_u32(&yfree_bar[yb]));
     }
-    if (ntiles > 0 && mbar_wait(smem_u32(&zdone_bar), 0, &abort_f)) {
+    if constexpr (F32) {
+#pragma unroll
+      for (int lc = 0; lc < NCT; ++lc) {
+        const int64_t col = (ct0 + lc) * kCols + warp * 32 + lane;
+        if (lc < nct && ntiles > 0 && col < a.n) {
+          float* dst = a.Zpart + static_cast<int64_t>(rg) * a.ell * a.n + col;
+#pragma unroll
+          for (int c = 0; c < LP; ++c)
+            if (c < a.ell) __stcg(dst + static_cast<int64_t>(c) * a.n, zsum[lc * LP + c]);
+        }
+      }
+    } else if (ntiles > 0 && mbar_wait(smem_u32(&zdone_bar), 0, &abort_f)) {
       tc_fence_after();
       for (int lc = 0; lc < nct; ++lc) {
         const int64_t col = (ct0 + lc) * kCols + warp * 32 + lane;
@@ -536,7 +662,7 @@ int num_sms() {
 int lp16(int ell) { return (ell + 15) / 16 * 16; }
 
 struct Plan {
-  int LP, split, stages, nct;
+  int LP, split, stages, nct, ring;
   size_t smem;
   int rowgroups, colgroups, tiles_per_group;   // rowgroups: the most of any column group
   int ctas;
@@ -544,20 +670,39 @@ struct Plan {
   GroupTable gt;
 };
 
-size_t smem_bytes(int LP, int split, int stages, int nct, bool f8 = false) {
+// ring: FP32 boxes in flight (FP32 X only)
+size_t smem_bytes(int LP, int split, int stages, int nct, int xk = kXkBf16, int ring = 0) {
   const size_t btile = static_cast<size_t>(split) * 2 * LP * kHalfCols * 2;
-  return static_cast<size_t>(stages) * kXStage + (f8 ? kF8Stages * kX8Stage : 0) + 2 * btile +
+  const size_t xin = xk == kXkF8 ? kF8Stages * kX8Stage
+                     : xk == kXkF32 ? static_cast<size_t>(ring) * kF32Box : 0;
+  return static_cast<size_t>(stages) * (xk == kXkF32 ? 2 : 1) * kXStage + xin + 2 * btile +
          static_cast<size_t>(nct) * btile + 1024;
 }
 
 // Deepest X pipeline that still keeps enough resident column tiles (4 stages with
 // min(4, NCT) tiles, else 3 stages with min(2, NCT), else 2 stages with one), then as many
 // resident column tiles as fit. nct = 0 means the configuration does not fit.
-void pick_stages(int LP, int split, int* stages, int* nct, bool f8 = false) {
-  const int cap = nct_max(LP);
+// FP32 X: one stage of hi + lo tiles (64 KB) and a ring of four FP32 boxes (one tile in
+// flight), or two boxes when the split bases leave no room for four.
+void pick_stages(int LP, int split, int* stages, int* nct, int xk = kXkBf16, int* ring = nullptr) {
+  const int cap = xk == kXkF32 ? nct_f32_max(LP) : nct_max(LP);
+  if (xk == kXkF32) {
+    *stages = 1;
+    for (int rg = kRingMax; rg >= 2; rg -= 2) {
+      int k = cap;
+      while (k > 0 && smem_bytes(LP, split, 1, k, xk, rg) > static_cast<size_t>(kSmemCap)) --k;
+      if (k > 0) {
+        *nct = k;
+        if (ring) *ring = rg;
+        return;
+      }
+    }
+    *nct = 0;
+    return;
+  }
   for (int s = kMaxStages; s >= 2; --s) {
     int k = cap;
-    while (k > 0 && smem_bytes(LP, split, s, k, f8) > static_cast<size_t>(kSmemCap)) --k;
+    while (k > 0 && smem_bytes(LP, split, s, k, xk) > static_cast<size_t>(kSmemCap)) --k;
     const int want = s == 4 ? (cap < 4 ? cap : 4) : s == 3 ? (cap < 2 ? cap : 2) : 1;
     if (k >= want && k > 0) {
       *stages = s;
@@ -569,12 +714,13 @@ void pick_stages(int LP, int split, int* stages, int* nct, bool f8 = false) {
   *nct = 0;
 }
 
-Plan plan_for(int64_t m, int64_t n, int ell, int split, bool f8 = false) {
+Plan plan_for(int64_t m, int64_t n, int ell, int split, int xk = kXkBf16) {
   Plan p;
   p.LP = lp16(ell);
   p.split = split;
-  pick_stages(p.LP, split, &p.stages, &p.nct, f8);
-  p.smem = smem_bytes(p.LP, split, p.stages, p.nct > 0 ? p.nct : 1, f8);
+  p.ring = 0;
+  pick_stages(p.LP, split, &p.stages, &p.nct, xk, &p.ring);
+  p.smem = smem_bytes(p.LP, split, p.stages, p.nct > 0 ? p.nct : 1, xk, p.ring);
   p.rowblocks = cdiv(m, kRows);
   p.coltiles = cdiv(n, kCols);
   const int nct = p.nct > 0 ? p.nct : 1;
@@ -628,32 +774,45 @@ Plan plan_for(int64_t m, int64_t n, int ell, int split, bool f8 = false) {
   return p;
 }
 
-template <int LP, int SPLIT, bool F8>
+template <int LP, int SPLIT, int XK>
 cudaError_t launch_t(const Launcher& L, const CUtensorMap& mx, const CUtensorMap& mv,
                      const CUtensorMap& mu, const TcArgs& a, size_t smem) {
-  auto k = dual_pass_tc_kernel<LP, SPLIT, F8>;
+  auto k = dual_pass_tc_kernel<LP, SPLIT, XK>;
   if (smem < 120 * 1024) smem = 120 * 1024;   // one CTA per SM: it owns the tensor memory
   cudaError_t err =
       cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (err != cudaSuccess) return err;
   dim3 grid(a.gt.table ? a.gt.cta0[a.n_colgroups] : a.n_colgroups * a.n_rowgroups);
-  k<<<grid, F8 ? kThreadsF8 : kThreads, smem, L.stream>>>(mx, mv, mu, a);
+  k<<<grid, XK != kXkBf16 ? kThreadsF8 : kThreads, smem, L.stream>>>(mx, mv, mu, a);
   L.count();
   return cudaGetLastError();
 }
 
-template <int SPLIT, bool F8>
+template <int SPLIT, int XK>
 cudaError_t launch_lp(int LP, const Launcher& L, const CUtensorMap& mx, const CUtensorMap& mv,
                       const CUtensorMap& mu, const TcArgs& a, size_t smem) {
   switch (LP) {
-    case 16: return launch_t<16, SPLIT, F8>(L, mx, mv, mu, a, smem);
-    case 32: return launch_t<32, SPLIT, F8>(L, mx, mv, mu, a, smem);
-    case 48: return launch_t<48, SPLIT, F8>(L, mx, mv, mu, a, smem);
-    case 64: return launch_t<64, SPLIT, F8>(L, mx, mv, mu, a, smem);
-    case 80: return launch_t<80, SPLIT, F8>(L, mx, mv, mu, a, smem);
-    case 96: return launch_t<96, SPLIT, F8>(L, mx, mv, mu, a, smem);
-    case 112: return launch_t<112, SPLIT, F8>(L, mx, mv, mu, a, smem);
-    case 128: return launch_t<128, SPLIT, F8>(L, mx, mv, mu, a, smem);
+    case 16: return launch_t<16, SPLIT, XK>(L, mx, mv, mu, a, smem);
+    case 32: return launch_t<32, SPLIT, XK>(L, mx, mv, mu, a, smem);
+    case 48: return launch_t<48, SPLIT, XK>(L, mx, mv, mu, a, smem);
+    case 64: return launch_t<64, SPLIT, XK>(L, mx, mv, mu, a, smem);
+    case 80: return launch_t<80, SPLIT, XK>(L, mx, mv, mu, a, smem);
+    case 96: return launch_t<96, SPLIT, XK>(L, mx, mv, mu, a, smem);
+    case 112: return launch_t<112, SPLIT, XK>(L, mx, mv, mu, a, smem);
+    case 128: return launch_t<128, SPLIT, XK>(L, mx, mv, mu, a, smem);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// FP32 X: the split bases fit shared memory up to LP = 80
+cudaError_t launch_lp_f32(int LP, const Launcher& L, const CUtensorMap& mx, const CUtensorMap& mv,
+                          const CUtensorMap& mu, const TcArgs& a, size_t smem) {
+  switch (LP) {
+    case 16: return launch_t<16, 2, kXkF32>(L, mx, mv, mu, a, smem);
+    case 32: return launch_t<32, 2, kXkF32>(L, mx, mv, mu, a, smem);
+    case 48: return launch_t<48, 2, kXkF32>(L, mx, mv, mu, a, smem);
+    case 64: return launch_t<64, 2, kXkF32>(L, mx, mv, mu, a, smem);
+    case 80: return launch_t<80, 2, kXkF32>(L, mx, mv, mu, a, smem);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -673,12 +832,24 @@ bool dual_pass_tc_split_supported(int ell) {
   return ell >= 1 && ell <= 128 && k > 0;
 }
 
+bool dual_pass_tc_f32_supported(int64_t m, int64_t n, int64_t ldx, int ell, const void* X) {
+  if (ell < 1 || ell > 80) return false;
+  // TMA: 16-byte aligned base and row pitch; every box starts at a column multiple of 32
+  if (ldx % 4 != 0 || (reinterpret_cast<uintptr_t>(X) & 15) != 0) return false;
+  if (m > (int64_t(1) << 31) - kRows || n > (int64_t(1) << 31) - kCols) return false;
+  int s = 0, k = 0, rg = 0;
+  pick_stages(lp16(ell), 2, &s, &k, kXkF32, &rg);
+  return k > 0 && encode_fn() != nullptr;
+}
+
 size_t dual_pass_tc_ws_bytes(int64_t m, int64_t n, int ell) {
-  // the largest of the layouts (plain and split operands, BF16 and FP8 X)
+  // the largest of the layouts (plain and split operands, BF16, FP8 and FP32 X)
   size_t best = 0;
-  for (int v = 0; v < 3; ++v) {
-    const int split = v == 1 ? 2 : 1;
-    const Plan p = plan_for(m, n, ell, split, v == 2);
+  for (int v = 0; v < 4; ++v) {
+    const int split = (v == 1 || v == 3) ? 2 : 1;
+    const int xk = v == 2 ? kXkF8 : v == 3 ? kXkF32 : kXkBf16;
+    if (v == 3 && ell > 80) continue;
+    const Plan p = plan_for(m, n, ell, split, xk);
     const int64_t ldv = (n + 7) / 8 * 8, ldu = (m + 7) / 8 * 8;
     const size_t b =
         sizeof(float) * static_cast<size_t>(p.colgroups * m * ell + p.rowgroups * n * ell) +
@@ -691,11 +862,11 @@ size_t dual_pass_tc_ws_bytes(int64_t m, int64_t n, int ell) {
 namespace {
 
 // Operand preparation, the kernel and the slot sums for one dual pass; mx maps X (BF16 halves of
-// 128 x 64, or FP8 tiles of 128 x 128), S / tn the FP8 tile scales.
-cudaError_t run_tc(const Launcher& L, const CUtensorMap& mx, bool f8, const uint8_t* S, int64_t tn,
+// 128 x 64, FP8 tiles of 128 x 128, or FP32 boxes of 128 x 32), S / tn the FP8 tile scales.
+cudaError_t run_tc(const Launcher& L, const CUtensorMap& mx, int xk, const uint8_t* S, int64_t tn,
                    int64_t m, int64_t n, int ell, const float* V, const float* U, float* Y,
                    float* Z, void* ws, int* status, int sp, bool z_kmajor) {
-  const Plan p = plan_for(m, n, ell, sp, f8);
+  const Plan p = plan_for(m, n, ell, sp, xk);
   if (p.nct < 1) return cudaErrorInvalidValue;
   const int64_t ldv = (n + 7) / 8 * 8, ldu = (m + 7) / 8 * 8;
   char* w = static_cast<char*>(ws);
@@ -738,10 +909,12 @@ cudaError_t run_tc(const Launcher& L, const CUtensorMap& mx, bool f8, const uint
   a.status = status;
   a.S = S;
   a.tn = tn;
-  const size_t smem = smem_bytes(p.LP, sp, p.stages, p.tiles_per_group, f8);
-  cudaError_t err = f8 ? launch_lp<1, true>(p.LP, L, mx, mv, mu, a, smem)
-                    : sp == 2 ? launch_lp<2, false>(p.LP, L, mx, mv, mu, a, smem)
-                              : launch_lp<1, false>(p.LP, L, mx, mv, mu, a, smem);
+  a.ring = p.ring;
+  const size_t smem = smem_bytes(p.LP, sp, p.stages, p.tiles_per_group, xk, p.ring);
+  cudaError_t err = xk == kXkF8 ? launch_lp<1, kXkF8>(p.LP, L, mx, mv, mu, a, smem)
+                    : xk == kXkF32 ? launch_lp_f32(p.LP, L, mx, mv, mu, a, smem)
+                    : sp == 2      ? launch_lp<2, kXkBf16>(p.LP, L, mx, mv, mu, a, smem)
+                                   : launch_lp<1, kXkBf16>(p.LP, L, mx, mv, mu, a, smem);
   if (err != cudaSuccess) return err;
   const int by = static_cast<int>(cdiv(m, kRedRows));
   dim3 gr(static_cast<unsigned>(by + cdiv(n, kRedRows)), static_cast<unsigned>(cdiv(ell, 8)));
@@ -763,7 +936,21 @@ cudaError_t launch_dual_pass_tc(const Launcher& L, const __nv_bfloat16* X, int64
   if (!make_map(&mx, X, static_cast<uint64_t>(n), static_cast<uint64_t>(m),
                 static_cast<uint64_t>(ldx), kHalfCols, kRows))
     return cudaErrorInvalidValue;
-  return run_tc(L, mx, false, nullptr, 0, m, n, ell, V, U, Y, Z, ws, status, sp, z_kmajor);
+  return run_tc(L, mx, kXkBf16, nullptr, 0, m, n, ell, V, U, Y, Z, ws, status, sp, z_kmajor);
+}
+
+cudaError_t launch_dual_pass_tc_f32(const Launcher& L, const float* X, int64_t m, int64_t n,
+                                    int64_t ldx, int ell, const float* V, const float* U, float* Y,
+                                    float* Z, void* ws, size_t ws_bytes, int* status,
+                                    bool z_kmajor) {
+  if (ws_bytes < dual_pass_tc_ws_bytes(m, n, ell) || !dual_pass_tc_f32_supported(m, n, ldx, ell, X))
+    return cudaErrorInvalidValue;
+  CUtensorMap mx;
+  if (!make_map_f32(&mx, X, static_cast<uint64_t>(n), static_cast<uint64_t>(m),
+                    static_cast<uint64_t>(ldx), 32, kRows, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_SWIZZLE_128B))
+    return cudaErrorInvalidValue;
+  return run_tc(L, mx, kXkF32, nullptr, 0, m, n, ell, V, U, Y, Z, ws, status, 2, z_kmajor);
 }
 
 bool dual_pass_tc_fp8_supported(int64_t m, int64_t n, int ell, const void* Xq) {
@@ -771,7 +958,7 @@ bool dual_pass_tc_fp8_supported(int64_t m, int64_t n, int ell, const void* Xq) {
   if (m < kRows || n < kCols) return false;   // the 128 x 128 box stays within the tensor
   if (m > (int64_t(1) << 31) - kRows || n > (int64_t(1) << 31) - kCols) return false;
   int s = 0, k = 0;
-  pick_stages(lp16(ell), 1, &s, &k, true);
+  pick_stages(lp16(ell), 1, &s, &k, kXkF8);
   return k > 0 && encode_fn() != nullptr;
 }
 
@@ -785,7 +972,7 @@ cudaError_t launch_dual_pass_tc_fp8(const Launcher& L, const uint8_t* Xq, int64_
   if (!make_map8(&mx, Xq, static_cast<uint64_t>(n), static_cast<uint64_t>(m),
                  static_cast<uint64_t>(ldq)))
     return cudaErrorInvalidValue;
-  return run_tc(L, mx, true, Xq + off, (n + 31) / 32, m, n, ell, V, U, Y, Z, ws, status, 1,
+  return run_tc(L, mx, kXkF8, Xq + off, (n + 31) / 32, m, n, ell, V, U, Y, Z, ws, status, 1,
                 z_kmajor);
 }
 

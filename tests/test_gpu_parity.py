@@ -69,8 +69,11 @@ def test_quantize_bf16_bit_exact(lib, ctx, shape):
 
 # ------------------------------------------------------------------ dual pass (Eq. 3.5 step)
 
+# FP32 X takes the tensor-core pass (hi + lo BF16 splits of X, V and U) when n is a multiple of 4
+# and ell <= 80, else the SIMT pass; both are held to 1e-5 of the FP64 products.
 DUAL_SHAPES = [(512, 256, 18), (300, 517, 18), (1000, 777, 40), (129, 130, 1), (257, 1025, 70),
-               (64, 64, 64), (2000, 300, 128)]
+               (64, 64, 64), (2000, 300, 128), (1000, 784, 40), (300, 1032, 70), (130, 132, 80),
+               (5000, 3000, 48), (77, 4, 3), (4096, 1000, 80), (20000, 5000, 40)]
 
 
 @pytest.mark.parametrize("m,n,ell", DUAL_SHAPES)
@@ -81,8 +84,29 @@ def test_dual_pass_fp32(lib, ctx, m, n, ell):
     U = rng.standard_normal((m, ell)).astype(np.float32)
     Y, Z = lib.nmf_dual_pass(ctx, cu(X), cu(V), cu(U))
     X64 = X.astype(np.float64)
-    assert rel(host(Y), X64 @ V) <= 1e-5
-    assert rel(host(Z), X64.T @ U) <= 1e-5
+    ey, ez = rel(host(Y), X64 @ V), rel(host(Z), X64.T @ U)
+    print(f"fp32 pass {m}x{n} l={ell} ({'tc' if n % 4 == 0 and ell <= 80 else 'simt'}): "
+          f"{ey:.2e} {ez:.2e}")
+    assert ey <= 1e-5 and ez <= 1e-5
+
+
+def test_dual_pass_fp32_tensor_core_is_deterministic_and_handles_signs(lib, ctx):
+    """Mixed signs and magnitudes spanning 2^-20 .. 2^20 (the split is relative per element),
+    and two runs bit-identical (fixed slot order)."""
+    rng = np.random.default_rng(5)
+    m, n, ell = 3000, 1024, 40
+    X = (rng.standard_normal((m, n)) * 2.0 ** rng.integers(-20, 21, (m, n))).astype(np.float32)
+    V = rng.standard_normal((n, ell)).astype(np.float32)
+    U = rng.standard_normal((m, ell)).astype(np.float32)
+    Y, Z = lib.nmf_dual_pass(ctx, cu(X), cu(V), cu(U))
+    Y2, Z2 = lib.nmf_dual_pass(ctx, cu(X), cu(V), cu(U))
+    assert torch.equal(Y, Y2) and torch.equal(Z, Z2)
+    X64 = X.astype(np.float64)
+    # each product is off by at most ~3 * 2^-18 of sum |x| |v|: compare against that scale
+    ay = np.abs(X64) @ np.abs(V.astype(np.float64))
+    az = np.abs(X64).T @ np.abs(U.astype(np.float64))
+    assert np.max(np.abs(host(Y) - X64 @ V) / ay) <= 2e-5
+    assert np.max(np.abs(host(Z) - X64.T @ U) / az) <= 2e-5
 
 
 def test_dual_pass_strided_x_and_single_sides(lib, ctx):
@@ -103,7 +127,9 @@ def test_dual_pass_strided_x_and_single_sides(lib, ctx):
                                      (2000, 520, 128), (5000, 3000, 40), (64, 8, 1),
                                      (3000, 4096, 100)])
 def test_dual_pass_bf16(lib, ctx, m, n, ell):
-    """BF16 X (n a multiple of 8 goes to the tcgen05/TMA kernel, other n to the SIMT kernel)."""
+    """BF16 X: n a multiple of 8 goes to the tcgen05/TMA kernel, which also rounds V and U to
+    BF16 (one BF16 operand each, as in the sketch passes); other n to the SIMT kernel, which
+    keeps V and U in FP32. Each is held to its own reference."""
     rng = np.random.default_rng(11 + m)
     X = rng.uniform(0, 1, (m, n)).astype(np.float32)
     V = rng.standard_normal((n, ell)).astype(np.float32)
@@ -111,13 +137,12 @@ def test_dual_pass_bf16(lib, ctx, m, n, ell):
     Xq = lib.nmf_quantize(ctx, cu(X))
     Y, Z = lib.nmf_dual_pass(ctx, Xq, cu(V), cu(U), prec="bf16")
     Xb = bf16_round(X).astype(np.float64)
-    Vb, Ub = V.astype(np.float64), U.astype(np.float64)
-    # the tensor-core path also rounds V, U to BF16; the SIMT path keeps them FP32
-    tol = 1e-5
-    if rel(host(Y), Xb @ Vb) > tol:
+    if n % 8 == 0:
         Vb, Ub = bf16_round(V).astype(np.float64), bf16_round(U).astype(np.float64)
-    assert rel(host(Y), Xb @ Vb) <= tol
-    assert rel(host(Z), Xb.T @ Ub) <= tol
+    else:
+        Vb, Ub = V.astype(np.float64), U.astype(np.float64)
+    assert rel(host(Y), Xb @ Vb) <= 1e-5
+    assert rel(host(Z), Xb.T @ Ub) <= 1e-5
 
 
 # ------------------------------------------------------------------ QR (Section 3)
@@ -155,12 +180,29 @@ def exact_rank_problem(seed, m, n, r, ell):
 
 
 def test_sketch_of_exact_low_rank_x_breaks_down_without_repair(lib, ctx):
+    """The SIMT pass keeps FP32 products (null directions of the pass output at ~1e-7 relative),
+    so CholeskyQR2 meets the dependent columns and reports the breakdown."""
     X, oL, oR = exact_rank_problem(3, 600, 400, 5, 12)
-    p = lib.params(600, 400, 5, 12, power_iters=2)
+    p = lib.params(600, 400, 5, 12, power_iters=2, flags=lib.FLAG_SIMT_DUAL_PASS)
     lib.nmf_sketch(ctx, p, cu(X), cu(oL), cu(oR))
     with pytest.raises(lib.NmfError) as e:
         lib.nmf_sync(ctx)
     assert e.value.status == 4
+
+
+def test_tensor_core_sketch_of_exact_low_rank_x_spans_x(lib, ctx):
+    """The FP32 tensor-core pass (hi + lo BF16 splits) leaves noise of ~4e-6 relative in the
+    null directions, above CholeskyQR2's pivot tolerance: the extra columns come out as
+    orthonormal noise directions (what the repair would draw) and the bases still capture X."""
+    m, n, r, ell = 600, 400, 5, 12
+    X, oL, oR = exact_rank_problem(3, m, n, r, ell)
+    p = lib.params(m, n, r, ell, power_iters=2)
+    QL, QR = lib.nmf_sketch(ctx, p, cu(X), cu(oL), cu(oR))
+    lib.nmf_sync(ctx)
+    QL, QR, X64 = host(QL), host(QR), X.astype(np.float64)
+    assert np.abs(QL.T @ QL - np.eye(ell)).max() <= 1e-5
+    assert np.abs(QR.T @ QR - np.eye(ell)).max() <= 1e-5
+    assert rel(QL @ (QL.T @ X64), X64) <= 1e-5 and rel(X64 @ QR @ QR.T, X64) <= 1e-5
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
