@@ -18,11 +18,13 @@
 // (16 KB, 128B-swizzled) into its own ring, and warps 6-13 rewrite it as the BF16 tile the MMAs
 // read, code times 2^k (exact in BF16), in the same swizzled layout, before signalling the MMA
 // issuer; the HBM stream is half that of BF16 X.
-// FP32 X: TMA brings each tile as four 128-row x 32-column boxes (16 KB, 128B-swizzled) into a
-// ring of boxes; warps 6-13 split every element into hi = bf16(x) and lo = bf16(x - hi) (x to
-// about 2^-18 relative) and write a BF16 hi tile and a BF16 lo tile. With V and U also entering
-// as hi + lo pairs, each product accumulates x_hi v_hi + x_hi v_lo + x_lo v_hi: FP32-grade sums
-// on the BF16 tensor cores from one FP32 stream of X. Partial
+// FP32 X: TMA brings each tile into a 64 KB stage as four 32-row x 128-column boxes (512-byte
+// rows, no swizzle); warps 6-13 read it into registers, meet at a barrier, and rewrite the stage
+// in place as a BF16 hi tile and a BF16 lo tile (hi = bf16(x), lo = bf16(x - hi): x to about
+// 2^-18 relative), which is the same 64 KB. Two stages let one tile convert while the previous
+// one's MMAs run. With V and U also entering as hi + lo pairs, each product accumulates
+// x_hi v_hi + x_hi v_lo + x_lo v_hi: FP32-grade sums on the BF16 tensor cores from one FP32
+// stream of X. Partial
 // sums of Y (one per column group) and Z (one per row group) are summed in a fixed slot order
 // by one slot-sum launch for both. Every mbarrier wait is bounded; on time-out the kernel
 // latches NMF_ERR_TIMEOUT, drains what it issued and frees its tensor memory.
@@ -48,8 +50,7 @@ constexpr int kThreadsF8 = 448;     // + warps 6-13: FP8 -> BF16 converters (two
 constexpr int kConv = kThreadsF8 - kThreads;
 constexpr int kF8Stages = 4;        // ring of FP8 tiles
 constexpr uint32_t kX8Stage = 128 * 128;   // one 128 x 128 E4M3 tile (16 KB)
-constexpr int kRingMax = 4;         // ring slots of the converted element types (FP8 tiles, FP32 boxes)
-constexpr uint32_t kF32Box = 128 * 128;    // one 128-row x 32-column FP32 box (16 KB)
+constexpr uint32_t kF32Box = 32 * 128 * 4;   // one 32-row x 128-column FP32 box (16 KB)
 
 // Element type of X inside the kernel: BF16 read by the MMAs directly, or FP8 / FP32 converted
 // to BF16 in shared memory first.
@@ -88,7 +89,7 @@ struct TcArgs {
   int* status;
   const uint8_t* S;               // FP8 X: E8M0 tile scales (row-major, tn a row)
   int64_t tn;
-  int ring;                       // FP32 X: boxes in the ring (<= kRingMax)
+  int nub;                        // U buffers (2, or 1 where shared memory is short)
 };
 
 // Two E4M3 codes (low byte = first element) times 2^k (exact) as a BF16 pair (low half first).
@@ -141,16 +142,17 @@ __global__ void __launch_bounds__(XK != kXkBf16 ? kThreadsF8 : kThreads, 1) dual
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-  const int stages = a.stages;
-  const int ring = F8 ? kF8Stages : a.ring;               // converted ring: FP8 tiles or FP32 boxes
+  const int stages = a.stages, nub = a.nub;
   unsigned char* Xs = smem;                              // [stages][kXStg]
-  unsigned char* X8 = Xs + stages * kXStg;               // FP8: [kF8Stages][16 KB]; FP32: [ring][16 KB]
-  unsigned char* Us = X8 + (F8 ? kF8Stages * kX8Stage : F32 ? ring * kF32Box : 0u);   // [2][SPLIT][2 halves][kBBox]
-  unsigned char* Vs = Us + 2 * kBTile;                   // [nct][SPLIT][2 halves][kBBox]
+  unsigned char* X8 = Xs + stages * kXStg;               // [kF8Stages][16 KB] (F8 only)
+  unsigned char* Us = X8 + (F8 ? kF8Stages * kX8Stage : 0u);   // [nub][SPLIT][2 halves][kBBox]
+  unsigned char* Vs = Us + nub * kBTile;                 // [nct][SPLIT][2 halves][kBBox]
   __shared__ __align__(8) uint64_t full_bar[kMaxStages], empty_bar[kMaxStages];
   __shared__ __align__(8) uint64_t u_full[2], u_empty[2], v_full;
   __shared__ __align__(8) uint64_t ydone_bar[2], yfree_bar[2], zdone_bar, drain_bar;
-  __shared__ __align__(8) uint64_t f8_full[kRingMax], f8_empty[kRingMax];
+  __shared__ __align__(8) uint64_t conv_bar;   // FP32: the converters' read-before-write barrier
+  // FP8: the ring of code tiles; FP32: f8_full[s] = the FP32 tile of stage s has landed
+  __shared__ __align__(8) uint64_t f8_full[kF8Stages], f8_empty[kF8Stages];
   __shared__ uint32_t tmem_base;
   __shared__ volatile int abort_f;
 
@@ -180,7 +182,7 @@ __global__ void __launch_bounds__(XK != kXkBf16 ? kThreadsF8 : kThreads, 1) dual
       mbar_init(smem_u32(&full_bar[s]), CONV ? kConv : 1);   // FP8 / FP32: the converters
       mbar_init(smem_u32(&empty_bar[s]), 1);
     }
-    for (int s = 0; s < kRingMax; ++s) {
+    for (int s = 0; s < kF8Stages; ++s) {
       mbar_init(smem_u32(&f8_full[s]), 1);
       mbar_init(smem_u32(&f8_empty[s]), kConv);
     }
@@ -193,6 +195,7 @@ __global__ void __launch_bounds__(XK != kXkBf16 ? kThreadsF8 : kThreads, 1) dual
     mbar_init(smem_u32(&v_full), 1);
     mbar_init(smem_u32(&zdone_bar), 1);
     mbar_init(smem_u32(&drain_bar), 1);
+    mbar_init(smem_u32(&conv_bar), kConv);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 5) tmem_alloc(smem_u32(&tmem_base), kTmemCols);
@@ -215,9 +218,9 @@ __global__ void __launch_bounds__(XK != kXkBf16 ? kThreadsF8 : kThreads, 1) dual
       int issued = 0, u_issued = 0;
       bool ok = true;
       for (int lr = 0; lr < nrb && ok; ++lr) {
-        const int ub = lr & 1;
+        const int ub = lr % nub;
         const int row0 = static_cast<int>((rb0 + lr) * kRows);
-        if (!mbar_wait(smem_u32(&u_empty[ub]), ((lr >> 1) & 1) ^ 1, &abort_f)) break;
+        if (!mbar_wait(smem_u32(&u_empty[ub]), ((lr / nub) & 1) ^ 1, &abort_f)) break;
         const uint32_t ubar = smem_u32(&u_full[ub]);
         mbar_expect_tx(ubar, kBTile);
         for (int sp = 0; sp < SPLIT; ++sp)
@@ -238,20 +241,17 @@ __global__ void __launch_bounds__(XK != kXkBf16 ? kThreadsF8 : kThreads, 1) dual
             mbar_expect_tx(fb, kX8Stage);
             tma_load_2d(smem_u32(X8 + s8 * kX8Stage), &mapX, col0, row0, fb, pol_x);
           } else if constexpr (F32) {
-            // four boxes of 32 columns; `issued` counts boxes
-            for (int q = 0; q < 4 && ok; ++q) {
-              const int b = 4 * tI + q, sl = b % ring;
-              if (!mbar_wait(smem_u32(&f8_empty[sl]), ((b / ring) & 1) ^ 1, &abort_f)) {
-                ok = false;
-                break;
-              }
-              const uint32_t fb = smem_u32(&f8_full[sl]);
-              mbar_expect_tx(fb, kF32Box);
-              tma_load_2d(smem_u32(X8 + sl * kF32Box), &mapX, col0 + 32 * q, row0, fb, pol_x);
-              issued = b + 1;
+            // the FP32 tile straight into its stage: four boxes of 32 rows
+            const int s = tI % stages;
+            if (!mbar_wait(smem_u32(&empty_bar[s]), ((tI / stages) & 1) ^ 1, &abort_f)) {
+              ok = false;
+              break;
             }
-            if (!ok) break;
-            continue;
+            unsigned char* st = Xs + s * kXStg;
+            const uint32_t fb = smem_u32(&f8_full[s]);
+            mbar_expect_tx(fb, 4 * kF32Box);
+            for (int q = 0; q < 4; ++q)
+              tma_load_2d(smem_u32(st + q * kF32Box), &mapX, col0, row0 + 32 * q, fb, pol_x);
           } else {
             const int s = tI % stages;
             const uint32_t ph = (tI / stages) & 1;
@@ -270,9 +270,9 @@ __global__ void __launch_bounds__(XK != kXkBf16 ? kThreadsF8 : kThreads, 1) dual
       }
       // every copy issued has landed before the CTA may leave
       mbar_drain(vb, 0);
-      for (int lr = u_issued - 2 > 0 ? u_issued - 2 : 0; lr < u_issued; ++lr)
-        mbar_drain(smem_u32(&u_full[lr & 1]), (lr >> 1) & 1);
-      const int rn = CONV ? ring : stages;   // units: FP8 tiles, FP32 boxes, BF16 tiles
+      for (int lr = u_issued - nub > 0 ? u_issued - nub : 0; lr < u_issued; ++lr)
+        mbar_drain(smem_u32(&u_full[lr % nub]), (lr / nub) & 1);
+      const int rn = F8 ? kF8Stages : stages;   // units: FP8 ring tiles, else stage tiles
       for (int tI = issued - rn > 0 ? issued - rn : 0; tI < issued; ++tI)
         mbar_drain(smem_u32(CONV ? &f8_full[tI % rn] : &full_bar[tI % rn]), (tI / rn) & 1);
     }
@@ -283,9 +283,9 @@ __global__ void __launch_bounds__(XK != kXkBf16 ? kThreadsF8 : kThreads, 1) dual
       constexpr uint32_t idZ = idesc_bf16(LP, 1);   // A = X tile, MN-major
       bool ok = mbar_wait(smem_u32(&v_full), 0, &abort_f);
       for (int lr = 0; lr < nrb && ok; ++lr) {
-        const int yb = lr & 1, ub = lr & 1;
+        const int yb = lr & 1, ub = lr % nub;
         if (!mbar_wait(smem_u32(&yfree_bar[yb]), ((lr >> 1) & 1) ^ 1, &abort_f) ||
-            !mbar_wait(smem_u32(&u_full[ub]), (lr >> 1) & 1, &abort_f)) {
+            !mbar_wait(smem_u32(&u_full[ub]), (lr / nub) & 1, &abort_f)) {
           ok = false;
           break;
         }
@@ -392,53 +392,52 @@ __global__ void __launch_bounds__(XK != kXkBf16 ? kThreadsF8 : kThreads, 1) dual
         }
       }
     } else if constexpr (F32) {
-      // thread t splits columns 16 part .. 16 part + 15 of every box of row ct
-      const int ct = (threadIdx.x - kThreads) & 127, part = (threadIdx.x - kThreads) >> 7;
-      const int sw = ct & 7;
-      bool ok = true;
-      for (int tI = 0; tI < ntiles && ok; ++tI) {
+      // Thread (converter warp cw, lane) takes row rb of every box (tile rows rb + 32 q) and the
+      // 16-byte chunks j, j + 8, j + 16, j + 24 of its 512-byte rows (j = lane % 8). The four
+      // rows of a warp are b, b + 4, b + 2, b + 6 (b = 8 (cw / 2) + cw % 2): a quarter-warp
+      // reads 128 contiguous bytes, and a half-warp's 8-byte stores fall in two rows whose
+      // swizzles differ by 4, so neither side has bank conflicts.
+      const int cw = warp - 6, j = lane & 7, k = lane >> 3;
+      const int rb = 8 * (cw >> 1) + (cw & 1) + (((k & 1) << 2) | (k & 2));
+      const int sw = rb & 7;   // tile row 32 q + rb has the same swizzle phase
+      for (int tI = 0; tI < ntiles; ++tI) {
         const int s = tI % stages;
-        if (!mbar_wait(smem_u32(&empty_bar[s]), ((tI / stages) & 1) ^ 1, &abort_f)) break;
-        unsigned char* dst = Xs + s * kXStg + ct * 128;
+        if (!mbar_wait(smem_u32(&f8_full[s]), (tI / stages) & 1, &abort_f)) break;
+        unsigned char* st = Xs + s * kXStg;
+        float4 x[4][4];   // [box q][chunk cc]
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+          for (int cc = 0; cc < 4; ++cc)
+            x[q][cc] = *reinterpret_cast<const float4*>(st + q * kF32Box + rb * 512 +
+                                                        (8 * cc + j) * 16);
+        // every converter has its FP32 values before any of the stage is overwritten (an
+        // mbarrier with a bounded wait, so that an abort cannot leave threads at the barrier)
+        mbar_arrive(smem_u32(&conv_bar));
+        if (!mbar_wait(smem_u32(&conv_bar), tI & 1, &abort_f)) break;
+#pragma unroll
         for (int q = 0; q < 4; ++q) {
-          const int b = 4 * tI + q, sl = b % ring;
-          if (!mbar_wait(smem_u32(&f8_full[sl]), (b / ring) & 1, &abort_f)) {
-            ok = false;
-            break;
-          }
-          // FP32 chunk c (columns 4c .. 4c + 3 of the box) of row ct sits at 16-byte slot c ^ sw
-          const unsigned char* src = X8 + sl * kF32Box + ct * 128;
-          float x[16];
+          unsigned char* rowp = st + (32 * q + rb) * 128;
 #pragma unroll
           for (int cc = 0; cc < 4; ++cc) {
-            const float4 v = *reinterpret_cast<const float4*>(src + (((4 * part + cc) ^ sw) << 4));
-            x[4 * cc] = v.x;
-            x[4 * cc + 1] = v.y;
-            x[4 * cc + 2] = v.z;
-            x[4 * cc + 3] = v.w;
+            const float4 v = x[q][cc];
+            const __nv_bfloat162 h0 = __floats2bfloat162_rn(v.x, v.y);
+            const __nv_bfloat162 h1 = __floats2bfloat162_rn(v.z, v.w);
+            const float2 f0 = __bfloat1622float2(h0), f1 = __bfloat1622float2(h1);
+            const __nv_bfloat162 l0 = __floats2bfloat162_rn(v.x - f0.x, v.y - f0.y);
+            const __nv_bfloat162 l1 = __floats2bfloat162_rn(v.z - f1.x, v.w - f1.y);
+            // columns 4 (8 cc + j) .. + 3: half cc / 2, BF16 chunk 4 (cc % 2) + j / 2, bytes
+            // 8 (j % 2) .. + 7 of it; the lo tile sits kXStage past the hi tile
+            unsigned char* d = rowp + (cc >> 1) * kXHalf +
+                               (((4 * (cc & 1) + (j >> 1)) ^ sw) << 4) + ((j & 1) << 3);
+            *reinterpret_cast<uint2*>(d) = make_uint2(*reinterpret_cast<const uint32_t*>(&h0),
+                                                      *reinterpret_cast<const uint32_t*>(&h1));
+            *reinterpret_cast<uint2*>(d + kXStage) =
+                make_uint2(*reinterpret_cast<const uint32_t*>(&l0),
+                           *reinterpret_cast<const uint32_t*>(&l1));
           }
-          uint32_t hi[8], lo[8];
-#pragma unroll
-          for (int h = 0; h < 8; ++h) {
-            const __nv_bfloat162 hb = __floats2bfloat162_rn(x[2 * h], x[2 * h + 1]);
-            const float2 hf = __bfloat1622float2(hb);
-            const __nv_bfloat162 lb = __floats2bfloat162_rn(x[2 * h] - hf.x, x[2 * h + 1] - hf.y);
-            hi[h] = *reinterpret_cast<const uint32_t*>(&hb);
-            lo[h] = *reinterpret_cast<const uint32_t*>(&lb);
-          }
-          mbar_arrive(smem_u32(&f8_empty[sl]));   // the box may be refilled
-          // tile columns 32 q + 16 part .. + 15: half q / 2, BF16 chunks j0 and j0 + 1
-          unsigned char* hrow = dst + (q >> 1) * kXHalf;
-          const int j0 = (q & 1) * 4 + 2 * part;
-          *reinterpret_cast<uint4*>(hrow + ((j0 ^ sw) << 4)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-          *reinterpret_cast<uint4*>(hrow + (((j0 + 1) ^ sw) << 4)) =
-              make_uint4(hi[4], hi[5], hi[6], hi[7]);
-          *reinterpret_cast<uint4*>(hrow + kXStage + ((j0 ^ sw) << 4)) =
-              make_uint4(lo[0], lo[1], lo[2], lo[3]);
-          *reinterpret_cast<uint4*>(hrow + kXStage + (((j0 + 1) ^ sw) << 4)) =
-              make_uint4(lo[4], lo[5], lo[6], lo[7]);
         }
-        if (!ok) break;
+        // the MMAs read the tiles through the async proxy
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive(smem_u32(&full_bar[s]));
       }
@@ -662,7 +661,7 @@ int num_sms() {
 int lp16(int ell) { return (ell + 15) / 16 * 16; }
 
 struct Plan {
-  int LP, split, stages, nct, ring;
+  int LP, split, stages, nct, nub;
   size_t smem;
   int rowgroups, colgroups, tiles_per_group;   // rowgroups: the most of any column group
   int ctas;
@@ -670,30 +669,30 @@ struct Plan {
   GroupTable gt;
 };
 
-// ring: FP32 boxes in flight (FP32 X only)
-size_t smem_bytes(int LP, int split, int stages, int nct, int xk = kXkBf16, int ring = 0) {
+// nub: U buffers (two unless shared memory is short)
+size_t smem_bytes(int LP, int split, int stages, int nct, int xk = kXkBf16, int nub = 2) {
   const size_t btile = static_cast<size_t>(split) * 2 * LP * kHalfCols * 2;
-  const size_t xin = xk == kXkF8 ? kF8Stages * kX8Stage
-                     : xk == kXkF32 ? static_cast<size_t>(ring) * kF32Box : 0;
-  return static_cast<size_t>(stages) * (xk == kXkF32 ? 2 : 1) * kXStage + xin + 2 * btile +
-         static_cast<size_t>(nct) * btile + 1024;
+  const size_t xin = xk == kXkF8 ? kF8Stages * kX8Stage : 0;
+  return static_cast<size_t>(stages) * (xk == kXkF32 ? 2 : 1) * kXStage + xin +
+         static_cast<size_t>(nub) * btile + static_cast<size_t>(nct) * btile + 1024;
 }
 
 // Deepest X pipeline that still keeps enough resident column tiles (4 stages with
 // min(4, NCT) tiles, else 3 stages with min(2, NCT), else 2 stages with one), then as many
 // resident column tiles as fit. nct = 0 means the configuration does not fit.
-// FP32 X: one stage of hi + lo tiles (64 KB) and a ring of four FP32 boxes (one tile in
-// flight), or two boxes when the split bases leave no room for four.
-void pick_stages(int LP, int split, int* stages, int* nct, int xk = kXkBf16, int* ring = nullptr) {
+// FP32 X: two 64 KB stages (FP32 tile, converted in place to hi + lo), two U buffers, or one
+// where the split bases leave no room for two (LP = 80).
+void pick_stages(int LP, int split, int* stages, int* nct, int xk = kXkBf16, int* nub = nullptr) {
   const int cap = xk == kXkF32 ? nct_f32_max(LP) : nct_max(LP);
+  if (nub) *nub = 2;
   if (xk == kXkF32) {
-    *stages = 1;
-    for (int rg = kRingMax; rg >= 2; rg -= 2) {
+    *stages = 2;
+    for (int u = 2; u >= 1; --u) {
       int k = cap;
-      while (k > 0 && smem_bytes(LP, split, 1, k, xk, rg) > static_cast<size_t>(kSmemCap)) --k;
+      while (k > 0 && smem_bytes(LP, split, 2, k, xk, u) > static_cast<size_t>(kSmemCap)) --k;
       if (k > 0) {
         *nct = k;
-        if (ring) *ring = rg;
+        if (nub) *nub = u;
         return;
       }
     }
@@ -718,9 +717,8 @@ Plan plan_for(int64_t m, int64_t n, int ell, int split, int xk = kXkBf16) {
   Plan p;
   p.LP = lp16(ell);
   p.split = split;
-  p.ring = 0;
-  pick_stages(p.LP, split, &p.stages, &p.nct, xk, &p.ring);
-  p.smem = smem_bytes(p.LP, split, p.stages, p.nct > 0 ? p.nct : 1, xk, p.ring);
+  pick_stages(p.LP, split, &p.stages, &p.nct, xk, &p.nub);
+  p.smem = smem_bytes(p.LP, split, p.stages, p.nct > 0 ? p.nct : 1, xk, p.nub);
   p.rowblocks = cdiv(m, kRows);
   p.coltiles = cdiv(n, kCols);
   const int nct = p.nct > 0 ? p.nct : 1;
@@ -837,8 +835,8 @@ bool dual_pass_tc_f32_supported(int64_t m, int64_t n, int64_t ldx, int ell, cons
   // TMA: 16-byte aligned base and row pitch; every box starts at a column multiple of 32
   if (ldx % 4 != 0 || (reinterpret_cast<uintptr_t>(X) & 15) != 0) return false;
   if (m > (int64_t(1) << 31) - kRows || n > (int64_t(1) << 31) - kCols) return false;
-  int s = 0, k = 0, rg = 0;
-  pick_stages(lp16(ell), 2, &s, &k, kXkF32, &rg);
+  int s = 0, k = 0, u = 0;
+  pick_stages(lp16(ell), 2, &s, &k, kXkF32, &u);
   return k > 0 && encode_fn() != nullptr;
 }
 
@@ -909,8 +907,8 @@ cudaError_t run_tc(const Launcher& L, const CUtensorMap& mx, int xk, const uint8
   a.status = status;
   a.S = S;
   a.tn = tn;
-  a.ring = p.ring;
-  const size_t smem = smem_bytes(p.LP, sp, p.stages, p.tiles_per_group, xk, p.ring);
+  a.nub = p.nub;
+  const size_t smem = smem_bytes(p.LP, sp, p.stages, p.tiles_per_group, xk, p.nub);
   cudaError_t err = xk == kXkF8 ? launch_lp<1, kXkF8>(p.LP, L, mx, mv, mu, a, smem)
                     : xk == kXkF32 ? launch_lp_f32(p.LP, L, mx, mv, mu, a, smem)
                     : sp == 2      ? launch_lp<2, kXkBf16>(p.LP, L, mx, mv, mu, a, smem)
@@ -947,8 +945,7 @@ cudaError_t launch_dual_pass_tc_f32(const Launcher& L, const float* X, int64_t m
     return cudaErrorInvalidValue;
   CUtensorMap mx;
   if (!make_map_f32(&mx, X, static_cast<uint64_t>(n), static_cast<uint64_t>(m),
-                    static_cast<uint64_t>(ldx), 32, kRows, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                    CU_TENSOR_MAP_SWIZZLE_128B))
+                    static_cast<uint64_t>(ldx), kCols, 32, CU_TENSOR_MAP_L2_PROMOTION_L2_256B))
     return cudaErrorInvalidValue;
   return run_tc(L, mx, kXkF32, nullptr, 0, m, n, ell, V, U, Y, Z, ws, status, 2, z_kmajor);
 }

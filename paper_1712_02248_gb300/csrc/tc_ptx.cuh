@@ -182,12 +182,11 @@ inline bool make_map(CUtensorMap* map, const void* base, uint64_t inner, uint64_
 }
 
 // 2-D FP32 tensor map: inner dimension `inner` elements (row pitch `pitch` elements, a multiple of
-// 4), `outer` rows, box `box_inner` x `box_outer`, zero fill outside, L2 promotion `promo`,
-// swizzle `swz` (128B needs box_inner <= 32: one 128-byte row a box row).
+// 4), `outer` rows, box `box_inner` x `box_outer`, no swizzle, zero fill outside, L2 promotion
+// `promo`.
 inline bool make_map_f32(CUtensorMap* map, const void* base, uint64_t inner, uint64_t outer,
                          uint64_t pitch, uint32_t box_inner, uint32_t box_outer,
-                         CUtensorMapL2promotion promo = CU_TENSOR_MAP_L2_PROMOTION_NONE,
-                         CUtensorMapSwizzle swz = CU_TENSOR_MAP_SWIZZLE_NONE) {
+                         CUtensorMapL2promotion promo = CU_TENSOR_MAP_L2_PROMOTION_NONE) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
   const cuuint64_t dims[2] = {inner, outer};
@@ -195,7 +194,7 @@ inline bool make_map_f32(CUtensorMap* map, const void* base, uint64_t inner, uin
   const cuuint32_t box[2] = {box_inner, box_outer};
   const cuuint32_t estr[2] = {1, 1};
   return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box,
-            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swz, promo,
+            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, promo,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
