@@ -166,6 +166,21 @@ size_t iterate_persistent_ws_bytes(int r, int ell);
 // if *done is non-zero on entry the launch does nothing.
 cudaError_t launch_iterate_persistent(const Launcher& L, const IterArgs& a, int iters, void* ws,
                                       size_t ws_bytes, int* status, float* mon, const int* done);
+// The solve's loop in the persistent kernel: iterations continue from solve[6] (a count, kept
+// as a double) and stop at the first check point (every `every` iterations, and the last of
+// `total`) where the error monitor, compared with `target` as the solve's gate does (margin
+// before the first exact check, margin_cal once solve[5] holds a calibration), calls for an
+// exact residual; the launch then leaves the count in solve[6], the estimate in solve[4] and
+// flags[1] = 1. flags[0] set on entry (converged) or no iterations left: flags[1] = 0, no work.
+struct SolveGate {
+  int total = 0, every = 0;
+  int* flags = nullptr;      // [0] converged, [1] exact check due
+  double* solve = nullptr;   // [0] ||X||^2, [3] BF16 rounding term, [4], [5], [6] as above
+  double target = 0.0, margin = 0.0, margin_cal = 0.0;
+};
+cudaError_t launch_iterate_persistent_gated(const Launcher& L, const IterArgs& a,
+                                            const SolveGate& g, void* ws, size_t ws_bytes,
+                                            int* status, float* mon);
 
 // Several independent problems in cooperative launches ("waves" packed into the SMs, one class
 // of padded rank and rule per launch); problem i runs iters[i] iterations on blocks[i] blocks

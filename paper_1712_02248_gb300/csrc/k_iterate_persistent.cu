@@ -40,6 +40,15 @@
 //
 // If *done is set on entry (an earlier residual check reached the target) the kernel returns at
 // once. Every wait is bounded: on time-out the kernel latches NMF_ERR_TIMEOUT and all blocks leave.
+//
+// Gated launches (the solve's loop): the launch continues from the iteration count left in
+// solve[6] and runs until an exact residual check is due. At every residual_every-th iteration
+// each block forms the monitor's estimate of the relative error from the sums (the same values
+// in every block, so every block takes the same decision) and compares it with the target as
+// the solve's gate does; the last iteration of the budget is always checked. The launch then
+// stops, leaving the count in solve[6], the estimate in solve[4] and the gate flag set, for the
+// exact residual and the decision that follow it in the stream. Checks the monitor rules out
+// cost a few microseconds inside the kernel instead of a return to the host and a relaunch.
 #include <algorithm>
 #include <vector>
 
@@ -471,8 +480,8 @@ __device__ __forceinline__ void update_rows(float (&v)[R][RP / NG], float (&s)[R
 // The whole run for one problem, executed by `G` co-resident blocks of which this is block
 // `bid` (all blocks of a problem call it with the same arguments).
 template <int RP, int RULE, int GA, int RA, int GB, int RC>
-__device__ __forceinline__ void iterate_body(const PArgs& a, const unsigned bid, const unsigned G,
-                                             float* sh) {
+__device__ __forceinline__ void iterate_body(const PArgs& a, const SolveGate& g,
+                                             const unsigned bid, const unsigned G, float* sh) {
   constexpr int CA = RP / GA, CBn = RP / GB;
   const int r = a.r, ell = a.ell, t = threadIdx.x;
   const int LQ = lq_of(ell), LS = lsx_of(ell);
@@ -499,8 +508,39 @@ __device__ __forceinline__ void iterate_body(const PArgs& a, const unsigned bid,
   const bool normalize = (RULE == 0);
   const bool reg = !(a.alpha == 0.f && a.beta == 0.f);
 
-  if (*reinterpret_cast<const volatile int*>(a.done)) return;   // the solve has converged
+  const bool gated = g.every > 0;
+  // iterations of this launch: a.iters, or (gated) what the budget leaves after solve[6]
+  const int start =
+      gated ? static_cast<int>(*reinterpret_cast<const volatile double*>(g.solve + 6)) : 0;
+  const int n_it = gated ? g.total - start : a.iters;
+  if (*reinterpret_cast<const volatile int*>(a.done) || n_it <= 0) {   // converged, or done
+    if (gated && bid == 0 && t == 0) g.flags[1] = 0;
+    return;
+  }
   unsigned epoch = 0;
+  __shared__ int gate_sh;
+  __shared__ double est_sh;
+  // monitor terms of the iteration whose sums sit in buffers phm: the cross term and
+  // <W^T W, H H^T> for the normalised W; every thread of the block gets both (fixed-order sums)
+  auto monitor = [&](int phm, float& cross, float& quad) {
+    const float* accA_r = a.accA + phm * kCopies * EA;
+    const float* accB_r = a.accB + phm * kCopies * EB;
+    float q2 = 0.f;
+    for (int e = t; e < RP * RP; e += kNT) {
+      const int p = e / RP, q = e - p * RP;
+      const float gww = acc_read(accA_r, EA, (LQ + p) * RP + q) / (sc[p] * sc[q]);
+      q2 = fmaf(gww, acc_read(accB_r, EB, p * (LQ + RP) + LQ + q), q2);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) q2 += __shfl_xor_sync(0xffffffffu, q2, o);
+    if ((t & 31) == 0) wred[t >> 5] = q2;
+    __syncthreads();
+    float sum = 0.f;
+    for (int wI = 0; wI < kNT / 32; ++wI) sum += wred[wI];
+    __syncthreads();
+    cross = acc_read(accB_r, EB, RP * (LQ + RP));
+    quad = sum;
+  };
 
   // ---- stage the slice (zero-padded) and the factors
   for (int j = t; j < RP; j += kNT) {
@@ -533,12 +573,11 @@ __device__ __forceinline__ void iterate_body(const PArgs& a, const unsigned bid,
               a.accB + (1 * kCopies + bid % kCopies) * EB);
   if (!grid_sync(a.bar, G, epoch, a.status, a.abort_flag, a.wait_cycles)) return;
 
-  for (int it = 0; it < a.iters; ++it) {
-    const int ph = it & 1, pr = ph ^ 1;
+  int ran = n_it;
+  for (int step = 0; step < n_it; ++step) {
+    const int ph = step & 1, pr = ph ^ 1;
+    const int it = start + step;   // iterations before this one
     // ================= phase A: rows of W
-    for (int64_t e = static_cast<int64_t>(bid) * kNT + t; e < kCopies * EA;
-         e += static_cast<int64_t>(G) * kNT)
-      a.accA[pr * kCopies * EA + e] = 0.f;
     {
       const float* accB_r = a.accB + pr * kCopies * EB;
       for (int e = t; e < RP * LQ; e += kNT) {
@@ -631,9 +670,14 @@ __device__ __forceinline__ void iterate_body(const PArgs& a, const unsigned bid,
     if (!grid_sync(a.bar, G, epoch, a.status, a.abort_flag, a.wait_cycles)) return;
 
     // ================= phase B: columns of H
+    // the previous iteration's sums are read for the last time in phase A (and by a gated
+    // launch's check after it): clear them for the next iteration
     for (int64_t e = static_cast<int64_t>(bid) * kNT + t; e < kCopies * EB;
          e += static_cast<int64_t>(G) * kNT)
       a.accB[pr * kCopies * EB + e] = 0.f;
+    for (int64_t e = static_cast<int64_t>(bid) * kNT + t; e < kCopies * EA;
+         e += static_cast<int64_t>(G) * kNT)
+      a.accA[pr * kCopies * EA + e] = 0.f;
     {
       const float* accA_r = a.accA + ph * kCopies * EA;
       for (int j = t; j < RP; j += kNT) {
@@ -740,31 +784,48 @@ __device__ __forceinline__ void iterate_body(const PArgs& a, const unsigned bid,
       atomicAdd(&accB_w[RP * (LQ + RP)], csum);
     }
     if (!grid_sync(a.bar, G, epoch, a.status, a.abort_flag, a.wait_cycles)) return;
+    if (gated && ((it + 1) % g.every == 0 || it + 1 == g.total)) {
+      // the solve's gate on the monitor, in every block; the sums of buffers ph stay intact
+      // until phase B of the next iteration, past a grid barrier
+      float cross, quad;
+      monitor(ph, cross, quad);
+      if (t == 0) {
+        const double x2 = g.solve[0];
+        const double e2 =
+            x2 - 2.0 * (static_cast<double>(cross) + g.solve[3]) + static_cast<double>(quad);
+        const double est = x2 > 0.0 ? sqrt(fmax(e2, 0.0) / x2) : 0.0;
+        int check = 1;
+        if (it + 1 < g.total && g.target > 0.0) {
+          const double cal = g.solve[5];
+          check = cal > 0.0 ? (est * cal <= g.target * (1.0 + g.margin_cal))
+                            : (est <= g.target * (1.0 + g.margin));
+        }
+        gate_sh = check;
+        est_sh = est;
+      }
+      __syncthreads();
+      if (gate_sh) {
+        ran = step + 1;
+        break;
+      }
+    }
   }
   // the last iteration's monitor terms: cross, and <W^T W, H H^T> for the normalised W
-  if (bid == 0 && a.iters > 0) {
-    const int ph = (a.iters - 1) & 1;
-    const float* accA_r = a.accA + ph * kCopies * EA;
-    const float* accB_r = a.accB + ph * kCopies * EB;
-    float q2 = 0.f;
-    for (int e = t; e < RP * RP; e += kNT) {
-      const int p = e / RP, q = e - p * RP;
-      const float gww = acc_read(accA_r, EA, (LQ + p) * RP + q) / (sc[p] * sc[q]);
-      q2 = fmaf(gww, acc_read(accB_r, EB, p * (LQ + RP) + LQ + q), q2);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) q2 += __shfl_xor_sync(0xffffffffu, q2, o);
-    if ((t & 31) == 0) wred[t >> 5] = q2;
-    __syncthreads();
+  if (bid == 0) {
+    float cross, quad;
+    monitor((ran - 1) & 1, cross, quad);
     if (t == 0) {
-      float s = 0.f;
-      for (int wI = 0; wI < kNT / 32; ++wI) s += wred[wI];
-      a.mon[0] = acc_read(accB_r, EB, RP * (LQ + RP));
-      a.mon[1] = s;
+      a.mon[0] = cross;
+      a.mon[1] = quad;
+      if (gated) {
+        g.solve[4] = est_sh;
+        g.solve[6] = static_cast<double>(start + ran);
+        g.flags[1] = 1;
+      }
     }
   }
   // write back: W normalised by the last s_j, H
-  if (a.iters > 0) {
+  {
     for (int e = t; e < nrows * r; e += kNT) {
       const int i = e / r, j = e - i * r;
       const float v = Ws[i * RP + j];
@@ -790,9 +851,9 @@ template <> struct Lanes<32> { static constexpr int GA = 2, RA = 1, GB = 2, RC =
 template <> struct Lanes<48> { static constexpr int GA = 4, RA = 1, GB = 4, RC = 1; };
 
 template <int RP, int RULE, int GA, int RA, int GB, int RC>
-__global__ void __launch_bounds__(kNT, 1) iterate_persistent_kernel(PArgs a) {
+__global__ void __launch_bounds__(kNT, 1) iterate_persistent_kernel(PArgs a, SolveGate g) {
   extern __shared__ __align__(16) float sh[];
-  iterate_body<RP, RULE, GA, RA, GB, RC>(a, blockIdx.x, gridDim.x, sh);
+  iterate_body<RP, RULE, GA, RA, GB, RC>(a, g, blockIdx.x, gridDim.x, sh);
 }
 
 // Several independent problems in one cooperative launch: blocks [start[p], start[p + 1]) run
@@ -814,8 +875,8 @@ __global__ void __launch_bounds__(kNT, 1) iterate_multi_kernel(const __grid_cons
     else hi = mid;
   }
   const PArgs a = M.p[lo];
-  iterate_body<RP, RULE, GA, RA, GB, RC>(a, blockIdx.x - M.start[lo], M.start[lo + 1] - M.start[lo],
-                                         sh);
+  iterate_body<RP, RULE, GA, RA, GB, RC>(a, SolveGate{}, blockIdx.x - M.start[lo],
+                                         M.start[lo + 1] - M.start[lo], sh);
 }
 
 size_t smem_floats(int RP, int ell, int RB, int CB) {
@@ -828,7 +889,7 @@ int rp_of(int r) { return r <= 8 ? 8 : r <= 16 ? 16 : r <= 24 ? 24 : r <= 32 ? 3
 
 template <int RP, int RULE, int GA = Lanes<RP>::GA, int RA = Lanes<RP>::RA,
           int GB = Lanes<RP>::GB, int RC = Lanes<RP>::RC>
-cudaError_t launch(const Launcher& L, PArgs& a, int grid) {
+cudaError_t launch(const Launcher& L, PArgs& a, SolveGate& g, int grid) {
   auto k = iterate_persistent_kernel<RP, RULE, GA, RA, GB, RC>;
   const size_t smem = sizeof(float) * smem_floats(RP, a.ell, a.RB, a.CB);
   cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -838,7 +899,7 @@ cudaError_t launch(const Launcher& L, PArgs& a, int grid) {
   if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kNT, smem)) != cudaSuccess)
     return err;
   if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
-  void* args[] = {&a};
+  void* args[] = {&a, &g};
   err = cudaLaunchCooperativeKernel(reinterpret_cast<void*>(k), dim3(grid), dim3(kNT), args, smem,
                                     L.stream);
   L.count();
@@ -869,16 +930,16 @@ bool iterate_persistent_supported(int64_t m, int64_t n, int r, int ell) {
          220 * 1024;
 }
 
-cudaError_t launch_iterate_persistent(const Launcher& L, const IterArgs& ia, int iters, void* ws,
-                                      size_t ws_bytes, int* status, float* mon, const int* done) {
-  if (ws_bytes < iterate_persistent_ws_bytes(ia.r, ia.ell)) return cudaErrorInvalidValue;
-  if (!iterate_persistent_supported(ia.m, ia.n, ia.r, ia.ell)) return cudaErrorInvalidValue;
-  if (iters <= 0) return cudaSuccess;
+namespace {
+
+// Arguments, cleared sums and the launch of one persistent run (iters, or the gate in a).
+cudaError_t run_persistent(const Launcher& L, const IterArgs& ia, int iters, void* ws,
+                           int* status, float* mon, const int* done, SolveGate g) {
+  PArgs a;
   char* p = static_cast<char*>(ws);
   const int RP = rp_of(ia.r), LQ = lq_of(ia.ell);
   const size_t ea = ea_size(RP, LQ), eb = eb_size(RP, LQ);
   const int grid = num_sms();
-  PArgs a;
   a.m = ia.m;
   a.n = ia.n;
   a.r = ia.r;
@@ -911,12 +972,31 @@ cudaError_t launch_iterate_persistent(const Launcher& L, const IterArgs& ia, int
   a.CB = static_cast<int>((ia.n + grid - 1) / grid);
   const bool mu = ia.rule != 0;
   switch (RP) {
-    case 8: return mu ? launch<8, 1>(L, a, grid) : launch<8, 0>(L, a, grid);
-    case 16: return mu ? launch<16, 1>(L, a, grid) : launch<16, 0>(L, a, grid);
-    case 24: return mu ? launch<24, 1>(L, a, grid) : launch<24, 0>(L, a, grid);
-    case 32: return mu ? launch<32, 1>(L, a, grid) : launch<32, 0>(L, a, grid);
-    default: return mu ? launch<48, 1>(L, a, grid) : launch<48, 0>(L, a, grid);
+    case 8: return mu ? launch<8, 1>(L, a, g, grid) : launch<8, 0>(L, a, g, grid);
+    case 16: return mu ? launch<16, 1>(L, a, g, grid) : launch<16, 0>(L, a, g, grid);
+    case 24: return mu ? launch<24, 1>(L, a, g, grid) : launch<24, 0>(L, a, g, grid);
+    case 32: return mu ? launch<32, 1>(L, a, g, grid) : launch<32, 0>(L, a, g, grid);
+    default: return mu ? launch<48, 1>(L, a, g, grid) : launch<48, 0>(L, a, g, grid);
   }
+}
+
+}  // namespace
+
+cudaError_t launch_iterate_persistent(const Launcher& L, const IterArgs& ia, int iters, void* ws,
+                                      size_t ws_bytes, int* status, float* mon, const int* done) {
+  if (ws_bytes < iterate_persistent_ws_bytes(ia.r, ia.ell)) return cudaErrorInvalidValue;
+  if (!iterate_persistent_supported(ia.m, ia.n, ia.r, ia.ell)) return cudaErrorInvalidValue;
+  if (iters <= 0) return cudaSuccess;
+  return run_persistent(L, ia, iters, ws, status, mon, done, SolveGate{});
+}
+
+cudaError_t launch_iterate_persistent_gated(const Launcher& L, const IterArgs& ia,
+                                            const SolveGate& g, void* ws, size_t ws_bytes,
+                                            int* status, float* mon) {
+  if (ws_bytes < iterate_persistent_ws_bytes(ia.r, ia.ell)) return cudaErrorInvalidValue;
+  if (!iterate_persistent_supported(ia.m, ia.n, ia.r, ia.ell)) return cudaErrorInvalidValue;
+  if (g.total <= 0 || g.every <= 0 || !g.flags || !g.solve) return cudaErrorInvalidValue;
+  return run_persistent(L, ia, 0, ws, status, mon, g.flags, g);
 }
 
 // ---------------------------------------------------------------- several problems at once

@@ -413,10 +413,9 @@ nmf_status compress_impl(nmf_ctx* ctx, const nmf_params* p, const void* X, int64
   return NMF_OK;
 }
 
-nmf_status iterate_impl(nmf_ctx* ctx, const nmf_params* p, const float* QL, const float* QR,
-                        const float* Xhat, const float* Xchk, float* W, float* H, int iters,
-                        Arena a, const int* done = nullptr) {
-  if (p->r > 64) return fail(ctx, NMF_ERR_UNSUPPORTED, "iterations support r <= 64");
+nmfrp::IterArgs iter_args(const nmf_ctx* ctx, const nmf_params* p, const float* QL,
+                          const float* QR, const float* Xhat, const float* Xchk, float* W,
+                          float* H) {
   nmfrp::IterArgs ia;
   ia.m = p->m;
   ia.n = p->n;
@@ -433,6 +432,14 @@ nmf_status iterate_impl(nmf_ctx* ctx, const nmf_params* p, const float* QL, cons
   ia.W = W;
   ia.H = H;
   ia.wait_cycles = ctx->wait_cycles;
+  return ia;
+}
+
+nmf_status iterate_impl(nmf_ctx* ctx, const nmf_params* p, const float* QL, const float* QR,
+                        const float* Xhat, const float* Xchk, float* W, float* H, int iters,
+                        Arena a, const int* done = nullptr) {
+  if (p->r > 64) return fail(ctx, NMF_ERR_UNSUPPORTED, "iterations support r <= 64");
+  const nmfrp::IterArgs ia = iter_args(ctx, p, QL, QR, Xhat, Xchk, W, H);
   Phase ph(ctx, NMF_PHASE_ITERATE);
   size_t rest = 0;
   void* ws = a.rest(&rest);
@@ -534,6 +541,22 @@ __global__ void solve_decide_kernel(const double* res2, double target, int iters
   if (solve[4] > 0.0) solve[5] = rel / solve[4];
   flags[3] += 1;
   if (target > 0.0 && rel <= target) flags[0] = 1;
+}
+
+// The same after a check that the persistent kernel's own gate asked for (it stops there): the
+// iteration count is the one it left in solve[6], `done` is also raised once the budget `total`
+// is spent, and the gate flag is cleared.
+__global__ void solve_decide_gated_kernel(const double* res2, double target, int total,
+                                          double* solve, int* flags) {
+  if (flags[0] || !flags[1]) return;
+  const double e2 = res2[0], x2 = solve[0];
+  const double rel = x2 > 0.0 ? sqrt(e2 / x2) : sqrt(e2);
+  solve[1] = rel;
+  solve[2] = solve[6];
+  if (solve[4] > 0.0) solve[5] = rel / solve[4];
+  flags[3] += 1;
+  flags[1] = 0;
+  if ((target > 0.0 && rel <= target) || solve[6] >= static_cast<double>(total)) flags[0] = 1;
 }
 
 // Workspace of the learned warm start for hidden width <= hidden_max: W_b, H_b, hscale, F_w, F_h,
@@ -1298,6 +1321,49 @@ nmf_status solve_impl(nmf_ctx* ctx, const nmf_params* p, int32_t init, const flo
   int done = 0, chunk = 0;
   bool stopped = false;
   nmf_status result = NMF_OK;
+  if (!staged && p->iters > 0) {
+    // The persistent kernel gates the checks itself and returns only when an exact residual is
+    // due; each launch resumes from the count it left on the device. The host queues one launch
+    // ahead (a launch after convergence does nothing) and stops once the device raises `done`.
+    if (p->r > 64) return fail(ctx, NMF_ERR_UNSUPPORTED, "iterations support r <= 64");
+    const nmfrp::IterArgs ia = iter_args(ctx, p, QL, QR, Xhat, Xchk, W, H);
+    nmfrp::SolveGate g;
+    g.total = p->iters;
+    g.every = every;
+    g.flags = ctx->d_flags;
+    g.solve = ctx->d_solve;
+    g.target = p->target_rel_err;
+    g.margin = margin;
+    g.margin_cal = margin_cal;
+    const int max_chunks = (p->iters + every - 1) / every + 2;
+    for (chunk = 0; chunk < max_chunks; ++chunk) {
+      {
+        Phase ph(ctx, NMF_PHASE_ITERATE);
+        NMF_CUDA(nmfrp::launch_iterate_persistent_gated(launcher(ctx), ia, g, ws, rest,
+                                                        ctx->d_status, ctx->d_mon),
+                 "iterate (persistent, gated)");
+      }
+      {
+        Phase ph(ctx, NMF_PHASE_RESIDUAL);
+        NMF_CUDA(nmfrp::launch_residual(launcher(ctx), X, m, n, ldx, W, H, p->r, ctx->d_res, ws,
+                                        rest, ctx->d_flags + 1, ctx->d_status),
+                 "residual");
+      }
+      solve_decide_gated_kernel<<<1, 1, 0, ctx->stream>>>(ctx->d_res, p->target_rel_err,
+                                                          p->iters, ctx->d_solve, ctx->d_flags);
+      ctx->launches += 1;
+      NMF_CUDA(cudaGetLastError(), "solve loop");
+      NMF_CUDA(cudaMemcpyAsync(ctx->h_done + (chunk & 1), ctx->d_flags, sizeof(int),
+                               cudaMemcpyDeviceToHost, ctx->stream),
+               "done copy");
+      NMF_CUDA(cudaEventRecord(ev[chunk & 1], ctx->stream), "event");
+      if (chunk >= 1) {
+        NMF_CUDA(cudaEventSynchronize(ev[(chunk - 1) & 1]), "event wait");
+        if (ctx->h_done[(chunk - 1) & 1]) break;
+      }
+    }
+    done = p->iters;   // the loop below does not run
+  }
   while (done < p->iters || (p->iters == 0 && chunk == 0)) {
     const int k = std::min(every, p->iters - done);
     if (k > 0 && (st = iterate_impl(ctx, p, QL, QR, Xhat, Xchk, W, H, k, a, ctx->d_flags)) != NMF_OK) {
