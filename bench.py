@@ -970,22 +970,24 @@ def main():
     dp_achieved = dp_bytes / (dp_ms / dp_n * 1e-3) / 1e9
     shares = {k: v[0] for k, v in phases.items() if v[1] > 0}
     dom = max(shares, key=shares.get)
-    # DRAM bytes of one iterate_persistent_kernel launch (10 iterations) from an ncu capture of
-    # the current kernel on this workload (profiles/iterate_persistent_kernel_dense_20000x5000_r20.md:
-    # 10.19 MB read, nothing written back within the launch): the slices are staged once a launch
-    it_traffic = 10.192896e6 if (m, n, r, ell) == (20000, 5000, 20, 40) else None
+    # DRAM bytes of one iterate_persistent_kernel launch from an ncu capture of the current
+    # kernel on this workload (profiles/iterate_persistent_kernel_dense_20000x5000_r20.md: 10.22 MB
+    # read, 6 KB written, for a launch of ~185 iterations and alike for one of ~32): the slices
+    # are staged once a launch, so the bytes do not grow with the iterations a gated launch runs
+    it_traffic = 10.221568e6 if (m, n, r, ell) == (20000, 5000, 20, 40) else None
     roofline = {"bound": "alu", "achieved": it_achieved, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": it_achieved / alu_peak, "traffic": it_traffic,
                 "kernel": "iterate_persistent_kernel (FastHALS-RP iterations)",
                 "peak_source": f"derived: {n_sms} SMs x 128 FP32 lanes x 2 FLOP x {sm_mhz:.0f} MHz",
                 "units": f"{flops_iter} FLOP per iteration x {iters_run} iterations",
+                "traffic_per": "launch (the slices are staged once a launch)",
                 "dominant_phase": dom,
                 "phase_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in phases.items()},
                 "phase_spans_per_step": {k: v[1] // args.steps for k, v in phases.items()}}
     # DRAM bytes of one BF16 pass launch at this workload from an ncu capture of the current
-    # kernel (profiles/dual_pass_tc_kernel_dense_20000x5000_l40_bf16.md: 207.92 MB read, 6.09 MB
+    # kernel (profiles/dual_pass_tc_kernel_dense_20000x5000_l40_bf16.md: 207.88 MB read, 6.00 MB
     # written: X and the operand copies read once)
-    dp_traffic = (207.92e6 + 6.09e6) if ((m, n, ell) == (20000, 5000, 40) and
+    dp_traffic = (207.88e6 + 6.00e6) if ((m, n, ell) == (20000, 5000, 40) and
                                          headline[0] == "bf16") else None
     roofline_hbm = {"bound": "hbm", "achieved": dp_achieved, "peak": hbm_peak, "unit": "GB/s",
                     "frac": dp_achieved / hbm_peak, "traffic": dp_traffic,
