@@ -198,7 +198,7 @@ nmf_status nmf_dual_pass(nmf_ctx* ctx, int32_t prec, const void* X, int64_t m, i
  * Thin QR of a tall FP32 matrix Y (rows x l, rows >= l): writes Q (rows x l, FP32, orthonormal
  * columns, the unique Q whose R has a positive diagonal; Section 3, Eq. 3.4-3.5). CholeskyQR2
  * (Fukaya et al. 2014): the Gram matrix Y^T Y, its factor and R^-1 are formed in float-float
- * arithmetic (about 44 significant bits) on the FP32 pipes; a non-positive pivot latches
+ * arithmetic (about 48 significant bits) on the FP32 pipes; a non-positive pivot latches
  * NMF_ERR_QR_BREAKDOWN. Q may alias Y.
  */
 nmf_status nmf_qr(nmf_ctx* ctx, const float* Y, int64_t rows, int32_t ell, float* Q);
@@ -440,8 +440,11 @@ nmf_status nmf_set_warmstart(nmf_ctx* ctx, int32_t hidden, int32_t r, const floa
  * is a check; with p->target_rel_err > 0 the solve stops at the first check whose exact relative
  * residual is <= the target, else after p->iters iterations. The exact residual of a check is
  * computed only when an error monitor built from the compressed data alone (||X||^2 -
- * 2 <W_tld^T X_hat, H> + <W^T W, H H^T>) is within 5 % of the target, and always for the last
- * check; the decision is taken on the device. With p->prec = BF16 the X passes read a BF16
+ * 2 <W_tld^T X_hat, H> + <W^T W, H H^T>) is within 5 % of the target before the first exact
+ * check, and within 0.2 % once scaled by the ratio exact / estimate of the last exact check;
+ * always for the last check. The decision is taken on the device: the persistent iteration
+ * kernel (r <= 48) applies it at every check point itself and returns only when an exact
+ * check is due. With p->prec = BF16 the X passes read a BF16
  * copy made in the workspace. W, H: in/out (read only for NMF_INIT_GIVEN). Synchronises the
  * stream. Outputs: *rel_err_host (the last exact relative residual), *iters_done_host
  * (iterations at that check; may be NULL).

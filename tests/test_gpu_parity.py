@@ -159,6 +159,38 @@ def test_qr_matches_oracle(lib, ctx, rows, ell):
     assert rel(Q, Qo) <= 1e-5
 
 
+def test_qr_at_condition_1e6_matches_oracle_where_fp32_cholesky_qr2_fails(lib, ctx):
+    """Singular values spread over six decades (condition ~1e6): the Gram matrix's condition
+    (~1e12) is beyond FP32 (2^-24 ~ 6e-8), so CholeskyQR2 with FP32 Grams loses orthogonality
+    or breaks down, while the float-float Gram, factor and first application (about 48
+    significant bits) give the unique Q to FP32 accuracy. The FP32 variant is formed here in
+    numpy float32 to show that the case does separate the two."""
+    rng = np.random.default_rng(77)
+    rows, ell = 20000, 40
+    U, _ = np.linalg.qr(rng.standard_normal((rows, ell)))
+    V, _ = np.linalg.qr(rng.standard_normal((ell, ell)))
+    Y = ((U * np.logspace(0, -6, ell)) @ V.T).astype(np.float32)
+    assert np.linalg.cond(Y.astype(np.float64)) > 5e5
+    Q = host(lib.nmf_qr(ctx, cu(Y)))
+    lib.nmf_sync(ctx)
+    Qo = O.qr_orthonormal(Y.astype(np.float64))
+    assert np.abs(Q.T @ Q - np.eye(ell)).max() <= 1e-5
+    assert rel(Q, Qo) <= 1e-5
+
+    def chol_qr_fp32(A):
+        G = (A.T @ A).astype(np.float32)
+        R = np.linalg.cholesky(G).T.astype(np.float32)
+        return np.linalg.solve(R.T, A.T).T.astype(np.float32)
+
+    try:
+        Q32 = chol_qr_fp32(chol_qr_fp32(Y))
+        fp32_err = float(np.abs(Q32.T.astype(np.float64) @ Q32 - np.eye(ell)).max())
+        fp32_err = fp32_err if np.isfinite(fp32_err) else np.inf
+    except np.linalg.LinAlgError:
+        fp32_err = np.inf
+    assert fp32_err > 1e-3
+
+
 def test_qr_breakdown_is_reported(lib, ctx):
     Y = np.random.default_rng(0).standard_normal((100, 8)).astype(np.float32)
     Y[:, 3] = 0.0
