@@ -69,7 +69,7 @@ cudaError_t launch_quantize_bf16(const Launcher& L, const float* X, int64_t m, i
                                  int64_t ldx, __nv_bfloat16* Xq, int64_t ldq);
 
 // The same copy plus ||X||^2 (into *x2_out) and <X - X_q, X> (into *corr_out), both FP64 on the
-// device; ws holds quantize_stats_ws_bytes() of block partials.
+// device (either pointer may be null); ws holds quantize_stats_ws_bytes() of block partials.
 size_t quantize_stats_ws_bytes();
 cudaError_t launch_quantize_bf16_stats(const Launcher& L, const float* X, int64_t m, int64_t n,
                                        int64_t ldx, __nv_bfloat16* Xq, int64_t ldq, double* x2_out,

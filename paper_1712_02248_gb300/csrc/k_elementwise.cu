@@ -297,9 +297,9 @@ __global__ void stats_final_kernel(const double* __restrict__ part, int nparts,
     a += __shfl_xor_sync(0xffffffffu, a, o);
     b += __shfl_xor_sync(0xffffffffu, b, o);
   }
-  if (threadIdx.x == 0) {
-    *x2_out = a;
-    *corr_out = b;
+  if (threadIdx.x == 0) {   // either destination may be null (that sum is not wanted)
+    if (x2_out) *x2_out = a;
+    if (corr_out) *corr_out = b;
   }
 }
 
