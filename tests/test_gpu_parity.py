@@ -508,6 +508,28 @@ def test_solve_stops_at_target(lib, ctx):
     assert relg <= 0.5 and it < 400 and it % 10 == 0
 
 
+def test_solve_budget_not_a_multiple_of_the_check_interval(lib, ctx):
+    """25 iterations with a check every 10 and no target: the persistent kernel stops for the
+    checks at 10 and 20 and for the forced one at the end of the budget (25), resuming from the
+    count it left on the device; every check is exact (no target), the reported iterations are
+    the budget, and W, H are the factors that last check measured. The same run as one launch
+    (a single check at the end) lands on the same error up to the FP32 rounding that the
+    relaunches reorder."""
+    pr = inputs.random_problem(12, 700, 500, 6, 14)
+    X = cu(pr.X)
+    p = lib.params(700, 500, 6, 14, power_iters=2, iters=25, residual_every=10, seed=2)
+    W, H = cu(pr.W0), cu(pr.H0)
+    e, it = lib.nmf_solve(ctx, p, X, W, H)
+    its, checks = lib.nmf_last_solve_info(ctx)
+    assert it == 25 and its == 25 and checks == 3
+    assert abs(lib.nmf_residual(ctx, p, X, W, H)[0] - e) <= 1e-6 * e
+    p1 = lib.params(700, 500, 6, 14, power_iters=2, iters=25, residual_every=0, seed=2)
+    W1, H1 = cu(pr.W0), cu(pr.H0)
+    e1, it1 = lib.nmf_solve(ctx, p1, X, W1, H1)
+    assert it1 == 25 and lib.nmf_last_solve_info(ctx)[1] == 1
+    assert abs(e - e1) <= 1e-3 * e1
+
+
 def test_invalid_arguments_are_rejected(lib, ctx):
     X = torch.zeros((10, 10), device=DEV)
     with pytest.raises(lib.NmfError) as e:
