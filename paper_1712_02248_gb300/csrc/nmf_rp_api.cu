@@ -236,14 +236,6 @@ nmf_status dual(nmf_ctx* ctx, const void* X, int prec, int64_t m, int64_t n, int
   return NMF_OK;
 }
 
-nmf_status qr(nmf_ctx* ctx, float* Y, int64_t rows, int ell, Arena a) {
-  Phase ph(ctx, NMF_PHASE_QR);
-  size_t rest = 0;
-  void* ws = a.rest(&rest);
-  NMF_CUDA(nmfrp::launch_qr(launcher(ctx), Y, rows, ell, Y, ws, rest, ctx->d_status), "qr");
-  return NMF_OK;
-}
-
 // QR of the m-side and the n-side output of one pass together (both chains of the sketch).
 nmf_status qr2(nmf_ctx* ctx, float* Ym, int64_t m, float* Yn, int64_t n, int ell, Arena a) {
   Phase ph(ctx, NMF_PHASE_QR);
@@ -1319,7 +1311,6 @@ nmf_status solve_impl(nmf_ctx* ctx, const nmf_params* p, int32_t init, const flo
   cudaEvent_t ev[2] = {pool_event(ctx), pool_event(ctx)};
   if (!ev[0] || !ev[1]) return fail(ctx, NMF_ERR_CUDA, "event creation");
   int done = 0, chunk = 0;
-  bool stopped = false;
   nmf_status result = NMF_OK;
   if (!staged && p->iters > 0) {
     // The persistent kernel gates the checks itself and returns only when an exact residual is
@@ -1395,15 +1386,11 @@ nmf_status solve_impl(nmf_ctx* ctx, const nmf_params* p, int32_t init, const flo
     const int look = staged ? chunk : chunk - 1;
     if (look >= 0) {
       NMF_CUDA(cudaEventSynchronize(ev[look & 1]), "event wait");
-      if (ctx->h_done[look & 1]) {
-        stopped = true;
-        break;
-      }
+      if (ctx->h_done[look & 1]) break;
     }
     ++chunk;
     if (p->iters == 0) break;
   }
-  (void)stopped;
   ctx->pool.push_back(ev[0]);
   ctx->pool.push_back(ev[1]);
   if (result != NMF_OK) return result;
